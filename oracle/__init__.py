@@ -1,0 +1,194 @@
+"""Python access to the CPU oracle (oracle.c) through ctypes.
+
+TEST INFRASTRUCTURE ONLY: the tests, ``__graft_entry__.smoke()`` and the CPU
+baseline leg of ``bench.py`` use this module; the product never imports it.
+
+Every function takes and returns numpy float64 arrays and follows the passage
+of arXiv 2310.08344 named in oracle.c.  Status codes: 0 ok, 1 invalid
+argument, 2 out of memory, 4 no convergence within the point table,
+5 non-finite value.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import threading
+
+import numpy as np
+
+from . import build as _build
+
+OK, E_INVAL, E_NOMEM, E_NOCONV, E_NONFINITE = 0, 1, 2, 4, 5
+ADVDIFF, BURGERS = 0, 1
+
+_lib = None
+_lock = threading.Lock()
+_leja_cache: dict[int, np.ndarray] = {}
+
+_dp = C.POINTER(C.c_double)
+_ip = C.POINTER(C.c_int)
+
+
+def _p(a):
+    return a.ctypes.data_as(_dp) if a is not None else None
+
+
+def lib():
+    global _lib
+    with _lock:
+        if _lib is None:
+            path = _build.build()
+            L = C.CDLL(path)
+            L.or_phi.restype = C.c_double
+            L.or_phi.argtypes = [C.c_int, C.c_double]
+            L.or_qreal_mant_dig.restype = C.c_int
+            L.or_leja_points.argtypes = [C.c_int, _dp]
+            L.or_divdiff_values.argtypes = [C.c_int, _dp, _dp, _dp]
+            L.or_leja_coeffs.argtypes = [C.c_int, C.c_double, C.c_double, C.c_double, _dp, C.c_int, _dp]
+            L.or_apply_advdiff.argtypes = [C.c_int, C.c_int, C.c_double, C.c_double, _dp, _dp]
+            L.or_burgers_f.argtypes = [C.c_int, C.c_int, C.c_double, _dp, _dp]
+            L.or_burgers_J.argtypes = [C.c_int, C.c_int, C.c_double, _dp, _dp, _dp]
+            L.or_power_iteration.argtypes = [C.c_int, C.c_int, C.c_int, C.c_double, C.c_double, _dp, _dp,
+                                             C.c_int, _dp, _ip]
+            L.or_leja_phi.argtypes = [C.c_int, C.c_int, C.c_int, C.c_double, C.c_double, _dp, C.c_int, _dp,
+                                      C.c_double, C.c_double, C.c_double, C.c_double, C.c_double, _dp, C.c_int,
+                                      _dp, _ip]
+            L.or_ros_eu.argtypes = [C.c_int, C.c_int, C.c_int, C.c_double, C.c_double, _dp, C.c_double,
+                                    C.c_double, C.c_double, C.c_double, C.c_double, _dp, C.c_int, _dp, _ip]
+            L.or_exprb32.argtypes = [C.c_int, C.c_int, C.c_int, C.c_double, C.c_double, _dp, C.c_double,
+                                     C.c_double, C.c_double, C.c_double, C.c_double, _dp, C.c_int, _dp, _dp,
+                                     _dp, _ip]
+            _lib = L
+    return _lib
+
+
+def _f64(a):
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+def qreal_mant_dig() -> int:
+    return lib().or_qreal_mant_dig()
+
+
+def phi(l: int, z: float) -> float:
+    """phi_l(z), evaluated in binary128 and rounded to double."""
+    return lib().or_phi(l, z)
+
+
+GOLDEN_LEJA = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "tests", "golden",
+                           "leja_points_oracle_1000.txt")
+
+
+def leja_points(K: int) -> np.ndarray:
+    """The first K greedy Leja points on [-2, 2].
+
+    Computed by the oracle (an exhaustive search over all node intervals);
+    K <= 1000 is served from the table that tests/golden/make_golden.py wrote
+    with this same oracle, so that the O(K^3) search runs once.
+    """
+    if K in _leja_cache:
+        return _leja_cache[K].copy()
+    if K <= 1000 and os.path.exists(GOLDEN_LEJA):
+        tab = np.loadtxt(GOLDEN_LEJA, dtype=np.float64)
+        if tab.shape[0] >= K:
+            _leja_cache[K] = tab[:K].copy()
+            return tab[:K].copy()
+    return leja_points_compute(K)
+
+
+def leja_points_compute(K: int) -> np.ndarray:
+    """Run the oracle's greedy Leja search (slow for K in the hundreds)."""
+    xi = np.zeros(K)
+    st = lib().or_leja_points(K, _p(xi))
+    if st != OK:
+        raise RuntimeError(f"or_leja_points status {st}")
+    _leja_cache[K] = xi.copy()
+    return xi
+
+
+def divdiff_values(x, f) -> np.ndarray:
+    x, f = _f64(x), _f64(f)
+    d = np.zeros_like(x)
+    st = lib().or_divdiff_values(len(x), _p(x), _p(f), _p(d))
+    if st != OK:
+        raise RuntimeError(f"or_divdiff_values status {st}")
+    return d
+
+
+def leja_coeffs(l: int, h: float, c: float, gamma: float, xi) -> np.ndarray:
+    xi = _f64(xi)
+    d = np.zeros_like(xi)
+    st = lib().or_leja_coeffs(l, h, c, gamma, _p(xi), len(xi), _p(d))
+    if st != OK:
+        raise RuntimeError(f"or_leja_coeffs status {st}")
+    return d
+
+
+def apply_advdiff(nx, ny, nu, a, v) -> np.ndarray:
+    v = _f64(v)
+    out = np.zeros_like(v)
+    lib().or_apply_advdiff(nx, ny, nu, a, _p(v), _p(out))
+    return out
+
+
+def burgers_f(nx, ny, nu, u) -> np.ndarray:
+    u = _f64(u)
+    out = np.zeros_like(u)
+    lib().or_burgers_f(nx, ny, nu, _p(u), _p(out))
+    return out
+
+
+def burgers_J(nx, ny, nu, u, v) -> np.ndarray:
+    u, v = _f64(u), _f64(v)
+    out = np.zeros_like(u)
+    lib().or_burgers_J(nx, ny, nu, _p(u), _p(v), _p(out))
+    return out
+
+
+def power_iteration(kind, nx, ny, nu, a, u, v0, max_iters=10):
+    v0 = _f64(v0)
+    u = _f64(u) if u is not None else None
+    rho = np.zeros(1)
+    it = C.c_int(0)
+    st = lib().or_power_iteration(kind, nx, ny, nu, a, _p(u), _p(v0), max_iters, _p(rho), C.byref(it))
+    return float(rho[0]), int(it.value), st
+
+
+def leja_phi(kind, nx, ny, nu, a, u, l, w, c, gamma, h, rtol, atol, xi):
+    w = _f64(w)
+    xi = _f64(xi)
+    u = _f64(u) if u is not None else None
+    out = np.zeros_like(w)
+    it = C.c_int(0)
+    st = lib().or_leja_phi(kind, nx, ny, nu, a, _p(u), l, _p(w), c, gamma, h, rtol, atol, _p(xi), len(xi),
+                           _p(out), C.byref(it))
+    return out, int(it.value), st
+
+
+def ros_eu(kind, nx, ny, nu, a, u, c, gamma, h, rtol, atol, xi):
+    u = _f64(u)
+    xi = _f64(xi)
+    out = np.zeros_like(u)
+    it = C.c_int(0)
+    st = lib().or_ros_eu(kind, nx, ny, nu, a, _p(u), c, gamma, h, rtol, atol, _p(xi), len(xi), _p(out),
+                         C.byref(it))
+    return out, int(it.value), st
+
+
+def exprb32(kind, nx, ny, nu, a, u, c, gamma, h, rtol, atol, xi):
+    u = _f64(u)
+    xi = _f64(xi)
+    lo = np.zeros_like(u)
+    hi = np.zeros_like(u)
+    err = np.zeros(1)
+    it = C.c_int(0)
+    st = lib().or_exprb32(kind, nx, ny, nu, a, _p(u), c, gamma, h, rtol, atol, _p(xi), len(xi), _p(lo), _p(hi),
+                          _p(err), C.byref(it))
+    return lo, hi, float(err[0]), int(it.value), st
+
+
+def spectral_interval(rho: float):
+    """c and gamma from a spectral-radius estimate: lambda = -1.05 rho,
+    c = lambda/2, gamma = -lambda/4 (Sec. 2.2, Listing 7)."""
+    lam = -1.05 * rho
+    return lam / 2.0, -lam / 4.0

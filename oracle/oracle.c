@@ -1,0 +1,463 @@
+/*
+ * CPU oracle for the Leja exponential-integrator hot path.
+ *
+ * TEST INFRASTRUCTURE ONLY.  Only the tests, the smoke check and the CPU
+ * baseline leg of the benchmark may load this file's library.  The product
+ * (the CUDA library under paper_2310_08344_gb300/) never calls it, shares no
+ * code, header, table or constant with it, and fails if its own extension is
+ * missing.
+ *
+ * Plain, slow, obviously correct: single-threaded loops in the order the
+ * paper states the algorithm, fp64 for vectors, IEEE binary128 for the scalar
+ * phi functions and the Newton divided differences.  Each function names the
+ * passage of Deka, Moriggl, Einkemmer, "LeXInt: GPU-accelerated exponential
+ * integrators package" (arXiv 2310.08344) that it follows.
+ *
+ * Readings where the paper is silent (stated again at each use):
+ *  - Leja points on [-2,2]: xi_0 = +2; later near-ties (log-products within
+ *    1e-12 relative) are broken toward the larger point.
+ *  - The interpolated function is f(xi) = phi_l(h (c + gamma xi)); the Newton
+ *    basis uses (A - c)/gamma - xi_m, which carries no h.
+ *  - Error estimate e_m = |d_m| * ||y_m||, stop when e_m <= rtol ||p_m|| + atol,
+ *    iters = m at the stop; ||x|| = ||x||_2 / sqrt(N).
+ *  - Iteration cap: K - 1 iterations for a table of K points, then NOCONV.
+ *  - Power iteration: w = Av, rho_k = ||w||/||v||, v <- w/||w||, stop at
+ *    max_iters or when |rho_k - rho_{k-1}| <= 1e-2 rho_k.
+ *  - The Jacobian action is the analytic linearisation of the stencil.
+ */
+#include <float.h>
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+
+#if LDBL_MANT_DIG == 113
+typedef long double qreal; /* IEEE binary128 on aarch64 Linux */
+#define QEXP expl
+#define QFABS fabsl
+#else
+#include <quadmath.h>
+typedef __float128 qreal; /* libquadmath on x86-64 */
+#define QEXP expq
+#define QFABS fabsq
+#endif
+
+enum { OR_OK = 0, OR_E_INVAL = 1, OR_E_NOMEM = 2, OR_E_NOCONV = 4, OR_E_NONFINITE = 5 };
+enum { OR_ADVDIFF = 0, OR_BURGERS = 1 };
+
+int or_qreal_mant_dig(void) {
+#if LDBL_MANT_DIG == 113
+  return LDBL_MANT_DIG;
+#else
+  return FLT128_MANT_DIG;
+#endif
+}
+
+/* ------------------------------------------------------------------------ */
+/* Leja points on [-2, 2]  (Sec. 2.1: the recursive Leja definition, with    */
+/* |z_0| the maximum modulus on the set; points are precomputed on [-2,2]).  */
+/* ------------------------------------------------------------------------ */
+
+static int cmp_double(const void* a, const void* b) {
+  double x = *(const double*)a, y = *(const double*)b;
+  return (x > y) - (x < y);
+}
+
+/* The maximiser of sum_k log|x - xi_k| inside the open interval (lo, hi)
+ * between two consecutive nodes.  It is the unique root of the derivative
+ * g(x) = sum_k 1/(x - xi_k), which falls from +inf to -inf on the interval.
+ * Newton steps, replaced by bisection whenever they leave the bracket. */
+static double interval_maximiser(const double* xi, int j, double lo, double hi) {
+  double x = 0.5 * (lo + hi);
+  for (int it = 0; it < 400; ++it) {
+    double g = 0.0, gp = 0.0;
+    for (int k = 0; k < j; ++k) {
+      double r = 1.0 / (x - xi[k]);
+      g += r;
+      gp -= r * r;
+    }
+    if (g == 0.0) break; /* exact critical point */
+    if (g > 0.0) lo = x; else hi = x;
+    double xn = x - g / gp;
+    if (!(xn > lo && xn < hi)) xn = 0.5 * (lo + hi);
+    if (fabs(xn - x) <= 2.0 * DBL_EPSILON * fabs(x) || hi - lo <= 4.0 * DBL_EPSILON * fabs(x)) {
+      x = xn;
+      break;
+    }
+    x = xn;
+  }
+  return x;
+}
+
+static double log_product(const double* xi, int j, double x) {
+  double s = 0.0;
+  for (int k = 0; k < j; ++k) s += log(fabs(x - xi[k]));
+  return s;
+}
+
+/* Greedy Leja sequence: xi_j maximises prod_{k<j} |x - xi_k| over [-2, 2].
+ * xi_0 = +2 (both ends have maximal modulus; the sign is a reading).
+ * xi_1 = -2 (|x - 2| is largest at the other end).  For j >= 2 both ends are
+ * nodes, so the maximum lies inside one of the intervals between consecutive
+ * nodes; every interval is searched.  Ties within 1e-12 (relative, in the
+ * log-product) go to the larger point.  Returns 0 on success. */
+int or_leja_points(int K, double* xi) {
+  if (K <= 0 || !xi) return OR_E_INVAL;
+  xi[0] = 2.0;
+  if (K > 1) xi[1] = -2.0;
+  if (K <= 2) return OR_OK;
+  double* sorted = (double*)malloc(sizeof(double) * (size_t)K);
+  double* cx = (double*)malloc(sizeof(double) * (size_t)K);
+  double* cl = (double*)malloc(sizeof(double) * (size_t)K);
+  if (!sorted || !cx || !cl) {
+    free(sorted); free(cx); free(cl);
+    return OR_E_NOMEM;
+  }
+  for (int j = 2; j < K; ++j) {
+    memcpy(sorted, xi, sizeof(double) * (size_t)j);
+    qsort(sorted, (size_t)j, sizeof(double), cmp_double);
+    double best = -INFINITY;
+    for (int q = 0; q + 1 < j; ++q) {
+      cx[q] = interval_maximiser(xi, j, sorted[q], sorted[q + 1]);
+      cl[q] = log_product(xi, j, cx[q]);
+      if (cl[q] > best) best = cl[q];
+    }
+    double tie = 1e-12 * fmax(1.0, fabs(best));
+    double pick = -INFINITY;
+    for (int q = 0; q + 1 < j; ++q)
+      if (cl[q] >= best - tie && cx[q] > pick) pick = cx[q];
+    xi[j] = pick;
+  }
+  free(sorted); free(cx); free(cl);
+  return OR_OK;
+}
+
+/* ------------------------------------------------------------------------ */
+/* phi functions (Sec. 1): phi_0 = exp, phi_{l+1}(z) = (phi_l(z) - 1/l!)/z.  */
+/* ------------------------------------------------------------------------ */
+
+static qreal q_factorial(int n) {
+  qreal f = 1;
+  for (int k = 2; k <= n; ++k) f *= (qreal)k;
+  return f;
+}
+
+/* phi_l(z) in binary128.  |z| < 1: the power series sum_k z^k/(k+l)!, which
+ * is the recursion solved for small z.  Otherwise the recursion itself,
+ * starting from exp(z). */
+static qreal q_phi(int l, qreal z) {
+  if (QFABS(z) < 1) {
+    qreal term = 1 / q_factorial(l), sum = term;
+    for (int k = 1; k < 400; ++k) {
+      term *= z / (qreal)(k + l);
+      sum += term;
+      if (QFABS(term) <= (qreal)1e-40 * QFABS(sum)) break;
+    }
+    return sum;
+  }
+  qreal phi = QEXP(z);
+  qreal inv_fact = 1; /* 1/k! */
+  for (int k = 0; k < l; ++k) {
+    phi = (phi - inv_fact) / z;
+    inv_fact /= (qreal)(k + 1);
+  }
+  return phi;
+}
+
+double or_phi(int l, double z) { return (double)q_phi(l, (qreal)z); }
+
+/* ------------------------------------------------------------------------ */
+/* Newton divided differences (Sec. 2.1, Eq. 2: the coefficients d_m of the  */
+/* Newton form at the Leja points).  Row-wise recursion in binary128:        */
+/* d_j <- f_j, then d_j <- (d_j - d_k)/(x_j - x_k) for k = 0..j-1.           */
+/* ------------------------------------------------------------------------ */
+
+static void q_divdiff(int n, const qreal* x, qreal* d) {
+  for (int j = 1; j < n; ++j)
+    for (int k = 0; k < j; ++k) d[j] = (d[j] - d[k]) / (x[j] - x[k]);
+}
+
+/* Divided differences of given values f at nodes x (both double). */
+int or_divdiff_values(int n, const double* x, const double* f, double* d) {
+  if (n <= 0) return OR_E_INVAL;
+  qreal* qx = (qreal*)malloc(sizeof(qreal) * (size_t)n);
+  qreal* qd = (qreal*)malloc(sizeof(qreal) * (size_t)n);
+  if (!qx || !qd) { free(qx); free(qd); return OR_E_NOMEM; }
+  for (int j = 0; j < n; ++j) { qx[j] = x[j]; qd[j] = f[j]; }
+  q_divdiff(n, qx, qd);
+  for (int j = 0; j < n; ++j) d[j] = (double)qd[j];
+  free(qx); free(qd);
+  return OR_OK;
+}
+
+/* d_j = f[xi_0, ..., xi_j] for f(xi) = phi_l(h (c + gamma xi))  (Eq. 2 with
+ * exp replaced by phi_l; the interpolation variable is xi in [-2, 2]). */
+int or_leja_coeffs(int l, double h, double c, double gamma, const double* xi, int K, double* d) {
+  if (K <= 0 || l < 0) return OR_E_INVAL;
+  qreal* qx = (qreal*)malloc(sizeof(qreal) * (size_t)K);
+  qreal* qd = (qreal*)malloc(sizeof(qreal) * (size_t)K);
+  if (!qx || !qd) { free(qx); free(qd); return OR_E_NOMEM; }
+  for (int j = 0; j < K; ++j) {
+    qx[j] = xi[j];
+    qd[j] = q_phi(l, (qreal)h * ((qreal)c + (qreal)gamma * qx[j]));
+  }
+  q_divdiff(K, qx, qd);
+  for (int j = 0; j < K; ++j) d[j] = (double)qd[j];
+  free(qx); free(qd);
+  return OR_OK;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Operators on the periodic grid x_i = i/nx, y_j = j/ny, index j*nx + i.    */
+/* Second-order central differences for both the Laplacian and the gradient. */
+/* ------------------------------------------------------------------------ */
+
+static long idx(int nx, int i, int j) { return (long)j * nx + i; }
+static int wrap(int i, int n) { return i < 0 ? i + n : (i >= n ? i - n : i); }
+
+/* A v = nu (v_xx + v_yy) + a (v_x + v_y)   (the linear diffusion-advection
+ * operator of Sec. 3, Problem I, with this build's coefficients). */
+void or_apply_advdiff(int nx, int ny, double nu, double a, const double* v, double* out) {
+  double dx = 1.0 / nx, dy = 1.0 / ny;
+  for (int j = 0; j < ny; ++j) {
+    int jn = wrap(j + 1, ny), js = wrap(j - 1, ny);
+    for (int i = 0; i < nx; ++i) {
+      int ie = wrap(i + 1, nx), iw = wrap(i - 1, nx);
+      double vc = v[idx(nx, i, j)];
+      double ve = v[idx(nx, ie, j)], vw = v[idx(nx, iw, j)];
+      double vn = v[idx(nx, i, jn)], vs = v[idx(nx, i, js)];
+      double lap = (ve - 2.0 * vc + vw) / (dx * dx) + (vn - 2.0 * vc + vs) / (dy * dy);
+      double grad = (ve - vw) / (2.0 * dx) + (vn - vs) / (2.0 * dy);
+      out[idx(nx, i, j)] = nu * lap + a * grad;
+    }
+  }
+}
+
+/* D v = v_x + v_y by central differences. */
+static void central_sum_grad(int nx, int ny, const double* v, double* out) {
+  double dx = 1.0 / nx, dy = 1.0 / ny;
+  for (int j = 0; j < ny; ++j) {
+    int jn = wrap(j + 1, ny), js = wrap(j - 1, ny);
+    for (int i = 0; i < nx; ++i) {
+      int ie = wrap(i + 1, nx), iw = wrap(i - 1, nx);
+      out[idx(nx, i, j)] = (v[idx(nx, ie, j)] - v[idx(nx, iw, j)]) / (2.0 * dx) +
+                           (v[idx(nx, i, jn)] - v[idx(nx, i, js)]) / (2.0 * dy);
+    }
+  }
+}
+
+/* f(u) = nu (u_xx + u_yy) - u (u_x + u_y)   (viscous Burgers). */
+void or_burgers_f(int nx, int ny, double nu, const double* u, double* out) {
+  long n = (long)nx * ny;
+  double* du = (double*)malloc(sizeof(double) * (size_t)n);
+  or_apply_advdiff(nx, ny, nu, 0.0, u, out);
+  central_sum_grad(nx, ny, u, du);
+  for (long k = 0; k < n; ++k) out[k] = out[k] - u[k] * du[k];
+  free(du);
+}
+
+/* J(u) v = nu (v_xx + v_yy) - v (u_x + u_y) - u (v_x + v_y): the exact
+ * derivative of or_burgers_f at u applied to v (the paper uses finite
+ * differences for this action, Sec. 2.3; the analytic form is the reading). */
+void or_burgers_J(int nx, int ny, double nu, const double* u, const double* v, double* out) {
+  long n = (long)nx * ny;
+  double* du = (double*)malloc(sizeof(double) * (size_t)n);
+  double* dv = (double*)malloc(sizeof(double) * (size_t)n);
+  or_apply_advdiff(nx, ny, nu, 0.0, v, out);
+  central_sum_grad(nx, ny, u, du);
+  central_sum_grad(nx, ny, v, dv);
+  for (long k = 0; k < n; ++k) out[k] = out[k] - v[k] * du[k] - u[k] * dv[k];
+  free(du);
+  free(dv);
+}
+
+/* The operator the Leja basis multiplies by: A for diffusion-advection,
+ * J(u) for Burgers. */
+typedef struct {
+  int kind, nx, ny;
+  double nu, a;
+  const double* u;
+} or_op;
+
+static void op_apply(const or_op* op, const double* v, double* out) {
+  if (op->kind == OR_BURGERS)
+    or_burgers_J(op->nx, op->ny, op->nu, op->u, v, out);
+  else
+    or_apply_advdiff(op->nx, op->ny, op->nu, op->a, v, out);
+}
+
+/* f(u): A u for diffusion-advection, the Burgers right-hand side otherwise. */
+static void op_rhs(const or_op* op, const double* u, double* out) {
+  if (op->kind == OR_BURGERS)
+    or_burgers_f(op->nx, op->ny, op->nu, u, out);
+  else
+    or_apply_advdiff(op->nx, op->ny, op->nu, op->a, u, out);
+}
+
+/* ||x|| = ||x||_2 / sqrt(N) (Sec. 2.2: l2 norm normalised to sqrt(N)). */
+static double nrm(const double* x, long n) {
+  double s = 0.0;
+  for (long k = 0; k < n; ++k) s += x[k] * x[k];
+  return sqrt(s / (double)n);
+}
+
+/* ------------------------------------------------------------------------ */
+/* Power iteration for the dominant eigenvalue modulus (Sec. 2, Listing 7).  */
+/* ------------------------------------------------------------------------ */
+
+int or_power_iteration(int kind, int nx, int ny, double nu, double a, const double* u,
+                       const double* v0, int max_iters, double* rho_out, int* iters_out) {
+  if (nx <= 0 || ny <= 0 || max_iters <= 0) return OR_E_INVAL;
+  or_op op = {kind, nx, ny, nu, a, u};
+  long n = (long)nx * ny;
+  double* v = (double*)malloc(sizeof(double) * (size_t)n);
+  double* w = (double*)malloc(sizeof(double) * (size_t)n);
+  if (!v || !w) { free(v); free(w); return OR_E_NOMEM; }
+  memcpy(v, v0, sizeof(double) * (size_t)n);
+  double rho = 0.0, rho_prev = 0.0;
+  int k;
+  for (k = 1; k <= max_iters; ++k) {
+    op_apply(&op, v, w);
+    double nw = nrm(w, n), nv = nrm(v, n);
+    rho = nw / nv;
+    for (long q = 0; q < n; ++q) v[q] = w[q] / nw;
+    if (k > 1 && fabs(rho - rho_prev) <= 1e-2 * rho) break;
+    rho_prev = rho;
+  }
+  if (k > max_iters) k = max_iters;
+  *rho_out = rho;
+  if (iters_out) *iters_out = k;
+  free(v);
+  free(w);
+  return isfinite(rho) ? OR_OK : OR_E_NONFINITE;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Leja interpolation of phi_l(h Op) w  (Sec. 2.1 Eq. 2; Sec. 2.2 and 2.3,   */
+/* the real_Leja_exp / real_Leja_phi_nl / real_Leja_phi interfaces).         */
+/*   y_0 = w, p_0 = d_0 w;                                                   */
+/*   y_{m+1} = ((Op - c)/gamma - xi_m) y_m,  p_{m+1} = p_m + d_{m+1} y_{m+1}; */
+/*   stop when |d_{m+1}| ||y_{m+1}|| <= rtol ||p_{m+1}|| + atol.             */
+/* ------------------------------------------------------------------------ */
+
+static int leja_phi_core(const or_op* op, int l, const double* w, double c, double gamma,
+                         double h, double rtol, double atol, const double* xi, int K,
+                         double* out, int* iters) {
+  long n = (long)op->nx * op->ny;
+  if (K < 2) return OR_E_INVAL;
+  double* d = (double*)malloc(sizeof(double) * (size_t)K);
+  double* y = (double*)malloc(sizeof(double) * (size_t)n);
+  double* t = (double*)malloc(sizeof(double) * (size_t)n);
+  if (!d || !y || !t) { free(d); free(y); free(t); return OR_E_NOMEM; }
+  or_leja_coeffs(l, h, c, gamma, xi, K, d);
+  for (long q = 0; q < n; ++q) {
+    y[q] = w[q];
+    out[q] = d[0] * w[q];
+  }
+  int status = OR_E_NOCONV;
+  *iters = K - 1;
+  for (int m = 0; m + 1 < K; ++m) {
+    op_apply(op, y, t);
+    for (long q = 0; q < n; ++q) y[q] = (t[q] - c * y[q]) / gamma - xi[m] * y[q];
+    for (long q = 0; q < n; ++q) out[q] = out[q] + d[m + 1] * y[q];
+    double e = fabs(d[m + 1]) * nrm(y, n);
+    double pn = nrm(out, n);
+    if (!isfinite(e) || !isfinite(pn)) {
+      *iters = m + 1;
+      status = OR_E_NONFINITE;
+      break;
+    }
+    if (e <= rtol * pn + atol) {
+      *iters = m + 1;
+      status = OR_OK;
+      break;
+    }
+  }
+  free(d);
+  free(y);
+  free(t);
+  return status;
+}
+
+int or_leja_phi(int kind, int nx, int ny, double nu, double a, const double* u, int l,
+                const double* w, double c, double gamma, double h, double rtol, double atol,
+                const double* xi, int K, double* out, int* iters) {
+  if (nx <= 0 || ny <= 0 || l < 0 || gamma == 0.0) return OR_E_INVAL;
+  or_op op = {kind, nx, ny, nu, a, u};
+  return leja_phi_core(&op, l, w, c, gamma, h, rtol, atol, xi, K, out, iters);
+}
+
+/* ------------------------------------------------------------------------ */
+/* Exponential Rosenbrock-Euler (Sec. 2.3, Listing 12):                      */
+/*   u+ = u + phi_1(h J(u)) h f(u).                                          */
+/* ------------------------------------------------------------------------ */
+
+int or_ros_eu(int kind, int nx, int ny, double nu, double a, const double* u, double c,
+              double gamma, double h, double rtol, double atol, const double* xi, int K,
+              double* u_out, int* iters) {
+  if (nx <= 0 || ny <= 0) return OR_E_INVAL;
+  or_op op = {kind, nx, ny, nu, a, u};
+  long n = (long)nx * ny;
+  double* f_u = (double*)malloc(sizeof(double) * (size_t)n);
+  double* p = (double*)malloc(sizeof(double) * (size_t)n);
+  if (!f_u || !p) { free(f_u); free(p); return OR_E_NOMEM; }
+  op_rhs(&op, u, f_u);
+  for (long q = 0; q < n; ++q) f_u[q] = h * f_u[q];
+  int st = leja_phi_core(&op, 1, f_u, c, gamma, h, rtol, atol, xi, K, p, iters);
+  for (long q = 0; q < n; ++q) u_out[q] = u[q] + p[q];
+  free(f_u);
+  free(p);
+  return st;
+}
+
+/* ------------------------------------------------------------------------ */
+/* EXPRB32 (Sec. 2.3, Listing 13), in the listing's stage order:             */
+/*   a   = u + phi_1(h J(u)) h f(u)                       (lower order)      */
+/*   R   = h (F(a) - F(u)),  F(k) = f(k) - J(u) k                            */
+/*   u3  = a + 2 phi_3(h J(u)) R                          (higher order)     */
+/*   err = ||2 phi_3(h J(u)) R||                                             */
+/* ------------------------------------------------------------------------ */
+
+int or_exprb32(int kind, int nx, int ny, double nu, double a, const double* u, double c,
+               double gamma, double h, double rtol, double atol, const double* xi, int K,
+               double* u_low, double* u_high, double* err, int* iters) {
+  if (nx <= 0 || ny <= 0) return OR_E_INVAL;
+  or_op op = {kind, nx, ny, nu, a, u};
+  long n = (long)nx * ny;
+  double* f_u = (double*)malloc(sizeof(double) * (size_t)n);
+  double* p1 = (double*)malloc(sizeof(double) * (size_t)n);
+  double* t1 = (double*)malloc(sizeof(double) * (size_t)n);
+  double* t2 = (double*)malloc(sizeof(double) * (size_t)n);
+  double* nl_u = (double*)malloc(sizeof(double) * (size_t)n);
+  double* nl_a = (double*)malloc(sizeof(double) * (size_t)n);
+  double* p3 = (double*)malloc(sizeof(double) * (size_t)n);
+  if (!f_u || !p1 || !t1 || !t2 || !nl_u || !nl_a || !p3) {
+    free(f_u); free(p1); free(t1); free(t2); free(nl_u); free(nl_a); free(p3);
+    return OR_E_NOMEM;
+  }
+  int it1 = 0, it2 = 0;
+  op_rhs(&op, u, f_u);
+  for (long q = 0; q < n; ++q) f_u[q] = h * f_u[q];
+  int st = leja_phi_core(&op, 1, f_u, c, gamma, h, rtol, atol, xi, K, p1, &it1);
+  for (long q = 0; q < n; ++q) u_low[q] = u[q] + p1[q];
+  /* F(u) = f(u) - J(u) u */
+  op_rhs(&op, u, t1);
+  op_apply(&op, u, t2);
+  for (long q = 0; q < n; ++q) nl_u[q] = t1[q] - t2[q];
+  /* F(a) = f(a) - J(u) a */
+  op_rhs(&op, u_low, t1);
+  op_apply(&op, u_low, t2);
+  for (long q = 0; q < n; ++q) nl_a[q] = t1[q] - t2[q];
+  /* R = h (F(a) - F(u)) */
+  for (long q = 0; q < n; ++q) t1[q] = h * nl_a[q] - h * nl_u[q];
+  int st2 = OR_OK;
+  if (st == OR_OK) st2 = leja_phi_core(&op, 3, t1, c, gamma, h, rtol, atol, xi, K, p3, &it2);
+  else memset(p3, 0, sizeof(double) * (size_t)n);
+  for (long q = 0; q < n; ++q) {
+    p3[q] = 2.0 * p3[q];
+    u_high[q] = u_low[q] + p3[q];
+  }
+  *err = nrm(p3, n);
+  *iters = it1 + it2;
+  free(f_u); free(p1); free(t1); free(t2); free(nl_u); free(nl_a); free(p3);
+  return st != OR_OK ? st : st2;
+}
