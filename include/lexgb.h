@@ -1,0 +1,189 @@
+/*
+ * lexgb.h -- C ABI of the GB300 (sm_103a) Leja exponential-integrator engine.
+ *
+ * The engine computes phi_l(hA)v, the action of the matrix exponential
+ * (l = 0) and of the phi_l functions on a vector, by Newton interpolation at
+ * real Leja points, and the exponential Rosenbrock-Euler and EXPRB32 steps
+ * built on it.  Citations refer to Deka, Moriggl, Einkemmer, "LeXInt:
+ * GPU-accelerated exponential integrators package" (arXiv 2310.08344).
+ *
+ * Conventions shared by every entry point
+ *  - Grid: periodic unit square, nx x ny points x_i = i/nx, y_j = j/ny; a
+ *    field is a contiguous array of nx*ny doubles, index j*nx + i (x fastest).
+ *    Contiguous data is what the paper's RHS functors require (Sec. 2).
+ *  - Operators (second-order central differences, periodic):
+ *      LX_ADVDIFF  A v = nu (v_xx + v_yy) + a (v_x + v_y)        (Sec. 3, Eq. 3)
+ *      LX_BURGERS  f(u) = nu (u_xx + u_yy) - u (u_x + u_y); the Jacobian
+ *                  action J(u)v = nu Lap v - v (u_x+u_y) - u (v_x+v_y) is the
+ *                  exact linearisation (the paper's finite-difference action,
+ *                  Sec. 2.3, is replaced by it).
+ *  - Norms: ||x|| = ||x||_2 / sqrt(N) (Sec. 2.2).
+ *  - Device pointers ("_dev") are CUDA global-memory pointers of the current
+ *    device; host pointers ("_host") are ordinary CPU memory.  The caller
+ *    allocates and owns every input and output buffer (Sec. 2.2, Listing 4);
+ *    the context owns its auxiliary vectors from setup to destroy (Sec. 2.3,
+ *    Listing 10).
+ *  - Streams: all device work of a context runs on the stream passed at setup
+ *    (NULL = the legacy default stream).  Every call synchronises that stream
+ *    once before it returns, so the scalars it reports (iters, err, rho) are
+ *    valid on return.  Calls on one context must not run concurrently.
+ *  - Errors: every call returns an lx_status.  On an error other than
+ *    LX_E_NOCONV the contents of the output buffers are unspecified; on
+ *    LX_E_NOCONV they hold the last partial sum of the Newton series, which
+ *    is not converged and must not be used as a result.
+ */
+#ifndef LEXGB_H
+#define LEXGB_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  LX_OK = 0,
+  LX_E_INVAL = 1,     /* invalid argument (sizes, NULL, aliasing, gamma == 0) */
+  LX_E_NOMEM = 2,     /* device or host allocation failed */
+  LX_E_CUDA = 3,      /* a CUDA runtime call failed (see lx_last_cuda_error) */
+  LX_E_NOCONV = 4,    /* Leja series not converged within the point table */
+  LX_E_NONFINITE = 5, /* a NaN or Inf appeared in a norm */
+  LX_E_TIMEOUT = 6    /* a bounded device-side wait gave up */
+} lx_status;
+
+enum { LX_ADVDIFF = 0, LX_BURGERS = 1 };          /* lx_problem.kind */
+enum { LX_FP64 = 0, LX_MIXED = 1 };              /* lx_problem.precision */
+enum { LX_ROS_EU = 0, LX_EXPRB32 = 1 };          /* integrator */
+
+typedef struct {
+  int nx, ny;     /* grid points per direction, each >= 1 */
+  double nu;      /* diffusion coefficient */
+  double a;       /* advection speed (LX_ADVDIFF only) */
+  int kind;       /* LX_ADVDIFF or LX_BURGERS */
+  int precision;  /* LX_FP64: all arithmetic in double.  LX_MIXED: the Newton
+                     basis y_m and its stencil in float, the coefficients,
+                     the polynomial p and both stopping norms in double */
+} lx_problem;
+
+typedef struct lx_ctx lx_ctx;
+
+/* Human-readable name of a status code (static storage). */
+const char* lx_status_str(lx_status s);
+
+/* Message of the last CUDA error seen by this library on the calling thread
+ * ("" if none). */
+const char* lx_last_cuda_error(void);
+
+/* ---------------------------------------------------------------------------
+ * Host numerics (no GPU needed)
+ * ------------------------------------------------------------------------- */
+
+/* The first K greedy Leja points on [-2, 2] (Sec. 2.1: xi_j maximises
+ * prod_{k<j} |x - xi_k|; |xi_0| is maximal).  Readings: xi_0 = +2; ties in
+ * the maximum (1e-12 relative in the log-product) go to the larger point.
+ * xi_out: host array of K doubles, written.  Computed once per process and
+ * cached.  LX_E_INVAL if K <= 0 or xi_out is NULL. */
+lx_status lx_leja_points(int K, double* xi_out);
+
+/* Newton coefficients d_j = f[xi_0, ..., xi_j], j < K, of
+ * f(xi) = phi_l(h (c + gamma xi)) at the points xi (Sec. 2.1, Eq. 2 with exp
+ * replaced by phi_l).  FP64, by Opitz' theorem with scaled Taylor sub-steps.
+ * xi: host array of K points; d_out: host array of K doubles, written.
+ * LX_E_INVAL for l < 0, K <= 0, NULL pointers, gamma == 0 or non-finite
+ * h*c, h*gamma; LX_E_NONFINITE if a coefficient overflows. */
+lx_status lx_leja_coeffs(int l, double h, double c, double gamma, const double* xi, int K, double* d_out);
+
+/* Number of Newton coefficients the engine computes and uses for (h, c,
+ * gamma) with a table of K points: the first J with the bound
+ * (h|gamma|)^J / J! * e^{max(0, h (c + 2|gamma|))} below 1e-40, plus 8, at
+ * most K.  The Leja loop stops with LX_E_NOCONV after J - 1 iterations. */
+int lx_leja_coeff_count(double h, double c, double gamma, int K);
+
+/* ---------------------------------------------------------------------------
+ * Context (the paper's struct Leja, Sec. 2.3 Listing 10)
+ * ------------------------------------------------------------------------- */
+
+/* Create a context for one problem: uploads the Leja point table, allocates
+ * the auxiliary vectors (two basis vectors, stage vectors of the integrator,
+ * reduction scratch) and builds the CUDA graph of the Leja loop.
+ *   prob        problem description (copied)
+ *   integrator  LX_ROS_EU or LX_EXPRB32 (the integrator expint_step runs)
+ *   max_leja    size K of the Leja point table, 16 <= K <= 4096 (0: 1000)
+ *   cuda_stream a cudaStream_t of the current device, or NULL
+ *   out         receives the context
+ * Errors: LX_E_INVAL (bad sizes/kind/precision), LX_E_NOMEM, LX_E_CUDA. */
+lx_status leja_setup(const lx_problem* prob, int integrator, int max_leja, void* cuda_stream, lx_ctx** out);
+
+/* Free the context and its device memory.  NULL is accepted. */
+void leja_destroy(lx_ctx* ctx);
+
+/* Spectral bound by power iteration (Sec. 2, Listing 7: the dominant
+ * eigenvalue gives c = lambda/2, gamma = -lambda/4 with lambda = -1.05 rho).
+ *   u_dev      linearisation point (LX_BURGERS: J(u); LX_ADVDIFF: ignored,
+ *              may be NULL)
+ *   v0_dev     start vector, N doubles, not modified (must not be constant:
+ *              constants are in the null space of the periodic operators)
+ *   max_iters  1..64 matrix-vector products
+ *   rho        receives the estimate ||A v_k|| / ||v_k|| of the last pass
+ *   iters      receives the number of passes (may be NULL)
+ * Stops after max_iters passes or when |rho_k - rho_{k-1}| <= 1e-2 rho_k. */
+lx_status power_bound(lx_ctx* ctx, const double* u_dev, const double* v0_dev, int max_iters, double* rho,
+                      int* iters);
+
+/* phi_l(h Op) w by Leja interpolation (Sec. 2.2 Listings 2-3, Sec. 2.3
+ * Listings 8, 9, 11: real_Leja_exp for l = 0, real_Leja_phi_nl /
+ * real_Leja_phi otherwise).  Op is A (LX_ADVDIFF) or J(u) (LX_BURGERS).
+ *   l          0..8
+ *   u_dev      linearisation point (LX_BURGERS), else ignored / NULL
+ *   w_dev      input vector (N doubles), not modified
+ *   out_dev    output p (N doubles); must not alias w_dev or u_dev
+ *   c, gamma   centre and quarter-width of the focal interval [c-2g, c+2g]
+ *   h          step size
+ *   rtol, atol stop when |d_m| ||y_m|| <= rtol ||p_m|| + atol
+ *   iters      receives the number of Leja iterations (matrix-vector
+ *              products) m at the stop (may be NULL)
+ * The loop runs as a CUDA graph whose while-node is ended by the device: no
+ * host synchronisation per iteration. */
+lx_status phi_l_apply(lx_ctx* ctx, int l, const double* u_dev, const double* w_dev, double* out_dev, double c,
+                      double gamma, double h, double rtol, double atol, int* iters);
+
+/* One step of the context's integrator (Sec. 2.2 Listings 5-6; Sec. 2.3
+ * Listings 12-13):
+ *   LX_ROS_EU   u_high = u + phi_1(h J(u)) h f(u); u_low unused (may be
+ *               NULL); err = 0.
+ *   LX_EXPRB32  u_low  = a = u + phi_1(h J(u)) h f(u)
+ *               u_high = a + 2 phi_3(h J(u)) R,  R = h (F(a) - F(u)),
+ *               F(k) = f(k) - J(u) k;  err = ||2 phi_3(h J(u)) R||.
+ *               (For the quadratic Burgers f, R = -h p (p_x + p_y) with
+ *               p = a - u, which is how the engine evaluates it.)
+ * u_dev is not modified; u_low_dev and u_high_dev must not alias u_dev or
+ * each other.  iters receives the total Leja iterations of the step. */
+lx_status expint_step(lx_ctx* ctx, const double* u_dev, double* u_low_dev, double* u_high_dev, double c,
+                      double gamma, double h, double rtol, double atol, double* err, int* iters);
+
+/* expint_step on HOST buffers: copies u_host to the device, runs the step
+ * and copies the results back (context-owned staging buffers; nothing is
+ * allocated per call).  For page-locked host memory the copies are
+ * asynchronous DMA transfers.  u_low_host may be NULL. */
+lx_status expint_step_host(lx_ctx* ctx, const double* u_host, double* u_low_host, double* u_high_host, double c,
+                           double gamma, double h, double rtol, double atol, double* err, int* iters);
+
+/* Timing of the Leja loops run by this context since the last reset: the
+ * summed CUDA-event time of the loop graphs (milliseconds, measured on the
+ * context stream) and the number of Leja iterations they ran.  The average
+ * duration of one fused Leja-iteration launch is loop_ms / iterations. */
+typedef struct {
+  double loop_ms;
+  long long loop_iterations;
+  long long loop_launches;
+  double power_ms;
+} lx_stats;
+lx_status lx_ctx_stats(lx_ctx* ctx, lx_stats* out, int reset);
+
+/* Kernel selection of the context (for diagnostics): writes a short name of
+ * the fused Leja-iteration kernel into buf (NUL-terminated, at most len). */
+lx_status lx_ctx_kernel_name(lx_ctx* ctx, char* buf, int len);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LEXGB_H */

@@ -1,0 +1,36 @@
+"""GB300-native Leja exponential-integrator engine (Python binding).
+
+A thin ctypes layer over the C ABI declared in include/lexgb.h: each function
+here has the name of the C entry point it calls and only marshals arguments
+(torch CUDA tensors or raw device addresses to pointers, numpy arrays to host
+pointers).  Every step of the computation runs in the CUDA library
+``_lexgb.so``; importing this package without that library raises.
+PyTorch is used only for device memory and streams.
+"""
+from __future__ import annotations
+
+from .binding import (  # noqa: F401
+    ADVDIFF,
+    BURGERS,
+    EXPRB32,
+    FP64,
+    MIXED,
+    ROS_EU,
+    STATUS,
+    Context,
+    LexgbError,
+    expint_step,
+    expint_step_host,
+    leja_destroy,
+    leja_setup,
+    lib,
+    lx_ctx_kernel_name,
+    lx_ctx_stats,
+    lx_leja_coeff_count,
+    lx_leja_coeffs,
+    lx_leja_points,
+    lx_status_str,
+    phi_l_apply,
+    power_bound,
+    spectral_interval,
+)

@@ -1,0 +1,234 @@
+"""ctypes marshalling for the C ABI of include/lexgb.h (no computation here)."""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import threading
+
+import numpy as np
+
+from . import _build
+
+OK, E_INVAL, E_NOMEM, E_CUDA, E_NOCONV, E_NONFINITE, E_TIMEOUT = range(7)
+STATUS = {0: "LX_OK", 1: "LX_E_INVAL", 2: "LX_E_NOMEM", 3: "LX_E_CUDA", 4: "LX_E_NOCONV", 5: "LX_E_NONFINITE",
+          6: "LX_E_TIMEOUT"}
+ADVDIFF, BURGERS = 0, 1
+FP64, MIXED = 0, 1
+ROS_EU, EXPRB32 = 0, 1
+
+_dp = C.POINTER(C.c_double)
+_ip = C.POINTER(C.c_int)
+_vp = C.c_void_p
+
+
+class LxProblem(C.Structure):
+    _fields_ = [("nx", C.c_int), ("ny", C.c_int), ("nu", C.c_double), ("a", C.c_double), ("kind", C.c_int),
+                ("precision", C.c_int)]
+
+
+class LxStats(C.Structure):
+    _fields_ = [("loop_ms", C.c_double), ("loop_iterations", C.c_longlong), ("loop_launches", C.c_longlong),
+                ("power_ms", C.c_double)]
+
+
+class LexgbError(RuntimeError):
+    def __init__(self, status, what=""):
+        self.status = status
+        super().__init__(f"{what}: {STATUS.get(status, status)} {lx_status_str(status)} {_cuda_err()}")
+
+
+_lib = None
+_lock = threading.Lock()
+
+
+def lib():
+    """Load _lexgb.so (building it first if the sources are newer)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            path = _build.LIB
+            if not _build.up_to_date():
+                if os.environ.get("LEXGB_NO_BUILD"):
+                    raise RuntimeError(f"{path} is missing or stale and LEXGB_NO_BUILD is set")
+                _build.build()
+            L = C.CDLL(path)
+            L.lx_status_str.restype = C.c_char_p
+            L.lx_status_str.argtypes = [C.c_int]
+            L.lx_last_cuda_error.restype = C.c_char_p
+            L.lx_leja_points.argtypes = [C.c_int, _dp]
+            L.lx_leja_coeffs.argtypes = [C.c_int, C.c_double, C.c_double, C.c_double, _dp, C.c_int, _dp]
+            L.lx_leja_coeff_count.argtypes = [C.c_double, C.c_double, C.c_double, C.c_int]
+            L.lx_leja_coeff_count.restype = C.c_int
+            L.leja_setup.argtypes = [C.POINTER(LxProblem), C.c_int, C.c_int, _vp, C.POINTER(_vp)]
+            L.leja_destroy.argtypes = [_vp]
+            L.leja_destroy.restype = None
+            L.power_bound.argtypes = [_vp, _vp, _vp, C.c_int, _dp, _ip]
+            L.phi_l_apply.argtypes = [_vp, C.c_int, _vp, _vp, _vp, C.c_double, C.c_double, C.c_double, C.c_double,
+                                      C.c_double, _ip]
+            L.expint_step.argtypes = [_vp, _vp, _vp, _vp, C.c_double, C.c_double, C.c_double, C.c_double,
+                                      C.c_double, _dp, _ip]
+            L.expint_step_host.argtypes = [_vp, _vp, _vp, _vp, C.c_double, C.c_double, C.c_double, C.c_double,
+                                           C.c_double, _dp, _ip]
+            L.lx_ctx_stats.argtypes = [_vp, C.POINTER(LxStats), C.c_int]
+            L.lx_ctx_kernel_name.argtypes = [_vp, C.c_char_p, C.c_int]
+            _lib = L
+    return _lib
+
+
+def _cuda_err():
+    try:
+        return lib().lx_last_cuda_error().decode()
+    except Exception:  # pragma: no cover
+        return ""
+
+
+def lx_status_str(status: int) -> str:
+    return lib().lx_status_str(int(status)).decode()
+
+
+def _dev(t):
+    """Device address of a torch CUDA float64 contiguous tensor, or an int."""
+    if t is None:
+        return None
+    if isinstance(t, int):
+        return t
+    if not (t.is_cuda and t.is_contiguous()):
+        raise ValueError("expected a contiguous CUDA tensor")
+    return t.data_ptr()
+
+
+def _host(a):
+    if a is None:
+        return None
+    if isinstance(a, int):
+        return a
+    if hasattr(a, "data_ptr"):  # torch CPU tensor (e.g. pinned)
+        if a.is_cuda or not a.is_contiguous():
+            raise ValueError("expected a contiguous CPU tensor")
+        return a.data_ptr()
+    if not (isinstance(a, np.ndarray) and a.flags.c_contiguous and a.dtype == np.float64):
+        raise ValueError("expected a C-contiguous float64 numpy array")
+    return a.ctypes.data
+
+
+def _stream_handle(stream):
+    if stream is None:
+        return None
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+# ------------------------------------------------------------------ host numerics
+def lx_leja_points(K: int) -> np.ndarray:
+    xi = np.zeros(K)
+    st = lib().lx_leja_points(K, xi.ctypes.data_as(_dp))
+    if st != OK:
+        raise LexgbError(st, "lx_leja_points")
+    return xi
+
+
+def lx_leja_coeffs(l: int, h: float, c: float, gamma: float, xi) -> np.ndarray:
+    xi = np.ascontiguousarray(xi, dtype=np.float64)
+    d = np.zeros_like(xi)
+    st = lib().lx_leja_coeffs(l, h, c, gamma, xi.ctypes.data_as(_dp), len(xi), d.ctypes.data_as(_dp))
+    if st != OK:
+        raise LexgbError(st, "lx_leja_coeffs")
+    return d
+
+
+def lx_leja_coeff_count(h: float, c: float, gamma: float, K: int) -> int:
+    return lib().lx_leja_coeff_count(h, c, gamma, K)
+
+
+def spectral_interval(rho: float):
+    """c and gamma from a spectral-radius estimate (lambda = -1.05 rho)."""
+    lam = -1.05 * rho
+    return lam / 2.0, -lam / 4.0
+
+
+# ------------------------------------------------------------------ context
+class Context:
+    """Owns an lx_ctx*; leja_destroy runs on close() or garbage collection."""
+
+    def __init__(self, handle, problem, integrator):
+        self.handle = handle
+        self.problem = problem
+        self.integrator = integrator
+
+    @property
+    def n(self):
+        return self.problem.nx * self.problem.ny
+
+    def close(self):
+        if self.handle:
+            lib().leja_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def leja_setup(nx, ny, nu, a=0.0, kind=ADVDIFF, precision=FP64, integrator=ROS_EU, max_leja=1000,
+               stream=None) -> Context:
+    prob = LxProblem(nx, ny, nu, a, kind, precision)
+    h = _vp()
+    st = lib().leja_setup(C.byref(prob), integrator, max_leja, _stream_handle(stream), C.byref(h))
+    if st != OK:
+        raise LexgbError(st, "leja_setup")
+    return Context(h.value, prob, integrator)
+
+
+def leja_destroy(ctx: Context):
+    ctx.close()
+
+
+def power_bound(ctx: Context, u, v0, max_iters=10):
+    """Returns (status, rho, passes)."""
+    rho = C.c_double(0.0)
+    it = C.c_int(0)
+    st = lib().power_bound(ctx.handle, _dev(u), _dev(v0), max_iters, C.byref(rho), C.byref(it))
+    return st, rho.value, it.value
+
+
+def phi_l_apply(ctx: Context, l, u, w, out, c, gamma, h, rtol, atol):
+    """Returns (status, iters)."""
+    it = C.c_int(0)
+    st = lib().phi_l_apply(ctx.handle, l, _dev(u), _dev(w), _dev(out), c, gamma, h, rtol, atol, C.byref(it))
+    return st, it.value
+
+
+def expint_step(ctx: Context, u, u_low, u_high, c, gamma, h, rtol, atol):
+    """Returns (status, err, iters)."""
+    err = C.c_double(0.0)
+    it = C.c_int(0)
+    st = lib().expint_step(ctx.handle, _dev(u), _dev(u_low), _dev(u_high), c, gamma, h, rtol, atol,
+                           C.byref(err), C.byref(it))
+    return st, err.value, it.value
+
+
+def expint_step_host(ctx: Context, u, u_low, u_high, c, gamma, h, rtol, atol):
+    """Host-buffer step (numpy float64 arrays or pinned CPU tensors).  Returns (status, err, iters)."""
+    err = C.c_double(0.0)
+    it = C.c_int(0)
+    st = lib().expint_step_host(ctx.handle, _host(u), _host(u_low), _host(u_high), c, gamma, h, rtol, atol,
+                                C.byref(err), C.byref(it))
+    return st, err.value, it.value
+
+
+def lx_ctx_stats(ctx: Context, reset=False) -> dict:
+    s = LxStats()
+    st = lib().lx_ctx_stats(ctx.handle, C.byref(s), 1 if reset else 0)
+    if st != OK:
+        raise LexgbError(st, "lx_ctx_stats")
+    return {"loop_ms": s.loop_ms, "loop_iterations": s.loop_iterations, "loop_launches": s.loop_launches,
+            "power_ms": s.power_ms}
+
+
+def lx_ctx_kernel_name(ctx: Context) -> str:
+    buf = C.create_string_buffer(128)
+    lib().lx_ctx_kernel_name(ctx.handle, buf, 128)
+    return buf.value.decode()

@@ -1,0 +1,556 @@
+// Context, CUDA-graph Leja loop and C ABI of the engine (see include/lexgb.h).
+//
+// A context is the GB300 counterpart of the paper's struct Leja (Sec. 2.3,
+// Listing 10): it owns the auxiliary device vectors from setup to destroy and
+// runs the integrators.  Each Leja loop is one launch of a CUDA graph whose
+// only node is a while-loop around the fused Leja-iteration kernel; the last
+// block of each iteration decides convergence and ends the loop from the
+// device, so the host synchronises once per API call instead of once per
+// iteration.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "leja_kernels.cuh"
+#include "lexgb_internal.h"
+
+using namespace lexgb;
+
+namespace {
+
+thread_local std::string g_last_cuda_error;
+
+bool cuda_ok(cudaError_t e, const char* what) {
+  if (e == cudaSuccess) return true;
+  g_last_cuda_error = std::string(what) + ": " + cudaGetErrorString(e);
+  return false;
+}
+
+#define LX_CUDA(call)                                   \
+  do {                                                  \
+    if (!cuda_ok((call), #call)) return LX_E_CUDA;      \
+  } while (0)
+
+constexpr int kMaxPower = 64;
+
+struct CoefSlot {
+  bool valid = false;
+  int l = -1, count = 0;
+  double h = 0, c = 0, gamma = 0;
+  double* dev = nullptr;
+  double* host = nullptr;  // pinned staging
+};
+
+// Kernel variants of the fused Leja iteration.
+enum Variant { kVec2 = 0, kVec1 = 1, kNumVariants = 2 };
+
+struct LoopGraph {
+  bool built = false;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  int grid = 0;
+  const void* func = nullptr;
+  const char* name = "";
+};
+
+}  // namespace
+
+struct lx_ctx {
+  lx_problem prob{};
+  int integrator = LX_ROS_EU;
+  int K = 1000;
+  cudaStream_t stream = nullptr;
+  int device = 0;
+  int sm_count = 0;
+  long long n = 0;
+  int strip_h = 32;
+  Geo geo{};
+
+  double* d_xi = nullptr;
+  CoefSlot coef[2];
+  void* d_y[2] = {nullptr, nullptr};
+  double* d_f = nullptr;   // h f(u), later R
+  double* d_s = nullptr;   // u_x + u_y (Burgers)
+  double* d_p3 = nullptr;  // phi_3 result (EXPRB32)
+  double* d_pw[2] = {nullptr, nullptr};  // power iteration ping-pong
+  double* d_io[3] = {nullptr, nullptr, nullptr};  // staging for expint_step_host
+  double* d_partials = nullptr;
+  int partials_cap = 0;
+  unsigned int* d_ticket = nullptr;
+  LoopState* d_state = nullptr;
+  LoopArgs* d_args = nullptr;
+  LoopState* h_state = nullptr;  // pinned
+
+  LoopGraph loop[kNumVariants];
+  int aux_grid = 0;
+
+  cudaEvent_t ev[8] = {};
+  int ev_used = 0;
+  cudaEvent_t ev_pow[2] = {};
+  lx_stats stats{};
+};
+
+namespace {
+
+size_t basis_bytes(const lx_ctx* c) {
+  return (size_t)c->n * (c->prob.precision == LX_MIXED ? sizeof(float) : sizeof(double));
+}
+
+template <int KIND, typename T, int VEC>
+const void* iter_kernel_ptr() {
+  return reinterpret_cast<const void*>(&leja_iter_kernel<KIND, T, VEC>);
+}
+
+const void* pick_kernel(int kind, int precision, int variant, const char** name) {
+  const bool mixed = precision == LX_MIXED;
+  const bool v2 = variant == kVec2;
+  if (kind == LX_ADVDIFF) {
+    if (!mixed) {
+      *name = v2 ? "leja_iter_advdiff_f64_v2" : "leja_iter_advdiff_f64_v1";
+      return v2 ? iter_kernel_ptr<0, double, 2>() : iter_kernel_ptr<0, double, 1>();
+    }
+    *name = v2 ? "leja_iter_advdiff_mixed_v2" : "leja_iter_advdiff_mixed_v1";
+    return v2 ? iter_kernel_ptr<0, float, 2>() : iter_kernel_ptr<0, float, 1>();
+  }
+  if (!mixed) {
+    *name = v2 ? "leja_iter_burgers_f64_v2" : "leja_iter_burgers_f64_v1";
+    return v2 ? iter_kernel_ptr<1, double, 2>() : iter_kernel_ptr<1, double, 1>();
+  }
+  *name = v2 ? "leja_iter_burgers_mixed_v2" : "leja_iter_burgers_mixed_v1";
+  return v2 ? iter_kernel_ptr<1, float, 2>() : iter_kernel_ptr<1, float, 1>();
+}
+
+int strips_for(const lx_ctx* c, int variant) {
+  const int vec = variant == kVec2 ? 2 : 1;
+  const int ncs = (c->prob.nx + 32 * vec - 1) / (32 * vec);
+  const int nrs = (c->prob.ny + c->strip_h - 1) / c->strip_h;
+  return ncs * nrs;
+}
+
+lx_status build_loop_graph(lx_ctx* c, int variant) {
+  LoopGraph& L = c->loop[variant];
+  if (L.built) return LX_OK;
+  L.func = pick_kernel(c->prob.kind, c->prob.precision, variant, &L.name);
+  int per_sm = 0;
+  LX_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, L.func, kThreadsPerBlock, 0));
+  per_sm = std::max(per_sm, 1);
+  const int want = (strips_for(c, variant) + kWarpsPerBlock - 1) / kWarpsPerBlock;
+  L.grid = std::max(1, std::min(want, per_sm * c->sm_count));
+  if (L.grid > c->partials_cap) return LX_E_INVAL;
+
+  LX_CUDA(cudaGraphCreate(&L.graph, 0));
+  cudaGraphConditionalHandle cond;
+  LX_CUDA(cudaGraphConditionalHandleCreate(&cond, L.graph, 1, cudaGraphCondAssignDefault));
+  // cudaGraphNodeParams holds a union without a default constructor: build it
+  // in zeroed raw storage.
+  alignas(cudaGraphNodeParams) unsigned char cp_raw[sizeof(cudaGraphNodeParams)];
+  std::memset(cp_raw, 0, sizeof(cp_raw));
+  cudaGraphNodeParams& cp = *reinterpret_cast<cudaGraphNodeParams*>(cp_raw);
+  cp.type = cudaGraphNodeTypeConditional;
+  cp.conditional.handle = cond;
+  cp.conditional.type = cudaGraphCondTypeWhile;
+  cp.conditional.size = 1;
+  cudaGraphNode_t cnode;
+  LX_CUDA(cudaGraphAddNode(&cnode, L.graph, nullptr, nullptr, 0, &cp));
+  cudaGraph_t body = cp.conditional.phGraph_out[0];
+
+  const LoopArgs* args = c->d_args;
+  LoopState* st = c->d_state;
+  double* partials = c->d_partials;
+  unsigned int* ticket = c->d_ticket;
+  void* kargs[] = {(void*)&args, (void*)&st, (void*)&partials, (void*)&ticket, (void*)&cond};
+  cudaKernelNodeParams kp;
+  std::memset(&kp, 0, sizeof(kp));
+  kp.func = const_cast<void*>(L.func);
+  kp.gridDim = dim3(L.grid);
+  kp.blockDim = dim3(kThreadsPerBlock);
+  kp.sharedMemBytes = 0;
+  kp.kernelParams = kargs;
+  cudaGraphNode_t knode;
+  LX_CUDA(cudaGraphAddKernelNode(&knode, body, nullptr, 0, &kp));
+  LX_CUDA(cudaGraphInstantiate(&L.exec, L.graph, 0));
+  L.built = true;
+  return LX_OK;
+}
+
+bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
+
+int choose_variant(const lx_ctx* c, const double* w, const double* out) {
+  if (c->prob.nx % 64 == 0 && aligned16(w) && aligned16(out) && aligned16(c->d_y[0]) && aligned16(c->d_y[1]))
+    return kVec2;
+  return kVec1;
+}
+
+lx_status ensure_coeffs(lx_ctx* c, int slot, int l, double h, double cc, double gamma) {
+  CoefSlot& S = c->coef[slot];
+  if (S.valid && S.l == l && S.h == h && S.c == cc && S.gamma == gamma) return LX_OK;
+  const int count = leja_coeff_count(h, cc, gamma, c->K);
+  std::vector<double> xi(count);
+  leja_points(count, xi.data());
+  int st = leja_coeffs(l, h, cc, gamma, xi.data(), count, S.host);
+  if (st != LX_OK) return (lx_status)st;
+  LX_CUDA(cudaMemcpyAsync(S.dev, S.host, sizeof(double) * count, cudaMemcpyHostToDevice, c->stream));
+  S.valid = true;
+  S.l = l;
+  S.h = h;
+  S.c = cc;
+  S.gamma = gamma;
+  S.count = count;
+  return LX_OK;
+}
+
+lx_status launch_loop(lx_ctx* c, int slot, int l, const double* u, const double* w, double* out, double cc,
+                      double gamma, double h, double rtol, double atol) {
+  lx_status st = ensure_coeffs(c, slot, l, h, cc, gamma);
+  if (st != LX_OK) return st;
+  const int variant = choose_variant(c, w, out);
+  st = build_loop_graph(c, variant);
+  if (st != LX_OK) return st;
+  const lx_problem& P = c->prob;
+  const double dx = 1.0 / P.nx, dy = 1.0 / P.ny;
+  const double ig = 1.0 / gamma;
+  LoopArgs a;
+  std::memset(&a, 0, sizeof(a));
+  a.nx = P.nx;
+  a.ny = P.ny;
+  a.n = c->n;
+  a.strip_h = c->strip_h;
+  a.kmax = c->coef[slot].count - 1;
+  a.w = w;
+  a.y0 = c->d_y[0];
+  a.y1 = c->d_y[1];
+  a.p = out;
+  a.u = u;
+  a.s = c->d_s;
+  a.xi = c->d_xi;
+  a.d = c->coef[slot].dev;
+  const double nx2 = P.nu / (dx * dx), ny2 = P.nu / (dy * dy);
+  if (P.kind == LX_ADVDIFF) {
+    a.wxp = (nx2 + P.a / (2 * dx)) * ig;
+    a.wxm = (nx2 - P.a / (2 * dx)) * ig;
+    a.wyp = (ny2 + P.a / (2 * dy)) * ig;
+    a.wym = (ny2 - P.a / (2 * dy)) * ig;
+  } else {
+    a.lx = nx2 * ig;
+    a.ly = ny2 * ig;
+    a.gx = ig / (2 * dx);
+    a.gy = ig / (2 * dy);
+    a.inv_gamma = ig;
+  }
+  a.wc0 = (-2.0 * nx2 - 2.0 * ny2 - cc) * ig;
+  a.rtol = rtol;
+  a.atol = atol;
+  set_loop_args_kernel<<<1, 1, 0, c->stream>>>(a, c->d_args, c->d_state, c->d_ticket);
+  LX_CUDA(cudaGetLastError());
+  if (c->ev_used + 2 > 8) return LX_E_INVAL;
+  LX_CUDA(cudaEventRecord(c->ev[c->ev_used], c->stream));
+  LX_CUDA(cudaGraphLaunch(c->loop[variant].exec, c->stream));
+  LX_CUDA(cudaEventRecord(c->ev[c->ev_used + 1], c->stream));
+  c->ev_used += 2;
+  return LX_OK;
+}
+
+int aux_blocks(const lx_ctx* c) {
+  const long long want = (c->n + kThreadsPerBlock - 1) / kThreadsPerBlock;
+  return (int)std::max<long long>(1, std::min<long long>(want, (long long)c->aux_grid));
+}
+
+lx_status begin_call(lx_ctx* c) {
+  c->ev_used = 0;
+  reset_call_kernel<<<1, 1, 0, c->stream>>>(c->d_state, c->d_ticket);
+  LX_CUDA(cudaGetLastError());
+  return LX_OK;
+}
+
+// Synchronise, fold the loop timings into the statistics, fetch the state.
+lx_status end_call(lx_ctx* c) {
+  LX_CUDA(cudaMemcpyAsync(c->h_state, c->d_state, sizeof(LoopState), cudaMemcpyDeviceToHost, c->stream));
+  LX_CUDA(cudaStreamSynchronize(c->stream));
+  for (int k = 0; k + 1 < c->ev_used; k += 2) {
+    float ms = 0.f;
+    LX_CUDA(cudaEventElapsedTime(&ms, c->ev[k], c->ev[k + 1]));
+    c->stats.loop_ms += ms;
+    c->stats.loop_launches += 1;
+  }
+  c->stats.loop_iterations += c->h_state->iters_total;
+  c->ev_used = 0;
+  return LX_OK;
+}
+
+bool valid_problem(const lx_problem* p) {
+  if (!p) return false;
+  if (p->nx < 1 || p->ny < 1) return false;
+  if ((long long)p->nx * p->ny > (1LL << 31)) return false;
+  if (p->kind != LX_ADVDIFF && p->kind != LX_BURGERS) return false;
+  if (p->precision != LX_FP64 && p->precision != LX_MIXED) return false;
+  if (!std::isfinite(p->nu) || !std::isfinite(p->a)) return false;
+  return true;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* lx_status_str(lx_status s) {
+  switch (s) {
+    case LX_OK: return "ok";
+    case LX_E_INVAL: return "invalid argument";
+    case LX_E_NOMEM: return "out of memory";
+    case LX_E_CUDA: return "CUDA error";
+    case LX_E_NOCONV: return "Leja series did not converge";
+    case LX_E_NONFINITE: return "non-finite value";
+    case LX_E_TIMEOUT: return "device wait timed out";
+  }
+  return "unknown status";
+}
+
+const char* lx_last_cuda_error(void) { return g_last_cuda_error.c_str(); }
+
+void leja_destroy(lx_ctx* c) {
+  if (!c) return;
+  for (auto& L : c->loop) {
+    if (L.exec) cudaGraphExecDestroy(L.exec);
+    if (L.graph) cudaGraphDestroy(L.graph);
+  }
+  for (auto& S : c->coef) {
+    if (S.dev) cudaFree(S.dev);
+    if (S.host) cudaFreeHost(S.host);
+  }
+  cudaFree(c->d_xi);
+  cudaFree(c->d_y[0]);
+  cudaFree(c->d_y[1]);
+  cudaFree(c->d_f);
+  cudaFree(c->d_s);
+  cudaFree(c->d_p3);
+  cudaFree(c->d_pw[0]);
+  cudaFree(c->d_pw[1]);
+  for (auto* p : c->d_io) cudaFree(p);
+  cudaFree(c->d_partials);
+  cudaFree(c->d_ticket);
+  cudaFree(c->d_state);
+  cudaFree(c->d_args);
+  if (c->h_state) cudaFreeHost(c->h_state);
+  for (auto& e : c->ev)
+    if (e) cudaEventDestroy(e);
+  for (auto& e : c->ev_pow)
+    if (e) cudaEventDestroy(e);
+  delete c;
+}
+
+lx_status leja_setup(const lx_problem* prob, int integrator, int max_leja, void* cuda_stream, lx_ctx** out) {
+  if (!out) return LX_E_INVAL;
+  *out = nullptr;
+  if (!valid_problem(prob)) return LX_E_INVAL;
+  if (integrator != LX_ROS_EU && integrator != LX_EXPRB32) return LX_E_INVAL;
+  if (max_leja == 0) max_leja = 1000;
+  if (max_leja < 16 || max_leja > 4096) return LX_E_INVAL;
+  lx_ctx* c = new lx_ctx();
+  c->prob = *prob;
+  c->integrator = integrator;
+  c->K = max_leja;
+  c->stream = reinterpret_cast<cudaStream_t>(cuda_stream);
+  c->n = (long long)prob->nx * prob->ny;
+  const double dx = 1.0 / prob->nx, dy = 1.0 / prob->ny;
+  c->geo = Geo{prob->nx, prob->ny, c->n, 1.0 / (dx * dx), 1.0 / (dy * dy), 1.0 / (2 * dx), 1.0 / (2 * dy)};
+  auto fail = [&](lx_status s) {
+    leja_destroy(c);
+    return s;
+  };
+  if (!cuda_ok(cudaGetDevice(&c->device), "cudaGetDevice")) return fail(LX_E_CUDA);
+  if (!cuda_ok(cudaDeviceGetAttribute(&c->sm_count, cudaDevAttrMultiProcessorCount, c->device), "sm count"))
+    return fail(LX_E_CUDA);
+  std::vector<double> xi(c->K);
+  if (leja_points(c->K, xi.data()) != LX_OK) return fail(LX_E_INVAL);
+
+  const size_t nb = sizeof(double) * (size_t)c->n;
+  auto dmalloc = [&](void** p, size_t bytes) { return cuda_ok(cudaMalloc(p, bytes), "cudaMalloc"); };
+  if (!dmalloc((void**)&c->d_xi, sizeof(double) * c->K)) return fail(LX_E_NOMEM);
+  for (auto& S : c->coef) {
+    if (!dmalloc((void**)&S.dev, sizeof(double) * c->K)) return fail(LX_E_NOMEM);
+    if (!cuda_ok(cudaMallocHost((void**)&S.host, sizeof(double) * c->K), "cudaMallocHost")) return fail(LX_E_NOMEM);
+  }
+  if (!dmalloc(&c->d_y[0], basis_bytes(c)) || !dmalloc(&c->d_y[1], basis_bytes(c))) return fail(LX_E_NOMEM);
+  if (!dmalloc((void**)&c->d_f, nb) || !dmalloc((void**)&c->d_s, nb)) return fail(LX_E_NOMEM);
+  if (integrator == LX_EXPRB32 && !dmalloc((void**)&c->d_p3, nb)) return fail(LX_E_NOMEM);
+  c->partials_cap = 64 * c->sm_count;
+  if (!dmalloc((void**)&c->d_partials, sizeof(double) * 2 * c->partials_cap)) return fail(LX_E_NOMEM);
+  if (!dmalloc((void**)&c->d_ticket, sizeof(unsigned int))) return fail(LX_E_NOMEM);
+  if (!dmalloc((void**)&c->d_state, sizeof(LoopState))) return fail(LX_E_NOMEM);
+  if (!dmalloc((void**)&c->d_args, sizeof(LoopArgs))) return fail(LX_E_NOMEM);
+  if (!cuda_ok(cudaMallocHost((void**)&c->h_state, sizeof(LoopState)), "cudaMallocHost")) return fail(LX_E_NOMEM);
+  for (auto& e : c->ev)
+    if (!cuda_ok(cudaEventCreate(&e), "cudaEventCreate")) return fail(LX_E_CUDA);
+  for (auto& e : c->ev_pow)
+    if (!cuda_ok(cudaEventCreate(&e), "cudaEventCreate")) return fail(LX_E_CUDA);
+  if (!cuda_ok(cudaMemsetAsync(c->d_ticket, 0, sizeof(unsigned int), c->stream), "memset") ||
+      !cuda_ok(cudaMemsetAsync(c->d_state, 0, sizeof(LoopState), c->stream), "memset") ||
+      !cuda_ok(cudaMemcpyAsync(c->d_xi, xi.data(), sizeof(double) * c->K, cudaMemcpyHostToDevice, c->stream),
+               "upload xi"))
+    return fail(LX_E_CUDA);
+  // the auxiliary kernels use one resident wave of the aux kernels' blocks
+  c->aux_grid = 4 * c->sm_count;
+  for (int v = 0; v < kNumVariants; ++v) {
+    if (v == kVec2 && prob->nx % 64 != 0) continue;
+    lx_status s = build_loop_graph(c, v);
+    if (s != LX_OK) return fail(s);
+  }
+  if (!cuda_ok(cudaStreamSynchronize(c->stream), "setup sync")) return fail(LX_E_CUDA);
+  *out = c;
+  return LX_OK;
+}
+
+lx_status power_bound(lx_ctx* c, const double* u, const double* v0, int max_iters, double* rho, int* iters) {
+  if (!c || !v0 || !rho || max_iters < 1 || max_iters > kMaxPower) return LX_E_INVAL;
+  if (c->prob.kind == LX_BURGERS && !u) return LX_E_INVAL;
+  const long long nb = sizeof(double) * c->n;
+  if (!c->d_pw[0]) {
+    if (!cuda_ok(cudaMalloc((void**)&c->d_pw[0], nb), "cudaMalloc") ||
+        !cuda_ok(cudaMalloc((void**)&c->d_pw[1], nb), "cudaMalloc"))
+      return LX_E_NOMEM;
+  }
+  const int G = aux_blocks(c);
+  const lx_problem& P = c->prob;
+  LX_CUDA(cudaEventRecord(c->ev_pow[0], c->stream));
+  if (P.kind == LX_BURGERS) {
+    rhs_kernel<1><<<G, kThreadsPerBlock, 0, c->stream>>>(c->geo, P.nu, 0.0, 0.0, u, nullptr, c->d_s);
+    LX_CUDA(cudaGetLastError());
+  }
+  power_start_kernel<<<G, kThreadsPerBlock, 0, c->stream>>>(c->n, v0, max_iters, c->d_partials, c->d_ticket,
+                                                             c->d_state);
+  LX_CUDA(cudaGetLastError());
+  for (int k = 1; k <= max_iters; ++k) {
+    const double* in = (k == 1) ? v0 : c->d_pw[(k - 2) & 1];
+    double* outv = c->d_pw[(k - 1) & 1];
+    if (P.kind == LX_ADVDIFF)
+      power_pass_kernel<0><<<G, kThreadsPerBlock, 0, c->stream>>>(c->geo, P.nu, P.a, nullptr, nullptr, in, outv,
+                                                                  c->d_partials, c->d_ticket, c->d_state);
+    else
+      power_pass_kernel<1><<<G, kThreadsPerBlock, 0, c->stream>>>(c->geo, P.nu, 0.0, u, c->d_s, in, outv,
+                                                                  c->d_partials, c->d_ticket, c->d_state);
+    LX_CUDA(cudaGetLastError());
+  }
+  LX_CUDA(cudaEventRecord(c->ev_pow[1], c->stream));
+  LX_CUDA(cudaMemcpyAsync(c->h_state, c->d_state, sizeof(LoopState), cudaMemcpyDeviceToHost, c->stream));
+  LX_CUDA(cudaStreamSynchronize(c->stream));
+  float ms = 0.f;
+  LX_CUDA(cudaEventElapsedTime(&ms, c->ev_pow[0], c->ev_pow[1]));
+  c->stats.power_ms += ms;
+  *rho = c->h_state->rho;
+  if (iters) *iters = c->h_state->pk;
+  return (lx_status)c->h_state->pstatus;
+}
+
+lx_status phi_l_apply(lx_ctx* c, int l, const double* u, const double* w, double* out, double cc, double gamma,
+                      double h, double rtol, double atol, int* iters) {
+  if (!c || !w || !out || l < 0 || l > 8 || !(gamma != 0.0) || !std::isfinite(h) || !std::isfinite(cc) ||
+      !std::isfinite(gamma) || !(rtol >= 0.0) || !(atol >= 0.0))
+    return LX_E_INVAL;
+  if ((const void*)out == (const void*)w || (u && (const void*)out == (const void*)u)) return LX_E_INVAL;
+  lx_status st = begin_call(c);
+  if (st != LX_OK) return st;
+  if (c->prob.kind == LX_BURGERS) {
+    if (!u) return LX_E_INVAL;
+    rhs_kernel<1><<<aux_blocks(c), kThreadsPerBlock, 0, c->stream>>>(c->geo, c->prob.nu, 0.0, 0.0, u, nullptr,
+                                                                       c->d_s);
+    LX_CUDA(cudaGetLastError());
+  }
+  st = launch_loop(c, 0, l, u, w, out, cc, gamma, h, rtol, atol);
+  if (st != LX_OK) return st;
+  st = end_call(c);
+  if (st != LX_OK) return st;
+  if (iters) *iters = c->h_state->iters_total;
+  return (lx_status)c->h_state->status_total;
+}
+
+lx_status expint_step(lx_ctx* c, const double* u, double* u_low, double* u_high, double cc, double gamma, double h,
+                      double rtol, double atol, double* err, int* iters) {
+  if (!c || !u || !u_high || !(gamma != 0.0) || !std::isfinite(h) || !std::isfinite(cc) || !std::isfinite(gamma) ||
+      !(rtol >= 0.0) || !(atol >= 0.0))
+    return LX_E_INVAL;
+  if ((const void*)u_high == (const void*)u) return LX_E_INVAL;
+  if (c->integrator == LX_EXPRB32 &&
+      (!u_low || (const void*)u_low == (const void*)u || (const void*)u_low == (const void*)u_high))
+    return LX_E_INVAL;
+  const lx_problem& P = c->prob;
+  const int G = aux_blocks(c);
+  lx_status st = begin_call(c);
+  if (st != LX_OK) return st;
+  // h f(u) and, for Burgers, u_x + u_y at the linearisation point
+  if (P.kind == LX_ADVDIFF)
+    rhs_kernel<0><<<G, kThreadsPerBlock, 0, c->stream>>>(c->geo, P.nu, P.a, h, u, c->d_f, c->d_s);
+  else
+    rhs_kernel<1><<<G, kThreadsPerBlock, 0, c->stream>>>(c->geo, P.nu, 0.0, h, u, c->d_f, c->d_s);
+  LX_CUDA(cudaGetLastError());
+  if (c->integrator == LX_ROS_EU) {
+    // p = phi_1(h J) h f(u) into u_high, then u_high = u + p
+    st = launch_loop(c, 0, 1, u, c->d_f, u_high, cc, gamma, h, rtol, atol);
+    if (st != LX_OK) return st;
+    add_kernel<<<G, kThreadsPerBlock, 0, c->stream>>>(c->n, u, u_high);
+    LX_CUDA(cudaGetLastError());
+    st = end_call(c);
+    if (st != LX_OK) return st;
+    if (err) *err = 0.0;
+  } else {
+    // p1 = phi_1(h J) h f(u) into u_low
+    st = launch_loop(c, 0, 1, u, c->d_f, u_low, cc, gamma, h, rtol, atol);
+    if (st != LX_OK) return st;
+    // R = h (F(a) - F(u)) into d_f, then a = u + p1 in u_low
+    if (P.kind == LX_ADVDIFF)
+      exprb32_stage_kernel<0><<<G, kThreadsPerBlock, 0, c->stream>>>(c->geo, h, u, u_low, c->d_f);
+    else
+      exprb32_stage_kernel<1><<<G, kThreadsPerBlock, 0, c->stream>>>(c->geo, h, u, u_low, c->d_f);
+    LX_CUDA(cudaGetLastError());
+    exprb32_a_kernel<<<G, kThreadsPerBlock, 0, c->stream>>>(c->n, u, u_low);
+    LX_CUDA(cudaGetLastError());
+    // p3 = phi_3(h J) R
+    st = launch_loop(c, 1, 3, u, c->d_f, c->d_p3, cc, gamma, h, rtol, atol);
+    if (st != LX_OK) return st;
+    // u_high = a + 2 p3, err = ||2 p3||
+    exprb32_final_kernel<<<G, kThreadsPerBlock, 0, c->stream>>>(c->n, u_low, c->d_p3, u_high, c->d_partials,
+                                                                 c->d_ticket, c->d_state);
+    LX_CUDA(cudaGetLastError());
+    st = end_call(c);
+    if (st != LX_OK) return st;
+    if (err) *err = c->h_state->red;
+  }
+  if (iters) *iters = c->h_state->iters_total;
+  return (lx_status)c->h_state->status_total;
+}
+
+lx_status expint_step_host(lx_ctx* c, const double* u_host, double* u_low_host, double* u_high_host, double cc,
+                           double gamma, double h, double rtol, double atol, double* err, int* iters) {
+  if (!c || !u_host || !u_high_host) return LX_E_INVAL;
+  if (c->integrator == LX_EXPRB32 && !u_low_host) return LX_E_INVAL;
+  const size_t nb = sizeof(double) * (size_t)c->n;
+  for (auto*& p : c->d_io)
+    if (!p && !cuda_ok(cudaMalloc((void**)&p, nb), "cudaMalloc")) return LX_E_NOMEM;
+  LX_CUDA(cudaMemcpyAsync(c->d_io[0], u_host, nb, cudaMemcpyHostToDevice, c->stream));
+  lx_status st = expint_step(c, c->d_io[0], c->d_io[1], c->d_io[2], cc, gamma, h, rtol, atol, err, iters);
+  if (st != LX_OK && st != LX_E_NOCONV) return st;
+  LX_CUDA(cudaMemcpyAsync(u_high_host, c->d_io[2], nb, cudaMemcpyDeviceToHost, c->stream));
+  if (c->integrator == LX_EXPRB32)
+    LX_CUDA(cudaMemcpyAsync(u_low_host, c->d_io[1], nb, cudaMemcpyDeviceToHost, c->stream));
+  LX_CUDA(cudaStreamSynchronize(c->stream));
+  return st;
+}
+
+lx_status lx_ctx_stats(lx_ctx* c, lx_stats* out, int reset) {
+  if (!c || !out) return LX_E_INVAL;
+  *out = c->stats;
+  if (reset) c->stats = lx_stats{};
+  return LX_OK;
+}
+
+lx_status lx_ctx_kernel_name(lx_ctx* c, char* buf, int len) {
+  if (!c || !buf || len <= 0) return LX_E_INVAL;
+  const int v = c->loop[kVec2].built ? kVec2 : kVec1;
+  std::snprintf(buf, (size_t)len, "%s", c->loop[v].name);
+  return LX_OK;
+}
+
+}  // extern "C"
