@@ -1,0 +1,348 @@
+"""Benchmark of the Leja exponential-integrator hot path on one GB300 per rank.
+
+Workload (default): 2D linear advection-diffusion u_t = nu (u_xx + u_yy) +
+a (u_x + u_y) on the periodic unit square, 4096 x 4096, nu = 1e-2, a = 1,
+second-order central differences, FP64, seeded sum-of-three-Gaussians initial
+state, exponential Rosenbrock-Euler steps with h = 50 dt_CFL, tolerance 1e-10,
+spectral bound from 10 power-iteration passes (once, before the timed steps).
+A bench "step" is one Rosenbrock-Euler step: h f(u), one phi_1 Leja loop of
+fused iterations, and u + p.
+
+Metric: GDOF * Leja-iterations per second = sum over steps of
+nx*ny*iters / time / 1e9, the whole job over all ranks.  Multi-GPU runs are
+independent replicas (the path has no exchange step), so scaling is weak.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--precision fp64|mixed]
+  python bench.py --impl reference   # the CPU oracle on a bounded sample
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+import synth  # noqa: E402
+
+METRIC = "GDOF*Leja-iter/s"
+UNIT = "GDOF*iter/s"
+NX = NY = 4096
+NU, ADV = 1e-2, 1.0
+CFL_MULT = 50.0
+TOL = 1e-10
+ALG_BYTES = {"fp64": 32, "mixed": 24}  # algorithmic bytes per point per fused Leja iteration
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=10)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", default="lexgb", choices=["lexgb", "reference"])
+    p.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
+    p.add_argument("--n", type=int, default=NX)
+    p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    return p.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", str(rank)))
+    return rank, world, local
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during a region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+        self._t = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except (FileNotFoundError, OSError):
+            self.proc = None
+            return
+        self._t = threading.Thread(target=self._read, daemon=True)
+        self._t.start()
+        time.sleep(0.3)
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        if self._t:
+            self._t.join(timeout=2)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [x.strip() for x in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, parts[5:9]):
+                if val.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            return json.load(f), "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
+
+
+def kernel_source_sha():
+    h = hashlib.sha256()
+    for rel in ("paper_2310_08344_gb300/csrc/leja_kernels.cuh", "paper_2310_08344_gb300/csrc/lexgb_capi.cu"):
+        with open(os.path.join(ROOT, rel), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def ncu_traffic(kernel_name: str, n_points: int):
+    """DRAM bytes per launch of the fused kernel from the committed ncu
+    summary, or None when the summary is for other kernel sources."""
+    path = os.path.join(ROOT, "profiles", "leja_iter_traffic.json")
+    if not os.path.exists(path):
+        return None
+    with open(path) as f:
+        rec = json.load(f)
+    ent = rec.get(kernel_name)
+    if not ent or ent.get("source_sha") != kernel_source_sha():
+        return None
+    return float(ent["dram_bytes_per_point"]) * n_points
+
+
+def cpu_baseline(n_sample: int, seconds_hint: str):
+    """The oracle, as it stands, on a bounded sample of the workload:
+    one Rosenbrock-Euler step at n_sample^2 (same recipe, h = 50 dt_CFL)."""
+    import oracle
+
+    u0 = synth.gaussians_ic(n_sample, n_sample, seed=1)
+    h = CFL_MULT * synth.cfl_step(n_sample, n_sample, NU, ADV)
+    v0 = synth.power_start(n_sample * n_sample, seed=5)
+    rho, _, _ = oracle.power_iteration(oracle.ADVDIFF, n_sample, n_sample, NU, ADV, None, v0, 10)
+    c, g = oracle.spectral_interval(rho)
+    xi = oracle.leja_points(1000)
+    t0 = time.perf_counter()
+    out, iters, st = oracle.ros_eu(oracle.ADVDIFF, n_sample, n_sample, NU, ADV, u0, c, g, h, TOL, TOL, xi)
+    dt = time.perf_counter() - t0
+    val = n_sample * n_sample * iters / dt / 1e9
+    return {"value": val, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"one Ros-Eu step at {n_sample}x{n_sample} ({iters} Leja iterations, {dt:.1f} s, "
+                      f"single-threaded C oracle){seconds_hint}"}
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return 0
+    n_sample = 1024
+    import oracle
+
+    u0 = synth.gaussians_ic(n_sample, n_sample, seed=1)
+    h = CFL_MULT * synth.cfl_step(n_sample, n_sample, NU, ADV)
+    v0 = synth.power_start(n_sample * n_sample, seed=5)
+    rho, _, _ = oracle.power_iteration(oracle.ADVDIFF, n_sample, n_sample, NU, ADV, None, v0, 10)
+    c, g = oracle.spectral_interval(rho)
+    xi = oracle.leja_points(1000)
+    u = u0.copy()
+    for _ in range(args.warmup):
+        u, it, st = oracle.ros_eu(oracle.ADVDIFF, n_sample, n_sample, NU, ADV, u, c, g, h, TOL, TOL, xi)
+    total = 0
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        u, it, st = oracle.ros_eu(oracle.ADVDIFF, n_sample, n_sample, NU, ADV, u, c, g, h, TOL, TOL, xi)
+        total += n_sample * n_sample * it
+    dt = time.perf_counter() - t0
+    val = total / dt / 1e9
+    line = {"impl": "reference", "metric": METRIC, "value": val, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3 / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": "advdiff-periodic-rosenbrock-euler", "nx": n_sample, "ny": n_sample, "nu": NU,
+                       "a": ADV, "h_over_dt_cfl": CFL_MULT, "tol": TOL,
+                       "note": "the CPU oracle on a bounded 1024^2 sample of the 4096^2 workload"},
+            "cpu_baseline": {"value": val, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": f"{args.steps} Ros-Eu steps at {n_sample}x{n_sample}, single-threaded"},
+            "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+    return 0
+
+
+def main():
+    args = parse()
+    rank, world, local = dist_env()
+    if args.impl == "reference":
+        return run_reference(args, rank, world)
+    import torch
+
+    import paper_2310_08344_gb300 as lx
+
+    if not torch.cuda.is_available():
+        raise SystemExit("bench.py needs a CUDA device")
+    torch.cuda.set_device(local)
+    pg = None
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+        pg = dist
+    n = args.n
+    N = n * n
+    prec = lx.MIXED if args.precision == "mixed" else lx.FP64
+    stream = torch.cuda.current_stream()
+    ctx = lx.leja_setup(n, n, NU, ADV, lx.ADVDIFF, prec, lx.ROS_EU, 1000, stream)
+    kname = lx.lx_ctx_kernel_name(ctx)
+    u0 = synth.gaussians_ic(n, n, seed=1)
+    h = CFL_MULT * synth.cfl_step(n, n, NU, ADV)
+    ua = torch.from_numpy(u0).cuda()
+    ub = torch.empty_like(ua)
+    v0 = torch.from_numpy(synth.power_start(N, seed=5)).cuda()
+    st, rho, _ = lx.power_bound(ctx, None, v0, 10)
+    if st != 0:
+        raise SystemExit(f"power_bound failed: {st}")
+    c, g = lx.spectral_interval(rho)
+
+    def step(src, dst):
+        st, err, it = lx.expint_step(ctx, src, None, dst, c, g, h, TOL, TOL)
+        if st != 0:
+            raise SystemExit(f"expint_step failed: {lx.STATUS.get(st, st)}")
+        return it
+
+    cur, nxt = ua, ub
+    for _ in range(max(args.warmup, 0)):
+        step(cur, nxt)
+        cur, nxt = nxt, cur
+    lx.lx_ctx_stats(ctx, reset=True)
+    clocks = ClockSampler(local)
+    clocks.start()
+    if pg:
+        pg.barrier()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    iters = []
+    for _ in range(args.steps):
+        iters.append(step(cur, nxt))
+        cur, nxt = nxt, cur
+    e1.record(stream)
+    torch.cuda.synchronize()
+    if pg:
+        pg.barrier()
+    clk = clocks.stop()
+    ms = e0.elapsed_time(e1)
+    stats = lx.lx_ctx_stats(ctx, reset=True)
+    units = float(N) * sum(iters)
+    t_local = ms / 1e3
+    if pg:
+        t = torch.tensor([t_local], device="cuda", dtype=torch.float64)
+        pg.all_reduce(t, op=pg.ReduceOp.MAX)
+        tot = torch.tensor([units], device="cuda", dtype=torch.float64)
+        pg.all_reduce(tot, op=pg.ReduceOp.SUM)
+        t_max, units_all = float(t.item()), float(tot.item())
+    else:
+        t_max, units_all = t_local, units
+    value = units_all / t_max / 1e9
+
+    # dominant kernel: the fused Leja iteration (one launch per iteration)
+    avg_launch_s = stats["loop_ms"] / 1e3 / max(stats["loop_iterations"], 1)
+    alg_bytes = ALG_BYTES[args.precision] * N
+    peaks, peak_src = measured_peaks()
+    achieved = alg_bytes / avg_launch_s / 1e9
+    traffic = ncu_traffic(kname, N)
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                "frac": achieved / peaks["hbm_gbs"], "traffic": traffic,
+                "kernel": kname, "alg_bytes_per_launch": alg_bytes, "avg_launch_us": avg_launch_s * 1e6,
+                "peak_source": f"{peak_src} (MEASURED_PEAKS.json hbm_gbs, burst copy)"}
+    launches = args.steps * 4 + int(stats["loop_iterations"])
+
+    # end to end through the host-buffer entry point
+    e2e = None
+    if not args.no_e2e:
+        hin = torch.from_numpy(cur.cpu().numpy()).pin_memory()
+        hout = torch.empty_like(hin).pin_memory()
+        st, err, it = lx.expint_step_host(ctx, hin, None, hout, c, g, h, TOL, TOL)  # warm
+        if pg:
+            pg.barrier()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        tot_it = 0
+        for _ in range(args.steps):
+            st, err, it = lx.expint_step_host(ctx, hin, None, hout, c, g, h, TOL, TOL)
+            if st != 0:
+                raise SystemExit(f"expint_step_host failed: {st}")
+            tot_it += it
+            hin, hout = hout, hin
+        dt = time.perf_counter() - t0
+        e_units = float(N) * tot_it
+        if pg:
+            tt = torch.tensor([dt], device="cuda", dtype=torch.float64)
+            pg.all_reduce(tt, op=pg.ReduceOp.MAX)
+            uu = torch.tensor([e_units], device="cuda", dtype=torch.float64)
+            pg.all_reduce(uu, op=pg.ReduceOp.SUM)
+            dt, e_units = float(tt.item()), float(uu.item())
+        e2e = {"value": e_units / dt / 1e9, "unit": UNIT, "h2d_bytes_per_step": 8 * N, "d2h_bytes_per_step": 8 * N,
+               "path": "expint_step_host (pinned host buffers, copies inside the timed region)"}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(2048, "")
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "f64" if args.precision == "fp64" else "f32+f64",
+                "data": "synthetic",
+                "config": {"workload": "advdiff-4096x4096-rosenbrock-euler" if n == 4096 else f"advdiff-{n}x{n}",
+                           "nx": n, "ny": n, "nu": NU, "a": ADV, "h_over_dt_cfl": CFL_MULT, "tol": TOL,
+                           "precision": args.precision, "integrator": "ros_eu", "parallelism": f"replicas{world}",
+                           "leja_iters_per_step": iters, "rho": rho,
+                           "l2": "inputs larger than L2 (128 MiB per vector, 512 MiB moved per Leja iteration)"},
+                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "clocks": clk}
+        print(json.dumps(line))
+    ctx.close()
+    if pg:
+        pg.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())
