@@ -40,7 +40,7 @@ NX = NY = 4096
 NU, ADV = 1e-2, 1.0
 CFL_MULT = 50.0
 TOL = 1e-10
-ALG_BYTES = {"fp64": 32, "mixed": 24}  # algorithmic bytes per point per fused Leja iteration
+ALG_BYTES = {"fp64": 32, "mixed": 24, "df64": 32}  # algorithmic bytes per point per fused Leja iteration
 
 
 def parse():
@@ -49,7 +49,7 @@ def parse():
     p.add_argument("--steps", type=int, default=10)
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="lexgb", choices=["lexgb", "reference"])
-    p.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
+    p.add_argument("--precision", default="fp64", choices=["fp64", "mixed", "df64"])
     p.add_argument("--n", type=int, default=NX)
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu-baseline", action="store_true")
@@ -130,7 +130,8 @@ def measured_peaks():
 
 def kernel_source_sha():
     h = hashlib.sha256()
-    for rel in ("paper_2310_08344_gb300/csrc/leja_kernels.cuh", "paper_2310_08344_gb300/csrc/lexgb_capi.cu"):
+    for rel in ("paper_2310_08344_gb300/csrc/leja_kernels.cuh", "paper_2310_08344_gb300/csrc/leja_df64.cuh",
+                "paper_2310_08344_gb300/csrc/lexgb_capi.cu"):
         with open(os.path.join(ROOT, rel), "rb") as f:
             h.update(f.read())
     return h.hexdigest()[:16]
@@ -226,7 +227,7 @@ def main():
         pg = dist
     n = args.n
     N = n * n
-    prec = lx.MIXED if args.precision == "mixed" else lx.FP64
+    prec = {"fp64": lx.FP64, "mixed": lx.MIXED, "df64": lx.DF64}[args.precision]
     stream = torch.cuda.current_stream()
     ctx = lx.leja_setup(n, n, NU, ADV, lx.ADVDIFF, prec, lx.ROS_EU, 1000, stream)
     kname = lx.lx_ctx_kernel_name(ctx)
@@ -329,7 +330,7 @@ def main():
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
-                "vs_baseline": None, "dtype": "f64" if args.precision == "fp64" else "f32+f64",
+                "vs_baseline": None, "dtype": {"fp64": "f64", "mixed": "f32+f64", "df64": "f32x2 (float-float, FP64-accurate)"}[args.precision],
                 "data": "synthetic",
                 "config": {"workload": "advdiff-4096x4096-rosenbrock-euler" if n == 4096 else f"advdiff-{n}x{n}",
                            "nx": n, "ny": n, "nu": NU, "a": ADV, "h_over_dt_cfl": CFL_MULT, "tol": TOL,

@@ -50,7 +50,7 @@ typedef enum {
 } lx_status;
 
 enum { LX_ADVDIFF = 0, LX_BURGERS = 1 };          /* lx_problem.kind */
-enum { LX_FP64 = 0, LX_MIXED = 1 };              /* lx_problem.precision */
+enum { LX_FP64 = 0, LX_MIXED = 1, LX_DF64 = 2 }; /* lx_problem.precision */
 enum { LX_ROS_EU = 0, LX_EXPRB32 = 1 };          /* integrator */
 
 typedef struct {
@@ -58,9 +58,15 @@ typedef struct {
   double nu;      /* diffusion coefficient */
   double a;       /* advection speed (LX_ADVDIFF only) */
   int kind;       /* LX_ADVDIFF or LX_BURGERS */
-  int precision;  /* LX_FP64: all arithmetic in double.  LX_MIXED: the Newton
-                     basis y_m and its stencil in float, the coefficients,
-                     the polynomial p and both stopping norms in double */
+  int precision;  /* LX_FP64: all arithmetic in double (FP64 pipe).
+                     LX_MIXED: the Newton basis y_m and its stencil in float;
+                     the coefficients, the polynomial p and both stopping
+                     norms in double.
+                     LX_DF64: FP64-accurate float-float ("double-float",
+                     48-bit significand) arithmetic on the FP32 pipe for the
+                     basis, the stencil and the polynomial; double inputs and
+                     outputs; norms accumulated in float-float from the
+                     leading float of each value.  LX_ADVDIFF only. */
 } lx_problem;
 
 typedef struct lx_ctx lx_ctx;
@@ -177,6 +183,13 @@ typedef struct {
   double power_ms;
 } lx_stats;
 lx_status lx_ctx_stats(lx_ctx* ctx, lx_stats* out, int reset);
+
+/* Loop launch mode: 0 (default) runs each Leja loop as one CUDA graph with a
+ * device-ended while node; 1 launches the iteration kernels from the host in
+ * batches of 8 with a status read-back per batch, for profilers that cannot
+ * see kernels inside conditional graphs.  The environment variable
+ * LEXGB_STREAM_LOOP=1 selects mode 1 at setup. */
+lx_status lx_ctx_set_loop_mode(lx_ctx* ctx, int stream_loop);
 
 /* Kernel selection of the context (for diagnostics): writes a short name of
  * the fused Leja-iteration kernel into buf (NUL-terminated, at most len). */

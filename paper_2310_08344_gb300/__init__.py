@@ -13,6 +13,7 @@ from .binding import (  # noqa: F401
     ADVDIFF,
     BURGERS,
     EXPRB32,
+    DF64,
     FP64,
     MIXED,
     ROS_EU,
@@ -25,6 +26,7 @@ from .binding import (  # noqa: F401
     leja_setup,
     lib,
     lx_ctx_kernel_name,
+    lx_ctx_set_loop_mode,
     lx_ctx_stats,
     lx_leja_coeff_count,
     lx_leja_coeffs,

@@ -13,7 +13,7 @@ OK, E_INVAL, E_NOMEM, E_CUDA, E_NOCONV, E_NONFINITE, E_TIMEOUT = range(7)
 STATUS = {0: "LX_OK", 1: "LX_E_INVAL", 2: "LX_E_NOMEM", 3: "LX_E_CUDA", 4: "LX_E_NOCONV", 5: "LX_E_NONFINITE",
           6: "LX_E_TIMEOUT"}
 ADVDIFF, BURGERS = 0, 1
-FP64, MIXED = 0, 1
+FP64, MIXED, DF64 = 0, 1, 2
 ROS_EU, EXPRB32 = 0, 1
 
 _dp = C.POINTER(C.c_double)
@@ -71,6 +71,7 @@ def lib():
                                            C.c_double, _dp, _ip]
             L.lx_ctx_stats.argtypes = [_vp, C.POINTER(LxStats), C.c_int]
             L.lx_ctx_kernel_name.argtypes = [_vp, C.c_char_p, C.c_int]
+            L.lx_ctx_set_loop_mode.argtypes = [_vp, C.c_int]
             _lib = L
     return _lib
 
@@ -232,3 +233,7 @@ def lx_ctx_kernel_name(ctx: Context) -> str:
     buf = C.create_string_buffer(128)
     lib().lx_ctx_kernel_name(ctx.handle, buf, 128)
     return buf.value.decode()
+
+
+def lx_ctx_set_loop_mode(ctx: Context, stream_loop: int) -> int:
+    return lib().lx_ctx_set_loop_mode(ctx.handle, int(stream_loop))

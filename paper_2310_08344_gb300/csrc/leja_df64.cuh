@@ -1,0 +1,324 @@
+// Double-float ("df64") form of the fused Leja iteration for GB300.
+//
+// GB300 issues FP64 fused multiply-adds at about 1/58 of its FP32 rate
+// (measured: ~0.6 T DFMA/s against ~35 T FFMA/s), so a stencil iteration
+// written in native double is bound by the FP64 pipe at about a third of the
+// HBM bandwidth.  This form keeps every vector value as an unevaluated sum of
+// two floats (hi + lo, 48 significant bits, relative rounding ~2^-48) and
+// does all per-point arithmetic on the FP32 pipe with error-free
+// transformations:
+//   TwoSum (Knuth), FastTwoSum (Dekker), TwoProduct by FMA, and the
+//   compensated dot product Dot2 of Ogita, Rump and Oishi (2005) for the
+//   five-point stencil.
+// The basis y_m and the polynomial p_m live in context buffers as float2
+// (8 bytes per point, the same traffic as double); the first iteration reads
+// the caller's double input and the loop ends with one conversion pass into
+// the caller's double output.  Inputs are scaled by an exact power of two so
+// that max|w| is in [1, 2): the float exponent range then covers the data.
+#pragma once
+
+#include "leja_kernels.cuh"
+
+namespace lexgb {
+
+struct dfv {
+  float h, l;
+};
+
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+  s = __fadd_rn(a, b);
+  const float bb = __fsub_rn(s, a);
+  e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+
+__device__ __forceinline__ void fast_two_sum(float a, float b, float& s, float& e) {
+  s = __fadd_rn(a, b);
+  e = __fsub_rn(b, __fsub_rn(s, a));
+}
+
+__device__ __forceinline__ void two_prod(float a, float b, float& p, float& e) {
+  p = __fmul_rn(a, b);
+  e = __fmaf_rn(a, b, -p);
+}
+
+// Split a double into hi + lo floats (exact up to the 48-bit precision).
+__device__ __forceinline__ dfv df_from_double(double x) {
+  dfv r;
+  r.h = __double2float_rn(x);
+  r.l = __double2float_rn(x - (double)r.h);
+  return r;
+}
+
+__device__ __forceinline__ double df_to_double(dfv a) { return (double)a.h + (double)a.l; }
+
+// sum_{k<5} w_k y_k with w_k = wh_k + wl_k, y_k = y_k.h + y_k.l (Dot2).
+__device__ __forceinline__ dfv df_dot5(const float (&wh)[5], const float (&wl)[5], const dfv (&y)[5]) {
+  float s, c, p, e, t;
+  two_prod(wh[0], y[0].h, s, c);
+#pragma unroll
+  for (int k = 1; k < 5; ++k) {
+    two_prod(wh[k], y[k].h, p, e);
+    two_sum(s, p, s, t);
+    c = __fadd_rn(c, __fadd_rn(t, e));
+  }
+#pragma unroll
+  for (int k = 0; k < 5; ++k) {
+    c = __fmaf_rn(wh[k], y[k].l, c);
+    c = __fmaf_rn(wl[k], y[k].h, c);
+  }
+  dfv r;
+  two_sum(s, c, r.h, r.l);
+  return r;
+}
+
+// p + d * y
+__device__ __forceinline__ dfv df_axpy(dfv d, dfv y, dfv p) {
+  float q, qe, s, t;
+  two_prod(d.h, y.h, q, qe);
+  qe = __fmaf_rn(d.h, y.l, qe);
+  qe = __fmaf_rn(d.l, y.h, qe);
+  two_sum(p.h, q, s, t);
+  t = __fadd_rn(t, __fadd_rn(p.l, qe));
+  dfv r;
+  fast_two_sum(s, t, r.h, r.l);
+  return r;
+}
+
+// d * y
+__device__ __forceinline__ dfv df_mul(dfv d, dfv y) {
+  float q, qe;
+  two_prod(d.h, y.h, q, qe);
+  qe = __fmaf_rn(d.h, y.l, qe);
+  qe = __fmaf_rn(d.l, y.h, qe);
+  dfv r;
+  fast_two_sum(q, qe, r.h, r.l);
+  return r;
+}
+
+// acc += x (x a float partial sum of squares)
+__device__ __forceinline__ void df_acc(dfv& acc, float x) {
+  float s, e;
+  two_sum(acc.h, x, s, e);
+  acc.h = s;
+  acc.l = __fadd_rn(acc.l, e);
+}
+
+__device__ __forceinline__ double pow2(int k) {  // 2^k for k in [-1022, 1023]
+  return __hiloint2double((k + 1023) << 20, 0);
+}
+
+template <int VEC>
+__device__ __forceinline__ void df_load_row(const float2* __restrict__ row, int c, int nx, dfv (&v)[VEC]) {
+  if constexpr (VEC == 4) {
+    const float4 a = __ldg(reinterpret_cast<const float4*>(row + c));
+    const float4 b = __ldg(reinterpret_cast<const float4*>(row + c + 2));
+    v[0] = {a.x, a.y};
+    v[1] = {a.z, a.w};
+    v[2] = {b.x, b.y};
+    v[3] = {b.z, b.w};
+  } else {
+#pragma unroll
+    for (int k = 0; k < VEC; ++k) {
+      const float2 t = (c + k < nx) ? __ldg(row + c + k) : make_float2(0.f, 0.f);
+      v[k] = {t.x, t.y};
+    }
+  }
+}
+
+// First iteration: the caller's double vector, scaled by 2^-k, split to df.
+template <int VEC>
+__device__ __forceinline__ void df_load_row(const double* __restrict__ row, int c, int nx, double sc, dfv (&v)[VEC]) {
+  if constexpr (VEC == 4) {
+    const double2 a = __ldg(reinterpret_cast<const double2*>(row + c));
+    const double2 b = __ldg(reinterpret_cast<const double2*>(row + c + 2));
+    v[0] = df_from_double(a.x * sc);
+    v[1] = df_from_double(a.y * sc);
+    v[2] = df_from_double(b.x * sc);
+    v[3] = df_from_double(b.y * sc);
+  } else {
+#pragma unroll
+    for (int k = 0; k < VEC; ++k) v[k] = df_from_double((c + k < nx) ? __ldg(row + c + k) * sc : 0.0);
+  }
+}
+
+template <int VEC>
+__device__ __forceinline__ void df_store_row(float2* __restrict__ row, int c, int nx, const dfv (&v)[VEC]) {
+  if constexpr (VEC == 4) {
+    *reinterpret_cast<float4*>(row + c) = make_float4(v[0].h, v[0].l, v[1].h, v[1].l);
+    *reinterpret_cast<float4*>(row + c + 2) = make_float4(v[2].h, v[2].l, v[3].h, v[3].l);
+  } else {
+#pragma unroll
+    for (int k = 0; k < VEC; ++k)
+      if (c + k < nx) row[c + k] = make_float2(v[k].h, v[k].l);
+  }
+}
+
+template <int VEC>
+__device__ __forceinline__ void df_load_p(const float2* __restrict__ row, int c, int nx, dfv (&v)[VEC]) {
+  if constexpr (VEC == 4) {
+    const float4 a = *reinterpret_cast<const float4*>(row + c);
+    const float4 b = *reinterpret_cast<const float4*>(row + c + 2);
+    v[0] = {a.x, a.y};
+    v[1] = {a.z, a.w};
+    v[2] = {b.x, b.y};
+    v[3] = {b.z, b.w};
+  } else {
+#pragma unroll
+    for (int k = 0; k < VEC; ++k) {
+      const float2 t = (c + k < nx) ? row[c + k] : make_float2(0.f, 0.f);
+      v[k] = {t.x, t.y};
+    }
+  }
+}
+
+__device__ __forceinline__ dfv shfl_up_df(dfv v) {
+  return {__shfl_up_sync(0xffffffffu, v.h, 1), __shfl_up_sync(0xffffffffu, v.l, 1)};
+}
+__device__ __forceinline__ dfv shfl_down_df(dfv v) {
+  return {__shfl_down_sync(0xffffffffu, v.h, 1), __shfl_down_sync(0xffffffffu, v.l, 1)};
+}
+
+// Halo value of the row as df (the first iteration reads doubles).
+__device__ __forceinline__ dfv df_point(const float2* __restrict__ src, size_t q, double) {
+  const float2 t = __ldg(src + q);
+  return {t.x, t.y};
+}
+__device__ __forceinline__ dfv df_point(const double* __restrict__ src, size_t q, double sc) {
+  return df_from_double(__ldg(src + q) * sc);
+}
+
+// One strip of the diffusion-advection iteration in df arithmetic.
+// S = double (first iteration, caller's w) or float2 (basis buffer).
+template <int VEC, typename S, bool FIRST>
+__device__ __forceinline__ void df_strip_advdiff(const LoopArgs& A, const S* __restrict__ src, float2* __restrict__ dst,
+                                                 float2* __restrict__ p, int col0, int r0, int r1,
+                                                 const float (&wh)[5], const float (&wl)[5], dfv d0, dfv dm1,
+                                                 double sc, dfv& accy, dfv& accp) {
+  const int lane = threadIdx.x & 31;
+  const int nx = A.nx, ny = A.ny;
+  const int c = col0 + lane * VEC;
+  const int cl = c + VEC - 1;
+  const bool active = c < nx;
+  const int cw = col0 == 0 ? nx - 1 : col0 - 1;
+  const int ce = (cl + 1 >= nx) ? 0 : cl + 1;
+  const bool need_e = active && (lane == 31 || cl + 1 >= nx);
+
+  dfv ys[VEC], yc[VEC], yn[VEC];
+  if constexpr (FIRST) {
+    df_load_row<VEC>(src + (size_t)wrap_dn(r0, ny) * nx, c, nx, sc, ys);
+    df_load_row<VEC>(src + (size_t)r0 * nx, c, nx, sc, yc);
+  } else {
+    df_load_row<VEC>(src + (size_t)wrap_dn(r0, ny) * nx, c, nx, ys);
+    df_load_row<VEC>(src + (size_t)r0 * nx, c, nx, yc);
+  }
+  for (int r = r0; r < r1; ++r) {
+    const size_t ro = (size_t)r * nx;
+    if constexpr (FIRST)
+      df_load_row<VEC>(src + (size_t)wrap_up(r, ny) * nx, c, nx, sc, yn);
+    else
+      df_load_row<VEC>(src + (size_t)wrap_up(r, ny) * nx, c, nx, yn);
+    dfv pold[VEC];
+    if constexpr (!FIRST) df_load_p<VEC>(p + ro, c, nx, pold);
+    dfv xw = shfl_up_df(yc[VEC - 1]);
+    dfv xe = shfl_down_df(yc[0]);
+    if (lane == 0) xw = df_point(src, ro + cw, sc);
+    if (need_e) xe = df_point(src, ro + ce, sc);
+    dfv ynew[VEC], pnew[VEC];
+    float fy = 0.f, fp = 0.f;
+#pragma unroll
+    for (int k = 0; k < VEC; ++k) {
+      // terms ordered E, W, N, S, C to match the weights
+      const dfv t[5] = {k == VEC - 1 ? xe : yc[(k + 1) % VEC], k == 0 ? xw : yc[(k + VEC - 1) % VEC], yn[k], ys[k],
+                        yc[k]};
+      ynew[k] = df_dot5(wh, wl, t);
+      const dfv po = FIRST ? df_mul(d0, yc[k]) : pold[k];
+      pnew[k] = df_axpy(dm1, ynew[k], po);
+      if (c + k < nx) {
+        fy = __fmaf_rn(ynew[k].h, ynew[k].h, fy);
+        fp = __fmaf_rn(pnew[k].h, pnew[k].h, fp);
+      }
+    }
+    df_acc(accy, fy);
+    df_acc(accp, fp);
+    if (active) {
+      df_store_row<VEC>(dst + ro, c, nx, ynew);
+      df_store_row<VEC>(p + ro, c, nx, pnew);
+    }
+#pragma unroll
+    for (int k = 0; k < VEC; ++k) {
+      ys[k] = yc[k];
+      yc[k] = yn[k];
+    }
+  }
+}
+
+template <int VEC>
+__global__ void __launch_bounds__(kThreadsPerBlock)
+    leja_iter_df_advdiff_kernel(const LoopArgs* __restrict__ Ap, LoopState* __restrict__ st,
+                                double* __restrict__ partials, unsigned int* __restrict__ ticket,
+                                cudaGraphConditionalHandle cond) {
+  const LoopArgs& A = *Ap;
+  const int m = __ldcg(&st->m);
+  if (__ldcg(&st->done)) return;
+  const int kexp = __ldcg(&st->kscale);
+  const double sc = pow2(-kexp);
+  const int nx = A.nx, ny = A.ny;
+  const int H = A.strip_h;
+  const int ncs = (nx + 32 * VEC - 1) / (32 * VEC);
+  const int nstrips = ncs * ((ny + H - 1) / H);
+  const double xim = __ldg(A.xi + m);
+  const double dm1d = __ldg(A.d + m + 1);
+  const dfv dm1 = df_from_double(dm1d);
+  const dfv d0 = df_from_double(__ldg(A.d));
+  const dfv wc = df_from_double(A.wc0 - xim);
+  const float wh[5] = {A.wf[0], A.wf[2], A.wf[4], A.wf[6], wc.h};
+  const float wl[5] = {A.wf[1], A.wf[3], A.wf[5], A.wf[7], wc.l};
+  float2* dst = reinterpret_cast<float2*>((m & 1) ? A.y1 : A.y0);
+  float2* p = A.pdf;
+  dfv accy = {0.f, 0.f}, accp = {0.f, 0.f};
+  const int warp = threadIdx.x >> 5;
+  for (int s = blockIdx.x * kWarpsPerBlock + warp; s < nstrips; s += gridDim.x * kWarpsPerBlock) {
+    const int col0 = (s % ncs) * 32 * VEC;
+    const int r0 = (s / ncs) * H;
+    const int r1 = min(r0 + H, ny);
+    if (m == 0) {
+      df_strip_advdiff<VEC, double, true>(A, A.w, dst, p, col0, r0, r1, wh, wl, d0, dm1, sc, accy, accp);
+    } else {
+      const float2* src = reinterpret_cast<const float2*>(((m - 1) & 1) ? A.y1 : A.y0);
+      df_strip_advdiff<VEC, float2, false>(A, src, dst, p, col0, r0, r1, wh, wl, d0, dm1, sc, accy, accp);
+    }
+  }
+  double sy = df_to_double(accy), sp = df_to_double(accp);
+  if (!last_block_total2(sy, sp, partials, ticket)) return;
+  if (threadIdx.x == 0) leja_finalize(A, st, m, dm1d, sy, sp, pow2(kexp), cond);
+}
+
+// max over |w| of the binary exponent, to choose the power-of-two scaling.
+__global__ void __launch_bounds__(kThreadsPerBlock) df_scale_kernel(long long n, const double* __restrict__ w,
+                                                                    LoopState* st) {
+  int e = 0;
+  for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < n; q += (long long)gridDim.x * blockDim.x)
+    e = max(e, (int)((__double2hiint(w[q]) >> 20) & 0x7ff));
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) e = max(e, __shfl_xor_sync(0xffffffffu, e, o));
+  if ((threadIdx.x & 31) == 0) atomicMax(&st->wexp, e);
+}
+
+// kscale from the maximal exponent (one thread).
+__global__ void df_scale_finish_kernel(LoopState* st) {
+  int e = st->wexp;  // biased; 0 for an all-zero (or subnormal) vector
+  int k = (e == 0) ? 0 : (e == 2047 ? 0 : e - 1023);
+  st->kscale = max(-1000, min(1000, k));
+}
+
+// out = (p.h + p.l) * 2^k
+__global__ void df_output_kernel(long long n, const float2* __restrict__ pdf, double* __restrict__ out,
+                                 const LoopState* st) {
+  const double s = pow2(__ldcg(&st->kscale));
+  for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < n; q += (long long)gridDim.x * blockDim.x) {
+    const float2 t = pdf[q];
+    out[q] = ((double)t.x + (double)t.y) * s;
+  }
+}
+
+}  // namespace lexgb

@@ -48,6 +48,9 @@ struct LoopArgs {
   //               - u (gx (yE - yW) + gy (yN - yS))
   double lx, ly, gx, gy, inv_gamma;
   double rtol, atol;
+  float wf[8];        // df64 form: hi/lo float parts of wxp, wxm, wyp, wym
+  float2* pdf;        // df64 form: the polynomial as float pairs
+  int use_cond;       // 1: end the graph's while-loop from the device
 };
 
 // Device-resident loop and reduction state.
@@ -65,6 +68,8 @@ struct LoopState {
   double rho, rho_prev;      // power iteration estimates
   double red;                // result of a reduction kernel (e.g. the step error)
   int pmax;                  // power iteration: pass limit
+  int wexp;                  // df64 form: largest biased exponent of |w|
+  int kscale;                // df64 form: w is scaled by 2^-kscale
   int pad;
 };
 
@@ -253,6 +258,39 @@ __device__ __forceinline__ bool last_block_total2(double& a, double& b, double* 
   return true;
 }
 
+// Stopping test of one Leja iteration (thread 0 of the last block):
+// converged when |d_{m+1}| ||y_{m+1}|| <= rtol ||p_{m+1}|| + atol (Sec. 2.2),
+// with ||x|| = sqrt(sum x^2 / N); nscale undoes an input scaling.
+__device__ __forceinline__ void leja_finalize(const LoopArgs& A, LoopState* st, int m, double dm1, double sy,
+                                              double sp, double nscale, cudaGraphConditionalHandle cond) {
+  const double inv_n = 1.0 / double(A.n);
+  const double ynorm = sqrt(sy * inv_n) * nscale, pnorm = sqrt(sp * inv_n) * nscale;
+  const double e = fabs(dm1) * ynorm;
+  const int m1 = m + 1;
+  int status = 0;
+  bool done = false;
+  if (!isfinite(e) || !isfinite(pnorm)) {
+    status = 5;  // LX_E_NONFINITE
+    done = true;
+  } else if (e <= A.rtol * pnorm + A.atol) {
+    done = true;
+  } else if (m1 >= A.kmax) {
+    status = 4;  // LX_E_NOCONV
+    done = true;
+  }
+  st->m = m1;
+  st->ynorm = ynorm;
+  st->pnorm = pnorm;
+  st->err = e;
+  if (done) {
+    st->status = status;
+    st->done = 1;
+    st->iters_total += m1;
+    if (st->status_total == 0) st->status_total = status;
+    if (A.use_cond) cudaGraphSetConditional(cond, 0);
+  }
+}
+
 template <int KIND, typename T, int VEC>
 __global__ void __launch_bounds__(kThreadsPerBlock)
     leja_iter_kernel(const LoopArgs* __restrict__ Ap, LoopState* __restrict__ st, double* __restrict__ partials,
@@ -283,34 +321,7 @@ __global__ void __launch_bounds__(kThreadsPerBlock)
     }
   }
   if (!last_block_total2(sy, sp, partials, ticket)) return;
-  if (threadIdx.x == 0) {
-    const double inv_n = 1.0 / double(A.n);
-    const double ynorm = sqrt(sy * inv_n), pnorm = sqrt(sp * inv_n);
-    const double e = fabs(dm1) * ynorm;
-    const int m1 = m + 1;
-    int status = 0;
-    bool done = false;
-    if (!isfinite(e) || !isfinite(pnorm)) {
-      status = 5;  // LX_E_NONFINITE
-      done = true;
-    } else if (e <= A.rtol * pnorm + A.atol) {
-      done = true;
-    } else if (m1 >= A.kmax) {
-      status = 4;  // LX_E_NOCONV
-      done = true;
-    }
-    st->m = m1;
-    st->ynorm = ynorm;
-    st->pnorm = pnorm;
-    st->err = e;
-    if (done) {
-      st->status = status;
-      st->done = 1;
-      st->iters_total += m1;
-      if (st->status_total == 0) st->status_total = status;
-      cudaGraphSetConditional(cond, 0);
-    }
-  }
+  if (threadIdx.x == 0) leja_finalize(A, st, m, dm1, sy, sp, 1.0, cond);
 }
 
 // Writes the loop arguments and resets the per-loop state (one thread).
@@ -319,6 +330,8 @@ __global__ void set_loop_args_kernel(LoopArgs args, LoopArgs* dst, LoopState* st
   st->m = 0;
   st->status = 0;
   st->done = 0;
+  st->wexp = 0;
+  st->kscale = 0;
   *ticket = 0u;
 }
 

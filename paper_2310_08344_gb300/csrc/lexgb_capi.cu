@@ -12,10 +12,12 @@
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <string>
 #include <vector>
 
+#include "leja_df64.cuh"
 #include "leja_kernels.cuh"
 #include "lexgb_internal.h"
 
@@ -79,8 +81,10 @@ struct lx_ctx {
   double* d_p3 = nullptr;  // phi_3 result (EXPRB32)
   double* d_pw[2] = {nullptr, nullptr};  // power iteration ping-pong
   double* d_io[3] = {nullptr, nullptr, nullptr};  // staging for expint_step_host
+  float2* d_pdf = nullptr;  // df64 form: polynomial as float pairs
   double* d_partials = nullptr;
   int partials_cap = 0;
+  int stream_loop = 0;  // 1: launch the iterations from the host (profilers)
   unsigned int* d_ticket = nullptr;
   LoopState* d_state = nullptr;
   LoopArgs* d_args = nullptr;
@@ -101,6 +105,9 @@ size_t basis_bytes(const lx_ctx* c) {
   return (size_t)c->n * (c->prob.precision == LX_MIXED ? sizeof(float) : sizeof(double));
 }
 
+// Points per thread of the wide variant.
+int wide_vec(const lx_ctx* c) { return c->prob.precision == LX_DF64 ? 4 : 2; }
+
 template <int KIND, typename T, int VEC>
 const void* iter_kernel_ptr() {
   return reinterpret_cast<const void*>(&leja_iter_kernel<KIND, T, VEC>);
@@ -109,6 +116,11 @@ const void* iter_kernel_ptr() {
 const void* pick_kernel(int kind, int precision, int variant, const char** name) {
   const bool mixed = precision == LX_MIXED;
   const bool v2 = variant == kVec2;
+  if (precision == LX_DF64) {
+    *name = v2 ? "leja_iter_df_advdiff_v4" : "leja_iter_df_advdiff_v1";
+    return v2 ? reinterpret_cast<const void*>(&leja_iter_df_advdiff_kernel<4>)
+              : reinterpret_cast<const void*>(&leja_iter_df_advdiff_kernel<1>);
+  }
   if (kind == LX_ADVDIFF) {
     if (!mixed) {
       *name = v2 ? "leja_iter_advdiff_f64_v2" : "leja_iter_advdiff_f64_v1";
@@ -126,7 +138,7 @@ const void* pick_kernel(int kind, int precision, int variant, const char** name)
 }
 
 int strips_for(const lx_ctx* c, int variant) {
-  const int vec = variant == kVec2 ? 2 : 1;
+  const int vec = variant == kVec2 ? wide_vec(c) : 1;
   const int ncs = (c->prob.nx + 32 * vec - 1) / (32 * vec);
   const int nrs = (c->prob.ny + c->strip_h - 1) / c->strip_h;
   return ncs * nrs;
@@ -178,9 +190,16 @@ lx_status build_loop_graph(lx_ctx* c, int variant) {
   return LX_OK;
 }
 
+int aux_blocks(const lx_ctx* c) {
+  const long long want = (c->n + kThreadsPerBlock - 1) / kThreadsPerBlock;
+  return (int)std::max<long long>(1, std::min<long long>(want, (long long)c->aux_grid));
+}
+
 bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
 
 int choose_variant(const lx_ctx* c, const double* w, const double* out) {
+  if (c->prob.precision == LX_DF64)  // out is written by the conversion pass
+    return (c->prob.nx % 128 == 0 && aligned16(w)) ? kVec2 : kVec1;
   if (c->prob.nx % 64 == 0 && aligned16(w) && aligned16(out) && aligned16(c->d_y[0]) && aligned16(c->d_y[1]))
     return kVec2;
   return kVec1;
@@ -245,19 +264,53 @@ lx_status launch_loop(lx_ctx* c, int slot, int l, const double* u, const double*
   a.wc0 = (-2.0 * nx2 - 2.0 * ny2 - cc) * ig;
   a.rtol = rtol;
   a.atol = atol;
+  const double wd[4] = {a.wxp, a.wxm, a.wyp, a.wym};
+  for (int k = 0; k < 4; ++k) {
+    const float hi = (float)wd[k];
+    a.wf[2 * k] = hi;
+    a.wf[2 * k + 1] = (float)(wd[k] - (double)hi);
+  }
+  a.pdf = c->d_pdf;
+  a.use_cond = c->stream_loop ? 0 : 1;
+  const bool df = P.precision == LX_DF64;
   set_loop_args_kernel<<<1, 1, 0, c->stream>>>(a, c->d_args, c->d_state, c->d_ticket);
   LX_CUDA(cudaGetLastError());
+  if (df) {
+    df_scale_kernel<<<aux_blocks(c), kThreadsPerBlock, 0, c->stream>>>(c->n, w, c->d_state);
+    LX_CUDA(cudaGetLastError());
+    df_scale_finish_kernel<<<1, 1, 0, c->stream>>>(c->d_state);
+    LX_CUDA(cudaGetLastError());
+  }
   if (c->ev_used + 2 > 8) return LX_E_INVAL;
   LX_CUDA(cudaEventRecord(c->ev[c->ev_used], c->stream));
-  LX_CUDA(cudaGraphLaunch(c->loop[variant].exec, c->stream));
+  if (!c->stream_loop) {
+    LX_CUDA(cudaGraphLaunch(c->loop[variant].exec, c->stream));
+  } else {
+    // Host-driven loop for profilers that cannot see kernels inside a
+    // conditional graph: batches of launches, each kernel returning at once
+    // after the device has set done.
+    LoopGraph& L = c->loop[variant];
+    const LoopArgs* args = c->d_args;
+    LoopState* stp = c->d_state;
+    double* partials = c->d_partials;
+    unsigned int* ticket = c->d_ticket;
+    cudaGraphConditionalHandle cond = 0;
+    void* kargs[] = {(void*)&args, (void*)&stp, (void*)&partials, (void*)&ticket, (void*)&cond};
+    for (int it = 0; it < a.kmax; it += 8) {
+      for (int k = 0; k < 8; ++k)
+        LX_CUDA(cudaLaunchKernel(L.func, dim3(L.grid), dim3(kThreadsPerBlock), kargs, 0, c->stream));
+      LX_CUDA(cudaMemcpyAsync(c->h_state, c->d_state, sizeof(LoopState), cudaMemcpyDeviceToHost, c->stream));
+      LX_CUDA(cudaStreamSynchronize(c->stream));
+      if (c->h_state->done) break;
+    }
+  }
   LX_CUDA(cudaEventRecord(c->ev[c->ev_used + 1], c->stream));
   c->ev_used += 2;
+  if (df) {
+    df_output_kernel<<<aux_blocks(c), kThreadsPerBlock, 0, c->stream>>>(c->n, c->d_pdf, out, c->d_state);
+    LX_CUDA(cudaGetLastError());
+  }
   return LX_OK;
-}
-
-int aux_blocks(const lx_ctx* c) {
-  const long long want = (c->n + kThreadsPerBlock - 1) / kThreadsPerBlock;
-  return (int)std::max<long long>(1, std::min<long long>(want, (long long)c->aux_grid));
 }
 
 lx_status begin_call(lx_ctx* c) {
@@ -287,7 +340,8 @@ bool valid_problem(const lx_problem* p) {
   if (p->nx < 1 || p->ny < 1) return false;
   if ((long long)p->nx * p->ny > (1LL << 31)) return false;
   if (p->kind != LX_ADVDIFF && p->kind != LX_BURGERS) return false;
-  if (p->precision != LX_FP64 && p->precision != LX_MIXED) return false;
+  if (p->precision != LX_FP64 && p->precision != LX_MIXED && p->precision != LX_DF64) return false;
+  if (p->precision == LX_DF64 && p->kind != LX_ADVDIFF) return false;
   if (!std::isfinite(p->nu) || !std::isfinite(p->a)) return false;
   return true;
 }
@@ -330,6 +384,7 @@ void leja_destroy(lx_ctx* c) {
   cudaFree(c->d_pw[0]);
   cudaFree(c->d_pw[1]);
   for (auto* p : c->d_io) cudaFree(p);
+  cudaFree(c->d_pdf);
   cudaFree(c->d_partials);
   cudaFree(c->d_ticket);
   cudaFree(c->d_state);
@@ -377,6 +432,12 @@ lx_status leja_setup(const lx_problem* prob, int integrator, int max_leja, void*
   if (!dmalloc(&c->d_y[0], basis_bytes(c)) || !dmalloc(&c->d_y[1], basis_bytes(c))) return fail(LX_E_NOMEM);
   if (!dmalloc((void**)&c->d_f, nb) || !dmalloc((void**)&c->d_s, nb)) return fail(LX_E_NOMEM);
   if (integrator == LX_EXPRB32 && !dmalloc((void**)&c->d_p3, nb)) return fail(LX_E_NOMEM);
+  if (prob->precision == LX_DF64 && !dmalloc((void**)&c->d_pdf, sizeof(float2) * (size_t)c->n))
+    return fail(LX_E_NOMEM);
+  {
+    const char* env = std::getenv("LEXGB_STREAM_LOOP");
+    c->stream_loop = (env && env[0] == '1') ? 1 : 0;
+  }
   c->partials_cap = 64 * c->sm_count;
   if (!dmalloc((void**)&c->d_partials, sizeof(double) * 2 * c->partials_cap)) return fail(LX_E_NOMEM);
   if (!dmalloc((void**)&c->d_ticket, sizeof(unsigned int))) return fail(LX_E_NOMEM);
@@ -395,7 +456,7 @@ lx_status leja_setup(const lx_problem* prob, int integrator, int max_leja, void*
   // the auxiliary kernels use one resident wave of the aux kernels' blocks
   c->aux_grid = 4 * c->sm_count;
   for (int v = 0; v < kNumVariants; ++v) {
-    if (v == kVec2 && prob->nx % 64 != 0) continue;
+    if (v == kVec2 && prob->nx % (32 * wide_vec(c)) != 0) continue;
     lx_status s = build_loop_graph(c, v);
     if (s != LX_OK) return fail(s);
   }
@@ -543,6 +604,12 @@ lx_status lx_ctx_stats(lx_ctx* c, lx_stats* out, int reset) {
   if (!c || !out) return LX_E_INVAL;
   *out = c->stats;
   if (reset) c->stats = lx_stats{};
+  return LX_OK;
+}
+
+lx_status lx_ctx_set_loop_mode(lx_ctx* c, int stream_loop) {
+  if (!c || (stream_loop != 0 && stream_loop != 1)) return LX_E_INVAL;
+  c->stream_loop = stream_loop;
   return LX_OK;
 }
 
