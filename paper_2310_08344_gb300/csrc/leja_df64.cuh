@@ -14,7 +14,12 @@
 // (8 bytes per point, the same traffic as double); the first iteration reads
 // the caller's double input and the loop ends with one conversion pass into
 // the caller's double output.  Inputs are scaled by an exact power of two so
-// that max|w| is in [1, 2): the float exponent range then covers the data.
+// that max|w| is in [1, 2), and the stored basis is renormalised every
+// iteration by a power of two 2^-dlt (folded exactly into the five stencil
+// weights and the Newton coefficient, so it costs nothing per point): the
+// stored vectors stay near unit norm even when the Newton basis itself grows
+// or decays by many orders of magnitude, and the float exponent range always
+// covers them.
 #pragma once
 
 #include "leja_kernels.cuh"
@@ -103,7 +108,10 @@ __device__ __forceinline__ void df_acc(dfv& acc, float x) {
   acc.l = __fadd_rn(acc.l, e);
 }
 
-__device__ __forceinline__ double pow2(int k) {  // 2^k for k in [-1022, 1023]
+// 2^k; 0 below the normal range, +inf above it (a vanished or overflowed basis).
+__device__ __forceinline__ double pow2(int k) {
+  if (k < -1022) return 0.0;
+  if (k > 1023) return __longlong_as_double(0x7ff0000000000000LL);
   return __hiloint2double((k + 1023) << 20, 0);
 }
 
@@ -261,6 +269,8 @@ __global__ void __launch_bounds__(kThreadsPerBlock)
   const int m = __ldcg(&st->m);
   if (__ldcg(&st->done)) return;
   const int kexp = __ldcg(&st->kscale);
+  const int sig = __ldcg(&st->sig);  // stored y_m = y_m 2^-sig
+  const int dlt = __ldcg(&st->dlt);  // stored y_{m+1} = y_{m+1} 2^-(sig + dlt)
   const double sc = pow2(-kexp);
   const int nx = A.nx, ny = A.ny;
   const int H = A.strip_h;
@@ -268,11 +278,14 @@ __global__ void __launch_bounds__(kThreadsPerBlock)
   const int nstrips = ncs * ((ny + H - 1) / H);
   const double xim = __ldg(A.xi + m);
   const double dm1d = __ldg(A.d + m + 1);
-  const dfv dm1 = df_from_double(dm1d);
+  // p (stored as p 2^-kexp) += d_{m+1} y_{m+1} = d_{m+1} 2^(sig+dlt-kexp) * stored y_{m+1}
+  const dfv dm1 = df_from_double(dm1d * pow2(sig + dlt - kexp));
   const dfv d0 = df_from_double(__ldg(A.d));
-  const dfv wc = df_from_double(A.wc0 - xim);
-  const float wh[5] = {A.wf[0], A.wf[2], A.wf[4], A.wf[6], wc.h};
-  const float wl[5] = {A.wf[1], A.wf[3], A.wf[5], A.wf[7], wc.l};
+  const double sw = pow2(-dlt);
+  const float swf = (float)sw;
+  const dfv wc = df_from_double((A.wc0 - xim) * sw);
+  const float wh[5] = {A.wf[0] * swf, A.wf[2] * swf, A.wf[4] * swf, A.wf[6] * swf, wc.h};
+  const float wl[5] = {A.wf[1] * swf, A.wf[3] * swf, A.wf[5] * swf, A.wf[7] * swf, wc.l};
   float2* dst = reinterpret_cast<float2*>((m & 1) ? A.y1 : A.y0);
   float2* p = A.pdf;
   dfv accy = {0.f, 0.f}, accp = {0.f, 0.f};
@@ -290,7 +303,15 @@ __global__ void __launch_bounds__(kThreadsPerBlock)
   }
   double sy = df_to_double(accy), sp = df_to_double(accp);
   if (!last_block_total2(sy, sp, partials, ticket)) return;
-  if (threadIdx.x == 0) leja_finalize(A, st, m, dm1d, sy, sp, pow2(kexp), cond);
+  if (threadIdx.x == 0) {
+    leja_finalize(A, st, m, dm1d, sy, sp, pow2(sig + dlt), pow2(kexp), cond);
+    // next renormalisation: bring the stored basis back to unit norm
+    const double rms = sqrt(sy / double(A.n));
+    int e = 0;
+    if (rms > 0.0 && isfinite(rms)) e = ilogb(rms);
+    st->sig = sig + dlt;
+    st->dlt = max(-100, min(100, e));
+  }
 }
 
 // max over |w| of the binary exponent, to choose the power-of-two scaling.
@@ -309,6 +330,8 @@ __global__ void df_scale_finish_kernel(LoopState* st) {
   int e = st->wexp;  // biased; 0 for an all-zero (or subnormal) vector
   int k = (e == 0) ? 0 : (e == 2047 ? 0 : e - 1023);
   st->kscale = max(-1000, min(1000, k));
+  st->sig = st->kscale;
+  st->dlt = 0;
 }
 
 // out = (p.h + p.l) * 2^k

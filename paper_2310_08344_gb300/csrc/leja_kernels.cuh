@@ -70,7 +70,8 @@ struct LoopState {
   int pmax;                  // power iteration: pass limit
   int wexp;                  // df64 form: largest biased exponent of |w|
   int kscale;                // df64 form: w is scaled by 2^-kscale
-  int pad;
+  int sig;                   // df64 form: the stored basis is y_m 2^-sig
+  int dlt;                   // df64 form: extra scaling 2^-dlt of the next step
 };
 
 __device__ __forceinline__ int wrap_up(int i, int n) { return i + 1 == n ? 0 : i + 1; }
@@ -262,9 +263,10 @@ __device__ __forceinline__ bool last_block_total2(double& a, double& b, double* 
 // converged when |d_{m+1}| ||y_{m+1}|| <= rtol ||p_{m+1}|| + atol (Sec. 2.2),
 // with ||x|| = sqrt(sum x^2 / N); nscale undoes an input scaling.
 __device__ __forceinline__ void leja_finalize(const LoopArgs& A, LoopState* st, int m, double dm1, double sy,
-                                              double sp, double nscale, cudaGraphConditionalHandle cond) {
+                                              double sp, double yscale, double pscale,
+                                              cudaGraphConditionalHandle cond) {
   const double inv_n = 1.0 / double(A.n);
-  const double ynorm = sqrt(sy * inv_n) * nscale, pnorm = sqrt(sp * inv_n) * nscale;
+  const double ynorm = sqrt(sy * inv_n) * yscale, pnorm = sqrt(sp * inv_n) * pscale;
   const double e = fabs(dm1) * ynorm;
   const int m1 = m + 1;
   int status = 0;
@@ -321,7 +323,7 @@ __global__ void __launch_bounds__(kThreadsPerBlock)
     }
   }
   if (!last_block_total2(sy, sp, partials, ticket)) return;
-  if (threadIdx.x == 0) leja_finalize(A, st, m, dm1, sy, sp, 1.0, cond);
+  if (threadIdx.x == 0) leja_finalize(A, st, m, dm1, sy, sp, 1.0, 1.0, cond);
 }
 
 // Writes the loop arguments and resets the per-loop state (one thread).
@@ -332,6 +334,8 @@ __global__ void set_loop_args_kernel(LoopArgs args, LoopArgs* dst, LoopState* st
   st->done = 0;
   st->wexp = 0;
   st->kscale = 0;
+  st->sig = 0;
+  st->dlt = 0;
   *ticket = 0u;
 }
 
