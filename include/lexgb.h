@@ -195,6 +195,41 @@ lx_status lx_ctx_set_loop_mode(lx_ctx* ctx, int stream_loop);
  * the fused Leja-iteration kernel into buf (NUL-terminated, at most len). */
 lx_status lx_ctx_kernel_name(lx_ctx* ctx, char* buf, int len);
 
+/* ---------------------------------------------------------------------------
+ * Allocation-free entry point.  The paper has no counterpart: it exists for
+ * callers that cannot allocate device memory at the point of the call --
+ * code that runs while a stream is being captured into a CUDA graph (where
+ * cudaMalloc/cudaFree are not allowed), applications whose own memory pool
+ * owns the device, and time-critical loops that cannot afford the implicit
+ * synchronisation of an allocation.
+ * ------------------------------------------------------------------------- */
+
+#define LX_NOALLOC_MAX_POINTS 262144 /* largest nx * ny (512 x 512) */
+#define LX_NOALLOC_MAX_LEJA 1000     /* Leja points / coefficients used at most */
+
+/* phi_l(hA)w for LX_ADVDIFF with LX_FP64 -- the same fused Leja-iteration
+ * kernel and stopping test as phi_l_apply -- without a context and without
+ * allocating memory.  Its scratch (two basis vectors, reduction partials,
+ * loop state, Leja points and coefficients; about 4.2 MB) is one fixed
+ * __device__ array inside the library, resident on every GPU that loads the
+ * library until the process exits.
+ *   prob         problem (kind LX_ADVDIFF, precision LX_FP64), nx*ny <=
+ *                LX_NOALLOC_MAX_POINTS; otherwise LX_E_INVAL with a message
+ *                in lx_last_cuda_error()
+ *   l, w_dev, out_dev, c, gamma, h, rtol, atol, iters: as in phi_l_apply
+ *                (out_dev must not alias w_dev)
+ *   cuda_stream  stream of the current device for all work (NULL: default);
+ *                the call synchronises it before returning
+ * Every call shares the scratch array and leaves its contents behind; each
+ * call clears what must start at zero.  Calls whose GPU work overlaps (other
+ * streams, other host threads) race on the array: serialise them.  The first
+ * call on a device resolves the array's device address, and the first call
+ * in the process computes the Leja point table on the host; make that first
+ * call before any stream capture starts.  The host side uses about 64 KB of
+ * stack. */
+lx_status phi_l_apply_noalloc(const lx_problem* prob, int l, const double* w_dev, double* out_dev, double c,
+                              double gamma, double h, double rtol, double atol, void* cuda_stream, int* iters);
+
 #ifdef __cplusplus
 }
 #endif

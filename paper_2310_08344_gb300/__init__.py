@@ -33,6 +33,7 @@ from .binding import (  # noqa: F401
     lx_leja_points,
     lx_status_str,
     phi_l_apply,
+    phi_l_apply_noalloc,
     power_bound,
     spectral_interval,
 )

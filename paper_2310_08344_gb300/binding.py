@@ -72,6 +72,8 @@ def lib():
             L.lx_ctx_stats.argtypes = [_vp, C.POINTER(LxStats), C.c_int]
             L.lx_ctx_kernel_name.argtypes = [_vp, C.c_char_p, C.c_int]
             L.lx_ctx_set_loop_mode.argtypes = [_vp, C.c_int]
+            L.phi_l_apply_noalloc.argtypes = [C.POINTER(LxProblem), C.c_int, _vp, _vp, C.c_double, C.c_double,
+                                              C.c_double, C.c_double, C.c_double, _vp, _ip]
             _lib = L
     return _lib
 
@@ -237,3 +239,12 @@ def lx_ctx_kernel_name(ctx: Context) -> str:
 
 def lx_ctx_set_loop_mode(ctx: Context, stream_loop: int) -> int:
     return lib().lx_ctx_set_loop_mode(ctx.handle, int(stream_loop))
+
+
+def phi_l_apply_noalloc(nx, ny, nu, a, l, w, out, c, gamma, h, rtol, atol, stream=None):
+    """Allocation-free phi_l(hA)w (diffusion-advection, FP64).  Returns (status, iters)."""
+    prob = LxProblem(nx, ny, nu, a, ADVDIFF, FP64)
+    it = C.c_int(0)
+    st = lib().phi_l_apply_noalloc(C.byref(prob), l, _dev(w), _dev(out), c, gamma, h, rtol, atol,
+                                   _stream_handle(stream), C.byref(it))
+    return st, it.value

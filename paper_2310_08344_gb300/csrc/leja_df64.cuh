@@ -315,7 +315,7 @@ __global__ void __launch_bounds__(kThreadsPerBlock)
 }
 
 // max over |w| of the binary exponent, to choose the power-of-two scaling.
-__global__ void __launch_bounds__(kThreadsPerBlock) df_scale_kernel(long long n, const double* __restrict__ w,
+static __global__ void __launch_bounds__(kThreadsPerBlock) df_scale_kernel(long long n, const double* __restrict__ w,
                                                                     LoopState* st) {
   int e = 0;
   for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < n; q += (long long)gridDim.x * blockDim.x)
@@ -326,7 +326,7 @@ __global__ void __launch_bounds__(kThreadsPerBlock) df_scale_kernel(long long n,
 }
 
 // kscale from the maximal exponent (one thread).
-__global__ void df_scale_finish_kernel(LoopState* st) {
+static __global__ void df_scale_finish_kernel(LoopState* st) {
   int e = st->wexp;  // biased; 0 for an all-zero (or subnormal) vector
   int k = (e == 0) ? 0 : (e == 2047 ? 0 : e - 1023);
   st->kscale = max(-1000, min(1000, k));
@@ -335,7 +335,7 @@ __global__ void df_scale_finish_kernel(LoopState* st) {
 }
 
 // out = (p.h + p.l) * 2^k
-__global__ void df_output_kernel(long long n, const float2* __restrict__ pdf, double* __restrict__ out,
+static __global__ void df_output_kernel(long long n, const float2* __restrict__ pdf, double* __restrict__ out,
                                  const LoopState* st) {
   const double s = pow2(__ldcg(&st->kscale));
   for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < n; q += (long long)gridDim.x * blockDim.x) {
@@ -345,3 +345,4 @@ __global__ void df_output_kernel(long long n, const float2* __restrict__ pdf, do
 }
 
 }  // namespace lexgb
+

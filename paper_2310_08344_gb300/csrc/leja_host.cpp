@@ -154,13 +154,20 @@ int leja_coeff_count(double h, double c, double gamma, int K) {
   return std::min(K, J + 8);
 }
 
-int leja_coeffs(int l, double h, double c, double gamma, const double* xi, int K, double* d) {
+int leja_coeffs_ws(int l, double h, double c, double gamma, const double* xi, int K, double* d, double* ws) {
   if (l < 0 || K <= 0 || !xi || !d || !(gamma != 0.0) || !std::isfinite(h * c) || !std::isfinite(h * gamma))
     return LX_E_INVAL;
   const int n = l + K;
   // Z: diagonal (0 x l, z_0..z_{K-1}); sub-diagonal 1 on the first l links,
   // h*gamma afterwards.  Shift by mu (mid-range of the diagonal).
-  std::vector<double> diag(n), sub(n, 0.0);
+  // workspace: diag, sub, v, term, nxt, acc (6 n doubles)
+  double* diag = ws;
+  double* sub = ws + n;
+  double* v = ws + 2 * n;
+  double* term = ws + 3 * n;
+  double* nxt = ws + 4 * n;
+  double* acc = ws + 5 * n;
+  for (int i = 0; i < n; ++i) sub[i] = 0.0;
   double zmin = 0.0, zmax = 0.0;
   for (int i = 0; i < l; ++i) diag[i] = 0.0;
   for (int j = 0; j < K; ++j) {
@@ -182,11 +189,10 @@ int leja_coeffs(int l, double h, double c, double gamma, const double* xi, int K
   // e^{mu} is applied a 1/s slice per sub-step, so v stays at the size of
   // exp(t Z) e_0 for every t and never overflows.
   const double emu_step = std::exp(mu * inv_s);
-  std::vector<double> v(n, 0.0), term(n), nxt(n);
+  for (int i = 0; i < n; ++i) v[i] = 0.0;
   v[0] = 1.0;
   for (int step = 0; step < s; ++step) {
-    term = v;
-    std::vector<double> acc = v;
+    for (int i = 0; i < n; ++i) term[i] = acc[i] = v[i];
     for (int k = 1; k < 60; ++k) {
       double tmax = 0.0, amax = 0.0;
       const double f = inv_s / k;
@@ -197,11 +203,11 @@ int leja_coeffs(int l, double h, double c, double gamma, const double* xi, int K
         tmax = std::max(tmax, std::fabs(nxt[i]));
         amax = std::max(amax, std::fabs(acc[i]));
       }
-      term.swap(nxt);
+      std::swap(term, nxt);
       if (tmax <= 1e-18 * amax) break;
     }
     for (int i = 0; i < n; ++i) acc[i] *= emu_step;
-    v.swap(acc);
+    std::swap(v, acc);
   }
   for (int j = 0; j < K; ++j) d[j] = v[l + j];
   // The first coefficient is phi_l(z_0); at z_0 = 0 (xi_0 = 2 on the interval
@@ -214,6 +220,12 @@ int leja_coeffs(int l, double h, double c, double gamma, const double* xi, int K
   for (int j = 0; j < K; ++j)
     if (!std::isfinite(d[j])) return LX_E_NONFINITE;
   return LX_OK;
+}
+
+int leja_coeffs(int l, double h, double c, double gamma, const double* xi, int K, double* d) {
+  if (l < 0 || K <= 0) return LX_E_INVAL;
+  std::vector<double> ws(6 * (size_t)(l + K));
+  return leja_coeffs_ws(l, h, c, gamma, xi, K, d, ws.data());
 }
 
 }  // namespace lexgb

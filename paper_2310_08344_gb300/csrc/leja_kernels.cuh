@@ -294,7 +294,7 @@ __device__ __forceinline__ void leja_finalize(const LoopArgs& A, LoopState* st, 
 }
 
 template <int KIND, typename T, int VEC>
-__global__ void __launch_bounds__(kThreadsPerBlock)
+static __global__ void __launch_bounds__(kThreadsPerBlock)
     leja_iter_kernel(const LoopArgs* __restrict__ Ap, LoopState* __restrict__ st, double* __restrict__ partials,
                      unsigned int* __restrict__ ticket, cudaGraphConditionalHandle cond) {
   const LoopArgs& A = *Ap;
@@ -327,7 +327,7 @@ __global__ void __launch_bounds__(kThreadsPerBlock)
 }
 
 // Writes the loop arguments and resets the per-loop state (one thread).
-__global__ void set_loop_args_kernel(LoopArgs args, LoopArgs* dst, LoopState* st, unsigned int* ticket) {
+static __global__ void set_loop_args_kernel(LoopArgs args, LoopArgs* dst, LoopState* st, unsigned int* ticket) {
   *dst = args;
   st->m = 0;
   st->status = 0;
@@ -340,7 +340,7 @@ __global__ void set_loop_args_kernel(LoopArgs args, LoopArgs* dst, LoopState* st
 }
 
 // Resets the per-call totals (one thread).
-__global__ void reset_call_kernel(LoopState* st, unsigned int* ticket) {
+static __global__ void reset_call_kernel(LoopState* st, unsigned int* ticket) {
   st->iters_total = 0;
   st->status_total = 0;
   st->red = 0.0;
@@ -385,7 +385,7 @@ __global__ void rhs_kernel(Geo g, double nu, double a, double h, const double* _
 }
 
 // out = x + y (in place allowed on y).
-__global__ void add_kernel(long long n, const double* __restrict__ x, double* y) {
+static __global__ void add_kernel(long long n, const double* __restrict__ x, double* y) {
   for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < n; q += (long long)gridDim.x * blockDim.x)
     y[q] = x[q] + y[q];
 }
@@ -410,13 +410,13 @@ __global__ void exprb32_stage_kernel(Geo g, double h, const double* __restrict__
 
 // a = u + p1 after the remainder has been formed (separate pass so that the
 // stencil above reads an unmodified p1).
-__global__ void exprb32_a_kernel(long long n, const double* __restrict__ u, double* __restrict__ p1_a) {
+static __global__ void exprb32_a_kernel(long long n, const double* __restrict__ u, double* __restrict__ p1_a) {
   for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < n; q += (long long)gridDim.x * blockDim.x)
     p1_a[q] = u[q] + p1_a[q];
 }
 
 // u_high = a + 2 p3 and err = ||2 p3|| (last-block reduction into st->red).
-__global__ void __launch_bounds__(kThreadsPerBlock)
+static __global__ void __launch_bounds__(kThreadsPerBlock)
     exprb32_final_kernel(long long n, const double* __restrict__ a, const double* __restrict__ p3,
                          double* __restrict__ u_high, double* __restrict__ partials, unsigned int* __restrict__ ticket,
                          LoopState* st) {
@@ -431,7 +431,7 @@ __global__ void __launch_bounds__(kThreadsPerBlock)
 }
 
 // sigma = 1/||v0|| and reset of the power-iteration state.
-__global__ void __launch_bounds__(kThreadsPerBlock)
+static __global__ void __launch_bounds__(kThreadsPerBlock)
     power_start_kernel(long long n, const double* __restrict__ v, int pmax, double* __restrict__ partials,
                        unsigned int* __restrict__ ticket, LoopState* st) {
   double s = 0.0, dummy = 0.0;
@@ -457,7 +457,7 @@ __global__ void __launch_bounds__(kThreadsPerBlock)
 // One power-iteration pass: w = Op(v) / ||v||, rho_k = ||w||, stop test
 // |rho_k - rho_{k-1}| <= 1e-2 rho_k or k = pmax.
 template <int KIND>
-__global__ void __launch_bounds__(kThreadsPerBlock)
+static __global__ void __launch_bounds__(kThreadsPerBlock)
     power_pass_kernel(Geo g, double nu, double a, const double* __restrict__ u, const double* __restrict__ sgrad,
                       const double* __restrict__ v, double* __restrict__ w, double* __restrict__ partials,
                       unsigned int* __restrict__ ticket, LoopState* st) {

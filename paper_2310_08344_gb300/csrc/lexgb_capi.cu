@@ -23,6 +23,10 @@
 
 using namespace lexgb;
 
+namespace lexgb {
+void set_last_error(const char* msg);
+}
+
 namespace {
 
 thread_local std::string g_last_cuda_error;
@@ -32,6 +36,12 @@ bool cuda_ok(cudaError_t e, const char* what) {
   g_last_cuda_error = std::string(what) + ": " + cudaGetErrorString(e);
   return false;
 }
+
+}  // namespace
+
+void lexgb::set_last_error(const char* msg) { g_last_cuda_error = msg; }
+
+namespace {
 
 #define LX_CUDA(call)                                   \
   do {                                                  \
