@@ -49,10 +49,11 @@ def parse():
     p.add_argument("--steps", type=int, default=10)
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="lexgb", choices=["lexgb", "reference"])
-    p.add_argument("--precision", default="fp64", choices=["fp64", "mixed", "df64"])
+    p.add_argument("--precision", default="df64", choices=["fp64", "mixed", "df64"])
     p.add_argument("--n", type=int, default=NX)
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--no-autotune", action="store_true")
     return p.parse_args()
 
 
@@ -230,6 +231,11 @@ def main():
     prec = {"fp64": lx.FP64, "mixed": lx.MIXED, "df64": lx.DF64}[args.precision]
     stream = torch.cuda.current_stream()
     ctx = lx.leja_setup(n, n, NU, ADV, lx.ADVDIFF, prec, lx.ROS_EU, 1000, stream)
+    tune = None
+    if not args.no_autotune:
+        st, tune = lx.lx_ctx_autotune(ctx, 10, None)
+        if st != 0:
+            raise SystemExit(f"autotune failed: {st}")
     kname = lx.lx_ctx_kernel_name(ctx)
     u0 = synth.gaussians_ic(n, n, seed=1)
     h = CFL_MULT * synth.cfl_step(n, n, NU, ADV)
@@ -336,6 +342,7 @@ def main():
                            "nx": n, "ny": n, "nu": NU, "a": ADV, "h_over_dt_cfl": CFL_MULT, "tol": TOL,
                            "precision": args.precision, "integrator": "ros_eu", "parallelism": f"replicas{world}",
                            "leja_iters_per_step": iters, "rho": rho,
+                           "kernel_selected": (tune or {}).get("selected", {"kernel": kname}),
                            "l2": "inputs larger than L2 (128 MiB per vector, 512 MiB moved per Leja iteration)"},
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "clocks": clk}
         print(json.dumps(line))

@@ -191,6 +191,22 @@ lx_status lx_ctx_stats(lx_ctx* ctx, lx_stats* out, int reset);
  * LEXGB_STREAM_LOOP=1 selects mode 1 at setup. */
 lx_status lx_ctx_set_loop_mode(lx_ctx* ctx, int stream_loop);
 
+/* Autotuner of the fused Leja iteration (a tile-shape search).  Times every
+ * candidate kernel of the context's (kind, precision) -- for LX_DF64 the
+ * shared-memory-pipelined kernel at 2, 3 and 4 resident blocks per SM and
+ * the register-window kernel -- at strip heights 8..128 rows, each for
+ * `iters` launches (1..50) on the context's own buffers, and selects the
+ * fastest for the vector-access ("wide") class.  cache_path (may be NULL) is
+ * a text file of lines "<device|SMs|nx x ny|kind|precision> <kernel> <strip
+ * height> <us>": a matching line is applied without timing, and a new
+ * result is appended.  report (may be NULL) receives a JSON summary.  The
+ * context's auxiliary vectors are overwritten (with zeros). */
+lx_status lx_ctx_autotune(lx_ctx* ctx, int iters, const char* cache_path, char* report, int len);
+
+/* Select a fused-iteration kernel by name (as reported by the autotuner or
+ * lx_ctx_kernel_name) and strip height. */
+lx_status lx_ctx_select_kernel(lx_ctx* ctx, const char* name, int strip_h);
+
 /* Kernel selection of the context (for diagnostics): writes a short name of
  * the fused Leja-iteration kernel into buf (NUL-terminated, at most len). */
 lx_status lx_ctx_kernel_name(lx_ctx* ctx, char* buf, int len);

@@ -25,7 +25,9 @@ from .binding import (  # noqa: F401
     leja_destroy,
     leja_setup,
     lib,
+    lx_ctx_autotune,
     lx_ctx_kernel_name,
+    lx_ctx_select_kernel,
     lx_ctx_set_loop_mode,
     lx_ctx_stats,
     lx_leja_coeff_count,

@@ -72,6 +72,8 @@ def lib():
             L.lx_ctx_stats.argtypes = [_vp, C.POINTER(LxStats), C.c_int]
             L.lx_ctx_kernel_name.argtypes = [_vp, C.c_char_p, C.c_int]
             L.lx_ctx_set_loop_mode.argtypes = [_vp, C.c_int]
+            L.lx_ctx_autotune.argtypes = [_vp, C.c_int, C.c_char_p, C.c_char_p, C.c_int]
+            L.lx_ctx_select_kernel.argtypes = [_vp, C.c_char_p, C.c_int]
             L.phi_l_apply_noalloc.argtypes = [C.POINTER(LxProblem), C.c_int, _vp, _vp, C.c_double, C.c_double,
                                               C.c_double, C.c_double, C.c_double, _vp, _ip]
             _lib = L
@@ -248,3 +250,17 @@ def phi_l_apply_noalloc(nx, ny, nu, a, l, w, out, c, gamma, h, rtol, atol, strea
     st = lib().phi_l_apply_noalloc(C.byref(prob), l, _dev(w), _dev(out), c, gamma, h, rtol, atol,
                                    _stream_handle(stream), C.byref(it))
     return st, it.value
+
+
+def lx_ctx_autotune(ctx: Context, iters=10, cache_path=None):
+    """Returns (status, report dict)."""
+    import json
+
+    buf = C.create_string_buffer(16384)
+    st = lib().lx_ctx_autotune(ctx.handle, iters, cache_path.encode() if cache_path else None, buf, 16384)
+    rep = json.loads(buf.value.decode()) if st == OK and buf.value else {}
+    return st, rep
+
+
+def lx_ctx_select_kernel(ctx: Context, name: str, strip_h: int) -> int:
+    return lib().lx_ctx_select_kernel(ctx.handle, name.encode(), strip_h)

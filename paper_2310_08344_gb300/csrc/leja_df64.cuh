@@ -346,3 +346,199 @@ static __global__ void df_output_kernel(long long n, const float2* __restrict__ 
 
 }  // namespace lexgb
 
+namespace lexgb {
+
+// ---------------------------------------------------------------------------
+// Pipelined df64 iteration (nx % 128 == 0): each warp stages the rows it is
+// about to need -- y with its two x-halo points, and p -- into a private
+// shared-memory ring with asynchronous copies (cp.async), kPipeAhead rows
+// ahead of the row it computes.  The bytes in flight then no longer occupy
+// registers, so a resident warp keeps several rows of loads outstanding.
+// ---------------------------------------------------------------------------
+
+constexpr int kPipeWarps = 4;
+constexpr int kPipeThreads = kPipeWarps * 32;
+constexpr int kPipeStages = 5;            // ring slots per warp
+constexpr int kPipeAhead = kPipeStages - 3;
+constexpr int kPipeRow = 128;             // points per warp row (4 per lane)
+constexpr int kYSlot = kPipeRow + 4;      // [pad][west halo][128 points][east halo][pad]
+constexpr int kPSlot = kPipeRow;
+constexpr int kSlotElems = kYSlot + kPSlot;
+constexpr int kPipeSmemBytes = kPipeWarps * kPipeStages * kSlotElems * 8;
+
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async8(void* smem, const void* gmem) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_wait() {
+  asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+}
+
+template <typename S>
+__device__ __forceinline__ dfv df_from_raw(const unsigned long long* e, double sc) {
+  if constexpr (sizeof(S) == 8 && !std::is_same<S, float2>::value) {
+    return df_from_double(__longlong_as_double((long long)*e) * sc);
+  } else {
+    const float2 t = *reinterpret_cast<const float2*>(e);
+    return {t.x, t.y};
+  }
+}
+
+template <typename S>
+__device__ __forceinline__ void df_from_raw4(const unsigned long long* e, double sc, dfv (&v)[4]) {
+  if constexpr (!std::is_same<S, float2>::value) {
+    const double2 a = *reinterpret_cast<const double2*>(e);
+    const double2 b = *reinterpret_cast<const double2*>(e + 2);
+    v[0] = df_from_double(a.x * sc);
+    v[1] = df_from_double(a.y * sc);
+    v[2] = df_from_double(b.x * sc);
+    v[3] = df_from_double(b.y * sc);
+  } else {
+    const float4 a = *reinterpret_cast<const float4*>(e);
+    const float4 b = *reinterpret_cast<const float4*>(e + 2);
+    v[0] = {a.x, a.y};
+    v[1] = {a.z, a.w};
+    v[2] = {b.x, b.y};
+    v[3] = {b.z, b.w};
+  }
+}
+
+template <typename S, bool FIRST>
+__device__ __forceinline__ void df_strip_pipe(const LoopArgs& A, const S* __restrict__ src, float2* __restrict__ dst,
+                                              float2* __restrict__ p, unsigned long long* ring, int col0, int r0,
+                                              int r1, const float (&wh)[5], const float (&wl)[5], dfv d0, dfv dm1,
+                                              double sc, dfv& accy, dfv& accp) {
+  const int lane = threadIdx.x & 31;
+  const int nx = A.nx, ny = A.ny;
+  const int c = col0 + lane * 4;
+  const int cw = col0 == 0 ? nx - 1 : col0 - 1;
+  const int ce = (col0 + kPipeRow >= nx) ? 0 : col0 + kPipeRow;
+  const int nrows = r1 - r0;           // rows computed
+  const int last_q = nrows + 1;        // y rows q = 0 .. nrows+1 (r0-1 .. r1)
+  auto slot = [&](int q) { return ring + (size_t)(q % kPipeStages) * kSlotElems; };
+  auto issue = [&](int q) {
+    if (q <= last_q) {
+      int ry = r0 - 1 + q;
+      ry = ry < 0 ? ry + ny : (ry >= ny ? ry - ny : ry);
+      unsigned long long* s = slot(q);
+      const S* row = src + (size_t)ry * nx;
+      cp_async16(s + 2 + lane * 4, row + c);
+      cp_async16(s + 4 + lane * 4, row + c + 2);
+      if (lane == 0) cp_async8(s + 1, row + cw);
+      if (lane == 31) cp_async8(s + 2 + kPipeRow, row + ce);
+      if constexpr (!FIRST) {
+        if (q >= 1 && q <= nrows) {
+          const float2* prow = p + (size_t)(r0 - 1 + q) * nx;
+          cp_async16(s + kYSlot + lane * 4, prow + c);
+          cp_async16(s + kYSlot + lane * 4 + 2, prow + c + 2);
+        }
+      }
+    }
+    cp_commit();
+  };
+  for (int q = 0; q < kPipeStages - 1; ++q) issue(q);
+  cp_wait<kPipeStages - 3>();
+  __syncwarp();
+  dfv ys[4], yc[4], yn[4];
+  df_from_raw4<S>(slot(0) + 2 + lane * 4, sc, ys);
+  df_from_raw4<S>(slot(1) + 2 + lane * 4, sc, yc);
+  for (int qc = 1; qc <= nrows; ++qc) {
+    issue(qc + kPipeStages - 2);
+    cp_wait<kPipeStages - 3>();
+    __syncwarp();
+    const unsigned long long* sn = slot(qc + 1);
+    const unsigned long long* scn = slot(qc);
+    df_from_raw4<S>(sn + 2 + lane * 4, sc, yn);
+    dfv pold[4];
+    if constexpr (!FIRST) df_from_raw4<float2>(scn + kYSlot + lane * 4, sc, pold);
+    dfv xw = shfl_up_df(yc[3]);
+    dfv xe = shfl_down_df(yc[0]);
+    if (lane == 0) xw = df_from_raw<S>(scn + 1, sc);
+    if (lane == 31) xe = df_from_raw<S>(scn + 2 + kPipeRow, sc);
+    dfv ynew[4], pnew[4];
+    float fy = 0.f, fp = 0.f;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      const dfv t[5] = {k == 3 ? xe : yc[k + 1], k == 0 ? xw : yc[k - 1], yn[k], ys[k], yc[k]};
+      ynew[k] = df_dot5(wh, wl, t);
+      const dfv po = FIRST ? df_mul(d0, yc[k]) : pold[k];
+      pnew[k] = df_axpy(dm1, ynew[k], po);
+      fy = __fmaf_rn(ynew[k].h, ynew[k].h, fy);
+      fp = __fmaf_rn(pnew[k].h, pnew[k].h, fp);
+    }
+    df_acc(accy, fy);
+    df_acc(accp, fp);
+    const size_t ro = (size_t)(r0 - 1 + qc) * nx;
+    df_store_row<4>(dst + ro, c, nx, ynew);
+    df_store_row<4>(p + ro, c, nx, pnew);
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      ys[k] = yc[k];
+      yc[k] = yn[k];
+    }
+    __syncwarp();
+  }
+  cp_wait<0>();
+  __syncwarp();
+}
+
+template <int MINB>
+__global__ void __launch_bounds__(kPipeThreads, MINB)
+    leja_iter_df_pipe_kernel(const LoopArgs* __restrict__ Ap, LoopState* __restrict__ st,
+                             double* __restrict__ partials, unsigned int* __restrict__ ticket,
+                             cudaGraphConditionalHandle cond) {
+  extern __shared__ __align__(16) unsigned long long pipe_smem[];
+  const LoopArgs& A = *Ap;
+  const int m = __ldcg(&st->m);
+  if (__ldcg(&st->done)) return;
+  const int kexp = __ldcg(&st->kscale);
+  const int sig = __ldcg(&st->sig);
+  const int dlt = __ldcg(&st->dlt);
+  const double sc = pow2(-kexp);
+  const int nx = A.nx, ny = A.ny;
+  const int H = A.strip_h;
+  const int ncs = nx / kPipeRow;
+  const int nstrips = ncs * ((ny + H - 1) / H);
+  const double xim = __ldg(A.xi + m);
+  const double dm1d = __ldg(A.d + m + 1);
+  const dfv dm1 = df_from_double(dm1d * pow2(sig + dlt - kexp));
+  const dfv d0 = df_from_double(__ldg(A.d));
+  const double sw = pow2(-dlt);
+  const float swf = (float)sw;
+  const dfv wc = df_from_double((A.wc0 - xim) * sw);
+  const float wh[5] = {A.wf[0] * swf, A.wf[2] * swf, A.wf[4] * swf, A.wf[6] * swf, wc.h};
+  const float wl[5] = {A.wf[1] * swf, A.wf[3] * swf, A.wf[5] * swf, A.wf[7] * swf, wc.l};
+  float2* dst = reinterpret_cast<float2*>((m & 1) ? A.y1 : A.y0);
+  dfv accy = {0.f, 0.f}, accp = {0.f, 0.f};
+  const int warp = threadIdx.x >> 5;
+  unsigned long long* ring = pipe_smem + (size_t)warp * kPipeStages * kSlotElems;
+  for (int s = blockIdx.x * kPipeWarps + warp; s < nstrips; s += gridDim.x * kPipeWarps) {
+    const int col0 = (s % ncs) * kPipeRow;
+    const int r0 = (s / ncs) * H;
+    const int r1 = min(r0 + H, ny);
+    if (m == 0) {
+      df_strip_pipe<double, true>(A, A.w, dst, A.pdf, ring, col0, r0, r1, wh, wl, d0, dm1, sc, accy, accp);
+    } else {
+      const float2* src = reinterpret_cast<const float2*>(((m - 1) & 1) ? A.y1 : A.y0);
+      df_strip_pipe<float2, false>(A, src, dst, A.pdf, ring, col0, r0, r1, wh, wl, d0, dm1, sc, accy, accp);
+    }
+  }
+  double sy = df_to_double(accy), sp = df_to_double(accp);
+  if (!last_block_total2(sy, sp, partials, ticket)) return;
+  if (threadIdx.x == 0) {
+    leja_finalize(A, st, m, dm1d, sy, sp, pow2(sig + dlt), pow2(kexp), cond);
+    const double rms = sqrt(sy / double(A.n));
+    int e = 0;
+    if (rms > 0.0 && isfinite(rms)) e = ilogb(rms);
+    st->sig = sig + dlt;
+    st->dlt = max(-100, min(100, e));
+  }
+}
+
+}  // namespace lexgb

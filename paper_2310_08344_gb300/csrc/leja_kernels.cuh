@@ -22,6 +22,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <type_traits>
+
 namespace lexgb {
 
 constexpr int kWarpsPerBlock = 8;
@@ -207,7 +209,7 @@ __device__ __forceinline__ void leja_strip(const LoopArgs& A, const S* __restric
 
 // Sum (a, b) over the block; returns the totals in thread 0.
 __device__ __forceinline__ void block_sum2(double& a, double& b) {
-  __shared__ double sa[kWarpsPerBlock], sb[kWarpsPerBlock];
+  __shared__ double sa[32], sb[32];
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {
     a += __shfl_xor_sync(0xffffffffu, a, o);
@@ -221,7 +223,8 @@ __device__ __forceinline__ void block_sum2(double& a, double& b) {
   __syncthreads();
   if (threadIdx.x == 0) {
     double x = 0.0, y = 0.0;
-    for (int w = 0; w < kWarpsPerBlock; ++w) {
+    const int nw = (int)(blockDim.x >> 5);
+    for (int w = 0; w < nw; ++w) {
       x += sa[w];
       y += sb[w];
     }

@@ -14,6 +14,8 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <fstream>
+#include <sstream>
 #include <string>
 #include <vector>
 
@@ -58,16 +60,26 @@ struct CoefSlot {
   double* host = nullptr;  // pinned staging
 };
 
-// Kernel variants of the fused Leja iteration.
+// Kernel classes of the fused Leja iteration: "wide" (vector accesses; needs
+// nx a multiple of the warp row and 16-byte aligned vectors) and "generic".
 enum Variant { kVec2 = 0, kVec1 = 1, kNumVariants = 2 };
+
+// One candidate implementation of the fused iteration.
+struct Cand {
+  const void* func;
+  int threads;  // block size
+  int smem;     // dynamic shared memory bytes
+  int vec;      // points per lane (warp row = 32 * vec points)
+  const char* name;
+};
 
 struct LoopGraph {
   bool built = false;
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
   int grid = 0;
-  const void* func = nullptr;
-  const char* name = "";
+  Cand cand{};
+  int strip_h = 32;
 };
 
 }  // namespace
@@ -92,6 +104,7 @@ struct lx_ctx {
   double* d_pw[2] = {nullptr, nullptr};  // power iteration ping-pong
   double* d_io[3] = {nullptr, nullptr, nullptr};  // staging for expint_step_host
   float2* d_pdf = nullptr;  // df64 form: polynomial as float pairs
+  double* d_tune = nullptr; // autotuner: output vector of the timing runs
   double* d_partials = nullptr;
   int partials_cap = 0;
   int stream_loop = 0;  // 1: launch the iterations from the host (profilers)
@@ -115,56 +128,85 @@ size_t basis_bytes(const lx_ctx* c) {
   return (size_t)c->n * (c->prob.precision == LX_MIXED ? sizeof(float) : sizeof(double));
 }
 
-// Points per thread of the wide variant.
-int wide_vec(const lx_ctx* c) { return c->prob.precision == LX_DF64 ? 4 : 2; }
 
 template <int KIND, typename T, int VEC>
-const void* iter_kernel_ptr() {
-  return reinterpret_cast<const void*>(&leja_iter_kernel<KIND, T, VEC>);
+Cand iter_cand(const char* name) {
+  return Cand{reinterpret_cast<const void*>(&leja_iter_kernel<KIND, T, VEC>), kThreadsPerBlock, 0, VEC, name};
 }
 
-const void* pick_kernel(int kind, int precision, int variant, const char** name) {
-  const bool mixed = precision == LX_MIXED;
-  const bool v2 = variant == kVec2;
+// Candidates for (kind, precision, class); the first is the default.
+std::vector<Cand> candidates(int kind, int precision, int cls) {
+  const bool wide = cls == kVec2;
+  std::vector<Cand> v;
   if (precision == LX_DF64) {
-    *name = v2 ? "leja_iter_df_advdiff_v4" : "leja_iter_df_advdiff_v1";
-    return v2 ? reinterpret_cast<const void*>(&leja_iter_df_advdiff_kernel<4>)
-              : reinterpret_cast<const void*>(&leja_iter_df_advdiff_kernel<1>);
-  }
-  if (kind == LX_ADVDIFF) {
-    if (!mixed) {
-      *name = v2 ? "leja_iter_advdiff_f64_v2" : "leja_iter_advdiff_f64_v1";
-      return v2 ? iter_kernel_ptr<0, double, 2>() : iter_kernel_ptr<0, double, 1>();
+    if (wide) {
+      v.push_back(Cand{reinterpret_cast<const void*>(&leja_iter_df_pipe_kernel<2>), kPipeThreads, kPipeSmemBytes, 4,
+                       "leja_iter_df_pipe_b2"});
+      v.push_back(Cand{reinterpret_cast<const void*>(&leja_iter_df_pipe_kernel<3>), kPipeThreads, kPipeSmemBytes, 4,
+                       "leja_iter_df_pipe_b3"});
+      v.push_back(Cand{reinterpret_cast<const void*>(&leja_iter_df_pipe_kernel<4>), kPipeThreads, kPipeSmemBytes, 4,
+                       "leja_iter_df_pipe_b4"});
+      v.push_back(Cand{reinterpret_cast<const void*>(&leja_iter_df_advdiff_kernel<4>), kThreadsPerBlock, 0, 4,
+                       "leja_iter_df_advdiff_v4"});
+    } else {
+      v.push_back(Cand{reinterpret_cast<const void*>(&leja_iter_df_advdiff_kernel<1>), kThreadsPerBlock, 0, 1,
+                       "leja_iter_df_advdiff_v1"});
     }
-    *name = v2 ? "leja_iter_advdiff_mixed_v2" : "leja_iter_advdiff_mixed_v1";
-    return v2 ? iter_kernel_ptr<0, float, 2>() : iter_kernel_ptr<0, float, 1>();
+    return v;
   }
-  if (!mixed) {
-    *name = v2 ? "leja_iter_burgers_f64_v2" : "leja_iter_burgers_f64_v1";
-    return v2 ? iter_kernel_ptr<1, double, 2>() : iter_kernel_ptr<1, double, 1>();
+  const bool mixed = precision == LX_MIXED;
+  if (kind == LX_ADVDIFF) {
+    if (!mixed)
+      v.push_back(wide ? iter_cand<0, double, 2>("leja_iter_advdiff_f64_v2")
+                       : iter_cand<0, double, 1>("leja_iter_advdiff_f64_v1"));
+    else
+      v.push_back(wide ? iter_cand<0, float, 2>("leja_iter_advdiff_mixed_v2")
+                       : iter_cand<0, float, 1>("leja_iter_advdiff_mixed_v1"));
+  } else {
+    if (!mixed)
+      v.push_back(wide ? iter_cand<1, double, 2>("leja_iter_burgers_f64_v2")
+                       : iter_cand<1, double, 1>("leja_iter_burgers_f64_v1"));
+    else
+      v.push_back(wide ? iter_cand<1, float, 2>("leja_iter_burgers_mixed_v2")
+                       : iter_cand<1, float, 1>("leja_iter_burgers_mixed_v1"));
   }
-  *name = v2 ? "leja_iter_burgers_mixed_v2" : "leja_iter_burgers_mixed_v1";
-  return v2 ? iter_kernel_ptr<1, float, 2>() : iter_kernel_ptr<1, float, 1>();
+  return v;
 }
 
-int strips_for(const lx_ctx* c, int variant) {
-  const int vec = variant == kVec2 ? wide_vec(c) : 1;
-  const int ncs = (c->prob.nx + 32 * vec - 1) / (32 * vec);
-  const int nrs = (c->prob.ny + c->strip_h - 1) / c->strip_h;
-  return ncs * nrs;
-}
+int wide_vec(const lx_ctx* c) { return candidates(c->prob.kind, c->prob.precision, kVec2)[0].vec; }
 
-lx_status build_loop_graph(lx_ctx* c, int variant) {
-  LoopGraph& L = c->loop[variant];
-  if (L.built) return LX_OK;
-  L.func = pick_kernel(c->prob.kind, c->prob.precision, variant, &L.name);
+int grid_for(const lx_ctx* c, const Cand& k, int strip_h, int* grid) {
+  const int ncs = (c->prob.nx + 32 * k.vec - 1) / (32 * k.vec);
+  const int nrs = (c->prob.ny + strip_h - 1) / strip_h;
+  const int wpb = k.threads / 32;
   int per_sm = 0;
-  LX_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, L.func, kThreadsPerBlock, 0));
+  if (!cuda_ok(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k.func, k.threads, k.smem), "occupancy"))
+    return LX_E_CUDA;
   per_sm = std::max(per_sm, 1);
-  const int want = (strips_for(c, variant) + kWarpsPerBlock - 1) / kWarpsPerBlock;
-  L.grid = std::max(1, std::min(want, per_sm * c->sm_count));
-  if (L.grid > c->partials_cap) return LX_E_INVAL;
+  const int want = (ncs * nrs + wpb - 1) / wpb;
+  *grid = std::max(1, std::min(want, per_sm * c->sm_count));
+  return *grid > c->partials_cap ? LX_E_INVAL : LX_OK;
+}
 
+void destroy_graph(LoopGraph& L) {
+  if (L.exec) cudaGraphExecDestroy(L.exec);
+  if (L.graph) cudaGraphDestroy(L.graph);
+  L.exec = nullptr;
+  L.graph = nullptr;
+  L.built = false;
+}
+
+// (Re)build the while-loop graph of class `variant` around candidate k.
+lx_status build_loop_graph(lx_ctx* c, int variant, const Cand& k, int strip_h) {
+  LoopGraph& L = c->loop[variant];
+  if (L.built && L.cand.func == k.func && L.strip_h == strip_h) return LX_OK;
+  destroy_graph(L);
+  int grid = 0;
+  int gs = grid_for(c, k, strip_h, &grid);
+  if (gs != LX_OK) return (lx_status)gs;
+  L.cand = k;
+  L.strip_h = strip_h;
+  L.grid = grid;
   LX_CUDA(cudaGraphCreate(&L.graph, 0));
   cudaGraphConditionalHandle cond;
   LX_CUDA(cudaGraphConditionalHandleCreate(&cond, L.graph, 1, cudaGraphCondAssignDefault));
@@ -188,10 +230,10 @@ lx_status build_loop_graph(lx_ctx* c, int variant) {
   void* kargs[] = {(void*)&args, (void*)&st, (void*)&partials, (void*)&ticket, (void*)&cond};
   cudaKernelNodeParams kp;
   std::memset(&kp, 0, sizeof(kp));
-  kp.func = const_cast<void*>(L.func);
+  kp.func = const_cast<void*>(k.func);
   kp.gridDim = dim3(L.grid);
-  kp.blockDim = dim3(kThreadsPerBlock);
-  kp.sharedMemBytes = 0;
+  kp.blockDim = dim3(k.threads);
+  kp.sharedMemBytes = k.smem;
   kp.kernelParams = kargs;
   cudaGraphNode_t knode;
   LX_CUDA(cudaGraphAddKernelNode(&knode, body, nullptr, 0, &kp));
@@ -208,11 +250,19 @@ int aux_blocks(const lx_ctx* c) {
 bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
 
 int choose_variant(const lx_ctx* c, const double* w, const double* out) {
+  const int rowpts = 32 * wide_vec(c);
+  if (c->prob.nx % rowpts != 0) return kVec1;
   if (c->prob.precision == LX_DF64)  // out is written by the conversion pass
-    return (c->prob.nx % 128 == 0 && aligned16(w)) ? kVec2 : kVec1;
-  if (c->prob.nx % 64 == 0 && aligned16(w) && aligned16(out) && aligned16(c->d_y[0]) && aligned16(c->d_y[1]))
-    return kVec2;
+    return aligned16(w) ? kVec2 : kVec1;
+  if (aligned16(w) && aligned16(out) && aligned16(c->d_y[0]) && aligned16(c->d_y[1])) return kVec2;
   return kVec1;
+}
+
+// Selected candidate of a class (built on first use with the default).
+lx_status ensure_graph(lx_ctx* c, int variant) {
+  if (c->loop[variant].built) return LX_OK;
+  const Cand k = candidates(c->prob.kind, c->prob.precision, variant)[0];
+  return build_loop_graph(c, variant, k, c->strip_h);
 }
 
 lx_status ensure_coeffs(lx_ctx* c, int slot, int l, double h, double cc, double gamma) {
@@ -238,7 +288,7 @@ lx_status launch_loop(lx_ctx* c, int slot, int l, const double* u, const double*
   lx_status st = ensure_coeffs(c, slot, l, h, cc, gamma);
   if (st != LX_OK) return st;
   const int variant = choose_variant(c, w, out);
-  st = build_loop_graph(c, variant);
+  st = ensure_graph(c, variant);
   if (st != LX_OK) return st;
   const lx_problem& P = c->prob;
   const double dx = 1.0 / P.nx, dy = 1.0 / P.ny;
@@ -248,7 +298,7 @@ lx_status launch_loop(lx_ctx* c, int slot, int l, const double* u, const double*
   a.nx = P.nx;
   a.ny = P.ny;
   a.n = c->n;
-  a.strip_h = c->strip_h;
+  a.strip_h = c->loop[variant].strip_h;
   a.kmax = c->coef[slot].count - 1;
   a.w = w;
   a.y0 = c->d_y[0];
@@ -308,7 +358,7 @@ lx_status launch_loop(lx_ctx* c, int slot, int l, const double* u, const double*
     void* kargs[] = {(void*)&args, (void*)&stp, (void*)&partials, (void*)&ticket, (void*)&cond};
     for (int it = 0; it < a.kmax; it += 8) {
       for (int k = 0; k < 8; ++k)
-        LX_CUDA(cudaLaunchKernel(L.func, dim3(L.grid), dim3(kThreadsPerBlock), kargs, 0, c->stream));
+        LX_CUDA(cudaLaunchKernel(L.cand.func, dim3(L.grid), dim3(L.cand.threads), kargs, L.cand.smem, c->stream));
       LX_CUDA(cudaMemcpyAsync(c->h_state, c->d_state, sizeof(LoopState), cudaMemcpyDeviceToHost, c->stream));
       LX_CUDA(cudaStreamSynchronize(c->stream));
       if (c->h_state->done) break;
@@ -377,10 +427,7 @@ const char* lx_last_cuda_error(void) { return g_last_cuda_error.c_str(); }
 
 void leja_destroy(lx_ctx* c) {
   if (!c) return;
-  for (auto& L : c->loop) {
-    if (L.exec) cudaGraphExecDestroy(L.exec);
-    if (L.graph) cudaGraphDestroy(L.graph);
-  }
+  for (auto& L : c->loop) destroy_graph(L);
   for (auto& S : c->coef) {
     if (S.dev) cudaFree(S.dev);
     if (S.host) cudaFreeHost(S.host);
@@ -395,6 +442,7 @@ void leja_destroy(lx_ctx* c) {
   cudaFree(c->d_pw[1]);
   for (auto* p : c->d_io) cudaFree(p);
   cudaFree(c->d_pdf);
+  cudaFree(c->d_tune);
   cudaFree(c->d_partials);
   cudaFree(c->d_ticket);
   cudaFree(c->d_state);
@@ -467,7 +515,7 @@ lx_status leja_setup(const lx_problem* prob, int integrator, int max_leja, void*
   c->aux_grid = 4 * c->sm_count;
   for (int v = 0; v < kNumVariants; ++v) {
     if (v == kVec2 && prob->nx % (32 * wide_vec(c)) != 0) continue;
-    lx_status s = build_loop_graph(c, v);
+    lx_status s = ensure_graph(c, v);
     if (s != LX_OK) return fail(s);
   }
   if (!cuda_ok(cudaStreamSynchronize(c->stream), "setup sync")) return fail(LX_E_CUDA);
@@ -626,7 +674,162 @@ lx_status lx_ctx_set_loop_mode(lx_ctx* c, int stream_loop) {
 lx_status lx_ctx_kernel_name(lx_ctx* c, char* buf, int len) {
   if (!c || !buf || len <= 0) return LX_E_INVAL;
   const int v = c->loop[kVec2].built ? kVec2 : kVec1;
-  std::snprintf(buf, (size_t)len, "%s", c->loop[v].name);
+  std::snprintf(buf, (size_t)len, "%s", c->loop[v].cand.name);
+  return LX_OK;
+}
+
+}  // extern "C"
+
+namespace {
+
+std::string tune_key(const lx_ctx* c) {
+  cudaDeviceProp prop;
+  std::string dev = "unknown";
+  if (cudaGetDeviceProperties(&prop, c->device) == cudaSuccess) dev = prop.name;
+  for (auto& ch : dev)
+    if (ch == ' ' || ch == '\t' || ch == '|') ch = '_';
+  std::ostringstream k;
+  k << dev << "|sm" << c->sm_count << "|" << c->prob.nx << "x" << c->prob.ny << "|kind" << c->prob.kind << "|prec"
+    << c->prob.precision;
+  return k.str();
+}
+
+// Average time of one fused iteration of candidate k with strip height H on
+// the context's own buffers (zero data; stopping disabled).
+lx_status tune_time(lx_ctx* c, const Cand& k, int H, int iters, double* us) {
+  int grid = 0;
+  int gs = grid_for(c, k, H, &grid);
+  if (gs != LX_OK) return (lx_status)gs;
+  const lx_problem& P = c->prob;
+  LoopArgs a;
+  std::memset(&a, 0, sizeof(a));
+  a.nx = P.nx;
+  a.ny = P.ny;
+  a.n = c->n;
+  a.strip_h = H;
+  a.kmax = c->coef[0].count - 1;
+  a.w = c->d_f;
+  a.y0 = c->d_y[0];
+  a.y1 = c->d_y[1];
+  a.p = c->d_tune;
+  a.u = c->d_f;
+  a.s = c->d_s;
+  a.xi = c->d_xi;
+  a.d = c->coef[0].dev;
+  a.wxp = a.wxm = a.wyp = a.wym = 0.25;
+  a.lx = a.ly = a.gx = a.gy = a.inv_gamma = 0.25;
+  a.wc0 = 1.0;
+  for (int q = 0; q < 8; ++q) a.wf[q] = (q & 1) ? 0.f : 0.25f;
+  a.pdf = c->d_pdf;
+  a.rtol = 0.0;
+  a.atol = -1.0;  // never converged: every launch does the full work
+  a.use_cond = 0;
+  set_loop_args_kernel<<<1, 1, 0, c->stream>>>(a, c->d_args, c->d_state, c->d_ticket);
+  LX_CUDA(cudaGetLastError());
+  const LoopArgs* args = c->d_args;
+  LoopState* stp = c->d_state;
+  double* partials = c->d_partials;
+  unsigned int* ticket = c->d_ticket;
+  cudaGraphConditionalHandle cond = 0;
+  void* kargs[] = {(void*)&args, (void*)&stp, (void*)&partials, (void*)&ticket, (void*)&cond};
+  LX_CUDA(cudaLaunchKernel(k.func, dim3(grid), dim3(k.threads), kargs, k.smem, c->stream));  // m = 0 path
+  LX_CUDA(cudaEventRecord(c->ev[0], c->stream));
+  for (int i = 0; i < iters; ++i)
+    LX_CUDA(cudaLaunchKernel(k.func, dim3(grid), dim3(k.threads), kargs, k.smem, c->stream));
+  LX_CUDA(cudaEventRecord(c->ev[1], c->stream));
+  LX_CUDA(cudaStreamSynchronize(c->stream));
+  float ms = 0.f;
+  LX_CUDA(cudaEventElapsedTime(&ms, c->ev[0], c->ev[1]));
+  *us = 1e3 * ms / iters;
+  return LX_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+lx_status lx_ctx_select_kernel(lx_ctx* c, const char* name, int strip_h) {
+  if (!c || !name || strip_h < 1) return LX_E_INVAL;
+  for (int v = 0; v < kNumVariants; ++v)
+    for (const Cand& k : candidates(c->prob.kind, c->prob.precision, v))
+      if (std::strcmp(k.name, name) == 0) {
+        if (v == kVec2 && c->prob.nx % (32 * k.vec) != 0) return LX_E_INVAL;
+        return build_loop_graph(c, v, k, strip_h);
+      }
+  return LX_E_INVAL;
+}
+
+lx_status lx_ctx_autotune(lx_ctx* c, int iters, const char* cache_path, char* report, int len) {
+  if (!c || iters < 1 || iters > 50) return LX_E_INVAL;
+  const int v = (c->prob.nx % (32 * wide_vec(c)) == 0) ? kVec2 : kVec1;
+  const std::string key = tune_key(c);
+  std::ostringstream rep;
+  rep << "{\"key\": \"" << key << "\", ";
+  if (cache_path && cache_path[0]) {
+    std::ifstream in(cache_path);
+    std::string line, found_name;
+    int found_h = 0;
+    while (std::getline(in, line)) {
+      std::istringstream ls(line);
+      std::string k, nm;
+      int hh = 0;
+      if (ls >> k >> nm >> hh && k == key) {
+        found_name = nm;
+        found_h = hh;
+      }
+    }
+    if (!found_name.empty() && lx_ctx_select_kernel(c, found_name.c_str(), found_h) == LX_OK) {
+      rep << "\"cached\": true, \"selected\": {\"kernel\": \"" << found_name << "\", \"strip_h\": " << found_h
+          << "}}";
+      if (report && len > 0) std::snprintf(report, (size_t)len, "%s", rep.str().c_str());
+      return LX_OK;
+    }
+  }
+  const size_t nb = sizeof(double) * (size_t)c->n;
+  if (!c->d_tune && !cuda_ok(cudaMalloc((void**)&c->d_tune, nb), "cudaMalloc")) return LX_E_NOMEM;
+  LX_CUDA(cudaMemsetAsync(c->d_y[0], 0, basis_bytes(c), c->stream));
+  LX_CUDA(cudaMemsetAsync(c->d_y[1], 0, basis_bytes(c), c->stream));
+  LX_CUDA(cudaMemsetAsync(c->d_f, 0, nb, c->stream));
+  LX_CUDA(cudaMemsetAsync(c->d_s, 0, nb, c->stream));
+  LX_CUDA(cudaMemsetAsync(c->d_tune, 0, nb, c->stream));
+  if (c->d_pdf) LX_CUDA(cudaMemsetAsync(c->d_pdf, 0, sizeof(float2) * (size_t)c->n, c->stream));
+  lx_status st = ensure_coeffs(c, 0, 0, 1.0, -20.0, 10.0);
+  if (st != LX_OK) return st;
+  if (c->coef[0].count < iters + 4) return LX_E_INVAL;
+  const int hs[] = {8, 16, 32, 64, 128};
+  double best = 1e30;
+  Cand best_k{};
+  int best_h = 32;
+  rep << "\"cached\": false, \"timings\": [";
+  bool first = true;
+  for (const Cand& k : candidates(c->prob.kind, c->prob.precision, v)) {
+    for (int H : hs) {
+      if (H > 2 * c->prob.ny && H != 8) continue;
+      double us = 0.0;
+      st = tune_time(c, k, H, iters, &us);
+      if (st == LX_E_INVAL) continue;  // grid beyond the partials capacity
+      if (st != LX_OK) return st;
+      rep << (first ? "" : ", ") << "{\"kernel\": \"" << k.name << "\", \"strip_h\": " << H << ", \"us\": " << us
+          << "}";
+      first = false;
+      if (us < best) {
+        best = us;
+        best_k = k;
+        best_h = H;
+      }
+    }
+  }
+  if (!best_k.func) return LX_E_CUDA;
+  st = build_loop_graph(c, v, best_k, best_h);
+  if (st != LX_OK) return st;
+  c->coef[0].valid = false;
+  rep << "], \"selected\": {\"kernel\": \"" << best_k.name << "\", \"strip_h\": " << best_h << ", \"us\": " << best
+      << "}}";
+  if (cache_path && cache_path[0]) {
+    std::ofstream out(cache_path, std::ios::app);
+    if (out) out << key << "\t" << best_k.name << "\t" << best_h << "\t" << best << "\n";
+  }
+  if (report && len > 0) std::snprintf(report, (size_t)len, "%s", rep.str().c_str());
   return LX_OK;
 }
 

@@ -293,3 +293,46 @@ def test_stream_loop_mode_matches_graph(lx):
         outs.append((it, out.cpu().numpy()))
     assert outs[0][0] == outs[1][0]
     assert np.array_equal(outs[0][1], outs[1][1])  # same kernels, same order: bitwise
+
+
+DF64_KERNELS = ["leja_iter_df_pipe_b2", "leja_iter_df_pipe_b3", "leja_iter_df_pipe_b4", "leja_iter_df_advdiff_v4"]
+
+
+@pytest.mark.parametrize("name", DF64_KERNELS)
+@pytest.mark.parametrize("strip_h", [8, 32, 128])
+def test_df64_candidates_parity(lx, xi_oracle, name, strip_h):
+    # every autotuner candidate, on a grid with several column strips and a
+    # ragged last row strip
+    nx, ny, nu, a = 256, 100, 1e-2, 0.5
+    u0 = synth.gaussians_ic(nx, ny, seed=5) + 0.05 * synth.random_field(nx * ny, 15)
+    h = 40 * synth.cfl_step(nx, ny, nu, a)
+    import fourier
+
+    c, g = oracle.spectral_interval(fourier.spectral_radius(nx, ny, nu, a))
+    ctx = lx.leja_setup(nx, ny, nu, a, lx.ADVDIFF, lx.DF64)
+    assert lx.lx_ctx_select_kernel(ctx, name, strip_h) == 0
+    assert lx.lx_ctx_kernel_name(ctx) == name
+    out = torch.empty(nx * ny, dtype=torch.float64, device="cuda")
+    st, it = lx.phi_l_apply(ctx, 1, None, dev(u0), out, c, g, h, TOL, TOL)
+    ref, it_o, st_o = oracle.leja_phi(oracle.ADVDIFF, nx, ny, nu, a, None, 1, u0, c, g, h, TOL, TOL, xi_oracle)
+    assert st == 0 and st_o == 0 and abs(it - it_o) <= 1
+    assert rel(out.cpu().numpy(), ref) <= TOL
+
+
+def test_autotune_selects_and_caches(lx, xi_oracle, tmp_path):
+    n, nu, a = 512, 1e-2, 0.5
+    ctx = lx.leja_setup(n, n, nu, a, lx.ADVDIFF, lx.DF64)
+    cache = str(tmp_path / "tune.txt")
+    st, rep = lx.lx_ctx_autotune(ctx, 5, cache)
+    assert st == 0 and not rep["cached"] and len(rep["timings"]) >= 4
+    sel = rep["selected"]["kernel"]
+    assert lx.lx_ctx_kernel_name(ctx) == sel
+    ctx2 = lx.leja_setup(n, n, nu, a, lx.ADVDIFF, lx.DF64)
+    st, rep2 = lx.lx_ctx_autotune(ctx2, 5, cache)
+    assert st == 0 and rep2["cached"] and rep2["selected"]["kernel"] == sel
+    # the tuned context still computes the right thing
+    u0, h, c, g = advdiff_case(n, n, nu, a, 2)
+    out = torch.empty(n * n, dtype=torch.float64, device="cuda")
+    st, it = lx.phi_l_apply(ctx, 0, None, dev(u0), out, c, g, h, TOL, TOL)
+    ref, it_o, st_o = oracle.leja_phi(oracle.ADVDIFF, n, n, nu, a, None, 0, u0, c, g, h, TOL, TOL, xi_oracle)
+    assert st == 0 and abs(it - it_o) <= 1 and rel(out.cpu().numpy(), ref) <= TOL
