@@ -172,6 +172,35 @@ lx_status expint_step(lx_ctx* ctx, const double* u_dev, double* u_low_dev, doubl
 lx_status expint_step_host(lx_ctx* ctx, const double* u_host, double* u_low_host, double* u_high_host, double c,
                            double gamma, double h, double rtol, double atol, double* err, int* iters);
 
+/* Classical step-size controller for the embedded third-order pair (the
+ * paper notes that the EXPRB32 error "may be used to control the step
+ * sizes", Sec. 2.2, without giving a controller):
+ *   h_new = h * min(2, max(0.2, 0.9 (tol/err)^(1/3)))   (factor 2 if err = 0).
+ * Host arithmetic only. */
+double lx_controller_classical(double h, double err, double tol);
+
+typedef struct {
+  double t;             /* in: start time; out: time reached */
+  double h;             /* in: first trial step (> 0); out: next proposed step */
+  int steps;            /* out: accepted steps */
+  int rejected;         /* out: rejected attempts */
+  long long leja_iters; /* out: Leja iterations of all attempts */
+  double last_err;      /* out: error estimate of the last attempt */
+  int power_iters;      /* in: power-iteration passes per attempt (0: 10) */
+} lx_integrate_info;
+
+/* Adaptive EXPRB32 integration of the context's problem from info->t to
+ * t_final (Listing 7's time loop with step control): every attempt takes a
+ * power-iteration bound at the current state from v0_dev (c, gamma from
+ * lambda = -1.05 rho), one expint_step with Leja tolerance leja_tol (rtol =
+ * atol), accepts the step when err <= tol and sets the next step size with
+ * lx_controller_classical.  u_dev (N doubles) holds the state and is updated
+ * in place.  Requires a context set up with LX_EXPRB32.  At most
+ * max_attempts attempts; info->t < t_final on return means the budget ran
+ * out.  The context's staging vectors are allocated on the first call. */
+lx_status lx_integrate(lx_ctx* ctx, double* u_dev, const double* v0_dev, double t_final, double tol,
+                       double leja_tol, int max_attempts, lx_integrate_info* info);
+
 /* Timing of the Leja loops run by this context since the last reset: the
  * summed CUDA-event time of the loop graphs (milliseconds, measured on the
  * context stream) and the number of Leja iterations they ran.  The average

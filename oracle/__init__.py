@@ -58,6 +58,11 @@ def lib():
             L.or_exprb32.argtypes = [C.c_int, C.c_int, C.c_int, C.c_double, C.c_double, _dp, C.c_double,
                                      C.c_double, C.c_double, C.c_double, C.c_double, _dp, C.c_int, _dp, _dp,
                                      _dp, _ip]
+            L.or_controller.restype = C.c_double
+            L.or_controller.argtypes = [C.c_double, C.c_double, C.c_double]
+            L.or_integrate_exprb32.argtypes = [C.c_int, C.c_int, C.c_int, C.c_double, C.c_double, _dp, _dp,
+                                               C.c_double, C.c_double, C.c_double, C.c_double, _dp, C.c_int,
+                                               C.c_int, _ip, _ip, C.POINTER(C.c_longlong), _dp, _dp]
             _lib = L
     return _lib
 
@@ -192,3 +197,20 @@ def spectral_interval(rho: float):
     c = lambda/2, gamma = -lambda/4 (Sec. 2.2, Listing 7)."""
     lam = -1.05 * rho
     return lam / 2.0, -lam / 4.0
+
+
+def controller(h, err, tol):
+    return lib().or_controller(h, err, tol)
+
+
+def integrate_exprb32(kind, nx, ny, nu, a, u0, v0, t_final, h0, tol, leja_tol, xi, max_attempts=1000):
+    """Adaptive EXPRB32 run; returns (u, steps, rejected, leja_iters, h_next, t, status)."""
+    u = _f64(u0).copy()
+    v0 = _f64(v0)
+    xi = _f64(xi)
+    steps, rej = C.c_int(0), C.c_int(0)
+    its = C.c_longlong(0)
+    h, t = np.zeros(1), np.zeros(1)
+    st = lib().or_integrate_exprb32(kind, nx, ny, nu, a, _p(u), _p(v0), t_final, h0, tol, leja_tol, _p(xi),
+                                    len(xi), max_attempts, C.byref(steps), C.byref(rej), C.byref(its), _p(h), _p(t))
+    return u, steps.value, rej.value, its.value, float(h[0]), float(t[0]), st

@@ -461,3 +461,66 @@ int or_exprb32(int kind, int nx, int ny, double nu, double a, const double* u, d
   free(f_u); free(p1); free(t1); free(t2); free(nl_u); free(nl_a); free(p3);
   return st != OR_OK ? st : st2;
 }
+
+/* ------------------------------------------------------------------------ */
+/* Step-size control with the embedded error (Sec. 2.2: the EXPRB32 error   */
+/* estimate "may be used to control the step sizes").  The paper gives no   */
+/* controller; the reading is the classical one for a third-order pair:     */
+/* accept when err <= tol, and h_new = h * min(2, max(0.2,                  */
+/* 0.9 (tol/err)^(1/3))) after every attempt (factor 2 when err = 0).       */
+/* Every attempt first takes 10 power-iteration passes from v0 at the       */
+/* current state for the spectral interval (Sec. 2.2, Listing 7).           */
+/* ------------------------------------------------------------------------ */
+
+double or_controller(double h, double err, double tol) {
+  double f;
+  if (!(err > 0.0)) f = 2.0;
+  else {
+    f = 0.9 * pow(tol / err, 1.0 / 3.0);
+    if (f > 2.0) f = 2.0;
+    if (f < 0.2) f = 0.2;
+  }
+  return h * f;
+}
+
+int or_integrate_exprb32(int kind, int nx, int ny, double nu, double a, double* u, const double* v0,
+                         double t_final, double h0, double tol, double leja_tol, const double* xi, int K,
+                         int max_attempts, int* steps_out, int* rejected_out, long long* iters_out,
+                         double* h_out, double* t_out) {
+  long n = (long)nx * ny;
+  double* lo = (double*)malloc(sizeof(double) * (size_t)n);
+  double* hi = (double*)malloc(sizeof(double) * (size_t)n);
+  if (!lo || !hi) { free(lo); free(hi); return OR_E_NOMEM; }
+  double t = 0.0, h = h0;
+  int steps = 0, rejected = 0, status = OR_OK;
+  long long iters_total = 0;
+  for (int att = 0; att < max_attempts && t < t_final; ++att) {
+    double hh = h < t_final - t ? h : t_final - t;
+    double rho;
+    int pit;
+    int st = or_power_iteration(kind, nx, ny, nu, a, u, v0, 10, &rho, &pit);
+    if (st != OR_OK) { status = st; break; }
+    double lam = -1.05 * rho, c = lam / 2.0, gamma = -lam / 4.0;
+    double err;
+    int it;
+    st = or_exprb32(kind, nx, ny, nu, a, u, c, gamma, hh, leja_tol, leja_tol, xi, K, lo, hi, &err, &it);
+    iters_total += it;
+    if (st != OR_OK) { status = st; break; }
+    if (err <= tol) {
+      memcpy(u, hi, sizeof(double) * (size_t)n);
+      t += hh;
+      ++steps;
+    } else {
+      ++rejected;
+    }
+    h = or_controller(hh, err, tol);
+  }
+  *steps_out = steps;
+  *rejected_out = rejected;
+  *iters_out = iters_total;
+  *h_out = h;
+  *t_out = t;
+  free(lo);
+  free(hi);
+  return status;
+}

@@ -25,6 +25,7 @@ from .binding import (  # noqa: F401
     leja_destroy,
     leja_setup,
     lib,
+    lx_controller_classical,
     lx_ctx_autotune,
     lx_ctx_kernel_name,
     lx_ctx_select_kernel,
@@ -32,6 +33,7 @@ from .binding import (  # noqa: F401
     lx_ctx_stats,
     lx_leja_coeff_count,
     lx_leja_coeffs,
+    lx_integrate,
     lx_leja_points,
     lx_status_str,
     phi_l_apply,

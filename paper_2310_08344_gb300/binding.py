@@ -31,6 +31,11 @@ class LxStats(C.Structure):
                 ("power_ms", C.c_double)]
 
 
+class LxIntegrateInfo(C.Structure):
+    _fields_ = [("t", C.c_double), ("h", C.c_double), ("steps", C.c_int), ("rejected", C.c_int),
+                ("leja_iters", C.c_longlong), ("last_err", C.c_double), ("power_iters", C.c_int)]
+
+
 class LexgbError(RuntimeError):
     def __init__(self, status, what=""):
         self.status = status
@@ -72,6 +77,10 @@ def lib():
             L.lx_ctx_stats.argtypes = [_vp, C.POINTER(LxStats), C.c_int]
             L.lx_ctx_kernel_name.argtypes = [_vp, C.c_char_p, C.c_int]
             L.lx_ctx_set_loop_mode.argtypes = [_vp, C.c_int]
+            L.lx_controller_classical.restype = C.c_double
+            L.lx_controller_classical.argtypes = [C.c_double, C.c_double, C.c_double]
+            L.lx_integrate.argtypes = [_vp, _vp, _vp, C.c_double, C.c_double, C.c_double, C.c_int,
+                                       C.POINTER(LxIntegrateInfo)]
             L.lx_ctx_autotune.argtypes = [_vp, C.c_int, C.c_char_p, C.c_char_p, C.c_int]
             L.lx_ctx_select_kernel.argtypes = [_vp, C.c_char_p, C.c_int]
             L.phi_l_apply_noalloc.argtypes = [C.POINTER(LxProblem), C.c_int, _vp, _vp, C.c_double, C.c_double,
@@ -264,3 +273,16 @@ def lx_ctx_autotune(ctx: Context, iters=10, cache_path=None):
 
 def lx_ctx_select_kernel(ctx: Context, name: str, strip_h: int) -> int:
     return lib().lx_ctx_select_kernel(ctx.handle, name.encode(), strip_h)
+
+
+def lx_controller_classical(h, err, tol) -> float:
+    return lib().lx_controller_classical(h, err, tol)
+
+
+def lx_integrate(ctx: Context, u, v0, t_final, tol, leja_tol, max_attempts=100000, t0=0.0, h0=None,
+                 power_iters=10):
+    """Adaptive EXPRB32 run updating u in place.  Returns (status, info dict)."""
+    info = LxIntegrateInfo(t0, h0, 0, 0, 0, 0.0, power_iters)
+    st = lib().lx_integrate(ctx.handle, _dev(u), _dev(v0), t_final, tol, leja_tol, max_attempts, C.byref(info))
+    return st, {"t": info.t, "h": info.h, "steps": info.steps, "rejected": info.rejected,
+                "leja_iters": info.leja_iters, "last_err": info.last_err}

@@ -834,3 +834,67 @@ lx_status lx_ctx_autotune(lx_ctx* c, int iters, const char* cache_path, char* re
 }
 
 }  // extern "C"
+
+extern "C" {
+
+double lx_controller_classical(double h, double err, double tol) {
+  double f;
+  if (!(err > 0.0)) {
+    f = 2.0;
+  } else {
+    f = 0.9 * std::cbrt(tol / err);
+    f = std::min(2.0, std::max(0.2, f));
+  }
+  return h * f;
+}
+
+lx_status lx_integrate(lx_ctx* c, double* u, const double* v0, double t_final, double tol, double leja_tol,
+                       int max_attempts, lx_integrate_info* info) {
+  if (!c || !u || !v0 || !info || !(tol > 0.0) || !(leja_tol > 0.0) || max_attempts < 1 || !(info->h > 0.0))
+    return LX_E_INVAL;
+  if (c->integrator != LX_EXPRB32) return LX_E_INVAL;
+  const size_t nb = sizeof(double) * (size_t)c->n;
+  for (int k = 1; k < 3; ++k)
+    if (!c->d_io[k] && !cuda_ok(cudaMalloc((void**)&c->d_io[k], nb), "cudaMalloc")) return LX_E_NOMEM;
+  const int passes = info->power_iters > 0 ? info->power_iters : 10;
+  double t = info->t, h = info->h;
+  int steps = 0, rejected = 0;
+  long long iters = 0;
+  lx_status status = LX_OK;
+  for (int att = 0; att < max_attempts && t < t_final; ++att) {
+    const double hh = std::min(h, t_final - t);
+    double rho = 0.0;
+    lx_status st = power_bound(c, u, v0, passes, &rho, nullptr);
+    if (st != LX_OK) {
+      status = st;
+      break;
+    }
+    const double lam = -1.05 * rho, cc = lam / 2.0, gamma = -lam / 4.0;
+    double err = 0.0;
+    int it = 0;
+    st = expint_step(c, u, c->d_io[1], c->d_io[2], cc, gamma, hh, leja_tol, leja_tol, &err, &it);
+    iters += it;
+    if (st != LX_OK) {
+      status = st;
+      break;
+    }
+    info->last_err = err;
+    if (err <= tol) {
+      LX_CUDA(cudaMemcpyAsync(u, c->d_io[2], nb, cudaMemcpyDeviceToDevice, c->stream));
+      t += hh;
+      ++steps;
+    } else {
+      ++rejected;
+    }
+    h = lx_controller_classical(hh, err, tol);
+  }
+  LX_CUDA(cudaStreamSynchronize(c->stream));
+  info->t = t;
+  info->h = h;
+  info->steps = steps;
+  info->rejected = rejected;
+  info->leja_iters = iters;
+  return status;
+}
+
+}  // extern "C"

@@ -336,3 +336,24 @@ def test_autotune_selects_and_caches(lx, xi_oracle, tmp_path):
     st, it = lx.phi_l_apply(ctx, 0, None, dev(u0), out, c, g, h, TOL, TOL)
     ref, it_o, st_o = oracle.leja_phi(oracle.ADVDIFF, n, n, nu, a, None, 0, u0, c, g, h, TOL, TOL, xi_oracle)
     assert st == 0 and abs(it - it_o) <= 1 and rel(out.cpu().numpy(), ref) <= TOL
+
+
+def test_adaptive_integration_matches_oracle(lx, xi_oracle):
+    # Adaptive EXPRB32 with the classical controller on Burgers: the same
+    # accepted/rejected sequence and the same final state as the oracle.
+    n, nu = 48, 5e-3
+    u0 = synth.burgers_ic(n, n, seed=1)
+    v0 = synth.power_start(n * n, seed=5)
+    h0 = 50 * synth.cfl_step(n, n, nu, np.abs(u0).max())
+    T, tol = 2 * h0, 1e-4
+    ref, steps_o, rej_o, its_o, h_o, t_o, st_o = oracle.integrate_exprb32(
+        oracle.BURGERS, n, n, nu, 0.0, u0, v0, T, h0, tol, TOL, xi_oracle)
+    assert st_o == 0 and abs(t_o - T) <= 1e-12 * T
+    ctx = lx.leja_setup(n, n, nu, 0.0, lx.BURGERS, lx.FP64, lx.EXPRB32)
+    u = dev(u0)
+    st, info = lx.lx_integrate(ctx, u, dev(v0), T, tol, TOL, 10000, 0.0, h0, 10)
+    assert st == 0
+    assert info["steps"] == steps_o and info["rejected"] == rej_o
+    assert abs(info["t"] - t_o) <= 1e-12 * T
+    assert abs(info["leja_iters"] - its_o) <= 2 * (steps_o + rej_o)
+    assert rel(u.cpu().numpy(), ref) <= 1e-9

@@ -83,3 +83,15 @@ def test_invalid_arguments(lx):
         lx.lx_leja_points(0)
     with pytest.raises(LexgbError):
         lx.lx_leja_coeffs(1, 1.0, -1.0, 0.0, np.array([2.0, -2.0]))
+
+
+def test_classical_controller_matches_oracle(lx):
+    rng = np.random.default_rng(2)
+    for _ in range(500):
+        h = 10 ** rng.uniform(-6, 0)
+        tol = 10 ** rng.uniform(-10, -2)
+        err = tol * 10 ** rng.uniform(-4, 4) if rng.uniform() > 0.05 else 0.0
+        a = lx.lx_controller_classical(h, err, tol)
+        b = oracle.controller(h, err, tol)
+        assert abs(a - b) <= 2e-15 * b  # cbrt vs pow(., 1/3): an ulp or two
+        assert 0.2 * h * (1 - 1e-15) <= a <= 2.0 * h * (1 + 1e-15)
