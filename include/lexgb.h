@@ -241,6 +241,38 @@ lx_status lx_ctx_select_kernel(lx_ctx* ctx, const char* name, int strip_h);
 lx_status lx_ctx_kernel_name(lx_ctx* ctx, char* buf, int len);
 
 /* ---------------------------------------------------------------------------
+ * Batched instances.  Not in the paper: many independent problems of uneven
+ * grid sizes advance through the Leja loop together -- one fused launch per
+ * iteration covers every instance that has not converged, each instance has
+ * its own coefficients, weights, stopping test and status, and one CUDA
+ * graph runs the whole loop.
+ * ------------------------------------------------------------------------- */
+
+typedef struct lx_batch lx_batch;
+
+/* Set up a batch of `count` diffusion-advection problems (kind LX_ADVDIFF,
+ * precision LX_FP64).  Allocates the per-instance basis vectors and the strip
+ * table.  max_leja as in leja_setup. */
+lx_status batch_setup(int count, const lx_problem* probs, int max_leja, void* cuda_stream, lx_batch** out);
+
+/* phi_l(h_i A_i) w_i for every instance i (Sec. 2.1 Eq. 2 per instance).
+ *   w_dev, out_dev   host arrays of `count` device pointers (inputs are not
+ *                    modified; out_dev[i] must not alias w_dev[i])
+ *   c, gamma, h      host arrays of `count` doubles
+ *   rtol, atol       stopping test, shared
+ *   iters, status    host arrays of `count` ints (may be NULL): Leja
+ *                    iterations and lx_status of each instance
+ * Returns LX_OK, a call-level error, or the first non-OK instance status. */
+lx_status batch_step(lx_batch* b, int l, const double* const* w_dev, double* const* out_dev, const double* c,
+                     const double* gamma, const double* h, double rtol, double atol, int* iters, int* status);
+
+/* Loop timing of the batch (as lx_ctx_stats; loop_iterations counts launches
+ * of the fused batch kernel). */
+lx_status batch_stats(lx_batch* b, lx_stats* out, int reset);
+
+void batch_destroy(lx_batch* b);
+
+/* ---------------------------------------------------------------------------
  * Allocation-free entry point.  The paper has no counterpart: it exists for
  * callers that cannot allocate device memory at the point of the call --
  * code that runs while a stream is being captured into a CUDA graph (where

@@ -18,8 +18,12 @@ from .binding import (  # noqa: F401
     MIXED,
     ROS_EU,
     STATUS,
+    Batch,
     Context,
     LexgbError,
+    batch_setup,
+    batch_stats,
+    batch_step,
     expint_step,
     expint_step_host,
     leja_destroy,

@@ -81,6 +81,12 @@ def lib():
             L.lx_controller_classical.argtypes = [C.c_double, C.c_double, C.c_double]
             L.lx_integrate.argtypes = [_vp, _vp, _vp, C.c_double, C.c_double, C.c_double, C.c_int,
                                        C.POINTER(LxIntegrateInfo)]
+            L.batch_setup.argtypes = [C.c_int, C.POINTER(LxProblem), C.c_int, _vp, C.POINTER(_vp)]
+            L.batch_step.argtypes = [_vp, C.c_int, C.POINTER(_vp), C.POINTER(_vp), _dp, _dp, _dp, C.c_double,
+                                     C.c_double, _ip, _ip]
+            L.batch_stats.argtypes = [_vp, C.POINTER(LxStats), C.c_int]
+            L.batch_destroy.argtypes = [_vp]
+            L.batch_destroy.restype = None
             L.lx_ctx_autotune.argtypes = [_vp, C.c_int, C.c_char_p, C.c_char_p, C.c_int]
             L.lx_ctx_select_kernel.argtypes = [_vp, C.c_char_p, C.c_int]
             L.phi_l_apply_noalloc.argtypes = [C.POINTER(LxProblem), C.c_int, _vp, _vp, C.c_double, C.c_double,
@@ -286,3 +292,57 @@ def lx_integrate(ctx: Context, u, v0, t_final, tol, leja_tol, max_attempts=10000
     st = lib().lx_integrate(ctx.handle, _dev(u), _dev(v0), t_final, tol, leja_tol, max_attempts, C.byref(info))
     return st, {"t": info.t, "h": info.h, "steps": info.steps, "rejected": info.rejected,
                 "leja_iters": info.leja_iters, "last_err": info.last_err}
+
+
+class Batch:
+    """Owns an lx_batch*."""
+
+    def __init__(self, handle, problems):
+        self.handle = handle
+        self.problems = problems
+
+    @property
+    def count(self):
+        return len(self.problems)
+
+    def close(self):
+        if self.handle:
+            lib().batch_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def batch_setup(problems, max_leja=1000, stream=None) -> Batch:
+    """problems: list of (nx, ny, nu, a)."""
+    arr = (LxProblem * len(problems))(*[LxProblem(nx, ny, nu, a, ADVDIFF, FP64) for (nx, ny, nu, a) in problems])
+    h = _vp()
+    st = lib().batch_setup(len(problems), arr, max_leja, _stream_handle(stream), C.byref(h))
+    if st != OK:
+        raise LexgbError(st, "batch_setup")
+    return Batch(h.value, list(problems))
+
+
+def batch_step(b: Batch, l, ws, outs, c, gamma, h, rtol, atol):
+    """Returns (status, iters[list], statuses[list])."""
+    B = b.count
+    wp = (_vp * B)(*[_dev(x) for x in ws])
+    op = (_vp * B)(*[_dev(x) for x in outs])
+    ca = np.ascontiguousarray(c, dtype=np.float64)
+    ga = np.ascontiguousarray(gamma, dtype=np.float64)
+    ha = np.ascontiguousarray(h, dtype=np.float64)
+    its = (C.c_int * B)()
+    sts = (C.c_int * B)()
+    st = lib().batch_step(b.handle, l, wp, op, ca.ctypes.data_as(_dp), ga.ctypes.data_as(_dp),
+                          ha.ctypes.data_as(_dp), rtol, atol, its, sts)
+    return st, list(its), list(sts)
+
+
+def batch_stats(b: Batch, reset=False) -> dict:
+    s = LxStats()
+    lib().batch_stats(b.handle, C.byref(s), 1 if reset else 0)
+    return {"loop_ms": s.loop_ms, "loop_iterations": s.loop_iterations, "loop_launches": s.loop_launches}

@@ -1,0 +1,156 @@
+// Batched Leja interpolation: many independent diffusion-advection instances
+// of uneven grid sizes in one launch per Leja iteration.
+//
+// The strips of all instances (32*VEC columns x H rows each) form one flat
+// list; warps take strips with a grid stride, so small and large instances
+// share every wave.  Each strip's partial sums go to its own slot; the warp
+// that finishes the last strip of an instance (an arrival ticket per
+// instance) adds that instance's partials in strip order, runs the stopping
+// test of Sec. 2.2 for it and, when it has converged (or failed), marks it
+// done: its strips are skipped by every later launch.  The last instance to
+// finish ends the CUDA graph's while loop.  All instances advance together,
+// so the iteration index m is global; the per-instance iteration counts are
+// the m at which each stopped.
+#pragma once
+
+#include "leja_kernels.cuh"
+
+namespace lexgb {
+
+struct BatchInst {
+  int nx, ny;
+  int first_strip, nstrips;
+  int kmax;
+  int done, status, iters;
+  double wxp, wxm, wyp, wym, wc0;
+  double rtol, atol;
+  const double* w;
+  double* y0;
+  double* y1;
+  double* p;
+  const double* d;
+  double ynorm, pnorm, err;
+};
+
+struct BatchState {
+  int m;       // global iteration index
+  int active;  // instances not yet done
+  int mmax;    // safety cap on m
+  int pad;
+};
+
+template <int VEC>
+__global__ void __launch_bounds__(kThreadsPerBlock)
+    leja_batch_kernel(BatchInst* __restrict__ inst, const int* __restrict__ strip_inst, BatchState* __restrict__ bs,
+                      double* __restrict__ partials, unsigned int* __restrict__ tickets,
+                      unsigned int* __restrict__ block_ticket, const double* __restrict__ xi, int H,
+                      int total_strips, cudaGraphConditionalHandle cond, int use_cond) {
+  const int m = __ldcg(&bs->m);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const double xim = __ldg(xi + m);
+  for (int s = blockIdx.x * kWarpsPerBlock + warp; s < total_strips; s += gridDim.x * kWarpsPerBlock) {
+    const int i = __ldg(strip_inst + s);
+    BatchInst* I = inst + i;
+    if (__ldcg(&I->done)) continue;
+    LoopArgs A;
+    A.nx = I->nx;
+    A.ny = I->ny;
+    A.wxp = I->wxp;
+    A.wxm = I->wxm;
+    A.wyp = I->wyp;
+    A.wym = I->wym;
+    A.u = nullptr;
+    A.s = nullptr;
+    const int ncs = (A.nx + 32 * VEC - 1) / (32 * VEC);
+    const int ls = s - I->first_strip;
+    const int col0 = (ls % ncs) * 32 * VEC;
+    const int r0 = (ls / ncs) * H;
+    const int r1 = min(r0 + H, A.ny);
+    const double* d = I->d;
+    const double dm1 = __ldg(d + m + 1);
+    const double d0 = __ldg(d);
+    const double wcm = I->wc0 - xim;
+    double* dst = (m & 1) ? I->y1 : I->y0;
+    double sy = 0.0, sp = 0.0;
+    if (m == 0) {
+      leja_strip<0, double, VEC, double, true>(A, I->w, dst, I->p, col0, r0, r1, wcm, d0, dm1, sy, sp);
+    } else {
+      const double* src = ((m - 1) & 1) ? I->y1 : I->y0;
+      leja_strip<0, double, VEC, double, false>(A, src, dst, I->p, col0, r0, r1, wcm, d0, dm1, sy, sp);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      sy += __shfl_xor_sync(0xffffffffu, sy, o);
+      sp += __shfl_xor_sync(0xffffffffu, sp, o);
+    }
+    unsigned last = 0;
+    if (lane == 0) {
+      partials[2 * (size_t)s] = sy;
+      partials[2 * (size_t)s + 1] = sp;
+      __threadfence();
+      last = (atomicAdd(tickets + i, 1u) == (unsigned)I->nstrips - 1u) ? 1u : 0u;
+    }
+    last = __shfl_sync(0xffffffffu, last, 0);
+    if (!last) continue;
+    // this warp finalises instance i: fixed-order sum of its strip partials
+    __threadfence();
+    double ty = 0.0, tp = 0.0;
+    for (int q = lane; q < I->nstrips; q += 32) {
+      ty += __ldcg(partials + 2 * (size_t)(I->first_strip + q));
+      tp += __ldcg(partials + 2 * (size_t)(I->first_strip + q) + 1);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      ty += __shfl_xor_sync(0xffffffffu, ty, o);
+      tp += __shfl_xor_sync(0xffffffffu, tp, o);
+    }
+    if (lane == 0) {
+      const double inv_n = 1.0 / ((double)A.nx * (double)A.ny);
+      const double ynorm = sqrt(ty * inv_n), pnorm = sqrt(tp * inv_n);
+      const double e = fabs(dm1) * ynorm;
+      const int m1 = m + 1;
+      int status = 0;
+      bool done = false;
+      if (!isfinite(e) || !isfinite(pnorm)) {
+        status = 5;
+        done = true;
+      } else if (e <= I->rtol * pnorm + I->atol) {
+        done = true;
+      } else if (m1 >= I->kmax) {
+        status = 4;
+        done = true;
+      }
+      I->ynorm = ynorm;
+      I->pnorm = pnorm;
+      I->err = e;
+      tickets[i] = 0u;
+      if (done) {
+        I->status = status;
+        I->iters = m1;
+        __threadfence();
+        I->done = 1;
+        if (atomicSub(&bs->active, 1) == 1 && use_cond) cudaGraphSetConditional(cond, 0);
+      }
+    }
+  }
+  // the last block to finish advances the global iteration index
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    if (atomicAdd(block_ticket, 1u) == gridDim.x - 1) {
+      *block_ticket = 0u;
+      bs->m = m + 1;
+      if (m + 1 >= bs->mmax && use_cond) cudaGraphSetConditional(cond, 0);
+    }
+  }
+}
+
+// Resets the batch loop state (one thread).
+static __global__ void batch_reset_kernel(BatchState* bs, int active, int mmax, unsigned int* block_ticket) {
+  bs->m = 0;
+  bs->active = active;
+  bs->mmax = mmax;
+  *block_ticket = 0u;
+}
+
+}  // namespace lexgb

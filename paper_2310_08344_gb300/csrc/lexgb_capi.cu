@@ -19,6 +19,7 @@
 #include <string>
 #include <vector>
 
+#include "leja_batch.cuh"
 #include "leja_df64.cuh"
 #include "leja_kernels.cuh"
 #include "lexgb_internal.h"
@@ -895,6 +896,280 @@ lx_status lx_integrate(lx_ctx* c, double* u, const double* v0, double t_final, d
   info->rejected = rejected;
   info->leja_iters = iters;
   return status;
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Batched instances (one launch per Leja iteration for all instances)
+// ---------------------------------------------------------------------------
+
+struct lx_batch {
+  int B = 0;
+  int K = 1000;
+  cudaStream_t stream = nullptr;
+  int sm_count = 0;
+  int H = 32;
+  std::vector<lx_problem> probs;
+  std::vector<int> first_strip[2], nstrips[2];
+  int total_strips[2] = {0, 0};
+  int* d_strip_inst[2] = {nullptr, nullptr};
+  BatchInst* d_inst = nullptr;
+  BatchInst* h_inst = nullptr;  // pinned
+  BatchState* d_bs = nullptr;
+  unsigned int* d_tickets = nullptr;
+  unsigned int* d_block_ticket = nullptr;
+  double* d_partials = nullptr;
+  double* d_xi = nullptr;
+  double* d_coef = nullptr;
+  double* h_coef = nullptr;  // pinned, B x K
+  struct Key {
+    bool valid = false;
+    int l = 0, count = 0;
+    double h = 0, c = 0, g = 0;
+  };
+  std::vector<Key> keys;
+  double* d_ybuf = nullptr;
+  std::vector<size_t> yoff;
+  cudaGraph_t graph[2] = {nullptr, nullptr};
+  cudaGraphExec_t exec[2] = {nullptr, nullptr};
+  int grid[2] = {0, 0};
+  cudaEvent_t ev[2] = {};
+  lx_stats stats{};
+};
+
+namespace {
+
+template <int VEC>
+const void* batch_kernel_ptr() {
+  return reinterpret_cast<const void*>(&leja_batch_kernel<VEC>);
+}
+
+lx_status build_batch_graph(lx_batch* b, int v) {
+  if (b->exec[v]) return LX_OK;
+  const void* fn = v == 0 ? batch_kernel_ptr<2>() : batch_kernel_ptr<1>();
+  int per_sm = 0;
+  LX_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kThreadsPerBlock, 0));
+  const int want = (b->total_strips[v] + kWarpsPerBlock - 1) / kWarpsPerBlock;
+  b->grid[v] = std::max(1, std::min(want, std::max(per_sm, 1) * b->sm_count));
+  LX_CUDA(cudaGraphCreate(&b->graph[v], 0));
+  cudaGraphConditionalHandle cond;
+  LX_CUDA(cudaGraphConditionalHandleCreate(&cond, b->graph[v], 1, cudaGraphCondAssignDefault));
+  alignas(cudaGraphNodeParams) unsigned char cp_raw[sizeof(cudaGraphNodeParams)];
+  std::memset(cp_raw, 0, sizeof(cp_raw));
+  cudaGraphNodeParams& cp = *reinterpret_cast<cudaGraphNodeParams*>(cp_raw);
+  cp.type = cudaGraphNodeTypeConditional;
+  cp.conditional.handle = cond;
+  cp.conditional.type = cudaGraphCondTypeWhile;
+  cp.conditional.size = 1;
+  cudaGraphNode_t cnode;
+  LX_CUDA(cudaGraphAddNode(&cnode, b->graph[v], nullptr, nullptr, 0, &cp));
+  cudaGraph_t body = cp.conditional.phGraph_out[0];
+  BatchInst* inst = b->d_inst;
+  const int* strip_inst = b->d_strip_inst[v];
+  BatchState* bs = b->d_bs;
+  double* partials = b->d_partials;
+  unsigned int* tickets = b->d_tickets;
+  unsigned int* bt = b->d_block_ticket;
+  const double* xi = b->d_xi;
+  int H = b->H, total = b->total_strips[v], use_cond = 1;
+  void* kargs[] = {(void*)&inst, (void*)&strip_inst, (void*)&bs, (void*)&partials, (void*)&tickets, (void*)&bt,
+                   (void*)&xi, (void*)&H, (void*)&total, (void*)&cond, (void*)&use_cond};
+  cudaKernelNodeParams kp;
+  std::memset(&kp, 0, sizeof(kp));
+  kp.func = const_cast<void*>(fn);
+  kp.gridDim = dim3(b->grid[v]);
+  kp.blockDim = dim3(kThreadsPerBlock);
+  kp.kernelParams = kargs;
+  cudaGraphNode_t knode;
+  LX_CUDA(cudaGraphAddKernelNode(&knode, body, nullptr, 0, &kp));
+  LX_CUDA(cudaGraphInstantiate(&b->exec[v], b->graph[v], 0));
+  return LX_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+void batch_destroy(lx_batch* b) {
+  if (!b) return;
+  for (int v = 0; v < 2; ++v) {
+    if (b->exec[v]) cudaGraphExecDestroy(b->exec[v]);
+    if (b->graph[v]) cudaGraphDestroy(b->graph[v]);
+    cudaFree(b->d_strip_inst[v]);
+  }
+  cudaFree(b->d_inst);
+  if (b->h_inst) cudaFreeHost(b->h_inst);
+  cudaFree(b->d_bs);
+  cudaFree(b->d_tickets);
+  cudaFree(b->d_block_ticket);
+  cudaFree(b->d_partials);
+  cudaFree(b->d_xi);
+  cudaFree(b->d_coef);
+  if (b->h_coef) cudaFreeHost(b->h_coef);
+  cudaFree(b->d_ybuf);
+  for (auto& e : b->ev)
+    if (e) cudaEventDestroy(e);
+  delete b;
+}
+
+lx_status batch_setup(int count, const lx_problem* probs, int max_leja, void* cuda_stream, lx_batch** out) {
+  if (!out || count < 1 || !probs) return LX_E_INVAL;
+  *out = nullptr;
+  if (max_leja == 0) max_leja = 1000;
+  if (max_leja < 16 || max_leja > 4096) return LX_E_INVAL;
+  for (int i = 0; i < count; ++i)
+    if (!valid_problem(probs + i) || probs[i].kind != LX_ADVDIFF || probs[i].precision != LX_FP64) return LX_E_INVAL;
+  lx_batch* b = new lx_batch();
+  auto fail = [&](lx_status s) {
+    batch_destroy(b);
+    return s;
+  };
+  b->B = count;
+  b->K = max_leja;
+  b->stream = reinterpret_cast<cudaStream_t>(cuda_stream);
+  b->probs.assign(probs, probs + count);
+  b->keys.resize(count);
+  int dev = 0;
+  if (!cuda_ok(cudaGetDevice(&dev), "cudaGetDevice") ||
+      !cuda_ok(cudaDeviceGetAttribute(&b->sm_count, cudaDevAttrMultiProcessorCount, dev), "sm count"))
+    return fail(LX_E_CUDA);
+  // strip tables for the wide (VEC = 2) and generic (VEC = 1) kernels
+  std::vector<int> table[2];
+  for (int v = 0; v < 2; ++v) {
+    const int vec = v == 0 ? 2 : 1;
+    b->first_strip[v].resize(count);
+    b->nstrips[v].resize(count);
+    for (int i = 0; i < count; ++i) {
+      const int ncs = (probs[i].nx + 32 * vec - 1) / (32 * vec);
+      const int nrs = (probs[i].ny + b->H - 1) / b->H;
+      b->first_strip[v][i] = (int)table[v].size();
+      b->nstrips[v][i] = ncs * nrs;
+      table[v].insert(table[v].end(), (size_t)ncs * nrs, i);
+    }
+    b->total_strips[v] = (int)table[v].size();
+  }
+  size_t ytot = 0;
+  for (int i = 0; i < count; ++i) {
+    b->yoff.push_back(ytot);
+    const size_t n = (size_t)probs[i].nx * probs[i].ny;
+    ytot += 2 * ((n + 31) / 32 * 32);
+  }
+  std::vector<double> xi(b->K);
+  if (leja_points(b->K, xi.data()) != LX_OK) return fail(LX_E_INVAL);
+  auto dm = [&](void** p, size_t bytes) { return cuda_ok(cudaMalloc(p, bytes), "cudaMalloc"); };
+  if (!dm((void**)&b->d_inst, sizeof(BatchInst) * count) ||
+      !cuda_ok(cudaMallocHost((void**)&b->h_inst, sizeof(BatchInst) * count), "cudaMallocHost") ||
+      !dm((void**)&b->d_bs, sizeof(BatchState)) || !dm((void**)&b->d_tickets, sizeof(unsigned) * count) ||
+      !dm((void**)&b->d_block_ticket, sizeof(unsigned)) ||
+      !dm((void**)&b->d_partials, sizeof(double) * 2 * (size_t)std::max(b->total_strips[0], b->total_strips[1])) ||
+      !dm((void**)&b->d_xi, sizeof(double) * b->K) || !dm((void**)&b->d_coef, sizeof(double) * b->K * count) ||
+      !cuda_ok(cudaMallocHost((void**)&b->h_coef, sizeof(double) * b->K * count), "cudaMallocHost") ||
+      !dm((void**)&b->d_ybuf, sizeof(double) * ytot))
+    return fail(LX_E_NOMEM);
+  for (int v = 0; v < 2; ++v) {
+    if (!dm((void**)&b->d_strip_inst[v], sizeof(int) * table[v].size())) return fail(LX_E_NOMEM);
+    if (!cuda_ok(cudaMemcpy(b->d_strip_inst[v], table[v].data(), sizeof(int) * table[v].size(),
+                            cudaMemcpyHostToDevice), "upload strips"))
+      return fail(LX_E_CUDA);
+  }
+  if (!cuda_ok(cudaMemcpy(b->d_xi, xi.data(), sizeof(double) * b->K, cudaMemcpyHostToDevice), "upload xi"))
+    return fail(LX_E_CUDA);
+  for (auto& e : b->ev)
+    if (!cuda_ok(cudaEventCreate(&e), "cudaEventCreate")) return fail(LX_E_CUDA);
+  *out = b;
+  return LX_OK;
+}
+
+lx_status batch_step(lx_batch* b, int l, const double* const* w, double* const* out, const double* cc,
+                     const double* gamma, const double* h, double rtol, double atol, int* iters, int* status) {
+  if (!b || !w || !out || !cc || !gamma || !h || l < 0 || l > 8 || !(rtol >= 0.0) || !(atol >= 0.0)) return LX_E_INVAL;
+  bool wide = true;
+  int mmax = 1;
+  for (int i = 0; i < b->B; ++i) {
+    if (!w[i] || !out[i] || w[i] == out[i] || !(gamma[i] != 0.0) || !std::isfinite(h[i] * cc[i]) ||
+        !std::isfinite(h[i] * gamma[i]))
+      return LX_E_INVAL;
+    if (b->probs[i].nx % 64 != 0 || !aligned16(w[i]) || !aligned16(out[i])) wide = false;
+  }
+  const int v = wide ? 0 : 1;
+  for (int i = 0; i < b->B; ++i) {
+    lx_batch::Key& k = b->keys[i];
+    double* hc = b->h_coef + (size_t)i * b->K;
+    if (!(k.valid && k.l == l && k.h == h[i] && k.c == cc[i] && k.g == gamma[i])) {
+      const int count = leja_coeff_count(h[i], cc[i], gamma[i], b->K);
+      std::vector<double> xi(count);
+      leja_points(count, xi.data());
+      int st = leja_coeffs(l, h[i], cc[i], gamma[i], xi.data(), count, hc);
+      if (st != LX_OK) return (lx_status)st;
+      LX_CUDA(cudaMemcpyAsync(b->d_coef + (size_t)i * b->K, hc, sizeof(double) * count, cudaMemcpyHostToDevice,
+                              b->stream));
+      k.valid = true;
+      k.l = l;
+      k.h = h[i];
+      k.c = cc[i];
+      k.g = gamma[i];
+      k.count = count;
+    }
+    const lx_problem& P = b->probs[i];
+    const double dx = 1.0 / P.nx, dy = 1.0 / P.ny, ig = 1.0 / gamma[i];
+    const double nx2 = P.nu / (dx * dx), ny2 = P.nu / (dy * dy);
+    BatchInst& I = b->h_inst[i];
+    std::memset(&I, 0, sizeof(I));
+    I.nx = P.nx;
+    I.ny = P.ny;
+    I.first_strip = b->first_strip[v][i];
+    I.nstrips = b->nstrips[v][i];
+    I.kmax = k.count - 1;
+    I.wxp = (nx2 + P.a / (2 * dx)) * ig;
+    I.wxm = (nx2 - P.a / (2 * dx)) * ig;
+    I.wyp = (ny2 + P.a / (2 * dy)) * ig;
+    I.wym = (ny2 - P.a / (2 * dy)) * ig;
+    I.wc0 = (-2.0 * nx2 - 2.0 * ny2 - cc[i]) * ig;
+    I.rtol = rtol;
+    I.atol = atol;
+    I.w = w[i];
+    const size_t n = (size_t)P.nx * P.ny;
+    I.y0 = b->d_ybuf + b->yoff[i];
+    I.y1 = I.y0 + (n + 31) / 32 * 32;
+    I.p = out[i];
+    I.d = b->d_coef + (size_t)i * b->K;
+    mmax = std::max(mmax, I.kmax);
+  }
+  lx_status st = build_batch_graph(b, v);
+  if (st != LX_OK) return st;
+  LX_CUDA(cudaMemcpyAsync(b->d_inst, b->h_inst, sizeof(BatchInst) * b->B, cudaMemcpyHostToDevice, b->stream));
+  LX_CUDA(cudaMemsetAsync(b->d_tickets, 0, sizeof(unsigned) * b->B, b->stream));
+  batch_reset_kernel<<<1, 1, 0, b->stream>>>(b->d_bs, b->B, mmax, b->d_block_ticket);
+  LX_CUDA(cudaGetLastError());
+  LX_CUDA(cudaEventRecord(b->ev[0], b->stream));
+  LX_CUDA(cudaGraphLaunch(b->exec[v], b->stream));
+  LX_CUDA(cudaEventRecord(b->ev[1], b->stream));
+  LX_CUDA(cudaMemcpyAsync(b->h_inst, b->d_inst, sizeof(BatchInst) * b->B, cudaMemcpyDeviceToHost, b->stream));
+  BatchState hs;
+  LX_CUDA(cudaMemcpyAsync(&hs, b->d_bs, sizeof(BatchState), cudaMemcpyDeviceToHost, b->stream));
+  LX_CUDA(cudaStreamSynchronize(b->stream));
+  float ms = 0.f;
+  LX_CUDA(cudaEventElapsedTime(&ms, b->ev[0], b->ev[1]));
+  b->stats.loop_ms += ms;
+  b->stats.loop_launches += 1;
+  b->stats.loop_iterations += hs.m;
+  lx_status first = LX_OK;
+  for (int i = 0; i < b->B; ++i) {
+    const BatchInst& I = b->h_inst[i];
+    const int sti = I.done ? I.status : (int)LX_E_NOCONV;
+    if (iters) iters[i] = I.done ? I.iters : hs.m;
+    if (status) status[i] = sti;
+    if (first == LX_OK && sti != LX_OK) first = (lx_status)sti;
+  }
+  return first;
+}
+
+lx_status batch_stats(lx_batch* b, lx_stats* out, int reset) {
+  if (!b || !out) return LX_E_INVAL;
+  *out = b->stats;
+  if (reset) b->stats = lx_stats{};
+  return LX_OK;
 }
 
 }  // extern "C"

@@ -1,0 +1,71 @@
+"""GPU parity of the batched form: every instance against the oracle.
+
+Instances of uneven sizes advance together in one launch per iteration; each
+must give the oracle's result for its own problem (relative L2 <= 1e-10,
+iterations +-1) and the oracle's status, including an advection-dominated
+instance where real Leja interpolation diverges (both report non-finite)."""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-10
+
+
+@pytest.fixture(scope="module")
+def lx():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2310_08344_gb300 as m
+
+    return m
+
+
+def _instances(sizes, seed):
+    rng = np.random.default_rng(seed)
+    out = []
+    for n in sizes:
+        nu = 10 ** rng.uniform(-2.5, -1.5)
+        a = rng.uniform(0.0, 1.0)
+        out.append((n[0], n[1], nu, a, int(rng.integers(1, 1000))))
+    return out
+
+
+def _symbol_radius(nx, ny, nu, a):
+    import fourier
+
+    return fourier.spectral_radius(nx, ny, nu, a)
+
+
+@pytest.mark.parametrize("sizes", [
+    [(64, 64), (128, 128), (192, 64), (64, 256), (128, 32), (256, 256), (64, 64), (128, 96)],   # wide kernel
+    [(64, 64), (96, 80), (33, 45), (128, 128), (1, 7), (70, 70)],                               # generic kernel
+])
+def test_batch_matches_oracle(lx, sizes):
+    inst = _instances(sizes, seed=len(sizes))
+    inst.append((128, 128, 1e-3, 2.0, 5))  # advection-dominated: diverges in both
+    xi = oracle.leja_points(1000)
+    b = lx.batch_setup([(nx, ny, nu, a) for (nx, ny, nu, a, _) in inst])
+    ws, outs, cs, gs, hs, refs = [], [], [], [], [], []
+    for (nx, ny, nu, a, s) in inst:
+        u0 = synth.gaussians_ic(nx, ny, seed=s)
+        h = 50 * synth.cfl_step(nx, ny, nu, a) if nx > 1 else 1e-3
+        c, g = oracle.spectral_interval(max(_symbol_radius(nx, ny, nu, a), 1.0))
+        ws.append(torch.from_numpy(u0).cuda())
+        outs.append(torch.empty(nx * ny, dtype=torch.float64, device="cuda"))
+        cs.append(c)
+        gs.append(g)
+        hs.append(h)
+        refs.append(oracle.leja_phi(oracle.ADVDIFF, nx, ny, nu, a, None, 0, u0, c, g, h, TOL, TOL, xi))
+    for rep in range(2):  # the second call reuses the cached coefficients
+        st, its, sts = lx.batch_step(b, 0, ws, outs, cs, gs, hs, TOL, TOL)
+        for k, (ref, it_o, st_o) in enumerate(refs):
+            assert sts[k] == st_o, (k, sts[k], st_o)
+            if st_o == 0:
+                assert abs(its[k] - it_o) <= 1, (k, its[k], it_o)
+                got = outs[k].cpu().numpy()
+                assert np.linalg.norm(got - ref) <= TOL * np.linalg.norm(ref), k
