@@ -273,6 +273,47 @@ lx_status batch_stats(lx_batch* b, lx_stats* out, int reset);
 void batch_destroy(lx_batch* b);
 
 /* ---------------------------------------------------------------------------
+ * Learned step-size controller (not in the paper): a 5 -> 64 -> 64 -> 64 -> 2
+ * ReLU MLP, BF16 weights and activations with FP32 accumulation on the tensor
+ * cores.  Inputs (per attempted step): log(rho h), log(h / dt_CFL),
+ * iters / 100, log10(err / tol), ||u||; outputs: log(h_next / h) and
+ * log(iters predicted).  It only proposes step sizes: the embedded error
+ * test still accepts or rejects every step.
+ * Parameter vector (FP32, mlp_param_count() floats): W1[5][64], b1[64],
+ * W2[64][64], b2[64], W3[64][64], b3[64], W4[64][2], b4[2] (W[i][j] joins
+ * input i to output j).  Normalisation vector (14 floats): mean_x[5],
+ * std_x[5], mean_y[2], std_y[2]; the network works on normalised values.
+ * ------------------------------------------------------------------------- */
+
+typedef struct lx_mlp lx_mlp;
+
+int mlp_param_count(void);
+
+/* Create a model for batches of up to batch_max rows from host weights and
+ * normalisation (both copied). */
+lx_status mlp_setup(int batch_max, const float* w_host, const float* norm_host, void* cuda_stream, lx_mlp** out);
+
+/* Current FP32 master weights to the host. */
+lx_status mlp_get_weights(lx_mlp* m, float* w_host);
+
+/* y[B][2] = net(x[B][5]), device row-major arrays. */
+lx_status mlp_forward(lx_mlp* m, const float* x_dev, float* y_dev, int B);
+
+/* The same for host arrays, B <= 64 (inference inside a time loop). */
+lx_status mlp_forward_host(lx_mlp* m, const float* x_host, float* y_host, int B);
+
+/* One training step on device arrays x[B][5], targets t[B][2]: the loss
+ * sum_rows sum_outputs (y_n - t_n)^2 / (2 B) on normalised values, its
+ * gradient (forward and backward on the tensor cores, per-CTA partials added
+ * in a fixed order), and with adam = 1 an Adam step (lr, beta 0.9 / 0.999,
+ * eps 1e-8) on the FP32 masters.  grad_host (may be NULL) receives the
+ * gradient, loss (may be NULL) the loss before the step.  B <= batch_max. */
+lx_status mlp_train_step(lx_mlp* m, const float* x_dev, const float* t_dev, int B, int adam, float lr,
+                         float* grad_host, float* loss);
+
+void mlp_destroy(lx_mlp* m);
+
+/* ---------------------------------------------------------------------------
  * Allocation-free entry point.  The paper has no counterpart: it exists for
  * callers that cannot allocate device memory at the point of the call --
  * code that runs while a stream is being captured into a CUDA graph (where

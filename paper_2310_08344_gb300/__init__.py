@@ -21,6 +21,7 @@ from .binding import (  # noqa: F401
     Batch,
     Context,
     LexgbError,
+    Mlp,
     batch_setup,
     batch_stats,
     batch_step,
@@ -40,6 +41,12 @@ from .binding import (  # noqa: F401
     lx_integrate,
     lx_leja_points,
     lx_status_str,
+    mlp_forward,
+    mlp_forward_host,
+    mlp_get_weights,
+    mlp_param_count,
+    mlp_setup,
+    mlp_train_step,
     phi_l_apply,
     phi_l_apply_noalloc,
     power_bound,

@@ -10,7 +10,7 @@ ROOT = os.path.dirname(PKG)
 CSRC = os.path.join(PKG, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 LIB = os.path.join(PKG, "_lexgb.so")
-SOURCES = ["lexgb_capi.cu", "lexgb_noalloc.cu", "leja_host.cpp"]
+SOURCES = ["lexgb_capi.cu", "lexgb_noalloc.cu", "lexgb_mlp.cu", "leja_host.cpp"]
 HEADERS = ["leja_kernels.cuh", "leja_df64.cuh", "leja_batch.cuh", "lexgb_internal.h"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
@@ -32,7 +32,7 @@ def up_to_date() -> bool:
 def nvcc_command(out: str, extra=()):
     nvcc = os.environ.get("NVCC", "nvcc")
     return [nvcc, "-O3", "-std=c++17", *ARCH, "-lineinfo", "-Xcompiler", "-fPIC,-O2", "-shared",
-            "--threads", "3", "-diag-suppress", "177", f"-I{INCLUDE}", *extra, *[os.path.join(CSRC, s) for s in SOURCES], "-o", out]
+            "--threads", "4", "-diag-suppress", "177", f"-I{INCLUDE}", *extra, *[os.path.join(CSRC, s) for s in SOURCES], "-o", out]
 
 
 def build(force: bool = False, verbose: bool = False) -> str:

@@ -87,6 +87,15 @@ def lib():
             L.batch_stats.argtypes = [_vp, C.POINTER(LxStats), C.c_int]
             L.batch_destroy.argtypes = [_vp]
             L.batch_destroy.restype = None
+            _fp = C.POINTER(C.c_float)
+            L.mlp_param_count.restype = C.c_int
+            L.mlp_setup.argtypes = [C.c_int, _fp, _fp, _vp, C.POINTER(_vp)]
+            L.mlp_get_weights.argtypes = [_vp, _fp]
+            L.mlp_forward.argtypes = [_vp, _vp, _vp, C.c_int]
+            L.mlp_forward_host.argtypes = [_vp, _fp, _fp, C.c_int]
+            L.mlp_train_step.argtypes = [_vp, _vp, _vp, C.c_int, C.c_int, C.c_float, _fp, _fp]
+            L.mlp_destroy.argtypes = [_vp]
+            L.mlp_destroy.restype = None
             L.lx_ctx_autotune.argtypes = [_vp, C.c_int, C.c_char_p, C.c_char_p, C.c_int]
             L.lx_ctx_select_kernel.argtypes = [_vp, C.c_char_p, C.c_int]
             L.phi_l_apply_noalloc.argtypes = [C.POINTER(LxProblem), C.c_int, _vp, _vp, C.c_double, C.c_double,
@@ -346,3 +355,74 @@ def batch_stats(b: Batch, reset=False) -> dict:
     s = LxStats()
     lib().batch_stats(b.handle, C.byref(s), 1 if reset else 0)
     return {"loop_ms": s.loop_ms, "loop_iterations": s.loop_iterations, "loop_launches": s.loop_launches}
+
+
+class Mlp:
+    """Owns an lx_mlp*."""
+
+    def __init__(self, handle):
+        self.handle = handle
+
+    def close(self):
+        if self.handle:
+            lib().mlp_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def _f32(a):
+    return np.ascontiguousarray(a, dtype=np.float32)
+
+
+def mlp_param_count() -> int:
+    return lib().mlp_param_count()
+
+
+def mlp_setup(batch_max, w, norm, stream=None) -> Mlp:
+    w, norm = _f32(w), _f32(norm)
+    h = _vp()
+    fp = C.POINTER(C.c_float)
+    st = lib().mlp_setup(batch_max, w.ctypes.data_as(fp), norm.ctypes.data_as(fp), _stream_handle(stream),
+                         C.byref(h))
+    if st != OK:
+        raise LexgbError(st, "mlp_setup")
+    return Mlp(h.value)
+
+
+def mlp_get_weights(m: Mlp) -> np.ndarray:
+    w = np.zeros(mlp_param_count(), dtype=np.float32)
+    st = lib().mlp_get_weights(m.handle, w.ctypes.data_as(C.POINTER(C.c_float)))
+    if st != OK:
+        raise LexgbError(st, "mlp_get_weights")
+    return w
+
+
+def mlp_forward(m: Mlp, x, y, B) -> int:
+    """x, y: CUDA float32 tensors [B,5], [B,2]."""
+    return lib().mlp_forward(m.handle, _dev(x), _dev(y), B)
+
+
+def mlp_forward_host(m: Mlp, x) -> np.ndarray:
+    x = _f32(x)
+    B = x.shape[0]
+    y = np.zeros((B, 2), dtype=np.float32)
+    fp = C.POINTER(C.c_float)
+    st = lib().mlp_forward_host(m.handle, x.ctypes.data_as(fp), y.ctypes.data_as(fp), B)
+    if st != OK:
+        raise LexgbError(st, "mlp_forward_host")
+    return y
+
+
+def mlp_train_step(m: Mlp, x, t, B, adam=True, lr=1e-3, want_grad=False):
+    """Returns (status, loss, grad or None)."""
+    fp = C.POINTER(C.c_float)
+    g = np.zeros(mlp_param_count(), dtype=np.float32) if want_grad else None
+    loss = C.c_float(0.0)
+    st = lib().mlp_train_step(m.handle, _dev(x), _dev(t), B, 1 if adam else 0, lr,
+                              g.ctypes.data_as(fp) if g is not None else None, C.byref(loss))
+    return st, float(loss.value), g
