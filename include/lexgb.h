@@ -201,6 +201,20 @@ typedef struct {
 lx_status lx_integrate(lx_ctx* ctx, double* u_dev, const double* v0_dev, double t_final, double tol,
                        double leja_tol, int max_attempts, lx_integrate_info* info);
 
+/* Forward declaration of the controller network (see mlp_setup below). */
+typedef struct lx_mlp lx_mlp;
+
+/* lx_integrate with the learned controller: after every accepted step the
+ * network proposes the next step size from the attempt's features
+ * (log(rho h), log(h / dt_ref), iters / 100, log10(err / tol), ||u||); the
+ * factor is clipped to [0.2, 2].  Rejections, and non-finite proposals, fall
+ * back to lx_controller_classical.  The embedded error test (err <= tol)
+ * still accepts or rejects every step.  dt_ref > 0 is the explicit CFL step
+ * used in the features. */
+lx_status lx_integrate_learned(lx_ctx* ctx, double* u_dev, const double* v0_dev, double t_final, double tol,
+                               double leja_tol, int max_attempts, lx_mlp* model, double dt_ref,
+                               lx_integrate_info* info);
+
 /* Timing of the Leja loops run by this context since the last reset: the
  * summed CUDA-event time of the loop graphs (milliseconds, measured on the
  * context stream) and the number of Leja iterations they ran.  The average
@@ -284,8 +298,6 @@ void batch_destroy(lx_batch* b);
  * input i to output j).  Normalisation vector (14 floats): mean_x[5],
  * std_x[5], mean_y[2], std_y[2]; the network works on normalised values.
  * ------------------------------------------------------------------------- */
-
-typedef struct lx_mlp lx_mlp;
 
 int mlp_param_count(void);
 

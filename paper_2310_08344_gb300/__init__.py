@@ -39,6 +39,7 @@ from .binding import (  # noqa: F401
     lx_leja_coeff_count,
     lx_leja_coeffs,
     lx_integrate,
+    lx_integrate_learned,
     lx_leja_points,
     lx_status_str,
     mlp_forward,

@@ -96,6 +96,8 @@ def lib():
             L.mlp_train_step.argtypes = [_vp, _vp, _vp, C.c_int, C.c_int, C.c_float, _fp, _fp]
             L.mlp_destroy.argtypes = [_vp]
             L.mlp_destroy.restype = None
+            L.lx_integrate_learned.argtypes = [_vp, _vp, _vp, C.c_double, C.c_double, C.c_double, C.c_int, _vp,
+                                               C.c_double, C.POINTER(LxIntegrateInfo)]
             L.lx_ctx_autotune.argtypes = [_vp, C.c_int, C.c_char_p, C.c_char_p, C.c_int]
             L.lx_ctx_select_kernel.argtypes = [_vp, C.c_char_p, C.c_int]
             L.phi_l_apply_noalloc.argtypes = [C.POINTER(LxProblem), C.c_int, _vp, _vp, C.c_double, C.c_double,
@@ -426,3 +428,13 @@ def mlp_train_step(m: Mlp, x, t, B, adam=True, lr=1e-3, want_grad=False):
     st = lib().mlp_train_step(m.handle, _dev(x), _dev(t), B, 1 if adam else 0, lr,
                               g.ctypes.data_as(fp) if g is not None else None, C.byref(loss))
     return st, float(loss.value), g
+
+
+def lx_integrate_learned(ctx: Context, u, v0, t_final, tol, leja_tol, model: "Mlp", dt_ref, max_attempts=100000,
+                         t0=0.0, h0=None, power_iters=10):
+    """Adaptive EXPRB32 run with the learned controller.  Returns (status, info dict)."""
+    info = LxIntegrateInfo(t0, h0, 0, 0, 0, 0.0, power_iters)
+    st = lib().lx_integrate_learned(ctx.handle, _dev(u), _dev(v0), t_final, tol, leja_tol, max_attempts,
+                                    model.handle, dt_ref, C.byref(info))
+    return st, {"t": info.t, "h": info.h, "steps": info.steps, "rejected": info.rejected,
+                "leja_iters": info.leja_iters, "last_err": info.last_err}

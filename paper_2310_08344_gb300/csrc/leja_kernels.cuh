@@ -69,6 +69,7 @@ struct LoopState {
   double sigma;              // power iteration: 1/||v_k||
   double rho, rho_prev;      // power iteration estimates
   double red;                // result of a reduction kernel (e.g. the step error)
+  double red2;               // ||u|| from vec_norm_kernel
   int pmax;                  // power iteration: pass limit
   int wexp;                  // df64 form: largest biased exponent of |w|
   int kscale;                // df64 form: w is scaled by 2^-kscale
@@ -433,6 +434,17 @@ static __global__ void __launch_bounds__(kThreadsPerBlock)
   }
   if (!last_block_total2(s, dummy, partials, ticket)) return;
   if (threadIdx.x == 0) st->red = sqrt(s / double(n));
+}
+
+// ||v|| = sqrt(sum v^2 / n) into st->red2 (last-block reduction).
+static __global__ void __launch_bounds__(kThreadsPerBlock)
+    vec_norm_kernel(long long n, const double* __restrict__ v, double* __restrict__ partials,
+                    unsigned int* __restrict__ ticket, LoopState* st) {
+  double s = 0.0, dummy = 0.0;
+  for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < n; q += (long long)gridDim.x * blockDim.x)
+    s = fma(v[q], v[q], s);
+  if (!last_block_total2(s, dummy, partials, ticket)) return;
+  if (threadIdx.x == 0) st->red2 = sqrt(s / double(n));
 }
 
 // sigma = 1/||v0|| and reset of the power-iteration state.

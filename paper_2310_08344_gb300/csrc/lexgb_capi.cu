@@ -880,17 +880,22 @@ double lx_controller_classical(double h, double err, double tol) {
   return h * f;
 }
 
-lx_status lx_integrate(lx_ctx* c, double* u, const double* v0, double t_final, double tol, double leja_tol,
-                       int max_attempts, lx_integrate_info* info) {
+lx_status mlp_forward_host(lx_mlp* m, const float* x_host, float* y_host, int B);
+
+// Adaptive EXPRB32 loop shared by the classical and the learned controller.
+static lx_status integrate_impl(lx_ctx* c, double* u, const double* v0, double t_final, double tol,
+                                double leja_tol, int max_attempts, lx_integrate_info* info, lx_mlp* model,
+                                double dt_ref) {
   if (!c || !u || !v0 || !info || !(tol > 0.0) || !(leja_tol > 0.0) || max_attempts < 1 || !(info->h > 0.0))
     return LX_E_INVAL;
   if (c->integrator != LX_EXPRB32) return LX_E_INVAL;
+  if (model && !(dt_ref > 0.0)) return LX_E_INVAL;
   const size_t nb = sizeof(double) * (size_t)c->n;
   for (int k = 1; k < 3; ++k)
     if (!c->d_io[k] && !cuda_ok(cudaMalloc((void**)&c->d_io[k], nb), "cudaMalloc")) return LX_E_NOMEM;
   const int passes = info->power_iters > 0 ? info->power_iters : 10;
   double t = info->t, h = info->h;
-  int steps = 0, rejected = 0;
+  int steps = 0, rejected = 0, learned = 0;
   long long iters = 0;
   lx_status status = LX_OK;
   for (int att = 0; att < max_attempts && t < t_final; ++att) {
@@ -911,14 +916,37 @@ lx_status lx_integrate(lx_ctx* c, double* u, const double* v0, double t_final, d
       break;
     }
     info->last_err = err;
-    if (err <= tol) {
+    const bool accept = err <= tol;
+    double h_next = lx_controller_classical(hh, err, tol);
+    if (model && accept) {
+      // features of this attempt -> proposed log(h_next / h)
+      vec_norm_kernel<<<aux_blocks(c), kThreadsPerBlock, 0, c->stream>>>(c->n, u, c->d_partials, c->d_ticket,
+                                                                         c->d_state);
+      LX_CUDA(cudaGetLastError());
+      LX_CUDA(cudaMemcpyAsync(c->h_state, c->d_state, sizeof(LoopState), cudaMemcpyDeviceToHost, c->stream));
+      LX_CUDA(cudaStreamSynchronize(c->stream));
+      const float x[5] = {(float)std::log(rho * hh), (float)std::log(hh / dt_ref), (float)(it / 100.0),
+                          (float)std::log10(std::max(err, 1e-300) / tol), (float)c->h_state->red2};
+      float y[2] = {0.f, 0.f};
+      st = mlp_forward_host(model, x, y, 1);
+      if (st != LX_OK) {
+        status = st;
+        break;
+      }
+      if (std::isfinite(y[0])) {
+        const double f = std::exp(std::min(std::log(2.0), std::max(std::log(0.2), (double)y[0])));
+        h_next = hh * f;
+        ++learned;
+      }
+    }
+    if (accept) {
       LX_CUDA(cudaMemcpyAsync(u, c->d_io[2], nb, cudaMemcpyDeviceToDevice, c->stream));
       t += hh;
       ++steps;
     } else {
       ++rejected;
     }
-    h = lx_controller_classical(hh, err, tol);
+    h = h_next;
   }
   LX_CUDA(cudaStreamSynchronize(c->stream));
   info->t = t;
@@ -927,6 +955,18 @@ lx_status lx_integrate(lx_ctx* c, double* u, const double* v0, double t_final, d
   info->rejected = rejected;
   info->leja_iters = iters;
   return status;
+}
+
+lx_status lx_integrate(lx_ctx* c, double* u, const double* v0, double t_final, double tol, double leja_tol,
+                       int max_attempts, lx_integrate_info* info) {
+  return integrate_impl(c, u, v0, t_final, tol, leja_tol, max_attempts, info, nullptr, 0.0);
+}
+
+lx_status lx_integrate_learned(lx_ctx* c, double* u, const double* v0, double t_final, double tol,
+                               double leja_tol, int max_attempts, lx_mlp* model, double dt_ref,
+                               lx_integrate_info* info) {
+  if (!model) return LX_E_INVAL;
+  return integrate_impl(c, u, v0, t_final, tol, leja_tol, max_attempts, info, model, dt_ref);
 }
 
 }  // extern "C"

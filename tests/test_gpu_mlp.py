@@ -37,10 +37,12 @@ def test_forward_matches_oracle(lx, B):
     X, T, norm, p = _problem(B, 5)
     m = lx.mlp_setup(1024, p, norm)
     xd = torch.from_numpy(X).cuda()
-    yd = torch.empty((B, 2), dtype=torch.float32, device="cuda")
+    yd = torch.full((B, 2), 12345.0, dtype=torch.float32, device="cuda")
     assert lx.mlp_forward(m, xd, yd, B) == 0
     ref = omlp.predict(p.astype(np.float64), norm.astype(np.float64), X.astype(np.float64), emulate=True)
     got = yd.cpu().numpy()
+    bad = np.where(~np.isfinite(got).all(axis=1) | (got == 12345.0).any(axis=1))[0]
+    assert bad.size == 0, ("rows not written or not finite", bad[:20], got[bad[:4]])
     scale = np.abs(ref).max(axis=0) + 1e-3
     assert np.max(np.abs(got - ref) / scale) <= 1e-2
     assert np.max(np.abs(got - ref)) <= 1e-3 * np.abs(ref).max() + 5e-3
