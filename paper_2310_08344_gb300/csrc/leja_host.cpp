@@ -183,7 +183,7 @@ int leja_coeffs_ws(int l, double h, double c, double gamma, const double* xi, in
     diag[i] -= mu;
     norm1 = std::max(norm1, std::fabs(diag[i]) + (i + 1 < n ? std::fabs(sub[i + 1]) : 0.0));
   }
-  const double theta = 0.5;
+  const double theta = 2.0;  // sub-step norm: ~22 Taylor terms reach 1e-18
   int s = std::max(1, (int)std::ceil(norm1 / theta));
   const double inv_s = 1.0 / s;
   // e^{mu} is applied a 1/s slice per sub-step, so v stays at the size of

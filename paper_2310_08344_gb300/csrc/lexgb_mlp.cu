@@ -167,6 +167,7 @@ __device__ void load_weights(MlpSmem& S, const __nv_bfloat16* __restrict__ wb, c
   }
   if (t < 8) S.b4[t] = t < kOut ? wf[kOffB4 + t] : 0.f;
   if (t < 2 * kIn + 2 * kOut) S.norm[t] = norm[t];
+  __syncthreads();  // the normalisation and weights are read by every thread next
 }
 
 // Forward pass of the CTA's 128 rows: X (normalised, bf16) -> H1 -> H2 -> H3
