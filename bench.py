@@ -460,7 +460,7 @@ def main():
                 "frac": achieved / peaks["hbm_gbs"], "traffic": traffic,
                 "kernel": kname, "alg_bytes_per_launch": alg_bytes, "avg_launch_us": avg_launch_s * 1e6,
                 "peak_source": f"{peak_src} (MEASURED_PEAKS.json hbm_gbs, burst copy)"}
-    launches = args.steps * 4 + int(stats["loop_iterations"])
+    launches = int(stats["kernels"])  # counted by the library on the context stream
 
     # end to end through the host-buffer entry point
     e2e = None

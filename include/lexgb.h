@@ -220,10 +220,11 @@ lx_status lx_integrate_learned(lx_ctx* ctx, double* u_dev, const double* v0_dev,
  * context stream) and the number of Leja iterations they ran.  The average
  * duration of one fused Leja-iteration launch is loop_ms / iterations. */
 typedef struct {
-  double loop_ms;
-  long long loop_iterations;
-  long long loop_launches;
-  double power_ms;
+  double loop_ms;             /* CUDA-event time of the Leja loops */
+  long long loop_iterations;  /* fused-iteration launches that did work */
+  long long loop_launches;    /* Leja loops run */
+  double power_ms;            /* CUDA-event time of power_bound calls */
+  long long kernels;          /* kernel launches of this library on the context's stream */
 } lx_stats;
 lx_status lx_ctx_stats(lx_ctx* ctx, lx_stats* out, int reset);
 

@@ -28,7 +28,7 @@ class LxProblem(C.Structure):
 
 class LxStats(C.Structure):
     _fields_ = [("loop_ms", C.c_double), ("loop_iterations", C.c_longlong), ("loop_launches", C.c_longlong),
-                ("power_ms", C.c_double)]
+                ("power_ms", C.c_double), ("kernels", C.c_longlong)]
 
 
 class LxIntegrateInfo(C.Structure):
@@ -256,7 +256,7 @@ def lx_ctx_stats(ctx: Context, reset=False) -> dict:
     if st != OK:
         raise LexgbError(st, "lx_ctx_stats")
     return {"loop_ms": s.loop_ms, "loop_iterations": s.loop_iterations, "loop_launches": s.loop_launches,
-            "power_ms": s.power_ms}
+            "power_ms": s.power_ms, "kernels": s.kernels}
 
 
 def lx_ctx_kernel_name(ctx: Context) -> str:

@@ -109,6 +109,7 @@ struct lx_ctx {
   double* d_partials = nullptr;
   int partials_cap = 0;
   int stream_loop = 0;  // 1: launch the iterations from the host (profilers)
+  int graph_iter_launches_pending = 0;  // a graph loop ran since the last end_call
   unsigned int* d_ticket = nullptr;
   LoopState* d_state = nullptr;
   LoopArgs* d_args = nullptr;
@@ -339,19 +340,23 @@ lx_status launch_loop(lx_ctx* c, int slot, int l, const double* u, const double*
   a.use_cond = c->stream_loop ? 0 : 1;
   const bool df = P.precision == LX_DF64;
   set_loop_args_kernel<<<1, 1, 0, c->stream>>>(a, c->d_args, c->d_state, c->d_ticket, wexp_known ? 0 : 1);
+  ++c->stats.kernels;
   LX_CUDA(cudaGetLastError());
   if (df) {
     if (!wexp_known) {
       df_scale_kernel<<<aux_blocks(c), kThreadsPerBlock, 0, c->stream>>>(c->n, w, c->d_state);
+      ++c->stats.kernels;
       LX_CUDA(cudaGetLastError());
     }
     df_scale_finish_kernel<<<1, 1, 0, c->stream>>>(c->d_state);
+    ++c->stats.kernels;
     LX_CUDA(cudaGetLastError());
   }
   if (c->ev_used + 2 > 8) return LX_E_INVAL;
   LX_CUDA(cudaEventRecord(c->ev[c->ev_used], c->stream));
   if (!c->stream_loop) {
     LX_CUDA(cudaGraphLaunch(c->loop[variant].exec, c->stream));
+    c->graph_iter_launches_pending = 1;
   } else {
     // Host-driven loop for profilers that cannot see kernels inside a
     // conditional graph: batches of launches, each kernel returning at once
@@ -366,6 +371,7 @@ lx_status launch_loop(lx_ctx* c, int slot, int l, const double* u, const double*
     for (int it = 0; it < a.kmax; it += 8) {
       for (int k = 0; k < 8; ++k)
         LX_CUDA(cudaLaunchKernel(L.cand.func, dim3(L.grid), dim3(L.cand.threads), kargs, L.cand.smem, c->stream));
+      c->stats.kernels += 8;
       LX_CUDA(cudaMemcpyAsync(c->h_state, c->d_state, sizeof(LoopState), cudaMemcpyDeviceToHost, c->stream));
       LX_CUDA(cudaStreamSynchronize(c->stream));
       if (c->h_state->done) break;
@@ -375,6 +381,7 @@ lx_status launch_loop(lx_ctx* c, int slot, int l, const double* u, const double*
   c->ev_used += 2;
   if (df) {
     df_output_kernel<<<aux_blocks(c), kThreadsPerBlock, 0, c->stream>>>(c->n, c->d_pdf, base, out, c->d_state);
+    ++c->stats.kernels;
     LX_CUDA(cudaGetLastError());
   }
   return LX_OK;
@@ -383,6 +390,7 @@ lx_status launch_loop(lx_ctx* c, int slot, int l, const double* u, const double*
 lx_status begin_call(lx_ctx* c) {
   c->ev_used = 0;
   reset_call_kernel<<<1, 1, 0, c->stream>>>(c->d_state, c->d_ticket);
+  ++c->stats.kernels;
   LX_CUDA(cudaGetLastError());
   return LX_OK;
 }
@@ -398,6 +406,8 @@ lx_status end_call(lx_ctx* c) {
     c->stats.loop_launches += 1;
   }
   c->stats.loop_iterations += c->h_state->iters_total;
+  c->stats.kernels += c->graph_iter_launches_pending ? c->h_state->iters_total : 0;
+  c->graph_iter_launches_pending = 0;
   c->ev_used = 0;
   return LX_OK;
 }
@@ -544,10 +554,12 @@ lx_status power_bound(lx_ctx* c, const double* u, const double* v0, int max_iter
   LX_CUDA(cudaEventRecord(c->ev_pow[0], c->stream));
   if (P.kind == LX_BURGERS) {
     rhs_kernel<1><<<G, kThreadsPerBlock, 0, c->stream>>>(c->geo, P.nu, 0.0, 0.0, u, nullptr, c->d_s);
+    ++c->stats.kernels;
     LX_CUDA(cudaGetLastError());
   }
   power_start_kernel<<<G, kThreadsPerBlock, 0, c->stream>>>(c->n, v0, max_iters, c->d_partials, c->d_ticket,
                                                              c->d_state);
+  ++c->stats.kernels;
   LX_CUDA(cudaGetLastError());
   for (int k = 1; k <= max_iters; ++k) {
     const double* in = (k == 1) ? v0 : c->d_pw[(k - 2) & 1];
@@ -558,6 +570,7 @@ lx_status power_bound(lx_ctx* c, const double* u, const double* v0, int max_iter
     else
       power_pass_kernel<1><<<G, kThreadsPerBlock, 0, c->stream>>>(c->geo, P.nu, 0.0, u, c->d_s, in, outv,
                                                                   c->d_partials, c->d_ticket, c->d_state);
+    ++c->stats.kernels;
     LX_CUDA(cudaGetLastError());
   }
   LX_CUDA(cudaEventRecord(c->ev_pow[1], c->stream));
@@ -583,6 +596,7 @@ lx_status phi_l_apply(lx_ctx* c, int l, const double* u, const double* w, double
     if (!u) return LX_E_INVAL;
     rhs_kernel<1><<<aux_blocks(c), kThreadsPerBlock, 0, c->stream>>>(c->geo, c->prob.nu, 0.0, 0.0, u, nullptr,
                                                                        c->d_s);
+    ++c->stats.kernels;
     LX_CUDA(cudaGetLastError());
   }
   st = launch_loop(c, 0, l, u, w, out, cc, gamma, h, rtol, atol);
@@ -622,6 +636,7 @@ lx_status expint_step(lx_ctx* c, const double* u, double* u_low, double* u_high,
       W.wf[2 * k + 1] = (float)(W.wd[k] - (double)W.wf[2 * k]);
     }
     rhs_df_advdiff_kernel<<<G, kThreadsPerBlock, 0, c->stream>>>(c->geo, u, W, c->d_f, c->d_state);
+    ++c->stats.kernels;
     LX_CUDA(cudaGetLastError());
     st = launch_loop(c, 0, 1, u, c->d_f, u_high, cc, gamma, h, rtol, atol, u, true);
     if (st != LX_OK) return st;
@@ -636,12 +651,14 @@ lx_status expint_step(lx_ctx* c, const double* u, double* u_low, double* u_high,
     rhs_kernel<0><<<G, kThreadsPerBlock, 0, c->stream>>>(c->geo, P.nu, P.a, h, u, c->d_f, c->d_s);
   else
     rhs_kernel<1><<<G, kThreadsPerBlock, 0, c->stream>>>(c->geo, P.nu, 0.0, h, u, c->d_f, c->d_s);
+  ++c->stats.kernels;
   LX_CUDA(cudaGetLastError());
   if (c->integrator == LX_ROS_EU) {
     // p = phi_1(h J) h f(u) into u_high, then u_high = u + p
     st = launch_loop(c, 0, 1, u, c->d_f, u_high, cc, gamma, h, rtol, atol);
     if (st != LX_OK) return st;
     add_kernel<<<G, kThreadsPerBlock, 0, c->stream>>>(c->n, u, u_high);
+    ++c->stats.kernels;
     LX_CUDA(cudaGetLastError());
     st = end_call(c);
     if (st != LX_OK) return st;
@@ -655,8 +672,10 @@ lx_status expint_step(lx_ctx* c, const double* u, double* u_low, double* u_high,
       exprb32_stage_kernel<0><<<G, kThreadsPerBlock, 0, c->stream>>>(c->geo, h, u, u_low, c->d_f);
     else
       exprb32_stage_kernel<1><<<G, kThreadsPerBlock, 0, c->stream>>>(c->geo, h, u, u_low, c->d_f);
+    ++c->stats.kernels;
     LX_CUDA(cudaGetLastError());
     exprb32_a_kernel<<<G, kThreadsPerBlock, 0, c->stream>>>(c->n, u, u_low);
+    ++c->stats.kernels;
     LX_CUDA(cudaGetLastError());
     // p3 = phi_3(h J) R
     st = launch_loop(c, 1, 3, u, c->d_f, c->d_p3, cc, gamma, h, rtol, atol);
@@ -664,6 +683,7 @@ lx_status expint_step(lx_ctx* c, const double* u, double* u_low, double* u_high,
     // u_high = a + 2 p3, err = ||2 p3||
     exprb32_final_kernel<<<G, kThreadsPerBlock, 0, c->stream>>>(c->n, u_low, c->d_p3, u_high, c->d_partials,
                                                                  c->d_ticket, c->d_state);
+    ++c->stats.kernels;
     LX_CUDA(cudaGetLastError());
     st = end_call(c);
     if (st != LX_OK) return st;
@@ -757,6 +777,7 @@ lx_status tune_time(lx_ctx* c, const Cand& k, int H, int iters, double* us) {
   a.atol = -1.0;  // never converged: every launch does the full work
   a.use_cond = 0;
   set_loop_args_kernel<<<1, 1, 0, c->stream>>>(a, c->d_args, c->d_state, c->d_ticket);
+  ++c->stats.kernels;
   LX_CUDA(cudaGetLastError());
   const LoopArgs* args = c->d_args;
   LoopState* stp = c->d_state;
@@ -922,6 +943,7 @@ static lx_status integrate_impl(lx_ctx* c, double* u, const double* v0, double t
       // features of this attempt -> proposed log(h_next / h)
       vec_norm_kernel<<<aux_blocks(c), kThreadsPerBlock, 0, c->stream>>>(c->n, u, c->d_partials, c->d_ticket,
                                                                          c->d_state);
+      ++c->stats.kernels;
       LX_CUDA(cudaGetLastError());
       LX_CUDA(cudaMemcpyAsync(c->h_state, c->d_state, sizeof(LoopState), cudaMemcpyDeviceToHost, c->stream));
       LX_CUDA(cudaStreamSynchronize(c->stream));
