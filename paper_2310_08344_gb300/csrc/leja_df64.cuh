@@ -629,3 +629,258 @@ __global__ void __launch_bounds__(kPipeThreads, MINB)
 }
 
 }  // namespace lexgb
+
+namespace lexgb {
+
+// ---------------------------------------------------------------------------
+// df64 Burgers: the Jacobian J(u) has point-wise weights
+//   wE = lx - q, wW = lx + q, wN = ly - q dx/dy, wS = ly + q dx/dy, wC = r - xi_m
+// with the per-point float pairs q and r prepared once per Leja loop.
+// ---------------------------------------------------------------------------
+
+constexpr int kSlotElemsB = kYSlot + 3 * kPipeRow;  // y (+halo), p, q, r
+constexpr int kPipeSmemBytesB = kPipeWarps * kPipeStages * kSlotElemsB * 8;
+
+__device__ __forceinline__ dfv df_add(dfv a, dfv b) {
+  float s, e;
+  two_sum(a.h, b.h, s, e);
+  e = __fadd_rn(e, __fadd_rn(a.l, b.l));
+  dfv r;
+  fast_two_sum(s, e, r.h, r.l);
+  return r;
+}
+
+__device__ __forceinline__ dfv df_neg(dfv a) { return {-a.h, -a.l}; }
+
+// q = u gx and r = wc0 - s ig as float pairs (gx = 1/(2 dx gamma), ig = 1/gamma).
+static __global__ void burgers_df_prep_kernel(long long n, const double* __restrict__ u, const double* __restrict__ s,
+                                              double gx, double ig, double wc0, float2* __restrict__ q,
+                                              float2* __restrict__ r) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    const dfv a = df_split_scaled(u[i] * gx, 0);
+    const dfv b = df_split_scaled(fma(-s[i], ig, wc0), 0);
+    q[i] = make_float2(a.h, a.l);
+    r[i] = make_float2(b.h, b.l);
+  }
+}
+
+template <typename S, bool FIRST>
+__device__ __forceinline__ void df_strip_pipe_burgers(const LoopArgs& A, const S* __restrict__ src,
+                                                      float2* __restrict__ dst, float2* __restrict__ p,
+                                                      unsigned long long* ring, int col0, int r0, int r1, dfv xim,
+                                                      float swf, dfv d0, dfv dm1, int sc, dfv& accy, dfv& accp) {
+  const int lane = threadIdx.x & 31;
+  const int nx = A.nx, ny = A.ny;
+  const int c = col0 + lane * 4;
+  const int cw = col0 == 0 ? nx - 1 : col0 - 1;
+  const int ce = (col0 + kPipeRow >= nx) ? 0 : col0 + kPipeRow;
+  const int nrows = r1 - r0;
+  const int last_q = nrows + 1;
+  const dfv lx = {A.bl[0], A.bl[1]}, ly = {A.bl[2], A.bl[3]}, rat = {A.bl[4], A.bl[5]};
+  const bool square = A.bl[4] == 1.0f && A.bl[5] == 0.0f;
+  auto slot = [&](int q) { return ring + (size_t)(q % kPipeStages) * kSlotElemsB; };
+  auto issue = [&](int q) {
+    if (q <= last_q) {
+      int ry = r0 - 1 + q;
+      ry = ry < 0 ? ry + ny : (ry >= ny ? ry - ny : ry);
+      unsigned long long* s = slot(q);
+      const S* row = src + (size_t)ry * nx;
+      cp_async16(s + 2 + lane * 4, row + c);
+      cp_async16(s + 4 + lane * 4, row + c + 2);
+      if (lane == 0) cp_async8(s + 1, row + cw);
+      if (lane == 31) cp_async8(s + 2 + kPipeRow, row + ce);
+      if (q >= 1 && q <= nrows) {
+        const size_t ro = (size_t)(r0 - 1 + q) * nx;
+        if constexpr (!FIRST) {
+          cp_async16(s + kYSlot + lane * 4, p + ro + c);
+          cp_async16(s + kYSlot + lane * 4 + 2, p + ro + c + 2);
+        }
+        cp_async16(s + kYSlot + kPipeRow + lane * 4, A.bq + ro + c);
+        cp_async16(s + kYSlot + kPipeRow + lane * 4 + 2, A.bq + ro + c + 2);
+        cp_async16(s + kYSlot + 2 * kPipeRow + lane * 4, A.br + ro + c);
+        cp_async16(s + kYSlot + 2 * kPipeRow + lane * 4 + 2, A.br + ro + c + 2);
+      }
+    }
+    cp_commit();
+  };
+  for (int q = 0; q < kPipeStages - 1; ++q) issue(q);
+  cp_wait<kPipeStages - 3>();
+  __syncwarp();
+  dfv ys[4], yc[4], yn[4];
+  df_from_raw4<S>(slot(0) + 2 + lane * 4, sc, ys);
+  df_from_raw4<S>(slot(1) + 2 + lane * 4, sc, yc);
+  for (int qc = 1; qc <= nrows; ++qc) {
+    issue(qc + kPipeStages - 2);
+    cp_wait<kPipeStages - 3>();
+    __syncwarp();
+    const unsigned long long* sn = slot(qc + 1);
+    const unsigned long long* scn = slot(qc);
+    df_from_raw4<S>(sn + 2 + lane * 4, sc, yn);
+    dfv pold[4], qv[4], rv[4];
+    if constexpr (!FIRST) df_from_raw4<float2>(scn + kYSlot + lane * 4, sc, pold);
+    df_from_raw4<float2>(scn + kYSlot + kPipeRow + lane * 4, sc, qv);
+    df_from_raw4<float2>(scn + kYSlot + 2 * kPipeRow + lane * 4, sc, rv);
+    dfv xw = shfl_up_df(yc[3]);
+    dfv xe = shfl_down_df(yc[0]);
+    if (lane == 0) xw = df_from_raw<S>(scn + 1, sc);
+    if (lane == 31) xe = df_from_raw<S>(scn + 2 + kPipeRow, sc);
+    dfv ynew[4], pnew[4];
+    float fy = 0.f, fp = 0.f;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      const dfv qy = square ? qv[k] : df_mul(qv[k], rat);
+      const dfv wE = df_add(lx, df_neg(qv[k])), wW = df_add(lx, qv[k]);
+      const dfv wN = df_add(ly, df_neg(qy)), wS = df_add(ly, qy);
+      const dfv wC = df_add(rv[k], xim);
+      const float wh[5] = {wE.h, wW.h, wN.h, wS.h, wC.h};
+      const float wl[5] = {wE.l, wW.l, wN.l, wS.l, wC.l};
+      const dfv t[5] = {k == 3 ? xe : yc[k + 1], k == 0 ? xw : yc[k - 1], yn[k], ys[k], yc[k]};
+      dfv v = df_dot5(wh, wl, t);
+      v.h *= swf;
+      v.l *= swf;
+      ynew[k] = v;
+      const dfv po = FIRST ? df_mul(d0, yc[k]) : pold[k];
+      pnew[k] = df_axpy(dm1, ynew[k], po);
+      fy = __fmaf_rn(ynew[k].h, ynew[k].h, fy);
+      fp = __fmaf_rn(pnew[k].h, pnew[k].h, fp);
+    }
+    df_acc(accy, fy);
+    df_acc(accp, fp);
+    const size_t ro = (size_t)(r0 - 1 + qc) * nx;
+    df_store_row<4>(dst + ro, c, nx, ynew);
+    df_store_row<4>(p + ro, c, nx, pnew);
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      ys[k] = yc[k];
+      yc[k] = yn[k];
+    }
+    __syncwarp();
+  }
+  cp_wait<0>();
+  __syncwarp();
+}
+
+template <int MINB>
+__global__ void __launch_bounds__(kPipeThreads, MINB)
+    leja_iter_df_pipe_burgers_kernel(const LoopArgs* __restrict__ Ap, LoopState* __restrict__ st,
+                                     double* __restrict__ partials, unsigned int* __restrict__ ticket,
+                                     cudaGraphConditionalHandle cond) {
+  extern __shared__ __align__(16) unsigned long long pipe_smem_b[];
+  const LoopArgs& A = *Ap;
+  const int m = __ldcg(&st->m);
+  if (__ldcg(&st->done)) return;
+  const int kexp = __ldcg(&st->kscale);
+  const int sig = __ldcg(&st->sig);
+  const int dlt = __ldcg(&st->dlt);
+  const int nx = A.nx, ny = A.ny;
+  const int H = A.strip_h;
+  const int ncs = nx / kPipeRow;
+  const int nstrips = ncs * ((ny + H - 1) / H);
+  const double xim_d = __ldg(A.xi + m);
+  const double dm1d = __ldg(A.d + m + 1);
+  const dfv dm1 = df_from_double(dm1d * pow2(sig + dlt - kexp));
+  const dfv d0 = df_from_double(__ldg(A.d));
+  const dfv xim = df_from_double(-xim_d);
+  const float swf = (float)pow2(-dlt);
+  float2* dst = reinterpret_cast<float2*>((m & 1) ? A.y1 : A.y0);
+  dfv accy = {0.f, 0.f}, accp = {0.f, 0.f};
+  const int warp = threadIdx.x >> 5;
+  unsigned long long* ring = pipe_smem_b + (size_t)warp * kPipeStages * kSlotElemsB;
+  for (int s = blockIdx.x * kPipeWarps + warp; s < nstrips; s += gridDim.x * kPipeWarps) {
+    const int col0 = (s % ncs) * kPipeRow;
+    const int r0 = (s / ncs) * H;
+    const int r1 = min(r0 + H, ny);
+    if (m == 0) {
+      df_strip_pipe_burgers<double, true>(A, A.w, dst, A.pdf, ring, col0, r0, r1, xim, swf, d0, dm1, kexp, accy,
+                                          accp);
+    } else {
+      const float2* src = reinterpret_cast<const float2*>(((m - 1) & 1) ? A.y1 : A.y0);
+      df_strip_pipe_burgers<float2, false>(A, src, dst, A.pdf, ring, col0, r0, r1, xim, swf, d0, dm1, kexp, accy,
+                                           accp);
+    }
+  }
+  double sy = df_to_double(accy), sp = df_to_double(accp);
+  if (!last_block_total2(sy, sp, partials, ticket)) return;
+  if (threadIdx.x == 0) {
+    leja_finalize(A, st, m, dm1d, sy, sp, pow2(sig + dlt), pow2(kexp), cond);
+    const double rms = sqrt(sy / double(A.n));
+    int e = 0;
+    if (rms > 0.0 && isfinite(rms)) e = ilogb(rms);
+    st->sig = sig + dlt;
+    st->dlt = max(-100, min(100, e));
+  }
+}
+
+// ---------------------------------------------------------------------------
+// df64 power-iteration pass: w = Op(v) / ||v|| with Op = A (KIND 0, constant
+// weights W) or J(u) (KIND 1, point-wise weights from q = u/(2dx),
+// r = -2nu/dx^2 - 2nu/dy^2 - (u_x+u_y)); v is the caller's double start
+// vector on the first pass (vin_double = 1), float pairs afterwards.
+// ---------------------------------------------------------------------------
+struct PowWeights {
+  float w[10];   // KIND 0: hi/lo of wE, wW, wN, wS, wC
+  float bl[6];   // KIND 1: hi/lo of lx = nu/dx^2, ly = nu/dy^2, dx/dy
+};
+
+template <int KIND>
+static __global__ void __launch_bounds__(kThreadsPerBlock)
+    power_pass_df_kernel(Geo g, const void* __restrict__ vin, int vin_double, float2* __restrict__ w,
+                         const float2* __restrict__ q, const float2* __restrict__ r, PowWeights W,
+                         double* __restrict__ partials, unsigned int* __restrict__ ticket, LoopState* st) {
+  if (__ldcg(&st->pdone)) return;
+  const dfv sg = df_from_double(__ldcg(&st->sigma));
+  dfv acc = {0.f, 0.f};
+  const double* vd = reinterpret_cast<const double*>(vin);
+  const float2* vf = reinterpret_cast<const float2*>(vin);
+  auto ld = [&](long long i) -> dfv {
+    if (vin_double) return df_split_scaled(__ldg(vd + i), 0);
+    const float2 t = __ldg(vf + i);
+    return {t.x, t.y};
+  };
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < g.n; i += (long long)gridDim.x * blockDim.x) {
+    long long e, ww, nn, ss;
+    neighbours(g, i, e, ww, nn, ss);
+    const dfv t[5] = {ld(e), ld(ww), ld(nn), ld(ss), ld(i)};
+    float wh[5], wl[5];
+    if (KIND == 0) {
+#pragma unroll
+      for (int k = 0; k < 5; ++k) {
+        wh[k] = W.w[2 * k];
+        wl[k] = W.w[2 * k + 1];
+      }
+    } else {
+      const float2 qq = __ldg(q + i), rr = __ldg(r + i);
+      const dfv qx = {qq.x, qq.y}, rv = {rr.x, rr.y};
+      const dfv lx = {W.bl[0], W.bl[1]}, ly = {W.bl[2], W.bl[3]}, rat = {W.bl[4], W.bl[5]};
+      const dfv qy = df_mul(qx, rat);
+      const dfv wE = df_add(lx, df_neg(qx)), wW = df_add(lx, qx), wN = df_add(ly, df_neg(qy)), wS = df_add(ly, qy);
+      wh[0] = wE.h; wl[0] = wE.l;
+      wh[1] = wW.h; wl[1] = wW.l;
+      wh[2] = wN.h; wl[2] = wN.l;
+      wh[3] = wS.h; wl[3] = wS.l;
+      wh[4] = rv.h; wl[4] = rv.l;
+    }
+    const dfv y = df_mul(sg, df_dot5(wh, wl, t));
+    w[i] = make_float2(y.h, y.l);
+    df_acc(acc, __fmul_rn(y.h, y.h));
+  }
+  double s = df_to_double(acc), dummy = 0.0;
+  if (!last_block_total2(s, dummy, partials, ticket)) return;
+  if (threadIdx.x == 0) {
+    const double rho = sqrt(s / double(g.n));
+    const int k = st->pk + 1;
+    st->pk = k;
+    st->rho = rho;
+    if (!isfinite(rho) || !(rho > 0.0)) {
+      st->pstatus = 5;
+      st->pdone = 1;
+    } else {
+      if ((k >= 2 && fabs(rho - st->rho_prev) <= 1e-2 * rho) || k >= st->pmax) st->pdone = 1;
+      st->rho_prev = rho;
+      st->sigma = 1.0 / rho;
+    }
+  }
+}
+
+}  // namespace lexgb
+

@@ -53,6 +53,12 @@ struct LoopArgs {
   float wf[8];        // df64 form: hi/lo float parts of wxp, wxm, wyp, wym
   float2* pdf;        // df64 form: the polynomial as float pairs
   int use_cond;       // 1: end the graph's while-loop from the device
+  // df64 Burgers form: per-point q = u / (2 dx gamma) and
+  // r = (-2 nu/dx^2 - 2 nu/dy^2 - c)/gamma - (u_x + u_y)/gamma as float pairs,
+  // and hi/lo of lx = nu/(dx^2 gamma), ly = nu/(dy^2 gamma), dx/dy
+  const float2* bq;
+  const float2* br;
+  float bl[6];
 };
 
 // Device-resident loop and reduction state.

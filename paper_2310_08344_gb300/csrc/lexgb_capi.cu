@@ -106,6 +106,8 @@ struct lx_ctx {
   double* d_io[3] = {nullptr, nullptr, nullptr};  // staging for expint_step_host
   float2* d_pdf = nullptr;  // df64 form: polynomial as float pairs
   double* d_tune = nullptr; // autotuner: output vector of the timing runs
+  float2* d_bq = nullptr;   // df64 Burgers: u / (2 dx gamma) per point
+  float2* d_br = nullptr;   // df64 Burgers: diagonal weight per point
   double* d_partials = nullptr;
   int partials_cap = 0;
   int stream_loop = 0;  // 1: launch the iterations from the host (profilers)
@@ -140,6 +142,15 @@ Cand iter_cand(const char* name) {
 std::vector<Cand> candidates(int kind, int precision, int cls) {
   const bool wide = cls == kVec2;
   std::vector<Cand> v;
+  if (precision == LX_DF64 && kind == LX_BURGERS) {
+    if (wide) {
+      v.push_back(Cand{reinterpret_cast<const void*>(&leja_iter_df_pipe_burgers_kernel<1>), kPipeThreads,
+                       kPipeSmemBytesB, 4, "leja_iter_df_pipe_burgers_b1"});
+      v.push_back(Cand{reinterpret_cast<const void*>(&leja_iter_df_pipe_burgers_kernel<2>), kPipeThreads,
+                       kPipeSmemBytesB, 4, "leja_iter_df_pipe_burgers_b2"});
+    }
+    return v;
+  }
   if (precision == LX_DF64) {
     if (wide) {
       v.push_back(Cand{reinterpret_cast<const void*>(&leja_iter_df_pipe_kernel<2>), kPipeThreads, kPipeSmemBytes, 4,
@@ -178,6 +189,9 @@ std::vector<Cand> candidates(int kind, int precision, int cls) {
 int wide_vec(const lx_ctx* c) { return candidates(c->prob.kind, c->prob.precision, kVec2)[0].vec; }
 
 int grid_for(const lx_ctx* c, const Cand& k, int strip_h, int* grid) {
+  if (k.smem > 48 * 1024 &&
+      !cuda_ok(cudaFuncSetAttribute(k.func, cudaFuncAttributeMaxDynamicSharedMemorySize, k.smem), "smem attribute"))
+    return LX_E_CUDA;
   const int ncs = (c->prob.nx + 32 * k.vec - 1) / (32 * k.vec);
   const int nrs = (c->prob.ny + strip_h - 1) / strip_h;
   const int wpb = k.threads / 32;
@@ -263,7 +277,13 @@ int choose_variant(const lx_ctx* c, const double* w, const double* out) {
 // Selected candidate of a class (built on first use with the default).
 lx_status ensure_graph(lx_ctx* c, int variant) {
   if (c->loop[variant].built) return LX_OK;
-  const Cand k = candidates(c->prob.kind, c->prob.precision, variant)[0];
+  const std::vector<Cand> cands = candidates(c->prob.kind, c->prob.precision, variant);
+  if (cands.empty()) {
+    set_last_error("no kernel for this layout: the float-float Burgers form needs nx % 128 == 0 and 16-byte "
+                   "aligned vectors");
+    return LX_E_INVAL;
+  }
+  const Cand k = cands[0];
   return build_loop_graph(c, variant, k, c->strip_h);
 }
 
@@ -339,6 +359,19 @@ lx_status launch_loop(lx_ctx* c, int slot, int l, const double* u, const double*
   a.pdf = c->d_pdf;
   a.use_cond = c->stream_loop ? 0 : 1;
   const bool df = P.precision == LX_DF64;
+  if (df && P.kind == LX_BURGERS) {
+    const double blv[3] = {nx2 * ig, ny2 * ig, dx / dy};
+    for (int k = 0; k < 3; ++k) {
+      a.bl[2 * k] = (float)blv[k];
+      a.bl[2 * k + 1] = (float)(blv[k] - (double)a.bl[2 * k]);
+    }
+    a.bq = c->d_bq;
+    a.br = c->d_br;
+    burgers_df_prep_kernel<<<aux_blocks(c), kThreadsPerBlock, 0, c->stream>>>(c->n, u, c->d_s, ig / (2 * dx), ig,
+                                                                               a.wc0, c->d_bq, c->d_br);
+    ++c->stats.kernels;
+    LX_CUDA(cudaGetLastError());
+  }
   set_loop_args_kernel<<<1, 1, 0, c->stream>>>(a, c->d_args, c->d_state, c->d_ticket, wexp_known ? 0 : 1);
   ++c->stats.kernels;
   LX_CUDA(cudaGetLastError());
@@ -418,7 +451,7 @@ bool valid_problem(const lx_problem* p) {
   if ((long long)p->nx * p->ny > (1LL << 31)) return false;
   if (p->kind != LX_ADVDIFF && p->kind != LX_BURGERS) return false;
   if (p->precision != LX_FP64 && p->precision != LX_MIXED && p->precision != LX_DF64) return false;
-  if (p->precision == LX_DF64 && p->kind != LX_ADVDIFF) return false;
+  if (p->precision == LX_DF64 && p->kind == LX_BURGERS && p->nx % 128 != 0) return false;
   if (!std::isfinite(p->nu) || !std::isfinite(p->a)) return false;
   return true;
 }
@@ -460,6 +493,8 @@ void leja_destroy(lx_ctx* c) {
   for (auto* p : c->d_io) cudaFree(p);
   cudaFree(c->d_pdf);
   cudaFree(c->d_tune);
+  cudaFree(c->d_bq);
+  cudaFree(c->d_br);
   cudaFree(c->d_partials);
   cudaFree(c->d_ticket);
   cudaFree(c->d_state);
@@ -508,6 +543,10 @@ lx_status leja_setup(const lx_problem* prob, int integrator, int max_leja, void*
   if (!dmalloc((void**)&c->d_f, nb) || !dmalloc((void**)&c->d_s, nb)) return fail(LX_E_NOMEM);
   if (integrator == LX_EXPRB32 && !dmalloc((void**)&c->d_p3, nb)) return fail(LX_E_NOMEM);
   if (prob->precision == LX_DF64 && !dmalloc((void**)&c->d_pdf, sizeof(float2) * (size_t)c->n))
+    return fail(LX_E_NOMEM);
+  if (prob->precision == LX_DF64 && prob->kind == LX_BURGERS &&
+      (!dmalloc((void**)&c->d_bq, sizeof(float2) * (size_t)c->n) ||
+       !dmalloc((void**)&c->d_br, sizeof(float2) * (size_t)c->n)))
     return fail(LX_E_NOMEM);
   {
     const char* env = std::getenv("LEXGB_STREAM_LOOP");
@@ -561,9 +600,49 @@ lx_status power_bound(lx_ctx* c, const double* u, const double* v0, int max_iter
                                                              c->d_state);
   ++c->stats.kernels;
   LX_CUDA(cudaGetLastError());
+  const bool dfp = P.precision == LX_DF64;
+  PowWeights PW;
+  std::memset(&PW, 0, sizeof(PW));
+  if (dfp) {
+    const double dx = 1.0 / P.nx, dy = 1.0 / P.ny;
+    const double nx2 = P.nu / (dx * dx), ny2 = P.nu / (dy * dy);
+    if (P.kind == LX_ADVDIFF) {
+      const double wd[5] = {nx2 + P.a / (2 * dx), nx2 - P.a / (2 * dx), ny2 + P.a / (2 * dy), ny2 - P.a / (2 * dy),
+                            -2.0 * nx2 - 2.0 * ny2};
+      for (int k = 0; k < 5; ++k) {
+        PW.w[2 * k] = (float)wd[k];
+        PW.w[2 * k + 1] = (float)(wd[k] - (double)PW.w[2 * k]);
+      }
+    } else {
+      const double blv[3] = {nx2, ny2, dx / dy};
+      for (int k = 0; k < 3; ++k) {
+        PW.bl[2 * k] = (float)blv[k];
+        PW.bl[2 * k + 1] = (float)(blv[k] - (double)PW.bl[2 * k]);
+      }
+      // q = u / (2 dx), r = -2 nu/dx^2 - 2 nu/dy^2 - (u_x + u_y)
+      burgers_df_prep_kernel<<<G, kThreadsPerBlock, 0, c->stream>>>(c->n, u, c->d_s, 1.0 / (2 * dx), 1.0,
+                                                                     -2.0 * nx2 - 2.0 * ny2, c->d_bq, c->d_br);
+      ++c->stats.kernels;
+      LX_CUDA(cudaGetLastError());
+    }
+  }
   for (int k = 1; k <= max_iters; ++k) {
     const double* in = (k == 1) ? v0 : c->d_pw[(k - 2) & 1];
     double* outv = c->d_pw[(k - 1) & 1];
+    if (dfp) {
+      float2* wf = reinterpret_cast<float2*>(outv);
+      if (P.kind == LX_ADVDIFF)
+        power_pass_df_kernel<0><<<G, kThreadsPerBlock, 0, c->stream>>>(c->geo, in, k == 1 ? 1 : 0, wf, nullptr,
+                                                                       nullptr, PW, c->d_partials, c->d_ticket,
+                                                                       c->d_state);
+      else
+        power_pass_df_kernel<1><<<G, kThreadsPerBlock, 0, c->stream>>>(c->geo, in, k == 1 ? 1 : 0, wf, c->d_bq,
+                                                                       c->d_br, PW, c->d_partials, c->d_ticket,
+                                                                       c->d_state);
+      ++c->stats.kernels;
+      LX_CUDA(cudaGetLastError());
+      continue;
+    }
     if (P.kind == LX_ADVDIFF)
       power_pass_kernel<0><<<G, kThreadsPerBlock, 0, c->stream>>>(c->geo, P.nu, P.a, nullptr, nullptr, in, outv,
                                                                   c->d_partials, c->d_ticket, c->d_state);

@@ -108,9 +108,9 @@ def test_phi_vec1_path_on_unaligned_views(lx, xi_oracle, prec):
     assert rel(outb[1:].cpu().numpy(), ref) <= TOL
 
 
-@pytest.mark.parametrize("nx,ny", [(64, 64), (96, 80), (70, 64)])
+@pytest.mark.parametrize("nx,ny,prec", [(64, 64, 0), (96, 80, 0), (70, 64, 0), (128, 128, 2), (256, 72, 2)])
 @pytest.mark.parametrize("l", [1, 3])
-def test_phi_burgers_jacobian(lx, xi_oracle, nx, ny, l):
+def test_phi_burgers_jacobian(lx, xi_oracle, nx, ny, l, prec):
     # nu such that 4 nu n / max|u| >= 5: the diffusion-dominated regime of the
     # 2048^2, nu = 5e-3 workload, where real Leja points apply
     nu = 2e-2
@@ -119,7 +119,7 @@ def test_phi_burgers_jacobian(lx, xi_oracle, nx, ny, l):
     h = 50 * synth.cfl_step(nx, ny, nu, np.abs(u).max())
     rho, _, _ = oracle.power_iteration(oracle.BURGERS, nx, ny, nu, 0.0, u, synth.power_start(nx * ny, 5), 10)
     c, g = oracle.spectral_interval(rho)
-    ctx = lx.leja_setup(nx, ny, nu, 0.0, lx.BURGERS, lx.FP64)
+    ctx = lx.leja_setup(nx, ny, nu, 0.0, lx.BURGERS, prec)
     out = torch.empty(nx * ny, dtype=torch.float64, device="cuda")
     st, it = lx.phi_l_apply(ctx, l, dev(u), dev(w), out, c, g, h, TOL, TOL)
     ref, it_o, st_o = oracle.leja_phi(oracle.BURGERS, nx, ny, nu, 0.0, u, l, w, c, g, h, TOL, TOL, xi_oracle)
@@ -128,12 +128,13 @@ def test_phi_burgers_jacobian(lx, xi_oracle, nx, ny, l):
     assert rel(out.cpu().numpy(), ref) <= TOL
 
 
-@pytest.mark.parametrize("kind,nx,ny", [(0, 64, 64), (0, 67, 45), (1, 64, 64), (1, 50, 70)])
-def test_power_bound(lx, kind, nx, ny):
+@pytest.mark.parametrize("kind,nx,ny,prec", [(0, 64, 64, 0), (0, 67, 45, 0), (1, 64, 64, 0), (1, 50, 70, 0),
+                                             (0, 64, 64, 2), (0, 67, 45, 2), (1, 128, 96, 2), (1, 256, 256, 2)])
+def test_power_bound(lx, kind, nx, ny, prec):
     nu, a = (1e-2, 1.0) if kind == 0 else (5e-3, 0.0)
     u = synth.burgers_ic(nx, ny, seed=2) if kind == 1 else None
     v0 = synth.power_start(nx * ny, seed=5)
-    ctx = lx.leja_setup(nx, ny, nu, a, kind, lx.FP64)
+    ctx = lx.leja_setup(nx, ny, nu, a, kind, prec)
     st, rho, it = lx.power_bound(ctx, dev(u) if u is not None else None, dev(v0), 10)
     rho_o, it_o, st_o = oracle.power_iteration(kind, nx, ny, nu, a, u, v0, 10)
     assert st == 0 and st_o == 0
@@ -142,7 +143,8 @@ def test_power_bound(lx, kind, nx, ny):
 
 
 @pytest.mark.parametrize("kind,integ,n,prec", [(0, 0, 64, 0), (0, 1, 64, 0), (0, 0, 128, 2), (0, 1, 128, 2),
-                                              (1, 0, 64, 0), (1, 1, 64, 0), (1, 1, 72, 0)])
+                                              (1, 0, 64, 0), (1, 1, 64, 0), (1, 1, 72, 0), (1, 0, 128, 2),
+                                              (1, 1, 128, 2)])
 def test_expint_step(lx, xi_oracle, kind, integ, n, prec):
     if kind == 0:
         # a = 0.5: with a = 1 at 64^2 the spectrum is far enough off the real
@@ -360,3 +362,28 @@ def test_adaptive_integration_matches_oracle(lx, xi_oracle):
     assert abs(info["t"] - t_o) <= 1e-12 * T
     assert abs(info["leja_iters"] - its_o) <= 2 * (steps_o + rej_o)
     assert rel(u.cpu().numpy(), ref) <= 1e-9
+
+
+@pytest.mark.parametrize("name", ["leja_iter_df_pipe_burgers_b1", "leja_iter_df_pipe_burgers_b2"])
+@pytest.mark.parametrize("strip_h", [8, 32, 128])
+def test_df64_burgers_candidates_parity(lx, xi_oracle, name, strip_h):
+    nx, ny, nu = 256, 100, 2e-2
+    u = synth.burgers_ic(nx, ny, seed=8)
+    w = synth.random_field(nx * ny, seed=9)
+    h = 40 * synth.cfl_step(nx, ny, nu, np.abs(u).max())
+    rho, _, _ = oracle.power_iteration(oracle.BURGERS, nx, ny, nu, 0.0, u, synth.power_start(nx * ny, 5), 10)
+    c, g = oracle.spectral_interval(rho)
+    ctx = lx.leja_setup(nx, ny, nu, 0.0, lx.BURGERS, lx.DF64)
+    assert lx.lx_ctx_select_kernel(ctx, name, strip_h) == 0
+    out = torch.empty(nx * ny, dtype=torch.float64, device="cuda")
+    st, it = lx.phi_l_apply(ctx, 3, dev(u), dev(w), out, c, g, h, TOL, TOL)
+    ref, it_o, st_o = oracle.leja_phi(oracle.BURGERS, nx, ny, nu, 0.0, u, 3, w, c, g, h, TOL, TOL, xi_oracle)
+    assert st == 0 and st_o == 0 and abs(it - it_o) <= 1
+    assert rel(out.cpu().numpy(), ref) <= TOL
+
+
+def test_df64_burgers_rejects_unsupported_layout(lx):
+    from paper_2310_08344_gb300 import LexgbError
+
+    with pytest.raises(LexgbError):
+        lx.leja_setup(96, 96, 2e-2, 0.0, lx.BURGERS, lx.DF64)
