@@ -124,6 +124,20 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def aggregate(dist, t_local, units_local, device="cuda"):
+    """Whole-job numbers of independent replicas: the slowest rank's time and
+    the units all ranks processed (one all-reduce each, not on the data path)."""
+    if dist is None:
+        return t_local, units_local
+    import torch
+
+    t = torch.tensor([t_local], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    u = torch.tensor([units_local], dtype=torch.float64, device=device)
+    dist.all_reduce(u, op=dist.ReduceOp.SUM)
+    return float(t.item()), float(u.item())
+
+
 def measured_peaks():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(path):
@@ -441,14 +455,7 @@ def main():
     stats = lx.lx_ctx_stats(ctx, reset=True)
     units = float(N) * sum(iters)
     t_local = ms / 1e3
-    if pg:
-        t = torch.tensor([t_local], device="cuda", dtype=torch.float64)
-        pg.all_reduce(t, op=pg.ReduceOp.MAX)
-        tot = torch.tensor([units], device="cuda", dtype=torch.float64)
-        pg.all_reduce(tot, op=pg.ReduceOp.SUM)
-        t_max, units_all = float(t.item()), float(tot.item())
-    else:
-        t_max, units_all = t_local, units
+    t_max, units_all = aggregate(pg, t_local, units)
     value = units_all / t_max / 1e9
 
     # dominant kernel: the fused Leja iteration (one launch per iteration)
@@ -482,12 +489,7 @@ def main():
             hin, hout = hout, hin
         dt = time.perf_counter() - t0
         e_units = float(N) * tot_it
-        if pg:
-            tt = torch.tensor([dt], device="cuda", dtype=torch.float64)
-            pg.all_reduce(tt, op=pg.ReduceOp.MAX)
-            uu = torch.tensor([e_units], device="cuda", dtype=torch.float64)
-            pg.all_reduce(uu, op=pg.ReduceOp.SUM)
-            dt, e_units = float(tt.item()), float(uu.item())
+        dt, e_units = aggregate(pg, dt, e_units)
         e2e = {"value": e_units / dt / 1e9, "unit": UNIT, "h2d_bytes_per_step": 8 * N, "d2h_bytes_per_step": 8 * N,
                "path": "expint_step_host (pinned host buffers, copies inside the timed region)"}
 
