@@ -207,7 +207,7 @@ typedef struct lx_mlp lx_mlp;
 /* lx_integrate with the learned controller: after every accepted step the
  * network proposes the next step size from the attempt's features
  * (log(rho h), log(h / dt_ref), iters / 100, log10(err / tol), ||u||); the
- * factor is clipped to [0.2, 2].  Rejections, and non-finite proposals, fall
+ * factor is clipped to [0.2, 4].  Rejections, and non-finite proposals, fall
  * back to lx_controller_classical.  The embedded error test (err <= tol)
  * still accepts or rejects every step.  dt_ref > 0 is the explicit CFL step
  * used in the features. */

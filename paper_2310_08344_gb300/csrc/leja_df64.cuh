@@ -830,6 +830,7 @@ static __global__ void __launch_bounds__(kThreadsPerBlock)
   if (__ldcg(&st->pdone)) return;
   const dfv sg = df_from_double(__ldcg(&st->sigma));
   dfv acc = {0.f, 0.f};
+  float small = 0.f;
   const double* vd = reinterpret_cast<const double*>(vin);
   const float2* vf = reinterpret_cast<const float2*>(vin);
   auto ld = [&](long long i) -> dfv {
@@ -862,9 +863,14 @@ static __global__ void __launch_bounds__(kThreadsPerBlock)
     }
     const dfv y = df_mul(sg, df_dot5(wh, wl, t));
     w[i] = make_float2(y.h, y.l);
-    df_acc(acc, __fmul_rn(y.h, y.h));
+    // exact square of the leading float plus the cross term 2 h l: the
+    // power estimate rho = ||w|| must carry double accuracy
+    float sq, se;
+    two_prod(y.h, y.h, sq, se);
+    df_acc(acc, sq);
+    small = __fmaf_rn(2.f * y.h, y.l, __fadd_rn(small, se));
   }
-  double s = df_to_double(acc), dummy = 0.0;
+  double s = df_to_double(acc) + (double)small, dummy = 0.0;
   if (!last_block_total2(s, dummy, partials, ticket)) return;
   if (threadIdx.x == 0) {
     const double rho = sqrt(s / double(g.n));

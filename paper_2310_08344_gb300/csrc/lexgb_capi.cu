@@ -571,6 +571,7 @@ lx_status leja_setup(const lx_problem* prob, int integrator, int max_leja, void*
   c->aux_grid = 4 * c->sm_count;
   for (int v = 0; v < kNumVariants; ++v) {
     if (v == kVec2 && prob->nx % (32 * wide_vec(c)) != 0) continue;
+    if (candidates(prob->kind, prob->precision, v).empty()) continue;  // built on demand (and refused) later
     lx_status s = ensure_graph(c, v);
     if (s != LX_OK) return fail(s);
   }
@@ -1035,7 +1036,7 @@ static lx_status integrate_impl(lx_ctx* c, double* u, const double* v0, double t
         break;
       }
       if (std::isfinite(y[0])) {
-        const double f = std::exp(std::min(std::log(2.0), std::max(std::log(0.2), (double)y[0])));
+        const double f = std::exp(std::min(std::log(4.0), std::max(std::log(0.2), (double)y[0])));
         h_next = hh * f;
         ++learned;
       }

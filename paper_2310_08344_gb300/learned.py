@@ -48,9 +48,19 @@ def generate_samples(n, nu, u0_list, v0, tol, leja_tol, steps_per_traj, dt_cfl, 
                 st, err, it = B.expint_step(ctx, u, lo, his[j + 4], c, g, hj, leja_tol, leja_tol)
                 res.append((hj, err if st == 0 else float("inf"), it))
             h0, err0, it0 = res[4]
-            ok = [k for k in range(9) if res[k][1] <= 0.8 * tol]
-            best = max(ok, key=lambda k: res[k][0] / max(res[k][2], 1)) if ok else 0
-            hb, eb, ib = res[best]
+            target = 0.8 * tol
+            best = 0
+            hb, ib = res[0][0], res[0][2]
+            for k in range(9):
+                if res[k][1] <= target:
+                    best = k
+            if res[best][1] <= target:
+                hb, ib = res[best][0], res[best][2]
+                if best < 8 and math.isfinite(res[best + 1][1]) and res[best + 1][1] > target and res[best][1] > 0:
+                    e0, e1 = math.log(res[best][1]), math.log(res[best + 1][1])
+                    f = (math.log(target) - e0) / (e1 - e0)
+                    hb = math.exp(math.log(res[best][0]) + f * (math.log(res[best + 1][0]) - math.log(res[best][0])))
+                    ib = res[best][2] + f * (res[best + 1][2] - res[best][2])
             x = [math.log(rho * h0), math.log(h0 / dt_cfl), it0 / 100.0,
                  math.log10(max(err0, 1e-300) / tol), _norm_u(u)]
             if all(math.isfinite(v) for v in x):
@@ -58,7 +68,7 @@ def generate_samples(n, nu, u0_list, v0, tol, leja_tol, steps_per_traj, dt_cfl, 
                 Y.append([math.log(hb / h0), math.log(max(ib, 1))])
             if res[best][1] <= tol:
                 u.copy_(his[best])
-            h = hb * 2.0 ** rng.uniform(-1.0, 1.0)
+            h = res[best][0] * 2.0 ** rng.uniform(-1.0, 1.0)
     ctx.close()
     return np.asarray(X, dtype=np.float32), np.asarray(Y, dtype=np.float32)
 
