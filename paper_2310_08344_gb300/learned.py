@@ -4,9 +4,12 @@ The network (see include/lexgb.h, mlp_*) maps the features of an attempted
 EXPRB32 step -- log(rho h), log(h / dt_CFL), iters / 100, log10(err / tol),
 ||u|| -- to log(h_next / h) and log(iters predicted).  Labels come from the
 method itself: at a state u with current step h, the nine steps
-h_j = h 2^(j/2), j = -4..4, are each attempted, and the label is the h_j with
-the largest h_j / iters_j among those with err_j <= 0.8 tol (the smallest
-h_j if none passes).  Every step of the computation (power bounds, EXPRB32
+h_j = h 2^(j/2), j = -4..4, are each attempted; the label step h* is where
+the measured error crosses 0.8 tol (log-log interpolation between the two
+neighbouring attempts; the largest attempt if all stay below, the smallest if
+none does).  That is the largest step the error test accepts with a margin,
+hence the one with the most simulated time per Leja iteration, since the
+iteration count grows sublinearly in h.  Every step of the computation (power bounds, EXPRB32
 steps, the network's forward and backward passes, Adam) runs in the CUDA
 library; this module only orchestrates the calls and keeps the samples.
 """
