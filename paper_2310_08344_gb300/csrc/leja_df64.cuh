@@ -452,6 +452,7 @@ constexpr int kYSlot = kPipeRow + 4;      // [pad][west halo][128 points][east h
 constexpr int kPSlot = kPipeRow;
 constexpr int kSlotElems = kYSlot + kPSlot;
 constexpr int kPipeSmemBytes = kPipeWarps * kPipeStages * kSlotElems * 8;
+constexpr int kPipeSmemBytes8 = kPipeWarps * 8 * kSlotElems * 8;  // the 8-stage variant
 
 __device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
   const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
@@ -496,7 +497,7 @@ __device__ __forceinline__ void df_from_raw4(const unsigned long long* e, int sc
   }
 }
 
-template <typename S, bool FIRST>
+template <int STAGES, typename S, bool FIRST>
 __device__ __forceinline__ void df_strip_pipe(const LoopArgs& A, const S* __restrict__ src, float2* __restrict__ dst,
                                               float2* __restrict__ p, unsigned long long* ring, int col0, int r0,
                                               int r1, const float (&wh)[5], const float (&wl)[5], dfv d0, dfv dm1,
@@ -508,7 +509,7 @@ __device__ __forceinline__ void df_strip_pipe(const LoopArgs& A, const S* __rest
   const int ce = (col0 + kPipeRow >= nx) ? 0 : col0 + kPipeRow;
   const int nrows = r1 - r0;           // rows computed
   const int last_q = nrows + 1;        // y rows q = 0 .. nrows+1 (r0-1 .. r1)
-  auto slot = [&](int q) { return ring + (size_t)(q % kPipeStages) * kSlotElems; };
+  auto slot = [&](int q) { return ring + (size_t)(q % STAGES) * kSlotElems; };
   auto issue = [&](int q) {
     if (q <= last_q) {
       int ry = r0 - 1 + q;
@@ -529,15 +530,15 @@ __device__ __forceinline__ void df_strip_pipe(const LoopArgs& A, const S* __rest
     }
     cp_commit();
   };
-  for (int q = 0; q < kPipeStages - 1; ++q) issue(q);
-  cp_wait<kPipeStages - 3>();
+  for (int q = 0; q < STAGES - 1; ++q) issue(q);
+  cp_wait<STAGES - 3>();
   __syncwarp();
   dfv ys[4], yc[4], yn[4];
   df_from_raw4<S>(slot(0) + 2 + lane * 4, sc, ys);
   df_from_raw4<S>(slot(1) + 2 + lane * 4, sc, yc);
   for (int qc = 1; qc <= nrows; ++qc) {
-    issue(qc + kPipeStages - 2);
-    cp_wait<kPipeStages - 3>();
+    issue(qc + STAGES - 2);
+    cp_wait<STAGES - 3>();
     __syncwarp();
     const unsigned long long* sn = slot(qc + 1);
     const unsigned long long* scn = slot(qc);
@@ -575,7 +576,7 @@ __device__ __forceinline__ void df_strip_pipe(const LoopArgs& A, const S* __rest
   __syncwarp();
 }
 
-template <int MINB>
+template <int MINB, int STAGES = kPipeStages>
 __global__ void __launch_bounds__(kPipeThreads, MINB)
     leja_iter_df_pipe_kernel(const LoopArgs* __restrict__ Ap, LoopState* __restrict__ st,
                              double* __restrict__ partials, unsigned int* __restrict__ ticket,
@@ -604,16 +605,17 @@ __global__ void __launch_bounds__(kPipeThreads, MINB)
   float2* dst = reinterpret_cast<float2*>((m & 1) ? A.y1 : A.y0);
   dfv accy = {0.f, 0.f}, accp = {0.f, 0.f};
   const int warp = threadIdx.x >> 5;
-  unsigned long long* ring = pipe_smem + (size_t)warp * kPipeStages * kSlotElems;
+  unsigned long long* ring = pipe_smem + (size_t)warp * STAGES * kSlotElems;
   for (int s = blockIdx.x * kPipeWarps + warp; s < nstrips; s += gridDim.x * kPipeWarps) {
     const int col0 = (s % ncs) * kPipeRow;
     const int r0 = (s / ncs) * H;
     const int r1 = min(r0 + H, ny);
     if (m == 0) {
-      df_strip_pipe<double, true>(A, A.w, dst, A.pdf, ring, col0, r0, r1, wh, wl, d0, dm1, sc, accy, accp);
+      df_strip_pipe<STAGES, double, true>(A, A.w, dst, A.pdf, ring, col0, r0, r1, wh, wl, d0, dm1, sc, accy, accp);
     } else {
       const float2* src = reinterpret_cast<const float2*>(((m - 1) & 1) ? A.y1 : A.y0);
-      df_strip_pipe<float2, false>(A, src, dst, A.pdf, ring, col0, r0, r1, wh, wl, d0, dm1, sc, accy, accp);
+      df_strip_pipe<STAGES, float2, false>(A, src, dst, A.pdf, ring, col0, r0, r1, wh, wl, d0, dm1, sc, accy,
+                                           accp);
     }
   }
   double sy = df_to_double(accy), sp = df_to_double(accp);

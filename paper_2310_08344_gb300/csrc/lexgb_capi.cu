@@ -159,6 +159,10 @@ std::vector<Cand> candidates(int kind, int precision, int cls) {
                        "leja_iter_df_pipe_b3"});
       v.push_back(Cand{reinterpret_cast<const void*>(&leja_iter_df_pipe_kernel<4>), kPipeThreads, kPipeSmemBytes, 4,
                        "leja_iter_df_pipe_b4"});
+      v.push_back(Cand{reinterpret_cast<const void*>(&leja_iter_df_pipe_kernel<2, 8>), kPipeThreads,
+                       kPipeSmemBytes8, 4, "leja_iter_df_pipe_b2_s8"});
+      v.push_back(Cand{reinterpret_cast<const void*>(&leja_iter_df_pipe_kernel<3, 8>), kPipeThreads,
+                       kPipeSmemBytes8, 4, "leja_iter_df_pipe_b3_s8"});
       v.push_back(Cand{reinterpret_cast<const void*>(&leja_iter_df_advdiff_kernel<4>), kThreadsPerBlock, 0, 4,
                        "leja_iter_df_advdiff_v4"});
     } else {

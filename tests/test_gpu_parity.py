@@ -299,7 +299,8 @@ def test_stream_loop_mode_matches_graph(lx):
     assert np.array_equal(outs[0][1], outs[1][1])  # same kernels, same order: bitwise
 
 
-DF64_KERNELS = ["leja_iter_df_pipe_b2", "leja_iter_df_pipe_b3", "leja_iter_df_pipe_b4", "leja_iter_df_advdiff_v4"]
+DF64_KERNELS = ["leja_iter_df_pipe_b2", "leja_iter_df_pipe_b3", "leja_iter_df_pipe_b4", "leja_iter_df_pipe_b2_s8",
+                "leja_iter_df_pipe_b3_s8", "leja_iter_df_advdiff_v4"]
 
 
 @pytest.mark.parametrize("name", DF64_KERNELS)
