@@ -704,7 +704,7 @@ lx_status expint_step(lx_ctx* c, const double* u, double* u_low, double* u_high,
   const int G = aux_blocks(c);
   lx_status st = begin_call(c);
   if (st != LX_OK) return st;
-  if (P.precision == LX_DF64 && c->integrator == LX_ROS_EU) {
+  if (P.precision == LX_DF64 && P.kind == LX_ADVDIFF && c->integrator == LX_ROS_EU) {
     // df64 Rosenbrock-Euler: h A u on the FP32 pipe (recording the input
     // scale), the Leja loop, and u + p fused into the loop's output pass
     const double dx = 1.0 / P.nx, dy = 1.0 / P.ny;
