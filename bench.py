@@ -329,6 +329,8 @@ def run_burgers(args, rank, world, local):
     finals = {}
     for prec_name, prec in (("fp64", lx.FP64), ("mixed", lx.MIXED), ("df64", lx.DF64)):
         ctx = lx.leja_setup(n, n, nu, 0.0, lx.BURGERS, prec, lx.EXPRB32, 1000, stream)
+        if not args.no_autotune:
+            lx.lx_ctx_autotune(ctx, 10, None)
         u = torch.from_numpy(u0).cuda()
         lo, hi = torch.empty_like(u), torch.empty_like(u)
 

@@ -288,7 +288,9 @@ lx_status ensure_graph(lx_ctx* c, int variant) {
     return LX_E_INVAL;
   }
   const Cand k = cands[0];
-  return build_loop_graph(c, variant, k, c->strip_h);
+  // pipelined kernels (dynamic shared memory) default to 8-row strips: one
+  // strip per warp then gives enough resident warps on mid-size grids
+  return build_loop_graph(c, variant, k, k.smem > 0 ? 8 : c->strip_h);
 }
 
 lx_status ensure_coeffs(lx_ctx* c, int slot, int l, double h, double cc, double gamma) {
