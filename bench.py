@@ -56,6 +56,7 @@ def parse():
     p.add_argument("--no-autotune", action="store_true")
     p.add_argument("--kernel", default=None, help="force a fused-iteration kernel (name) instead of autotuning")
     p.add_argument("--strip-h", type=int, default=8)
+    p.add_argument("--unroll", type=int, default=None, help="fused-iteration launches per graph-loop pass")
     p.add_argument("--workload", default="advdiff4096", choices=["advdiff4096", "batch256", "burgers2048"])
     return p.parse_args()
 
@@ -405,6 +406,8 @@ def main():
     prec = {"fp64": lx.FP64, "mixed": lx.MIXED, "df64": lx.DF64}[args.precision]
     stream = torch.cuda.current_stream()
     ctx = lx.leja_setup(n, n, NU, ADV, lx.ADVDIFF, prec, lx.ROS_EU, 1000, stream)
+    if args.unroll and lx.lx_ctx_set_graph_unroll(ctx, args.unroll) != 0:
+        raise SystemExit(f"bad --unroll {args.unroll}")
     tune = None
     if args.kernel:
         if lx.lx_ctx_select_kernel(ctx, args.kernel, args.strip_h) != 0:

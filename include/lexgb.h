@@ -235,10 +235,20 @@ lx_status lx_ctx_stats(lx_ctx* ctx, lx_stats* out, int reset);
  * LEXGB_STREAM_LOOP=1 selects mode 1 at setup. */
 lx_status lx_ctx_set_loop_mode(lx_ctx* ctx, int stream_loop);
 
+/* Graph loop unrolling: the while body of each loop graph holds `unroll`
+ * (1..8, default 4) chained launches of the fused iteration, so the loop
+ * condition is evaluated once per `unroll` iterations; launches that start
+ * after the device-side stop return without work (at most unroll - 1 per
+ * loop).  Results are identical for every value.  Rebuilds the context's
+ * loop graphs with their selected kernels. */
+lx_status lx_ctx_set_graph_unroll(lx_ctx* ctx, int unroll);
+
 /* Autotuner of the fused Leja iteration (a tile-shape search).  Times every
  * candidate kernel of the context's (kind, precision) -- for LX_DF64 the
  * shared-memory-pipelined kernel at 2, 3 and 4 resident blocks per SM and
- * the register-window kernel -- at strip heights 8..128 rows, each for
+ * the register-window kernel -- at strip heights 8..128 rows and, for the
+ * pipelined kernels, strip height 0 (one balanced contiguous row range per
+ * warp), each for
  * `iters` launches (1..50) on the context's own buffers, and selects the
  * fastest for the vector-access ("wide") class.  cache_path (may be NULL) is
  * a text file of lines "<device|SMs|nx x ny|kind|precision> <kernel> <strip
@@ -248,7 +258,8 @@ lx_status lx_ctx_set_loop_mode(lx_ctx* ctx, int stream_loop);
 lx_status lx_ctx_autotune(lx_ctx* ctx, int iters, const char* cache_path, char* report, int len);
 
 /* Select a fused-iteration kernel by name (as reported by the autotuner or
- * lx_ctx_kernel_name) and strip height. */
+ * lx_ctx_kernel_name) and strip height (>= 1 rows, or 0 for balanced row
+ * ranges, pipelined kernels only; LX_E_INVAL otherwise). */
 lx_status lx_ctx_select_kernel(lx_ctx* ctx, const char* name, int strip_h);
 
 /* Kernel selection of the context (for diagnostics): writes a short name of

@@ -77,6 +77,7 @@ def lib():
             L.lx_ctx_stats.argtypes = [_vp, C.POINTER(LxStats), C.c_int]
             L.lx_ctx_kernel_name.argtypes = [_vp, C.c_char_p, C.c_int]
             L.lx_ctx_set_loop_mode.argtypes = [_vp, C.c_int]
+            L.lx_ctx_set_graph_unroll.argtypes = [_vp, C.c_int]
             L.lx_controller_classical.restype = C.c_double
             L.lx_controller_classical.argtypes = [C.c_double, C.c_double, C.c_double]
             L.lx_integrate.argtypes = [_vp, _vp, _vp, C.c_double, C.c_double, C.c_double, C.c_int,
@@ -267,6 +268,10 @@ def lx_ctx_kernel_name(ctx: Context) -> str:
 
 def lx_ctx_set_loop_mode(ctx: Context, stream_loop: int) -> int:
     return lib().lx_ctx_set_loop_mode(ctx.handle, int(stream_loop))
+
+
+def lx_ctx_set_graph_unroll(ctx: Context, unroll: int) -> int:
+    return lib().lx_ctx_set_graph_unroll(ctx.handle, int(unroll))
 
 
 def phi_l_apply_noalloc(nx, ny, nu, a, l, w, out, c, gamma, h, rtol, atol, stream=None):

@@ -304,6 +304,7 @@ __global__ void __launch_bounds__(kThreadsPerBlock)
                                 cudaGraphConditionalHandle cond) {
   const LoopArgs& A = *Ap;
   const int m = __ldcg(&st->m);
+  count_launch(st);
   if (__ldcg(&st->done)) return;
   const int kexp = __ldcg(&st->kscale);
   const int sig = __ldcg(&st->sig);  // stored y_m = y_m 2^-sig
@@ -468,6 +469,33 @@ __device__ __forceinline__ void cp_wait() {
   asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
 }
 
+// Rows a warp processes, as segments (col0, r0, r1) of one warp-row column
+// strip: strips of H rows dealt round-robin over the nw warps (H > 0), or
+// one contiguous, evenly sized range of the ncs * ny (column strip, row)
+// lines per warp (H == 0), which balances the warps and reads each halo row
+// only twice per warp instead of once per strip.
+template <typename F>
+__device__ __forceinline__ void for_each_segment(int nx, int ny, int H, int wid, int nw, F&& f) {
+  const int ncs = nx / kPipeRow;
+  if (H > 0) {
+    const int nstrips = ncs * ((ny + H - 1) / H);
+    for (int s = wid; s < nstrips; s += nw) {
+      const int r0 = (s / ncs) * H;
+      f((s % ncs) * kPipeRow, r0, min(r0 + H, ny));
+    }
+  } else {
+    const long long T = (long long)ncs * ny;
+    long long t = T * wid / nw;
+    const long long t1 = T * (wid + 1) / nw;
+    while (t < t1) {
+      const int cs = (int)(t / ny), r0 = (int)(t % ny);
+      const int r1 = (int)min((long long)ny, (long long)r0 + (t1 - t));
+      f(cs * kPipeRow, r0, r1);
+      t += r1 - r0;
+    }
+  }
+}
+
 template <typename S>
 __device__ __forceinline__ dfv df_from_raw(const unsigned long long* e, int sc) {
   if constexpr (sizeof(S) == 8 && !std::is_same<S, float2>::value) {
@@ -584,6 +612,7 @@ __global__ void __launch_bounds__(kPipeThreads, MINB)
   extern __shared__ __align__(16) unsigned long long pipe_smem[];
   const LoopArgs& A = *Ap;
   const int m = __ldcg(&st->m);
+  count_launch(st);
   if (__ldcg(&st->done)) return;
   const int kexp = __ldcg(&st->kscale);
   const int sig = __ldcg(&st->sig);
@@ -591,8 +620,6 @@ __global__ void __launch_bounds__(kPipeThreads, MINB)
   const int sc = kexp;
   const int nx = A.nx, ny = A.ny;
   const int H = A.strip_h;
-  const int ncs = nx / kPipeRow;
-  const int nstrips = ncs * ((ny + H - 1) / H);
   const double xim = __ldg(A.xi + m);
   const double dm1d = __ldg(A.d + m + 1);
   const dfv dm1 = df_from_double(dm1d * pow2(sig + dlt - kexp));
@@ -606,18 +633,14 @@ __global__ void __launch_bounds__(kPipeThreads, MINB)
   dfv accy = {0.f, 0.f}, accp = {0.f, 0.f};
   const int warp = threadIdx.x >> 5;
   unsigned long long* ring = pipe_smem + (size_t)warp * STAGES * kSlotElems;
-  for (int s = blockIdx.x * kPipeWarps + warp; s < nstrips; s += gridDim.x * kPipeWarps) {
-    const int col0 = (s % ncs) * kPipeRow;
-    const int r0 = (s / ncs) * H;
-    const int r1 = min(r0 + H, ny);
-    if (m == 0) {
+  const float2* src = reinterpret_cast<const float2*>(((m - 1) & 1) ? A.y1 : A.y0);
+  for_each_segment(nx, ny, H, blockIdx.x * kPipeWarps + warp, gridDim.x * kPipeWarps, [&](int col0, int r0, int r1) {
+    if (m == 0)
       df_strip_pipe<STAGES, double, true>(A, A.w, dst, A.pdf, ring, col0, r0, r1, wh, wl, d0, dm1, sc, accy, accp);
-    } else {
-      const float2* src = reinterpret_cast<const float2*>(((m - 1) & 1) ? A.y1 : A.y0);
+    else
       df_strip_pipe<STAGES, float2, false>(A, src, dst, A.pdf, ring, col0, r0, r1, wh, wl, d0, dm1, sc, accy,
                                            accp);
-    }
-  }
+  });
   double sy = df_to_double(accy), sp = df_to_double(accp);
   if (!last_block_total2(sy, sp, partials, ticket)) return;
   if (threadIdx.x == 0) {
@@ -770,14 +793,13 @@ __global__ void __launch_bounds__(kPipeThreads, MINB)
   extern __shared__ __align__(16) unsigned long long pipe_smem_b[];
   const LoopArgs& A = *Ap;
   const int m = __ldcg(&st->m);
+  count_launch(st);
   if (__ldcg(&st->done)) return;
   const int kexp = __ldcg(&st->kscale);
   const int sig = __ldcg(&st->sig);
   const int dlt = __ldcg(&st->dlt);
   const int nx = A.nx, ny = A.ny;
   const int H = A.strip_h;
-  const int ncs = nx / kPipeRow;
-  const int nstrips = ncs * ((ny + H - 1) / H);
   const double xim_d = __ldg(A.xi + m);
   const double dm1d = __ldg(A.d + m + 1);
   const dfv dm1 = df_from_double(dm1d * pow2(sig + dlt - kexp));
@@ -788,19 +810,15 @@ __global__ void __launch_bounds__(kPipeThreads, MINB)
   dfv accy = {0.f, 0.f}, accp = {0.f, 0.f};
   const int warp = threadIdx.x >> 5;
   unsigned long long* ring = pipe_smem_b + (size_t)warp * kPipeStages * kSlotElemsB;
-  for (int s = blockIdx.x * kPipeWarps + warp; s < nstrips; s += gridDim.x * kPipeWarps) {
-    const int col0 = (s % ncs) * kPipeRow;
-    const int r0 = (s / ncs) * H;
-    const int r1 = min(r0 + H, ny);
-    if (m == 0) {
+  const float2* src = reinterpret_cast<const float2*>(((m - 1) & 1) ? A.y1 : A.y0);
+  for_each_segment(nx, ny, H, blockIdx.x * kPipeWarps + warp, gridDim.x * kPipeWarps, [&](int col0, int r0, int r1) {
+    if (m == 0)
       df_strip_pipe_burgers<double, true>(A, A.w, dst, A.pdf, ring, col0, r0, r1, xim, swf, d0, dm1, kexp, accy,
                                           accp);
-    } else {
-      const float2* src = reinterpret_cast<const float2*>(((m - 1) & 1) ? A.y1 : A.y0);
+    else
       df_strip_pipe_burgers<float2, false>(A, src, dst, A.pdf, ring, col0, r0, r1, xim, swf, d0, dm1, kexp, accy,
                                            accp);
-    }
-  }
+  });
   double sy = df_to_double(accy), sp = df_to_double(accp);
   if (!last_block_total2(sy, sp, partials, ticket)) return;
   if (threadIdx.x == 0) {

@@ -81,7 +81,13 @@ struct LoopState {
   int kscale;                // df64 form: w is scaled by 2^-kscale
   int sig;                   // df64 form: the stored basis is y_m 2^-sig
   int dlt;                   // df64 form: extra scaling 2^-dlt of the next step
+  int launches;              // fused-iteration launches of the call (incl. ones that found done)
 };
+
+// One thread per launch records it (launches of one loop are stream-ordered).
+__device__ __forceinline__ void count_launch(LoopState* st) {
+  if (blockIdx.x == 0 && threadIdx.x == 0) st->launches += 1;
+}
 
 __device__ __forceinline__ int wrap_up(int i, int n) { return i + 1 == n ? 0 : i + 1; }
 __device__ __forceinline__ int wrap_dn(int i, int n) { return i == 0 ? n - 1 : i - 1; }
@@ -309,6 +315,7 @@ static __global__ void __launch_bounds__(kThreadsPerBlock)
                      unsigned int* __restrict__ ticket, cudaGraphConditionalHandle cond) {
   const LoopArgs& A = *Ap;
   const int m = __ldcg(&st->m);
+  count_launch(st);
   if (__ldcg(&st->done)) return;
   const int nx = A.nx, ny = A.ny;
   const int H = A.strip_h;
@@ -355,6 +362,7 @@ static __global__ void reset_call_kernel(LoopState* st, unsigned int* ticket) {
   st->wexp = 0;
   st->iters_total = 0;
   st->status_total = 0;
+  st->launches = 0;
   st->red = 0.0;
   *ticket = 0u;
 }

@@ -81,6 +81,7 @@ struct LoopGraph {
   int grid = 0;
   Cand cand{};
   int strip_h = 32;
+  int unroll = 1;
 };
 
 }  // namespace
@@ -111,6 +112,7 @@ struct lx_ctx {
   double* d_partials = nullptr;
   int partials_cap = 0;
   int stream_loop = 0;  // 1: launch the iterations from the host (profilers)
+  int graph_unroll = 4; // fused-iteration kernel nodes per pass of the graph's while body
   int graph_iter_launches_pending = 0;  // a graph loop ran since the last end_call
   unsigned int* d_ticket = nullptr;
   LoopState* d_state = nullptr;
@@ -197,13 +199,17 @@ int grid_for(const lx_ctx* c, const Cand& k, int strip_h, int* grid) {
       !cuda_ok(cudaFuncSetAttribute(k.func, cudaFuncAttributeMaxDynamicSharedMemorySize, k.smem), "smem attribute"))
     return LX_E_CUDA;
   const int ncs = (c->prob.nx + 32 * k.vec - 1) / (32 * k.vec);
-  const int nrs = (c->prob.ny + strip_h - 1) / strip_h;
   const int wpb = k.threads / 32;
+  // strip_h == 0 (pipelined kernels only): one balanced row range per warp,
+  // at least 4 rows each
+  if (strip_h == 0 && k.smem == 0) return LX_E_INVAL;
+  const long long units = strip_h > 0 ? (long long)ncs * ((c->prob.ny + strip_h - 1) / strip_h)
+                                      : ((long long)ncs * c->prob.ny + 3) / 4;
   int per_sm = 0;
   if (!cuda_ok(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k.func, k.threads, k.smem), "occupancy"))
     return LX_E_CUDA;
   per_sm = std::max(per_sm, 1);
-  const int want = (ncs * nrs + wpb - 1) / wpb;
+  const int want = (int)std::min<long long>((units + wpb - 1) / wpb, 1 << 30);
   *grid = std::max(1, std::min(want, per_sm * c->sm_count));
   return *grid > c->partials_cap ? LX_E_INVAL : LX_OK;
 }
@@ -219,13 +225,14 @@ void destroy_graph(LoopGraph& L) {
 // (Re)build the while-loop graph of class `variant` around candidate k.
 lx_status build_loop_graph(lx_ctx* c, int variant, const Cand& k, int strip_h) {
   LoopGraph& L = c->loop[variant];
-  if (L.built && L.cand.func == k.func && L.strip_h == strip_h) return LX_OK;
+  if (L.built && L.cand.func == k.func && L.strip_h == strip_h && L.unroll == c->graph_unroll) return LX_OK;
   destroy_graph(L);
   int grid = 0;
   int gs = grid_for(c, k, strip_h, &grid);
   if (gs != LX_OK) return (lx_status)gs;
   L.cand = k;
   L.strip_h = strip_h;
+  L.unroll = c->graph_unroll;
   L.grid = grid;
   LX_CUDA(cudaGraphCreate(&L.graph, 0));
   cudaGraphConditionalHandle cond;
@@ -255,8 +262,14 @@ lx_status build_loop_graph(lx_ctx* c, int variant, const Cand& k, int strip_h) {
   kp.blockDim = dim3(k.threads);
   kp.sharedMemBytes = k.smem;
   kp.kernelParams = kargs;
-  cudaGraphNode_t knode;
-  LX_CUDA(cudaGraphAddKernelNode(&knode, body, nullptr, 0, &kp));
+  // `unroll` chained launches per pass of the body: the while condition is
+  // evaluated once per pass; launches after the stop return at once.
+  cudaGraphNode_t prev = nullptr;
+  for (int u = 0; u < L.unroll; ++u) {
+    cudaGraphNode_t knode;
+    LX_CUDA(cudaGraphAddKernelNode(&knode, body, prev ? &prev : nullptr, prev ? 1 : 0, &kp));
+    prev = knode;
+  }
   LX_CUDA(cudaGraphInstantiate(&L.exec, L.graph, 0));
   L.built = true;
   return LX_OK;
@@ -445,7 +458,7 @@ lx_status end_call(lx_ctx* c) {
     c->stats.loop_launches += 1;
   }
   c->stats.loop_iterations += c->h_state->iters_total;
-  c->stats.kernels += c->graph_iter_launches_pending ? c->h_state->iters_total : 0;
+  c->stats.kernels += c->graph_iter_launches_pending ? c->h_state->launches : 0;
   c->graph_iter_launches_pending = 0;
   c->ev_used = 0;
   return LX_OK;
@@ -809,6 +822,18 @@ lx_status lx_ctx_set_loop_mode(lx_ctx* c, int stream_loop) {
   return LX_OK;
 }
 
+lx_status lx_ctx_set_graph_unroll(lx_ctx* c, int unroll) {
+  if (!c || unroll < 1 || unroll > 8) return LX_E_INVAL;
+  c->graph_unroll = unroll;
+  for (int v = 0; v < kNumVariants; ++v) {
+    LoopGraph& L = c->loop[v];
+    if (!L.built) continue;
+    const lx_status st = build_loop_graph(c, v, L.cand, L.strip_h);
+    if (st != LX_OK) return st;
+  }
+  return LX_OK;
+}
+
 lx_status lx_ctx_kernel_name(lx_ctx* c, char* buf, int len) {
   if (!c || !buf || len <= 0) return LX_E_INVAL;
   const int v = c->loop[kVec2].built ? kVec2 : kVec1;
@@ -858,7 +883,11 @@ lx_status tune_time(lx_ctx* c, const Cand& k, int H, int iters, double* us) {
   a.lx = a.ly = a.gx = a.gy = a.inv_gamma = 0.25;
   a.wc0 = 1.0;
   for (int q = 0; q < 8; ++q) a.wf[q] = (q & 1) ? 0.f : 0.25f;
+  for (int q = 0; q < 6; ++q) a.bl[q] = (q & 1) ? 0.f : 0.25f;
   a.pdf = c->d_pdf;
+  a.bq = c->d_bq;  // df64 Burgers point weights (allocated for that form only)
+  a.br = c->d_br;
+  if (P.precision == LX_DF64 && P.kind == LX_BURGERS && (!a.bq || !a.br)) return LX_E_INVAL;
   a.rtol = 0.0;
   a.atol = -1.0;  // never converged: every launch does the full work
   a.use_cond = 0;
@@ -888,7 +917,7 @@ lx_status tune_time(lx_ctx* c, const Cand& k, int H, int iters, double* us) {
 extern "C" {
 
 lx_status lx_ctx_select_kernel(lx_ctx* c, const char* name, int strip_h) {
-  if (!c || !name || strip_h < 1) return LX_E_INVAL;
+  if (!c || !name || strip_h < 0) return LX_E_INVAL;
   for (int v = 0; v < kNumVariants; ++v)
     for (const Cand& k : candidates(c->prob.kind, c->prob.precision, v))
       if (std::strcmp(k.name, name) == 0) {
@@ -932,10 +961,12 @@ lx_status lx_ctx_autotune(lx_ctx* c, int iters, const char* cache_path, char* re
   LX_CUDA(cudaMemsetAsync(c->d_s, 0, nb, c->stream));
   LX_CUDA(cudaMemsetAsync(c->d_tune, 0, nb, c->stream));
   if (c->d_pdf) LX_CUDA(cudaMemsetAsync(c->d_pdf, 0, sizeof(float2) * (size_t)c->n, c->stream));
+  if (c->d_bq) LX_CUDA(cudaMemsetAsync(c->d_bq, 0, sizeof(float2) * (size_t)c->n, c->stream));
+  if (c->d_br) LX_CUDA(cudaMemsetAsync(c->d_br, 0, sizeof(float2) * (size_t)c->n, c->stream));
   lx_status st = ensure_coeffs(c, 0, 0, 1.0, -20.0, 10.0);
   if (st != LX_OK) return st;
   if (c->coef[0].count < iters + 4) return LX_E_INVAL;
-  const int hs[] = {8, 16, 32, 64, 128};
+  const int hs[] = {0, 8, 16, 32, 64, 128};
   double best = 1e30;
   Cand best_k{};
   int best_h = 32;
@@ -944,6 +975,7 @@ lx_status lx_ctx_autotune(lx_ctx* c, int iters, const char* cache_path, char* re
   for (const Cand& k : candidates(c->prob.kind, c->prob.precision, v)) {
     for (int H : hs) {
       if (H > 2 * c->prob.ny && H != 8) continue;
+      if (H == 0 && k.smem == 0) continue;  // balanced ranges: pipelined kernels only
       double us = 0.0;
       st = tune_time(c, k, H, iters, &us);
       if (st == LX_E_INVAL) continue;  // grid beyond the partials capacity

@@ -299,15 +299,48 @@ def test_stream_loop_mode_matches_graph(lx):
     assert np.array_equal(outs[0][1], outs[1][1])  # same kernels, same order: bitwise
 
 
+@pytest.mark.parametrize("prec", ["fp64", "df64"])
+def test_graph_unroll_is_bitwise_neutral(lx, prec):
+    # Several fused-iteration launches per pass of the graph's while body:
+    # the launches after the device-side stop return without work, so the
+    # result and the iteration count do not change; the launch counter
+    # includes those empty launches.
+    n, nu, a = 256, 1e-2, 0.5
+    u0, h, c, g = advdiff_case(n, n, nu, a, 3)
+    res = []
+    for unroll in (1, 3, 8):
+        ctx = lx.leja_setup(n, n, nu, a, lx.ADVDIFF, getattr(lx, prec.upper()))
+        assert lx.lx_ctx_set_graph_unroll(ctx, unroll) == 0
+        out = torch.empty(n * n, dtype=torch.float64, device="cuda")
+        lx.lx_ctx_stats(ctx, reset=True)
+        st, it = lx.phi_l_apply(ctx, 1, None, dev(u0), out, c, g, h, TOL, TOL)
+        s = lx.lx_ctx_stats(ctx)
+        assert st == 0 and s["loop_iterations"] == it
+        res.append((it, out.cpu().numpy(), s["kernels"]))
+    assert lx.lx_ctx_set_graph_unroll(ctx, 0) != 0 and lx.lx_ctx_set_graph_unroll(ctx, 9) != 0
+    for it, out, kern in res[1:]:
+        assert it == res[0][0] and np.array_equal(out, res[0][1])
+    it = res[0][0]
+    # kernels = fixed per-call launches + fused-iteration launches
+    fixed = res[0][2] - it
+    for unroll, (_, _, kern) in zip((3, 8), res[1:]):
+        assert kern - fixed == -(-it // unroll) * unroll
+
+
 DF64_KERNELS = ["leja_iter_df_pipe_b2", "leja_iter_df_pipe_b3", "leja_iter_df_pipe_b4", "leja_iter_df_pipe_b2_s8",
                 "leja_iter_df_pipe_b3_s8", "leja_iter_df_advdiff_v4"]
 
 
 @pytest.mark.parametrize("name", DF64_KERNELS)
-@pytest.mark.parametrize("strip_h", [8, 32, 128])
+@pytest.mark.parametrize("strip_h", [0, 8, 32, 128])
 def test_df64_candidates_parity(lx, xi_oracle, name, strip_h):
     # every autotuner candidate, on a grid with several column strips and a
-    # ragged last row strip
+    # ragged last row strip; strip_h 0 = balanced row ranges (pipelined
+    # kernels only; ranges that cross a column strip are split)
+    if strip_h == 0 and not name.startswith("leja_iter_df_pipe"):
+        ctx = lx.leja_setup(256, 100, 1e-2, 0.5, lx.ADVDIFF, lx.DF64)
+        assert lx.lx_ctx_select_kernel(ctx, name, 0) != 0
+        return
     nx, ny, nu, a = 256, 100, 1e-2, 0.5
     u0 = synth.gaussians_ic(nx, ny, seed=5) + 0.05 * synth.random_field(nx * ny, 15)
     h = 40 * synth.cfl_step(nx, ny, nu, a)
@@ -366,7 +399,7 @@ def test_adaptive_integration_matches_oracle(lx, xi_oracle):
 
 
 @pytest.mark.parametrize("name", ["leja_iter_df_pipe_burgers_b1", "leja_iter_df_pipe_burgers_b2"])
-@pytest.mark.parametrize("strip_h", [8, 32, 128])
+@pytest.mark.parametrize("strip_h", [0, 8, 32, 128])
 def test_df64_burgers_candidates_parity(lx, xi_oracle, name, strip_h):
     nx, ny, nu = 256, 100, 2e-2
     u = synth.burgers_ic(nx, ny, seed=8)
@@ -381,6 +414,26 @@ def test_df64_burgers_candidates_parity(lx, xi_oracle, name, strip_h):
     ref, it_o, st_o = oracle.leja_phi(oracle.BURGERS, nx, ny, nu, 0.0, u, 3, w, c, g, h, TOL, TOL, xi_oracle)
     assert st == 0 and st_o == 0 and abs(it - it_o) <= 1
     assert rel(out.cpu().numpy(), ref) <= TOL
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed", "df64"])
+def test_autotune_burgers_contexts(lx, xi_oracle, prec):
+    # the autotuner's timing runs on a Burgers context (point-wise weights),
+    # then a phi_3 call with the selected kernel against the oracle
+    nx, ny, nu = 256, 128, 2e-2
+    ctx = lx.leja_setup(nx, ny, nu, 0.0, lx.BURGERS, getattr(lx, prec.upper()))
+    st, rep = lx.lx_ctx_autotune(ctx, 5, None)
+    assert st == 0 and rep["selected"]["kernel"] == lx.lx_ctx_kernel_name(ctx)
+    u = synth.burgers_ic(nx, ny, seed=8)
+    w = synth.random_field(nx * ny, seed=9)
+    h = 40 * synth.cfl_step(nx, ny, nu, np.abs(u).max())
+    rho, _, _ = oracle.power_iteration(oracle.BURGERS, nx, ny, nu, 0.0, u, synth.power_start(nx * ny, 5), 10)
+    c, g = oracle.spectral_interval(rho)
+    out = torch.empty(nx * ny, dtype=torch.float64, device="cuda")
+    st, it = lx.phi_l_apply(ctx, 3, dev(u), dev(w), out, c, g, h, TOL, TOL)
+    ref, it_o, st_o = oracle.leja_phi(oracle.BURGERS, nx, ny, nu, 0.0, u, 3, w, c, g, h, TOL, TOL, xi_oracle)
+    assert st == 0 and st_o == 0 and abs(it - it_o) <= (3 if prec == "mixed" else 1)
+    assert rel(out.cpu().numpy(), ref) <= (1e-5 if prec == "mixed" else TOL)
 
 
 def test_df64_burgers_rejects_unsupported_layout(lx):
