@@ -172,6 +172,18 @@ lx_status expint_step(lx_ctx* ctx, const double* u_dev, double* u_low_dev, doubl
 lx_status expint_step_host(lx_ctx* ctx, const double* u_host, double* u_low_host, double* u_high_host, double c,
                            double gamma, double h, double rtol, double atol, double* err, int* iters);
 
+/* Time-independent source term S (Sec. 4, the diffusion-advection problem
+ * with sources; any kind): after this call expint_step, expint_step_host
+ * and lx_integrate integrate u' = f(u) + S, i.e. the right-hand side of
+ * every step is h (f(u) + S); the Jacobian, the spectral bound and the
+ * EXPRB32 remainder R = h (F(a) - F(u)) are unchanged (S cancels in R).
+ * For a linear f this makes the Rosenbrock-Euler step
+ * u + h phi_1(h A) (A u + S), the exact solution of the affine problem.
+ * s_dev: device vector of nx*ny doubles, borrowed (it must stay valid and
+ * unchanged while steps run); NULL removes the source.  phi_l_apply is not
+ * affected. */
+lx_status lx_ctx_set_source(lx_ctx* ctx, const double* s_dev);
+
 /* Classical step-size controller for the embedded third-order pair (the
  * paper notes that the EXPRB32 error "may be used to control the step
  * sizes", Sec. 2.2, without giving a controller):
@@ -245,12 +257,13 @@ lx_status lx_ctx_set_graph_unroll(lx_ctx* ctx, int unroll);
 
 /* Autotuner of the fused Leja iteration (a tile-shape search).  Times every
  * candidate kernel of the context's (kind, precision) -- for LX_DF64 the
- * shared-memory-pipelined kernel at 2, 3 and 4 resident blocks per SM and
- * the register-window kernel -- at strip heights 8..128 rows and, for the
+ * shared-memory-pipelined kernel at 2, 3 and 4 resident blocks per SM, the
+ * register-window kernel and the two-step (two Leja iterations per pass
+ * over memory) pipelined kernel -- at strip heights 8..128 rows and, for the
  * pipelined kernels, strip height 0 (one balanced contiguous row range per
  * warp), each for
  * `iters` launches (1..50) on the context's own buffers, and selects the
- * fastest for the vector-access ("wide") class.  cache_path (may be NULL) is
+ * fastest per Leja iteration for the vector-access ("wide") class.  cache_path (may be NULL) is
  * a text file of lines "<device|SMs|nx x ny|kind|precision> <kernel> <strip
  * height> <us>": a matching line is applied without timing, and a new
  * result is appended.  report (may be NULL) receives a JSON summary.  The
@@ -265,6 +278,10 @@ lx_status lx_ctx_select_kernel(lx_ctx* ctx, const char* name, int strip_h);
 /* Kernel selection of the context (for diagnostics): writes a short name of
  * the fused Leja-iteration kernel into buf (NUL-terminated, at most len). */
 lx_status lx_ctx_kernel_name(lx_ctx* ctx, char* buf, int len);
+
+/* Leja iterations per launch of the selected fused-iteration kernel: 1, or 2
+ * for the two-step (temporally blocked) kernels; 0 before any selection. */
+int lx_ctx_iters_per_launch(lx_ctx* ctx);
 
 /* ---------------------------------------------------------------------------
  * Batched instances.  Not in the paper: many independent problems of uneven

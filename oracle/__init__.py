@@ -58,6 +58,12 @@ def lib():
             L.or_exprb32.argtypes = [C.c_int, C.c_int, C.c_int, C.c_double, C.c_double, _dp, C.c_double,
                                      C.c_double, C.c_double, C.c_double, C.c_double, _dp, C.c_int, _dp, _dp,
                                      _dp, _ip]
+            L.or_ros_eu_src.argtypes = [C.c_int, C.c_int, C.c_int, C.c_double, C.c_double, _dp, _dp,
+                                        C.c_double, C.c_double, C.c_double, C.c_double, C.c_double, _dp, C.c_int,
+                                        _dp, _ip]
+            L.or_exprb32_src.argtypes = [C.c_int, C.c_int, C.c_int, C.c_double, C.c_double, _dp, _dp,
+                                         C.c_double, C.c_double, C.c_double, C.c_double, C.c_double, _dp, C.c_int,
+                                         _dp, _dp, _dp, _ip]
             L.or_controller.restype = C.c_double
             L.or_controller.argtypes = [C.c_double, C.c_double, C.c_double]
             L.or_integrate_exprb32.argtypes = [C.c_int, C.c_int, C.c_int, C.c_double, C.c_double, _dp, _dp,
@@ -170,25 +176,28 @@ def leja_phi(kind, nx, ny, nu, a, u, l, w, c, gamma, h, rtol, atol, xi):
     return out, int(it.value), st
 
 
-def ros_eu(kind, nx, ny, nu, a, u, c, gamma, h, rtol, atol, xi):
+def ros_eu(kind, nx, ny, nu, a, u, c, gamma, h, rtol, atol, xi, source=None):
+    """Rosenbrock-Euler step; source: optional time-independent S added to f."""
     u = _f64(u)
     xi = _f64(xi)
+    S = _f64(source) if source is not None else None
     out = np.zeros_like(u)
     it = C.c_int(0)
-    st = lib().or_ros_eu(kind, nx, ny, nu, a, _p(u), c, gamma, h, rtol, atol, _p(xi), len(xi), _p(out),
-                         C.byref(it))
+    st = lib().or_ros_eu_src(kind, nx, ny, nu, a, _p(u), _p(S) if S is not None else None, c, gamma, h, rtol, atol,
+                             _p(xi), len(xi), _p(out), C.byref(it))
     return out, int(it.value), st
 
 
-def exprb32(kind, nx, ny, nu, a, u, c, gamma, h, rtol, atol, xi):
+def exprb32(kind, nx, ny, nu, a, u, c, gamma, h, rtol, atol, xi, source=None):
     u = _f64(u)
     xi = _f64(xi)
+    S = _f64(source) if source is not None else None
     lo = np.zeros_like(u)
     hi = np.zeros_like(u)
     err = np.zeros(1)
     it = C.c_int(0)
-    st = lib().or_exprb32(kind, nx, ny, nu, a, _p(u), c, gamma, h, rtol, atol, _p(xi), len(xi), _p(lo), _p(hi),
-                          _p(err), C.byref(it))
+    st = lib().or_exprb32_src(kind, nx, ny, nu, a, _p(u), _p(S) if S is not None else None, c, gamma, h, rtol,
+                              atol, _p(xi), len(xi), _p(lo), _p(hi), _p(err), C.byref(it))
     return lo, hi, float(err[0]), int(it.value), st
 
 

@@ -271,11 +271,13 @@ void or_burgers_J(int nx, int ny, double nu, const double* u, const double* v, d
 }
 
 /* The operator the Leja basis multiplies by: A for diffusion-advection,
- * J(u) for Burgers. */
+ * J(u) for Burgers.  S (may be NULL): a time-independent source added to
+ * the right-hand side (Problem II of Sec. 4); it does not enter J. */
 typedef struct {
   int kind, nx, ny;
   double nu, a;
   const double* u;
+  const double* S;
 } or_op;
 
 static void op_apply(const or_op* op, const double* v, double* out) {
@@ -285,12 +287,17 @@ static void op_apply(const or_op* op, const double* v, double* out) {
     or_apply_advdiff(op->nx, op->ny, op->nu, op->a, v, out);
 }
 
-/* f(u): A u for diffusion-advection, the Burgers right-hand side otherwise. */
+/* f(u): A u for diffusion-advection, the Burgers right-hand side otherwise,
+ * plus the source S when there is one. */
 static void op_rhs(const or_op* op, const double* u, double* out) {
   if (op->kind == OR_BURGERS)
     or_burgers_f(op->nx, op->ny, op->nu, u, out);
   else
     or_apply_advdiff(op->nx, op->ny, op->nu, op->a, u, out);
+  if (op->S) {
+    long n = (long)op->nx * op->ny;
+    for (long q = 0; q < n; ++q) out[q] = out[q] + op->S[q];
+  }
 }
 
 /* ||x|| = ||x||_2 / sqrt(N) (Sec. 2.2: l2 norm normalised to sqrt(N)). */
@@ -391,11 +398,13 @@ int or_leja_phi(int kind, int nx, int ny, double nu, double a, const double* u, 
 /*   u+ = u + phi_1(h J(u)) h f(u).                                          */
 /* ------------------------------------------------------------------------ */
 
-int or_ros_eu(int kind, int nx, int ny, double nu, double a, const double* u, double c,
-              double gamma, double h, double rtol, double atol, const double* xi, int K,
-              double* u_out, int* iters) {
+/* With a source (Problem II, Sec. 4): f(u) = A u + S, so the step is
+ * u+ = u + phi_1(h A) h (A u + S). */
+int or_ros_eu_src(int kind, int nx, int ny, double nu, double a, const double* u, const double* S,
+                  double c, double gamma, double h, double rtol, double atol, const double* xi, int K,
+                  double* u_out, int* iters) {
   if (nx <= 0 || ny <= 0) return OR_E_INVAL;
-  or_op op = {kind, nx, ny, nu, a, u};
+  or_op op = {kind, nx, ny, nu, a, u, S};
   long n = (long)nx * ny;
   double* f_u = (double*)malloc(sizeof(double) * (size_t)n);
   double* p = (double*)malloc(sizeof(double) * (size_t)n);
@@ -409,6 +418,12 @@ int or_ros_eu(int kind, int nx, int ny, double nu, double a, const double* u, do
   return st;
 }
 
+int or_ros_eu(int kind, int nx, int ny, double nu, double a, const double* u, double c,
+              double gamma, double h, double rtol, double atol, const double* xi, int K,
+              double* u_out, int* iters) {
+  return or_ros_eu_src(kind, nx, ny, nu, a, u, NULL, c, gamma, h, rtol, atol, xi, K, u_out, iters);
+}
+
 /* ------------------------------------------------------------------------ */
 /* EXPRB32 (Sec. 2.3, Listing 13), in the listing's stage order:             */
 /*   a   = u + phi_1(h J(u)) h f(u)                       (lower order)      */
@@ -417,11 +432,11 @@ int or_ros_eu(int kind, int nx, int ny, double nu, double a, const double* u, do
 /*   err = ||2 phi_3(h J(u)) R||                                             */
 /* ------------------------------------------------------------------------ */
 
-int or_exprb32(int kind, int nx, int ny, double nu, double a, const double* u, double c,
-               double gamma, double h, double rtol, double atol, const double* xi, int K,
-               double* u_low, double* u_high, double* err, int* iters) {
+int or_exprb32_src(int kind, int nx, int ny, double nu, double a, const double* u, const double* S,
+                   double c, double gamma, double h, double rtol, double atol, const double* xi, int K,
+                   double* u_low, double* u_high, double* err, int* iters) {
   if (nx <= 0 || ny <= 0) return OR_E_INVAL;
-  or_op op = {kind, nx, ny, nu, a, u};
+  or_op op = {kind, nx, ny, nu, a, u, S};
   long n = (long)nx * ny;
   double* f_u = (double*)malloc(sizeof(double) * (size_t)n);
   double* p1 = (double*)malloc(sizeof(double) * (size_t)n);
@@ -460,6 +475,13 @@ int or_exprb32(int kind, int nx, int ny, double nu, double a, const double* u, d
   *iters = it1 + it2;
   free(f_u); free(p1); free(t1); free(t2); free(nl_u); free(nl_a); free(p3);
   return st != OR_OK ? st : st2;
+}
+
+int or_exprb32(int kind, int nx, int ny, double nu, double a, const double* u, double c,
+               double gamma, double h, double rtol, double atol, const double* xi, int K,
+               double* u_low, double* u_high, double* err, int* iters) {
+  return or_exprb32_src(kind, nx, ny, nu, a, u, NULL, c, gamma, h, rtol, atol, xi, K, u_low, u_high, err,
+                        iters);
 }
 
 /* ------------------------------------------------------------------------ */

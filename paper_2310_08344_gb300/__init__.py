@@ -34,8 +34,10 @@ from .binding import (  # noqa: F401
     lx_ctx_autotune,
     lx_ctx_kernel_name,
     lx_ctx_select_kernel,
+    lx_ctx_iters_per_launch,
     lx_ctx_set_loop_mode,
     lx_ctx_set_graph_unroll,
+    lx_ctx_set_source,
     lx_ctx_stats,
     lx_leja_coeff_count,
     lx_leja_coeffs,

@@ -78,6 +78,7 @@ def lib():
             L.lx_ctx_kernel_name.argtypes = [_vp, C.c_char_p, C.c_int]
             L.lx_ctx_set_loop_mode.argtypes = [_vp, C.c_int]
             L.lx_ctx_set_graph_unroll.argtypes = [_vp, C.c_int]
+            L.lx_ctx_set_source.argtypes = [_vp, _vp]
             L.lx_controller_classical.restype = C.c_double
             L.lx_controller_classical.argtypes = [C.c_double, C.c_double, C.c_double]
             L.lx_integrate.argtypes = [_vp, _vp, _vp, C.c_double, C.c_double, C.c_double, C.c_int,
@@ -101,6 +102,8 @@ def lib():
                                                C.c_double, C.POINTER(LxIntegrateInfo)]
             L.lx_ctx_autotune.argtypes = [_vp, C.c_int, C.c_char_p, C.c_char_p, C.c_int]
             L.lx_ctx_select_kernel.argtypes = [_vp, C.c_char_p, C.c_int]
+            L.lx_ctx_iters_per_launch.argtypes = [_vp]
+            L.lx_ctx_iters_per_launch.restype = C.c_int
             L.phi_l_apply_noalloc.argtypes = [C.POINTER(LxProblem), C.c_int, _vp, _vp, C.c_double, C.c_double,
                                               C.c_double, C.c_double, C.c_double, _vp, _ip]
             _lib = L
@@ -274,6 +277,18 @@ def lx_ctx_set_graph_unroll(ctx: Context, unroll: int) -> int:
     return lib().lx_ctx_set_graph_unroll(ctx.handle, int(unroll))
 
 
+def lx_ctx_set_source(ctx: Context, source) -> int:
+    """Borrow a CUDA float64 tensor of nx*ny values as the source S (None
+    removes it); the context keeps a reference so the tensor stays alive."""
+    if source is None:
+        ctx._source = None
+        return lib().lx_ctx_set_source(ctx.handle, None)
+    if hasattr(source, "numel") and source.numel() != ctx.n:
+        raise ValueError("source must have nx*ny values")
+    ctx._source = source
+    return lib().lx_ctx_set_source(ctx.handle, _dev(source))
+
+
 def phi_l_apply_noalloc(nx, ny, nu, a, l, w, out, c, gamma, h, rtol, atol, stream=None):
     """Allocation-free phi_l(hA)w (diffusion-advection, FP64).  Returns (status, iters)."""
     prob = LxProblem(nx, ny, nu, a, ADVDIFF, FP64)
@@ -295,6 +310,10 @@ def lx_ctx_autotune(ctx: Context, iters=10, cache_path=None):
 
 def lx_ctx_select_kernel(ctx: Context, name: str, strip_h: int) -> int:
     return lib().lx_ctx_select_kernel(ctx.handle, name.encode(), strip_h)
+
+
+def lx_ctx_iters_per_launch(ctx: Context) -> int:
+    return int(lib().lx_ctx_iters_per_launch(ctx.handle))
 
 
 def lx_controller_classical(h, err, tol) -> float:

@@ -375,11 +375,20 @@ static __global__ void df_scale_finish_kernel(LoopState* st) {
 // out = base + (p.h + p.l) 2^k  (base may be NULL): the loop's conversion
 // pass, fused with the Rosenbrock-Euler update u + p when base = u.
 static __global__ void df_output_kernel(long long n, const float2* __restrict__ pdf, const double* __restrict__ base,
-                                        double* __restrict__ out, const LoopState* st) {
+                                        double* __restrict__ out, const LoopState* st, const float2* __restrict__ y0,
+                                        const float2* __restrict__ y1) {
   const int k = __ldcg(&st->kscale);
+  const int fix = __ldcg(&st->fix);
+  const dfv fd = df_from_double(-__ldcg(&st->fix_d));
+  const float2* yb = __ldcg(&st->fix_buf) ? y1 : y0;
   for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < n; q += (long long)gridDim.x * blockDim.x) {
     const float2 t = pdf[q];
-    const double v = f2d_scaled(t.x, k) + f2d_scaled(t.y, k);
+    dfv pv = {t.x, t.y};
+    if (fix) {  // a two-step loop that stopped after its first step
+      const float2 y = yb[q];
+      pv = df_axpy(fd, dfv{y.x, y.y}, pv);
+    }
+    const double v = f2d_scaled(pv.h, k) + f2d_scaled(pv.l, k);
     out[q] = base ? base[q] + v : v;
   }
 }
@@ -388,7 +397,8 @@ static __global__ void df_output_kernel(long long n, const float2* __restrict__ 
 // five stencil points), written as double; also records max exponent of the
 // result for the scaling of the Leja loop that follows.  wf: hi/lo of the
 // five weights h*(wE, wW, wN, wS, wC).  Points whose inputs are outside the
-// float range use double arithmetic.
+// float range use double arithmetic.  src (may be NULL): a time-independent
+// source, added as h * src in double (problem with sources, Sec. 4).
 struct RhsWeights {
   float wf[10];   // hi/lo of h*(wE, wW, wN, wS, wC)
   double wd[5];   // the same weights in double
@@ -396,7 +406,7 @@ struct RhsWeights {
 
 static __global__ void __launch_bounds__(kThreadsPerBlock)
     rhs_df_advdiff_kernel(Geo g, const double* __restrict__ u, RhsWeights W, double* __restrict__ f_out,
-                          LoopState* st) {
+                          LoopState* st, const double* __restrict__ src = nullptr, double h = 0.0) {
   float wh[5], wl[5];
   const double* wd = W.wd;
 #pragma unroll
@@ -424,6 +434,7 @@ static __global__ void __launch_bounds__(kThreadsPerBlock)
     } else {
       r = wd[0] * v[0] + wd[1] * v[1] + wd[2] * v[2] + wd[3] * v[3] + wd[4] * v[4];
     }
+    if (src) r = r + h * __ldg(src + q);
     f_out[q] = r;
     emax = max(emax, (int)((__double2hiint(r) >> 20) & 0x7ff));
   }

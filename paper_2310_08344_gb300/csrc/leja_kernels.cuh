@@ -82,6 +82,9 @@ struct LoopState {
   int sig;                   // df64 form: the stored basis is y_m 2^-sig
   int dlt;                   // df64 form: extra scaling 2^-dlt of the next step
   int launches;              // fused-iteration launches of the call (incl. ones that found done)
+  int fix;                   // two-step loops that stopped at an odd count: p holds one more term,
+  int fix_buf;               //   fix_d * (basis buffer fix_buf), to be subtracted by the output pass
+  double fix_d;
 };
 
 // One thread per launch records it (launches of one loop are stream-ordered).
@@ -350,6 +353,7 @@ static __global__ void set_loop_args_kernel(LoopArgs args, LoopArgs* dst, LoopSt
   st->m = 0;
   st->status = 0;
   st->done = 0;
+  st->fix = 0;
   if (reset_wexp) st->wexp = 0;
   st->kscale = 0;
   st->sig = 0;
@@ -385,20 +389,23 @@ __device__ __forceinline__ void neighbours(const Geo& g, long long q, long long&
 }
 
 // h f(u) into f_out; for Burgers also (u_x + u_y) into s_out.  f_out may be
-// NULL (only s is wanted).
+// NULL (only s is wanted).  src (may be NULL): a time-independent source
+// added to f (the diffusion-advection problem with sources, Sec. 4).
 template <int KIND>
 __global__ void rhs_kernel(Geo g, double nu, double a, double h, const double* __restrict__ u,
-                           double* __restrict__ f_out, double* __restrict__ s_out) {
+                           double* __restrict__ f_out, double* __restrict__ s_out,
+                           const double* __restrict__ src = nullptr) {
   for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < g.n; q += (long long)gridDim.x * blockDim.x) {
     long long e, w, nn, s;
     neighbours(g, q, e, w, nn, s);
     const double uc = u[q], ue = u[e], uw = u[w], un = u[nn], us = u[s];
     const double lap = (ue - 2.0 * uc + uw) * g.idx2 + (un - 2.0 * uc + us) * g.idy2;
     const double grad = (ue - uw) * g.i2dx + (un - us) * g.i2dy;
+    const double sq = src ? src[q] : 0.0;
     if (KIND == 0) {
-      if (f_out) f_out[q] = h * (nu * lap + a * grad);
+      if (f_out) f_out[q] = h * (nu * lap + a * grad + sq);
     } else {
-      if (f_out) f_out[q] = h * (nu * lap - uc * grad);
+      if (f_out) f_out[q] = h * (nu * lap - uc * grad + sq);
       s_out[q] = grad;
     }
   }

@@ -21,6 +21,7 @@
 
 #include "leja_batch.cuh"
 #include "leja_df64.cuh"
+#include "leja_df64_2step.cuh"
 #include "leja_kernels.cuh"
 #include "lexgb_internal.h"
 
@@ -72,6 +73,7 @@ struct Cand {
   int smem;     // dynamic shared memory bytes
   int vec;      // points per lane (warp row = 32 * vec points)
   const char* name;
+  int ipl = 1;  // Leja iterations per launch
 };
 
 struct LoopGraph {
@@ -109,6 +111,7 @@ struct lx_ctx {
   double* d_tune = nullptr; // autotuner: output vector of the timing runs
   float2* d_bq = nullptr;   // df64 Burgers: u / (2 dx gamma) per point
   float2* d_br = nullptr;   // df64 Burgers: diagonal weight per point
+  const double* d_src = nullptr;  // caller's time-independent source (borrowed), or NULL
   double* d_partials = nullptr;
   int partials_cap = 0;
   int stream_loop = 0;  // 1: launch the iterations from the host (profilers)
@@ -155,6 +158,8 @@ std::vector<Cand> candidates(int kind, int precision, int cls) {
   }
   if (precision == LX_DF64) {
     if (wide) {
+      v.push_back(Cand{reinterpret_cast<const void*>(&leja_iter_df_pipe2_kernel<2, 6>), kPipeThreads,
+                       pipe2_smem_bytes<6>(), 4, "leja_iter_df_pipe2_b2_s6", 2});
       v.push_back(Cand{reinterpret_cast<const void*>(&leja_iter_df_pipe_kernel<2>), kPipeThreads, kPipeSmemBytes, 4,
                        "leja_iter_df_pipe_b2"});
       v.push_back(Cand{reinterpret_cast<const void*>(&leja_iter_df_pipe_kernel<3>), kPipeThreads, kPipeSmemBytes, 4,
@@ -167,6 +172,14 @@ std::vector<Cand> candidates(int kind, int precision, int cls) {
                        kPipeSmemBytes8, 4, "leja_iter_df_pipe_b3_s8"});
       v.push_back(Cand{reinterpret_cast<const void*>(&leja_iter_df_advdiff_kernel<4>), kThreadsPerBlock, 0, 4,
                        "leja_iter_df_advdiff_v4"});
+      v.push_back(Cand{reinterpret_cast<const void*>(&leja_iter_df_pipe2_kernel<1, 5>), kPipeThreads,
+                       pipe2_smem_bytes<5>(), 4, "leja_iter_df_pipe2_b1", 2});
+      v.push_back(Cand{reinterpret_cast<const void*>(&leja_iter_df_pipe2_kernel<2, 5>), kPipeThreads,
+                       pipe2_smem_bytes<5>(), 4, "leja_iter_df_pipe2_b2", 2});
+      v.push_back(Cand{reinterpret_cast<const void*>(&leja_iter_df_pipe2_kernel<3, 5>), kPipeThreads,
+                       pipe2_smem_bytes<5>(), 4, "leja_iter_df_pipe2_b3", 2});
+      v.push_back(Cand{reinterpret_cast<const void*>(&leja_iter_df_pipe2_kernel<3, 6>), kPipeThreads,
+                       pipe2_smem_bytes<6>(), 4, "leja_iter_df_pipe2_b3_s6", 2});
     } else {
       v.push_back(Cand{reinterpret_cast<const void*>(&leja_iter_df_advdiff_kernel<1>), kThreadsPerBlock, 0, 1,
                        "leja_iter_df_advdiff_v1"});
@@ -301,9 +314,10 @@ lx_status ensure_graph(lx_ctx* c, int variant) {
     return LX_E_INVAL;
   }
   const Cand k = cands[0];
-  // pipelined kernels (dynamic shared memory) default to 8-row strips: one
-  // strip per warp then gives enough resident warps on mid-size grids
-  return build_loop_graph(c, variant, k, k.smem > 0 ? 8 : c->strip_h);
+  // pipelined kernels (dynamic shared memory) default to 8-row strips (one
+  // strip per warp then gives enough resident warps on mid-size grids), the
+  // two-step kernel to balanced row ranges (its halo rows cost arithmetic)
+  return build_loop_graph(c, variant, k, k.ipl == 2 ? 0 : (k.smem > 0 ? 8 : c->strip_h));
 }
 
 lx_status ensure_coeffs(lx_ctx* c, int slot, int l, double h, double cc, double gamma) {
@@ -432,7 +446,9 @@ lx_status launch_loop(lx_ctx* c, int slot, int l, const double* u, const double*
   LX_CUDA(cudaEventRecord(c->ev[c->ev_used + 1], c->stream));
   c->ev_used += 2;
   if (df) {
-    df_output_kernel<<<aux_blocks(c), kThreadsPerBlock, 0, c->stream>>>(c->n, c->d_pdf, base, out, c->d_state);
+    df_output_kernel<<<aux_blocks(c), kThreadsPerBlock, 0, c->stream>>>(
+        c->n, c->d_pdf, base, out, c->d_state, static_cast<const float2*>(c->d_y[0]),
+        static_cast<const float2*>(c->d_y[1]));
     ++c->stats.kernels;
     LX_CUDA(cudaGetLastError());
   }
@@ -572,7 +588,8 @@ lx_status leja_setup(const lx_problem* prob, int integrator, int max_leja, void*
     c->stream_loop = (env && env[0] == '1') ? 1 : 0;
   }
   c->partials_cap = 64 * c->sm_count;
-  if (!dmalloc((void**)&c->d_partials, sizeof(double) * 2 * c->partials_cap)) return fail(LX_E_NOMEM);
+  // up to four partial sums per block (the two-step kernel)
+  if (!dmalloc((void**)&c->d_partials, sizeof(double) * 4 * c->partials_cap)) return fail(LX_E_NOMEM);
   if (!dmalloc((void**)&c->d_ticket, sizeof(unsigned int))) return fail(LX_E_NOMEM);
   if (!dmalloc((void**)&c->d_state, sizeof(LoopState))) return fail(LX_E_NOMEM);
   if (!dmalloc((void**)&c->d_args, sizeof(LoopArgs))) return fail(LX_E_NOMEM);
@@ -734,7 +751,7 @@ lx_status expint_step(lx_ctx* c, const double* u, double* u_low, double* u_high,
       W.wf[2 * k] = (float)W.wd[k];
       W.wf[2 * k + 1] = (float)(W.wd[k] - (double)W.wf[2 * k]);
     }
-    rhs_df_advdiff_kernel<<<G, kThreadsPerBlock, 0, c->stream>>>(c->geo, u, W, c->d_f, c->d_state);
+    rhs_df_advdiff_kernel<<<G, kThreadsPerBlock, 0, c->stream>>>(c->geo, u, W, c->d_f, c->d_state, c->d_src, h);
     ++c->stats.kernels;
     LX_CUDA(cudaGetLastError());
     st = launch_loop(c, 0, 1, u, c->d_f, u_high, cc, gamma, h, rtol, atol, u, true);
@@ -747,9 +764,9 @@ lx_status expint_step(lx_ctx* c, const double* u, double* u_low, double* u_high,
   }
   // h f(u) and, for Burgers, u_x + u_y at the linearisation point
   if (P.kind == LX_ADVDIFF)
-    rhs_kernel<0><<<G, kThreadsPerBlock, 0, c->stream>>>(c->geo, P.nu, P.a, h, u, c->d_f, c->d_s);
+    rhs_kernel<0><<<G, kThreadsPerBlock, 0, c->stream>>>(c->geo, P.nu, P.a, h, u, c->d_f, c->d_s, c->d_src);
   else
-    rhs_kernel<1><<<G, kThreadsPerBlock, 0, c->stream>>>(c->geo, P.nu, 0.0, h, u, c->d_f, c->d_s);
+    rhs_kernel<1><<<G, kThreadsPerBlock, 0, c->stream>>>(c->geo, P.nu, 0.0, h, u, c->d_f, c->d_s, c->d_src);
   ++c->stats.kernels;
   LX_CUDA(cudaGetLastError());
   if (c->integrator == LX_ROS_EU) {
@@ -822,6 +839,12 @@ lx_status lx_ctx_set_loop_mode(lx_ctx* c, int stream_loop) {
   return LX_OK;
 }
 
+lx_status lx_ctx_set_source(lx_ctx* c, const double* s_dev) {
+  if (!c) return LX_E_INVAL;
+  c->d_src = s_dev;
+  return LX_OK;
+}
+
 lx_status lx_ctx_set_graph_unroll(lx_ctx* c, int unroll) {
   if (!c || unroll < 1 || unroll > 8) return LX_E_INVAL;
   c->graph_unroll = unroll;
@@ -841,6 +864,12 @@ lx_status lx_ctx_kernel_name(lx_ctx* c, char* buf, int len) {
   return LX_OK;
 }
 
+int lx_ctx_iters_per_launch(lx_ctx* c) {
+  if (!c) return 0;
+  const int v = c->loop[kVec2].built ? kVec2 : kVec1;
+  return c->loop[v].built ? c->loop[v].cand.ipl : 0;
+}
+
 }  // extern "C"
 
 namespace {
@@ -857,8 +886,8 @@ std::string tune_key(const lx_ctx* c) {
   return k.str();
 }
 
-// Average time of one fused iteration of candidate k with strip height H on
-// the context's own buffers (zero data; stopping disabled).
+// Average time per Leja iteration of candidate k with strip height H on the
+// context's own buffers (zero data; stopping disabled).
 lx_status tune_time(lx_ctx* c, const Cand& k, int H, int iters, double* us) {
   int grid = 0;
   int gs = grid_for(c, k, H, &grid);
@@ -908,7 +937,7 @@ lx_status tune_time(lx_ctx* c, const Cand& k, int H, int iters, double* us) {
   LX_CUDA(cudaStreamSynchronize(c->stream));
   float ms = 0.f;
   LX_CUDA(cudaEventElapsedTime(&ms, c->ev[0], c->ev[1]));
-  *us = 1e3 * ms / iters;
+  *us = 1e3 * ms / iters / k.ipl;  // per Leja iteration
   return LX_OK;
 }
 
@@ -965,7 +994,7 @@ lx_status lx_ctx_autotune(lx_ctx* c, int iters, const char* cache_path, char* re
   if (c->d_br) LX_CUDA(cudaMemsetAsync(c->d_br, 0, sizeof(float2) * (size_t)c->n, c->stream));
   lx_status st = ensure_coeffs(c, 0, 0, 1.0, -20.0, 10.0);
   if (st != LX_OK) return st;
-  if (c->coef[0].count < iters + 4) return LX_E_INVAL;
+  if (c->coef[0].count < 2 * iters + 4) return LX_E_INVAL;
   const int hs[] = {0, 8, 16, 32, 64, 128};
   double best = 1e30;
   Cand best_k{};

@@ -77,6 +77,25 @@ def burgers_ic(nx: int, ny: int | None = None, seed: int = 1) -> np.ndarray:
     return np.ascontiguousarray(u.reshape(-1))
 
 
+def source_field(nx: int, ny: int | None = None, seed: int = 21) -> np.ndarray:
+    """Time-independent source S of the diffusion-advection problem with
+    sources: two periodic Gaussians of unit height.
+
+    S = sum_{k<2} exp(-|x - c_k|^2_per / s_k), c_k ~ U[0,1)^2,
+    s_k ~ U[0.01, 0.0125] (the squared widths 0.04 and 0.05 of the paper's
+    two source Gaussians on [-1,1]^2, rescaled to the unit square).
+    """
+    ny = nx if ny is None else ny
+    rng = np.random.default_rng(seed)
+    centres = rng.uniform(0.0, 1.0, size=(2, 2))
+    s2 = rng.uniform(0.01, 0.0125, size=2)
+    X, Y = grid(nx, ny)
+    S = np.zeros((ny, nx), dtype=np.float64)
+    for k in range(2):
+        S += np.exp(-_periodic_sq_dist(X, Y, centres[k, 0], centres[k, 1]) / s2[k])
+    return np.ascontiguousarray(S.reshape(-1))
+
+
 def power_start(n_points: int, seed: int = 12345) -> np.ndarray:
     """Start vector of the power iteration: standard normal entries.
 

@@ -180,6 +180,49 @@ def test_expint_step(lx, xi_oracle, kind, integ, n, prec):
             assert abs(err - rerr) <= 1e-6 * rerr
 
 
+@pytest.mark.parametrize("kind,integ,n,prec", [(0, 0, 64, 0), (0, 1, 64, 0), (0, 0, 128, 2), (0, 1, 128, 2),
+                                              (1, 0, 64, 0), (1, 1, 64, 0), (1, 1, 128, 2)])
+def test_expint_step_with_source(lx, xi_oracle, kind, integ, n, prec):
+    # time-independent source S (the paper's problem with sources): every
+    # step integrates u' = f(u) + S
+    if kind == 0:
+        nu, a = 1e-2, 0.5
+        u = synth.gaussians_ic(n, n, seed=8)
+        h = 50 * synth.cfl_step(n, n, nu, a)
+    else:
+        nu, a = 2e-2, 0.0
+        u = synth.burgers_ic(n, n, seed=8)
+        h = 50 * synth.cfl_step(n, n, nu, np.abs(u).max())
+    S = synth.source_field(n, n, seed=22)
+    rho, _, _ = oracle.power_iteration(kind, n, n, nu, a, u if kind == 1 else None,
+                                       synth.power_start(n * n, 5), 10)
+    c, g = oracle.spectral_interval(rho)
+    ctx = lx.leja_setup(n, n, nu, a, kind, prec, integ)
+    Sd = dev(S)
+    assert lx.lx_ctx_set_source(ctx, Sd) == 0
+    lo = torch.empty(n * n, dtype=torch.float64, device="cuda")
+    hi = torch.empty(n * n, dtype=torch.float64, device="cuda")
+    st, err, it = lx.expint_step(ctx, dev(u), lo, hi, c, g, h, TOL, TOL)
+    if integ == 0:
+        ref, it_o, st_o = oracle.ros_eu(kind, n, n, nu, a, u, c, g, h, TOL, TOL, xi_oracle, source=S)
+        assert st == 0 and st_o == 0 and abs(it - it_o) <= 1
+        assert rel(hi.cpu().numpy(), ref) <= TOL
+    else:
+        rlo, rhi, rerr, it_o, st_o = oracle.exprb32(kind, n, n, nu, a, u, c, g, h, TOL, TOL, xi_oracle, source=S)
+        assert st == 0 and st_o == 0 and abs(it - it_o) <= 2
+        assert rel(lo.cpu().numpy(), rlo) <= TOL and rel(hi.cpu().numpy(), rhi) <= TOL
+        if kind == 0:  # affine right-hand side: the remainder is round-off on both sides
+            assert err <= 1e-14 and rerr <= 1e-14
+        else:
+            assert abs(err - rerr) <= 1e-6 * rerr
+    # removing the source gives the source-free step back
+    assert lx.lx_ctx_set_source(ctx, None) == 0
+    st, err, it = lx.expint_step(ctx, dev(u), lo, hi, c, g, h, TOL, TOL)
+    ref0 = (oracle.ros_eu(kind, n, n, nu, a, u, c, g, h, TOL, TOL, xi_oracle)[0] if integ == 0 else
+            oracle.exprb32(kind, n, n, nu, a, u, c, g, h, TOL, TOL, xi_oracle)[1])
+    assert st == 0 and rel(hi.cpu().numpy(), ref0) <= TOL
+
+
 def test_expint_step_host_buffers(lx, xi_oracle):
     n, nu = 64, 2e-2
     u = synth.burgers_ic(n, n, seed=9)
@@ -316,19 +359,24 @@ def test_graph_unroll_is_bitwise_neutral(lx, prec):
         st, it = lx.phi_l_apply(ctx, 1, None, dev(u0), out, c, g, h, TOL, TOL)
         s = lx.lx_ctx_stats(ctx)
         assert st == 0 and s["loop_iterations"] == it
+        ipl = lx.lx_ctx_iters_per_launch(ctx)
         res.append((it, out.cpu().numpy(), s["kernels"]))
     assert lx.lx_ctx_set_graph_unroll(ctx, 0) != 0 and lx.lx_ctx_set_graph_unroll(ctx, 9) != 0
     for it, out, kern in res[1:]:
         assert it == res[0][0] and np.array_equal(out, res[0][1])
     it = res[0][0]
-    # kernels = fixed per-call launches + fused-iteration launches
-    fixed = res[0][2] - it
+    # kernels = fixed per-call launches + fused-iteration launches (ipl Leja
+    # iterations each, rounded up to whole passes of the graph body)
+    work = -(-it // ipl)
+    fixed = res[0][2] - work
     for unroll, (_, _, kern) in zip((3, 8), res[1:]):
-        assert kern - fixed == -(-it // unroll) * unroll
+        assert kern - fixed == -(-work // unroll) * unroll
 
 
+PIPE2_KERNELS = ["leja_iter_df_pipe2_b1", "leja_iter_df_pipe2_b2", "leja_iter_df_pipe2_b2_s6", "leja_iter_df_pipe2_b3",
+                 "leja_iter_df_pipe2_b3_s6"]
 DF64_KERNELS = ["leja_iter_df_pipe_b2", "leja_iter_df_pipe_b3", "leja_iter_df_pipe_b4", "leja_iter_df_pipe_b2_s8",
-                "leja_iter_df_pipe_b3_s8", "leja_iter_df_advdiff_v4"]
+                "leja_iter_df_pipe_b3_s8", "leja_iter_df_advdiff_v4"] + PIPE2_KERNELS
 
 
 @pytest.mark.parametrize("name", DF64_KERNELS)
@@ -355,6 +403,60 @@ def test_df64_candidates_parity(lx, xi_oracle, name, strip_h):
     ref, it_o, st_o = oracle.leja_phi(oracle.ADVDIFF, nx, ny, nu, a, None, 1, u0, c, g, h, TOL, TOL, xi_oracle)
     assert st == 0 and st_o == 0 and abs(it - it_o) <= 1
     assert rel(out.cpu().numpy(), ref) <= TOL
+
+
+@pytest.mark.parametrize("strip_h", [0, 8])
+def test_two_step_kernel_both_stop_parities(lx, xi_oracle, strip_h):
+    # Two Leja iterations per launch: a loop that stops after the first of
+    # the two returns p_{m+1} through the output pass's correction.  Both
+    # parities of the stop index must occur and agree with the one-step
+    # kernel and the oracle.
+    nx, ny, nu, a = 256, 96, 1e-2, 0.5
+    u0 = synth.gaussians_ic(nx, ny, seed=4) + 0.05 * synth.random_field(nx * ny, 16)
+    import fourier
+
+    c, g = oracle.spectral_interval(fourier.spectral_radius(nx, ny, nu, a))
+    one = lx.leja_setup(nx, ny, nu, a, lx.ADVDIFF, lx.DF64)
+    two = lx.leja_setup(nx, ny, nu, a, lx.ADVDIFF, lx.DF64)
+    assert lx.lx_ctx_select_kernel(one, "leja_iter_df_pipe_b2", 8) == 0
+    assert lx.lx_ctx_select_kernel(two, "leja_iter_df_pipe2_b2", strip_h) == 0
+    assert lx.lx_ctx_iters_per_launch(two) == 2 and lx.lx_ctx_iters_per_launch(one) == 1
+    o1 = torch.empty(nx * ny, dtype=torch.float64, device="cuda")
+    o2 = torch.empty_like(o1)
+    parities = set()
+    for l in (0, 1, 3):
+        for cfl in (4, 9, 20, 41):
+            h = cfl * synth.cfl_step(nx, ny, nu, a)
+            st1, it1 = lx.phi_l_apply(one, l, None, dev(u0), o1, c, g, h, TOL, TOL)
+            st2, it2 = lx.phi_l_apply(two, l, None, dev(u0), o2, c, g, h, TOL, TOL)
+            ref, it_o, st_o = oracle.leja_phi(oracle.ADVDIFF, nx, ny, nu, a, None, l, u0, c, g, h, TOL, TOL,
+                                              xi_oracle)
+            assert st1 == st2 == st_o == 0
+            assert abs(it2 - it1) <= 1 and abs(it2 - it_o) <= 1
+            assert rel(o2.cpu().numpy(), ref) <= TOL
+            if it1 == it2:
+                assert rel(o2.cpu().numpy(), o1.cpu().numpy()) <= 1e-13
+            parities.add(it2 % 2)
+    assert parities == {0, 1}
+
+
+@pytest.mark.parametrize("kmax_pts", [16, 17])
+def test_two_step_kernel_statuses(lx, kmax_pts):
+    nx, ny, nu, a = 128, 64, 1e-2, 1.0
+    u0, h, c, g = advdiff_case(nx, ny, nu, a, 1)
+    ctx = lx.leja_setup(nx, ny, nu, a, lx.ADVDIFF, lx.DF64, max_leja=kmax_pts)
+    assert lx.lx_ctx_select_kernel(ctx, "leja_iter_df_pipe2_b2", 8) == 0
+    out = torch.empty(nx * ny, dtype=torch.float64, device="cuda")
+    st, it = lx.phi_l_apply(ctx, 0, None, dev(u0), out, c, g, h, TOL, TOL)
+    assert st == 4 and it == kmax_pts - 1  # LX_E_NOCONV at the last coefficient, either parity
+    bad = u0.copy()
+    bad[77] = np.nan
+    ctx2 = lx.leja_setup(nx, ny, nu, a, lx.ADVDIFF, lx.DF64)
+    assert lx.lx_ctx_select_kernel(ctx2, "leja_iter_df_pipe2_b2", 8) == 0
+    st, it = lx.phi_l_apply(ctx2, 0, None, dev(bad), out, c, g, h, TOL, TOL)
+    assert st == 5 and it == 1
+    st, it = lx.phi_l_apply(ctx2, 0, None, dev(u0), out, c, g, h, TOL, TOL)
+    assert st == 0
 
 
 def test_autotune_selects_and_caches(lx, xi_oracle, tmp_path):

@@ -172,6 +172,50 @@ def test_exprb32_linear_has_zero_remainder():
     assert err == 0.0 and np.array_equal(lo, hi)
 
 
+def _exact_with_source(n, nu, a, h, u0, S):
+    # u' = A u + S over one step h, mode by mode: exp(h lam) u^ + h phi_1(h lam) S^
+    from fourier import phi_complex, symbol
+
+    lam = symbol(n, n, nu, a)
+    U = np.fft.fft2(u0.reshape(n, n))
+    Sh = np.fft.fft2(S.reshape(n, n))
+    return np.real(np.fft.ifft2(np.exp(h * lam) * U + h * phi_complex(1, h * lam) * Sh)).reshape(-1)
+
+
+@pytest.mark.parametrize("seed", [1, 2])
+def test_ros_eu_with_source_is_exact_for_linear_problem(seed):
+    # Problem II of Sec. 4: with f(u) = A u + S the Rosenbrock-Euler step is
+    # the exact solution of the linear ODE with a constant source
+    n, nu, a = 64, 1e-2, 1.0
+    u0, h, c, gamma = _cfg1(seed, n=n)
+    S = synth.source_field(n, n, seed=20 + seed)
+    xi = oracle.leja_points(400)
+    out, iters, st = oracle.ros_eu(oracle.ADVDIFF, n, n, nu, a, u0, c, gamma, h, TOL, TOL, xi, source=S)
+    assert st == oracle.OK
+    ref = _exact_with_source(n, nu, a, h, u0, S)
+    assert rel_l2(out, ref) <= 100 * TOL
+    # without the source the step differs by h phi_1(hA) S, which is not small
+    plain, _, _ = oracle.ros_eu(oracle.ADVDIFF, n, n, nu, a, u0, c, gamma, h, TOL, TOL, xi)
+    assert rel_l2(plain, ref) > 1e-2
+
+
+def test_source_mean_growth_and_exprb32_remainder():
+    # 1^T A = 0, so the mean grows by exactly h mean(S) per step; and the
+    # EXPRB32 remainder stays 0 for an affine right-hand side
+    n, nu, a = 48, 1e-2, 0.7
+    u0, h, c, gamma = _cfg1(3, n=n, a=a)
+    S = synth.source_field(n, n, seed=31)
+    xi = oracle.leja_points(400)
+    out, _, st = oracle.ros_eu(oracle.ADVDIFF, n, n, nu, a, u0, c, gamma, h, TOL, TOL, xi, source=S)
+    assert st == oracle.OK
+    assert abs((out.mean() - u0.mean()) - h * S.mean()) <= 1e-12 * (abs(h * S.mean()) + abs(u0.mean()))
+    lo, hi, err, it, st = oracle.exprb32(oracle.ADVDIFF, n, n, nu, a, u0, c, gamma, h, TOL, TOL, xi, source=S)
+    # F(k) = (A k + S) - A k is S up to the rounding of the two sums, so R
+    # and the error estimate vanish to round-off only
+    assert st == oracle.OK and err <= 1e-15 * np.linalg.norm(u0) and rel_l2(hi, lo) <= 1e-15
+    assert np.array_equal(lo, out)
+
+
 def _burgers_run(step, u0, n, nu, T, nsteps, xi, tol=1e-13):
     h = T / nsteps
     u = u0.copy()
