@@ -151,6 +151,27 @@ lx_status power_bound(lx_ctx* ctx, const double* u_dev, const double* v0_dev, in
 lx_status phi_l_apply(lx_ctx* ctx, int l, const double* u_dev, const double* w_dev, double* out_dev, double c,
                       double gamma, double h, double rtol, double atol, int* iters);
 
+/* "Vertical" interpolation (Sec. 2.3, real_Leja_phi with several integrator
+ * coefficients): out[j] = phi_l(alpha[j] h J) w for j < nc (1..4) from ONE
+ * Newton basis at the same Leja points, shift cc and scale gamma -- only the
+ * divided differences (of phi_l(alpha_j h (cc + gamma xi))) differ per j, so
+ * one fused launch per iteration moves y once and the nc polynomials once.
+ * The loop stops at the first iteration at which every polynomial passes its
+ * own test |d^(j)_{m+1}| ||y_{m+1}|| <= rtol ||p^(j)|| + atol (the paper
+ * states no rule for several polynomials; this is the reading used), so
+ * *iters is at least the largest single-alpha count.
+ *   alpha: host array of nc step fractions, each > 0 (typically <= 1; the
+ *          table length follows the largest one);
+ *   out:   host array of nc distinct device pointers (nx*ny doubles each, not
+ *          aliasing u or w);
+ *   u, w, cc, gamma, h, rtol, atol: as in phi_l_apply.
+ * LX_DF64 contexts need nx % 128 == 0 and a 16-byte aligned w (else
+ * LX_E_INVAL).  Buffers for the nc polynomials are allocated on first use
+ * and kept until leja_destroy. */
+lx_status phi_l_apply_vertical(lx_ctx* ctx, int l, int nc, const double* alpha, const double* u,
+                               const double* w, double* const* out, double cc, double gamma, double h,
+                               double rtol, double atol, int* iters);
+
 /* One step of the context's integrator (Sec. 2.2 Listings 5-6; Sec. 2.3
  * Listings 12-13):
  *   LX_ROS_EU   u_high = u + phi_1(h J(u)) h f(u); u_low unused (may be

@@ -58,6 +58,9 @@ def lib():
             L.or_exprb32.argtypes = [C.c_int, C.c_int, C.c_int, C.c_double, C.c_double, _dp, C.c_double,
                                      C.c_double, C.c_double, C.c_double, C.c_double, _dp, C.c_int, _dp, _dp,
                                      _dp, _ip]
+            L.or_leja_phi_vertical.argtypes = [C.c_int, C.c_int, C.c_int, C.c_double, C.c_double, _dp, C.c_int,
+                                               C.c_int, _dp, _dp, C.c_double, C.c_double, C.c_double, C.c_double,
+                                               C.c_double, _dp, C.c_int, _dp, _ip]
             L.or_ros_eu_src.argtypes = [C.c_int, C.c_int, C.c_int, C.c_double, C.c_double, _dp, _dp,
                                         C.c_double, C.c_double, C.c_double, C.c_double, C.c_double, _dp, C.c_int,
                                         _dp, _ip]
@@ -173,6 +176,20 @@ def leja_phi(kind, nx, ny, nu, a, u, l, w, c, gamma, h, rtol, atol, xi):
     it = C.c_int(0)
     st = lib().or_leja_phi(kind, nx, ny, nu, a, _p(u), l, _p(w), c, gamma, h, rtol, atol, _p(xi), len(xi),
                            _p(out), C.byref(it))
+    return out, int(it.value), st
+
+
+def leja_phi_vertical(kind, nx, ny, nu, a, u, l, alphas, w, c, gamma, h, rtol, atol, xi):
+    """phi_l(alpha_j h Op) w for every alpha_j from one Newton basis; returns
+    (outputs [nc, n], iters, status)."""
+    w = _f64(w)
+    xi = _f64(xi)
+    al = _f64(alphas)
+    u = _f64(u) if u is not None else None
+    out = np.zeros((len(al), w.size))
+    it = C.c_int(0)
+    st = lib().or_leja_phi_vertical(kind, nx, ny, nu, a, _p(u), l, len(al), _p(al), _p(w), c, gamma, h, rtol, atol,
+                                    _p(xi), len(xi), out.ctypes.data_as(_dp), C.byref(it))
     return out, int(it.value), st
 
 

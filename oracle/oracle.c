@@ -394,6 +394,66 @@ int or_leja_phi(int kind, int nx, int ny, double nu, double a, const double* u, 
 }
 
 /* ------------------------------------------------------------------------ */
+/* "Vertical" interpolation (Sec. 2.3, real_Leja_phi with several integrator */
+/* coefficients): phi_l(alpha_j h Op) w for nc step fractions alpha_j from   */
+/* one Newton basis.  The nodes, the shift c and the scale gamma are shared, */
+/* so y_m is the same for every j; only the divided differences differ:      */
+/*   d^(j)_k = f_j[xi_0..xi_k],  f_j(xi) = phi_l(alpha_j h (c + gamma xi)),  */
+/*   p^(j)_{m+1} = p^(j)_m + d^(j)_{m+1} y_{m+1}.                            */
+/* The paper does not state the stop rule; the reading is that the loop     */
+/* stops at the first m at which every polynomial passes its own test        */
+/* |d^(j)_{m+1}| ||y_{m+1}|| <= rtol ||p^(j)_{m+1}|| + atol.                 */
+/* out: nc vectors of n values, polynomial j at out + j n.                   */
+/* ------------------------------------------------------------------------ */
+
+int or_leja_phi_vertical(int kind, int nx, int ny, double nu, double a, const double* u, int l, int nc,
+                         const double* alpha, const double* w, double c, double gamma, double h,
+                         double rtol, double atol, const double* xi, int K, double* out, int* iters) {
+  if (nx <= 0 || ny <= 0 || l < 0 || gamma == 0.0 || nc < 1 || K < 2) return OR_E_INVAL;
+  or_op op = {kind, nx, ny, nu, a, u};
+  long n = (long)nx * ny;
+  double* d = (double*)malloc(sizeof(double) * (size_t)K * (size_t)nc);
+  double* y = (double*)malloc(sizeof(double) * (size_t)n);
+  double* t = (double*)malloc(sizeof(double) * (size_t)n);
+  if (!d || !y || !t) { free(d); free(y); free(t); return OR_E_NOMEM; }
+  for (int j = 0; j < nc; ++j) or_leja_coeffs(l, alpha[j] * h, c, gamma, xi, K, d + (size_t)j * K);
+  for (long q = 0; q < n; ++q) y[q] = w[q];
+  for (int j = 0; j < nc; ++j)
+    for (long q = 0; q < n; ++q) out[(size_t)j * n + q] = d[(size_t)j * K] * w[q];
+  int status = OR_E_NOCONV;
+  *iters = K - 1;
+  for (int m = 0; m + 1 < K; ++m) {
+    op_apply(&op, y, t);
+    for (long q = 0; q < n; ++q) y[q] = (t[q] - c * y[q]) / gamma - xi[m] * y[q];
+    double yn = nrm(y, n);
+    int all_pass = 1, finite = isfinite(yn);
+    for (int j = 0; j < nc; ++j) {
+      double* p = out + (size_t)j * n;
+      double dj = d[(size_t)j * K + m + 1];
+      for (long q = 0; q < n; ++q) p[q] = p[q] + dj * y[q];
+      double e = fabs(dj) * yn;
+      double pn = nrm(p, n);
+      if (!isfinite(e) || !isfinite(pn)) finite = 0;
+      if (!(e <= rtol * pn + atol)) all_pass = 0;
+    }
+    if (!finite) {
+      *iters = m + 1;
+      status = OR_E_NONFINITE;
+      break;
+    }
+    if (all_pass) {
+      *iters = m + 1;
+      status = OR_OK;
+      break;
+    }
+  }
+  free(d);
+  free(y);
+  free(t);
+  return status;
+}
+
+/* ------------------------------------------------------------------------ */
 /* Exponential Rosenbrock-Euler (Sec. 2.3, Listing 12):                      */
 /*   u+ = u + phi_1(h J(u)) h f(u).                                          */
 /* ------------------------------------------------------------------------ */

@@ -38,6 +38,7 @@ from .binding import (  # noqa: F401
     lx_ctx_set_loop_mode,
     lx_ctx_set_graph_unroll,
     lx_ctx_set_source,
+    phi_l_apply_vertical,
     lx_ctx_stats,
     lx_leja_coeff_count,
     lx_leja_coeffs,

@@ -70,6 +70,8 @@ def lib():
             L.power_bound.argtypes = [_vp, _vp, _vp, C.c_int, _dp, _ip]
             L.phi_l_apply.argtypes = [_vp, C.c_int, _vp, _vp, _vp, C.c_double, C.c_double, C.c_double, C.c_double,
                                       C.c_double, _ip]
+            L.phi_l_apply_vertical.argtypes = [_vp, C.c_int, C.c_int, _dp, _vp, _vp, C.POINTER(C.c_void_p),
+                                               C.c_double, C.c_double, C.c_double, C.c_double, C.c_double, _ip]
             L.expint_step.argtypes = [_vp, _vp, _vp, _vp, C.c_double, C.c_double, C.c_double, C.c_double,
                                       C.c_double, _dp, _ip]
             L.expint_step_host.argtypes = [_vp, _vp, _vp, _vp, C.c_double, C.c_double, C.c_double, C.c_double,
@@ -233,6 +235,19 @@ def phi_l_apply(ctx: Context, l, u, w, out, c, gamma, h, rtol, atol):
     """Returns (status, iters)."""
     it = C.c_int(0)
     st = lib().phi_l_apply(ctx.handle, l, _dev(u), _dev(w), _dev(out), c, gamma, h, rtol, atol, C.byref(it))
+    return st, it.value
+
+
+def phi_l_apply_vertical(ctx: Context, l, alphas, u, w, outs, c, gamma, h, rtol, atol):
+    """phi_l(alpha_j h J) w into outs[j] for every alpha_j, one Newton basis.
+    Returns (status, iters)."""
+    al = np.ascontiguousarray(alphas, dtype=np.float64)
+    if len(outs) != al.size:
+        raise ValueError("one output per alpha")
+    ptrs = (C.c_void_p * al.size)(*[_dev(o) for o in outs])
+    it = C.c_int(0)
+    st = lib().phi_l_apply_vertical(ctx.handle, l, al.size, al.ctypes.data_as(_dp), _dev(u), _dev(w), ptrs, c,
+                                    gamma, h, rtol, atol, C.byref(it))
     return st, it.value
 
 

@@ -85,6 +85,10 @@ __device__ __forceinline__ dfv df_split_scaled(double x, int k) {
   return r;
 }
 
+// Rare path of f2d_scaled, kept out of line so that the compiler branches
+// around it instead of evaluating it (on the FP64 pipe) for every value.
+static __device__ __noinline__ double f2d_scaled_slow(float f, int k) { return (double)f * pow2(k); }
+
 // Exact float -> double by integer operations (zero and subnormals -> 0;
 // infinities and NaN through the conversion instruction), then scaled by 2^k
 // through the exponent field when that stays in range.
@@ -93,7 +97,7 @@ __device__ __forceinline__ double f2d_scaled(float f, int k) {
   const int e = (int)((b >> 23) & 0xffu);
   if (e == 0) return 0.0;
   const int ed = e + 896 + k;
-  if (e == 0xff || ed < 1 || ed > 2046) return (double)f * pow2(k);
+  if (e == 0xff || ed < 1 || ed > 2046) return f2d_scaled_slow(f, k);
   const unsigned long long db = ((unsigned long long)(b & 0x80000000u) << 32) | ((unsigned long long)ed << 52) |
                                 ((unsigned long long)(b & 0x7fffffu) << 29);
   return __longlong_as_double((long long)db);
@@ -613,6 +617,140 @@ __device__ __forceinline__ void df_strip_pipe(const LoopArgs& A, const S* __rest
   }
   cp_wait<0>();
   __syncwarp();
+}
+
+// h A u (+ h S) for the diffusion-advection operator when nx % 128 == 0 and
+// u, f_out, src are 16-byte aligned: warps take balanced row ranges of
+// 128-column strips; each lane keeps 4 consecutive points of three rows in
+// registers (two rows loaded ahead), so every value of u is loaded and split
+// into floats once, and loads and stores are 16 bytes wide.  A row whose
+// inputs include a value outside the float range is computed in double by
+// the whole warp.  Records the largest exponent of the result like
+// rhs_df_advdiff_kernel.
+__device__ __forceinline__ bool df_in_range(double x) {
+  const int ex = (int)((__double_as_longlong(x) >> 52) & 0x7ff);
+  return ex == 0 || (ex > 1023 - 100 && ex < 1023 + 100);
+}
+
+static __global__ void __launch_bounds__(kThreadsPerBlock)
+    rhs_df_advdiff_rows_kernel(int nx, int ny, const double* __restrict__ u, RhsWeights W,
+                               double* __restrict__ f_out, LoopState* st, const double* __restrict__ src, double h) {
+  float wh[5], wl[5];
+  const double* wd = W.wd;
+#pragma unroll
+  for (int k = 0; k < 5; ++k) {
+    wh[k] = W.wf[2 * k];
+    wl[k] = W.wf[2 * k + 1];
+  }
+  const int lane = threadIdx.x & 31;
+  const int warp = threadIdx.x >> 5;
+  int emax = 0;
+  struct Row {
+    double v[4];
+    dfv f[4];   // v split into float pairs (meaningless where v is out of the float range)
+    double hx;  // lane 0: west halo point, lane 31: east halo point
+    bool ok;    // every value of this lane's part of the row is in the float range
+  };
+  for_each_segment(nx, ny, 0, blockIdx.x * kWarpsPerBlock + warp, gridDim.x * kWarpsPerBlock,
+                   [&](int col0, int r0, int r1) {
+    const int c = col0 + lane * 4;
+    const int cw = col0 == 0 ? nx - 1 : col0 - 1;
+    const int ce = (col0 + kPipeRow >= nx) ? 0 : col0 + kPipeRow;
+    auto load = [&](int r, Row& R) {
+      r = r < 0 ? r + ny : (r >= ny ? r - ny : r);
+      const double* row = u + (size_t)r * nx;
+      const double2 a = __ldg(reinterpret_cast<const double2*>(row + c));
+      const double2 b = __ldg(reinterpret_cast<const double2*>(row + c + 2));
+      R.v[0] = a.x;
+      R.v[1] = a.y;
+      R.v[2] = b.x;
+      R.v[3] = b.y;
+      R.hx = lane == 0 ? __ldg(row + cw) : (lane == 31 ? __ldg(row + ce) : 0.0);
+      R.ok = df_in_range(R.hx);
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        R.ok = R.ok && df_in_range(R.v[k]);
+        R.f[k] = df_split_scaled(R.v[k], 0);
+      }
+    };
+    Row S, C, N, NN;
+    load(r0 - 1, S);
+    load(r0, C);
+    load(r0 + 1, N);
+    for (int r = r0; r < r1; ++r) {
+      if (r + 1 < r1) load(r + 2, NN);
+      const double xw0 = __shfl_up_sync(0xffffffffu, C.v[3], 1);
+      const double xe0 = __shfl_down_sync(0xffffffffu, C.v[0], 1);
+      const double xw = lane == 0 ? C.hx : xw0;
+      const double xe = lane == 31 ? C.hx : xe0;
+      double res[4];
+      if (__all_sync(0xffffffffu, S.ok && C.ok && N.ok)) {
+        const dfv dw = lane == 0 ? df_split_scaled(xw, 0) : shfl_up_df(C.f[3]);
+        const dfv de = lane == 31 ? df_split_scaled(xe, 0) : shfl_down_df(C.f[0]);
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+          const dfv t[5] = {k == 3 ? de : C.f[k + 1], k == 0 ? dw : C.f[k - 1], N.f[k], S.f[k], C.f[k]};
+          const dfv d = df_dot5(wh, wl, t);
+          res[k] = f2d_scaled(d.h, 0) + f2d_scaled(d.l, 0);
+        }
+      } else {
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+          const double e = k == 3 ? xe : C.v[k + 1], w = k == 0 ? xw : C.v[k - 1];
+          res[k] = wd[0] * e + wd[1] * w + wd[2] * N.v[k] + wd[3] * S.v[k] + wd[4] * C.v[k];
+        }
+      }
+      const size_t ro = (size_t)r * nx + c;
+      if (src) {
+        const double2 s0 = __ldg(reinterpret_cast<const double2*>(src + ro));
+        const double2 s1 = __ldg(reinterpret_cast<const double2*>(src + ro + 2));
+        res[0] = res[0] + h * s0.x;
+        res[1] = res[1] + h * s0.y;
+        res[2] = res[2] + h * s1.x;
+        res[3] = res[3] + h * s1.y;
+      }
+      *reinterpret_cast<double2*>(f_out + ro) = make_double2(res[0], res[1]);
+      *reinterpret_cast<double2*>(f_out + ro + 2) = make_double2(res[2], res[3]);
+#pragma unroll
+      for (int k = 0; k < 4; ++k) emax = max(emax, (int)((__double2hiint(res[k]) >> 20) & 0x7ff));
+      S = C;
+      C = N;
+      N = NN;
+    }
+  });
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) emax = max(emax, __shfl_xor_sync(0xffffffffu, emax, o));
+  if (lane == 0) atomicMax(&st->wexp, emax);
+}
+
+// p as float pairs -> double (times 2^kscale), plus base when given; two
+// points per step with 16-byte accesses (n even, base and out 16-byte
+// aligned).  Same semantics as df_output_kernel, including the correction of
+// a two-step loop that stopped after its first iteration.
+static __global__ void __launch_bounds__(kThreadsPerBlock)
+    df_output2_kernel(long long n2, const float4* __restrict__ pdf, const double2* __restrict__ base,
+                      double2* __restrict__ out, const LoopState* st, const float4* __restrict__ y0,
+                      const float4* __restrict__ y1) {
+  const int k = __ldcg(&st->kscale);
+  const int fix = __ldcg(&st->fix);
+  const dfv fd = df_from_double(-__ldcg(&st->fix_d));
+  const float4* yb = __ldcg(&st->fix_buf) ? y1 : y0;
+  for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < n2; q += (long long)gridDim.x * blockDim.x) {
+    const float4 t = pdf[q];
+    dfv a = {t.x, t.y}, b = {t.z, t.w};
+    if (fix) {
+      const float4 y = yb[q];
+      a = df_axpy(fd, dfv{y.x, y.y}, a);
+      b = df_axpy(fd, dfv{y.z, y.w}, b);
+    }
+    double2 r = make_double2(f2d_scaled(a.h, k) + f2d_scaled(a.l, k), f2d_scaled(b.h, k) + f2d_scaled(b.l, k));
+    if (base) {
+      const double2 bb = base[q];
+      r.x = bb.x + r.x;
+      r.y = bb.y + r.y;
+    }
+    out[q] = r;
+  }
 }
 
 template <int MINB, int STAGES = kPipeStages>

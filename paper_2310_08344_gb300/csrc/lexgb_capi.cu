@@ -24,6 +24,7 @@
 #include "leja_df64_2step.cuh"
 #include "leja_kernels.cuh"
 #include "lexgb_internal.h"
+#include "lexgb_vertical.h"
 
 using namespace lexgb;
 
@@ -123,6 +124,13 @@ struct lx_ctx {
   LoopState* h_state = nullptr;  // pinned
 
   LoopGraph loop[kNumVariants];
+  // vertical interpolation (lazily allocated): argument block, one
+  // coefficient table of K doubles per polynomial, df64 polynomials beyond
+  // the first (which uses d_pdf), and the loop graphs by class and count
+  VertArgs* d_vargs = nullptr;
+  double* d_vcoef = nullptr;
+  float2* d_pdfv[kMaxVertical] = {};
+  LoopGraph vloop[kNumVariants][kMaxVertical];
   int aux_grid = 0;
 
   cudaEvent_t ev[8] = {};
@@ -338,17 +346,14 @@ lx_status ensure_coeffs(lx_ctx* c, int slot, int l, double h, double cc, double 
   return LX_OK;
 }
 
-// One Leja loop.  df64 form only: `base` (may be NULL) is added to the
-// output in the conversion pass, and wexp_known says that the kernel that
-// wrote w has already recorded its largest exponent.
-lx_status launch_loop(lx_ctx* c, int slot, int l, const double* u, const double* w, double* out, double cc,
-                      double gamma, double h, double rtol, double atol, const double* base = nullptr,
-                      bool wexp_known = false) {
-  lx_status st = ensure_coeffs(c, slot, l, h, cc, gamma);
-  if (st != LX_OK) return st;
-  const int variant = choose_variant(c, w, out);
-  st = ensure_graph(c, variant);
-  if (st != LX_OK) return st;
+// Loop arguments of one Leja loop (operator weights for the interval
+// (c, gamma), tolerances, buffers) and the per-loop preparation kernels: the
+// df64 Burgers point weights, the argument upload and state reset, and the
+// df64 input scaling (wexp_known: the kernel that wrote w has already
+// recorded its largest exponent).  d: divided differences with kmax + 1
+// entries.
+lx_status prepare_loop(lx_ctx* c, int strip_h, int kmax, const double* d, const double* u, const double* w,
+                       double* out, double cc, double gamma, double rtol, double atol, bool wexp_known) {
   const lx_problem& P = c->prob;
   const double dx = 1.0 / P.nx, dy = 1.0 / P.ny;
   const double ig = 1.0 / gamma;
@@ -357,8 +362,8 @@ lx_status launch_loop(lx_ctx* c, int slot, int l, const double* u, const double*
   a.nx = P.nx;
   a.ny = P.ny;
   a.n = c->n;
-  a.strip_h = c->loop[variant].strip_h;
-  a.kmax = c->coef[slot].count - 1;
+  a.strip_h = strip_h;
+  a.kmax = kmax;
   a.w = w;
   a.y0 = c->d_y[0];
   a.y1 = c->d_y[1];
@@ -366,7 +371,7 @@ lx_status launch_loop(lx_ctx* c, int slot, int l, const double* u, const double*
   a.u = u;
   a.s = c->d_s;
   a.xi = c->d_xi;
-  a.d = c->coef[slot].dev;
+  a.d = d;
   const double nx2 = P.nu / (dx * dx), ny2 = P.nu / (dy * dy);
   if (P.kind == LX_ADVDIFF) {
     a.wxp = (nx2 + P.a / (2 * dx)) * ig;
@@ -418,6 +423,24 @@ lx_status launch_loop(lx_ctx* c, int slot, int l, const double* u, const double*
     ++c->stats.kernels;
     LX_CUDA(cudaGetLastError());
   }
+  return LX_OK;
+}
+
+// One Leja loop.  df64 form only: `base` (may be NULL) is added to the
+// output in the conversion pass, and wexp_known says that the kernel that
+// wrote w has already recorded its largest exponent.
+lx_status launch_loop(lx_ctx* c, int slot, int l, const double* u, const double* w, double* out, double cc,
+                      double gamma, double h, double rtol, double atol, const double* base = nullptr,
+                      bool wexp_known = false) {
+  lx_status st = ensure_coeffs(c, slot, l, h, cc, gamma);
+  if (st != LX_OK) return st;
+  const int variant = choose_variant(c, w, out);
+  st = ensure_graph(c, variant);
+  if (st != LX_OK) return st;
+  st = prepare_loop(c, c->loop[variant].strip_h, c->coef[slot].count - 1, c->coef[slot].dev, u, w, out, cc, gamma,
+                    rtol, atol, wexp_known);
+  if (st != LX_OK) return st;
+  const bool df = c->prob.precision == LX_DF64;
   if (c->ev_used + 2 > 8) return LX_E_INVAL;
   LX_CUDA(cudaEventRecord(c->ev[c->ev_used], c->stream));
   if (!c->stream_loop) {
@@ -434,7 +457,7 @@ lx_status launch_loop(lx_ctx* c, int slot, int l, const double* u, const double*
     unsigned int* ticket = c->d_ticket;
     cudaGraphConditionalHandle cond = 0;
     void* kargs[] = {(void*)&args, (void*)&stp, (void*)&partials, (void*)&ticket, (void*)&cond};
-    for (int it = 0; it < a.kmax; it += 8) {
+    for (int it = 0; it < c->coef[slot].count - 1; it += 8) {
       for (int k = 0; k < 8; ++k)
         LX_CUDA(cudaLaunchKernel(L.cand.func, dim3(L.grid), dim3(L.cand.threads), kargs, L.cand.smem, c->stream));
       c->stats.kernels += 8;
@@ -445,7 +468,17 @@ lx_status launch_loop(lx_ctx* c, int slot, int l, const double* u, const double*
   }
   LX_CUDA(cudaEventRecord(c->ev[c->ev_used + 1], c->stream));
   c->ev_used += 2;
-  if (df) {
+  if (df && c->n % 2 == 0 && aligned16(out) && (!base || aligned16(base))) {
+    const long long n2 = c->n / 2;
+    const int G2 = (int)std::max<long long>(1, std::min<long long>((n2 + kThreadsPerBlock - 1) / kThreadsPerBlock,
+                                                                   8LL * c->sm_count));
+    df_output2_kernel<<<G2, kThreadsPerBlock, 0, c->stream>>>(
+        n2, reinterpret_cast<const float4*>(c->d_pdf), reinterpret_cast<const double2*>(base),
+        reinterpret_cast<double2*>(out), c->d_state, static_cast<const float4*>(c->d_y[0]),
+        static_cast<const float4*>(c->d_y[1]));
+    ++c->stats.kernels;
+    LX_CUDA(cudaGetLastError());
+  } else if (df) {
     df_output_kernel<<<aux_blocks(c), kThreadsPerBlock, 0, c->stream>>>(
         c->n, c->d_pdf, base, out, c->d_state, static_cast<const float2*>(c->d_y[0]),
         static_cast<const float2*>(c->d_y[1]));
@@ -513,6 +546,11 @@ const char* lx_last_cuda_error(void) { return g_last_cuda_error.c_str(); }
 void leja_destroy(lx_ctx* c) {
   if (!c) return;
   for (auto& L : c->loop) destroy_graph(L);
+  for (auto& row : c->vloop)
+    for (auto& L : row) destroy_graph(L);
+  cudaFree(c->d_vargs);
+  cudaFree(c->d_vcoef);
+  for (int j = 1; j < kMaxVertical; ++j) cudaFree(c->d_pdfv[j]);
   for (auto& S : c->coef) {
     if (S.dev) cudaFree(S.dev);
     if (S.host) cudaFreeHost(S.host);
@@ -588,8 +626,10 @@ lx_status leja_setup(const lx_problem* prob, int integrator, int max_leja, void*
     c->stream_loop = (env && env[0] == '1') ? 1 : 0;
   }
   c->partials_cap = 64 * c->sm_count;
-  // up to four partial sums per block (the two-step kernel)
-  if (!dmalloc((void**)&c->d_partials, sizeof(double) * 4 * c->partials_cap)) return fail(LX_E_NOMEM);
+  // up to 1 + kMaxVertical partial sums per block (vertical loops; the
+  // two-step kernel uses four)
+  if (!dmalloc((void**)&c->d_partials, sizeof(double) * (1 + kMaxVertical) * c->partials_cap))
+    return fail(LX_E_NOMEM);
   if (!dmalloc((void**)&c->d_ticket, sizeof(unsigned int))) return fail(LX_E_NOMEM);
   if (!dmalloc((void**)&c->d_state, sizeof(LoopState))) return fail(LX_E_NOMEM);
   if (!dmalloc((void**)&c->d_args, sizeof(LoopArgs))) return fail(LX_E_NOMEM);
@@ -723,6 +763,170 @@ lx_status phi_l_apply(lx_ctx* c, int l, const double* u, const double* w, double
   return (lx_status)c->h_state->status_total;
 }
 
+lx_status phi_l_apply_vertical(lx_ctx* c, int l, int nc, const double* alpha, const double* u, const double* w,
+                               double* const* out, double cc, double gamma, double h, double rtol, double atol,
+                               int* iters) {
+  if (!c || !w || !out || !alpha || nc < 1 || nc > kMaxVertical || l < 0 || l > 8 || !(gamma != 0.0) ||
+      !std::isfinite(h) || !std::isfinite(cc) || !std::isfinite(gamma) || !(rtol >= 0.0) || !(atol >= 0.0))
+    return LX_E_INVAL;
+  for (int j = 0; j < nc; ++j) {
+    if (!out[j] || !(alpha[j] > 0.0) || !std::isfinite(alpha[j])) return LX_E_INVAL;
+    if ((const void*)out[j] == (const void*)w || (u && (const void*)out[j] == (const void*)u)) return LX_E_INVAL;
+    for (int k = 0; k < j; ++k)
+      if (out[k] == out[j]) return LX_E_INVAL;
+  }
+  const lx_problem& P = c->prob;
+  if (P.kind == LX_BURGERS && !u) return LX_E_INVAL;
+  const bool df = P.precision == LX_DF64;
+  bool wide;
+  if (df) {
+    if (P.nx % kPipeRow != 0 || !aligned16(w)) {
+      set_last_error("vertical float-float interpolation needs nx % 128 == 0 and a 16-byte aligned w");
+      return LX_E_INVAL;
+    }
+    wide = true;
+  } else {
+    wide = P.nx % 64 == 0 && aligned16(w) && aligned16(c->d_y[0]) && aligned16(c->d_y[1]);
+    for (int j = 0; j < nc; ++j) wide = wide && aligned16(out[j]);
+  }
+  const void* fn = vertical_kernel(P.kind, P.precision, wide, nc);
+  if (!fn) return LX_E_INVAL;
+  // lazily allocated vertical buffers
+  if (!c->d_vargs && !cuda_ok(cudaMalloc((void**)&c->d_vargs, sizeof(VertArgs)), "cudaMalloc")) return LX_E_NOMEM;
+  if (!c->d_vcoef &&
+      !cuda_ok(cudaMalloc((void**)&c->d_vcoef, sizeof(double) * kMaxVertical * (size_t)c->K), "cudaMalloc"))
+    return LX_E_NOMEM;
+  c->d_pdfv[0] = c->d_pdf;
+  for (int j = 1; df && j < nc; ++j)
+    if (!c->d_pdfv[j] && !cuda_ok(cudaMalloc((void**)&c->d_pdfv[j], sizeof(float2) * (size_t)c->n), "cudaMalloc"))
+      return LX_E_NOMEM;
+  lx_status st = begin_call(c);
+  if (st != LX_OK) return st;
+  if (P.kind == LX_BURGERS) {
+    rhs_kernel<1><<<aux_blocks(c), kThreadsPerBlock, 0, c->stream>>>(c->geo, P.nu, 0.0, 0.0, u, nullptr, c->d_s);
+    ++c->stats.kernels;
+    LX_CUDA(cudaGetLastError());
+  }
+  // divided differences of phi_l(alpha_j h (c + gamma xi)) on a common table
+  // long enough for the largest alpha_j
+  int count = 2;
+  for (int j = 0; j < nc; ++j) count = std::max(count, leja_coeff_count(alpha[j] * h, cc, gamma, c->K));
+  std::vector<double> xi(count), dh((size_t)nc * count);
+  leja_points(count, xi.data());
+  for (int j = 0; j < nc; ++j) {
+    const int cs = leja_coeffs(l, alpha[j] * h, cc, gamma, xi.data(), count, dh.data() + (size_t)j * count);
+    if (cs != LX_OK) return (lx_status)cs;
+    LX_CUDA(cudaMemcpyAsync(c->d_vcoef + (size_t)j * c->K, dh.data() + (size_t)j * count, sizeof(double) * count,
+                            cudaMemcpyHostToDevice, c->stream));
+  }
+  LX_CUDA(cudaStreamSynchronize(c->stream));  // dh is host memory of this frame
+  const int variant = wide ? kVec2 : kVec1;
+  const int H = df ? 8 : c->strip_h;
+  LoopGraph& L = c->vloop[variant][nc - 1];
+  if (!L.built || L.cand.func != fn) {
+    destroy_graph(L);
+    const Cand k{fn, kThreadsPerBlock, 0, df ? 4 : (wide ? 2 : 1), "leja_iter_vertical"};
+    int grid = 0;
+    const int gs = grid_for(c, k, H, &grid);
+    if (gs != LX_OK) return (lx_status)gs;
+    L.cand = k;
+    L.strip_h = H;
+    L.grid = grid;
+    L.unroll = c->graph_unroll;
+    LX_CUDA(cudaGraphCreate(&L.graph, 0));
+    cudaGraphConditionalHandle cond;
+    LX_CUDA(cudaGraphConditionalHandleCreate(&cond, L.graph, 1, cudaGraphCondAssignDefault));
+    alignas(cudaGraphNodeParams) unsigned char cp_raw[sizeof(cudaGraphNodeParams)];
+    std::memset(cp_raw, 0, sizeof(cp_raw));
+    cudaGraphNodeParams& cp = *reinterpret_cast<cudaGraphNodeParams*>(cp_raw);
+    cp.type = cudaGraphNodeTypeConditional;
+    cp.conditional.handle = cond;
+    cp.conditional.type = cudaGraphCondTypeWhile;
+    cp.conditional.size = 1;
+    cudaGraphNode_t cnode;
+    LX_CUDA(cudaGraphAddNode(&cnode, L.graph, nullptr, nullptr, 0, &cp));
+    cudaGraph_t body = cp.conditional.phGraph_out[0];
+    const LoopArgs* args = c->d_args;
+    const VertArgs* vargs = c->d_vargs;
+    LoopState* stp = c->d_state;
+    double* partials = c->d_partials;
+    unsigned int* ticket = c->d_ticket;
+    void* kargs[] = {(void*)&args, (void*)&vargs, (void*)&stp, (void*)&partials, (void*)&ticket, (void*)&cond};
+    cudaKernelNodeParams kp;
+    std::memset(&kp, 0, sizeof(kp));
+    kp.func = const_cast<void*>(fn);
+    kp.gridDim = dim3(L.grid);
+    kp.blockDim = dim3(kThreadsPerBlock);
+    kp.kernelParams = kargs;
+    cudaGraphNode_t prev = nullptr;
+    for (int q = 0; q < L.unroll; ++q) {
+      cudaGraphNode_t knode;
+      LX_CUDA(cudaGraphAddKernelNode(&knode, body, prev ? &prev : nullptr, prev ? 1 : 0, &kp));
+      prev = knode;
+    }
+    LX_CUDA(cudaGraphInstantiate(&L.exec, L.graph, 0));
+    L.built = true;
+  }
+  st = prepare_loop(c, H, count - 1, c->d_vcoef, u, w, out[0], cc, gamma, rtol, atol, false);
+  if (st != LX_OK) return st;
+  VertArgs V;
+  std::memset(&V, 0, sizeof(V));
+  V.np = nc;
+  for (int j = 0; j < nc; ++j) {
+    V.d[j] = c->d_vcoef + (size_t)j * c->K;
+    V.p[j] = out[j];
+    V.pdf[j] = c->d_pdfv[j];
+  }
+  LX_CUDA(upload_vertical_args(V, c->d_vargs, c->stream));
+  ++c->stats.kernels;
+  if (c->ev_used + 2 > 8) return LX_E_INVAL;
+  LX_CUDA(cudaEventRecord(c->ev[c->ev_used], c->stream));
+  if (!c->stream_loop) {
+    LX_CUDA(cudaGraphLaunch(L.exec, c->stream));
+    c->graph_iter_launches_pending = 1;
+  } else {
+    const LoopArgs* args = c->d_args;
+    const VertArgs* vargs = c->d_vargs;
+    LoopState* stp = c->d_state;
+    double* partials = c->d_partials;
+    unsigned int* ticket = c->d_ticket;
+    cudaGraphConditionalHandle cond = 0;
+    void* kargs[] = {(void*)&args, (void*)&vargs, (void*)&stp, (void*)&partials, (void*)&ticket, (void*)&cond};
+    for (int it = 0; it < count - 1; it += 8) {
+      for (int q = 0; q < 8; ++q)
+        LX_CUDA(cudaLaunchKernel(fn, dim3(L.grid), dim3(kThreadsPerBlock), kargs, 0, c->stream));
+      c->stats.kernels += 8;
+      LX_CUDA(cudaMemcpyAsync(c->h_state, c->d_state, sizeof(LoopState), cudaMemcpyDeviceToHost, c->stream));
+      LX_CUDA(cudaStreamSynchronize(c->stream));
+      if (c->h_state->done) break;
+    }
+  }
+  LX_CUDA(cudaEventRecord(c->ev[c->ev_used + 1], c->stream));
+  c->ev_used += 2;
+  if (df) {
+    for (int j = 0; j < nc; ++j) {
+      if (c->n % 2 == 0 && aligned16(out[j])) {
+        const long long n2 = c->n / 2;
+        const int G2 = (int)std::max<long long>(
+            1, std::min<long long>((n2 + kThreadsPerBlock - 1) / kThreadsPerBlock, 8LL * c->sm_count));
+        df_output2_kernel<<<G2, kThreadsPerBlock, 0, c->stream>>>(
+            n2, reinterpret_cast<const float4*>(c->d_pdfv[j]), nullptr, reinterpret_cast<double2*>(out[j]),
+            c->d_state, static_cast<const float4*>(c->d_y[0]), static_cast<const float4*>(c->d_y[1]));
+      } else {
+        df_output_kernel<<<aux_blocks(c), kThreadsPerBlock, 0, c->stream>>>(
+            c->n, c->d_pdfv[j], nullptr, out[j], c->d_state, static_cast<const float2*>(c->d_y[0]),
+            static_cast<const float2*>(c->d_y[1]));
+      }
+      ++c->stats.kernels;
+      LX_CUDA(cudaGetLastError());
+    }
+  }
+  st = end_call(c);
+  if (st != LX_OK) return st;
+  if (iters) *iters = c->h_state->iters_total;
+  return (lx_status)c->h_state->status_total;
+}
+
 lx_status expint_step(lx_ctx* c, const double* u, double* u_low, double* u_high, double cc, double gamma, double h,
                       double rtol, double atol, double* err, int* iters) {
   if (!c || !u || !u_high || !(gamma != 0.0) || !std::isfinite(h) || !std::isfinite(cc) || !std::isfinite(gamma) ||
@@ -751,7 +955,19 @@ lx_status expint_step(lx_ctx* c, const double* u, double* u_low, double* u_high,
       W.wf[2 * k] = (float)W.wd[k];
       W.wf[2 * k + 1] = (float)(W.wd[k] - (double)W.wf[2 * k]);
     }
-    rhs_df_advdiff_kernel<<<G, kThreadsPerBlock, 0, c->stream>>>(c->geo, u, W, c->d_f, c->d_state, c->d_src, h);
+    if (P.nx % kPipeRow == 0 && aligned16(u) && (!c->d_src || aligned16(c->d_src))) {
+      // row-window form: at most the resident blocks, at least 4 rows per warp
+      int per_sm = 0;
+      LX_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, rhs_df_advdiff_rows_kernel, kThreadsPerBlock, 0));
+      const long long lines = (long long)(P.nx / kPipeRow) * P.ny;
+      const int GR = (int)std::max<long long>(
+          1, std::min<long long>((lines / 4 + kWarpsPerBlock - 1) / kWarpsPerBlock,
+                                 (long long)std::max(per_sm, 1) * c->sm_count));
+      rhs_df_advdiff_rows_kernel<<<GR, kThreadsPerBlock, 0, c->stream>>>(P.nx, P.ny, u, W, c->d_f, c->d_state,
+                                                                          c->d_src, h);
+    } else {
+      rhs_df_advdiff_kernel<<<G, kThreadsPerBlock, 0, c->stream>>>(c->geo, u, W, c->d_f, c->d_state, c->d_src, h);
+    }
     ++c->stats.kernels;
     LX_CUDA(cudaGetLastError());
     st = launch_loop(c, 0, 1, u, c->d_f, u_high, cc, gamma, h, rtol, atol, u, true);

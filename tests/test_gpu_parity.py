@@ -223,6 +223,32 @@ def test_expint_step_with_source(lx, xi_oracle, kind, integ, n, prec):
     assert st == 0 and rel(hi.cpu().numpy(), ref0) <= TOL
 
 
+@pytest.mark.parametrize("nx,ny", [(128, 100), (256, 7)])
+@pytest.mark.parametrize("scale", [1.0, 1e100, 1e-100])
+@pytest.mark.parametrize("offset", [0, 1])
+def test_df64_ros_eu_rhs_forms(lx, xi_oracle, nx, ny, scale, offset):
+    # the float-float Rosenbrock-Euler path: row-window h A u (aligned input,
+    # nx % 128 == 0) or the point-wise fallback (offset view), and inputs far
+    # outside the float range (computed in double inside the same kernels).
+    # 1e+-100: outside the float range, while the oracle's sums of squares
+    # still fit in a double.
+    nu, a = 1e-2, 0.5
+    u = synth.gaussians_ic(nx, ny, seed=12) + 0.1
+    h = 30 * synth.cfl_step(nx, ny, nu, a)
+    import fourier
+
+    c, g = oracle.spectral_interval(fourier.spectral_radius(nx, ny, nu, a))
+    ctx = lx.leja_setup(nx, ny, nu, a, lx.ADVDIFF, lx.DF64, lx.ROS_EU)
+    buf = torch.empty(nx * ny + 1, dtype=torch.float64, device="cuda")
+    ud = buf[offset:offset + nx * ny]
+    ud.copy_(torch.from_numpy(u * scale))
+    hi = torch.empty(nx * ny, dtype=torch.float64, device="cuda")
+    st, err, it = lx.expint_step(ctx, ud, None, hi, c, g, h, TOL, TOL * scale)
+    ref, it_o, st_o = oracle.ros_eu(0, nx, ny, nu, a, u * scale, c, g, h, TOL, TOL * scale, xi_oracle)
+    assert st == 0 and st_o == 0 and abs(it - it_o) <= 1 and it_o > 5
+    assert rel(hi.cpu().numpy(), ref) <= TOL
+
+
 def test_expint_step_host_buffers(lx, xi_oracle):
     n, nu = 64, 2e-2
     u = synth.burgers_ic(n, n, seed=9)
@@ -543,3 +569,59 @@ def test_df64_burgers_rejects_unsupported_layout(lx):
 
     with pytest.raises(LexgbError):
         lx.leja_setup(96, 96, 2e-2, 0.0, lx.BURGERS, lx.DF64)
+
+
+VERT_CASES = [(0, "FP64", 64, 64), (0, "FP64", 100, 37), (0, "MIXED", 64, 64), (0, "DF64", 128, 96),
+              (1, "FP64", 64, 64), (1, "FP64", 72, 40), (1, "DF64", 128, 64)]
+
+
+@pytest.mark.parametrize("kind,prec,nx,ny", VERT_CASES)
+@pytest.mark.parametrize("nc", [1, 3, 4])
+def test_phi_vertical_matches_oracle(lx, xi_oracle, kind, prec, nx, ny, nc):
+    # phi_l(alpha_j h J) w for several step fractions from one Newton basis
+    l = 1
+    alphas = [0.25, 0.5, 0.75, 1.0][-nc:]
+    if kind == 0:
+        nu, a = 1e-2, 0.5
+        u = None
+        w = synth.gaussians_ic(nx, ny, seed=14) + 0.05 * synth.random_field(nx * ny, 15)
+        h = 40 * synth.cfl_step(nx, ny, nu, a)
+        rho, _, _ = oracle.power_iteration(0, nx, ny, nu, a, None, synth.power_start(nx * ny, 5), 10)
+    else:
+        nu, a = 2e-2, 0.0
+        u = synth.burgers_ic(nx, ny, seed=14)
+        w = synth.random_field(nx * ny, seed=15)
+        h = 40 * synth.cfl_step(nx, ny, nu, np.abs(u).max())
+        rho, _, _ = oracle.power_iteration(1, nx, ny, nu, 0.0, u, synth.power_start(nx * ny, 5), 10)
+    c, g = oracle.spectral_interval(rho)
+    ctx = lx.leja_setup(nx, ny, nu, a, kind, getattr(lx, prec))
+    outs = [torch.empty(nx * ny, dtype=torch.float64, device="cuda") for _ in alphas]
+    st, it = lx.phi_l_apply_vertical(ctx, l, alphas, dev(u) if u is not None else None, dev(w), outs, c, g, h, TOL,
+                                     TOL)
+    refs, it_o, st_o = oracle.leja_phi_vertical(kind, nx, ny, nu, a, u, l, alphas, w, c, g, h, TOL, TOL, xi_oracle)
+    assert st == 0 and st_o == 0
+    bar = 1e-5 if prec == "MIXED" else TOL
+    assert abs(it - it_o) <= (3 if prec == "MIXED" else 1)
+    for j in range(nc):
+        assert rel(outs[j].cpu().numpy(), refs[j]) <= bar, (j, rel(outs[j].cpu().numpy(), refs[j]))
+    if nc == 1 and prec != "MIXED":
+        # one polynomial: the same result as phi_l_apply at h * alpha
+        one = torch.empty_like(outs[0])
+        st1, it1 = lx.phi_l_apply(ctx, l, dev(u) if u is not None else None, dev(w), one, c, g, h * alphas[0], TOL,
+                                  TOL)
+        assert st1 == 0 and abs(it1 - it) <= 1
+        assert rel(outs[0].cpu().numpy(), one.cpu().numpy()) <= 1e-12
+
+
+def test_phi_vertical_rejects_bad_arguments(lx):
+    n = 64
+    ctx = lx.leja_setup(n, n, 1e-2, 0.5, lx.ADVDIFF, lx.FP64)
+    w = dev(synth.gaussians_ic(n, n, seed=1))
+    o = [torch.empty(n * n, dtype=torch.float64, device="cuda") for _ in range(5)]
+    args = (-1.0e3, 250.0, 1e-3, TOL, TOL)
+    assert lx.phi_l_apply_vertical(ctx, 1, [1.0] * 5, None, w, o, *args)[0] == 1  # more than four
+    assert lx.phi_l_apply_vertical(ctx, 1, [0.5, -1.0], None, w, o[:2], *args)[0] == 1  # alpha <= 0
+    assert lx.phi_l_apply_vertical(ctx, 1, [0.5, 1.0], None, w, [o[0], o[0]], *args)[0] == 1  # same output twice
+    assert lx.phi_l_apply_vertical(ctx, 1, [0.5, 1.0], None, w, [o[0], w], *args)[0] == 1  # output aliases w
+    ctxb = lx.leja_setup(n, n, 2e-2, 0.0, lx.BURGERS, lx.FP64)
+    assert lx.phi_l_apply_vertical(ctxb, 1, [1.0], None, w, o[:1], *args)[0] == 1  # Burgers needs u

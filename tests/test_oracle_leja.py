@@ -172,6 +172,48 @@ def test_exprb32_linear_has_zero_remainder():
     assert err == 0.0 and np.array_equal(lo, hi)
 
 
+@pytest.mark.parametrize("l", [0, 1, 2])
+def test_vertical_interpolation_matches_fourier(l):
+    # phi_l(alpha_j h A) w for three step fractions from one Newton basis
+    # against the exact Fourier solution of each
+    n, nu, a = 64, 1e-2, 0.7
+    u0, h, c, gamma = _cfg1(4, n=n, a=a)
+    xi = oracle.leja_points(400)
+    alphas = [1.0 / 3.0, 2.0 / 3.0, 1.0]
+    outs, iters, st = oracle.leja_phi_vertical(oracle.ADVDIFF, n, n, nu, a, None, l, alphas, u0, c, gamma, h, TOL,
+                                               TOL, xi)
+    assert st == oracle.OK
+    singles = []
+    for j, al in enumerate(alphas):
+        ref = phi_apply(l, n, n, nu, a, al * h, u0)
+        assert rel_l2(outs[j], ref) <= 100 * TOL, (j, rel_l2(outs[j], ref))
+        one, it1, st1 = oracle.leja_phi(oracle.ADVDIFF, n, n, nu, a, None, l, u0, c, gamma, al * h, TOL, TOL, xi)
+        assert st1 == oracle.OK
+        singles.append(it1)
+    # the shared loop runs until the slowest polynomial has converged
+    assert iters >= max(singles)
+    assert singles[0] < singles[-1]  # smaller steps need fewer terms
+
+
+def test_vertical_interpolation_burgers_jacobian_dense():
+    # phi_1(alpha h J(u)) w against the dense augmented-matrix exponential
+    n, nu = 10, 2e-2
+    u = synth.burgers_ic(n, n, seed=3)
+    w = synth.random_field(n * n, seed=4)
+    h = 20 * synth.cfl_step(n, n, nu, np.abs(u).max())
+    J = _dense(lambda e: oracle.burgers_J(n, n, nu, u, e), n * n)
+    rho = np.max(np.abs(np.linalg.eigvals(J)))
+    c, gamma = oracle.spectral_interval(rho)
+    xi = oracle.leja_points(400)
+    alphas = [0.5, 1.0]
+    outs, iters, st = oracle.leja_phi_vertical(oracle.BURGERS, n, n, nu, 0.0, u, 1, alphas, w, c, gamma, h, 1e-12,
+                                               1e-12, xi)
+    assert st == oracle.OK
+    for j, al in enumerate(alphas):
+        ref = _phi_dense(al * h * J, w, 1)
+        assert rel_l2(outs[j], ref) <= 1e-9
+
+
 def _exact_with_source(n, nu, a, h, u0, S):
     # u' = A u + S over one step h, mode by mode: exp(h lam) u^ + h phi_1(h lam) S^
     from fourier import phi_complex, symbol
