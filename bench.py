@@ -59,7 +59,8 @@ def parse():
     p.add_argument("--unroll", type=int, default=None, help="fused-iteration launches per graph-loop pass")
     p.add_argument("--source", action="store_true",
                    help="diffusion-advection with a time-independent source S (u' = A u + S)")
-    p.add_argument("--workload", default="advdiff4096", choices=["advdiff4096", "batch256", "burgers2048"])
+    p.add_argument("--workload", default="advdiff4096",
+                   choices=["advdiff4096", "batch256", "burgers2048", "vertical4096"])
     return p.parse_args()
 
 
@@ -314,6 +315,76 @@ def run_batch(args, rank, world, local):
     return 0
 
 
+def run_vertical(args, rank, world, local):
+    """Vertical interpolation at 4096^2 (diffusion-advection, nu = 1e-2, a = 1,
+    h = 50 dt_CFL): phi_1(alpha_j h A) w for alpha = 1/4, 1/2, 3/4, 1 from one
+    Newton basis, against four separate phi_l_apply calls, each form in FP64
+    and float-float; also the largest difference between the two forms."""
+    import torch
+
+    import paper_2310_08344_gb300 as lx
+
+    torch.cuda.set_device(local)
+    stream = torch.cuda.current_stream()
+    n = args.n
+    N = n * n
+    alphas = [0.25, 0.5, 0.75, 1.0]
+    w = torch.from_numpy(synth.gaussians_ic(n, n, seed=1)).cuda()
+    h = CFL_MULT * synth.cfl_step(n, n, NU, ADV)
+    c, g = lx.spectral_interval(symbol_radius(n, NU, ADV))
+    forms = {}
+    for prec_name, prec in (("fp64", lx.FP64), ("df64", lx.DF64)):
+        ctx = lx.leja_setup(n, n, NU, ADV, lx.ADVDIFF, prec, lx.ROS_EU, 1000, stream)
+        outs_v = [torch.empty(N, dtype=torch.float64, device="cuda") for _ in alphas]
+        outs_s = [torch.empty(N, dtype=torch.float64, device="cuda") for _ in alphas]
+
+        def vertical():
+            st, it = lx.phi_l_apply_vertical(ctx, 1, alphas, None, w, outs_v, c, g, h, TOL, TOL)
+            if st != 0:
+                raise SystemExit(f"phi_l_apply_vertical failed: {st}")
+            return it
+
+        def separate():
+            its = []
+            for j, al in enumerate(alphas):
+                st, it = lx.phi_l_apply(ctx, 1, None, w, outs_s[j], c, g, h * al, TOL, TOL)
+                if st != 0:
+                    raise SystemExit(f"phi_l_apply failed: {st}")
+                its.append(it)
+            return its
+
+        res = {}
+        for name, fn in (("vertical", vertical), ("separate", separate)):
+            for _ in range(max(args.warmup, 1)):
+                fn()
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            its = None
+            for _ in range(args.steps):
+                its = fn()
+            e1.record(stream)
+            torch.cuda.synchronize()
+            res[name] = {"ms_per_call": e0.elapsed_time(e1) / args.steps, "leja_iters": its}
+        diff = max(float(torch.linalg.norm(outs_v[j] - outs_s[j]) / torch.linalg.norm(outs_s[j]))
+                   for j in range(len(alphas)))
+        res["speedup_vs_separate"] = res["separate"]["ms_per_call"] / res["vertical"]["ms_per_call"]
+        res["max_rel_l2_vertical_vs_separate"] = diff
+        forms[prec_name] = res
+        ctx.close()
+    best = forms["df64"]["vertical"]
+    line = {"metric": "ms per vertical phi call (4 step fractions)", "value": best["ms_per_call"],
+            "unit": "ms", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": best["ms_per_call"], "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32x2 (float-float, FP64-accurate)", "data": "synthetic",
+            "config": {"workload": f"vertical-{n}x{n}-phi1-alpha4", "alphas": alphas, "nu": NU, "a": ADV,
+                       "h_over_dt_cfl": CFL_MULT, "tol": TOL},
+            "forms": forms}
+    if rank == 0:
+        print(json.dumps(line))
+    return 0
+
+
 def run_burgers(args, rank, world, local):
     """Viscous Burgers 2048^2, nu = 5e-3, EXPRB32 steps of h = 50 dt_CFL with
     a power-iteration bound before every step; FP64 and mixed forms, and the
@@ -391,6 +462,8 @@ def main():
         return run_batch(args, rank, world, local)
     if args.workload == "burgers2048":
         return run_burgers(args, rank, world, local)
+    if args.workload == "vertical4096":
+        return run_vertical(args, rank, world, local)
     import torch
 
     import paper_2310_08344_gb300 as lx

@@ -20,6 +20,8 @@ from . import build as _build
 
 OK, E_INVAL, E_NOMEM, E_NOCONV, E_NONFINITE = 0, 1, 2, 4, 5
 ADVDIFF, BURGERS = 0, 1
+# the paper's discretisation (periodic [-1,1]^2, third-order upwind gradient)
+ADVDIFF_UP3, BURGERS_UP3 = 2, 3
 
 _lib = None
 _lock = threading.Lock()
@@ -48,6 +50,9 @@ def lib():
             L.or_apply_advdiff.argtypes = [C.c_int, C.c_int, C.c_double, C.c_double, _dp, _dp]
             L.or_burgers_f.argtypes = [C.c_int, C.c_int, C.c_double, _dp, _dp]
             L.or_burgers_J.argtypes = [C.c_int, C.c_int, C.c_double, _dp, _dp, _dp]
+            L.or_apply_advdiff_up3.argtypes = [C.c_int, C.c_int, C.c_double, C.c_double, _dp, _dp]
+            L.or_burgers_up3_f.argtypes = [C.c_int, C.c_int, C.c_double, C.c_double, _dp, _dp]
+            L.or_burgers_up3_J.argtypes = [C.c_int, C.c_int, C.c_double, C.c_double, _dp, _dp, _dp]
             L.or_power_iteration.argtypes = [C.c_int, C.c_int, C.c_int, C.c_double, C.c_double, _dp, _dp,
                                              C.c_int, _dp, _ip]
             L.or_leja_phi.argtypes = [C.c_int, C.c_int, C.c_int, C.c_double, C.c_double, _dp, C.c_int, _dp,
@@ -142,6 +147,30 @@ def apply_advdiff(nx, ny, nu, a, v) -> np.ndarray:
     v = _f64(v)
     out = np.zeros_like(v)
     lib().or_apply_advdiff(nx, ny, nu, a, _p(v), _p(out))
+    return out
+
+
+def apply_advdiff_up3(nx, ny, nu, a, v) -> np.ndarray:
+    """nu (v_xx + v_yy) + a (v_x + v_y) on periodic [-1,1]^2, upwind gradient."""
+    v = _f64(v)
+    out = np.zeros_like(v)
+    lib().or_apply_advdiff_up3(nx, ny, nu, a, _p(v), _p(out))
+    return out
+
+
+def burgers_up3_f(nx, ny, nu, a, u) -> np.ndarray:
+    """nu (u_xx + u_yy) + (a/2) ((u^2)_x + (u^2)_y) on periodic [-1,1]^2."""
+    u = _f64(u)
+    out = np.zeros_like(u)
+    lib().or_burgers_up3_f(nx, ny, nu, a, _p(u), _p(out))
+    return out
+
+
+def burgers_up3_J(nx, ny, nu, a, u, v) -> np.ndarray:
+    u = _f64(u)
+    v = _f64(v)
+    out = np.zeros_like(v)
+    lib().or_burgers_up3_J(nx, ny, nu, a, _p(u), _p(v), _p(out))
     return out
 
 

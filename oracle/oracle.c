@@ -42,7 +42,7 @@ typedef __float128 qreal; /* libquadmath on x86-64 */
 #endif
 
 enum { OR_OK = 0, OR_E_INVAL = 1, OR_E_NOMEM = 2, OR_E_NOCONV = 4, OR_E_NONFINITE = 5 };
-enum { OR_ADVDIFF = 0, OR_BURGERS = 1 };
+enum { OR_ADVDIFF = 0, OR_BURGERS = 1, OR_ADVDIFF_UP3 = 2, OR_BURGERS_UP3 = 3 };
 
 int or_qreal_mant_dig(void) {
 #if LDBL_MANT_DIG == 113
@@ -270,6 +270,100 @@ void or_burgers_J(int nx, int ny, double nu, const double* u, const double* v, d
   free(dv);
 }
 
+/* ------------------------------------------------------------------------ */
+/* The paper's own discretisation (Sec. 4): periodic [-1,1]^2 (spacing       */
+/* 2/nx, 2/ny), the Laplacian by second-order central differences and the    */
+/* gradient by the third-order upwind-biased scheme.  For a term +a v_x with */
+/* a > 0 the characteristics run toward -x, so the upwind side is +x:        */
+/*   (D v)_i = (-v_{i+2} + 6 v_{i+1} - 3 v_i - 2 v_{i-1}) / (6 dx);          */
+/* for a < 0 the mirror image (2 v_{i+1} + 3 v_i - 6 v_{i-1} + v_{i-2})/(6dx).*/
+/* ------------------------------------------------------------------------ */
+
+/* Periodic index for any offset. */
+static int wrapm(int i, int n) {
+  i %= n;
+  return i < 0 ? i + n : i;
+}
+
+/* out = (D_x + D_y) v with the upwind side given by the sign s (+1 / -1). */
+static void up3_sum_grad(int nx, int ny, int s, const double* v, double* out) {
+  double dx = 2.0 / nx, dy = 2.0 / ny;
+  for (int j = 0; j < ny; ++j) {
+    for (int i = 0; i < nx; ++i) {
+      double gx, gy;
+      const double* row = v + (long)j * nx;
+      if (s > 0) {
+        gx = (-row[wrapm(i + 2, nx)] + 6.0 * row[wrapm(i + 1, nx)] - 3.0 * row[i] - 2.0 * row[wrapm(i - 1, nx)]) /
+             (6.0 * dx);
+        gy = (-v[idx(nx, i, wrapm(j + 2, ny))] + 6.0 * v[idx(nx, i, wrapm(j + 1, ny))] - 3.0 * row[i] -
+              2.0 * v[idx(nx, i, wrapm(j - 1, ny))]) / (6.0 * dy);
+      } else {
+        gx = (2.0 * row[wrapm(i + 1, nx)] + 3.0 * row[i] - 6.0 * row[wrapm(i - 1, nx)] + row[wrapm(i - 2, nx)]) /
+             (6.0 * dx);
+        gy = (2.0 * v[idx(nx, i, wrapm(j + 1, ny))] + 3.0 * row[i] - 6.0 * v[idx(nx, i, wrapm(j - 1, ny))] +
+              v[idx(nx, i, wrapm(j - 2, ny))]) / (6.0 * dy);
+      }
+      out[idx(nx, i, j)] = gx + gy;
+    }
+  }
+}
+
+/* out = nu (v_xx + v_yy) by central differences on [-1,1]^2. */
+static void lap_pm1(int nx, int ny, double nu, const double* v, double* out) {
+  double dx = 2.0 / nx, dy = 2.0 / ny;
+  for (int j = 0; j < ny; ++j) {
+    int jn = wrap(j + 1, ny), js = wrap(j - 1, ny);
+    for (int i = 0; i < nx; ++i) {
+      int ie = wrap(i + 1, nx), iw = wrap(i - 1, nx);
+      double vc = v[idx(nx, i, j)];
+      out[idx(nx, i, j)] = nu * ((v[idx(nx, ie, j)] - 2.0 * vc + v[idx(nx, iw, j)]) / (dx * dx) +
+                                 (v[idx(nx, i, jn)] - 2.0 * vc + v[idx(nx, i, js)]) / (dy * dy));
+    }
+  }
+}
+
+/* A v = nu (v_xx + v_yy) + a (v_x + v_y), upwind gradient (Problem I, Sec. 4,
+ * with nu the diffusion and a the advection coefficient). */
+void or_apply_advdiff_up3(int nx, int ny, double nu, double a, const double* v, double* out) {
+  long n = (long)nx * ny;
+  double* g = (double*)malloc(sizeof(double) * (size_t)n);
+  lap_pm1(nx, ny, nu, v, out);
+  if (a != 0.0) {
+    up3_sum_grad(nx, ny, a > 0.0 ? 1 : -1, v, g);
+    for (long k = 0; k < n; ++k) out[k] = out[k] + a * g[k];
+  }
+  free(g);
+}
+
+/* f(u) = nu (u_xx + u_yy) + (a/2) ((u^2)_x + (u^2)_y)   (Problem III, Sec. 4,
+ * the flux form; the upwind side follows the sign of a, i.e. the reading
+ * takes u > 0 as in the paper's initial state). */
+void or_burgers_up3_f(int nx, int ny, double nu, double a, const double* u, double* out) {
+  long n = (long)nx * ny;
+  double* u2 = (double*)malloc(sizeof(double) * (size_t)n);
+  double* g = (double*)malloc(sizeof(double) * (size_t)n);
+  lap_pm1(nx, ny, nu, u, out);
+  for (long k = 0; k < n; ++k) u2[k] = u[k] * u[k];
+  up3_sum_grad(nx, ny, a >= 0.0 ? 1 : -1, u2, g);
+  for (long k = 0; k < n; ++k) out[k] = out[k] + 0.5 * a * g[k];
+  free(u2);
+  free(g);
+}
+
+/* J(u) v = nu (v_xx + v_yy) + a ((u v)_x + (u v)_y): the exact derivative of
+ * or_burgers_up3_f (the difference operator is linear). */
+void or_burgers_up3_J(int nx, int ny, double nu, double a, const double* u, const double* v, double* out) {
+  long n = (long)nx * ny;
+  double* uv = (double*)malloc(sizeof(double) * (size_t)n);
+  double* g = (double*)malloc(sizeof(double) * (size_t)n);
+  lap_pm1(nx, ny, nu, v, out);
+  for (long k = 0; k < n; ++k) uv[k] = u[k] * v[k];
+  up3_sum_grad(nx, ny, a >= 0.0 ? 1 : -1, uv, g);
+  for (long k = 0; k < n; ++k) out[k] = out[k] + a * g[k];
+  free(uv);
+  free(g);
+}
+
 /* The operator the Leja basis multiplies by: A for diffusion-advection,
  * J(u) for Burgers.  S (may be NULL): a time-independent source added to
  * the right-hand side (Problem II of Sec. 4); it does not enter J. */
@@ -283,6 +377,10 @@ typedef struct {
 static void op_apply(const or_op* op, const double* v, double* out) {
   if (op->kind == OR_BURGERS)
     or_burgers_J(op->nx, op->ny, op->nu, op->u, v, out);
+  else if (op->kind == OR_ADVDIFF_UP3)
+    or_apply_advdiff_up3(op->nx, op->ny, op->nu, op->a, v, out);
+  else if (op->kind == OR_BURGERS_UP3)
+    or_burgers_up3_J(op->nx, op->ny, op->nu, op->a, op->u, v, out);
   else
     or_apply_advdiff(op->nx, op->ny, op->nu, op->a, v, out);
 }
@@ -292,6 +390,10 @@ static void op_apply(const or_op* op, const double* v, double* out) {
 static void op_rhs(const or_op* op, const double* u, double* out) {
   if (op->kind == OR_BURGERS)
     or_burgers_f(op->nx, op->ny, op->nu, u, out);
+  else if (op->kind == OR_ADVDIFF_UP3)
+    or_apply_advdiff_up3(op->nx, op->ny, op->nu, op->a, u, out);
+  else if (op->kind == OR_BURGERS_UP3)
+    or_burgers_up3_f(op->nx, op->ny, op->nu, op->a, u, out);
   else
     or_apply_advdiff(op->nx, op->ny, op->nu, op->a, u, out);
   if (op->S) {

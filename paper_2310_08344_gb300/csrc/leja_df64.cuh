@@ -123,6 +123,26 @@ __device__ __forceinline__ dfv df_dot5(const float (&wh)[5], const float (&wl)[5
   return r;
 }
 
+// sum_{k<3} w_k y_k, the same compensated scheme as df_dot5.
+__device__ __forceinline__ dfv df_dot3(const float (&wh)[3], const float (&wl)[3], const dfv (&y)[3]) {
+  float s, c, p, e, t;
+  two_prod(wh[0], y[0].h, s, c);
+#pragma unroll
+  for (int k = 1; k < 3; ++k) {
+    two_prod(wh[k], y[k].h, p, e);
+    two_sum(s, p, s, t);
+    c = __fadd_rn(c, __fadd_rn(t, e));
+  }
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    c = __fmaf_rn(wh[k], y[k].l, c);
+    c = __fmaf_rn(wl[k], y[k].h, c);
+  }
+  dfv r;
+  two_sum(s, c, r.h, r.l);
+  return r;
+}
+
 // p + d * y
 __device__ __forceinline__ dfv df_axpy(dfv d, dfv y, dfv p) {
   float q, qe, s, t;
@@ -685,8 +705,12 @@ static __global__ void __launch_bounds__(kThreadsPerBlock)
       const double xe = lane == 31 ? C.hx : xe0;
       double res[4];
       if (__all_sync(0xffffffffu, S.ok && C.ok && N.ok)) {
-        const dfv dw = lane == 0 ? df_split_scaled(xw, 0) : shfl_up_df(C.f[3]);
-        const dfv de = lane == 31 ? df_split_scaled(xe, 0) : shfl_down_df(C.f[0]);
+        // every lane takes part in both shuffles (full-mask shuffles must not
+        // sit in a divergent branch); lanes 0 and 31 then use their halo
+        const dfv sw = shfl_up_df(C.f[3]);
+        const dfv se = shfl_down_df(C.f[0]);
+        const dfv dw = lane == 0 ? df_split_scaled(xw, 0) : sw;
+        const dfv de = lane == 31 ? df_split_scaled(xe, 0) : se;
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
           const dfv t[5] = {k == 3 ? de : C.f[k + 1], k == 0 ? dw : C.f[k - 1], N.f[k], S.f[k], C.f[k]};
@@ -851,7 +875,7 @@ __device__ __forceinline__ void df_strip_pipe_burgers(const LoopArgs& A, const S
   const int nrows = r1 - r0;
   const int last_q = nrows + 1;
   const dfv lx = {A.bl[0], A.bl[1]}, ly = {A.bl[2], A.bl[3]}, rat = {A.bl[4], A.bl[5]};
-  const bool square = A.bl[4] == 1.0f && A.bl[5] == 0.0f;
+  const bool square = A.bl[4] == 1.0f && A.bl[5] == 0.0f && A.bl[0] == A.bl[2] && A.bl[1] == A.bl[3];
   auto slot = [&](int q) { return ring + (size_t)(q % kPipeStages) * kSlotElemsB; };
   auto issue = [&](int q) {
     if (q <= last_q) {
@@ -902,14 +926,25 @@ __device__ __forceinline__ void df_strip_pipe_burgers(const LoopArgs& A, const S
     float fy = 0.f, fp = 0.f;
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
-      const dfv qy = square ? qv[k] : df_mul(qv[k], rat);
+      const dfv ye = k == 3 ? xe : yc[k + 1], yw = k == 0 ? xw : yc[k - 1];
       const dfv wE = df_add(lx, df_neg(qv[k])), wW = df_add(lx, qv[k]);
-      const dfv wN = df_add(ly, df_neg(qy)), wS = df_add(ly, qy);
       const dfv wC = df_add(rv[k], xim);
-      const float wh[5] = {wE.h, wW.h, wN.h, wS.h, wC.h};
-      const float wl[5] = {wE.l, wW.l, wN.l, wS.l, wC.l};
-      const dfv t[5] = {k == 3 ? xe : yc[k + 1], k == 0 ? xw : yc[k - 1], yn[k], ys[k], yc[k]};
-      dfv v = df_dot5(wh, wl, t);
+      dfv v;
+      if (square) {
+        // nx == ny: the north and south weights equal the east and west ones,
+        // so J y = wE (yE + yN) + wW (yW + yS) + wC yC (three products)
+        const float wh[3] = {wE.h, wW.h, wC.h};
+        const float wl[3] = {wE.l, wW.l, wC.l};
+        const dfv t[3] = {df_add(ye, yn[k]), df_add(yw, ys[k]), yc[k]};
+        v = df_dot3(wh, wl, t);
+      } else {
+        const dfv qy = df_mul(qv[k], rat);
+        const dfv wN = df_add(ly, df_neg(qy)), wS = df_add(ly, qy);
+        const float wh[5] = {wE.h, wW.h, wN.h, wS.h, wC.h};
+        const float wl[5] = {wE.l, wW.l, wN.l, wS.l, wC.l};
+        const dfv t[5] = {ye, yw, yn[k], ys[k], yc[k]};
+        v = df_dot5(wh, wl, t);
+      }
       v.h *= swf;
       v.l *= swf;
       ynew[k] = v;

@@ -96,6 +96,57 @@ def source_field(nx: int, ny: int | None = None, seed: int = 21) -> np.ndarray:
     return np.ascontiguousarray(S.reshape(-1))
 
 
+def grid_pm1(nx: int, ny: int):
+    """Cell coordinates of the periodic [-1,1)^2 grid, x_i = -1 + 2 i / nx."""
+    x = -1.0 + 2.0 * np.arange(nx) / nx
+    y = -1.0 + 2.0 * np.arange(ny) / ny
+    return np.meshgrid(x, y, indexing="xy")
+
+
+def problem1_ic(nx: int, ny: int | None = None, seed: int | None = None) -> np.ndarray:
+    """Initial state of the paper's diffusion-advection problems on [-1,1)^2:
+    1 + exp(-((x - x0)^2 + (y - y0)^2) / 0.01) with (x0, y0) = (-0.5, -0.5);
+    a seed moves the centre by U[-0.1, 0.1]^2 (test variants)."""
+    ny = nx if ny is None else ny
+    x0, y0 = -0.5, -0.5
+    if seed is not None:
+        rng = np.random.default_rng(seed)
+        x0, y0 = np.array([x0, y0]) + rng.uniform(-0.1, 0.1, size=2)
+    X, Y = grid_pm1(nx, ny)
+    return np.ascontiguousarray((1.0 + np.exp(-((X - x0) ** 2 + (Y - y0) ** 2) / 0.01)).reshape(-1))
+
+
+def problem2_source(nx: int, ny: int | None = None) -> np.ndarray:
+    """Source of the paper's diffusion-advection problem with sources on
+    [-1,1)^2: exp(-((x+0.4)^2 + (y-0.6)^2)/0.05) + exp(-((x-0.25)^2 + (y+0.1)^2)/0.04)."""
+    ny = nx if ny is None else ny
+    X, Y = grid_pm1(nx, ny)
+    S = np.exp(-((X + 0.4) ** 2 + (Y - 0.6) ** 2) / 0.05) + np.exp(-((X - 0.25) ** 2 + (Y + 0.1) ** 2) / 0.04)
+    return np.ascontiguousarray(S.reshape(-1))
+
+
+def problem3_ic(nx: int, ny: int | None = None, seed: int | None = None) -> np.ndarray:
+    """Initial state of the paper's Burgers problem on [-1,1)^2:
+    2 + 0.01 (sin 2 pi x + sin 2 pi y + sin(8 pi x + 0.3) + sin(8 pi y + 0.3));
+    a seed adds U[0, 1) phases to the four sines (test variants)."""
+    ny = nx if ny is None else ny
+    ph = np.zeros(4) if seed is None else np.random.default_rng(seed).uniform(0.0, 1.0, size=4)
+    X, Y = grid_pm1(nx, ny)
+    u = 2.0 + 0.01 * (np.sin(2 * np.pi * X + ph[0]) + np.sin(2 * np.pi * Y + ph[1]) +
+                      np.sin(8 * np.pi * X + 0.3 + ph[2]) + np.sin(8 * np.pi * Y + 0.3 + ph[3]))
+    return np.ascontiguousarray(u.reshape(-1))
+
+
+def cfl_step_pm1(nx: int, ny: int, nu: float, adv: float) -> float:
+    """Explicit step limit on [-1,1)^2 (spacing 2/n), read as for cfl_step:
+    min(dx^2 / (4 nu), dx / (2 |adv|))."""
+    dx = 2.0 / max(nx, ny)
+    lim = dx * dx / (4.0 * nu) if nu > 0 else np.inf
+    if adv != 0.0:
+        lim = min(lim, dx / (2.0 * abs(adv)))
+    return float(lim)
+
+
 def power_start(n_points: int, seed: int = 12345) -> np.ndarray:
     """Start vector of the power iteration: standard normal entries.
 

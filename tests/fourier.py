@@ -25,6 +25,30 @@ def symbol(nx, ny, nu, a):
     return re + 1j * im
 
 
+def symbol_up3(nx, ny, nu, a):
+    """Symbol of the paper's discretisation on periodic [-1,1)^2 (spacing
+    2/n): central Laplacian plus a times the third-order upwind gradient,
+    whose one-axis stencil for a > 0 is (-v_{i+2} + 6 v_{i+1} - 3 v_i - 2 v_{i-1}) / 6
+    (mirrored for a < 0)."""
+    tx = 2 * np.pi * np.fft.fftfreq(nx)
+    ty = 2 * np.pi * np.fft.fftfreq(ny)
+    TX, TY = np.meshgrid(tx, ty, indexing="xy")
+    dx, dy = 2.0 / nx, 2.0 / ny
+
+    def sigma(t):
+        if a >= 0:
+            return (-np.exp(2j * t) + 6 * np.exp(1j * t) - 3 - 2 * np.exp(-1j * t)) / 6.0
+        return (2 * np.exp(1j * t) + 3 - 6 * np.exp(-1j * t) + np.exp(-2j * t)) / 6.0
+
+    lap = nu * (2 * np.cos(TX) - 2) / dx**2 + nu * (2 * np.cos(TY) - 2) / dy**2
+    return lap + a * (sigma(TX) / dx + sigma(TY) / dy)
+
+
+def phi_apply_symbol(l, lam, h, v, nx, ny):
+    V = np.fft.fft2(np.asarray(v, dtype=np.float64).reshape(ny, nx))
+    return np.real(np.fft.ifft2(phi_complex(l, h * lam) * V)).reshape(-1)
+
+
 def phi_complex(l, z):
     """phi_l(z) elementwise for complex arrays: power series for |z| < 1,
     the recursion phi_{k+1} = (phi_k - 1/k!)/z from exp otherwise."""
