@@ -60,7 +60,9 @@ def parse():
     p.add_argument("--source", action="store_true",
                    help="diffusion-advection with a time-independent source S (u' = A u + S)")
     p.add_argument("--workload", default="advdiff4096",
-                   choices=["advdiff4096", "batch256", "burgers2048", "vertical4096"])
+                   choices=["advdiff4096", "batch256", "burgers2048", "vertical4096", "paper1", "paper2",
+                            "paper3"])
+    p.add_argument("--cfl", type=float, default=100.0, help="paper workloads: step size in units of dt_CFL")
     return p.parse_args()
 
 
@@ -315,6 +317,103 @@ def run_batch(args, rank, world, local):
     return 0
 
 
+def run_paper(args, rank, world, local):
+    """The paper's own test problems (Sec. 4) on periodic [-1,1)^2 with the
+    third-order upwind gradient and the central Laplacian, diffusion 1 and
+    advection / flux coefficient 10, tolerance 1e-12:
+      paper1: u_t = A u, one exp(h A) u per step (Leja exponential),
+      paper2: u_t = A u + S, Rosenbrock-Euler (phi_1 of A u + S),
+      paper3: u_t = Lap u + 5 ((u^2)_x + (u^2)_y), EXPRB32 with a power
+              bound before every step.
+    Grid --n (the paper uses 8192 and 16384), h = --cfl x dt_CFL."""
+    import torch
+
+    import paper_2310_08344_gb300 as lx
+
+    torch.cuda.set_device(local)
+    stream = torch.cuda.current_stream()
+    n = args.n
+    N = n * n
+    nu, a, tol = 1.0, 10.0, 1e-12
+    which = args.workload
+    prec_name = args.precision if which != "paper3" or args.precision != "df64" else "fp64"
+    prec = {"fp64": lx.FP64, "mixed": lx.MIXED, "df64": lx.DF64}[prec_name]
+    kind = lx.BURGERS_UP3 if which == "paper3" else lx.ADVDIFF_UP3
+    integ = lx.EXPRB32 if which == "paper3" else lx.ROS_EU
+    ctx = lx.leja_setup(n, n, nu, a, kind, prec, integ, 1000, stream)
+    u0 = synth.problem3_ic(n, n) if which == "paper3" else synth.problem1_ic(n, n)
+    ua = torch.from_numpy(u0).cuda()
+    ub = torch.empty_like(ua)
+    lo = torch.empty_like(ua)
+    v0 = torch.from_numpy(synth.power_start(N, seed=5)).cuda()
+    amax = a * (float(np.abs(u0).max()) if which == "paper3" else 1.0)
+    h = args.cfl * synth.cfl_step_pm1(n, n, nu, amax)
+    src = None
+    if which == "paper2":
+        src = torch.from_numpy(synth.problem2_source(n, n)).cuda()
+        lx.lx_ctx_set_source(ctx, src)
+    st, rho, _ = lx.power_bound(ctx, ua if which == "paper3" else None, v0, 10)
+    c, g = lx.spectral_interval(rho)
+
+    def step(x, y):
+        nonlocal c, g
+        if which == "paper1":
+            st, it = lx.phi_l_apply(ctx, 0, None, x, y, c, g, h, tol, tol)
+            return st, it
+        if which == "paper3":
+            st, r, _ = lx.power_bound(ctx, x, v0, 10)
+            c, g = lx.spectral_interval(r)
+            st2, err, it = lx.expint_step(ctx, x, lo, y, c, g, h, tol, tol)
+            return st or st2, it
+        st, err, it = lx.expint_step(ctx, x, None, y, c, g, h, tol, tol)
+        return st, it
+
+    cur, nxt = ua, ub
+    for _ in range(max(args.warmup, 1)):
+        st, it = step(cur, nxt)
+        if st != 0:
+            raise SystemExit(f"{which} step failed: {st}")
+        cur, nxt = nxt, cur
+    lx.lx_ctx_stats(ctx, reset=True)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    iters = []
+    for _ in range(args.steps):
+        st, it = step(cur, nxt)
+        if st != 0:
+            raise SystemExit(f"{which} step failed: {st}")
+        iters.append(it)
+        cur, nxt = nxt, cur
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    stats = lx.lx_ctx_stats(ctx, reset=True)
+    value = float(N) * sum(iters) / (ms / 1e3) / 1e9
+    ipl = lx.lx_ctx_iters_per_launch(ctx)
+    avg_iter_s = stats["loop_ms"] / 1e3 / max(stats["loop_iterations"], 1)
+    alg = (40 if which == "paper3" else 32) * N  # y, p read + write (+ u for J(u)) per iteration
+    peaks, peak_src = measured_peaks()
+    achieved = alg / avg_iter_s / 1e9
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None,
+            "dtype": {"fp64": "f64", "mixed": "f32+f64", "df64": "f32x2 (float-float, FP64-accurate)"}[prec_name],
+            "data": "synthetic",
+            "config": {"workload": f"{which}-{n}x{n}-upwind3-[-1,1]^2", "diffusion": nu, "advection": a,
+                       "h_over_dt_cfl": args.cfl, "tol": tol, "precision": prec_name,
+                       "leja_iters_per_step": iters, "kernel": lx.lx_ctx_kernel_name(ctx)},
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                         "frac": achieved / peaks["hbm_gbs"], "traffic": None, "iterations_per_launch": ipl,
+                         "alg_bytes_per_iteration": alg, "avg_iteration_us": avg_iter_s * 1e6,
+                         "peak_source": f"{peak_src} (MEASURED_PEAKS.json hbm_gbs, burst copy)"},
+            "gpu_launches": int(stats["kernels"])}
+    if rank == 0:
+        print(json.dumps(line))
+    ctx.close()
+    return 0
+
+
 def run_vertical(args, rank, world, local):
     """Vertical interpolation at 4096^2 (diffusion-advection, nu = 1e-2, a = 1,
     h = 50 dt_CFL): phi_1(alpha_j h A) w for alpha = 1/4, 1/2, 3/4, 1 from one
@@ -464,6 +563,8 @@ def main():
         return run_burgers(args, rank, world, local)
     if args.workload == "vertical4096":
         return run_vertical(args, rank, world, local)
+    if args.workload in ("paper1", "paper2", "paper3"):
+        return run_paper(args, rank, world, local)
     import torch
 
     import paper_2310_08344_gb300 as lx

@@ -17,6 +17,20 @@
  *                  action J(u)v = nu Lap v - v (u_x+u_y) - u (v_x+v_y) is the
  *                  exact linearisation (the paper's finite-difference action,
  *                  Sec. 2.3, is replaced by it).
+ *  - The paper's own discretisation (Sec. 4): periodic [-1,1)^2 (spacing
+ *    2/nx, 2/ny), the Laplacian by second-order central differences and the
+ *    gradient by the third-order upwind-biased scheme -- for a term +a v_x,
+ *    a > 0: (-v_{i+2} + 6 v_{i+1} - 3 v_i - 2 v_{i-1}) / (6 dx), mirrored for
+ *    a < 0:
+ *      LX_ADVDIFF_UP3  A v = nu (v_xx + v_yy) + a (v_x + v_y)  (Problems I, II
+ *                      with nu = 1, a = 10)
+ *      LX_BURGERS_UP3  f(u) = nu (u_xx + u_yy) + (a/2) ((u^2)_x + (u^2)_y)
+ *                      (Problem III with nu = 1, a = 10), J(u) v = nu Lap v +
+ *                      a ((u v)_x + (u v)_y); the upwind side follows the sign
+ *                      of a (the paper's state stays positive).
+ *    LX_DF64 is available for LX_ADVDIFF_UP3 (not LX_BURGERS_UP3); batches,
+ *    vertical interpolation and the allocation-free entry point take the
+ *    central operators only.
  *  - Norms: ||x|| = ||x||_2 / sqrt(N) (Sec. 2.2).
  *  - Device pointers ("_dev") are CUDA global-memory pointers of the current
  *    device; host pointers ("_host") are ordinary CPU memory.  The caller
@@ -49,15 +63,16 @@ typedef enum {
   LX_E_TIMEOUT = 6    /* a bounded device-side wait gave up */
 } lx_status;
 
-enum { LX_ADVDIFF = 0, LX_BURGERS = 1 };          /* lx_problem.kind */
+enum { LX_ADVDIFF = 0, LX_BURGERS = 1, LX_ADVDIFF_UP3 = 2, LX_BURGERS_UP3 = 3 }; /* lx_problem.kind */
 enum { LX_FP64 = 0, LX_MIXED = 1, LX_DF64 = 2 }; /* lx_problem.precision */
 enum { LX_ROS_EU = 0, LX_EXPRB32 = 1 };          /* integrator */
 
 typedef struct {
   int nx, ny;     /* grid points per direction, each >= 1 */
   double nu;      /* diffusion coefficient */
-  double a;       /* advection speed (LX_ADVDIFF only) */
-  int kind;       /* LX_ADVDIFF or LX_BURGERS */
+  double a;       /* advection speed (LX_ADVDIFF, LX_ADVDIFF_UP3); flux
+                     coefficient (LX_BURGERS_UP3); unused by LX_BURGERS */
+  int kind;       /* LX_ADVDIFF, LX_BURGERS, LX_ADVDIFF_UP3, LX_BURGERS_UP3 */
   int precision;  /* LX_FP64: all arithmetic in double (FP64 pipe).
                      LX_MIXED: the Newton basis y_m and its stencil in float;
                      the coefficients, the polynomial p and both stopping
@@ -66,7 +81,7 @@ typedef struct {
                      48-bit significand) arithmetic on the FP32 pipe for the
                      basis, the stencil and the polynomial; double inputs and
                      outputs; norms accumulated in float-float from the
-                     leading float of each value.  LX_ADVDIFF only. */
+                     leading float of each value.  Not for LX_BURGERS_UP3. */
 } lx_problem;
 
 typedef struct lx_ctx lx_ctx;
@@ -123,7 +138,7 @@ void leja_destroy(lx_ctx* ctx);
 
 /* Spectral bound by power iteration (Sec. 2, Listing 7: the dominant
  * eigenvalue gives c = lambda/2, gamma = -lambda/4 with lambda = -1.05 rho).
- *   u_dev      linearisation point (LX_BURGERS: J(u); LX_ADVDIFF: ignored,
+ *   u_dev      linearisation point (Burgers kinds: J(u); diffusion-advection: ignored,
  *              may be NULL)
  *   v0_dev     start vector, N doubles, not modified (must not be constant:
  *              constants are in the null space of the periodic operators)
@@ -136,9 +151,9 @@ lx_status power_bound(lx_ctx* ctx, const double* u_dev, const double* v0_dev, in
 
 /* phi_l(h Op) w by Leja interpolation (Sec. 2.2 Listings 2-3, Sec. 2.3
  * Listings 8, 9, 11: real_Leja_exp for l = 0, real_Leja_phi_nl /
- * real_Leja_phi otherwise).  Op is A (LX_ADVDIFF) or J(u) (LX_BURGERS).
+ * real_Leja_phi otherwise).  Op is A (diffusion-advection kinds) or J(u) (Burgers kinds).
  *   l          0..8
- *   u_dev      linearisation point (LX_BURGERS), else ignored / NULL
+ *   u_dev      linearisation point (Burgers kinds), else ignored / NULL
  *   w_dev      input vector (N doubles), not modified
  *   out_dev    output p (N doubles); must not alias w_dev or u_dev
  *   c, gamma   centre and quarter-width of the focal interval [c-2g, c+2g]

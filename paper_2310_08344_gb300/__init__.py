@@ -11,6 +11,8 @@ from __future__ import annotations
 
 from .binding import (  # noqa: F401
     ADVDIFF,
+    ADVDIFF_UP3,
+    BURGERS_UP3,
     BURGERS,
     EXPRB32,
     DF64,

@@ -13,6 +13,7 @@ OK, E_INVAL, E_NOMEM, E_CUDA, E_NOCONV, E_NONFINITE, E_TIMEOUT = range(7)
 STATUS = {0: "LX_OK", 1: "LX_E_INVAL", 2: "LX_E_NOMEM", 3: "LX_E_CUDA", 4: "LX_E_NOCONV", 5: "LX_E_NONFINITE",
           6: "LX_E_TIMEOUT"}
 ADVDIFF, BURGERS = 0, 1
+ADVDIFF_UP3, BURGERS_UP3 = 2, 3  # the paper's discretisation: periodic [-1,1)^2, third-order upwind gradient
 FP64, MIXED, DF64 = 0, 1, 2
 ROS_EU, EXPRB32 = 0, 1
 

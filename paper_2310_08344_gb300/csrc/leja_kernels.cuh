@@ -29,6 +29,15 @@ namespace lexgb {
 constexpr int kWarpsPerBlock = 8;
 constexpr int kThreadsPerBlock = kWarpsPerBlock * 32;
 
+// Constants of the upwind operators on periodic [-1,1)^2 (see leja_upwind.cuh).
+struct Up3Op {
+  int nx, ny;
+  long long n;
+  int s;            // upwind side along both axes: +1 (a >= 0) or -1
+  double cxx, cyy;  // nu / dx^2, nu / dy^2
+  double gx, gy;    // |a| / (6 dx), |a| / (6 dy)
+};
+
 // Device-resident arguments of one Leja loop, written by set_loop_args before
 // each graph launch so that the graph itself never changes.
 struct LoopArgs {
@@ -59,6 +68,9 @@ struct LoopArgs {
   const float2* bq;
   const float2* br;
   float bl[6];
+  // upwind operators: constants and the shift c of the spectral interval
+  Up3Op up;
+  double up_c;
 };
 
 // Device-resident loop and reduction state.
@@ -531,6 +543,23 @@ static __global__ void __launch_bounds__(kThreadsPerBlock)
       st->rho_prev = rho;
       st->sigma = 1.0 / rho;
     }
+  }
+}
+
+// End of a power-iteration pass (thread 0 of the last block): s = sum w^2
+// over the n points of w = Op(v) / ||v||.
+__device__ __forceinline__ void power_pass_finish(LoopState* st, double s, long long n) {
+  const double rho = sqrt(s / double(n));
+  const int k = st->pk + 1;
+  st->pk = k;
+  st->rho = rho;
+  if (!isfinite(rho) || !(rho > 0.0)) {
+    st->pstatus = 5;
+    st->pdone = 1;
+  } else {
+    if ((k >= 2 && fabs(rho - st->rho_prev) <= 1e-2 * rho) || k >= st->pmax) st->pdone = 1;
+    st->rho_prev = rho;
+    st->sigma = 1.0 / rho;
   }
 }
 

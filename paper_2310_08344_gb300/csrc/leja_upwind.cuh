@@ -1,0 +1,297 @@
+// The paper's own discretisation (Sec. 4): periodic [-1,1)^2 with spacing
+// 2/nx, 2/ny, the Laplacian by second-order central differences and the
+// gradient by the third-order upwind-biased scheme.  Along one axis, for a
+// term +a v_x with a > 0 (characteristics toward -x, upwind side +x):
+//   (D v)_i = (-v_{i+2} + 6 v_{i+1} - 3 v_i - 2 v_{i-1}) / (6 dx),
+// and its mirror image for a < 0.  Writing s = sign(a) and the offsets o s
+// (o = -1, 0, 1, 2), a D v_i = |a| / (6 dx) * sum_o k_o v_{i + o s} with
+// k = (-2, -3, 6, -1): one stencil of seven points (the centre shared by
+// both axes).
+//   LX_ADVDIFF_UP3:  A v  = nu lap v + a (D_x + D_y) v
+//   LX_BURGERS_UP3:  f(u) = nu lap u + (a/2) (D_x + D_y) (u^2)   (flux form)
+//                    J(u) v = nu lap v + a (D_x + D_y) (u v)
+// The kernels here are point-wise (one thread per point, neighbours through
+// the caches).
+#pragma once
+
+#include "leja_df64.cuh"
+
+namespace lexgb {
+
+// k_o of the upwind stencil for o = -1, 0, 1, 2 (scalars: usable in device code)
+constexpr double kUp3Km = -2.0, kUp3K0 = -3.0, kUp3K1 = 6.0, kUp3K2 = -1.0;
+
+__device__ __forceinline__ int up3_wrap(int i, int n) {
+  // offsets are within [-2, 2]; n >= 1
+  while (i < 0) i += n;
+  while (i >= n) i -= n;
+  return i;
+}
+
+// Indices of the seven stencil points of (i, j): [C, X(-s), X(s), X(2s),
+// Y(-s), Y(s), Y(2s)].
+__device__ __forceinline__ void up3_points(const Up3Op& o, int i, int j, long long (&q)[7]) {
+  const int s = o.s;
+  const long long row = (long long)j * o.nx;
+  q[0] = row + i;
+  q[1] = row + up3_wrap(i - s, o.nx);
+  q[2] = row + up3_wrap(i + s, o.nx);
+  q[3] = row + up3_wrap(i + 2 * s, o.nx);
+  q[4] = (long long)up3_wrap(j - s, o.ny) * o.nx + i;
+  q[5] = (long long)up3_wrap(j + s, o.ny) * o.nx + i;
+  q[6] = (long long)up3_wrap(j + 2 * s, o.ny) * o.nx + i;
+}
+
+// Constant weights of A (diffusion-advection) at the seven points.
+__device__ __forceinline__ void up3_weights(const Up3Op& o, double (&w)[7]) {
+  w[0] = -2.0 * o.cxx - 2.0 * o.cyy + kUp3K0 * (o.gx + o.gy);
+  w[1] = o.cxx + kUp3Km * o.gx;
+  w[2] = o.cxx + kUp3K1 * o.gx;
+  w[3] = kUp3K2 * o.gx;
+  w[4] = o.cyy + kUp3Km * o.gy;
+  w[5] = o.cyy + kUp3K1 * o.gy;
+  w[6] = kUp3K2 * o.gy;
+}
+
+// Op(v) at one point: A v (BURGERS = false) or J(u) v (BURGERS = true); for
+// the right-hand side of Burgers pass v = u and half = true, which gives
+// nu lap u + (a/2) D(u^2).
+template <bool BURGERS, typename T, typename V>
+__device__ __forceinline__ T up3_apply(const Up3Op& o, const double* __restrict__ u, const V* __restrict__ v,
+                                       const long long (&q)[7], bool half = false) {
+  T vv[7];
+#pragma unroll
+  for (int k = 0; k < 7; ++k) vv[k] = T(v[q[k]]);
+  const T lap = T(o.cxx) * (vv[1] + vv[2] - T(2) * vv[0]) + T(o.cyy) * (vv[4] + vv[5] - T(2) * vv[0]);
+  T dx, dy;
+  if constexpr (BURGERS) {
+    T uu[7];
+#pragma unroll
+    for (int k = 0; k < 7; ++k) uu[k] = T(u[q[k]]);
+    const T f = half ? T(0.5) : T(1);
+    dx = T(kUp3Km) * uu[1] * vv[1] + T(kUp3K0) * uu[0] * vv[0] + T(kUp3K1) * uu[2] * vv[2] +
+         T(kUp3K2) * uu[3] * vv[3];
+    dy = T(kUp3Km) * uu[4] * vv[4] + T(kUp3K0) * uu[0] * vv[0] + T(kUp3K1) * uu[5] * vv[5] +
+         T(kUp3K2) * uu[6] * vv[6];
+    return lap + f * (T(o.gx) * dx + T(o.gy) * dy);
+  } else {
+    dx = T(kUp3Km) * vv[1] + T(kUp3K0) * vv[0] + T(kUp3K1) * vv[2] + T(kUp3K2) * vv[3];
+    dy = T(kUp3Km) * vv[4] + T(kUp3K0) * vv[0] + T(kUp3K1) * vv[5] + T(kUp3K2) * vv[6];
+    return lap + T(o.gx) * dx + T(o.gy) * dy;
+  }
+}
+
+// Point (i, j) of flat index q for q < 2^31 (checked at setup).
+__device__ __forceinline__ void up3_ij(const Up3Op& o, long long q, int& i, int& j) {
+  const unsigned qq = (unsigned)q;
+  j = (int)(qq / (unsigned)o.nx);
+  i = (int)(qq - (unsigned)j * (unsigned)o.nx);
+}
+
+// One fused Leja iteration on the upwind operators (FP64 / mixed basis):
+// y_{m+1} = (Op y_m - c y_m)/gamma - xi_m y_m, p_{m+1} = p_m + d_{m+1} y_{m+1},
+// the two norms, and the stop test in the last block.
+template <bool BURGERS, typename T>
+static __global__ void __launch_bounds__(kThreadsPerBlock)
+    leja_iter_up3_kernel(const LoopArgs* __restrict__ Ap, LoopState* __restrict__ st, double* __restrict__ partials,
+                         unsigned int* __restrict__ ticket, cudaGraphConditionalHandle cond) {
+  const LoopArgs& A = *Ap;
+  const int m = __ldcg(&st->m);
+  count_launch(st);
+  if (__ldcg(&st->done)) return;
+  const Up3Op o = A.up;
+  const double xim = __ldg(A.xi + m);
+  const double dm1 = __ldg(A.d + m + 1);
+  const double d0 = __ldg(A.d);
+  const T ig = T(A.inv_gamma);
+  const T cs = T(-A.up_c * A.inv_gamma - xim);  // -c/gamma - xi_m
+  T* dst = reinterpret_cast<T*>((m & 1) ? A.y1 : A.y0);
+  const T* src = reinterpret_cast<const T*>(((m - 1) & 1) ? A.y1 : A.y0);
+  double sy = 0.0, sp = 0.0;
+  for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < o.n; q += (long long)gridDim.x * blockDim.x) {
+    int i, j;
+    up3_ij(o, q, i, j);
+    long long pts[7];
+    up3_points(o, i, j, pts);
+    T v, yc;
+    if (m == 0) {
+      v = up3_apply<BURGERS, T, double>(o, A.u, A.w, pts);
+      yc = T(__ldg(A.w + q));
+    } else {
+      v = up3_apply<BURGERS, T, T>(o, A.u, src, pts);
+      yc = src[q];
+    }
+    v = ig * v + cs * yc;
+    dst[q] = v;
+    const double vd = double(v);
+    const double po = m == 0 ? d0 * double(yc) : A.p[q];
+    const double pn = fma(dm1, vd, po);
+    A.p[q] = pn;
+    sy = fma(vd, vd, sy);
+    sp = fma(pn, pn, sp);
+  }
+  if (!last_block_total2(sy, sp, partials, ticket)) return;
+  if (threadIdx.x == 0) leja_finalize(A, st, m, dm1, sy, sp, 1.0, 1.0, cond);
+}
+
+// Float-float form of the upwind diffusion-advection iteration (constant
+// weights, Dot2 over the seven points; storage scaling as the other df64
+// kernels: stored y_m = y_m 2^-sig, p in 2^-kscale units, the new basis
+// vector renormalised by 2^-dlt).
+__device__ __forceinline__ dfv df_dot7(const float (&wh)[7], const float (&wl)[7], const dfv (&y)[7]) {
+  float s, c, p, e, t;
+  two_prod(wh[0], y[0].h, s, c);
+#pragma unroll
+  for (int k = 1; k < 7; ++k) {
+    two_prod(wh[k], y[k].h, p, e);
+    two_sum(s, p, s, t);
+    c = __fadd_rn(c, __fadd_rn(t, e));
+  }
+#pragma unroll
+  for (int k = 0; k < 7; ++k) {
+    c = __fmaf_rn(wh[k], y[k].l, c);
+    c = __fmaf_rn(wl[k], y[k].h, c);
+  }
+  dfv r;
+  two_sum(s, c, r.h, r.l);
+  return r;
+}
+
+static __global__ void __launch_bounds__(kThreadsPerBlock)
+    leja_iter_df_up3_kernel(const LoopArgs* __restrict__ Ap, LoopState* __restrict__ st,
+                            double* __restrict__ partials, unsigned int* __restrict__ ticket,
+                            cudaGraphConditionalHandle cond) {
+  const LoopArgs& A = *Ap;
+  const int m = __ldcg(&st->m);
+  count_launch(st);
+  if (__ldcg(&st->done)) return;
+  const int kexp = __ldcg(&st->kscale);
+  const int sig = __ldcg(&st->sig);
+  const int dlt = __ldcg(&st->dlt);
+  const Up3Op o = A.up;
+  const double xim = __ldg(A.xi + m);
+  const double dm1d = __ldg(A.d + m + 1);
+  const dfv dm1 = df_from_double(dm1d * pow2(sig + dlt - kexp));
+  const dfv d0 = df_from_double(__ldg(A.d));
+  const double sw = pow2(-dlt);
+  double wd[7];
+  up3_weights(o, wd);
+  float wh[7], wl[7];
+#pragma unroll
+  for (int k = 0; k < 7; ++k) {
+    double wk = wd[k] * A.inv_gamma;
+    if (k == 0) wk += -A.up_c * A.inv_gamma - xim;
+    const dfv t = df_from_double(wk * sw);
+    wh[k] = t.h;
+    wl[k] = t.l;
+  }
+  float2* dst = reinterpret_cast<float2*>((m & 1) ? A.y1 : A.y0);
+  const float2* src = reinterpret_cast<const float2*>(((m - 1) & 1) ? A.y1 : A.y0);
+  dfv accy = {0.f, 0.f}, accp = {0.f, 0.f};
+  for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < o.n; q += (long long)gridDim.x * blockDim.x) {
+    int i, j;
+    up3_ij(o, q, i, j);
+    long long pts[7];
+    up3_points(o, i, j, pts);
+    dfv t[7];
+    if (m == 0) {
+#pragma unroll
+      for (int k = 0; k < 7; ++k) t[k] = df_split_scaled(__ldg(A.w + pts[k]), kexp);
+    } else {
+#pragma unroll
+      for (int k = 0; k < 7; ++k) {
+        const float2 f = __ldg(src + pts[k]);
+        t[k] = {f.x, f.y};
+      }
+    }
+    const dfv v = df_dot7(wh, wl, t);
+    dst[q] = make_float2(v.h, v.l);
+    dfv po;
+    if (m == 0) {
+      po = df_mul(d0, t[0]);
+    } else {
+      const float2 f = A.pdf[q];
+      po = {f.x, f.y};
+    }
+    const dfv pn = df_axpy(dm1, v, po);
+    A.pdf[q] = make_float2(pn.h, pn.l);
+    df_acc(accy, __fmul_rn(v.h, v.h));
+    df_acc(accp, __fmul_rn(pn.h, pn.h));
+  }
+  double sy = df_to_double(accy), sp = df_to_double(accp);
+  if (!last_block_total2(sy, sp, partials, ticket)) return;
+  if (threadIdx.x == 0) {
+    leja_finalize(A, st, m, dm1d, sy, sp, pow2(sig + dlt), pow2(kexp), cond);
+    const double rms = sqrt(sy / double(A.n));
+    int e = 0;
+    if (rms > 0.0 && isfinite(rms)) e = ilogb(rms);
+    st->sig = sig + dlt;
+    st->dlt = max(-100, min(100, e));
+  }
+}
+
+// h (f(u) + S) for the upwind operators.
+template <bool BURGERS>
+static __global__ void __launch_bounds__(kThreadsPerBlock)
+    rhs_up3_kernel(Up3Op o, double h, const double* __restrict__ u, const double* __restrict__ src,
+                   double* __restrict__ f_out) {
+  for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < o.n; q += (long long)gridDim.x * blockDim.x) {
+    int i, j;
+    up3_ij(o, q, i, j);
+    long long pts[7];
+    up3_points(o, i, j, pts);
+    double f = up3_apply<BURGERS, double, double>(o, u, u, pts, true);
+    if (src) f += src[q];
+    f_out[q] = h * f;
+  }
+}
+
+// EXPRB32 remainder for the upwind Burgers operator: with p1 = a - u,
+// F(a) - F(u) = (a/2) D(p1^2) exactly (quadratic flux), so R = h (a/2) D(p1^2);
+// R = 0 for the linear operator.
+template <bool BURGERS>
+static __global__ void __launch_bounds__(kThreadsPerBlock)
+    exprb32_stage_up3_kernel(Up3Op o, double h, const double* __restrict__ p1, double* __restrict__ R) {
+  for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < o.n; q += (long long)gridDim.x * blockDim.x) {
+    if constexpr (BURGERS) {
+      int i, j;
+      up3_ij(o, q, i, j);
+      long long pts[7];
+      up3_points(o, i, j, pts);
+      double sq[7];
+#pragma unroll
+      for (int k = 0; k < 7; ++k) {
+        const double v = p1[pts[k]];
+        sq[k] = v * v;
+      }
+      const double dx = kUp3Km * sq[1] + kUp3K0 * sq[0] + kUp3K1 * sq[2] + kUp3K2 * sq[3];
+      const double dy = kUp3Km * sq[4] + kUp3K0 * sq[0] + kUp3K1 * sq[5] + kUp3K2 * sq[6];
+      R[q] = h * 0.5 * (o.gx * dx + o.gy * dy);
+    } else {
+      R[q] = 0.0;
+    }
+  }
+}
+
+// One power-iteration pass on the upwind operators: w = Op(v) / ||v||.
+template <bool BURGERS>
+static __global__ void __launch_bounds__(kThreadsPerBlock)
+    power_pass_up3_kernel(Up3Op o, const double* __restrict__ u, const double* __restrict__ v, double* __restrict__ w,
+                          double* __restrict__ partials, unsigned int* __restrict__ ticket, LoopState* st) {
+  if (__ldcg(&st->pdone)) return;
+  const double sigma = __ldcg(&st->sigma);
+  double s = 0.0, dummy = 0.0;
+  for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < o.n; q += (long long)gridDim.x * blockDim.x) {
+    int i, j;
+    up3_ij(o, q, i, j);
+    long long pts[7];
+    up3_points(o, i, j, pts);
+    const double r = up3_apply<BURGERS, double, double>(o, u, v, pts) * sigma;
+    w[q] = r;
+    s = fma(r, r, s);
+  }
+  if (!last_block_total2(s, dummy, partials, ticket)) return;
+  if (threadIdx.x == 0) power_pass_finish(st, s, o.n);
+}
+
+}  // namespace lexgb

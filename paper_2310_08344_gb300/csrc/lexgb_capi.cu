@@ -22,6 +22,7 @@
 #include "leja_batch.cuh"
 #include "leja_df64.cuh"
 #include "leja_df64_2step.cuh"
+#include "leja_upwind.cuh"
 #include "leja_kernels.cuh"
 #include "lexgb_internal.h"
 #include "lexgb_vertical.h"
@@ -99,6 +100,7 @@ struct lx_ctx {
   long long n = 0;
   int strip_h = 32;
   Geo geo{};
+  Up3Op up3{};  // constants of the upwind operators (kinds LX_*_UP3)
 
   double* d_xi = nullptr;
   CoefSlot coef[2];
@@ -151,10 +153,35 @@ Cand iter_cand(const char* name) {
   return Cand{reinterpret_cast<const void*>(&leja_iter_kernel<KIND, T, VEC>), kThreadsPerBlock, 0, VEC, name};
 }
 
+bool is_burgers(int kind) { return kind == LX_BURGERS || kind == LX_BURGERS_UP3; }
+bool is_up3(int kind) { return kind == LX_ADVDIFF_UP3 || kind == LX_BURGERS_UP3; }
+
 // Candidates for (kind, precision, class); the first is the default.
 std::vector<Cand> candidates(int kind, int precision, int cls) {
   const bool wide = cls == kVec2;
   std::vector<Cand> v;
+  if (is_up3(kind)) {
+    // point-wise kernels: one candidate, the same for both classes
+    const bool b = kind == LX_BURGERS_UP3;
+    const void* f = nullptr;
+    const char* name = nullptr;
+    if (precision == LX_DF64) {
+      if (!b) {
+        f = reinterpret_cast<const void*>(&leja_iter_df_up3_kernel);
+        name = "leja_iter_df_up3";
+      }
+    } else if (precision == LX_MIXED) {
+      f = b ? reinterpret_cast<const void*>(&leja_iter_up3_kernel<true, float>)
+            : reinterpret_cast<const void*>(&leja_iter_up3_kernel<false, float>);
+      name = b ? "leja_iter_burgers_up3_mixed" : "leja_iter_advdiff_up3_mixed";
+    } else {
+      f = b ? reinterpret_cast<const void*>(&leja_iter_up3_kernel<true, double>)
+            : reinterpret_cast<const void*>(&leja_iter_up3_kernel<false, double>);
+      name = b ? "leja_iter_burgers_up3_f64" : "leja_iter_advdiff_up3_f64";
+    }
+    if (f) v.push_back(Cand{f, kThreadsPerBlock, 0, 1, name});
+    return v;
+  }
   if (precision == LX_DF64 && kind == LX_BURGERS) {
     if (wide) {
       v.push_back(Cand{reinterpret_cast<const void*>(&leja_iter_df_pipe_burgers_kernel<1>), kPipeThreads,
@@ -388,6 +415,9 @@ lx_status prepare_loop(lx_ctx* c, int strip_h, int kmax, const double* d, const 
   a.wc0 = (-2.0 * nx2 - 2.0 * ny2 - cc) * ig;
   a.rtol = rtol;
   a.atol = atol;
+  a.up = c->up3;
+  a.up_c = cc;
+  if (is_up3(P.kind)) a.inv_gamma = ig;
   const double wd[4] = {a.wxp, a.wxm, a.wyp, a.wym};
   for (int k = 0; k < 4; ++k) {
     const float hi = (float)wd[k];
@@ -517,7 +547,9 @@ bool valid_problem(const lx_problem* p) {
   if (!p) return false;
   if (p->nx < 1 || p->ny < 1) return false;
   if ((long long)p->nx * p->ny > (1LL << 31)) return false;
-  if (p->kind != LX_ADVDIFF && p->kind != LX_BURGERS) return false;
+  if (p->kind != LX_ADVDIFF && p->kind != LX_BURGERS && p->kind != LX_ADVDIFF_UP3 && p->kind != LX_BURGERS_UP3)
+    return false;
+  if (p->precision == LX_DF64 && p->kind == LX_BURGERS_UP3) return false;
   if (p->precision != LX_FP64 && p->precision != LX_MIXED && p->precision != LX_DF64) return false;
   if (p->precision == LX_DF64 && p->kind == LX_BURGERS && p->nx % 128 != 0) return false;
   if (!std::isfinite(p->nu) || !std::isfinite(p->a)) return false;
@@ -595,6 +627,12 @@ lx_status leja_setup(const lx_problem* prob, int integrator, int max_leja, void*
   c->n = (long long)prob->nx * prob->ny;
   const double dx = 1.0 / prob->nx, dy = 1.0 / prob->ny;
   c->geo = Geo{prob->nx, prob->ny, c->n, 1.0 / (dx * dx), 1.0 / (dy * dy), 1.0 / (2 * dx), 1.0 / (2 * dy)};
+  {
+    // upwind operators on [-1,1)^2: spacing 2/n
+    const double ux = 2.0 / prob->nx, uy = 2.0 / prob->ny;
+    c->up3 = Up3Op{prob->nx, prob->ny, c->n, prob->a >= 0.0 ? 1 : -1, prob->nu / (ux * ux), prob->nu / (uy * uy),
+                   std::fabs(prob->a) / (6.0 * ux), std::fabs(prob->a) / (6.0 * uy)};
+  }
   auto fail = [&](lx_status s) {
     leja_destroy(c);
     return s;
@@ -658,7 +696,7 @@ lx_status leja_setup(const lx_problem* prob, int integrator, int max_leja, void*
 
 lx_status power_bound(lx_ctx* c, const double* u, const double* v0, int max_iters, double* rho, int* iters) {
   if (!c || !v0 || !rho || max_iters < 1 || max_iters > kMaxPower) return LX_E_INVAL;
-  if (c->prob.kind == LX_BURGERS && !u) return LX_E_INVAL;
+  if (is_burgers(c->prob.kind) && !u) return LX_E_INVAL;
   const long long nb = sizeof(double) * c->n;
   if (!c->d_pw[0]) {
     if (!cuda_ok(cudaMalloc((void**)&c->d_pw[0], nb), "cudaMalloc") ||
@@ -677,7 +715,7 @@ lx_status power_bound(lx_ctx* c, const double* u, const double* v0, int max_iter
                                                              c->d_state);
   ++c->stats.kernels;
   LX_CUDA(cudaGetLastError());
-  const bool dfp = P.precision == LX_DF64;
+  const bool dfp = P.precision == LX_DF64 && !is_up3(P.kind);  // upwind kinds: FP64 passes
   PowWeights PW;
   std::memset(&PW, 0, sizeof(PW));
   if (dfp) {
@@ -720,7 +758,13 @@ lx_status power_bound(lx_ctx* c, const double* u, const double* v0, int max_iter
       LX_CUDA(cudaGetLastError());
       continue;
     }
-    if (P.kind == LX_ADVDIFF)
+    if (P.kind == LX_ADVDIFF_UP3)
+      power_pass_up3_kernel<false><<<G, kThreadsPerBlock, 0, c->stream>>>(c->up3, nullptr, in, outv, c->d_partials,
+                                                                          c->d_ticket, c->d_state);
+    else if (P.kind == LX_BURGERS_UP3)
+      power_pass_up3_kernel<true><<<G, kThreadsPerBlock, 0, c->stream>>>(c->up3, u, in, outv, c->d_partials,
+                                                                         c->d_ticket, c->d_state);
+    else if (P.kind == LX_ADVDIFF)
       power_pass_kernel<0><<<G, kThreadsPerBlock, 0, c->stream>>>(c->geo, P.nu, P.a, nullptr, nullptr, in, outv,
                                                                   c->d_partials, c->d_ticket, c->d_state);
     else
@@ -746,10 +790,10 @@ lx_status phi_l_apply(lx_ctx* c, int l, const double* u, const double* w, double
       !std::isfinite(gamma) || !(rtol >= 0.0) || !(atol >= 0.0))
     return LX_E_INVAL;
   if ((const void*)out == (const void*)w || (u && (const void*)out == (const void*)u)) return LX_E_INVAL;
+  if (is_burgers(c->prob.kind) && !u) return LX_E_INVAL;
   lx_status st = begin_call(c);
   if (st != LX_OK) return st;
   if (c->prob.kind == LX_BURGERS) {
-    if (!u) return LX_E_INVAL;
     rhs_kernel<1><<<aux_blocks(c), kThreadsPerBlock, 0, c->stream>>>(c->geo, c->prob.nu, 0.0, 0.0, u, nullptr,
                                                                        c->d_s);
     ++c->stats.kernels;
@@ -776,7 +820,11 @@ lx_status phi_l_apply_vertical(lx_ctx* c, int l, int nc, const double* alpha, co
       if (out[k] == out[j]) return LX_E_INVAL;
   }
   const lx_problem& P = c->prob;
-  if (P.kind == LX_BURGERS && !u) return LX_E_INVAL;
+  if (is_burgers(P.kind) && !u) return LX_E_INVAL;
+  if (is_up3(P.kind)) {
+    set_last_error("vertical interpolation is built for the central-difference operators");
+    return LX_E_INVAL;
+  }
   const bool df = P.precision == LX_DF64;
   bool wide;
   if (df) {
@@ -981,8 +1029,12 @@ lx_status expint_step(lx_ctx* c, const double* u, double* u_low, double* u_high,
   // h f(u) and, for Burgers, u_x + u_y at the linearisation point
   if (P.kind == LX_ADVDIFF)
     rhs_kernel<0><<<G, kThreadsPerBlock, 0, c->stream>>>(c->geo, P.nu, P.a, h, u, c->d_f, c->d_s, c->d_src);
-  else
+  else if (P.kind == LX_BURGERS)
     rhs_kernel<1><<<G, kThreadsPerBlock, 0, c->stream>>>(c->geo, P.nu, 0.0, h, u, c->d_f, c->d_s, c->d_src);
+  else if (P.kind == LX_ADVDIFF_UP3)
+    rhs_up3_kernel<false><<<G, kThreadsPerBlock, 0, c->stream>>>(c->up3, h, u, c->d_src, c->d_f);
+  else
+    rhs_up3_kernel<true><<<G, kThreadsPerBlock, 0, c->stream>>>(c->up3, h, u, c->d_src, c->d_f);
   ++c->stats.kernels;
   LX_CUDA(cudaGetLastError());
   if (c->integrator == LX_ROS_EU) {
@@ -1002,8 +1054,12 @@ lx_status expint_step(lx_ctx* c, const double* u, double* u_low, double* u_high,
     // R = h (F(a) - F(u)) into d_f, then a = u + p1 in u_low
     if (P.kind == LX_ADVDIFF)
       exprb32_stage_kernel<0><<<G, kThreadsPerBlock, 0, c->stream>>>(c->geo, h, u, u_low, c->d_f);
-    else
+    else if (P.kind == LX_BURGERS)
       exprb32_stage_kernel<1><<<G, kThreadsPerBlock, 0, c->stream>>>(c->geo, h, u, u_low, c->d_f);
+    else if (P.kind == LX_ADVDIFF_UP3)
+      exprb32_stage_up3_kernel<false><<<G, kThreadsPerBlock, 0, c->stream>>>(c->up3, h, u_low, c->d_f);
+    else
+      exprb32_stage_up3_kernel<true><<<G, kThreadsPerBlock, 0, c->stream>>>(c->up3, h, u_low, c->d_f);
     ++c->stats.kernels;
     LX_CUDA(cudaGetLastError());
     exprb32_a_kernel<<<G, kThreadsPerBlock, 0, c->stream>>>(c->n, u, u_low);
@@ -1124,6 +1180,8 @@ lx_status tune_time(lx_ctx* c, const Cand& k, int H, int iters, double* us) {
   a.s = c->d_s;
   a.xi = c->d_xi;
   a.d = c->coef[0].dev;
+  a.up = c->up3;
+  a.up_c = -20.0;
   a.wxp = a.wxm = a.wyp = a.wym = 0.25;
   a.lx = a.ly = a.gx = a.gy = a.inv_gamma = 0.25;
   a.wc0 = 1.0;

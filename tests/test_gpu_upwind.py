@@ -1,0 +1,145 @@
+"""GPU parity on the paper's own discretisation (periodic [-1,1)^2, central
+Laplacian, third-order upwind gradient): the diffusion-advection problems
+with and without a source (the paper's Problems I and II) and the flux-form
+Burgers problem (Problem III), against the oracle on the same inputs.
+Bar: relative L2 <= 1e-10 and the same Leja iteration count +-1 (FP64 and
+float-float); the mixed form is held to 1e-5 and reported.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-10
+NU, A = 1.0, 10.0  # the paper's Problems I-III: diffusion 1, advection / flux coefficient 10
+
+
+@pytest.fixture(scope="module")
+def lx():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2310_08344_gb300 as m
+
+    return m
+
+
+@pytest.fixture(scope="module")
+def xi_oracle():
+    return oracle.leja_points(1000)
+
+
+def rel(a, b):
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+def dev(x):
+    return torch.from_numpy(np.ascontiguousarray(x)).cuda()
+
+
+def _interval(kind, nx, ny, a, u):
+    rho, _, _ = oracle.power_iteration(kind, nx, ny, NU, a, u, synth.power_start(nx * ny, 5), 10)
+    return oracle.spectral_interval(rho)
+
+
+@pytest.mark.parametrize("prec", ["FP64", "MIXED", "DF64"])
+@pytest.mark.parametrize("nx,ny", [(64, 64), (96, 50), (128, 128)])
+@pytest.mark.parametrize("a", [A, -4.0])
+def test_phi_advdiff_up3(lx, xi_oracle, prec, nx, ny, a):
+    u0 = synth.problem1_ic(nx, ny, seed=3)
+    h = 50 * synth.cfl_step_pm1(nx, ny, NU, a)
+    c, g = _interval(oracle.ADVDIFF_UP3, nx, ny, a, None)
+    ctx = lx.leja_setup(nx, ny, NU, a, lx.ADVDIFF_UP3, getattr(lx, prec))
+    out = torch.empty(nx * ny, dtype=torch.float64, device="cuda")
+    for l in (0, 1):
+        st, it = lx.phi_l_apply(ctx, l, None, dev(u0), out, c, g, h, TOL, TOL)
+        ref, it_o, st_o = oracle.leja_phi(oracle.ADVDIFF_UP3, nx, ny, NU, a, None, l, u0, c, g, h, TOL, TOL, xi_oracle)
+        assert st == 0 and st_o == 0
+        e = rel(out.cpu().numpy(), ref)
+        if prec == "MIXED":
+            print(f"mixed up3 {nx}x{ny} l={l}: rel_l2 vs FP64 oracle {e:.3e}")
+            assert e <= 1e-5 and abs(it - it_o) <= 3
+        else:
+            assert e <= TOL and abs(it - it_o) <= 1
+
+
+@pytest.mark.parametrize("prec", ["FP64", "MIXED"])
+@pytest.mark.parametrize("nx,ny", [(64, 64), (80, 48)])
+def test_phi_burgers_up3(lx, xi_oracle, prec, nx, ny):
+    u = synth.problem3_ic(nx, ny, seed=4)
+    w = synth.random_field(nx * ny, seed=5)
+    h = 30 * synth.cfl_step_pm1(nx, ny, NU, A * np.abs(u).max())
+    c, g = _interval(oracle.BURGERS_UP3, nx, ny, A, u)
+    ctx = lx.leja_setup(nx, ny, NU, A, lx.BURGERS_UP3, getattr(lx, prec))
+    out = torch.empty(nx * ny, dtype=torch.float64, device="cuda")
+    st, it = lx.phi_l_apply(ctx, 1, dev(u), dev(w), out, c, g, h, TOL, TOL)
+    ref, it_o, st_o = oracle.leja_phi(oracle.BURGERS_UP3, nx, ny, NU, A, u, 1, w, c, g, h, TOL, TOL, xi_oracle)
+    assert st == 0 and st_o == 0
+    bar = 1e-5 if prec == "MIXED" else TOL
+    assert rel(out.cpu().numpy(), ref) <= bar and abs(it - it_o) <= (3 if prec == "MIXED" else 1)
+
+
+@pytest.mark.parametrize("kind", [2, 3])
+@pytest.mark.parametrize("prec", ["FP64", "DF64"])
+def test_power_bound_up3(lx, kind, prec):
+    if kind == 3 and prec == "DF64":
+        pytest.skip("float-float form not offered for the upwind Burgers operator")
+    nx, ny = 96, 64
+    u = synth.problem3_ic(nx, ny, seed=6) if kind == 3 else None
+    v0 = synth.power_start(nx * ny, 5)
+    ctx = lx.leja_setup(nx, ny, NU, A, kind, getattr(lx, prec))
+    st, rho, it = lx.power_bound(ctx, dev(u) if u is not None else None, dev(v0), 10)
+    rho_o, it_o, st_o = oracle.power_iteration(kind, nx, ny, NU, A, u, v0, 10)
+    assert st == 0 and st_o == 0 and it == it_o
+    assert abs(rho - rho_o) <= 1e-12 * rho_o
+
+
+@pytest.mark.parametrize("kind,integ,prec,source", [(2, 0, "FP64", False), (2, 0, "FP64", True), (2, 0, "DF64", True),
+                                                    (2, 1, "DF64", False), (3, 0, "FP64", False),
+                                                    (3, 1, "FP64", False), (3, 1, "FP64", True)])
+def test_expint_step_up3(lx, xi_oracle, kind, integ, prec, source):
+    # Problem I (Ros-Eu), Problem II (with the paper's source), Problem III
+    # (EXPRB32, with and without a source)
+    n = 64
+    if kind == 2:
+        u = synth.problem1_ic(n, n)
+        h = 50 * synth.cfl_step_pm1(n, n, NU, A)
+    else:
+        u = synth.problem3_ic(n, n)
+        h = 30 * synth.cfl_step_pm1(n, n, NU, A * np.abs(u).max())
+    S = synth.problem2_source(n, n) if source else None
+    c, g = _interval(kind, n, n, A, u if kind == 3 else None)
+    ctx = lx.leja_setup(n, n, NU, A, kind, getattr(lx, prec), integ)
+    if source:
+        Sd = dev(S)
+        assert lx.lx_ctx_set_source(ctx, Sd) == 0
+    lo = torch.empty(n * n, dtype=torch.float64, device="cuda")
+    hi = torch.empty(n * n, dtype=torch.float64, device="cuda")
+    st, err, it = lx.expint_step(ctx, dev(u), lo, hi, c, g, h, TOL, TOL)
+    if integ == 0:
+        ref, it_o, st_o = oracle.ros_eu(kind, n, n, NU, A, u, c, g, h, TOL, TOL, xi_oracle, source=S)
+        assert st == 0 and st_o == 0 and abs(it - it_o) <= 1
+        assert rel(hi.cpu().numpy(), ref) <= TOL
+    else:
+        rlo, rhi, rerr, it_o, st_o = oracle.exprb32(kind, n, n, NU, A, u, c, g, h, TOL, TOL, xi_oracle, source=S)
+        assert st == 0 and st_o == 0 and abs(it - it_o) <= 2
+        assert rel(lo.cpu().numpy(), rlo) <= TOL and rel(hi.cpu().numpy(), rhi) <= TOL
+        if kind == 2:
+            assert err <= 1e-14 and rerr <= 1e-14
+        else:
+            assert abs(err - rerr) <= 1e-6 * rerr
+
+
+def test_up3_forms_not_offered(lx):
+    from paper_2310_08344_gb300 import LexgbError
+
+    with pytest.raises(LexgbError):
+        lx.leja_setup(128, 128, NU, A, lx.BURGERS_UP3, lx.DF64)
+    ctx = lx.leja_setup(64, 64, NU, A, lx.ADVDIFF_UP3, lx.FP64)
+    w = dev(synth.problem1_ic(64, 64))
+    outs = [torch.empty(64 * 64, dtype=torch.float64, device="cuda")]
+    st, _ = lx.phi_l_apply_vertical(ctx, 1, [1.0], None, w, outs, -1e3, 250.0, 1e-3, TOL, TOL)
+    assert st == 1
