@@ -14,7 +14,7 @@
 // the caches).
 #pragma once
 
-#include "leja_df64.cuh"
+#include "leja_df64_2step.cuh"
 
 namespace lexgb {
 
@@ -292,6 +292,175 @@ static __global__ void __launch_bounds__(kThreadsPerBlock)
   }
   if (!last_block_total2(s, dummy, partials, ticket)) return;
   if (threadIdx.x == 0) power_pass_finish(st, s, o.n);
+}
+
+}  // namespace lexgb
+
+namespace lexgb {
+
+// ---------------------------------------------------------------------------
+// Pipelined float-float iteration for the upwind diffusion-advection
+// operator (nx % 128 == 0): the same warp-per-row-range layout as the
+// central-difference pipelined kernel.  Rows r0-2 .. r1+1 stream through a
+// shared-memory ring (two-point column halos); each lane keeps its four
+// points of five consecutive rows in registers, so the seven-point stencil
+// takes its y-neighbours from the register window and its x-neighbours from
+// the centre row (shuffles, and the ring's halo for lanes 0 and 31).
+// ---------------------------------------------------------------------------
+constexpr int kUpStages = 7;  // ring slots per warp (two rows in flight)
+constexpr int kUpSmemBytes = kPipeWarps * kUpStages * kSlotElems2 * 8;
+
+template <typename S, bool FIRST>
+__device__ __forceinline__ void df_strip_up3(const LoopArgs& A, const S* __restrict__ src, float2* __restrict__ dst,
+                                             float2* __restrict__ p, unsigned long long* ring, int col0, int r0,
+                                             int r1, const float (&wh)[7], const float (&wl)[7], dfv d0, dfv dm1,
+                                             int sc, int s, dfv& accy, dfv& accp) {
+  const int lane = threadIdx.x & 31;
+  const int nx = A.nx, ny = A.ny;
+  const int c = col0 + lane * 4;
+  const int cw = col0 == 0 ? nx - 2 : col0 - 2;
+  const int ce = (col0 + kPipeRow >= nx) ? 0 : col0 + kPipeRow;
+  const int nrows = r1 - r0;
+  const int last_q = nrows + 3;  // rows q = 0 .. nrows+3 are r0-2 .. r1+1
+  auto slot = [&](int q) { return ring + (size_t)(q % kUpStages) * kSlotElems2; };
+  auto issue = [&](int q) {
+    if (q <= last_q) {
+      const int ry = wrap_row(r0 - 2 + q, ny);
+      unsigned long long* sl = slot(q);
+      const S* row = src + (size_t)ry * nx;
+      cp_async16(sl + 2 + lane * 4, row + c);
+      cp_async16(sl + 4 + lane * 4, row + c + 2);
+      if (lane == 0) cp_async16(sl, row + cw);
+      if (lane == 31) cp_async16(sl + 2 + kPipeRow, row + ce);
+      if constexpr (!FIRST) {
+        if (q >= 4) {  // p of output row r0 + q - 4 arrives with y row r0 + q - 2
+          const float2* prow = p + (size_t)(r0 + q - 4) * nx;
+          cp_async16(sl + kY2Slot + lane * 4, prow + c);
+          cp_async16(sl + kY2Slot + lane * 4 + 2, prow + c + 2);
+        }
+      }
+    }
+    cp_commit();
+  };
+  // window rows: w0..w4 = grid rows r-2 .. r+2 of output row r
+  dfv w0[4], w1[4], w2[4], w3[4], w4[4];
+  for (int q = 0; q < kUpStages - 1; ++q) issue(q);
+  cp_wait<kUpStages - 5>();  // rows 0..3 complete
+  __syncwarp();
+  df_from_raw4<S>(slot(0) + 2 + lane * 4, sc, w0);
+  df_from_raw4<S>(slot(1) + 2 + lane * 4, sc, w1);
+  df_from_raw4<S>(slot(2) + 2 + lane * 4, sc, w2);
+  df_from_raw4<S>(slot(3) + 2 + lane * 4, sc, w3);
+  for (int a = 0; a < nrows; ++a) {
+    issue(a + kUpStages - 1);
+    cp_wait<kUpStages - 5>();  // row a+4 complete
+    __syncwarp();
+    const unsigned long long* sn = slot(a + 4);
+    const unsigned long long* sc2 = slot(a + 2);  // centre row: halo points
+    df_from_raw4<S>(sn + 2 + lane * 4, sc, w4);
+    dfv pold[4];
+    if constexpr (!FIRST) df_from_raw4<float2>(sn + kY2Slot + lane * 4, 0, pold);
+    // x-neighbours of the centre row
+    const dfv u3 = shfl_up_df(w2[3]), u2 = shfl_up_df(w2[2]);
+    const dfv d0n = shfl_down_df(w2[0]), d1n = shfl_down_df(w2[1]);
+    // (lane 0 / lane 31 read their halo from the ring; the selects keep the
+    // shuffles above outside any divergent branch)
+    const dfv hw1 = df_from_raw<S>(sc2 + 1, sc), hw2 = df_from_raw<S>(sc2 + 0, sc);
+    const dfv he1 = df_from_raw<S>(sc2 + 2 + kPipeRow, sc), he2 = df_from_raw<S>(sc2 + 3 + kPipeRow, sc);
+    const dfv wm1 = lane == 0 ? hw1 : u3, wm2 = lane == 0 ? hw2 : u2;  // columns c-1, c-2
+    const dfv ep1 = lane == 31 ? he1 : d0n, ep2 = lane == 31 ? he2 : d1n;  // columns c+4, c+5
+    const dfv xm1[4] = {wm1, w2[0], w2[1], w2[2]};
+    const dfv xm2[4] = {wm2, wm1, w2[0], w2[1]};
+    const dfv xp1[4] = {w2[1], w2[2], w2[3], ep1};
+    const dfv xp2[4] = {w2[2], w2[3], ep1, ep2};
+    dfv ynew[4], pnew[4];
+    float fy = 0.f, fp = 0.f;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      // [C, X(-s), X(s), X(2s), Y(-s), Y(s), Y(2s)]
+      const dfv t[7] = {w2[k],
+                        s > 0 ? xm1[k] : xp1[k],
+                        s > 0 ? xp1[k] : xm1[k],
+                        s > 0 ? xp2[k] : xm2[k],
+                        s > 0 ? w1[k] : w3[k],
+                        s > 0 ? w3[k] : w1[k],
+                        s > 0 ? w4[k] : w0[k]};
+      ynew[k] = df_dot7(wh, wl, t);
+      const dfv po = FIRST ? df_mul(d0, w2[k]) : pold[k];
+      pnew[k] = df_axpy(dm1, ynew[k], po);
+      fy = __fmaf_rn(ynew[k].h, ynew[k].h, fy);
+      fp = __fmaf_rn(pnew[k].h, pnew[k].h, fp);
+    }
+    df_acc(accy, fy);
+    df_acc(accp, fp);
+    const size_t ro = (size_t)(r0 + a) * nx;
+    df_store_row<4>(dst + ro, c, nx, ynew);
+    df_store_row<4>(p + ro, c, nx, pnew);
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      w0[k] = w1[k];
+      w1[k] = w2[k];
+      w2[k] = w3[k];
+      w3[k] = w4[k];
+    }
+    __syncwarp();
+  }
+  cp_wait<0>();
+  __syncwarp();
+}
+
+template <int MINB>
+__global__ void __launch_bounds__(kPipeThreads, MINB)
+    leja_iter_df_pipe_up3_kernel(const LoopArgs* __restrict__ Ap, LoopState* __restrict__ st,
+                                 double* __restrict__ partials, unsigned int* __restrict__ ticket,
+                                 cudaGraphConditionalHandle cond) {
+  extern __shared__ __align__(16) unsigned long long up3_smem[];
+  const LoopArgs& A = *Ap;
+  const int m = __ldcg(&st->m);
+  count_launch(st);
+  if (__ldcg(&st->done)) return;
+  const int kexp = __ldcg(&st->kscale);
+  const int sig = __ldcg(&st->sig);
+  const int dlt = __ldcg(&st->dlt);
+  const Up3Op o = A.up;
+  const double xim = __ldg(A.xi + m);
+  const double dm1d = __ldg(A.d + m + 1);
+  const dfv dm1 = df_from_double(dm1d * pow2(sig + dlt - kexp));
+  const dfv d0 = df_from_double(__ldg(A.d));
+  const double sw = pow2(-dlt);
+  double wd[7];
+  up3_weights(o, wd);
+  float wh[7], wl[7];
+#pragma unroll
+  for (int k = 0; k < 7; ++k) {
+    double wk = wd[k] * A.inv_gamma;
+    if (k == 0) wk += -A.up_c * A.inv_gamma - xim;
+    const dfv t = df_from_double(wk * sw);
+    wh[k] = t.h;
+    wl[k] = t.l;
+  }
+  float2* dst = reinterpret_cast<float2*>((m & 1) ? A.y1 : A.y0);
+  const float2* src = reinterpret_cast<const float2*>(((m - 1) & 1) ? A.y1 : A.y0);
+  dfv accy = {0.f, 0.f}, accp = {0.f, 0.f};
+  const int warp = threadIdx.x >> 5;
+  unsigned long long* ring = up3_smem + (size_t)warp * kUpStages * kSlotElems2;
+  for_each_segment(o.nx, o.ny, A.strip_h, blockIdx.x * kPipeWarps + warp, gridDim.x * kPipeWarps,
+                   [&](int col0, int r0, int r1) {
+    if (m == 0)
+      df_strip_up3<double, true>(A, A.w, dst, A.pdf, ring, col0, r0, r1, wh, wl, d0, dm1, kexp, o.s, accy, accp);
+    else
+      df_strip_up3<float2, false>(A, src, dst, A.pdf, ring, col0, r0, r1, wh, wl, d0, dm1, kexp, o.s, accy, accp);
+  });
+  double sy = df_to_double(accy), sp = df_to_double(accp);
+  if (!last_block_total2(sy, sp, partials, ticket)) return;
+  if (threadIdx.x == 0) {
+    leja_finalize(A, st, m, dm1d, sy, sp, pow2(sig + dlt), pow2(kexp), cond);
+    const double rms = sqrt(sy / double(A.n));
+    int e = 0;
+    if (rms > 0.0 && isfinite(rms)) e = ilogb(rms);
+    st->sig = sig + dlt;
+    st->dlt = max(-100, min(100, e));
+  }
 }
 
 }  // namespace lexgb

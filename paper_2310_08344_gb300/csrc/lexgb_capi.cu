@@ -166,6 +166,13 @@ std::vector<Cand> candidates(int kind, int precision, int cls) {
     const void* f = nullptr;
     const char* name = nullptr;
     if (precision == LX_DF64) {
+      if (!b && wide) {
+        // pipelined (nx % 128 == 0, aligned vectors), then the point-wise form
+        v.push_back(Cand{reinterpret_cast<const void*>(&leja_iter_df_pipe_up3_kernel<3>), kPipeThreads,
+                         kUpSmemBytes, 4, "leja_iter_df_pipe_up3_b3"});
+        v.push_back(Cand{reinterpret_cast<const void*>(&leja_iter_df_pipe_up3_kernel<2>), kPipeThreads,
+                         kUpSmemBytes, 4, "leja_iter_df_pipe_up3_b2"});
+      }
       if (!b) {
         f = reinterpret_cast<const void*>(&leja_iter_df_up3_kernel);
         name = "leja_iter_df_up3";
@@ -188,6 +195,10 @@ std::vector<Cand> candidates(int kind, int precision, int cls) {
                        kPipeSmemBytesB, 4, "leja_iter_df_pipe_burgers_b1"});
       v.push_back(Cand{reinterpret_cast<const void*>(&leja_iter_df_pipe_burgers_kernel<2>), kPipeThreads,
                        kPipeSmemBytesB, 4, "leja_iter_df_pipe_burgers_b2"});
+      v.push_back(Cand{reinterpret_cast<const void*>(&leja_iter_df_pipe2_burgers_kernel<1, 5>), kPipeThreads,
+                       pipe2b_smem_bytes<5>(), 4, "leja_iter_df_pipe2_burgers_b1", 2});
+      v.push_back(Cand{reinterpret_cast<const void*>(&leja_iter_df_pipe2_burgers_kernel<2, 5>), kPipeThreads,
+                       pipe2b_smem_bytes<5>(), 4, "leja_iter_df_pipe2_burgers_b2", 2});
     }
     return v;
   }

@@ -143,3 +143,22 @@ def test_up3_forms_not_offered(lx):
     outs = [torch.empty(64 * 64, dtype=torch.float64, device="cuda")]
     st, _ = lx.phi_l_apply_vertical(ctx, 1, [1.0], None, w, outs, -1e3, 250.0, 1e-3, TOL, TOL)
     assert st == 1
+
+
+@pytest.mark.parametrize("name,strip_h", [("leja_iter_df_pipe_up3_b3", 0), ("leja_iter_df_pipe_up3_b3", 8),
+                                          ("leja_iter_df_pipe_up3_b2", 32), ("leja_iter_df_up3", 8)])
+@pytest.mark.parametrize("a", [A, -4.0])
+def test_df64_up3_candidates(lx, xi_oracle, name, strip_h, a):
+    # every float-float candidate of the upwind operator on a grid with two
+    # column strips and a ragged row range, both upwind sides
+    nx, ny = 256, 100
+    u0 = synth.problem1_ic(nx, ny, seed=7)
+    h = 40 * synth.cfl_step_pm1(nx, ny, NU, a)
+    c, g = _interval(oracle.ADVDIFF_UP3, nx, ny, a, None)
+    ctx = lx.leja_setup(nx, ny, NU, a, lx.ADVDIFF_UP3, lx.DF64)
+    assert lx.lx_ctx_select_kernel(ctx, name, strip_h) == 0
+    out = torch.empty(nx * ny, dtype=torch.float64, device="cuda")
+    st, it = lx.phi_l_apply(ctx, 1, None, dev(u0), out, c, g, h, TOL, TOL)
+    ref, it_o, st_o = oracle.leja_phi(oracle.ADVDIFF_UP3, nx, ny, NU, a, None, 1, u0, c, g, h, TOL, TOL, xi_oracle)
+    assert st == 0 and st_o == 0 and abs(it - it_o) <= 1
+    assert rel(out.cpu().numpy(), ref) <= TOL
