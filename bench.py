@@ -336,7 +336,7 @@ def run_paper(args, rank, world, local):
     N = n * n
     nu, a, tol = 1.0, 10.0, 1e-12
     which = args.workload
-    prec_name = args.precision if which != "paper3" or args.precision != "df64" else "fp64"
+    prec_name = args.precision
     prec = {"fp64": lx.FP64, "mixed": lx.MIXED, "df64": lx.DF64}[prec_name]
     kind = lx.BURGERS_UP3 if which == "paper3" else lx.ADVDIFF_UP3
     integ = lx.EXPRB32 if which == "paper3" else lx.ROS_EU
@@ -503,8 +503,9 @@ def run_burgers(args, rank, world, local):
     finals = {}
     for prec_name, prec in (("fp64", lx.FP64), ("mixed", lx.MIXED), ("df64", lx.DF64)):
         ctx = lx.leja_setup(n, n, nu, 0.0, lx.BURGERS, prec, lx.EXPRB32, 1000, stream)
+        tune = None
         if not args.no_autotune:
-            lx.lx_ctx_autotune(ctx, 10, None)
+            _, tune = lx.lx_ctx_autotune(ctx, 10, None)
         u = torch.from_numpy(u0).cuda()
         lo, hi = torch.empty_like(u), torch.empty_like(u)
 
@@ -536,7 +537,10 @@ def run_burgers(args, rank, world, local):
         results[prec_name] = {"value": N * sum(its) / (ms / 1e3) / 1e9, "ms_per_step": ms / args.steps,
                               "leja_iters": its, "err_estimates": errs,
                               "avg_iteration_us": 1e3 * stt["loop_ms"] / max(stt["loop_iterations"], 1),
-                              "power_ms_per_step": stt["power_ms"] / args.steps}
+                              "power_ms_per_step": stt["power_ms"] / args.steps,
+                              "kernel": lx.lx_ctx_kernel_name(ctx),
+                              "autotune_us_per_iteration": {f"{t['kernel']}/H{t['strip_h']}": round(t["us"], 2)
+                                                            for t in (tune or {}).get("timings", [])}}
         finals[prec_name] = u.clone()
         ctx.close()
     d = float((finals["mixed"] - finals["fp64"]).norm().item() / finals["fp64"].norm().item())

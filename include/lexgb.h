@@ -28,7 +28,7 @@
  *                      (Problem III with nu = 1, a = 10), J(u) v = nu Lap v +
  *                      a ((u v)_x + (u v)_y); the upwind side follows the sign
  *                      of a (the paper's state stays positive).
- *    LX_DF64 is available for LX_ADVDIFF_UP3 (not LX_BURGERS_UP3); batches,
+ *    LX_DF64 with LX_BURGERS_UP3 needs nx % 128 == 0 (as LX_BURGERS); batches,
  *    vertical interpolation and the allocation-free entry point take the
  *    central operators only.
  *  - Norms: ||x|| = ||x||_2 / sqrt(N) (Sec. 2.2).
@@ -81,7 +81,8 @@ typedef struct {
                      48-bit significand) arithmetic on the FP32 pipe for the
                      basis, the stencil and the polynomial; double inputs and
                      outputs; norms accumulated in float-float from the
-                     leading float of each value.  Not for LX_BURGERS_UP3. */
+                     leading float of each value.  The Burgers kinds
+                     need nx % 128 == 0 in this form. */
 } lx_problem;
 
 typedef struct lx_ctx lx_ctx;
@@ -255,7 +256,10 @@ typedef struct lx_mlp lx_mlp;
 /* lx_integrate with the learned controller: after every accepted step the
  * network proposes the next step size from the attempt's features
  * (log(rho h), log(h / dt_ref), iters / 100, log10(err / tol), ||u||); the
- * factor is clipped to [0.2, 4].  Rejections, and non-finite proposals, fall
+ * factor is clipped to [0.2, 16] (the classical controller grows by at most
+ * 2 per step; the network, trained on steps up to 16 times the current one,
+ * may jump further, e.g. from a cautious first step).  Rejections, and
+ * non-finite proposals, fall
  * back to lx_controller_classical.  The embedded error test (err <= tol)
  * still accepts or rejects every step.  dt_ref > 0 is the explicit CFL step
  * used in the features. */

@@ -464,3 +464,225 @@ __global__ void __launch_bounds__(kPipeThreads, MINB)
 }
 
 }  // namespace lexgb
+
+namespace lexgb {
+
+// ---------------------------------------------------------------------------
+// Pipelined float-float iteration for the upwind Burgers Jacobian
+// J(u) v = nu lap v + a (D_x + D_y)(u v)  (nx % 128 == 0).  With
+// q = u |a| / (6 dx gamma) as float pairs (prepared once per Leja loop) and
+// rat = dx/dy, the weight of v at the point o s of the x stencil is
+// lx [o = +-1] + k_o q (and lap centre terms at o = 0), on the y stencil
+// ly [o = +-1] + k_o rat q, so each point needs q on the same seven points
+// as y: q streams through the ring beside y with the same two-point halos.
+// ---------------------------------------------------------------------------
+constexpr int kSlotElemsUB = 2 * kY2Slot + kPipeRow;  // y (halo 2), q (halo 2), p
+constexpr int kUpSmemBytesB = kPipeWarps * kUpStages * kSlotElemsUB * 8;
+
+// q = u * scale as float pairs.
+static __global__ void __launch_bounds__(kThreadsPerBlock)
+    up3_df_prep_kernel(long long n, const double* __restrict__ u, double scale, float2* __restrict__ q) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    const dfv a = df_split_scaled(u[i] * scale, 0);
+    q[i] = make_float2(a.h, a.l);
+  }
+}
+
+__device__ __forceinline__ dfv df_scale_f(dfv a, float k) {  // a * k, k a small integer
+  float p, e;
+  two_prod(a.h, k, p, e);
+  e = __fmaf_rn(a.l, k, e);
+  dfv r;
+  fast_two_sum(p, e, r.h, r.l);
+  return r;
+}
+
+template <typename S, bool FIRST>
+__device__ __forceinline__ void df_strip_burgers_up3(const LoopArgs& A, const S* __restrict__ src,
+                                                     float2* __restrict__ dst, float2* __restrict__ p,
+                                                     unsigned long long* ring, int col0, int r0, int r1, dfv cc0,
+                                                     dfv lxs, dfv lys, dfv rat, bool square, float swf, dfv d0,
+                                                     dfv dm1, int sc, int s, dfv& accy, dfv& accp) {
+  const int lane = threadIdx.x & 31;
+  const int nx = A.nx, ny = A.ny;
+  const int c = col0 + lane * 4;
+  const int cw = col0 == 0 ? nx - 2 : col0 - 2;
+  const int ce = (col0 + kPipeRow >= nx) ? 0 : col0 + kPipeRow;
+  const int nrows = r1 - r0;
+  const int last_q = nrows + 3;
+  auto slot = [&](int q) { return ring + (size_t)(q % kUpStages) * kSlotElemsUB; };
+  auto issue = [&](int q) {
+    if (q <= last_q) {
+      const int ry = wrap_row(r0 - 2 + q, ny);
+      unsigned long long* sl = slot(q);
+      const S* row = src + (size_t)ry * nx;
+      cp_async16(sl + 2 + lane * 4, row + c);
+      cp_async16(sl + 4 + lane * 4, row + c + 2);
+      if (lane == 0) cp_async16(sl, row + cw);
+      if (lane == 31) cp_async16(sl + 2 + kPipeRow, row + ce);
+      const float2* qrow = A.bq + (size_t)ry * nx;
+      unsigned long long* sq = sl + kY2Slot;
+      cp_async16(sq + 2 + lane * 4, qrow + c);
+      cp_async16(sq + 4 + lane * 4, qrow + c + 2);
+      if (lane == 0) cp_async16(sq, qrow + cw);
+      if (lane == 31) cp_async16(sq + 2 + kPipeRow, qrow + ce);
+      if constexpr (!FIRST) {
+        if (q >= 4) {
+          const float2* prow = p + (size_t)(r0 + q - 4) * nx;
+          unsigned long long* sp = sl + 2 * kY2Slot;
+          cp_async16(sp + lane * 4, prow + c);
+          cp_async16(sp + lane * 4 + 2, prow + c + 2);
+        }
+      }
+    }
+    cp_commit();
+  };
+  dfv w0[4], w1[4], w2[4], w3[4], w4[4];   // y rows r-2 .. r+2
+  dfv g0[4], g1[4], g2[4], g3[4], g4[4];   // q rows r-2 .. r+2
+  for (int q = 0; q < kUpStages - 1; ++q) issue(q);
+  cp_wait<kUpStages - 5>();
+  __syncwarp();
+  df_from_raw4<S>(slot(0) + 2 + lane * 4, sc, w0);
+  df_from_raw4<S>(slot(1) + 2 + lane * 4, sc, w1);
+  df_from_raw4<S>(slot(2) + 2 + lane * 4, sc, w2);
+  df_from_raw4<S>(slot(3) + 2 + lane * 4, sc, w3);
+  df_from_raw4<float2>(slot(0) + kY2Slot + 2 + lane * 4, 0, g0);
+  df_from_raw4<float2>(slot(1) + kY2Slot + 2 + lane * 4, 0, g1);
+  df_from_raw4<float2>(slot(2) + kY2Slot + 2 + lane * 4, 0, g2);
+  df_from_raw4<float2>(slot(3) + kY2Slot + 2 + lane * 4, 0, g3);
+  for (int a = 0; a < nrows; ++a) {
+    issue(a + kUpStages - 1);
+    cp_wait<kUpStages - 5>();
+    __syncwarp();
+    const unsigned long long* sn = slot(a + 4);
+    const unsigned long long* sc2 = slot(a + 2);
+    df_from_raw4<S>(sn + 2 + lane * 4, sc, w4);
+    df_from_raw4<float2>(sn + kY2Slot + 2 + lane * 4, 0, g4);
+    dfv pold[4];
+    if constexpr (!FIRST) df_from_raw4<float2>(sn + 2 * kY2Slot + lane * 4, 0, pold);
+    // x-neighbours of the centre row, of y and of q (shuffles outside any
+    // divergent branch; lanes 0 and 31 take the ring's halo)
+    const dfv yu3 = shfl_up_df(w2[3]), yu2 = shfl_up_df(w2[2]);
+    const dfv yd0 = shfl_down_df(w2[0]), yd1 = shfl_down_df(w2[1]);
+    const dfv qu3 = shfl_up_df(g2[3]), qu2 = shfl_up_df(g2[2]);
+    const dfv qd0 = shfl_down_df(g2[0]), qd1 = shfl_down_df(g2[1]);
+    const unsigned long long* hq = sc2 + kY2Slot;
+    const dfv ym1 = lane == 0 ? df_from_raw<S>(sc2 + 1, sc) : yu3, ym2 = lane == 0 ? df_from_raw<S>(sc2, sc) : yu2;
+    const dfv yp1 = lane == 31 ? df_from_raw<S>(sc2 + 2 + kPipeRow, sc) : yd0;
+    const dfv yp2 = lane == 31 ? df_from_raw<S>(sc2 + 3 + kPipeRow, sc) : yd1;
+    const dfv qm1 = lane == 0 ? df_from_raw<float2>(hq + 1, 0) : qu3, qm2 = lane == 0 ? df_from_raw<float2>(hq, 0) : qu2;
+    const dfv qp1 = lane == 31 ? df_from_raw<float2>(hq + 2 + kPipeRow, 0) : qd0;
+    const dfv qp2 = lane == 31 ? df_from_raw<float2>(hq + 3 + kPipeRow, 0) : qd1;
+    const dfv yxm1[4] = {ym1, w2[0], w2[1], w2[2]}, yxm2[4] = {ym2, ym1, w2[0], w2[1]};
+    const dfv yxp1[4] = {w2[1], w2[2], w2[3], yp1}, yxp2[4] = {w2[2], w2[3], yp1, yp2};
+    const dfv qxm1[4] = {qm1, g2[0], g2[1], g2[2]}, qxm2[4] = {qm2, qm1, g2[0], g2[1]};
+    const dfv qxp1[4] = {g2[1], g2[2], g2[3], qp1}, qxp2[4] = {g2[2], g2[3], qp1, qp2};
+    dfv ynew[4], pnew[4];
+    float fy = 0.f, fp = 0.f;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      // stencil points [C, X(-s), X(s), X(2s), Y(-s), Y(s), Y(2s)] of y and q
+      const dfv yv[7] = {w2[k], s > 0 ? yxm1[k] : yxp1[k], s > 0 ? yxp1[k] : yxm1[k], s > 0 ? yxp2[k] : yxm2[k],
+                         s > 0 ? w1[k] : w3[k], s > 0 ? w3[k] : w1[k], s > 0 ? w4[k] : w0[k]};
+      const dfv qv[7] = {g2[k], s > 0 ? qxm1[k] : qxp1[k], s > 0 ? qxp1[k] : qxm1[k], s > 0 ? qxp2[k] : qxm2[k],
+                         s > 0 ? g1[k] : g3[k], s > 0 ? g3[k] : g1[k], s > 0 ? g4[k] : g0[k]};
+      dfv qy[7];
+#pragma unroll
+      for (int j = 4; j < 7; ++j) qy[j] = square ? qv[j] : df_mul(qv[j], rat);
+      const dfv qcy = square ? qv[0] : df_mul(qv[0], rat);
+      dfv wv[7];
+      wv[0] = df_add(cc0, df_scale_f(df_add(qv[0], qcy), (float)kUp3K0));
+      wv[1] = df_add(lxs, df_scale_f(qv[1], (float)kUp3Km));
+      wv[2] = df_add(lxs, df_scale_f(qv[2], (float)kUp3K1));
+      wv[3] = df_scale_f(qv[3], (float)kUp3K2);
+      wv[4] = df_add(lys, df_scale_f(qy[4], (float)kUp3Km));
+      wv[5] = df_add(lys, df_scale_f(qy[5], (float)kUp3K1));
+      wv[6] = df_scale_f(qy[6], (float)kUp3K2);
+      float wh[7], wl[7];
+#pragma unroll
+      for (int j = 0; j < 7; ++j) {
+        wh[j] = wv[j].h;
+        wl[j] = wv[j].l;
+      }
+      dfv v = df_dot7(wh, wl, yv);
+      v.h *= swf;
+      v.l *= swf;
+      ynew[k] = v;
+      const dfv po = FIRST ? df_mul(d0, w2[k]) : pold[k];
+      pnew[k] = df_axpy(dm1, v, po);
+      fy = __fmaf_rn(v.h, v.h, fy);
+      fp = __fmaf_rn(pnew[k].h, pnew[k].h, fp);
+    }
+    df_acc(accy, fy);
+    df_acc(accp, fp);
+    const size_t ro = (size_t)(r0 + a) * nx;
+    df_store_row<4>(dst + ro, c, nx, ynew);
+    df_store_row<4>(p + ro, c, nx, pnew);
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      w0[k] = w1[k];
+      w1[k] = w2[k];
+      w2[k] = w3[k];
+      w3[k] = w4[k];
+      g0[k] = g1[k];
+      g1[k] = g2[k];
+      g2[k] = g3[k];
+      g3[k] = g4[k];
+    }
+    __syncwarp();
+  }
+  cp_wait<0>();
+  __syncwarp();
+}
+
+template <int MINB>
+__global__ void __launch_bounds__(kPipeThreads, MINB)
+    leja_iter_df_pipe_burgers_up3_kernel(const LoopArgs* __restrict__ Ap, LoopState* __restrict__ st,
+                                         double* __restrict__ partials, unsigned int* __restrict__ ticket,
+                                         cudaGraphConditionalHandle cond) {
+  extern __shared__ __align__(16) unsigned long long up3b_smem[];
+  const LoopArgs& A = *Ap;
+  const int m = __ldcg(&st->m);
+  count_launch(st);
+  if (__ldcg(&st->done)) return;
+  const int kexp = __ldcg(&st->kscale);
+  const int sig = __ldcg(&st->sig);
+  const int dlt = __ldcg(&st->dlt);
+  const Up3Op o = A.up;
+  const double xim = __ldg(A.xi + m);
+  const double dm1d = __ldg(A.d + m + 1);
+  const dfv dm1 = df_from_double(dm1d * pow2(sig + dlt - kexp));
+  const dfv d0 = df_from_double(__ldg(A.d));
+  const float swf = (float)pow2(-dlt);
+  const double ig = A.inv_gamma;
+  const dfv cc0 = df_from_double((-2.0 * o.cxx - 2.0 * o.cyy - A.up_c) * ig - xim);
+  const dfv lxs = df_from_double(o.cxx * ig), lys = df_from_double(o.cyy * ig);
+  const dfv rat = df_from_double(o.gy / o.gx);
+  const bool square = o.gx == o.gy;
+  float2* dst = reinterpret_cast<float2*>((m & 1) ? A.y1 : A.y0);
+  const float2* src = reinterpret_cast<const float2*>(((m - 1) & 1) ? A.y1 : A.y0);
+  dfv accy = {0.f, 0.f}, accp = {0.f, 0.f};
+  const int warp = threadIdx.x >> 5;
+  unsigned long long* ring = up3b_smem + (size_t)warp * kUpStages * kSlotElemsUB;
+  for_each_segment(o.nx, o.ny, A.strip_h, blockIdx.x * kPipeWarps + warp, gridDim.x * kPipeWarps,
+                   [&](int col0, int r0, int r1) {
+    if (m == 0)
+      df_strip_burgers_up3<double, true>(A, A.w, dst, A.pdf, ring, col0, r0, r1, cc0, lxs, lys, rat, square, swf, d0,
+                                         dm1, kexp, o.s, accy, accp);
+    else
+      df_strip_burgers_up3<float2, false>(A, src, dst, A.pdf, ring, col0, r0, r1, cc0, lxs, lys, rat, square, swf,
+                                          d0, dm1, kexp, o.s, accy, accp);
+  });
+  double sy = df_to_double(accy), sp = df_to_double(accp);
+  if (!last_block_total2(sy, sp, partials, ticket)) return;
+  if (threadIdx.x == 0) {
+    leja_finalize(A, st, m, dm1d, sy, sp, pow2(sig + dlt), pow2(kexp), cond);
+    const double rms = sqrt(sy / double(A.n));
+    int e = 0;
+    if (rms > 0.0 && isfinite(rms)) e = ilogb(rms);
+    st->sig = sig + dlt;
+    st->dlt = max(-100, min(100, e));
+  }
+}
+
+}  // namespace lexgb

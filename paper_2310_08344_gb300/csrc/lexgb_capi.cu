@@ -166,6 +166,12 @@ std::vector<Cand> candidates(int kind, int precision, int cls) {
     const void* f = nullptr;
     const char* name = nullptr;
     if (precision == LX_DF64) {
+      if (b && wide) {
+        v.push_back(Cand{reinterpret_cast<const void*>(&leja_iter_df_pipe_burgers_up3_kernel<2>), kPipeThreads,
+                         kUpSmemBytesB, 4, "leja_iter_df_pipe_burgers_up3_b2"});
+        v.push_back(Cand{reinterpret_cast<const void*>(&leja_iter_df_pipe_burgers_up3_kernel<1>), kPipeThreads,
+                         kUpSmemBytesB, 4, "leja_iter_df_pipe_burgers_up3_b1"});
+      }
       if (!b && wide) {
         // pipelined (nx % 128 == 0, aligned vectors), then the point-wise form
         v.push_back(Cand{reinterpret_cast<const void*>(&leja_iter_df_pipe_up3_kernel<3>), kPipeThreads,
@@ -429,6 +435,13 @@ lx_status prepare_loop(lx_ctx* c, int strip_h, int kmax, const double* d, const 
   a.up = c->up3;
   a.up_c = cc;
   if (is_up3(P.kind)) a.inv_gamma = ig;
+  if (P.precision == LX_DF64 && P.kind == LX_BURGERS_UP3) {
+    // q = u |a| / (6 dx gamma) as float pairs for the point weights
+    a.bq = c->d_bq;
+    up3_df_prep_kernel<<<aux_blocks(c), kThreadsPerBlock, 0, c->stream>>>(c->n, u, c->up3.gx * ig, c->d_bq);
+    ++c->stats.kernels;
+    LX_CUDA(cudaGetLastError());
+  }
   const double wd[4] = {a.wxp, a.wxm, a.wyp, a.wym};
   for (int k = 0; k < 4; ++k) {
     const float hi = (float)wd[k];
@@ -560,7 +573,7 @@ bool valid_problem(const lx_problem* p) {
   if ((long long)p->nx * p->ny > (1LL << 31)) return false;
   if (p->kind != LX_ADVDIFF && p->kind != LX_BURGERS && p->kind != LX_ADVDIFF_UP3 && p->kind != LX_BURGERS_UP3)
     return false;
-  if (p->precision == LX_DF64 && p->kind == LX_BURGERS_UP3) return false;
+  if (p->precision == LX_DF64 && p->kind == LX_BURGERS_UP3 && p->nx % 128 != 0) return false;
   if (p->precision != LX_FP64 && p->precision != LX_MIXED && p->precision != LX_DF64) return false;
   if (p->precision == LX_DF64 && p->kind == LX_BURGERS && p->nx % 128 != 0) return false;
   if (!std::isfinite(p->nu) || !std::isfinite(p->a)) return false;
@@ -666,7 +679,7 @@ lx_status leja_setup(const lx_problem* prob, int integrator, int max_leja, void*
   if (integrator == LX_EXPRB32 && !dmalloc((void**)&c->d_p3, nb)) return fail(LX_E_NOMEM);
   if (prob->precision == LX_DF64 && !dmalloc((void**)&c->d_pdf, sizeof(float2) * (size_t)c->n))
     return fail(LX_E_NOMEM);
-  if (prob->precision == LX_DF64 && prob->kind == LX_BURGERS &&
+  if (prob->precision == LX_DF64 && (prob->kind == LX_BURGERS || prob->kind == LX_BURGERS_UP3) &&
       (!dmalloc((void**)&c->d_bq, sizeof(float2) * (size_t)c->n) ||
        !dmalloc((void**)&c->d_br, sizeof(float2) * (size_t)c->n)))
     return fail(LX_E_NOMEM);
@@ -1388,7 +1401,7 @@ static lx_status integrate_impl(lx_ctx* c, double* u, const double* v0, double t
         break;
       }
       if (std::isfinite(y[0])) {
-        const double f = std::exp(std::min(std::log(4.0), std::max(std::log(0.2), (double)y[0])));
+        const double f = std::exp(std::min(std::log(16.0), std::max(std::log(0.2), (double)y[0])));
         h_next = hh * f;
         ++learned;
       }

@@ -3,8 +3,10 @@
 The network (see include/lexgb.h, mlp_*) maps the features of an attempted
 EXPRB32 step -- log(rho h), log(h / dt_CFL), iters / 100, log10(err / tol),
 ||u|| -- to log(h_next / h) and log(iters predicted).  Labels come from the
-method itself: at a state u with current step h, the nine steps
-h_j = h 2^(j/2), j = -4..4, are each attempted; the label step h* is where
+method itself: at a state u with current step h, the thirteen steps
+h_j = h 2^(j/2), j = -4..8 (a quarter to sixteen times h), are each
+attempted in increasing order until one exceeds the target below; the
+label step h* is where
 the measured error crosses 0.8 tol (log-log interpolation between the two
 neighbouring attempts; the largest attempt if all stay below, the smallest if
 none does).  That is the largest step the error test accepts with a margin,
@@ -34,32 +36,39 @@ def generate_samples(n, nu, u0_list, v0, tol, leja_tol, steps_per_traj, dt_cfl, 
     import torch
 
     ctx = B.leja_setup(n, n, nu, 0.0, B.BURGERS, B.FP64, B.EXPRB32, 1000, stream)
+    js = list(range(-4, 9))
+    j0 = js.index(0)
     lo = torch.empty_like(u0_list[0])
-    his = [torch.empty_like(u0_list[0]) for _ in range(9)]
+    his = [torch.empty_like(u0_list[0]) for _ in js]
     X, Y = [], []
     for u0 in u0_list:
         u = u0.clone()
-        h = dt_cfl * 50.0 * (2.0 ** rng.uniform(-2.0, 1.0) if h_scale is None else h_scale)
+        # current steps from ~dt_CFL (a cautious start) to 100 dt_CFL
+        h = dt_cfl * 50.0 * (2.0 ** rng.uniform(-6.0, 1.0) if h_scale is None else h_scale)
         for _ in range(steps_per_traj):
             st, rho, _ = B.power_bound(ctx, u, v0, 10)
             if st != 0:
                 break
             c, g = B.spectral_interval(rho)
-            res = []
-            for j in range(-4, 5):
-                hj = h * 2.0 ** (j / 2.0)
-                st, err, it = B.expint_step(ctx, u, lo, his[j + 4], c, g, hj, leja_tol, leja_tol)
-                res.append((hj, err if st == 0 else float("inf"), it))
-            h0, err0, it0 = res[4]
             target = 0.8 * tol
+            res = []
+            for k, j in enumerate(js):
+                hj = h * 2.0 ** (j / 2.0)
+                st, err, it = B.expint_step(ctx, u, lo, his[k], c, g, hj, leja_tol, leja_tol)
+                e = err if st == 0 else float("inf")
+                res.append((hj, e, it))
+                if j >= 0 and not (e <= target):
+                    break  # past the target: larger steps only cost more Leja iterations
+            h0, err0, it0 = res[j0]
             best = 0
             hb, ib = res[0][0], res[0][2]
-            for k in range(9):
+            for k in range(len(res)):
                 if res[k][1] <= target:
                     best = k
             if res[best][1] <= target:
                 hb, ib = res[best][0], res[best][2]
-                if best < 8 and math.isfinite(res[best + 1][1]) and res[best + 1][1] > target and res[best][1] > 0:
+                if best < len(res) - 1 and math.isfinite(res[best + 1][1]) and res[best + 1][1] > target and \
+                        res[best][1] > 0:
                     e0, e1 = math.log(res[best][1]), math.log(res[best + 1][1])
                     f = (math.log(target) - e0) / (e1 - e0)
                     hb = math.exp(math.log(res[best][0]) + f * (math.log(res[best + 1][0]) - math.log(res[best][0])))
@@ -72,6 +81,8 @@ def generate_samples(n, nu, u0_list, v0, tol, leja_tol, steps_per_traj, dt_cfl, 
             if res[best][1] <= tol:
                 u.copy_(his[best])
             h = res[best][0] * 2.0 ** rng.uniform(-1.0, 1.0)
+            if rng.uniform() < 0.2:  # now and then a cautious step again
+                h = dt_cfl * 50.0 * 2.0 ** rng.uniform(-6.0, 0.0)
     ctx.close()
     return np.asarray(X, dtype=np.float32), np.asarray(Y, dtype=np.float32)
 

@@ -66,8 +66,8 @@ def test_phi_advdiff_up3(lx, xi_oracle, prec, nx, ny, a):
             assert e <= TOL and abs(it - it_o) <= 1
 
 
-@pytest.mark.parametrize("prec", ["FP64", "MIXED"])
-@pytest.mark.parametrize("nx,ny", [(64, 64), (80, 48)])
+@pytest.mark.parametrize("prec,nx,ny", [("FP64", 64, 64), ("FP64", 80, 48), ("MIXED", 64, 64), ("MIXED", 80, 48),
+                                        ("DF64", 128, 128), ("DF64", 256, 72)])
 def test_phi_burgers_up3(lx, xi_oracle, prec, nx, ny):
     u = synth.problem3_ic(nx, ny, seed=4)
     w = synth.random_field(nx * ny, seed=5)
@@ -85,9 +85,7 @@ def test_phi_burgers_up3(lx, xi_oracle, prec, nx, ny):
 @pytest.mark.parametrize("kind", [2, 3])
 @pytest.mark.parametrize("prec", ["FP64", "DF64"])
 def test_power_bound_up3(lx, kind, prec):
-    if kind == 3 and prec == "DF64":
-        pytest.skip("float-float form not offered for the upwind Burgers operator")
-    nx, ny = 96, 64
+    nx, ny = 128, 64
     u = synth.problem3_ic(nx, ny, seed=6) if kind == 3 else None
     v0 = synth.power_start(nx * ny, 5)
     ctx = lx.leja_setup(nx, ny, NU, A, kind, getattr(lx, prec))
@@ -99,11 +97,12 @@ def test_power_bound_up3(lx, kind, prec):
 
 @pytest.mark.parametrize("kind,integ,prec,source", [(2, 0, "FP64", False), (2, 0, "FP64", True), (2, 0, "DF64", True),
                                                     (2, 1, "DF64", False), (3, 0, "FP64", False),
-                                                    (3, 1, "FP64", False), (3, 1, "FP64", True)])
+                                                    (3, 1, "FP64", False), (3, 1, "FP64", True), (3, 1, "DF64", False),
+                                                    (3, 0, "DF64", True)])
 def test_expint_step_up3(lx, xi_oracle, kind, integ, prec, source):
     # Problem I (Ros-Eu), Problem II (with the paper's source), Problem III
     # (EXPRB32, with and without a source)
-    n = 64
+    n = 128 if prec == "DF64" else 64
     if kind == 2:
         u = synth.problem1_ic(n, n)
         h = 50 * synth.cfl_step_pm1(n, n, NU, A)
@@ -137,7 +136,7 @@ def test_up3_forms_not_offered(lx):
     from paper_2310_08344_gb300 import LexgbError
 
     with pytest.raises(LexgbError):
-        lx.leja_setup(128, 128, NU, A, lx.BURGERS_UP3, lx.DF64)
+        lx.leja_setup(96, 96, NU, A, lx.BURGERS_UP3, lx.DF64)  # float-float Burgers needs nx % 128 == 0
     ctx = lx.leja_setup(64, 64, NU, A, lx.ADVDIFF_UP3, lx.FP64)
     w = dev(synth.problem1_ic(64, 64))
     outs = [torch.empty(64 * 64, dtype=torch.float64, device="cuda")]
@@ -160,5 +159,23 @@ def test_df64_up3_candidates(lx, xi_oracle, name, strip_h, a):
     out = torch.empty(nx * ny, dtype=torch.float64, device="cuda")
     st, it = lx.phi_l_apply(ctx, 1, None, dev(u0), out, c, g, h, TOL, TOL)
     ref, it_o, st_o = oracle.leja_phi(oracle.ADVDIFF_UP3, nx, ny, NU, a, None, 1, u0, c, g, h, TOL, TOL, xi_oracle)
+    assert st == 0 and st_o == 0 and abs(it - it_o) <= 1
+    assert rel(out.cpu().numpy(), ref) <= TOL
+
+
+@pytest.mark.parametrize("name,strip_h", [("leja_iter_df_pipe_burgers_up3_b2", 0), ("leja_iter_df_pipe_burgers_up3_b2", 8),
+                                          ("leja_iter_df_pipe_burgers_up3_b1", 32)])
+@pytest.mark.parametrize("a", [A, -4.0])
+def test_df64_burgers_up3_candidates(lx, xi_oracle, name, strip_h, a):
+    nx, ny = 256, 100
+    u = synth.problem3_ic(nx, ny, seed=9) * np.sign(a)  # keep a u > 0 (the upwind side follows sign(a))
+    w = synth.random_field(nx * ny, seed=10)
+    h = 30 * synth.cfl_step_pm1(nx, ny, NU, abs(a) * np.abs(u).max())
+    c, g = _interval(oracle.BURGERS_UP3, nx, ny, a, u)
+    ctx = lx.leja_setup(nx, ny, NU, a, lx.BURGERS_UP3, lx.DF64)
+    assert lx.lx_ctx_select_kernel(ctx, name, strip_h) == 0
+    out = torch.empty(nx * ny, dtype=torch.float64, device="cuda")
+    st, it = lx.phi_l_apply(ctx, 3, dev(u), dev(w), out, c, g, h, TOL, TOL)
+    ref, it_o, st_o = oracle.leja_phi(oracle.BURGERS_UP3, nx, ny, NU, a, u, 3, w, c, g, h, TOL, TOL, xi_oracle)
     assert st == 0 and st_o == 0 and abs(it - it_o) <= 1
     assert rel(out.cpu().numpy(), ref) <= TOL
