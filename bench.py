@@ -63,6 +63,8 @@ def parse():
                    choices=["advdiff4096", "batch256", "burgers2048", "vertical4096", "paper1", "paper2",
                             "paper3"])
     p.add_argument("--cfl", type=float, default=100.0, help="paper workloads: step size in units of dt_CFL")
+    p.add_argument("--tf", type=float, default=None,
+                   help="paper workloads: integrate to this final time and report the end-to-end time")
     return p.parse_args()
 
 
@@ -325,10 +327,16 @@ def run_paper(args, rank, world, local):
       paper2: u_t = A u + S, Rosenbrock-Euler (phi_1 of A u + S),
       paper3: u_t = Lap u + 5 ((u^2)_x + (u^2)_y), EXPRB32 with a power
               bound before every step.
-    Grid --n (the paper uses 8192 and 16384), h = --cfl x dt_CFL."""
+    Grid --n (the paper uses 8192 and 16384), h = --cfl x dt_CFL.  With --tf
+    the run integrates from t = 0 to that final time (the last step shortened)
+    and reports the device time of the whole integration, for comparison with
+    the paper's end-to-end runtimes (16384^2, T_f = 2e-6, 100 dt_CFL)."""
     import torch
 
     import paper_2310_08344_gb300 as lx
+
+    if args.tf is not None:
+        return run_paper_tf(args, rank, world, local)
 
     torch.cuda.set_device(local)
     stream = torch.cuda.current_stream()
@@ -408,6 +416,85 @@ def run_paper(args, rank, world, local):
                          "alg_bytes_per_iteration": alg, "avg_iteration_us": avg_iter_s * 1e6,
                          "peak_source": f"{peak_src} (MEASURED_PEAKS.json hbm_gbs, burst copy)"},
             "gpu_launches": int(stats["kernels"])}
+    if rank == 0:
+        print(json.dumps(line))
+    ctx.close()
+    return 0
+
+
+# The paper's end-to-end runtimes on one A100 for 16384^2, T_f = 2e-6,
+# dt = 100 dt_CFL, tol 1e-12 (its runtime table; context, another machine).
+PAPER_A100_S = {"paper1": 4.76, "paper2": 4.14, "paper3": 15.5}
+
+
+def run_paper_tf(args, rank, world, local):
+    import torch
+
+    import paper_2310_08344_gb300 as lx
+
+    torch.cuda.set_device(local)
+    stream = torch.cuda.current_stream()
+    n = args.n
+    N = n * n
+    nu, a, tol = 1.0, 10.0, 1e-12
+    which = args.workload
+    prec = {"fp64": lx.FP64, "mixed": lx.MIXED, "df64": lx.DF64}[args.precision]
+    kind = lx.BURGERS_UP3 if which == "paper3" else lx.ADVDIFF_UP3
+    integ = lx.EXPRB32 if which == "paper3" else lx.ROS_EU
+    ctx = lx.leja_setup(n, n, nu, a, kind, prec, integ, 1000, stream)
+    u0 = synth.problem3_ic(n, n) if which == "paper3" else synth.problem1_ic(n, n)
+    amax = a * (float(np.abs(u0).max()) if which == "paper3" else 1.0)
+    h = args.cfl * synth.cfl_step_pm1(n, n, nu, amax)
+    v0 = torch.from_numpy(synth.power_start(N, seed=5)).cuda()
+    src = torch.from_numpy(synth.problem2_source(n, n)).cuda() if which == "paper2" else None
+    if src is not None:
+        lx.lx_ctx_set_source(ctx, src)
+    ua = torch.from_numpy(u0).cuda()
+    ub, lo = torch.empty_like(ua), torch.empty_like(ua)
+
+    def integrate(u, v):
+        t, steps, iters = 0.0, 0, 0
+        st, rho, _ = lx.power_bound(ctx, u if which == "paper3" else None, v0, 10)
+        c, g = lx.spectral_interval(rho)
+        while t < args.tf * (1 - 1e-12):
+            hh = min(h, args.tf - t)
+            if which == "paper3":
+                st, rho, _ = lx.power_bound(ctx, u, v0, 10)
+                c, g = lx.spectral_interval(rho)
+                st, err, it = lx.expint_step(ctx, u, lo, v, c, g, hh, tol, tol)
+            elif which == "paper1":
+                st, it = lx.phi_l_apply(ctx, 0, None, u, v, c, g, hh, tol, tol)
+            else:
+                st, err, it = lx.expint_step(ctx, u, None, v, c, g, hh, tol, tol)
+            if st != 0:
+                raise SystemExit(f"{which} step failed: {st}")
+            u, v = v, u
+            t += hh
+            steps += 1
+            iters += it
+        return steps, iters
+
+    integrate(ua.clone(), ub)  # warm-up run (graphs, coefficients)
+    u = ua.clone()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    steps, iters = integrate(u, ub)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    sec = e0.elapsed_time(e1) / 1e3
+    ref = PAPER_A100_S.get(which) if (n == 16384 and abs(args.tf - 2e-6) < 1e-18 and args.cfl == 100.0) else None
+    line = {"metric": "s to T_f (end to end, device time)", "value": sec, "unit": "s", "n_gpus": world,
+            "steps": steps, "warmup": 1, "ms_per_step": sec * 1e3 / max(steps, 1), "higher_is_better": False,
+            "scaling": "weak", "vs_baseline": (sec / ref) if ref else None,
+            "dtype": {"fp64": "f64", "mixed": "f32+f64", "df64": "f32x2 (float-float, FP64-accurate)"}[args.precision],
+            "data": "synthetic",
+            "config": {"workload": f"{which}-{n}x{n}-upwind3-[-1,1]^2-tf{args.tf:g}", "tf": args.tf,
+                       "h_over_dt_cfl": args.cfl, "tol": tol, "leja_iters_total": iters,
+                       "gdof_leja_iter_per_s": N * iters / sec / 1e9, "kernel": lx.lx_ctx_kernel_name(ctx),
+                       "paper_a100_s": ref,
+                       "note": "vs_baseline = this time / the paper's A100 time for the same workload (context: "
+                               "another machine, and dt_CFL read as min(dx^2/4nu, dx/2a))"}}
     if rank == 0:
         print(json.dumps(line))
     ctx.close()
