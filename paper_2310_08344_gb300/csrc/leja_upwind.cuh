@@ -686,3 +686,85 @@ __global__ void __launch_bounds__(kPipeThreads, MINB)
 }
 
 }  // namespace lexgb
+
+namespace lexgb {
+
+// One power-iteration pass on the upwind operators in float-float (one
+// thread per point): w = Op(v) / ||v|| with v the caller's doubles on the
+// first pass and float pairs afterwards.  Op = A (constant weights) or J(u)
+// (weights from q = u |a| / (6 dx) as float pairs).  The squares of w are
+// accumulated exactly enough for a double-accurate rho, as in the central
+// float-float pass.
+template <bool BURGERS>
+static __global__ void __launch_bounds__(kThreadsPerBlock)
+    power_pass_df_up3_kernel(Up3Op o, const void* __restrict__ vin, int vin_double, float2* __restrict__ w,
+                             const float2* __restrict__ q, double* __restrict__ partials,
+                             unsigned int* __restrict__ ticket, LoopState* st) {
+  if (__ldcg(&st->pdone)) return;
+  const dfv sg = df_from_double(__ldcg(&st->sigma));
+  const double* vd = reinterpret_cast<const double*>(vin);
+  const float2* vf = reinterpret_cast<const float2*>(vin);
+  auto ld = [&](long long i) -> dfv {
+    if (vin_double) return df_split_scaled(__ldg(vd + i), 0);
+    const float2 t = __ldg(vf + i);
+    return {t.x, t.y};
+  };
+  double wd[7];
+  up3_weights(o, wd);
+  const dfv lxs = df_from_double(o.cxx), lys = df_from_double(o.cyy), rat = df_from_double(o.gy / o.gx);
+  const dfv cc0 = df_from_double(-2.0 * o.cxx - 2.0 * o.cyy);
+  float ch[7], cl[7];
+#pragma unroll
+  for (int k = 0; k < 7; ++k) {
+    const dfv t = df_from_double(wd[k]);
+    ch[k] = t.h;
+    cl[k] = t.l;
+  }
+  dfv acc = {0.f, 0.f};
+  float small = 0.f;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < o.n; i += (long long)gridDim.x * blockDim.x) {
+    int pi, pj;
+    up3_ij(o, i, pi, pj);
+    long long pts[7];
+    up3_points(o, pi, pj, pts);
+    dfv t[7];
+#pragma unroll
+    for (int k = 0; k < 7; ++k) t[k] = ld(pts[k]);
+    dfv y;
+    if constexpr (BURGERS) {
+      dfv qv[7];
+#pragma unroll
+      for (int k = 0; k < 7; ++k) {
+        const float2 f = __ldg(q + pts[k]);
+        qv[k] = {f.x, f.y};
+      }
+      dfv wv[7];
+      wv[0] = df_add(cc0, df_scale_f(df_add(qv[0], df_mul(qv[0], rat)), (float)kUp3K0));
+      wv[1] = df_add(lxs, df_scale_f(qv[1], (float)kUp3Km));
+      wv[2] = df_add(lxs, df_scale_f(qv[2], (float)kUp3K1));
+      wv[3] = df_scale_f(qv[3], (float)kUp3K2);
+      wv[4] = df_add(lys, df_scale_f(df_mul(qv[4], rat), (float)kUp3Km));
+      wv[5] = df_add(lys, df_scale_f(df_mul(qv[5], rat), (float)kUp3K1));
+      wv[6] = df_scale_f(df_mul(qv[6], rat), (float)kUp3K2);
+      float wh[7], wl[7];
+#pragma unroll
+      for (int k = 0; k < 7; ++k) {
+        wh[k] = wv[k].h;
+        wl[k] = wv[k].l;
+      }
+      y = df_mul(sg, df_dot7(wh, wl, t));
+    } else {
+      y = df_mul(sg, df_dot7(ch, cl, t));
+    }
+    w[i] = make_float2(y.h, y.l);
+    float sq, se;
+    two_prod(y.h, y.h, sq, se);
+    df_acc(acc, sq);
+    small = __fmaf_rn(2.f * y.h, y.l, __fadd_rn(small, se));
+  }
+  double s = df_to_double(acc) + (double)small, dummy = 0.0;
+  if (!last_block_total2(s, dummy, partials, ticket)) return;
+  if (threadIdx.x == 0) power_pass_finish(st, s, o.n);
+}
+
+}  // namespace lexgb

@@ -739,7 +739,14 @@ lx_status power_bound(lx_ctx* c, const double* u, const double* v0, int max_iter
                                                              c->d_state);
   ++c->stats.kernels;
   LX_CUDA(cudaGetLastError());
-  const bool dfp = P.precision == LX_DF64 && !is_up3(P.kind);  // upwind kinds: FP64 passes
+  const bool dfp = P.precision == LX_DF64 && !is_up3(P.kind);
+  const bool dfu = P.precision == LX_DF64 && is_up3(P.kind);  // float-float passes of the upwind kinds
+  if (dfu && P.kind == LX_BURGERS_UP3) {
+    // q = u |a| / (6 dx) as float pairs for the point weights of J(u)
+    up3_df_prep_kernel<<<G, kThreadsPerBlock, 0, c->stream>>>(c->n, u, c->up3.gx, c->d_bq);
+    ++c->stats.kernels;
+    LX_CUDA(cudaGetLastError());
+  }
   PowWeights PW;
   std::memset(&PW, 0, sizeof(PW));
   if (dfp) {
@@ -778,6 +785,18 @@ lx_status power_bound(lx_ctx* c, const double* u, const double* v0, int max_iter
         power_pass_df_kernel<1><<<G, kThreadsPerBlock, 0, c->stream>>>(c->geo, in, k == 1 ? 1 : 0, wf, c->d_bq,
                                                                        c->d_br, PW, c->d_partials, c->d_ticket,
                                                                        c->d_state);
+      ++c->stats.kernels;
+      LX_CUDA(cudaGetLastError());
+      continue;
+    }
+    if (dfu) {
+      float2* wf = reinterpret_cast<float2*>(outv);
+      if (P.kind == LX_ADVDIFF_UP3)
+        power_pass_df_up3_kernel<false><<<G, kThreadsPerBlock, 0, c->stream>>>(
+            c->up3, in, k == 1 ? 1 : 0, wf, nullptr, c->d_partials, c->d_ticket, c->d_state);
+      else
+        power_pass_df_up3_kernel<true><<<G, kThreadsPerBlock, 0, c->stream>>>(
+            c->up3, in, k == 1 ? 1 : 0, wf, c->d_bq, c->d_partials, c->d_ticket, c->d_state);
       ++c->stats.kernels;
       LX_CUDA(cudaGetLastError());
       continue;
