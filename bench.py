@@ -283,6 +283,21 @@ def run_batch(args, rank, world, local):
     ms = e0.elapsed_time(e1)
     stats = lx.batch_stats(b, reset=True)
     value = units / (ms / 1e3) / 1e9
+    # the same batch in float-float (every n here is a multiple of 128)
+    bd = lx.batch_setup(probs, 1000, stream, precision=lx.DF64)
+    for _ in range(args.warmup):
+        lx.batch_step(bd, 0, ws, outs, cs, gs, hs, TOL, TOL)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    dunits = 0.0
+    for _ in range(args.steps):
+        st, its_d, sts_d = lx.batch_step(bd, 0, ws, outs, cs, gs, hs, TOL, TOL)
+        dunits += float(np.dot(npts, its_d))
+    e1.record(stream)
+    torch.cuda.synchronize()
+    dms = e0.elapsed_time(e1)
+    dvalue = dunits / (dms / 1e3) / 1e9
+    bd.close()
     # plain form: one context and one phi_l_apply (one graph loop) per instance
     ctxs = [lx.leja_setup(n, n, nu, a, lx.ADVDIFF, lx.FP64, lx.ROS_EU, 1000, stream) for (n, _, nu, a) in probs]
     for _ in range(max(1, args.warmup)):
@@ -310,7 +325,10 @@ def run_batch(args, rank, world, local):
                        "batch_launches_per_step": stats["loop_iterations"] / max(args.steps, 1)},
             "plain": {"value": pvalue, "unit": UNIT, "ms_per_step": pdt * 1e3 / plain_steps,
                       "path": "one phi_l_apply (graph loop) per instance"},
-            "speedup_vs_plain": (pdt / plain_steps) / (ms / 1e3 / args.steps)}
+            "speedup_vs_plain": (pdt / plain_steps) / (ms / 1e3 / args.steps),
+            "float_float_batch": {"value": dvalue, "unit": UNIT, "ms_per_step": dms / args.steps,
+                                  "converged_instances": sum(1 for s_ in sts_d if s_ == 0),
+                                  "speedup_vs_plain": (pdt / plain_steps) / (dms / 1e3 / args.steps)}}
     if rank == 0:
         print(json.dumps(line))
     for ctx in ctxs:

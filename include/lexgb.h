@@ -333,9 +333,11 @@ int lx_ctx_iters_per_launch(lx_ctx* ctx);
 
 typedef struct lx_batch lx_batch;
 
-/* Set up a batch of `count` diffusion-advection problems (kind LX_ADVDIFF,
- * precision LX_FP64).  Allocates the per-instance basis vectors and the strip
- * table.  max_leja as in leja_setup. */
+/* Set up a batch of `count` diffusion-advection problems (kind LX_ADVDIFF),
+ * all of precision LX_FP64, or all LX_DF64 with nx % 128 == 0 (float-float
+ * batches then also need 16-byte aligned w and out in batch_step, else
+ * LX_E_INVAL there).  Allocates the per-instance basis vectors (and, for
+ * LX_DF64, polynomials) and the strip table.  max_leja as in leja_setup. */
 lx_status batch_setup(int count, const lx_problem* probs, int max_leja, void* cuda_stream, lx_batch** out);
 
 /* phi_l(h_i A_i) w_i for every instance i (Sec. 2.1 Eq. 2 per instance).

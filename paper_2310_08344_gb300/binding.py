@@ -368,9 +368,10 @@ class Batch:
             pass
 
 
-def batch_setup(problems, max_leja=1000, stream=None) -> Batch:
-    """problems: list of (nx, ny, nu, a)."""
-    arr = (LxProblem * len(problems))(*[LxProblem(nx, ny, nu, a, ADVDIFF, FP64) for (nx, ny, nu, a) in problems])
+def batch_setup(problems, max_leja=1000, stream=None, precision=FP64) -> Batch:
+    """problems: list of (nx, ny, nu, a); precision FP64 or DF64 (every nx % 128 == 0)."""
+    arr = (LxProblem * len(problems))(*[LxProblem(nx, ny, nu, a, ADVDIFF, precision)
+                                        for (nx, ny, nu, a) in problems])
     h = _vp()
     st = lib().batch_setup(len(problems), arr, max_leja, _stream_handle(stream), C.byref(h))
     if st != OK:

@@ -310,11 +310,14 @@ namespace lexgb {
 constexpr int kUpStages = 7;  // ring slots per warp (two rows in flight)
 constexpr int kUpSmemBytes = kPipeWarps * kUpStages * kSlotElems2 * 8;
 
-template <typename S, bool FIRST>
+// SG: the upwind side (+1 or -1), a template parameter so that the choice
+// of the stencil points costs no per-point selects.
+template <typename S, bool FIRST, int SG>
 __device__ __forceinline__ void df_strip_up3(const LoopArgs& A, const S* __restrict__ src, float2* __restrict__ dst,
                                              float2* __restrict__ p, unsigned long long* ring, int col0, int r0,
                                              int r1, const float (&wh)[7], const float (&wl)[7], dfv d0, dfv dm1,
-                                             int sc, int s, dfv& accy, dfv& accp) {
+                                             int sc, dfv& accy, dfv& accp) {
+  constexpr int s = SG;
   const int lane = threadIdx.x & 31;
   const int nx = A.nx, ny = A.ny;
   const int c = col0 + lane * 4;
@@ -446,10 +449,17 @@ __global__ void __launch_bounds__(kPipeThreads, MINB)
   unsigned long long* ring = up3_smem + (size_t)warp * kUpStages * kSlotElems2;
   for_each_segment(o.nx, o.ny, A.strip_h, blockIdx.x * kPipeWarps + warp, gridDim.x * kPipeWarps,
                    [&](int col0, int r0, int r1) {
-    if (m == 0)
-      df_strip_up3<double, true>(A, A.w, dst, A.pdf, ring, col0, r0, r1, wh, wl, d0, dm1, kexp, o.s, accy, accp);
-    else
-      df_strip_up3<float2, false>(A, src, dst, A.pdf, ring, col0, r0, r1, wh, wl, d0, dm1, kexp, o.s, accy, accp);
+    if (m == 0) {
+      if (o.s > 0)
+        df_strip_up3<double, true, 1>(A, A.w, dst, A.pdf, ring, col0, r0, r1, wh, wl, d0, dm1, kexp, accy, accp);
+      else
+        df_strip_up3<double, true, -1>(A, A.w, dst, A.pdf, ring, col0, r0, r1, wh, wl, d0, dm1, kexp, accy, accp);
+    } else {
+      if (o.s > 0)
+        df_strip_up3<float2, false, 1>(A, src, dst, A.pdf, ring, col0, r0, r1, wh, wl, d0, dm1, kexp, accy, accp);
+      else
+        df_strip_up3<float2, false, -1>(A, src, dst, A.pdf, ring, col0, r0, r1, wh, wl, d0, dm1, kexp, accy, accp);
+    }
   });
   double sy = df_to_double(accy), sp = df_to_double(accp);
   if (!last_block_total2(sy, sp, partials, ticket)) return;
@@ -497,12 +507,13 @@ __device__ __forceinline__ dfv df_scale_f(dfv a, float k) {  // a * k, k a small
   return r;
 }
 
-template <typename S, bool FIRST>
+template <typename S, bool FIRST, int SG>
 __device__ __forceinline__ void df_strip_burgers_up3(const LoopArgs& A, const S* __restrict__ src,
                                                      float2* __restrict__ dst, float2* __restrict__ p,
                                                      unsigned long long* ring, int col0, int r0, int r1, dfv cc0,
                                                      dfv lxs, dfv lys, dfv rat, bool square, float swf, dfv d0,
-                                                     dfv dm1, int sc, int s, dfv& accy, dfv& accp) {
+                                                     dfv dm1, int sc, dfv& accy, dfv& accp) {
+  constexpr int s = SG;
   const int lane = threadIdx.x & 31;
   const int nx = A.nx, ny = A.ny;
   const int c = col0 + lane * 4;
@@ -666,12 +677,21 @@ __global__ void __launch_bounds__(kPipeThreads, MINB)
   unsigned long long* ring = up3b_smem + (size_t)warp * kUpStages * kSlotElemsUB;
   for_each_segment(o.nx, o.ny, A.strip_h, blockIdx.x * kPipeWarps + warp, gridDim.x * kPipeWarps,
                    [&](int col0, int r0, int r1) {
-    if (m == 0)
-      df_strip_burgers_up3<double, true>(A, A.w, dst, A.pdf, ring, col0, r0, r1, cc0, lxs, lys, rat, square, swf, d0,
-                                         dm1, kexp, o.s, accy, accp);
-    else
-      df_strip_burgers_up3<float2, false>(A, src, dst, A.pdf, ring, col0, r0, r1, cc0, lxs, lys, rat, square, swf,
-                                          d0, dm1, kexp, o.s, accy, accp);
+    if (m == 0) {
+      if (o.s > 0)
+        df_strip_burgers_up3<double, true, 1>(A, A.w, dst, A.pdf, ring, col0, r0, r1, cc0, lxs, lys, rat, square,
+                                              swf, d0, dm1, kexp, accy, accp);
+      else
+        df_strip_burgers_up3<double, true, -1>(A, A.w, dst, A.pdf, ring, col0, r0, r1, cc0, lxs, lys, rat, square,
+                                               swf, d0, dm1, kexp, accy, accp);
+    } else {
+      if (o.s > 0)
+        df_strip_burgers_up3<float2, false, 1>(A, src, dst, A.pdf, ring, col0, r0, r1, cc0, lxs, lys, rat, square,
+                                               swf, d0, dm1, kexp, accy, accp);
+      else
+        df_strip_burgers_up3<float2, false, -1>(A, src, dst, A.pdf, ring, col0, r0, r1, cc0, lxs, lys, rat, square,
+                                                swf, d0, dm1, kexp, accy, accp);
+    }
   });
   double sy = df_to_double(accy), sp = df_to_double(accp);
   if (!last_block_total2(sy, sp, partials, ticket)) return;

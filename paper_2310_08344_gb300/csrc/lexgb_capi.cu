@@ -1463,6 +1463,9 @@ lx_status lx_integrate_learned(lx_ctx* c, double* u, const double* v0, double t_
 
 struct lx_batch {
   int B = 0;
+  bool df = false;            // float-float batch (every nx % 128 == 0)
+  float2* d_pbuf = nullptr;   // df: the polynomials as float pairs
+  std::vector<size_t> poff;
   int K = 1000;
   cudaStream_t stream = nullptr;
   int sm_count = 0;
@@ -1504,7 +1507,8 @@ const void* batch_kernel_ptr() {
 
 lx_status build_batch_graph(lx_batch* b, int v) {
   if (b->exec[v]) return LX_OK;
-  const void* fn = v == 0 ? batch_kernel_ptr<2>() : batch_kernel_ptr<1>();
+  const void* fn = b->df ? reinterpret_cast<const void*>(&leja_batch_df_kernel)
+                         : (v == 0 ? batch_kernel_ptr<2>() : batch_kernel_ptr<1>());
   int per_sm = 0;
   LX_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kThreadsPerBlock, 0));
   const int want = (b->total_strips[v] + kWarpsPerBlock - 1) / kWarpsPerBlock;
@@ -1565,6 +1569,7 @@ void batch_destroy(lx_batch* b) {
   cudaFree(b->d_coef);
   if (b->h_coef) cudaFreeHost(b->h_coef);
   cudaFree(b->d_ybuf);
+  cudaFree(b->d_pbuf);
   for (auto& e : b->ev)
     if (e) cudaEventDestroy(e);
   delete b;
@@ -1575,9 +1580,14 @@ lx_status batch_setup(int count, const lx_problem* probs, int max_leja, void* cu
   *out = nullptr;
   if (max_leja == 0) max_leja = 1000;
   if (max_leja < 16 || max_leja > 4096) return LX_E_INVAL;
+  // one precision for the whole batch: FP64, or float-float with nx % 128 == 0
+  const bool df = probs[0].precision == LX_DF64;
   for (int i = 0; i < count; ++i)
-    if (!valid_problem(probs + i) || probs[i].kind != LX_ADVDIFF || probs[i].precision != LX_FP64) return LX_E_INVAL;
+    if (!valid_problem(probs + i) || probs[i].kind != LX_ADVDIFF ||
+        probs[i].precision != (df ? LX_DF64 : LX_FP64) || (df && probs[i].nx % 128 != 0))
+      return LX_E_INVAL;
   lx_batch* b = new lx_batch();
+  b->df = df;
   auto fail = [&](lx_status s) {
     batch_destroy(b);
     return s;
@@ -1591,10 +1601,11 @@ lx_status batch_setup(int count, const lx_problem* probs, int max_leja, void* cu
   if (!cuda_ok(cudaGetDevice(&dev), "cudaGetDevice") ||
       !cuda_ok(cudaDeviceGetAttribute(&b->sm_count, cudaDevAttrMultiProcessorCount, dev), "sm count"))
     return fail(LX_E_CUDA);
-  // strip tables for the wide (VEC = 2) and generic (VEC = 1) kernels
+  // strip tables for the wide (VEC = 2; float-float: 4) and generic (VEC = 1)
+  // kernels
   std::vector<int> table[2];
   for (int v = 0; v < 2; ++v) {
-    const int vec = v == 0 ? 2 : 1;
+    const int vec = v == 0 ? (df ? 4 : 2) : 1;
     b->first_strip[v].resize(count);
     b->nstrips[v].resize(count);
     for (int i = 0; i < count; ++i) {
@@ -1606,11 +1617,13 @@ lx_status batch_setup(int count, const lx_problem* probs, int max_leja, void* cu
     }
     b->total_strips[v] = (int)table[v].size();
   }
-  size_t ytot = 0;
+  size_t ytot = 0, ptot = 0;
   for (int i = 0; i < count; ++i) {
     b->yoff.push_back(ytot);
+    b->poff.push_back(ptot);
     const size_t n = (size_t)probs[i].nx * probs[i].ny;
     ytot += 2 * ((n + 31) / 32 * 32);
+    ptot += (n + 31) / 32 * 32;
   }
   std::vector<double> xi(b->K);
   if (leja_points(b->K, xi.data()) != LX_OK) return fail(LX_E_INVAL);
@@ -1622,7 +1635,7 @@ lx_status batch_setup(int count, const lx_problem* probs, int max_leja, void* cu
       !dm((void**)&b->d_partials, sizeof(double) * 2 * (size_t)std::max(b->total_strips[0], b->total_strips[1])) ||
       !dm((void**)&b->d_xi, sizeof(double) * b->K) || !dm((void**)&b->d_coef, sizeof(double) * b->K * count) ||
       !cuda_ok(cudaMallocHost((void**)&b->h_coef, sizeof(double) * b->K * count), "cudaMallocHost") ||
-      !dm((void**)&b->d_ybuf, sizeof(double) * ytot))
+      !dm((void**)&b->d_ybuf, sizeof(double) * ytot) || (df && !dm((void**)&b->d_pbuf, sizeof(float2) * ptot)))
     return fail(LX_E_NOMEM);
   for (int v = 0; v < 2; ++v) {
     if (!dm((void**)&b->d_strip_inst[v], sizeof(int) * table[v].size())) return fail(LX_E_NOMEM);
@@ -1649,6 +1662,7 @@ lx_status batch_step(lx_batch* b, int l, const double* const* w, double* const* 
       return LX_E_INVAL;
     if (b->probs[i].nx % 64 != 0 || !aligned16(w[i]) || !aligned16(out[i])) wide = false;
   }
+  if (b->df && !wide) return LX_E_INVAL;  // float-float batches need 16-byte aligned w and out
   const int v = wide ? 0 : 1;
   for (int i = 0; i < b->B; ++i) {
     lx_batch::Key& k = b->keys[i];
@@ -1691,6 +1705,16 @@ lx_status batch_step(lx_batch* b, int l, const double* const* w, double* const* 
     I.y1 = I.y0 + (n + 31) / 32 * 32;
     I.p = out[i];
     I.d = b->d_coef + (size_t)i * b->K;
+    if (b->df) {
+      I.yf0 = reinterpret_cast<float2*>(I.y0);
+      I.yf1 = reinterpret_cast<float2*>(I.y1);
+      I.pf = b->d_pbuf + b->poff[i];
+      const double wd[4] = {I.wxp, I.wxm, I.wyp, I.wym};
+      for (int q = 0; q < 4; ++q) {
+        I.wf[2 * q] = (float)wd[q];
+        I.wf[2 * q + 1] = (float)(wd[q] - (double)I.wf[2 * q]);
+      }
+    }
     mmax = std::max(mmax, I.kmax);
   }
   lx_status st = build_batch_graph(b, v);
@@ -1699,9 +1723,22 @@ lx_status batch_step(lx_batch* b, int l, const double* const* w, double* const* 
   LX_CUDA(cudaMemsetAsync(b->d_tickets, 0, sizeof(unsigned) * b->B, b->stream));
   batch_reset_kernel<<<1, 1, 0, b->stream>>>(b->d_bs, b->B, mmax, b->d_block_ticket);
   LX_CUDA(cudaGetLastError());
+  if (b->df) {
+    // per-instance power-of-two input scaling
+    batch_df_scale_kernel<<<b->grid[v], kThreadsPerBlock, 0, b->stream>>>(b->d_inst, b->d_strip_inst[v], b->H,
+                                                                          b->total_strips[v]);
+    LX_CUDA(cudaGetLastError());
+    batch_df_scale_finish_kernel<<<(b->B + 255) / 256, 256, 0, b->stream>>>(b->d_inst, b->B);
+    LX_CUDA(cudaGetLastError());
+  }
   LX_CUDA(cudaEventRecord(b->ev[0], b->stream));
   LX_CUDA(cudaGraphLaunch(b->exec[v], b->stream));
   LX_CUDA(cudaEventRecord(b->ev[1], b->stream));
+  if (b->df) {
+    batch_df_output_kernel<<<b->grid[v], kThreadsPerBlock, 0, b->stream>>>(b->d_inst, b->d_strip_inst[v], b->H,
+                                                                           b->total_strips[v]);
+    LX_CUDA(cudaGetLastError());
+  }
   LX_CUDA(cudaMemcpyAsync(b->h_inst, b->d_inst, sizeof(BatchInst) * b->B, cudaMemcpyDeviceToHost, b->stream));
   BatchState hs;
   LX_CUDA(cudaMemcpyAsync(&hs, b->d_bs, sizeof(BatchState), cudaMemcpyDeviceToHost, b->stream));

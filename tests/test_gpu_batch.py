@@ -85,3 +85,34 @@ def test_batch_matches_oracle(lx, sizes):
                 assert abs(its[k] - it_o) <= 1, (k, its[k], it_o)
                 got = outs[k].cpu().numpy()
                 assert np.linalg.norm(got - ref) <= TOL * np.linalg.norm(ref), k
+
+
+def test_batch_float_float_matches_oracle(lx):
+    # float-float batch: every nx a multiple of 128, uneven sizes and
+    # coefficients, each instance against the oracle
+    sizes = [(128, 128), (256, 64), (128, 200), (384, 128), (128, 37), (256, 256)]
+    inst = _instances(sizes, seed=11)
+    xi = oracle.leja_points(1000)
+    b = lx.batch_setup([(nx, ny, nu, a) for (nx, ny, nu, a, _) in inst], precision=lx.DF64)
+    ws, outs, cs, gs, hs, refs = [], [], [], [], [], []
+    for (nx, ny, nu, a, s) in inst:
+        u0 = synth.gaussians_ic(nx, ny, seed=s) * 10.0 ** (s % 7 - 3)  # magnitudes 1e-3 .. 1e3 per instance
+        h = 50 * synth.cfl_step(nx, ny, nu, a)
+        c, g = oracle.spectral_interval(max(_symbol_radius(nx, ny, nu, a), 1.0))
+        ws.append(torch.from_numpy(u0).cuda())
+        outs.append(torch.empty(nx * ny, dtype=torch.float64, device="cuda"))
+        cs.append(c)
+        gs.append(g)
+        hs.append(h)
+        refs.append(oracle.leja_phi(oracle.ADVDIFF, nx, ny, nu, a, None, 1, u0, c, g, h, TOL, 0.0, xi))
+    for rep in range(2):
+        st, its, sts = lx.batch_step(b, 1, ws, outs, cs, gs, hs, TOL, 0.0)
+        for k, (ref, it_o, st_o) in enumerate(refs):
+            assert st_o == 0 and sts[k] == 0, (k, sts[k])
+            assert abs(its[k] - it_o) <= 1, (k, its[k], it_o)
+            got = outs[k].cpu().numpy()
+            assert np.linalg.norm(got - ref) <= TOL * np.linalg.norm(ref), k
+    from paper_2310_08344_gb300 import LexgbError
+
+    with pytest.raises(LexgbError):
+        lx.batch_setup([(96, 96, 1e-2, 0.5)], precision=lx.DF64)  # nx % 128 != 0
