@@ -838,6 +838,7 @@ namespace lexgb {
 
 constexpr int kSlotElemsB = kYSlot + 3 * kPipeRow;  // y (+halo), p, q, r
 constexpr int kPipeSmemBytesB = kPipeWarps * kPipeStages * kSlotElemsB * 8;
+constexpr int kPipeSmemBytesB4 = kPipeWarps * 4 * kSlotElemsB * 8;  // the 4-stage variant (3 blocks/SM)
 
 __device__ __forceinline__ dfv df_add(dfv a, dfv b) {
   float s, e;
@@ -862,7 +863,7 @@ static __global__ void burgers_df_prep_kernel(long long n, const double* __restr
   }
 }
 
-template <typename S, bool FIRST>
+template <typename S, bool FIRST, int STAGES = kPipeStages>
 __device__ __forceinline__ void df_strip_pipe_burgers(const LoopArgs& A, const S* __restrict__ src,
                                                       float2* __restrict__ dst, float2* __restrict__ p,
                                                       unsigned long long* ring, int col0, int r0, int r1, dfv xim,
@@ -876,7 +877,7 @@ __device__ __forceinline__ void df_strip_pipe_burgers(const LoopArgs& A, const S
   const int last_q = nrows + 1;
   const dfv lx = {A.bl[0], A.bl[1]}, ly = {A.bl[2], A.bl[3]}, rat = {A.bl[4], A.bl[5]};
   const bool square = A.bl[4] == 1.0f && A.bl[5] == 0.0f && A.bl[0] == A.bl[2] && A.bl[1] == A.bl[3];
-  auto slot = [&](int q) { return ring + (size_t)(q % kPipeStages) * kSlotElemsB; };
+  auto slot = [&](int q) { return ring + (size_t)(q % STAGES) * kSlotElemsB; };
   auto issue = [&](int q) {
     if (q <= last_q) {
       int ry = r0 - 1 + q;
@@ -901,15 +902,15 @@ __device__ __forceinline__ void df_strip_pipe_burgers(const LoopArgs& A, const S
     }
     cp_commit();
   };
-  for (int q = 0; q < kPipeStages - 1; ++q) issue(q);
-  cp_wait<kPipeStages - 3>();
+  for (int q = 0; q < STAGES - 1; ++q) issue(q);
+  cp_wait<STAGES - 3>();
   __syncwarp();
   dfv ys[4], yc[4], yn[4];
   df_from_raw4<S>(slot(0) + 2 + lane * 4, sc, ys);
   df_from_raw4<S>(slot(1) + 2 + lane * 4, sc, yc);
   for (int qc = 1; qc <= nrows; ++qc) {
-    issue(qc + kPipeStages - 2);
-    cp_wait<kPipeStages - 3>();
+    issue(qc + STAGES - 2);
+    cp_wait<STAGES - 3>();
     __syncwarp();
     const unsigned long long* sn = slot(qc + 1);
     const unsigned long long* scn = slot(qc);
@@ -969,7 +970,7 @@ __device__ __forceinline__ void df_strip_pipe_burgers(const LoopArgs& A, const S
   __syncwarp();
 }
 
-template <int MINB>
+template <int MINB, int STAGES = kPipeStages>
 __global__ void __launch_bounds__(kPipeThreads, MINB)
     leja_iter_df_pipe_burgers_kernel(const LoopArgs* __restrict__ Ap, LoopState* __restrict__ st,
                                      double* __restrict__ partials, unsigned int* __restrict__ ticket,
@@ -993,14 +994,14 @@ __global__ void __launch_bounds__(kPipeThreads, MINB)
   float2* dst = reinterpret_cast<float2*>((m & 1) ? A.y1 : A.y0);
   dfv accy = {0.f, 0.f}, accp = {0.f, 0.f};
   const int warp = threadIdx.x >> 5;
-  unsigned long long* ring = pipe_smem_b + (size_t)warp * kPipeStages * kSlotElemsB;
+  unsigned long long* ring = pipe_smem_b + (size_t)warp * STAGES * kSlotElemsB;
   const float2* src = reinterpret_cast<const float2*>(((m - 1) & 1) ? A.y1 : A.y0);
   for_each_segment(nx, ny, H, blockIdx.x * kPipeWarps + warp, gridDim.x * kPipeWarps, [&](int col0, int r0, int r1) {
     if (m == 0)
-      df_strip_pipe_burgers<double, true>(A, A.w, dst, A.pdf, ring, col0, r0, r1, xim, swf, d0, dm1, kexp, accy,
+      df_strip_pipe_burgers<double, true, STAGES>(A, A.w, dst, A.pdf, ring, col0, r0, r1, xim, swf, d0, dm1, kexp, accy,
                                           accp);
     else
-      df_strip_pipe_burgers<float2, false>(A, src, dst, A.pdf, ring, col0, r0, r1, xim, swf, d0, dm1, kexp, accy,
+      df_strip_pipe_burgers<float2, false, STAGES>(A, src, dst, A.pdf, ring, col0, r0, r1, xim, swf, d0, dm1, kexp, accy,
                                            accp);
   });
   double sy = df_to_double(accy), sp = df_to_double(accp);

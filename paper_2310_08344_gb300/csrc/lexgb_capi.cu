@@ -201,6 +201,8 @@ std::vector<Cand> candidates(int kind, int precision, int cls) {
                        kPipeSmemBytesB, 4, "leja_iter_df_pipe_burgers_b1"});
       v.push_back(Cand{reinterpret_cast<const void*>(&leja_iter_df_pipe_burgers_kernel<2>), kPipeThreads,
                        kPipeSmemBytesB, 4, "leja_iter_df_pipe_burgers_b2"});
+      v.push_back(Cand{reinterpret_cast<const void*>(&leja_iter_df_pipe_burgers_kernel<3, 4>), kPipeThreads,
+                       kPipeSmemBytesB4, 4, "leja_iter_df_pipe_burgers_b3_s4"});
       v.push_back(Cand{reinterpret_cast<const void*>(&leja_iter_df_pipe2_burgers_kernel<1, 5>), kPipeThreads,
                        pipe2b_smem_bytes<5>(), 4, "leja_iter_df_pipe2_burgers_b1", 2});
       v.push_back(Cand{reinterpret_cast<const void*>(&leja_iter_df_pipe2_burgers_kernel<2, 5>), kPipeThreads,
