@@ -29,6 +29,8 @@ _leja_cache: dict[int, np.ndarray] = {}
 
 _dp = C.POINTER(C.c_double)
 _ip = C.POINTER(C.c_int)
+# a caller's right-hand side f(in, out, user) over n doubles (Sec. 2)
+_RHS = C.CFUNCTYPE(None, _dp, _dp, C.c_void_p)
 
 
 def _p(a):
@@ -77,6 +79,19 @@ def lib():
             L.or_integrate_exprb32.argtypes = [C.c_int, C.c_int, C.c_int, C.c_double, C.c_double, _dp, _dp,
                                                C.c_double, C.c_double, C.c_double, C.c_double, _dp, C.c_int,
                                                C.c_int, _ip, _ip, C.POINTER(C.c_longlong), _dp, _dp]
+            L.or_fd_jv.argtypes = [C.c_int, C.c_int, C.c_int, C.c_double, C.c_double, _RHS, C.c_void_p, C.c_double,
+                                   _dp, _dp, _dp]
+            L.or_power_iteration_fd.argtypes = [C.c_int, C.c_int, C.c_int, C.c_double, C.c_double, _RHS,
+                                                C.c_void_p, C.c_double, _dp, _dp, C.c_int, _dp, _ip]
+            L.or_leja_phi_fd.argtypes = [C.c_int, C.c_int, C.c_int, C.c_double, C.c_double, _RHS, C.c_void_p,
+                                         C.c_double, _dp, C.c_int, _dp, C.c_double, C.c_double, C.c_double,
+                                         C.c_double, C.c_double, _dp, C.c_int, _dp, _ip]
+            L.or_ros_eu_fd.argtypes = [C.c_int, C.c_int, C.c_int, C.c_double, C.c_double, _RHS, C.c_void_p,
+                                       C.c_double, _dp, C.c_double, C.c_double, C.c_double, C.c_double, C.c_double,
+                                       _dp, C.c_int, _dp, _ip]
+            L.or_exprb32_fd.argtypes = [C.c_int, C.c_int, C.c_int, C.c_double, C.c_double, _RHS, C.c_void_p,
+                                        C.c_double, _dp, C.c_double, C.c_double, C.c_double, C.c_double,
+                                        C.c_double, _dp, C.c_int, _dp, _dp, _dp, _ip]
             _lib = L
     return _lib
 
@@ -269,3 +284,83 @@ def integrate_exprb32(kind, nx, ny, nu, a, u0, v0, t_final, h0, tol, leja_tol, x
     st = lib().or_integrate_exprb32(kind, nx, ny, nu, a, _p(u), _p(v0), t_final, h0, tol, leja_tol, _p(xi),
                                     len(xi), max_attempts, C.byref(steps), C.byref(rej), C.byref(its), _p(h), _p(t))
     return u, steps.value, rej.value, its.value, float(h[0]), float(t[0]), st
+
+
+# ---------------------------------------------------------------------------
+# The unfused form: Jacobian action by central finite differences of f
+# (Sec. 2.3), f the kind's own (rhs=None) or a Python function of one float64
+# array returning f(u) (Sec. 2's user right-hand side).
+# ---------------------------------------------------------------------------
+
+EPS0_FD = 2.0 ** -18  # default relative difference step, about the cube root of the unit roundoff
+
+
+def _rhs_cb(rhs, n):
+    if rhs is None:
+        return _RHS()
+
+    def cb(inp, out, _user):
+        x = np.ctypeslib.as_array(inp, shape=(n,))
+        y = np.ctypeslib.as_array(out, shape=(n,))
+        y[:] = rhs(x.copy())
+
+    return _RHS(cb)
+
+
+def fd_jv(kind, nx, ny, nu, a, u, v, eps0=EPS0_FD, rhs=None):
+    """J(u) v = [f(u + e v) - f(u - e v)] / (2 e), e = eps0 (1 + ||u||) / ||v||."""
+    v = _f64(v)
+    u = _f64(u) if u is not None else None
+    out = np.zeros_like(v)
+    cb = _rhs_cb(rhs, v.size)
+    st = lib().or_fd_jv(kind, nx, ny, nu, a, cb, None, eps0, _p(u), _p(v), _p(out))
+    if st != OK:
+        raise RuntimeError(f"or_fd_jv status {st}")
+    return out
+
+
+def power_iteration_fd(kind, nx, ny, nu, a, u, v0, max_iters=10, eps0=EPS0_FD, rhs=None):
+    v0 = _f64(v0)
+    u = _f64(u) if u is not None else None
+    rho = np.zeros(1)
+    it = C.c_int(0)
+    cb = _rhs_cb(rhs, v0.size)
+    st = lib().or_power_iteration_fd(kind, nx, ny, nu, a, cb, None, eps0, _p(u), _p(v0), max_iters, _p(rho),
+                                     C.byref(it))
+    return float(rho[0]), int(it.value), st
+
+
+def leja_phi_fd(kind, nx, ny, nu, a, u, l, w, c, gamma, h, rtol, atol, xi, eps0=EPS0_FD, rhs=None):
+    w = _f64(w)
+    xi = _f64(xi)
+    u = _f64(u) if u is not None else None
+    out = np.zeros_like(w)
+    it = C.c_int(0)
+    cb = _rhs_cb(rhs, w.size)
+    st = lib().or_leja_phi_fd(kind, nx, ny, nu, a, cb, None, eps0, _p(u), l, _p(w), c, gamma, h, rtol, atol,
+                              _p(xi), len(xi), _p(out), C.byref(it))
+    return out, int(it.value), st
+
+
+def ros_eu_fd(kind, nx, ny, nu, a, u, c, gamma, h, rtol, atol, xi, eps0=EPS0_FD, rhs=None):
+    u = _f64(u)
+    xi = _f64(xi)
+    out = np.zeros_like(u)
+    it = C.c_int(0)
+    cb = _rhs_cb(rhs, u.size)
+    st = lib().or_ros_eu_fd(kind, nx, ny, nu, a, cb, None, eps0, _p(u), c, gamma, h, rtol, atol, _p(xi), len(xi),
+                            _p(out), C.byref(it))
+    return out, int(it.value), st
+
+
+def exprb32_fd(kind, nx, ny, nu, a, u, c, gamma, h, rtol, atol, xi, eps0=EPS0_FD, rhs=None):
+    u = _f64(u)
+    xi = _f64(xi)
+    lo = np.zeros_like(u)
+    hi = np.zeros_like(u)
+    err = np.zeros(1)
+    it = C.c_int(0)
+    cb = _rhs_cb(rhs, u.size)
+    st = lib().or_exprb32_fd(kind, nx, ny, nu, a, cb, None, eps0, _p(u), c, gamma, h, rtol, atol, _p(xi), len(xi),
+                             _p(lo), _p(hi), _p(err), C.byref(it))
+    return lo, hi, float(err[0]), int(it.value), st

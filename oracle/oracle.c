@@ -23,7 +23,12 @@
  *  - Iteration cap: K - 1 iterations for a table of K points, then NOCONV.
  *  - Power iteration: w = Av, rho_k = ||w||/||v||, v <- w/||w||, stop at
  *    max_iters or when |rho_k - rho_{k-1}| <= 1e-2 rho_k.
- *  - The Jacobian action is the analytic linearisation of the stencil.
+ *  - The Jacobian action is the analytic linearisation of the stencil; the
+ *    "_fd" entry points instead take it by finite differences of f (Sec. 2.3),
+ *    read as the central quotient J(u)v = [f(u + e v) - f(u - e v)] / (2e)
+ *    with e = eps0 (1 + ||u||) / ||v|| (J(u)0 = 0; a NULL u is u = 0), and
+ *    f either the problem kind's own or a caller's function (Sec. 2: the
+ *    right-hand side takes an input and an output pointer).
  */
 #include <float.h>
 #include <math.h>
@@ -367,15 +372,53 @@ void or_burgers_up3_J(int nx, int ny, double nu, double a, const double* u, cons
 /* The operator the Leja basis multiplies by: A for diffusion-advection,
  * J(u) for Burgers.  S (may be NULL): a time-independent source added to
  * the right-hand side (Problem II of Sec. 4); it does not enter J. */
+typedef void (*or_rhs_fn)(const double* in, double* out, void* user);
+
 typedef struct {
   int kind, nx, ny;
   double nu, a;
   const double* u;
   const double* S;
+  or_rhs_fn f;   /* caller's right-hand side, or NULL for the kind's own */
+  void* user;    /* passed to f */
+  double eps0;   /* > 0: Jacobian action by central finite differences */
 } or_op;
 
+static void op_rhs(const or_op* op, const double* u, double* out);
+static double nrm(const double* x, long n);
+
+/* J(u) v by the central difference quotient of f (Sec. 2.3: the action of
+ * the Jacobian is taken numerically), e = eps0 (1 + ||u||) / ||v||. */
+static void op_apply_fd(const or_op* op, const double* v, double* out) {
+  long n = (long)op->nx * op->ny;
+  double vn = nrm(v, n);
+  if (vn == 0.0) {
+    for (long q = 0; q < n; ++q) out[q] = 0.0;
+    return;
+  }
+  double un = op->u ? nrm(op->u, n) : 0.0;
+  double e = op->eps0 * (1.0 + un) / vn;
+  double* x = (double*)malloc(sizeof(double) * (size_t)n);
+  double* fp = (double*)malloc(sizeof(double) * (size_t)n);
+  if (!x || !fp) {
+    free(x);
+    free(fp);
+    for (long q = 0; q < n; ++q) out[q] = NAN;
+    return;
+  }
+  for (long q = 0; q < n; ++q) x[q] = (op->u ? op->u[q] : 0.0) + e * v[q];
+  op_rhs(op, x, fp);
+  for (long q = 0; q < n; ++q) x[q] = (op->u ? op->u[q] : 0.0) - e * v[q];
+  op_rhs(op, x, out);
+  for (long q = 0; q < n; ++q) out[q] = (fp[q] - out[q]) / (2.0 * e);
+  free(x);
+  free(fp);
+}
+
 static void op_apply(const or_op* op, const double* v, double* out) {
-  if (op->kind == OR_BURGERS)
+  if (op->eps0 > 0.0)
+    op_apply_fd(op, v, out);
+  else if (op->kind == OR_BURGERS)
     or_burgers_J(op->nx, op->ny, op->nu, op->u, v, out);
   else if (op->kind == OR_ADVDIFF_UP3)
     or_apply_advdiff_up3(op->nx, op->ny, op->nu, op->a, v, out);
@@ -388,7 +431,9 @@ static void op_apply(const or_op* op, const double* v, double* out) {
 /* f(u): A u for diffusion-advection, the Burgers right-hand side otherwise,
  * plus the source S when there is one. */
 static void op_rhs(const or_op* op, const double* u, double* out) {
-  if (op->kind == OR_BURGERS)
+  if (op->f)
+    op->f(u, out, op->user);
+  else if (op->kind == OR_BURGERS)
     or_burgers_f(op->nx, op->ny, op->nu, u, out);
   else if (op->kind == OR_ADVDIFF_UP3)
     or_apply_advdiff_up3(op->nx, op->ny, op->nu, op->a, u, out);
@@ -413,11 +458,9 @@ static double nrm(const double* x, long n) {
 /* Power iteration for the dominant eigenvalue modulus (Sec. 2, Listing 7).  */
 /* ------------------------------------------------------------------------ */
 
-int or_power_iteration(int kind, int nx, int ny, double nu, double a, const double* u,
-                       const double* v0, int max_iters, double* rho_out, int* iters_out) {
-  if (nx <= 0 || ny <= 0 || max_iters <= 0) return OR_E_INVAL;
-  or_op op = {kind, nx, ny, nu, a, u};
-  long n = (long)nx * ny;
+static int power_core(const or_op* opp, const double* v0, int max_iters, double* rho_out, int* iters_out) {
+  const or_op op = *opp;
+  long n = (long)op.nx * op.ny;
   double* v = (double*)malloc(sizeof(double) * (size_t)n);
   double* w = (double*)malloc(sizeof(double) * (size_t)n);
   if (!v || !w) { free(v); free(w); return OR_E_NOMEM; }
@@ -438,6 +481,13 @@ int or_power_iteration(int kind, int nx, int ny, double nu, double a, const doub
   free(v);
   free(w);
   return isfinite(rho) ? OR_OK : OR_E_NONFINITE;
+}
+
+int or_power_iteration(int kind, int nx, int ny, double nu, double a, const double* u,
+                       const double* v0, int max_iters, double* rho_out, int* iters_out) {
+  if (nx <= 0 || ny <= 0 || max_iters <= 0) return OR_E_INVAL;
+  or_op op = {kind, nx, ny, nu, a, u};
+  return power_core(&op, v0, max_iters, rho_out, iters_out);
 }
 
 /* ------------------------------------------------------------------------ */
@@ -562,12 +612,10 @@ int or_leja_phi_vertical(int kind, int nx, int ny, double nu, double a, const do
 
 /* With a source (Problem II, Sec. 4): f(u) = A u + S, so the step is
  * u+ = u + phi_1(h A) h (A u + S). */
-int or_ros_eu_src(int kind, int nx, int ny, double nu, double a, const double* u, const double* S,
-                  double c, double gamma, double h, double rtol, double atol, const double* xi, int K,
-                  double* u_out, int* iters) {
-  if (nx <= 0 || ny <= 0) return OR_E_INVAL;
-  or_op op = {kind, nx, ny, nu, a, u, S};
-  long n = (long)nx * ny;
+static int ros_eu_core(const or_op* opp, const double* u, double c, double gamma, double h, double rtol,
+                       double atol, const double* xi, int K, double* u_out, int* iters) {
+  const or_op op = *opp;
+  long n = (long)op.nx * op.ny;
   double* f_u = (double*)malloc(sizeof(double) * (size_t)n);
   double* p = (double*)malloc(sizeof(double) * (size_t)n);
   if (!f_u || !p) { free(f_u); free(p); return OR_E_NOMEM; }
@@ -578,6 +626,14 @@ int or_ros_eu_src(int kind, int nx, int ny, double nu, double a, const double* u
   free(f_u);
   free(p);
   return st;
+}
+
+int or_ros_eu_src(int kind, int nx, int ny, double nu, double a, const double* u, const double* S,
+                  double c, double gamma, double h, double rtol, double atol, const double* xi, int K,
+                  double* u_out, int* iters) {
+  if (nx <= 0 || ny <= 0) return OR_E_INVAL;
+  or_op op = {kind, nx, ny, nu, a, u, S};
+  return ros_eu_core(&op, u, c, gamma, h, rtol, atol, xi, K, u_out, iters);
 }
 
 int or_ros_eu(int kind, int nx, int ny, double nu, double a, const double* u, double c,
@@ -594,12 +650,11 @@ int or_ros_eu(int kind, int nx, int ny, double nu, double a, const double* u, do
 /*   err = ||2 phi_3(h J(u)) R||                                             */
 /* ------------------------------------------------------------------------ */
 
-int or_exprb32_src(int kind, int nx, int ny, double nu, double a, const double* u, const double* S,
-                   double c, double gamma, double h, double rtol, double atol, const double* xi, int K,
-                   double* u_low, double* u_high, double* err, int* iters) {
-  if (nx <= 0 || ny <= 0) return OR_E_INVAL;
-  or_op op = {kind, nx, ny, nu, a, u, S};
-  long n = (long)nx * ny;
+static int exprb32_core(const or_op* opp, const double* u, double c, double gamma, double h, double rtol,
+                        double atol, const double* xi, int K, double* u_low, double* u_high, double* err,
+                        int* iters) {
+  const or_op op = *opp;
+  long n = (long)op.nx * op.ny;
   double* f_u = (double*)malloc(sizeof(double) * (size_t)n);
   double* p1 = (double*)malloc(sizeof(double) * (size_t)n);
   double* t1 = (double*)malloc(sizeof(double) * (size_t)n);
@@ -637,6 +692,14 @@ int or_exprb32_src(int kind, int nx, int ny, double nu, double a, const double* 
   *iters = it1 + it2;
   free(f_u); free(p1); free(t1); free(t2); free(nl_u); free(nl_a); free(p3);
   return st != OR_OK ? st : st2;
+}
+
+int or_exprb32_src(int kind, int nx, int ny, double nu, double a, const double* u, const double* S,
+                   double c, double gamma, double h, double rtol, double atol, const double* xi, int K,
+                   double* u_low, double* u_high, double* err, int* iters) {
+  if (nx <= 0 || ny <= 0) return OR_E_INVAL;
+  or_op op = {kind, nx, ny, nu, a, u, S};
+  return exprb32_core(&op, u, c, gamma, h, rtol, atol, xi, K, u_low, u_high, err, iters);
 }
 
 int or_exprb32(int kind, int nx, int ny, double nu, double a, const double* u, double c,
@@ -707,4 +770,63 @@ int or_integrate_exprb32(int kind, int nx, int ny, double nu, double a, double* 
   free(lo);
   free(hi);
   return status;
+}
+
+/* ------------------------------------------------------------------------ */
+/* The unfused form with a finite-difference Jacobian action (Sec. 2.3) and  */
+/* a caller's right-hand side (Sec. 2).  f: NULL for the kind's own f (nu,   */
+/* a, nx, ny as in the fused entry points), else f(in, out, user) over       */
+/* nx*ny values.  eps0 > 0: the relative difference step (see the header).   */
+/* ------------------------------------------------------------------------ */
+
+static int fd_op(int kind, int nx, int ny, double nu, double a, or_rhs_fn f, void* user, double eps0,
+                 const double* u, or_op* op) {
+  if (nx <= 0 || ny <= 0 || !(eps0 > 0.0)) return OR_E_INVAL;
+  or_op o = {kind, nx, ny, nu, a, u, NULL, f, user, eps0};
+  *op = o;
+  return OR_OK;
+}
+
+int or_fd_jv(int kind, int nx, int ny, double nu, double a, or_rhs_fn f, void* user, double eps0,
+             const double* u, const double* v, double* out) {
+  or_op op;
+  int st = fd_op(kind, nx, ny, nu, a, f, user, eps0, u, &op);
+  if (st != OR_OK) return st;
+  op_apply(&op, v, out);
+  return OR_OK;
+}
+
+int or_power_iteration_fd(int kind, int nx, int ny, double nu, double a, or_rhs_fn f, void* user, double eps0,
+                          const double* u, const double* v0, int max_iters, double* rho_out, int* iters_out) {
+  or_op op;
+  int st = fd_op(kind, nx, ny, nu, a, f, user, eps0, u, &op);
+  if (st != OR_OK || max_iters <= 0) return OR_E_INVAL;
+  return power_core(&op, v0, max_iters, rho_out, iters_out);
+}
+
+int or_leja_phi_fd(int kind, int nx, int ny, double nu, double a, or_rhs_fn f, void* user, double eps0,
+                   const double* u, int l, const double* w, double c, double gamma, double h, double rtol,
+                   double atol, const double* xi, int K, double* out, int* iters) {
+  or_op op;
+  int st = fd_op(kind, nx, ny, nu, a, f, user, eps0, u, &op);
+  if (st != OR_OK || l < 0 || gamma == 0.0) return OR_E_INVAL;
+  return leja_phi_core(&op, l, w, c, gamma, h, rtol, atol, xi, K, out, iters);
+}
+
+int or_ros_eu_fd(int kind, int nx, int ny, double nu, double a, or_rhs_fn f, void* user, double eps0,
+                 const double* u, double c, double gamma, double h, double rtol, double atol, const double* xi,
+                 int K, double* u_out, int* iters) {
+  or_op op;
+  int st = fd_op(kind, nx, ny, nu, a, f, user, eps0, u, &op);
+  if (st != OR_OK) return st;
+  return ros_eu_core(&op, u, c, gamma, h, rtol, atol, xi, K, u_out, iters);
+}
+
+int or_exprb32_fd(int kind, int nx, int ny, double nu, double a, or_rhs_fn f, void* user, double eps0,
+                  const double* u, double c, double gamma, double h, double rtol, double atol, const double* xi,
+                  int K, double* u_low, double* u_high, double* err, int* iters) {
+  or_op op;
+  int st = fd_op(kind, nx, ny, nu, a, f, user, eps0, u, &op);
+  if (st != OR_OK) return st;
+  return exprb32_core(&op, u, c, gamma, h, rtol, atol, xi, K, u_low, u_high, err, iters);
 }
