@@ -60,7 +60,8 @@ typedef enum {
   LX_E_CUDA = 3,      /* a CUDA runtime call failed (see lx_last_cuda_error) */
   LX_E_NOCONV = 4,    /* Leja series not converged within the point table */
   LX_E_NONFINITE = 5, /* a NaN or Inf appeared in a norm */
-  LX_E_TIMEOUT = 6    /* a bounded device-side wait gave up */
+  LX_E_TIMEOUT = 6,   /* a bounded device-side wait gave up */
+  LX_E_CALLBACK = 7   /* a caller's right-hand side function reported an error */
 } lx_status;
 
 enum { LX_ADVDIFF = 0, LX_BURGERS = 1, LX_ADVDIFF_UP3 = 2, LX_BURGERS_UP3 = 3 }; /* lx_problem.kind */
@@ -430,6 +431,85 @@ void mlp_destroy(lx_mlp* m);
  * stack. */
 lx_status phi_l_apply_noalloc(const lx_problem* prob, int l, const double* w_dev, double* out_dev, double c,
                               double gamma, double h, double rtol, double atol, void* cuda_stream, int* iters);
+
+/* ---------------------------------------------------------------------------
+ * Unfused form: a caller's right-hand side and a finite-difference Jacobian
+ * (Sec. 2: the user supplies f as a function of an input and an output
+ * pointer to contiguous data, with its parameters held by a functor;
+ * Sec. 2.3: the action of the Jacobian is taken by finite differences).
+ *
+ * The engine cannot fuse an arbitrary f into its stencil kernels, so every
+ * Jacobian product costs two calls of f plus two passes of the engine's
+ * own kernels (the perturbed states, then the Newton update with its
+ * stopping norms).  Reading of the difference quotient (the paper gives no
+ * formula): the central quotient
+ *     J(u) v = [f(u + e v) - f(u - e v)] / (2 e),  e = eps0 (1 + ||u||) / ||v||,
+ * second-order in e and exact up to rounding for f of degree <= 2; J(u) 0 = 0.
+ * FP64 throughout.  Everything else (Leja points, coefficients, stopping
+ * test, integrator stages in the order of Sec. 2.3 Listings 12-13) is as in
+ * the fused entry points.
+ * ------------------------------------------------------------------------- */
+
+/* Right-hand side: out_dev = f(in_dev) for n doubles (device pointers, never
+ * aliasing), enqueued on cuda_stream (the context's stream; the engine's
+ * kernels that follow run on the same stream, so the function may return
+ * before its work completes).  user: the pointer given at setup (the
+ * functor's parameters).  Return 0 on success; any other value makes the
+ * calling entry point stop and return LX_E_CALLBACK. */
+typedef int (*lx_rhs_fn)(const double* in_dev, double* out_dev, void* user, void* cuda_stream);
+
+/* The engine's own right-hand side of a problem, in lx_rhs_fn form: user is
+ * a const lx_problem* (kinds LX_ADVDIFF .. LX_BURGERS_UP3; the precision
+ * field is ignored, the arithmetic is FP64).  f is A u for the
+ * diffusion-advection kinds and the Burgers right-hand side otherwise.
+ * Returns 0, or 1 for an invalid problem or a failed launch. */
+int lx_rhs_builtin(const double* in_dev, double* out_dev, void* user, void* cuda_stream);
+
+typedef struct lx_rhs_ctx lx_rhs_ctx;
+
+/* Context of the unfused form (the paper's struct Leja with its RHS
+ * functor): the Leja point table, the basis and stage vectors (about 11 n
+ * doubles for LX_EXPRB32, 8 n for LX_ROS_EU) and the reduction scratch.
+ *   n           number of unknowns, 1 <= n <= 2^31
+ *   f, user     the right-hand side (kept; called from the calling thread)
+ *   eps0        relative difference step, > 0; 0 selects 2^-18 (about the
+ *               cube root of the unit roundoff, which balances the O(e^2)
+ *               truncation against the rounding of f amplified by 1/e)
+ *   integrator, max_leja, cuda_stream, out: as in leja_setup
+ * Errors: LX_E_INVAL, LX_E_NOMEM, LX_E_CUDA. */
+lx_status leja_setup_rhs(long long n, lx_rhs_fn f, void* user, double eps0, int integrator, int max_leja,
+                         void* cuda_stream, lx_rhs_ctx** out);
+
+void leja_destroy_rhs(lx_rhs_ctx* ctx);
+
+/* power_bound with J(u) by differences (u_dev NULL: u = 0, i.e. the
+ * operator of a linear f).  Arguments and stopping rule as power_bound. */
+lx_status power_bound_rhs(lx_rhs_ctx* ctx, const double* u_dev, const double* v0_dev, int max_iters,
+                          double* rho, int* iters);
+
+/* phi_l(h J(u)) w with J(u) by differences (u_dev NULL: u = 0).  Arguments,
+ * stopping test and iteration count as phi_l_apply.  The loop is driven
+ * from the host (f cannot run inside a device-ended graph loop); the host
+ * reads the device's stop flag one iteration behind, so at most one
+ * further pair of f calls runs after the stop, on unchanged buffers. */
+lx_status phi_l_apply_rhs(lx_rhs_ctx* ctx, int l, const double* u_dev, const double* w_dev, double* out_dev,
+                          double c, double gamma, double h, double rtol, double atol, int* iters);
+
+/* One step of the context's integrator, as expint_step, with f from the
+ * callback and J(u) by differences; EXPRB32 evaluates
+ * R = h (F(a) - F(u)), F(k) = f(k) - J(u) k, as written (no simplification
+ * for a particular f). */
+lx_status expint_step_rhs(lx_rhs_ctx* ctx, const double* u_dev, double* u_low_dev, double* u_high_dev, double c,
+                          double gamma, double h, double rtol, double atol, double* err, int* iters);
+
+/* Counters of the context: Leja iterations, right-hand-side calls and
+ * engine kernel launches since the last reset. */
+typedef struct {
+  long long leja_iterations;
+  long long rhs_calls;
+  long long kernels;
+} lx_rhs_stats;
+lx_status lx_rhs_ctx_stats(lx_rhs_ctx* ctx, lx_rhs_stats* out, int reset);
 
 #ifdef __cplusplus
 }

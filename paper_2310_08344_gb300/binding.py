@@ -9,9 +9,9 @@ import numpy as np
 
 from . import _build
 
-OK, E_INVAL, E_NOMEM, E_CUDA, E_NOCONV, E_NONFINITE, E_TIMEOUT = range(7)
+OK, E_INVAL, E_NOMEM, E_CUDA, E_NOCONV, E_NONFINITE, E_TIMEOUT, E_CALLBACK = range(8)
 STATUS = {0: "LX_OK", 1: "LX_E_INVAL", 2: "LX_E_NOMEM", 3: "LX_E_CUDA", 4: "LX_E_NOCONV", 5: "LX_E_NONFINITE",
-          6: "LX_E_TIMEOUT"}
+          6: "LX_E_TIMEOUT", 7: "LX_E_CALLBACK"}
 ADVDIFF, BURGERS = 0, 1
 ADVDIFF_UP3, BURGERS_UP3 = 2, 3  # the paper's discretisation: periodic [-1,1)^2, third-order upwind gradient
 FP64, MIXED, DF64 = 0, 1, 2
@@ -35,6 +35,14 @@ class LxStats(C.Structure):
 class LxIntegrateInfo(C.Structure):
     _fields_ = [("t", C.c_double), ("h", C.c_double), ("steps", C.c_int), ("rejected", C.c_int),
                 ("leja_iters", C.c_longlong), ("last_err", C.c_double), ("power_iters", C.c_int)]
+
+
+class LxRhsStats(C.Structure):
+    _fields_ = [("leja_iterations", C.c_longlong), ("rhs_calls", C.c_longlong), ("kernels", C.c_longlong)]
+
+
+# lx_rhs_fn: int f(const double* in, double* out, void* user, void* stream)
+RHS_FN = C.CFUNCTYPE(C.c_int, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p)
 
 
 class LexgbError(RuntimeError):
@@ -109,6 +117,17 @@ def lib():
             L.lx_ctx_iters_per_launch.restype = C.c_int
             L.phi_l_apply_noalloc.argtypes = [C.POINTER(LxProblem), C.c_int, _vp, _vp, C.c_double, C.c_double,
                                               C.c_double, C.c_double, C.c_double, _vp, _ip]
+            L.lx_rhs_builtin.argtypes = [_vp, _vp, _vp, _vp]
+            L.lx_rhs_builtin.restype = C.c_int
+            L.leja_setup_rhs.argtypes = [C.c_longlong, _vp, _vp, C.c_double, C.c_int, C.c_int, _vp, C.POINTER(_vp)]
+            L.leja_destroy_rhs.argtypes = [_vp]
+            L.leja_destroy_rhs.restype = None
+            L.power_bound_rhs.argtypes = [_vp, _vp, _vp, C.c_int, _dp, _ip]
+            L.phi_l_apply_rhs.argtypes = [_vp, C.c_int, _vp, _vp, _vp, C.c_double, C.c_double, C.c_double,
+                                          C.c_double, C.c_double, _ip]
+            L.expint_step_rhs.argtypes = [_vp, _vp, _vp, _vp, C.c_double, C.c_double, C.c_double, C.c_double,
+                                          C.c_double, _dp, _ip]
+            L.lx_rhs_ctx_stats.argtypes = [_vp, C.POINTER(LxRhsStats), C.c_int]
             _lib = L
     return _lib
 
@@ -479,3 +498,133 @@ def lx_integrate_learned(ctx: Context, u, v0, t_final, tol, leja_tol, model: "Ml
                                     model.handle, dt_ref, C.byref(info))
     return st, {"t": info.t, "h": info.h, "steps": info.steps, "rejected": info.rejected,
                 "leja_iters": info.leja_iters, "last_err": info.last_err}
+
+
+# ------------------------------------------------------------------ unfused form (caller's right-hand side)
+class _DevRange:
+    """n doubles at a device address, described by __cuda_array_interface__
+    so that torch can view them without a copy."""
+
+    def __init__(self, ptr, n):
+        self.__cuda_array_interface__ = {"shape": (n,), "typestr": "<f8", "data": (ptr, False), "version": 2,
+                                         "strides": None}
+
+
+def rhs_function(f, n):
+    """Wrap a Python right-hand side f(x, out) -- x, out: torch CUDA float64
+    views of n values (no copy); f writes f(x) into out with torch operations
+    -- as an lx_rhs_fn.  It runs on the stream the engine passes.  An
+    exception inside f is printed and reported to the engine as an error."""
+    import sys
+    import traceback
+
+    import torch
+
+    views = {}
+
+    def view(ptr):
+        t = views.get(ptr)
+        if t is None:
+            t = torch.as_tensor(_DevRange(ptr, n), device="cuda")
+            views[ptr] = t
+        return t
+
+    def cb(inp, out, _user, stream):
+        try:
+            s = torch.cuda.ExternalStream(stream) if stream else torch.cuda.default_stream()
+            with torch.cuda.stream(s):
+                f(view(inp), view(out))
+            return 0
+        except Exception:  # reported to the engine as LX_E_CALLBACK
+            traceback.print_exc(file=sys.stderr)
+            return 1
+
+    return RHS_FN(cb)
+
+
+class RhsContext:
+    """Owns an lx_rhs_ctx* and keeps its right-hand side alive."""
+
+    def __init__(self, handle, n, integrator, keep):
+        self.handle = handle
+        self.n = n
+        self.integrator = integrator
+        self._keep = keep
+
+    def close(self):
+        if self.handle:
+            lib().leja_destroy_rhs(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def leja_setup_rhs(n, f=None, problem=None, eps0=0.0, integrator=ROS_EU, max_leja=1000, stream=None) -> RhsContext:
+    """f: a Python f(x, out) (see rhs_function), or None with problem =
+    (nx, ny, nu, a, kind) for the engine's own right-hand side
+    (lx_rhs_builtin)."""
+    if f is None:
+        if problem is None:
+            raise ValueError("need f or problem")
+        nx, ny, nu, a, kind = problem
+        prob = LxProblem(nx, ny, nu, a, kind, FP64)
+        keep = (prob,)
+        fn = C.cast(lib().lx_rhs_builtin, _vp).value
+        user = C.addressof(prob)
+    else:
+        cb = rhs_function(f, n)
+        keep = (cb,)
+        fn = C.cast(cb, _vp).value
+        user = None
+    h = _vp()
+    st = lib().leja_setup_rhs(n, fn, user, eps0, integrator, max_leja, _stream_handle(stream), C.byref(h))
+    if st != OK:
+        raise LexgbError(st, "leja_setup_rhs")
+    return RhsContext(h.value, n, integrator, keep)
+
+
+def leja_destroy_rhs(ctx: RhsContext):
+    ctx.close()
+
+
+def lx_rhs_builtin(problem, x, out, stream=None) -> int:
+    """The engine's own f(x) into out for problem = (nx, ny, nu, a, kind)."""
+    nx, ny, nu, a, kind = problem
+    prob = LxProblem(nx, ny, nu, a, kind, FP64)
+    return lib().lx_rhs_builtin(_dev(x), _dev(out), C.addressof(prob), _stream_handle(stream))
+
+
+def power_bound_rhs(ctx: RhsContext, u, v0, max_iters=10):
+    """Returns (status, rho, passes)."""
+    rho = C.c_double(0.0)
+    it = C.c_int(0)
+    st = lib().power_bound_rhs(ctx.handle, _dev(u), _dev(v0), max_iters, C.byref(rho), C.byref(it))
+    return st, rho.value, it.value
+
+
+def phi_l_apply_rhs(ctx: RhsContext, l, u, w, out, c, gamma, h, rtol, atol):
+    """Returns (status, iters)."""
+    it = C.c_int(0)
+    st = lib().phi_l_apply_rhs(ctx.handle, l, _dev(u), _dev(w), _dev(out), c, gamma, h, rtol, atol, C.byref(it))
+    return st, it.value
+
+
+def expint_step_rhs(ctx: RhsContext, u, u_low, u_high, c, gamma, h, rtol, atol):
+    """Returns (status, err, iters)."""
+    err = C.c_double(0.0)
+    it = C.c_int(0)
+    st = lib().expint_step_rhs(ctx.handle, _dev(u), _dev(u_low), _dev(u_high), c, gamma, h, rtol, atol,
+                               C.byref(err), C.byref(it))
+    return st, err.value, it.value
+
+
+def lx_rhs_ctx_stats(ctx: RhsContext, reset=False) -> dict:
+    s = LxRhsStats()
+    st = lib().lx_rhs_ctx_stats(ctx.handle, C.byref(s), 1 if reset else 0)
+    if st != OK:
+        raise LexgbError(st, "lx_rhs_ctx_stats")
+    return {"leja_iterations": s.leja_iterations, "rhs_calls": s.rhs_calls, "kernels": s.kernels}
