@@ -61,7 +61,7 @@ def parse():
                    help="diffusion-advection with a time-independent source S (u' = A u + S)")
     p.add_argument("--workload", default="advdiff4096",
                    choices=["advdiff4096", "batch256", "burgers2048", "vertical4096", "paper1", "paper2",
-                            "paper3"])
+                            "paper3", "rhs4096"])
     p.add_argument("--cfl", type=float, default=100.0, help="paper workloads: step size in units of dt_CFL")
     p.add_argument("--tf", type=float, default=None,
                    help="paper workloads: integrate to this final time and report the end-to-end time")
@@ -367,6 +367,8 @@ def run_paper(args, rank, world, local):
     kind = lx.BURGERS_UP3 if which == "paper3" else lx.ADVDIFF_UP3
     integ = lx.EXPRB32 if which == "paper3" else lx.ROS_EU
     ctx = lx.leja_setup(n, n, nu, a, kind, prec, integ, 1000, stream)
+    if args.kernel and lx.lx_ctx_select_kernel(ctx, args.kernel, args.strip_h) != 0:
+        raise SystemExit(f"unknown kernel {args.kernel}")
     u0 = synth.problem3_ic(n, n) if which == "paper3" else synth.problem1_ic(n, n)
     ua = torch.from_numpy(u0).cuda()
     ub = torch.empty_like(ua)
@@ -460,6 +462,8 @@ def run_paper_tf(args, rank, world, local):
     kind = lx.BURGERS_UP3 if which == "paper3" else lx.ADVDIFF_UP3
     integ = lx.EXPRB32 if which == "paper3" else lx.ROS_EU
     ctx = lx.leja_setup(n, n, nu, a, kind, prec, integ, 1000, stream)
+    if args.kernel and lx.lx_ctx_select_kernel(ctx, args.kernel, args.strip_h) != 0:
+        raise SystemExit(f"unknown kernel {args.kernel}")
     u0 = synth.problem3_ic(n, n) if which == "paper3" else synth.problem1_ic(n, n)
     amax = a * (float(np.abs(u0).max()) if which == "paper3" else 1.0)
     h = args.cfl * synth.cfl_step_pm1(n, n, nu, amax)
@@ -589,6 +593,99 @@ def run_vertical(args, rank, world, local):
     return 0
 
 
+def run_rhs(args, rank, world, local):
+    """The unfused form (a caller's right-hand side, the Jacobian action by
+    central differences) on the 4096^2 diffusion-advection Rosenbrock-Euler
+    step (nu = 1e-2, a = 1, h = 50 dt_CFL, tol 1e-10): f from the engine's
+    own FP64 right-hand side (lx_rhs_builtin) and from a Python/torch
+    function, against the fused FP64 and float-float paths on the same step.
+    Algorithmic bytes per point per Leja iteration of the unfused form:
+    perturbation 32 (u, y in; x+, x- out), two calls of f 2 x 16, update 48
+    (f(x+), f(x-), y, p in; y', p out) = 112."""
+    import torch
+
+    import paper_2310_08344_gb300 as lx
+
+    torch.cuda.set_device(local)
+    stream = torch.cuda.current_stream()
+    n = args.n
+    N = n * n
+    u = torch.from_numpy(synth.gaussians_ic(n, n, seed=1)).cuda()
+    h = CFL_MULT * synth.cfl_step(n, n, NU, ADV)
+    c, g = lx.spectral_interval(symbol_radius(n, NU, ADV))
+    prob = (n, n, NU, ADV, lx.ADVDIFF)
+
+    def f_torch(x, out):
+        X = x.view(n, n)
+        L = (torch.roll(X, 1, 1) + torch.roll(X, -1, 1) - 2 * X) * (n * n) + \
+            (torch.roll(X, 1, 0) + torch.roll(X, -1, 0) - 2 * X) * (n * n)
+        G = (torch.roll(X, -1, 1) - torch.roll(X, 1, 1) + torch.roll(X, -1, 0) - torch.roll(X, 1, 0)) * (n / 2)
+        out.copy_((NU * L + ADV * G).view(-1))
+
+    out = torch.empty(N, dtype=torch.float64, device="cuda")
+    forms = {}
+    results = {}
+    for name in ("unfused_builtin", "unfused_torch", "fused_fp64", "fused_df64"):
+        if name.startswith("unfused"):
+            ctx = lx.leja_setup_rhs(N, f=f_torch if name == "unfused_torch" else None,
+                                    problem=None if name == "unfused_torch" else prob, stream=stream)
+
+            def step():
+                st, err, it = lx.expint_step_rhs(ctx, u, None, out, c, g, h, TOL, TOL)
+                if st != 0:
+                    raise SystemExit(f"expint_step_rhs failed: {st}")
+                return it
+        else:
+            ctx = lx.leja_setup(n, n, NU, ADV, lx.ADVDIFF, lx.FP64 if name == "fused_fp64" else lx.DF64,
+                                lx.ROS_EU, 1000, stream)
+            if name == "fused_df64" and not args.no_autotune:
+                lx.lx_ctx_autotune(ctx, iters=10)
+
+            def step():
+                st, err, it = lx.expint_step(ctx, u, None, out, c, g, h, TOL, TOL)
+                if st != 0:
+                    raise SystemExit(f"expint_step failed: {st}")
+                return it
+        for _ in range(max(args.warmup, 1)):
+            step()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        its = 0
+        for _ in range(args.steps):
+            its += step()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / args.steps
+        rec = {"ms_per_step": ms, "leja_iters_per_step": its / args.steps,
+               "gdof_iter_per_s": N * its / args.steps / (ms * 1e-3) / 1e9}
+        if name.startswith("unfused"):
+            rec["rhs_calls"] = lx.lx_rhs_ctx_stats(ctx)["rhs_calls"]
+            rec["algorithmic_gbs"] = 112.0 * N * its / args.steps / (ms * 1e-3) / 1e9
+        results[name] = out.clone()
+        forms[name] = rec
+        ctx.close()
+    for name in ("unfused_builtin", "unfused_torch", "fused_df64"):
+        forms[name]["rel_l2_vs_fused_fp64"] = float(torch.linalg.norm(results[name] - results["fused_fp64"]) /
+                                                    torch.linalg.norm(results["fused_fp64"]))
+    best = forms["unfused_builtin"]
+    peaks, peak_src = measured_peaks()
+    hbm = peaks["hbm_gbs"]
+    line = {"metric": "GDOF*Leja-iter/s", "value": best["gdof_iter_per_s"], "unit": "GDOF*iter/s",
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": best["ms_per_step"],
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": f"rhs-unfused-{n}x{n}-rosenbrock-euler", "nu": NU, "a": ADV,
+                       "h_over_dt_cfl": CFL_MULT, "tol": TOL, "eps0": 2.0 ** -18,
+                       "l2": "inputs larger than L2 (128 MiB per vector)"},
+            "roofline": {"bound": "hbm", "achieved": best["algorithmic_gbs"], "peak": hbm, "unit": "GB/s",
+                         "frac": best["algorithmic_gbs"] / hbm, "traffic": None, "peak_source": peak_src,
+                         "note": "whole unfused Leja loop, 112 algorithmic bytes per point-iteration"},
+            "forms": forms}
+    if rank == 0:
+        print(json.dumps(line))
+    return 0
+
+
 def run_burgers(args, rank, world, local):
     """Viscous Burgers 2048^2, nu = 5e-3, EXPRB32 steps of h = 50 dt_CFL with
     a power-iteration bound before every step; FP64 and mixed forms, and the
@@ -672,6 +769,8 @@ def main():
         return run_burgers(args, rank, world, local)
     if args.workload == "vertical4096":
         return run_vertical(args, rank, world, local)
+    if args.workload == "rhs4096":
+        return run_rhs(args, rank, world, local)
     if args.workload in ("paper1", "paper2", "paper3"):
         return run_paper(args, rank, world, local)
     import torch

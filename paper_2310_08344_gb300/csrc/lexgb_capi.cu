@@ -76,6 +76,7 @@ struct Cand {
   int vec;      // points per lane (warp row = 32 * vec points)
   const char* name;
   int ipl = 1;  // Leja iterations per launch
+  int strip = -1;  // default strip height when not autotuned (-1: by kind of kernel)
 };
 
 struct LoopGraph {
@@ -134,6 +135,7 @@ struct lx_ctx {
   float2* d_pdfv[kMaxVertical] = {};
   LoopGraph vloop[kNumVariants][kMaxVertical];
   int aux_grid = 0;
+  int pow_pipe_grid = 0;  // grid of the pipelined upwind Burgers power pass (0: not yet sized)
 
   cudaEvent_t ev[8] = {};
   int ev_used = 0;
@@ -167,6 +169,13 @@ std::vector<Cand> candidates(int kind, int precision, int cls) {
     const char* name = nullptr;
     if (precision == LX_DF64) {
       if (b && wide) {
+        // product form first (z = q y formed once per point, constant
+        // weights; 592 us per iteration at 8192^2 with balanced row ranges,
+        // against 782 us for the point-weight form), then the point-weight form
+        v.push_back(Cand{reinterpret_cast<const void*>(&leja_iter_df_pipe_burgers_up3z_kernel<3, 5>), kPipeThreads,
+                         up3z_smem_bytes<5>(), 4, "leja_iter_df_pipe_burgers_up3z_b3", 1, 0});
+        v.push_back(Cand{reinterpret_cast<const void*>(&leja_iter_df_pipe_burgers_up3z_kernel<2, 6>), kPipeThreads,
+                         up3z_smem_bytes<6>(), 4, "leja_iter_df_pipe_burgers_up3z_b2", 1, 0});
         v.push_back(Cand{reinterpret_cast<const void*>(&leja_iter_df_pipe_burgers_up3_kernel<2>), kPipeThreads,
                          kUpSmemBytesB, 4, "leja_iter_df_pipe_burgers_up3_b2"});
         v.push_back(Cand{reinterpret_cast<const void*>(&leja_iter_df_pipe_burgers_up3_kernel<1>), kPipeThreads,
@@ -174,10 +183,12 @@ std::vector<Cand> candidates(int kind, int precision, int cls) {
       }
       if (!b && wide) {
         // pipelined (nx % 128 == 0, aligned vectors), then the point-wise form
+        // (balanced row ranges by default: 389 us per iteration at 8192^2
+        // against 411 us with 8-row strips)
         v.push_back(Cand{reinterpret_cast<const void*>(&leja_iter_df_pipe_up3_kernel<3>), kPipeThreads,
-                         kUpSmemBytes, 4, "leja_iter_df_pipe_up3_b3"});
+                         kUpSmemBytes, 4, "leja_iter_df_pipe_up3_b3", 1, 0});
         v.push_back(Cand{reinterpret_cast<const void*>(&leja_iter_df_pipe_up3_kernel<2>), kPipeThreads,
-                         kUpSmemBytes, 4, "leja_iter_df_pipe_up3_b2"});
+                         kUpSmemBytes, 4, "leja_iter_df_pipe_up3_b2", 1, 0});
       }
       if (!b) {
         f = reinterpret_cast<const void*>(&leja_iter_df_up3_kernel);
@@ -368,10 +379,12 @@ lx_status ensure_graph(lx_ctx* c, int variant) {
     return LX_E_INVAL;
   }
   const Cand k = cands[0];
+  // a candidate's own default strip height if it has one; otherwise
   // pipelined kernels (dynamic shared memory) default to 8-row strips (one
   // strip per warp then gives enough resident warps on mid-size grids), the
   // two-step kernel to balanced row ranges (its halo rows cost arithmetic)
-  return build_loop_graph(c, variant, k, k.ipl == 2 ? 0 : (k.smem > 0 ? 8 : c->strip_h));
+  const int strip = k.strip >= 0 ? k.strip : (k.ipl == 2 ? 0 : (k.smem > 0 ? 8 : c->strip_h));
+  return build_loop_graph(c, variant, k, strip);
 }
 
 lx_status ensure_coeffs(lx_ctx* c, int slot, int l, double h, double cc, double gamma) {
@@ -595,6 +608,7 @@ const char* lx_status_str(lx_status s) {
     case LX_E_NOCONV: return "Leja series did not converge";
     case LX_E_NONFINITE: return "non-finite value";
     case LX_E_TIMEOUT: return "device wait timed out";
+    case LX_E_CALLBACK: return "right-hand side function failed";
   }
   return "unknown status";
 }
@@ -720,6 +734,20 @@ lx_status leja_setup(const lx_problem* prob, int integrator, int max_leja, void*
   return LX_OK;
 }
 
+// Grid of the pipelined upwind Burgers power pass: one balanced row range
+// (at least four rows) per warp, at most the resident blocks of one wave.
+lx_status size_pow_pipe_grid(lx_ctx* c) {
+  const void* f = reinterpret_cast<const void*>(&power_pass_df_pipe_burgers_up3z_kernel<3, 5>);
+  LX_CUDA(cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, up3z_smem_bytes<5>()));
+  int per_sm = 0;
+  LX_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, f, kPipeThreads, up3z_smem_bytes<5>()));
+  per_sm = std::max(per_sm, 1);
+  const long long units = ((long long)(c->prob.nx / kPipeRow) * c->prob.ny + 3) / 4;
+  const int want = (int)std::min<long long>((units + kPipeWarps - 1) / kPipeWarps, 1 << 30);
+  c->pow_pipe_grid = std::max(1, std::min({want, per_sm * c->sm_count, c->partials_cap}));
+  return LX_OK;
+}
+
 lx_status power_bound(lx_ctx* c, const double* u, const double* v0, int max_iters, double* rho, int* iters) {
   if (!c || !v0 || !rho || max_iters < 1 || max_iters > kMaxPower) return LX_E_INVAL;
   if (is_burgers(c->prob.kind) && !u) return LX_E_INVAL;
@@ -793,12 +821,22 @@ lx_status power_bound(lx_ctx* c, const double* u, const double* v0, int max_iter
     }
     if (dfu) {
       float2* wf = reinterpret_cast<float2*>(outv);
-      if (P.kind == LX_ADVDIFF_UP3)
+      if (P.kind == LX_ADVDIFF_UP3) {
         power_pass_df_up3_kernel<false><<<G, kThreadsPerBlock, 0, c->stream>>>(
             c->up3, in, k == 1 ? 1 : 0, wf, nullptr, c->d_partials, c->d_ticket, c->d_state);
-      else
+      } else if (aligned16(in)) {
+        // pipelined product form (the float-float Burgers form has nx % 128 == 0)
+        if (c->pow_pipe_grid == 0) {
+          lx_status gs = size_pow_pipe_grid(c);
+          if (gs != LX_OK) return gs;
+        }
+        power_pass_df_pipe_burgers_up3z_kernel<3, 5><<<c->pow_pipe_grid, kPipeThreads, up3z_smem_bytes<5>(),
+                                                         c->stream>>>(c->up3, in, k == 1 ? 1 : 0, wf, c->d_bq,
+                                                                      c->d_partials, c->d_ticket, c->d_state);
+      } else {
         power_pass_df_up3_kernel<true><<<G, kThreadsPerBlock, 0, c->stream>>>(
             c->up3, in, k == 1 ? 1 : 0, wf, c->d_bq, c->d_partials, c->d_ticket, c->d_state);
+      }
       ++c->stats.kernels;
       LX_CUDA(cudaGetLastError());
       continue;

@@ -84,13 +84,15 @@ def test_phi_burgers_up3(lx, xi_oracle, prec, nx, ny):
 
 @pytest.mark.parametrize("kind", [2, 3])
 @pytest.mark.parametrize("prec", ["FP64", "DF64"])
-def test_power_bound_up3(lx, kind, prec):
-    nx, ny = 128, 64
-    u = synth.problem3_ic(nx, ny, seed=6) if kind == 3 else None
+@pytest.mark.parametrize("nx,ny,a", [(128, 64, A), (256, 100, A), (256, 100, -4.0)])
+def test_power_bound_up3(lx, kind, prec, nx, ny, a):
+    # (the float-float Burgers passes run the pipelined product-form kernel:
+    # two column strips and a ragged row range on the larger grid)
+    u = synth.problem3_ic(nx, ny, seed=6) * np.sign(a) if kind == 3 else None
     v0 = synth.power_start(nx * ny, 5)
-    ctx = lx.leja_setup(nx, ny, NU, A, kind, getattr(lx, prec))
+    ctx = lx.leja_setup(nx, ny, NU, a, kind, getattr(lx, prec))
     st, rho, it = lx.power_bound(ctx, dev(u) if u is not None else None, dev(v0), 10)
-    rho_o, it_o, st_o = oracle.power_iteration(kind, nx, ny, NU, A, u, v0, 10)
+    rho_o, it_o, st_o = oracle.power_iteration(kind, nx, ny, NU, a, u, v0, 10)
     assert st == 0 and st_o == 0 and it == it_o
     assert abs(rho - rho_o) <= 1e-12 * rho_o
 
@@ -164,7 +166,12 @@ def test_df64_up3_candidates(lx, xi_oracle, name, strip_h, a):
 
 
 @pytest.mark.parametrize("name,strip_h", [("leja_iter_df_pipe_burgers_up3_b2", 0), ("leja_iter_df_pipe_burgers_up3_b2", 8),
-                                          ("leja_iter_df_pipe_burgers_up3_b1", 32)])
+                                          ("leja_iter_df_pipe_burgers_up3_b1", 32),
+                                          ("leja_iter_df_pipe_burgers_up3z_b3", 0),
+                                          ("leja_iter_df_pipe_burgers_up3z_b3", 8),
+                                          ("leja_iter_df_pipe_burgers_up3z_b3", 128),
+                                          ("leja_iter_df_pipe_burgers_up3z_b2", 0),
+                                          ("leja_iter_df_pipe_burgers_up3z_b2", 32)])
 @pytest.mark.parametrize("a", [A, -4.0])
 def test_df64_burgers_up3_candidates(lx, xi_oracle, name, strip_h, a):
     nx, ny = 256, 100
