@@ -28,9 +28,8 @@
  *                      (Problem III with nu = 1, a = 10), J(u) v = nu Lap v +
  *                      a ((u v)_x + (u v)_y); the upwind side follows the sign
  *                      of a (the paper's state stays positive).
- *    LX_DF64 with LX_BURGERS_UP3 needs nx % 128 == 0 (as LX_BURGERS); batches,
- *    vertical interpolation and the allocation-free entry point take the
- *    central operators only.
+ *    LX_DF64 with LX_BURGERS_UP3 needs nx % 128 == 0 (as LX_BURGERS); batches
+ *    and the allocation-free entry point take the central operators only.
  *  - Norms: ||x|| = ||x||_2 / sqrt(N) (Sec. 2.2).
  *  - Device pointers ("_dev") are CUDA global-memory pointers of the current
  *    device; host pointers ("_host") are ordinary CPU memory.  The caller
@@ -182,9 +181,10 @@ lx_status phi_l_apply(lx_ctx* ctx, int l, const double* u_dev, const double* w_d
  *   out:   host array of nc distinct device pointers (nx*ny doubles each, not
  *          aliasing u or w);
  *   u, w, cc, gamma, h, rtol, atol: as in phi_l_apply.
- * LX_DF64 contexts need nx % 128 == 0 and a 16-byte aligned w (else
- * LX_E_INVAL).  Buffers for the nc polynomials are allocated on first use
- * and kept until leja_destroy. */
+ * LX_DF64 contexts of the central operators need nx % 128 == 0 and a 16-byte
+ * aligned w (else LX_E_INVAL); the upwind kinds run one thread per point
+ * and take any layout.  Buffers for the nc polynomials are allocated on
+ * first use and kept until leja_destroy. */
 lx_status phi_l_apply_vertical(lx_ctx* ctx, int l, int nc, const double* alpha, const double* u,
                                const double* w, double* const* out, double cc, double gamma, double h,
                                double rtol, double atol, int* iters);

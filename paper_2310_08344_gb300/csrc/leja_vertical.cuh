@@ -14,7 +14,7 @@
 // write, against NP separate loops that each move y and one polynomial.
 #pragma once
 
-#include "leja_df64_2step.cuh"
+#include "leja_upwind.cuh"
 #include "lexgb_vertical.h"
 
 namespace lexgb {
@@ -355,6 +355,202 @@ static __global__ void __launch_bounds__(kThreadsPerBlock)
     double tp[NP];
 #pragma unroll
     for (int j = 0; j < NP; ++j) tp[j] = sums[1 + j];
+    leja_finalize_vertical<NP>(A, st, m, dm1d, sums[0], tp, pow2(sig + dlt), pow2(kexp), cond);
+    const double rms = sqrt(sums[0] / double(A.n));
+    int e = 0;
+    if (rms > 0.0 && isfinite(rms)) e = ilogb(rms);
+    st->sig = sig + dlt;
+    st->dlt = max(-100, min(100, e));
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Vertical loops on the paper's upwind operators (periodic [-1,1)^2, Sec. 4),
+// one thread per point with the seven stencil points through the caches, as
+// the one-polynomial point-wise kernels: FP64 / mixed basis (T), and
+// float-float with both operators (Burgers: the seven point weights from
+// q = u |a| / (6 dx gamma)).
+// ---------------------------------------------------------------------------
+template <bool BURGERS, typename T, int NP>
+static __global__ void __launch_bounds__(kThreadsPerBlock)
+    leja_iter_up3_vertical_kernel(const LoopArgs* __restrict__ Ap, const VertArgs* __restrict__ Vp,
+                                  LoopState* __restrict__ st, double* __restrict__ partials,
+                                  unsigned int* __restrict__ ticket, cudaGraphConditionalHandle cond) {
+  const LoopArgs& A = *Ap;
+  const VertArgs& V = *Vp;
+  const int m = __ldcg(&st->m);
+  count_launch(st);
+  if (__ldcg(&st->done)) return;
+  const Up3Op o = A.up;
+  const double xim = __ldg(A.xi + m);
+  double d0[NP], dm1[NP], sp[NP];
+#pragma unroll
+  for (int j = 0; j < NP; ++j) {
+    d0[j] = __ldg(V.d[j]);
+    dm1[j] = __ldg(V.d[j] + m + 1);
+    sp[j] = 0.0;
+  }
+  const T ig = T(A.inv_gamma);
+  const T cs = T(-A.up_c * A.inv_gamma - xim);  // -c/gamma - xi_m
+  T* dst = reinterpret_cast<T*>((m & 1) ? A.y1 : A.y0);
+  const T* src = reinterpret_cast<const T*>(((m - 1) & 1) ? A.y1 : A.y0);
+  double sy = 0.0;
+  for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < o.n; q += (long long)gridDim.x * blockDim.x) {
+    int i, j;
+    up3_ij(o, q, i, j);
+    long long pts[7];
+    up3_points(o, i, j, pts);
+    T v, yc;
+    if (m == 0) {
+      v = up3_apply<BURGERS, T, double>(o, A.u, A.w, pts);
+      yc = T(__ldg(A.w + q));
+    } else {
+      v = up3_apply<BURGERS, T, T>(o, A.u, src, pts);
+      yc = src[q];
+    }
+    v = ig * v + cs * yc;
+    dst[q] = v;
+    const double vd = double(v);
+    sy = fma(vd, vd, sy);
+#pragma unroll
+    for (int k = 0; k < NP; ++k) {
+      const double po = m == 0 ? d0[k] * double(yc) : V.p[k][q];
+      const double pn = fma(dm1[k], vd, po);
+      V.p[k][q] = pn;
+      sp[k] = fma(pn, pn, sp[k]);
+    }
+  }
+  double sums[1 + NP];
+  sums[0] = sy;
+#pragma unroll
+  for (int k = 0; k < NP; ++k) sums[1 + k] = sp[k];
+  if (!last_block_total_n<1 + NP>(sums, partials, ticket)) return;
+  if (threadIdx.x == 0) {
+    double tp[NP];
+#pragma unroll
+    for (int k = 0; k < NP; ++k) tp[k] = sums[1 + k];
+    leja_finalize_vertical<NP>(A, st, m, dm1, sums[0], tp, 1.0, 1.0, cond);
+  }
+}
+
+template <bool BURGERS, int NP>
+static __global__ void __launch_bounds__(kThreadsPerBlock)
+    leja_iter_df_up3_vertical_kernel(const LoopArgs* __restrict__ Ap, const VertArgs* __restrict__ Vp,
+                                     LoopState* __restrict__ st, double* __restrict__ partials,
+                                     unsigned int* __restrict__ ticket, cudaGraphConditionalHandle cond) {
+  const LoopArgs& A = *Ap;
+  const VertArgs& V = *Vp;
+  const int m = __ldcg(&st->m);
+  count_launch(st);
+  if (__ldcg(&st->done)) return;
+  const int kexp = __ldcg(&st->kscale);
+  const int sig = __ldcg(&st->sig);
+  const int dlt = __ldcg(&st->dlt);
+  const Up3Op o = A.up;
+  const double xim = __ldg(A.xi + m);
+  const double ysc = pow2(sig + dlt - kexp);
+  double dm1d[NP];
+  dfv d0[NP], dm1[NP], accp[NP];
+#pragma unroll
+  for (int k = 0; k < NP; ++k) {
+    dm1d[k] = __ldg(V.d[k] + m + 1);
+    dm1[k] = df_from_double(dm1d[k] * ysc);
+    d0[k] = df_from_double(__ldg(V.d[k]));
+    accp[k] = dfv{0.f, 0.f};
+  }
+  const double sw = pow2(-dlt);
+  const float swf = (float)sw;
+  const double ig = A.inv_gamma;
+  // diffusion-advection: the seven constant weights (shift and 2^-dlt folded in)
+  float wh[7], wl[7];
+  {
+    double wd[7];
+    up3_weights(o, wd);
+#pragma unroll
+    for (int k = 0; k < 7; ++k) {
+      double wk = wd[k] * ig;
+      if (k == 0) wk += -A.up_c * ig - xim;
+      const dfv t = df_from_double(wk * sw);
+      wh[k] = t.h;
+      wl[k] = t.l;
+    }
+  }
+  // Burgers: the constant parts of the point weights
+  const dfv cc0 = df_from_double((-2.0 * o.cxx - 2.0 * o.cyy - A.up_c) * ig - xim);
+  const dfv lxs = df_from_double(o.cxx * ig), lys = df_from_double(o.cyy * ig);
+  const dfv rat = df_from_double(o.gy / o.gx);
+  float2* dst = reinterpret_cast<float2*>((m & 1) ? A.y1 : A.y0);
+  const float2* src = reinterpret_cast<const float2*>(((m - 1) & 1) ? A.y1 : A.y0);
+  dfv accy = {0.f, 0.f};
+  for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < o.n; q += (long long)gridDim.x * blockDim.x) {
+    int i, j;
+    up3_ij(o, q, i, j);
+    long long pts[7];
+    up3_points(o, i, j, pts);
+    dfv t[7];
+    if (m == 0) {
+#pragma unroll
+      for (int k = 0; k < 7; ++k) t[k] = df_split_scaled(__ldg(A.w + pts[k]), kexp);
+    } else {
+#pragma unroll
+      for (int k = 0; k < 7; ++k) {
+        const float2 f = __ldg(src + pts[k]);
+        t[k] = {f.x, f.y};
+      }
+    }
+    dfv v;
+    if constexpr (BURGERS) {
+      dfv qv[7];
+#pragma unroll
+      for (int k = 0; k < 7; ++k) {
+        const float2 f = __ldg(A.bq + pts[k]);
+        qv[k] = {f.x, f.y};
+      }
+      dfv wv[7];
+      wv[0] = df_add(cc0, df_scale_f(df_add(qv[0], df_mul(qv[0], rat)), (float)kUp3K0));
+      wv[1] = df_add(lxs, df_scale_f(qv[1], (float)kUp3Km));
+      wv[2] = df_add(lxs, df_scale_f(qv[2], (float)kUp3K1));
+      wv[3] = df_scale_f(qv[3], (float)kUp3K2);
+      wv[4] = df_add(lys, df_scale_f(df_mul(qv[4], rat), (float)kUp3Km));
+      wv[5] = df_add(lys, df_scale_f(df_mul(qv[5], rat), (float)kUp3K1));
+      wv[6] = df_scale_f(df_mul(qv[6], rat), (float)kUp3K2);
+      float bh[7], bl[7];
+#pragma unroll
+      for (int k = 0; k < 7; ++k) {
+        bh[k] = wv[k].h;
+        bl[k] = wv[k].l;
+      }
+      v = df_dot7(bh, bl, t);
+      v.h *= swf;
+      v.l *= swf;
+    } else {
+      v = df_dot7(wh, wl, t);
+    }
+    dst[q] = make_float2(v.h, v.l);
+    df_acc(accy, __fmul_rn(v.h, v.h));
+#pragma unroll
+    for (int k = 0; k < NP; ++k) {
+      dfv po;
+      if (m == 0) {
+        po = df_mul(d0[k], t[0]);
+      } else {
+        const float2 f = V.pdf[k][q];
+        po = {f.x, f.y};
+      }
+      const dfv pn = df_axpy(dm1[k], v, po);
+      V.pdf[k][q] = make_float2(pn.h, pn.l);
+      df_acc(accp[k], __fmul_rn(pn.h, pn.h));
+    }
+  }
+  double sums[1 + NP];
+  sums[0] = df_to_double(accy);
+#pragma unroll
+  for (int k = 0; k < NP; ++k) sums[1 + k] = df_to_double(accp[k]);
+  if (!last_block_total_n<1 + NP>(sums, partials, ticket)) return;
+  if (threadIdx.x == 0) {
+    double tp[NP];
+#pragma unroll
+    for (int k = 0; k < NP; ++k) tp[k] = sums[1 + k];
     leja_finalize_vertical<NP>(A, st, m, dm1d, sums[0], tp, pow2(sig + dlt), pow2(kexp), cond);
     const double rms = sqrt(sums[0] / double(A.n));
     int e = 0;

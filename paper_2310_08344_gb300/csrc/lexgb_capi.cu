@@ -904,13 +904,12 @@ lx_status phi_l_apply_vertical(lx_ctx* c, int l, int nc, const double* alpha, co
   }
   const lx_problem& P = c->prob;
   if (is_burgers(P.kind) && !u) return LX_E_INVAL;
-  if (is_up3(P.kind)) {
-    set_last_error("vertical interpolation is built for the central-difference operators");
-    return LX_E_INVAL;
-  }
   const bool df = P.precision == LX_DF64;
+  const bool up = is_up3(P.kind);  // point-wise kernels: no layout requirement
   bool wide;
-  if (df) {
+  if (up) {
+    wide = false;
+  } else if (df) {
     if (P.nx % kPipeRow != 0 || !aligned16(w)) {
       set_last_error("vertical float-float interpolation needs nx % 128 == 0 and a 16-byte aligned w");
       return LX_E_INVAL;
@@ -952,11 +951,11 @@ lx_status phi_l_apply_vertical(lx_ctx* c, int l, int nc, const double* alpha, co
   }
   LX_CUDA(cudaStreamSynchronize(c->stream));  // dh is host memory of this frame
   const int variant = wide ? kVec2 : kVec1;
-  const int H = df ? 8 : c->strip_h;
+  const int H = (df && !up) ? 8 : c->strip_h;
   LoopGraph& L = c->vloop[variant][nc - 1];
   if (!L.built || L.cand.func != fn) {
     destroy_graph(L);
-    const Cand k{fn, kThreadsPerBlock, 0, df ? 4 : (wide ? 2 : 1), "leja_iter_vertical"};
+    const Cand k{fn, kThreadsPerBlock, 0, (df && !up) ? 4 : (wide ? 2 : 1), "leja_iter_vertical"};
     int grid = 0;
     const int gs = grid_for(c, k, H, &grid);
     if (gs != LX_OK) return (lx_status)gs;

@@ -139,11 +139,34 @@ def test_up3_forms_not_offered(lx):
 
     with pytest.raises(LexgbError):
         lx.leja_setup(96, 96, NU, A, lx.BURGERS_UP3, lx.DF64)  # float-float Burgers needs nx % 128 == 0
-    ctx = lx.leja_setup(64, 64, NU, A, lx.ADVDIFF_UP3, lx.FP64)
-    w = dev(synth.problem1_ic(64, 64))
-    outs = [torch.empty(64 * 64, dtype=torch.float64, device="cuda")]
-    st, _ = lx.phi_l_apply_vertical(ctx, 1, [1.0], None, w, outs, -1e3, 250.0, 1e-3, TOL, TOL)
-    assert st == 1
+
+
+@pytest.mark.parametrize("kind,prec,nx,ny", [(2, "FP64", 64, 64), (2, "FP64", 96, 50), (2, "MIXED", 64, 64),
+                                             (2, "DF64", 96, 50), (2, "DF64", 128, 64), (3, "FP64", 80, 48),
+                                             (3, "DF64", 128, 64), (3, "MIXED", 64, 64)])
+@pytest.mark.parametrize("alphas", [[1.0], [0.25, 0.5, 0.75, 1.0], [0.5, 1.0, 0.3]])
+def test_phi_vertical_up3(lx, xi_oracle, kind, prec, nx, ny, alphas):
+    # several phi_1(alpha_j h Op) w from one Newton basis on the paper's
+    # discretisation, against the oracle's vertical loop (same stop rule)
+    if kind == 2:
+        u = None
+        w = synth.problem1_ic(nx, ny, seed=11)
+        h = 50 * synth.cfl_step_pm1(nx, ny, NU, A)
+    else:
+        u = synth.problem3_ic(nx, ny, seed=12)
+        w = synth.random_field(nx * ny, seed=13)
+        h = 30 * synth.cfl_step_pm1(nx, ny, NU, A * np.abs(u).max())
+    c, g = _interval(kind, nx, ny, A, u)
+    ctx = lx.leja_setup(nx, ny, NU, A, kind, getattr(lx, prec))
+    outs = [torch.empty(nx * ny, dtype=torch.float64, device="cuda") for _ in alphas]
+    st, it = lx.phi_l_apply_vertical(ctx, 1, alphas, dev(u) if u is not None else None, dev(w), outs, c, g, h,
+                                     TOL, TOL)
+    ref, it_o, st_o = oracle.leja_phi_vertical(kind, nx, ny, NU, A, u, 1, alphas, w, c, g, h, TOL, TOL, xi_oracle)
+    assert st == 0 and st_o == 0
+    bar, dit = (1e-5, 3) if prec == "MIXED" else (TOL, 1)
+    assert abs(it - it_o) <= dit
+    for j in range(len(alphas)):
+        assert rel(outs[j].cpu().numpy(), ref[j]) <= bar
 
 
 @pytest.mark.parametrize("name,strip_h", [("leja_iter_df_pipe_up3_b3", 0), ("leja_iter_df_pipe_up3_b3", 8),
