@@ -23,6 +23,7 @@
 #include "leja_df64.cuh"
 #include "leja_df64_2step.cuh"
 #include "leja_upwind.cuh"
+#include "leja_upwind_2step.cuh"
 #include "leja_kernels.cuh"
 #include "lexgb_internal.h"
 #include "lexgb_vertical.h"
@@ -183,12 +184,18 @@ std::vector<Cand> candidates(int kind, int precision, int cls) {
       }
       if (!b && wide) {
         // pipelined (nx % 128 == 0, aligned vectors), then the point-wise form
-        // (balanced row ranges by default: 389 us per iteration at 8192^2
-        // against 411 us with 8-row strips)
+        // two Leja iterations per pass first (379 us per iteration at 8192^2),
+        // then one (390 us; 411 us with 8-row strips instead of balanced row
+        // ranges): the kernels are issue-bound, so halving the traffic gains
+        // only what the smaller instruction count per iteration gives
+        v.push_back(Cand{reinterpret_cast<const void*>(&leja_iter_df_pipe2_up3_kernel<3, 6>), kPipeThreads,
+                         up3_2step_smem_bytes<6>(), 4, "leja_iter_df_pipe2_up3_b3", 2, 0});
         v.push_back(Cand{reinterpret_cast<const void*>(&leja_iter_df_pipe_up3_kernel<3>), kPipeThreads,
                          kUpSmemBytes, 4, "leja_iter_df_pipe_up3_b3", 1, 0});
         v.push_back(Cand{reinterpret_cast<const void*>(&leja_iter_df_pipe_up3_kernel<2>), kPipeThreads,
                          kUpSmemBytes, 4, "leja_iter_df_pipe_up3_b2", 1, 0});
+        v.push_back(Cand{reinterpret_cast<const void*>(&leja_iter_df_pipe2_up3_kernel<2, 6>), kPipeThreads,
+                         up3_2step_smem_bytes<6>(), 4, "leja_iter_df_pipe2_up3_b2", 2, 0});
       }
       if (!b) {
         f = reinterpret_cast<const void*>(&leja_iter_df_up3_kernel);

@@ -170,7 +170,9 @@ def test_phi_vertical_up3(lx, xi_oracle, kind, prec, nx, ny, alphas):
 
 
 @pytest.mark.parametrize("name,strip_h", [("leja_iter_df_pipe_up3_b3", 0), ("leja_iter_df_pipe_up3_b3", 8),
-                                          ("leja_iter_df_pipe_up3_b2", 32), ("leja_iter_df_up3", 8)])
+                                          ("leja_iter_df_pipe_up3_b2", 32), ("leja_iter_df_up3", 8),
+                                          ("leja_iter_df_pipe2_up3_b3", 0), ("leja_iter_df_pipe2_up3_b3", 8),
+                                          ("leja_iter_df_pipe2_up3_b3", 32), ("leja_iter_df_pipe2_up3_b2", 0)])
 @pytest.mark.parametrize("a", [A, -4.0])
 def test_df64_up3_candidates(lx, xi_oracle, name, strip_h, a):
     # every float-float candidate of the upwind operator on a grid with two
@@ -209,3 +211,26 @@ def test_df64_burgers_up3_candidates(lx, xi_oracle, name, strip_h, a):
     ref, it_o, st_o = oracle.leja_phi(oracle.BURGERS_UP3, nx, ny, NU, a, u, 3, w, c, g, h, TOL, TOL, xi_oracle)
     assert st == 0 and st_o == 0 and abs(it - it_o) <= 1
     assert rel(out.cpu().numpy(), ref) <= TOL
+
+
+@pytest.mark.parametrize("name", ["leja_iter_df_pipe2_up3_b3", "leja_iter_df_pipe_up3_b3"])
+@pytest.mark.parametrize("tol", [1e-10, 3e-9, 1e-7, 1e-5])
+@pytest.mark.parametrize("a", [A, -4.0])
+def test_df64_up3_two_step_stop_parities(lx, xi_oracle, name, tol, a):
+    # the two-step kernel tests the stop after each of its two iterations;
+    # several tolerances give odd and even counts, and an odd stop must
+    # return p_{m+1} (the output pass removes the extra term)
+    nx, ny = 128, 72
+    u0 = synth.problem1_ic(nx, ny, seed=17)
+    h = 40 * synth.cfl_step_pm1(nx, ny, NU, a)
+    c, g = _interval(oracle.ADVDIFF_UP3, nx, ny, a, None)
+    ctx = lx.leja_setup(nx, ny, NU, a, lx.ADVDIFF_UP3, lx.DF64)
+    assert lx.lx_ctx_select_kernel(ctx, name, 0) == 0
+    out = torch.empty(nx * ny, dtype=torch.float64, device="cuda")
+    for l in (0, 1):
+        st, it = lx.phi_l_apply(ctx, l, None, dev(u0), out, c, g, h, tol, tol)
+        ref, it_o, st_o = oracle.leja_phi(oracle.ADVDIFF_UP3, nx, ny, NU, a, None, l, u0, c, g, h, tol, tol,
+                                          xi_oracle)
+        assert st == 0 and st_o == 0 and abs(it - it_o) <= 1
+        bar = 1e-10 if it == it_o else 100 * tol
+        assert rel(out.cpu().numpy(), ref) <= bar
