@@ -311,12 +311,15 @@ constexpr int kUpStages = 7;  // ring slots per warp (two rows in flight)
 constexpr int kUpSmemBytes = kPipeWarps * kUpStages * kSlotElems2 * 8;
 
 // SG: the upwind side (+1 or -1), a template parameter so that the choice
-// of the stencil points costs no per-point selects.
-template <typename S, bool FIRST, int SG>
+// of the stencil points costs no per-point selects.  POWER: one
+// power-iteration pass instead (w = A v * sg, no polynomial, sum w^2 to
+// double accuracy in accy and *small).
+template <typename S, bool FIRST, int SG, bool POWER = false>
 __device__ __forceinline__ void df_strip_up3(const LoopArgs& A, const S* __restrict__ src, float2* __restrict__ dst,
                                              float2* __restrict__ p, unsigned long long* ring, int col0, int r0,
                                              int r1, const float (&wh)[7], const float (&wl)[7], dfv d0, dfv dm1,
-                                             int sc, dfv& accy, dfv& accp) {
+                                             int sc, dfv& accy, dfv& accp, dfv sg = dfv{0.f, 0.f},
+                                             float* small = nullptr) {
   constexpr int s = SG;
   const int lane = threadIdx.x & 31;
   const int nx = A.nx, ny = A.ny;
@@ -335,7 +338,7 @@ __device__ __forceinline__ void df_strip_up3(const LoopArgs& A, const S* __restr
       cp_async16(sl + 4 + lane * 4, row + c + 2);
       if (lane == 0) cp_async16(sl, row + cw);
       if (lane == 31) cp_async16(sl + 2 + kPipeRow, row + ce);
-      if constexpr (!FIRST) {
+      if constexpr (!FIRST && !POWER) {
         if (q >= 4) {  // p of output row r0 + q - 4 arrives with y row r0 + q - 2
           const float2* prow = p + (size_t)(r0 + q - 4) * nx;
           cp_async16(sl + kY2Slot + lane * 4, prow + c);
@@ -362,7 +365,7 @@ __device__ __forceinline__ void df_strip_up3(const LoopArgs& A, const S* __restr
     const unsigned long long* sc2 = slot(a + 2);  // centre row: halo points
     df_from_raw4<S>(sn + 2 + lane * 4, sc, w4);
     dfv pold[4];
-    if constexpr (!FIRST) df_from_raw4<float2>(sn + kY2Slot + lane * 4, 0, pold);
+    if constexpr (!FIRST && !POWER) df_from_raw4<float2>(sn + kY2Slot + lane * 4, 0, pold);
     // x-neighbours of the centre row
     const dfv u3 = shfl_up_df(w2[3]), u2 = shfl_up_df(w2[2]);
     const dfv d0n = shfl_down_df(w2[0]), d1n = shfl_down_df(w2[1]);
@@ -389,16 +392,26 @@ __device__ __forceinline__ void df_strip_up3(const LoopArgs& A, const S* __restr
                         s > 0 ? w3[k] : w1[k],
                         s > 0 ? w4[k] : w0[k]};
       ynew[k] = df_dot7(wh, wl, t);
-      const dfv po = FIRST ? df_mul(d0, w2[k]) : pold[k];
-      pnew[k] = df_axpy(dm1, ynew[k], po);
-      fy = __fmaf_rn(ynew[k].h, ynew[k].h, fy);
-      fp = __fmaf_rn(pnew[k].h, pnew[k].h, fp);
+      if constexpr (POWER) {
+        ynew[k] = df_mul(sg, ynew[k]);
+        float sq, se;
+        two_prod(ynew[k].h, ynew[k].h, sq, se);
+        df_acc(accy, sq);
+        *small = __fmaf_rn(2.f * ynew[k].h, ynew[k].l, __fadd_rn(*small, se));
+      } else {
+        const dfv po = FIRST ? df_mul(d0, w2[k]) : pold[k];
+        pnew[k] = df_axpy(dm1, ynew[k], po);
+        fy = __fmaf_rn(ynew[k].h, ynew[k].h, fy);
+        fp = __fmaf_rn(pnew[k].h, pnew[k].h, fp);
+      }
     }
-    df_acc(accy, fy);
-    df_acc(accp, fp);
     const size_t ro = (size_t)(r0 + a) * nx;
     df_store_row<4>(dst + ro, c, nx, ynew);
-    df_store_row<4>(p + ro, c, nx, pnew);
+    if constexpr (!POWER) {
+      df_acc(accy, fy);
+      df_acc(accp, fp);
+      df_store_row<4>(p + ro, c, nx, pnew);
+    }
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
       w0[k] = w1[k];
@@ -1116,6 +1129,59 @@ __global__ void __launch_bounds__(kPipeThreads, MINB)
       else
         df_strip_burgers_up3z<float2, false, -1, STAGES, true>(A, vf, w, nullptr, ring, col0, r0, r1, wh, wl, 1.f,
                                                                zero, zero, 0, acc, unused, sg, &small);
+    }
+  });
+  double s = df_to_double(acc) + (double)small, dummy = 0.0;
+  if (!last_block_total2(s, dummy, partials, ticket)) return;
+  if (threadIdx.x == 0) power_pass_finish(st, s, o.n);
+}
+
+// One power-iteration pass on the upwind diffusion-advection operator in the
+// pipelined form (nx % 128 == 0, 16-byte aligned vectors): w = A v / ||v||,
+// rho_k = ||w||, the stop test of power_pass_finish; v is the caller's
+// doubles on the first pass (vin_double), float pairs after.
+template <int MINB>
+__global__ void __launch_bounds__(kPipeThreads, MINB)
+    power_pass_df_pipe_up3_kernel(Up3Op o, const void* __restrict__ vin, int vin_double, float2* __restrict__ w,
+                                  double* __restrict__ partials, unsigned int* __restrict__ ticket, LoopState* st) {
+  extern __shared__ __align__(16) unsigned long long up3p_smem[];
+  if (__ldcg(&st->pdone)) return;
+  const dfv sg = df_from_double(__ldcg(&st->sigma));
+  double wd[7];
+  up3_weights(o, wd);
+  float wh[7], wl[7];
+#pragma unroll
+  for (int k = 0; k < 7; ++k) {
+    const dfv t = df_from_double(wd[k]);
+    wh[k] = t.h;
+    wl[k] = t.l;
+  }
+  LoopArgs A;
+  A.nx = o.nx;
+  A.ny = o.ny;
+  dfv acc = {0.f, 0.f}, unused = {0.f, 0.f};
+  float small = 0.f;
+  const dfv zero = {0.f, 0.f};
+  const int warp = threadIdx.x >> 5;
+  unsigned long long* ring = up3p_smem + (size_t)warp * kUpStages * kSlotElems2;
+  const double* vd = reinterpret_cast<const double*>(vin);
+  const float2* vf = reinterpret_cast<const float2*>(vin);
+  for_each_segment(o.nx, o.ny, 0, blockIdx.x * kPipeWarps + warp, gridDim.x * kPipeWarps,
+                   [&](int col0, int r0, int r1) {
+    if (vin_double) {
+      if (o.s > 0)
+        df_strip_up3<double, true, 1, true>(A, vd, w, nullptr, ring, col0, r0, r1, wh, wl, zero, zero, 0, acc,
+                                            unused, sg, &small);
+      else
+        df_strip_up3<double, true, -1, true>(A, vd, w, nullptr, ring, col0, r0, r1, wh, wl, zero, zero, 0, acc,
+                                             unused, sg, &small);
+    } else {
+      if (o.s > 0)
+        df_strip_up3<float2, false, 1, true>(A, vf, w, nullptr, ring, col0, r0, r1, wh, wl, zero, zero, 0, acc,
+                                             unused, sg, &small);
+      else
+        df_strip_up3<float2, false, -1, true>(A, vf, w, nullptr, ring, col0, r0, r1, wh, wl, zero, zero, 0, acc,
+                                              unused, sg, &small);
     }
   });
   double s = df_to_double(acc) + (double)small, dummy = 0.0;

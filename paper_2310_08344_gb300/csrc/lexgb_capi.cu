@@ -136,7 +136,7 @@ struct lx_ctx {
   float2* d_pdfv[kMaxVertical] = {};
   LoopGraph vloop[kNumVariants][kMaxVertical];
   int aux_grid = 0;
-  int pow_pipe_grid = 0;  // grid of the pipelined upwind Burgers power pass (0: not yet sized)
+  int pow_pipe_grid = 0;  // grid of the pipelined upwind power pass (0: not yet sized)
 
   cudaEvent_t ev[8] = {};
   int ev_used = 0;
@@ -741,13 +741,16 @@ lx_status leja_setup(const lx_problem* prob, int integrator, int max_leja, void*
   return LX_OK;
 }
 
-// Grid of the pipelined upwind Burgers power pass: one balanced row range
+// Grid of the pipelined upwind power pass: one balanced row range
 // (at least four rows) per warp, at most the resident blocks of one wave.
 lx_status size_pow_pipe_grid(lx_ctx* c) {
-  const void* f = reinterpret_cast<const void*>(&power_pass_df_pipe_burgers_up3z_kernel<3, 5>);
-  LX_CUDA(cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, up3z_smem_bytes<5>()));
+  const bool b = c->prob.kind == LX_BURGERS_UP3;
+  const void* f = b ? reinterpret_cast<const void*>(&power_pass_df_pipe_burgers_up3z_kernel<3, 5>)
+                    : reinterpret_cast<const void*>(&power_pass_df_pipe_up3_kernel<3>);
+  const int smem = b ? up3z_smem_bytes<5>() : kUpSmemBytes;
+  LX_CUDA(cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
   int per_sm = 0;
-  LX_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, f, kPipeThreads, up3z_smem_bytes<5>()));
+  LX_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, f, kPipeThreads, smem));
   per_sm = std::max(per_sm, 1);
   const long long units = ((long long)(c->prob.nx / kPipeRow) * c->prob.ny + 3) / 4;
   const int want = (int)std::min<long long>((units + kPipeWarps - 1) / kPipeWarps, 1 << 30);
@@ -828,15 +831,19 @@ lx_status power_bound(lx_ctx* c, const double* u, const double* v0, int max_iter
     }
     if (dfu) {
       float2* wf = reinterpret_cast<float2*>(outv);
-      if (P.kind == LX_ADVDIFF_UP3) {
+      const bool pipe = P.nx % kPipeRow == 0 && aligned16(in);
+      if (pipe && c->pow_pipe_grid == 0) {
+        lx_status gs = size_pow_pipe_grid(c);
+        if (gs != LX_OK) return gs;
+      }
+      if (P.kind == LX_ADVDIFF_UP3 && pipe) {
+        power_pass_df_pipe_up3_kernel<3><<<c->pow_pipe_grid, kPipeThreads, kUpSmemBytes, c->stream>>>(
+            c->up3, in, k == 1 ? 1 : 0, wf, c->d_partials, c->d_ticket, c->d_state);
+      } else if (P.kind == LX_ADVDIFF_UP3) {
         power_pass_df_up3_kernel<false><<<G, kThreadsPerBlock, 0, c->stream>>>(
             c->up3, in, k == 1 ? 1 : 0, wf, nullptr, c->d_partials, c->d_ticket, c->d_state);
-      } else if (aligned16(in)) {
-        // pipelined product form (the float-float Burgers form has nx % 128 == 0)
-        if (c->pow_pipe_grid == 0) {
-          lx_status gs = size_pow_pipe_grid(c);
-          if (gs != LX_OK) return gs;
-        }
+      } else if (pipe) {
+        // pipelined product form
         power_pass_df_pipe_burgers_up3z_kernel<3, 5><<<c->pow_pipe_grid, kPipeThreads, up3z_smem_bytes<5>(),
                                                          c->stream>>>(c->up3, in, k == 1 ? 1 : 0, wf, c->d_bq,
                                                                       c->d_partials, c->d_ticket, c->d_state);

@@ -234,3 +234,51 @@ def test_df64_up3_two_step_stop_parities(lx, xi_oracle, name, tol, a):
         assert st == 0 and st_o == 0 and abs(it - it_o) <= 1
         bar = 1e-10 if it == it_o else 100 * tol
         assert rel(out.cpu().numpy(), ref) <= bar
+
+
+def test_full_size_problem1_exact(lx):
+    # Problem I at 4096^2 with the paper's tolerance and step (100 dt_CFL),
+    # default kernel (two Leja iterations per pass): exp(hA)u against the
+    # exact Fourier solution of the discrete operator
+    from fourier import phi_apply_symbol, symbol_up3
+
+    n = 4096
+    u0 = synth.problem1_ic(n, n)
+    lam = symbol_up3(n, n, NU, A)
+    c, g = oracle.spectral_interval(float(np.abs(lam).max()))
+    h = 100 * synth.cfl_step_pm1(n, n, NU, A)
+    ctx = lx.leja_setup(n, n, NU, A, lx.ADVDIFF_UP3, lx.DF64)
+    out = torch.empty(n * n, dtype=torch.float64, device="cuda")
+    st, it = lx.phi_l_apply(ctx, 0, None, dev(u0), out, c, g, h, 1e-12, 1e-12)
+    assert st == 0
+    e = rel(out.cpu().numpy(), phi_apply_symbol(0, lam, h, u0, n, n))
+    print(f"Problem I 4096^2: {lx.lx_ctx_kernel_name(ctx)}, iters {it}, rel_l2 vs exact {e:.3e}")
+    assert e <= 1e-9
+
+
+def test_full_size_problem3_properties(lx):
+    # Problem III at 4096^2, one EXPRB32 step of 100 dt_CFL at tol 1e-12:
+    # the flux form conserves the mean exactly (1^T J = 0 and sum R = 0), and
+    # the float-float and FP64 paths (independent kernels) agree
+    n = 4096
+    u0 = synth.problem3_ic(n, n)
+    v0 = synth.power_start(n * n, seed=5)
+    h = 100 * synth.cfl_step_pm1(n, n, NU, A * np.abs(u0).max())
+    res = {}
+    for prec in ("DF64", "FP64"):
+        ctx = lx.leja_setup(n, n, NU, A, lx.BURGERS_UP3, getattr(lx, prec), lx.EXPRB32)
+        ud = dev(u0)
+        st, rho, _ = lx.power_bound(ctx, ud, dev(v0), 10)
+        assert st == 0
+        c, g = lx.spectral_interval(rho)
+        lo, hi = torch.empty_like(ud), torch.empty_like(ud)
+        st, err, it = lx.expint_step(ctx, ud, lo, hi, c, g, h, 1e-12, 1e-12)
+        assert st == 0
+        res[prec] = (lo.cpu().numpy(), hi.cpu().numpy(), err, it)
+        del ctx
+    lo, hi, err, it = res["DF64"]
+    assert abs(hi.mean() - u0.mean()) <= 1e-12 * np.abs(u0).max()
+    assert abs(lo.mean() - u0.mean()) <= 1e-12 * np.abs(u0).max()
+    assert rel(hi, res["FP64"][1]) <= 1e-10 and rel(lo, res["FP64"][0]) <= 1e-10
+    assert abs(it - res["FP64"][3]) <= 2 and abs(err - res["FP64"][2]) <= 1e-6 * res["FP64"][2] + 1e-15
+    print(f"Problem III 4096^2: iters {it}, err {err:.3e}, df64 vs FP64 {rel(hi, res['FP64'][1]):.2e}")
