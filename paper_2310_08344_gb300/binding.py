@@ -520,11 +520,13 @@ def rhs_function(f, n):
 
     import torch
 
-    views = {}
+    views = {}  # the engine passes a few fixed buffers; callers' vectors may vary
 
     def view(ptr):
         t = views.get(ptr)
         if t is None:
+            if len(views) >= 32:
+                views.clear()
             t = torch.as_tensor(_DevRange(ptr, n), device="cuda")
             views[ptr] = t
         return t
