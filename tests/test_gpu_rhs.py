@@ -265,3 +265,36 @@ def test_rhs_setup_rejects(lx):
         lx.leja_setup_rhs(64, problem=(8, 8, 1.0, 0.0, 0), eps0=-1.0)
     with pytest.raises(LexgbError):
         lx.leja_setup_rhs(64, problem=(8, 8, 1.0, 0.0, 0), integrator=5)
+
+
+def test_rhs_statuses_match_oracle(lx, xi):
+    # a non-finite right-hand side and a too-small point table give the
+    # statuses of the oracle's loop (LX_E_NONFINITE, LX_E_NOCONV)
+    nx = ny = 32
+    n = nx * ny
+    w = synth.random_field(n, seed=21)
+
+    def f_nan(x, out):
+        out.copy_(-x)
+        out[5] = float("nan")
+
+    ctx = lx.leja_setup_rhs(n, f=f_nan)
+    out = torch.empty(n, dtype=torch.float64, device="cuda")
+    st, it = lx.phi_l_apply_rhs(ctx, 1, None, dev(w), out, -1.0, 0.5, 1.0, TOL, TOL)
+
+    def f_nan_np(x):
+        y = -x.copy()
+        y[5] = np.nan
+        return y
+
+    _, it_o, st_o = oracle.leja_phi_fd(0, nx, ny, 0, 0, None, 1, w, -1.0, 0.5, 1.0, TOL, TOL, xi, rhs=f_nan_np)
+    assert st == st_o == lx.binding.E_NONFINITE and it == it_o == 1
+    # a stiff linear f with a 16-point table: the engine's coefficient count
+    # bounds the loop first, and both sides report no convergence
+    small = lx.leja_setup_rhs(n, problem=(nx, ny, 1.0, 0.0, 0), max_leja=16)
+    rho = 8.0 * nx * nx
+    c, g = oracle.spectral_interval(rho)
+    st, it = lx.phi_l_apply_rhs(small, 0, None, dev(w), out, c, g, 50.0 / rho, 1e-14, 1e-14)
+    _, it_o, st_o = oracle.leja_phi_fd(0, nx, ny, 1.0, 0.0, None, 0, w, c, g, 50.0 / rho, 1e-14, 1e-14,
+                                       oracle.leja_points(16))
+    assert st == lx.binding.E_NOCONV and st_o == oracle.E_NOCONV
