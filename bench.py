@@ -54,6 +54,7 @@ def parse():
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-autotune", action="store_true")
+    p.add_argument("--no-plain", action="store_true", help="skip the plain-form (native FP64) comparison")
     p.add_argument("--kernel", default=None, help="force a fused-iteration kernel (name) instead of autotuning")
     p.add_argument("--strip-h", type=int, default=8)
     p.add_argument("--unroll", type=int, default=None, help="fused-iteration launches per graph-loop pass")
@@ -878,6 +879,40 @@ def main():
                             "so frac can exceed the kernel's own DRAM share (min_dram_frac)")
     launches = int(stats["kernels"])  # counted by the library on the context stream
 
+    # the plain form (native FP64 kernels) on the same steps from the same
+    # initial state: time per step and the difference of the final states
+    plain = None
+    if not args.no_plain and args.precision != "fp64":
+        ctxp = lx.leja_setup(n, n, NU, ADV, lx.ADVDIFF, lx.FP64, lx.ROS_EU, 1000, stream)
+        if args.source:
+            lx.lx_ctx_set_source(ctxp, src_field)
+        pc, pn = torch.from_numpy(u0).cuda(), torch.empty_like(ua)
+
+        def pstep(s_, d_):
+            st, err, it = lx.expint_step(ctxp, s_, None, d_, c, g, h, TOL, TOL)
+            if st != 0:
+                raise SystemExit(f"plain expint_step failed: {lx.STATUS.get(st, st)}")
+            return it
+
+        for _ in range(max(args.warmup, 0)):
+            pstep(pc, pn)
+            pc, pn = pn, pc
+        torch.cuda.synchronize()
+        p0, p1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        p0.record(stream)
+        pits = []
+        for _ in range(args.steps):
+            pits.append(pstep(pc, pn))
+            pc, pn = pn, pc
+        p1.record(stream)
+        torch.cuda.synchronize()
+        pms = p0.elapsed_time(p1) / args.steps
+        plain = {"precision": "fp64 (native FP64 kernels)", "kernel": lx.lx_ctx_kernel_name(ctxp),
+                 "value": float(N) * sum(pits) / (pms * args.steps / 1e3) / 1e9, "ms_per_step": pms,
+                 "leja_iters_per_step": pits, "chosen_speedup": pms / (ms / args.steps),
+                 "rel_l2_final_chosen_vs_plain": float(torch.linalg.norm(cur - pc) / torch.linalg.norm(pc))}
+        ctxp.close()
+
     # end to end through the host-buffer entry point
     e2e = None
     if not args.no_e2e:
@@ -917,7 +952,8 @@ def main():
                            "leja_iters_per_step": iters, "rho": rho,
                            "kernel_selected": (tune or {}).get("selected", {"kernel": kname}),
                            "l2": "inputs larger than L2 (128 MiB per vector, 512 MiB moved per Leja iteration)"},
-                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "clocks": clk}
+                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "clocks": clk,
+                "plain": plain}
         print(json.dumps(line))
     ctx.close()
     if pg:
