@@ -166,14 +166,15 @@ def kernel_source_sha():
 
 def ncu_traffic(kernel_name: str, n_points: int):
     """DRAM bytes per launch of the fused kernel from the committed ncu
-    summary, or None when the summary is for other kernel sources."""
+    summary, or None when the summary is for other kernel sources or another
+    grid size (the L2-resident share depends on the size)."""
     path = os.path.join(ROOT, "profiles", "leja_iter_traffic.json")
     if not os.path.exists(path):
         return None
     with open(path) as f:
         rec = json.load(f)
     ent = rec.get(kernel_name)
-    if not ent or ent.get("source_sha") != kernel_source_sha():
+    if not ent or ent.get("source_sha") != kernel_source_sha() or int(ent.get("points", 0)) != n_points:
         return None
     return float(ent["dram_bytes_per_point"]) * n_points
 
