@@ -300,7 +300,9 @@ lx_status lx_ctx_set_graph_unroll(lx_ctx* ctx, int unroll);
  * candidate kernel of the context's (kind, precision) -- for LX_DF64 the
  * shared-memory-pipelined kernel at 2, 3 and 4 resident blocks per SM, the
  * register-window kernel and the two-step (two Leja iterations per pass
- * over memory) pipelined kernel -- at strip heights 8..128 rows and, for the
+ * over memory) pipelined kernel; for the upwind kinds the one- and two-step
+ * pipelined kernels, the point-wise kernel and, for LX_BURGERS_UP3, the
+ * product-form and point-weight forms -- at strip heights 8..128 rows and, for the
  * pipelined kernels, strip height 0 (one balanced contiguous row range per
  * warp), each for
  * `iters` launches (1..50) on the context's own buffers, and selects the
