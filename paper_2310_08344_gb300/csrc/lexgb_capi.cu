@@ -196,6 +196,8 @@ std::vector<Cand> candidates(int kind, int precision, int cls) {
                          kUpSmemBytes, 4, "leja_iter_df_pipe_up3_b2", 1, 0});
         v.push_back(Cand{reinterpret_cast<const void*>(&leja_iter_df_pipe2_up3_kernel<2, 6>), kPipeThreads,
                          up3_2step_smem_bytes<6>(), 4, "leja_iter_df_pipe2_up3_b2", 2, 0});
+        v.push_back(Cand{reinterpret_cast<const void*>(&leja_iter_df_pipe2_up3_kernel<4, 5>), kPipeThreads,
+                         up3_2step_smem_bytes<5>(), 4, "leja_iter_df_pipe2_up3_b4", 2, 0});
       }
       if (!b) {
         f = reinterpret_cast<const void*>(&leja_iter_df_up3_kernel);

@@ -172,7 +172,8 @@ def test_phi_vertical_up3(lx, xi_oracle, kind, prec, nx, ny, alphas):
 @pytest.mark.parametrize("name,strip_h", [("leja_iter_df_pipe_up3_b3", 0), ("leja_iter_df_pipe_up3_b3", 8),
                                           ("leja_iter_df_pipe_up3_b2", 32), ("leja_iter_df_up3", 8),
                                           ("leja_iter_df_pipe2_up3_b3", 0), ("leja_iter_df_pipe2_up3_b3", 8),
-                                          ("leja_iter_df_pipe2_up3_b3", 32), ("leja_iter_df_pipe2_up3_b2", 0)])
+                                          ("leja_iter_df_pipe2_up3_b3", 32), ("leja_iter_df_pipe2_up3_b2", 0),
+                                          ("leja_iter_df_pipe2_up3_b4", 0)])
 @pytest.mark.parametrize("a", [A, -4.0])
 def test_df64_up3_candidates(lx, xi_oracle, name, strip_h, a):
     # every float-float candidate of the upwind operator on a grid with two
