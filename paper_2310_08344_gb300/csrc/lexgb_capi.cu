@@ -1572,12 +1572,23 @@ const void* batch_kernel_ptr() {
 
 lx_status build_batch_graph(lx_batch* b, int v) {
   if (b->exec[v]) return LX_OK;
-  const void* fn = b->df ? reinterpret_cast<const void*>(&leja_batch_df_kernel)
-                         : (v == 0 ? batch_kernel_ptr<2>() : batch_kernel_ptr<1>());
+  const void* fn = v == 0 ? batch_kernel_ptr<2>() : batch_kernel_ptr<1>();
   int per_sm = 0;
   LX_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kThreadsPerBlock, 0));
   const int want = (b->total_strips[v] + kWarpsPerBlock - 1) / kWarpsPerBlock;
+  // grid of the auxiliary per-strip kernels (and of the FP64 iteration)
   b->grid[v] = std::max(1, std::min(want, std::max(per_sm, 1) * b->sm_count));
+  int threads = kThreadsPerBlock, smem = 0, grid = b->grid[v];
+  if (b->df) {
+    // float-float: the shared-memory-pipelined strip, 4 warps per block
+    fn = reinterpret_cast<const void*>(&leja_batch_df_pipe_kernel<3, kPipeStages>);
+    threads = kPipeThreads;
+    smem = kPipeSmemBytes;
+    LX_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+    LX_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, threads, smem));
+    const int wantp = (b->total_strips[v] + kPipeWarps - 1) / kPipeWarps;
+    grid = std::max(1, std::min(wantp, std::max(per_sm, 1) * b->sm_count));
+  }
   LX_CUDA(cudaGraphCreate(&b->graph[v], 0));
   cudaGraphConditionalHandle cond;
   LX_CUDA(cudaGraphConditionalHandleCreate(&cond, b->graph[v], 1, cudaGraphCondAssignDefault));
@@ -1604,8 +1615,9 @@ lx_status build_batch_graph(lx_batch* b, int v) {
   cudaKernelNodeParams kp;
   std::memset(&kp, 0, sizeof(kp));
   kp.func = const_cast<void*>(fn);
-  kp.gridDim = dim3(b->grid[v]);
-  kp.blockDim = dim3(kThreadsPerBlock);
+  kp.gridDim = dim3(grid);
+  kp.blockDim = dim3(threads);
+  kp.sharedMemBytes = (unsigned)smem;
   kp.kernelParams = kargs;
   cudaGraphNode_t knode;
   LX_CUDA(cudaGraphAddKernelNode(&knode, body, nullptr, 0, &kp));
