@@ -1580,10 +1580,11 @@ lx_status build_batch_graph(lx_batch* b, int v) {
   b->grid[v] = std::max(1, std::min(want, std::max(per_sm, 1) * b->sm_count));
   int threads = kThreadsPerBlock, smem = 0, grid = b->grid[v];
   if (b->df) {
-    // float-float: the shared-memory-pipelined strip, 4 warps per block
-    fn = reinterpret_cast<const void*>(&leja_batch_df_pipe_kernel<3, kPipeStages>);
+    // float-float: two Leja iterations per pass on the shared-memory-
+    // pipelined strip, 4 warps per block
+    fn = reinterpret_cast<const void*>(&leja_batch_df_pipe2_kernel<3, 5>);
     threads = kPipeThreads;
-    smem = kPipeSmemBytes;
+    smem = pipe2_smem_bytes<5>();
     LX_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
     LX_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, threads, smem));
     const int wantp = (b->total_strips[v] + kPipeWarps - 1) / kPipeWarps;
@@ -1709,7 +1710,7 @@ lx_status batch_setup(int count, const lx_problem* probs, int max_leja, void* cu
       !cuda_ok(cudaMallocHost((void**)&b->h_inst, sizeof(BatchInst) * count), "cudaMallocHost") ||
       !dm((void**)&b->d_bs, sizeof(BatchState)) || !dm((void**)&b->d_tickets, sizeof(unsigned) * count) ||
       !dm((void**)&b->d_block_ticket, sizeof(unsigned)) ||
-      !dm((void**)&b->d_partials, sizeof(double) * 2 * (size_t)std::max(b->total_strips[0], b->total_strips[1])) ||
+      !dm((void**)&b->d_partials, sizeof(double) * 4 * (size_t)std::max(b->total_strips[0], b->total_strips[1])) ||
       !dm((void**)&b->d_xi, sizeof(double) * b->K) || !dm((void**)&b->d_coef, sizeof(double) * b->K * count) ||
       !cuda_ok(cudaMallocHost((void**)&b->h_coef, sizeof(double) * b->K * count), "cudaMallocHost") ||
       !dm((void**)&b->d_ybuf, sizeof(double) * ytot) || (df && !dm((void**)&b->d_pbuf, sizeof(float2) * ptot)))
