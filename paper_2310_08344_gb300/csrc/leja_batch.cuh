@@ -162,7 +162,7 @@ __global__ void __launch_bounds__(kThreadsPerBlock)
 
 // ---------------------------------------------------------------------------
 // Float-float batches (every instance nx % 128 == 0): the same strip list
-// with 4 points per lane, the register-window df64 strip of the one-context
+// with 4 points per lane, the two-step pipelined strip of the one-context
 // kernel, and a per-instance storage scaling.
 // ---------------------------------------------------------------------------
 
@@ -199,185 +199,6 @@ static __global__ void batch_df_scale_finish_kernel(BatchInst* __restrict__ inst
     I->sig = I->kscale;
     I->dlt = 0;
   }
-}
-
-// One warp's strip of a float-float batched iteration is done: publish its
-// partial sums; the warp that completes an instance adds the instance's
-// partials in strip order, runs its stopping test (Sec. 2.2) and
-// renormalises its next basis vector.
-__device__ __forceinline__ void batch_df_strip_done(BatchInst* I, int i, int s, int m, double dm1d, int sig,
-                                                    int dlt, int kexp, double sy, double sp, BatchState* bs,
-                                                    double* __restrict__ partials,
-                                                    unsigned int* __restrict__ tickets,
-                                                    cudaGraphConditionalHandle cond, int use_cond) {
-  const int lane = threadIdx.x & 31;
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) {
-    sy += __shfl_xor_sync(0xffffffffu, sy, o);
-    sp += __shfl_xor_sync(0xffffffffu, sp, o);
-  }
-  unsigned last = 0;
-  if (lane == 0) {
-    partials[2 * (size_t)s] = sy;
-    partials[2 * (size_t)s + 1] = sp;
-    __threadfence();
-    last = (atomicAdd(tickets + i, 1u) == (unsigned)I->nstrips - 1u) ? 1u : 0u;
-  }
-  last = __shfl_sync(0xffffffffu, last, 0);
-  if (!last) return;
-  __threadfence();
-  double ty = 0.0, tp = 0.0;
-  for (int q = lane; q < I->nstrips; q += 32) {
-    ty += __ldcg(partials + 2 * (size_t)(I->first_strip + q));
-    tp += __ldcg(partials + 2 * (size_t)(I->first_strip + q) + 1);
-  }
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) {
-    ty += __shfl_xor_sync(0xffffffffu, ty, o);
-    tp += __shfl_xor_sync(0xffffffffu, tp, o);
-  }
-  if (lane == 0) {
-    const double inv_n = 1.0 / ((double)I->nx * (double)I->ny);
-    const double ynorm = sqrt(ty * inv_n) * pow2(sig + dlt), pnorm = sqrt(tp * inv_n) * pow2(kexp);
-    const double e = fabs(dm1d) * ynorm;
-    const int m1 = m + 1;
-    int status = 0;
-    bool done = false;
-    if (!isfinite(e) || !isfinite(pnorm)) {
-      status = 5;
-      done = true;
-    } else if (e <= I->rtol * pnorm + I->atol) {
-      done = true;
-    } else if (m1 >= I->kmax) {
-      status = 4;
-      done = true;
-    }
-    I->ynorm = ynorm;
-    I->pnorm = pnorm;
-    I->err = e;
-    // renormalisation of the next basis vector of this instance
-    const double rms = sqrt(ty * inv_n);
-    int ex = 0;
-    if (rms > 0.0 && isfinite(rms)) ex = ilogb(rms);
-    I->sig = sig + dlt;
-    I->dlt = max(-100, min(100, ex));
-    tickets[i] = 0u;
-    if (done) {
-      I->status = status;
-      I->iters = m1;
-      __threadfence();
-      I->done = 1;
-      if (atomicSub(&bs->active, 1) == 1 && use_cond) cudaGraphSetConditional(cond, 0);
-    }
-  }
-}
-
-// The last block of a batched launch advances the iteration index.
-__device__ __forceinline__ void batch_df_launch_done(int m, BatchState* bs, unsigned int* __restrict__ block_ticket,
-                                                     cudaGraphConditionalHandle cond, int use_cond) {
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    __threadfence();
-    if (atomicAdd(block_ticket, 1u) == gridDim.x - 1) {
-      *block_ticket = 0u;
-      bs->m = m + 1;
-      if (m + 1 >= bs->mmax && use_cond) cudaGraphSetConditional(cond, 0);
-    }
-  }
-}
-
-static __global__ void __launch_bounds__(kThreadsPerBlock)
-    leja_batch_df_kernel(BatchInst* __restrict__ inst, const int* __restrict__ strip_inst,
-                         BatchState* __restrict__ bs, double* __restrict__ partials, unsigned int* __restrict__ tickets,
-                         unsigned int* __restrict__ block_ticket, const double* __restrict__ xi, int H,
-                         int total_strips, cudaGraphConditionalHandle cond, int use_cond) {
-  const int m = __ldcg(&bs->m);
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const double xim = __ldg(xi + m);
-  for (int s = blockIdx.x * kWarpsPerBlock + warp; s < total_strips; s += gridDim.x * kWarpsPerBlock) {
-    const int i = __ldg(strip_inst + s);
-    BatchInst* I = inst + i;
-    if (__ldcg(&I->done)) continue;
-    LoopArgs A;
-    A.nx = I->nx;
-    A.ny = I->ny;
-    const int kexp = __ldcg(&I->kscale), sig = __ldcg(&I->sig), dlt = __ldcg(&I->dlt);
-    const int ncs = A.nx / 128;
-    const int ls = s - I->first_strip;
-    const int col0 = (ls % ncs) * 128;
-    const int r0 = (ls / ncs) * H;
-    const int r1 = min(r0 + H, A.ny);
-    const double dm1d = __ldg(I->d + m + 1);
-    const dfv dm1 = df_from_double(dm1d * pow2(sig + dlt - kexp));
-    const dfv d0 = df_from_double(__ldg(I->d));
-    const double sw = pow2(-dlt);
-    const float swf = (float)sw;
-    const dfv wc = df_from_double((I->wc0 - xim) * sw);
-    const float wh[5] = {I->wf[0] * swf, I->wf[2] * swf, I->wf[4] * swf, I->wf[6] * swf, wc.h};
-    const float wl[5] = {I->wf[1] * swf, I->wf[3] * swf, I->wf[5] * swf, I->wf[7] * swf, wc.l};
-    float2* dst = (m & 1) ? I->yf1 : I->yf0;
-    dfv accy = {0.f, 0.f}, accp = {0.f, 0.f};
-    if (m == 0) {
-      df_strip_advdiff<4, double, true>(A, I->w, dst, I->pf, col0, r0, r1, wh, wl, d0, dm1, kexp, accy, accp);
-    } else {
-      const float2* src = ((m - 1) & 1) ? I->yf1 : I->yf0;
-      df_strip_advdiff<4, float2, false>(A, src, dst, I->pf, col0, r0, r1, wh, wl, d0, dm1, kexp, accy, accp);
-    }
-    batch_df_strip_done(I, i, s, m, dm1d, sig, dlt, kexp, df_to_double(accy), df_to_double(accp), bs, partials,
-                        tickets, cond, use_cond);
-  }
-  batch_df_launch_done(m, bs, block_ticket, cond, use_cond);
-}
-
-// Float-float batched iteration with the shared-memory-pipelined strip of the
-// single-problem kernel (cp.async ring of STAGES rows per warp): the same
-// strip table, per-instance reductions and stop tests as leja_batch_df_kernel.
-template <int MINB, int STAGES>
-__global__ void __launch_bounds__(kPipeThreads, MINB)
-    leja_batch_df_pipe_kernel(BatchInst* __restrict__ inst, const int* __restrict__ strip_inst,
-                              BatchState* __restrict__ bs, double* __restrict__ partials,
-                              unsigned int* __restrict__ tickets, unsigned int* __restrict__ block_ticket,
-                              const double* __restrict__ xi, int H, int total_strips, cudaGraphConditionalHandle cond,
-                              int use_cond) {
-  extern __shared__ __align__(16) unsigned long long bpipe_smem[];
-  const int m = __ldcg(&bs->m);
-  const int warp = threadIdx.x >> 5;
-  const double xim = __ldg(xi + m);
-  unsigned long long* ring = bpipe_smem + (size_t)warp * STAGES * kSlotElems;
-  for (int s = blockIdx.x * kPipeWarps + warp; s < total_strips; s += gridDim.x * kPipeWarps) {
-    const int i = __ldg(strip_inst + s);
-    BatchInst* I = inst + i;
-    if (__ldcg(&I->done)) continue;
-    LoopArgs A;
-    A.nx = I->nx;
-    A.ny = I->ny;
-    const int kexp = __ldcg(&I->kscale), sig = __ldcg(&I->sig), dlt = __ldcg(&I->dlt);
-    const int ncs = A.nx / 128;
-    const int ls = s - I->first_strip;
-    const int col0 = (ls % ncs) * 128;
-    const int r0 = (ls / ncs) * H;
-    const int r1 = min(r0 + H, A.ny);
-    const double dm1d = __ldg(I->d + m + 1);
-    const dfv dm1 = df_from_double(dm1d * pow2(sig + dlt - kexp));
-    const dfv d0 = df_from_double(__ldg(I->d));
-    const double sw = pow2(-dlt);
-    const float swf = (float)sw;
-    const dfv wc = df_from_double((I->wc0 - xim) * sw);
-    const float wh[5] = {I->wf[0] * swf, I->wf[2] * swf, I->wf[4] * swf, I->wf[6] * swf, wc.h};
-    const float wl[5] = {I->wf[1] * swf, I->wf[3] * swf, I->wf[5] * swf, I->wf[7] * swf, wc.l};
-    float2* dst = (m & 1) ? I->yf1 : I->yf0;
-    dfv accy = {0.f, 0.f}, accp = {0.f, 0.f};
-    if (m == 0) {
-      df_strip_pipe<STAGES, double, true>(A, I->w, dst, I->pf, ring, col0, r0, r1, wh, wl, d0, dm1, kexp, accy, accp);
-    } else {
-      const float2* src = ((m - 1) & 1) ? I->yf1 : I->yf0;
-      df_strip_pipe<STAGES, float2, false>(A, src, dst, I->pf, ring, col0, r0, r1, wh, wl, d0, dm1, kexp, accy,
-                                           accp);
-    }
-    batch_df_strip_done(I, i, s, m, dm1d, sig, dlt, kexp, df_to_double(accy), df_to_double(accp), bs, partials,
-                        tickets, cond, use_cond);
-  }
-  batch_df_launch_done(m, bs, block_ticket, cond, use_cond);
 }
 
 // Two Leja iterations per pass for the float-float batch (the two-step strip
