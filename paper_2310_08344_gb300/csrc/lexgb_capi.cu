@@ -227,6 +227,11 @@ std::vector<Cand> candidates(int kind, int precision, int cls) {
                        pipe2b_smem_bytes<5>(), 4, "leja_iter_df_pipe2_burgers_b1", 2});
       v.push_back(Cand{reinterpret_cast<const void*>(&leja_iter_df_pipe2_burgers_kernel<2, 5>), kPipeThreads,
                        pipe2b_smem_bytes<5>(), 4, "leja_iter_df_pipe2_burgers_b2", 2});
+      // more resident blocks with shorter rings (shared memory is the limit)
+      v.push_back(Cand{reinterpret_cast<const void*>(&leja_iter_df_pipe2_burgers_kernel<3, 4>), kPipeThreads,
+                       pipe2b_smem_bytes<4>(), 4, "leja_iter_df_pipe2_burgers_b3_s4", 2});
+      v.push_back(Cand{reinterpret_cast<const void*>(&leja_iter_df_pipe_burgers_kernel<4, 3>), kPipeThreads,
+                       kPipeWarps * 3 * kSlotElemsB * 8, 4, "leja_iter_df_pipe_burgers_b4_s3"});
     }
     return v;
   }

@@ -529,7 +529,8 @@ def test_adaptive_integration_matches_oracle(lx, xi_oracle):
 
 @pytest.mark.parametrize("name", ["leja_iter_df_pipe_burgers_b1", "leja_iter_df_pipe_burgers_b2",
                                   "leja_iter_df_pipe_burgers_b3_s4", "leja_iter_df_pipe2_burgers_b1",
-                                  "leja_iter_df_pipe2_burgers_b2"])
+                                  "leja_iter_df_pipe2_burgers_b2", "leja_iter_df_pipe2_burgers_b3_s4",
+                                  "leja_iter_df_pipe_burgers_b4_s3"])
 @pytest.mark.parametrize("strip_h", [0, 8, 32, 128])
 def test_df64_burgers_candidates_parity(lx, xi_oracle, name, strip_h):
     nx, ny, nu = 256, 100, 2e-2
