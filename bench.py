@@ -55,6 +55,7 @@ def parse():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-autotune", action="store_true")
     p.add_argument("--no-plain", action="store_true", help="skip the plain-form (native FP64) comparison")
+    p.add_argument("--tol", type=float, default=TOL, help="default workload: Leja tolerance (rtol = atol)")
     p.add_argument("--kernel", default=None, help="force a fused-iteration kernel (name) instead of autotuning")
     p.add_argument("--strip-h", type=int, default=8)
     p.add_argument("--unroll", type=int, default=None, help="fused-iteration launches per graph-loop pass")
@@ -820,7 +821,7 @@ def main():
             raise SystemExit("lx_ctx_set_source failed")
 
     def step(src, dst):
-        st, err, it = lx.expint_step(ctx, src, None, dst, c, g, h, TOL, TOL)
+        st, err, it = lx.expint_step(ctx, src, None, dst, c, g, h, args.tol, args.tol)
         if st != 0:
             raise SystemExit(f"expint_step failed: {lx.STATUS.get(st, st)}")
         return it
@@ -890,7 +891,7 @@ def main():
         pc, pn = torch.from_numpy(u0).cuda(), torch.empty_like(ua)
 
         def pstep(s_, d_):
-            st, err, it = lx.expint_step(ctxp, s_, None, d_, c, g, h, TOL, TOL)
+            st, err, it = lx.expint_step(ctxp, s_, None, d_, c, g, h, args.tol, args.tol)
             if st != 0:
                 raise SystemExit(f"plain expint_step failed: {lx.STATUS.get(st, st)}")
             return it
@@ -919,14 +920,14 @@ def main():
     if not args.no_e2e:
         hin = torch.from_numpy(cur.cpu().numpy()).pin_memory()
         hout = torch.empty_like(hin).pin_memory()
-        st, err, it = lx.expint_step_host(ctx, hin, None, hout, c, g, h, TOL, TOL)  # warm
+        st, err, it = lx.expint_step_host(ctx, hin, None, hout, c, g, h, args.tol, args.tol)  # warm
         if pg:
             pg.barrier()
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         tot_it = 0
         for _ in range(args.steps):
-            st, err, it = lx.expint_step_host(ctx, hin, None, hout, c, g, h, TOL, TOL)
+            st, err, it = lx.expint_step_host(ctx, hin, None, hout, c, g, h, args.tol, args.tol)
             if st != 0:
                 raise SystemExit(f"expint_step_host failed: {st}")
             tot_it += it
@@ -948,7 +949,7 @@ def main():
                 "data": "synthetic",
                 "config": {"workload": ("advdiff-4096x4096-rosenbrock-euler" if n == 4096 else f"advdiff-{n}x{n}")
                            + ("-source" if args.source else ""),
-                           "nx": n, "ny": n, "nu": NU, "a": ADV, "h_over_dt_cfl": CFL_MULT, "tol": TOL,
+                           "nx": n, "ny": n, "nu": NU, "a": ADV, "h_over_dt_cfl": CFL_MULT, "tol": args.tol,
                            "precision": args.precision, "integrator": "ros_eu", "parallelism": f"replicas{world}",
                            "leja_iters_per_step": iters, "rho": rho,
                            "kernel_selected": (tune or {}).get("selected", {"kernel": kname}),

@@ -329,9 +329,12 @@ int lx_ctx_iters_per_launch(lx_ctx* ctx);
 /* ---------------------------------------------------------------------------
  * Batched instances.  Not in the paper: many independent problems of uneven
  * grid sizes advance through the Leja loop together -- one fused launch per
- * iteration covers every instance that has not converged, each instance has
- * its own coefficients, weights, stopping test and status, and one CUDA
- * graph runs the whole loop.
+ * iteration (LX_FP64) or per two iterations (LX_DF64, with the stopping
+ * test after each) covers every instance that has not converged, each
+ * instance has its own coefficients, weights, stopping test and status, and
+ * one CUDA graph runs the whole loop (with LEXGB_STREAM_LOOP=1 in the
+ * environment at setup, the host launches the same kernel instead, for
+ * profilers that cannot see kernels inside a conditional graph).
  * ------------------------------------------------------------------------- */
 
 typedef struct lx_batch lx_batch;

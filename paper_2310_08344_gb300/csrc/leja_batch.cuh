@@ -61,6 +61,7 @@ __global__ void __launch_bounds__(kThreadsPerBlock)
                       unsigned int* __restrict__ block_ticket, const double* __restrict__ xi, int H,
                       int total_strips, cudaGraphConditionalHandle cond, int use_cond) {
   const int m = __ldcg(&bs->m);
+  if (m >= bs->mmax) return;  // host-driven launches past the end of the loop
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const double xim = __ldg(xi + m);
   for (int s = blockIdx.x * kWarpsPerBlock + warp; s < total_strips; s += gridDim.x * kWarpsPerBlock) {
@@ -215,6 +216,7 @@ __global__ void __launch_bounds__(kPipeThreads, MINB)
                                cudaGraphConditionalHandle cond, int use_cond) {
   extern __shared__ __align__(16) unsigned long long bpipe2_smem[];
   const int m = __ldcg(&bs->m);
+  if (m >= bs->mmax) return;  // host-driven launches past the end of the loop
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const double xa = __ldg(xi + m), xb = __ldg(xi + m + 1);
   unsigned long long* ring = bpipe2_smem + (size_t)warp * STAGES * kSlotElems2;

@@ -1547,6 +1547,11 @@ struct lx_batch {
   BatchInst* d_inst = nullptr;
   BatchInst* h_inst = nullptr;  // pinned
   BatchState* d_bs = nullptr;
+  // host-driven loop (profilers cannot see kernels inside a conditional
+  // graph): the loop kernel and its launch shape per vector class
+  int stream_loop = 0;
+  const void* loop_fn[2] = {nullptr, nullptr};
+  int loop_grid[2] = {0, 0}, loop_threads[2] = {0, 0}, loop_smem[2] = {0, 0};
   unsigned int* d_tickets = nullptr;
   unsigned int* d_block_ticket = nullptr;
   double* d_partials = nullptr;
@@ -1620,6 +1625,10 @@ lx_status build_batch_graph(lx_batch* b, int v) {
                    (void*)&xi, (void*)&H, (void*)&total, (void*)&cond, (void*)&use_cond};
   cudaKernelNodeParams kp;
   std::memset(&kp, 0, sizeof(kp));
+  b->loop_fn[v] = fn;
+  b->loop_grid[v] = grid;
+  b->loop_threads[v] = threads;
+  b->loop_smem[v] = smem;
   kp.func = const_cast<void*>(fn);
   kp.gridDim = dim3(grid);
   kp.blockDim = dim3(threads);
@@ -1671,6 +1680,10 @@ lx_status batch_setup(int count, const lx_problem* probs, int max_leja, void* cu
       return LX_E_INVAL;
   lx_batch* b = new lx_batch();
   b->df = df;
+  {
+    const char* env = std::getenv("LEXGB_STREAM_LOOP");
+    b->stream_loop = (env && env[0] == '1') ? 1 : 0;
+  }
   auto fail = [&](lx_status s) {
     batch_destroy(b);
     return s;
@@ -1815,7 +1828,32 @@ lx_status batch_step(lx_batch* b, int l, const double* const* w, double* const* 
     LX_CUDA(cudaGetLastError());
   }
   LX_CUDA(cudaEventRecord(b->ev[0], b->stream));
-  LX_CUDA(cudaGraphLaunch(b->exec[v], b->stream));
+  if (!b->stream_loop) {
+    LX_CUDA(cudaGraphLaunch(b->exec[v], b->stream));
+  } else {
+    // the same kernel launched from the host in batches of 8 (launches past
+    // the end return at once)
+    BatchInst* inst = b->d_inst;
+    const int* strip_inst = b->d_strip_inst[v];
+    BatchState* bs = b->d_bs;
+    double* partials = b->d_partials;
+    unsigned int* tickets = b->d_tickets;
+    unsigned int* bt = b->d_block_ticket;
+    const double* xi = b->d_xi;
+    int H = b->H, total = b->total_strips[v], use_cond = 0;
+    cudaGraphConditionalHandle cond = 0;
+    void* kargs[] = {(void*)&inst, (void*)&strip_inst, (void*)&bs, (void*)&partials, (void*)&tickets, (void*)&bt,
+                     (void*)&xi, (void*)&H, (void*)&total, (void*)&cond, (void*)&use_cond};
+    for (int it = 0; it < mmax; it += 8) {
+      for (int q = 0; q < 8; ++q)
+        LX_CUDA(cudaLaunchKernel(b->loop_fn[v], dim3(b->loop_grid[v]), dim3(b->loop_threads[v]), kargs,
+                                 (size_t)b->loop_smem[v], b->stream));
+      BatchState hs0;
+      LX_CUDA(cudaMemcpyAsync(&hs0, b->d_bs, sizeof(BatchState), cudaMemcpyDeviceToHost, b->stream));
+      LX_CUDA(cudaStreamSynchronize(b->stream));
+      if (hs0.active <= 0 || hs0.m >= mmax) break;
+    }
+  }
   LX_CUDA(cudaEventRecord(b->ev[1], b->stream));
   if (b->df) {
     batch_df_output_kernel<<<b->grid[v], kThreadsPerBlock, 0, b->stream>>>(b->d_inst, b->d_strip_inst[v], b->H,
