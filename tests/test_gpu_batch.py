@@ -125,3 +125,32 @@ def test_batch_float_float_matches_oracle(lx):
 
     with pytest.raises(LexgbError):
         lx.batch_setup([(96, 96, 1e-2, 0.5)], precision=lx.DF64)  # nx % 128 != 0
+
+
+def test_batch_host_loop_matches_graph(lx, monkeypatch):
+    # the host-driven loop (for profilers) launches the same kernel as the
+    # graph's while loop: identical results and iteration counts
+    sizes = [(128, 128), (256, 64), (128, 37)]
+    inst = _instances(sizes, seed=13)
+    ws, cs, gs, hs = [], [], [], []
+    for (nx, ny, nu, a, s) in inst:
+        ws.append(torch.from_numpy(synth.gaussians_ic(nx, ny, seed=s)).cuda())
+        hs.append(50 * synth.cfl_step(nx, ny, nu, a))
+        c, g = oracle.spectral_interval(max(_symbol_radius(nx, ny, nu, a), 1.0))
+        cs.append(c)
+        gs.append(g)
+    res = {}
+    for mode in ("0", "1"):
+        monkeypatch.setenv("LEXGB_STREAM_LOOP", mode)
+        for prec in (lx.FP64, lx.DF64):
+            b = lx.batch_setup([(nx, ny, nu, a) for (nx, ny, nu, a, _) in inst], precision=prec)
+            outs = [torch.empty(nx * ny, dtype=torch.float64, device="cuda") for (nx, ny, _, _, _) in inst]
+            st, its, sts = lx.batch_step(b, 1, ws, outs, cs, gs, hs, TOL, 0.0)
+            assert st == 0
+            res[(mode, prec)] = (list(its), [o.cpu().numpy() for o in outs])
+    for prec in (lx.FP64, lx.DF64):
+        a_its, a_out = res[("0", prec)]
+        b_its, b_out = res[("1", prec)]
+        assert a_its == b_its
+        for x, y in zip(a_out, b_out):
+            assert np.array_equal(x, y)
