@@ -63,7 +63,7 @@ def parse():
                    help="diffusion-advection with a time-independent source S (u' = A u + S)")
     p.add_argument("--workload", default="advdiff4096",
                    choices=["advdiff4096", "batch256", "burgers2048", "vertical4096", "paper1", "paper2",
-                            "paper3", "rhs4096"])
+                            "paper3", "rhs4096", "learned2048"])
     p.add_argument("--cfl", type=float, default=100.0, help="paper workloads: step size in units of dt_CFL")
     p.add_argument("--tf", type=float, default=None,
                    help="paper workloads: integrate to this final time and report the end-to-end time")
@@ -689,6 +689,84 @@ def run_rhs(args, rank, world, local):
     return 0
 
 
+def run_learned(args, rank, world, local):
+    """The learned step-size controller on the scope's test: trained on
+    Burgers trajectories at 96^2 (nu = 2e-2, tol 1e-4, thirteen candidate
+    steps per state) with the library's tensor-core kernels, then applied to
+    Burgers at n^2 (default 2048^2, nu = 5e-3) adaptive to T = 200 dt_CFL,
+    against the classical controller from the same first step; the embedded
+    error test accepts or rejects every step in both runs.  Reported: Leja
+    iterations, steps, rejections, wall time and the error of the final state
+    against a tight-tolerance run."""
+    import torch
+
+    import paper_2310_08344_gb300 as lx
+    from paper_2310_08344_gb300 import learned
+
+    torch.cuda.set_device(local)
+    stream = torch.cuda.current_stream()
+    tol, leja_tol = 1e-4, 1e-10
+    # training at 96^2
+    nt, nut = 96, 2e-2
+    rng = np.random.default_rng(11)
+    v0t = torch.from_numpy(synth.power_start(nt * nt, seed=5)).cuda()
+    ics = [torch.from_numpy(synth.burgers_ic(nt, nt, seed=100 + k)).cuda() for k in range(24)]
+    dtt = synth.cfl_step(nt, nt, nut, 1.0)
+    t0 = time.perf_counter()
+    X, Y = learned.generate_samples(nt, nut, ics, v0t, tol, leja_tol, 40, dtt, rng)
+    t_gen = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    model, norm, losses = learned.train(X, Y, epochs=300, batch=256, lr=2e-3, seed=0)
+    t_train = time.perf_counter() - t0
+    # the test at n^2
+    n = args.n if args.n != NX else 2048
+    nu = 5e-3
+    N = n * n
+    dt = synth.cfl_step(n, n, nu, 1.0)
+    T = 200 * dt
+    u0 = synth.burgers_ic(n, n, seed=12)
+    v0 = torch.from_numpy(synth.power_start(N, seed=5)).cuda()
+    prec = {"fp64": lx.FP64, "mixed": lx.MIXED, "df64": lx.DF64}[args.precision]
+    ctx = lx.leja_setup(n, n, nu, 0.0, lx.BURGERS, prec, lx.EXPRB32, 1000, stream)
+    ref = torch.from_numpy(u0).cuda()
+    st, info_ref = lx.lx_integrate(ctx, ref, v0, T, 1e-9, leja_tol, 100000, 0.0, 3 * dt, 10)
+    if st != 0:
+        raise SystemExit(f"reference run failed: {st}")
+    runs = {}
+    h0 = 10 * dt
+    for name in ("classical", "learned", "classical", "learned"):  # the second pair is timed warm
+        u = torch.from_numpy(u0).cuda()
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
+        if name == "classical":
+            st, info = lx.lx_integrate(ctx, u, v0, T, tol, leja_tol, 100000, 0.0, h0, 10)
+        else:
+            st, info = lx.lx_integrate_learned(ctx, u, v0, T, tol, leja_tol, model, dt, 100000, 0.0, h0, 10)
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - t1
+        if st != 0:
+            raise SystemExit(f"{name} run failed: {st}")
+        err = float((u - ref).norm().item() / ref.norm().item())
+        runs[name] = {"leja_iters": info["leja_iters"], "steps": info["steps"], "rejected": info["rejected"],
+                      "wall_ms": wall * 1e3, "rel_err_vs_tight": err}
+    c, l = runs["classical"], runs["learned"]
+    gain = c["leja_iters"] / max(l["leja_iters"], 1)
+    line = {"metric": "Leja iterations to T, classical / learned controller", "value": gain, "unit": "ratio",
+            "n_gpus": world, "steps": 1, "warmup": 1, "ms_per_step": l["wall_ms"], "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None,
+            "dtype": {"fp64": "f64", "mixed": "f32+f64", "df64": "f32x2 (float-float, FP64-accurate)"}[args.precision],
+            "data": "synthetic",
+            "config": {"workload": f"learned-controller-burgers-{n}x{n}", "nu": nu, "t_final_over_dt_cfl": 200,
+                       "tol": tol, "leja_tol": leja_tol, "first_step_over_dt_cfl": 10,
+                       "training": {"grid": nt, "nu": nut, "samples": int(X.shape[0]), "generate_s": t_gen,
+                                    "train_s": t_train, "final_loss": float(losses[-1])}},
+            "runs": runs, "wall_gain": c["wall_ms"] / l["wall_ms"]}
+    if rank == 0:
+        print(json.dumps(line))
+    ctx.close()
+    return 0
+
+
 def run_burgers(args, rank, world, local):
     """Viscous Burgers 2048^2, nu = 5e-3, EXPRB32 steps of h = 50 dt_CFL with
     a power-iteration bound before every step; FP64 and mixed forms, and the
@@ -774,6 +852,8 @@ def main():
         return run_vertical(args, rank, world, local)
     if args.workload == "rhs4096":
         return run_rhs(args, rank, world, local)
+    if args.workload == "learned2048":
+        return run_learned(args, rank, world, local)
     if args.workload in ("paper1", "paper2", "paper3"):
         return run_paper(args, rank, world, local)
     import torch
