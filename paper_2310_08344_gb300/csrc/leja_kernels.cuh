@@ -107,6 +107,20 @@ __device__ __forceinline__ void count_launch(LoopState* st) {
 __device__ __forceinline__ int wrap_up(int i, int n) { return i + 1 == n ? 0 : i + 1; }
 __device__ __forceinline__ int wrap_dn(int i, int n) { return i == 0 ? n - 1 : i - 1; }
 
+// float -> double without the conversion unit (which issues at the FP64
+// rate on GB300): for a normal float the double's bits are its sign, its
+// exponent rebiased by 1023 - 127 and its 23 mantissa bits; zeros,
+// subnormals, infinities and NaNs take the ordinary conversion.  Exact.
+__device__ __forceinline__ double f2d_int(float f) {
+  const unsigned b = __float_as_uint(f);
+  const unsigned e = (b >> 23) & 0xffu;
+  if (e == 0u || e == 0xffu) return (double)f;
+  const unsigned hi = (b & 0x80000000u) | ((e + 896u) << 20) | ((b & 0x7fffffu) >> 3);
+  return __hiloint2double((int)hi, (int)(b << 29));
+}
+__device__ __forceinline__ double to_double(float f) { return f2d_int(f); }
+__device__ __forceinline__ double to_double(double d) { return d; }
+
 template <typename S, int VEC>
 __device__ __forceinline__ void load_vec(const S* __restrict__ row, int c, int nx, S (&v)[VEC]) {
   if constexpr (VEC == 2) {
@@ -215,7 +229,7 @@ __device__ __forceinline__ void leja_strip(const LoopArgs& A, const S* __restric
         v = fma(-T(uu[k]), gxy, v);
       }
       ynew[k] = v;
-      const double vd = double(v);
+      const double vd = to_double(v);
       const double po = FIRST ? d0 * double(yc[k]) : pold[k];
       pnew[k] = fma(dm1, vd, po);
       if (active) {

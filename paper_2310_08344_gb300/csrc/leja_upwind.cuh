@@ -123,7 +123,7 @@ static __global__ void __launch_bounds__(kThreadsPerBlock)
     }
     v = ig * v + cs * yc;
     dst[q] = v;
-    const double vd = double(v);
+    const double vd = to_double(v);
     const double po = m == 0 ? d0 * double(yc) : A.p[q];
     const double pn = fma(dm1, vd, po);
     A.p[q] = pn;

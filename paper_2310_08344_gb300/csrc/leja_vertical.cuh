@@ -123,7 +123,7 @@ __device__ __forceinline__ void leja_strip_vertical(const LoopArgs& A, const Ver
         v = fma(-T(uu[k]), gxy, v);
       }
       ynew[k] = v;
-      const double vd = double(v);
+      const double vd = to_double(v);
       if (active) sy = fma(vd, vd, sy);
 #pragma unroll
       for (int j = 0; j < NP; ++j) {
@@ -410,7 +410,7 @@ static __global__ void __launch_bounds__(kThreadsPerBlock)
     }
     v = ig * v + cs * yc;
     dst[q] = v;
-    const double vd = double(v);
+    const double vd = to_double(v);
     sy = fma(vd, vd, sy);
 #pragma unroll
     for (int k = 0; k < NP; ++k) {
