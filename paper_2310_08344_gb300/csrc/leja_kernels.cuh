@@ -71,6 +71,9 @@ struct LoopArgs {
   // upwind operators: constants and the shift c of the spectral interval
   Up3Op up;
   double up_c;
+  // mixed Burgers form: u and u_x + u_y as floats (converted once per loop)
+  const float* uf;
+  const float* sf;
 };
 
 // Device-resident loop and reduction state.
@@ -199,12 +202,17 @@ __device__ __forceinline__ void leja_strip(const LoopArgs& A, const S* __restric
     if (need_e) xe = __ldg(src + ro + ce);
     double pold[VEC];
     if constexpr (!FIRST) load_p<VEC>(p + ro, c, nx, pold);
-    double uu[VEC], ss[VEC];
+    T uu[VEC], ss[VEC];
     if constexpr (KIND == 1) {
 #pragma unroll
       for (int k = 0; k < VEC; ++k) {
-        uu[k] = active ? __ldg(A.u + ro + c + k) : 0.0;
-        ss[k] = active ? __ldg(A.s + ro + c + k) : 0.0;
+        if constexpr (std::is_same<T, float>::value) {
+          uu[k] = active ? __ldg(A.uf + ro + c + k) : 0.f;
+          ss[k] = active ? __ldg(A.sf + ro + c + k) : 0.f;
+        } else {
+          uu[k] = active ? __ldg(A.u + ro + c + k) : 0.0;
+          ss[k] = active ? __ldg(A.s + ro + c + k) : 0.0;
+        }
       }
     }
     T ynew[VEC];
@@ -435,6 +443,12 @@ __global__ void rhs_kernel(Geo g, double nu, double a, double h, const double* _
       s_out[q] = grad;
     }
   }
+}
+
+// Float copy of a double vector (the mixed Burgers form's u and u_x + u_y).
+static __global__ void to_float_kernel(long long n, const double* __restrict__ x, float* __restrict__ y) {
+  for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < n; q += (long long)gridDim.x * blockDim.x)
+    y[q] = (float)x[q];
 }
 
 // out = x + y (in place allowed on y).

@@ -93,12 +93,17 @@ __device__ __forceinline__ void leja_strip_vertical(const LoopArgs& A, const Ver
 #pragma unroll
     for (int j = 0; j < NP; ++j)
       if constexpr (!FIRST) load_p<VEC>(V.p[j] + ro, c, nx, pold[j]);
-    double uu[VEC], ss[VEC];
+    T uu[VEC], ss[VEC];
     if constexpr (KIND == 1) {
 #pragma unroll
       for (int k = 0; k < VEC; ++k) {
-        uu[k] = active ? __ldg(A.u + ro + c + k) : 0.0;
-        ss[k] = active ? __ldg(A.s + ro + c + k) : 0.0;
+        if constexpr (std::is_same<T, float>::value) {
+          uu[k] = active ? __ldg(A.uf + ro + c + k) : 0.f;
+          ss[k] = active ? __ldg(A.sf + ro + c + k) : 0.f;
+        } else {
+          uu[k] = active ? __ldg(A.u + ro + c + k) : 0.0;
+          ss[k] = active ? __ldg(A.s + ro + c + k) : 0.0;
+        }
       }
     }
     T ynew[VEC];

@@ -116,6 +116,8 @@ struct lx_ctx {
   double* d_tune = nullptr; // autotuner: output vector of the timing runs
   float2* d_bq = nullptr;   // df64 Burgers: u / (2 dx gamma) per point
   float2* d_br = nullptr;   // df64 Burgers: diagonal weight per point
+  float* d_uf = nullptr;    // mixed Burgers: u as floats
+  float* d_sf = nullptr;    // mixed Burgers: u_x + u_y as floats
   const double* d_src = nullptr;  // caller's time-independent source (borrowed), or NULL
   double* d_partials = nullptr;
   int partials_cap = 0;
@@ -474,6 +476,15 @@ lx_status prepare_loop(lx_ctx* c, int strip_h, int kmax, const double* d, const 
   a.up = c->up3;
   a.up_c = cc;
   if (is_up3(P.kind)) a.inv_gamma = ig;
+  if (P.precision == LX_MIXED && P.kind == LX_BURGERS) {
+    // the mixed form's float copies of u and u_x + u_y, once per loop
+    a.uf = c->d_uf;
+    a.sf = c->d_sf;
+    to_float_kernel<<<aux_blocks(c), kThreadsPerBlock, 0, c->stream>>>(c->n, u, c->d_uf);
+    to_float_kernel<<<aux_blocks(c), kThreadsPerBlock, 0, c->stream>>>(c->n, c->d_s, c->d_sf);
+    c->stats.kernels += 2;
+    LX_CUDA(cudaGetLastError());
+  }
   if (P.precision == LX_DF64 && P.kind == LX_BURGERS_UP3) {
     // q = u |a| / (6 dx gamma) as float pairs for the point weights
     a.bq = c->d_bq;
@@ -656,6 +667,8 @@ void leja_destroy(lx_ctx* c) {
   cudaFree(c->d_y[1]);
   cudaFree(c->d_f);
   cudaFree(c->d_s);
+  cudaFree(c->d_uf);
+  cudaFree(c->d_sf);
   cudaFree(c->d_p3);
   cudaFree(c->d_pw[0]);
   cudaFree(c->d_pw[1]);
@@ -718,6 +731,10 @@ lx_status leja_setup(const lx_problem* prob, int integrator, int max_leja, void*
   if (!dmalloc((void**)&c->d_f, nb) || !dmalloc((void**)&c->d_s, nb)) return fail(LX_E_NOMEM);
   if (integrator == LX_EXPRB32 && !dmalloc((void**)&c->d_p3, nb)) return fail(LX_E_NOMEM);
   if (prob->precision == LX_DF64 && !dmalloc((void**)&c->d_pdf, sizeof(float2) * (size_t)c->n))
+    return fail(LX_E_NOMEM);
+  if (prob->precision == LX_MIXED && prob->kind == LX_BURGERS &&
+      (!dmalloc((void**)&c->d_uf, sizeof(float) * (size_t)c->n) ||
+       !dmalloc((void**)&c->d_sf, sizeof(float) * (size_t)c->n)))
     return fail(LX_E_NOMEM);
   if (prob->precision == LX_DF64 && (prob->kind == LX_BURGERS || prob->kind == LX_BURGERS_UP3) &&
       (!dmalloc((void**)&c->d_bq, sizeof(float2) * (size_t)c->n) ||
@@ -1291,6 +1308,8 @@ lx_status tune_time(lx_ctx* c, const Cand& k, int H, int iters, double* us) {
   a.p = c->d_tune;
   a.u = c->d_f;
   a.s = c->d_s;
+  a.uf = c->d_uf;  // (mixed Burgers; zeroed with the other buffers)
+  a.sf = c->d_sf;
   a.xi = c->d_xi;
   a.d = c->coef[0].dev;
   a.up = c->up3;
@@ -1379,6 +1398,8 @@ lx_status lx_ctx_autotune(lx_ctx* c, int iters, const char* cache_path, char* re
   if (c->d_pdf) LX_CUDA(cudaMemsetAsync(c->d_pdf, 0, sizeof(float2) * (size_t)c->n, c->stream));
   if (c->d_bq) LX_CUDA(cudaMemsetAsync(c->d_bq, 0, sizeof(float2) * (size_t)c->n, c->stream));
   if (c->d_br) LX_CUDA(cudaMemsetAsync(c->d_br, 0, sizeof(float2) * (size_t)c->n, c->stream));
+  if (c->d_uf) LX_CUDA(cudaMemsetAsync(c->d_uf, 0, sizeof(float) * (size_t)c->n, c->stream));
+  if (c->d_sf) LX_CUDA(cudaMemsetAsync(c->d_sf, 0, sizeof(float) * (size_t)c->n, c->stream));
   lx_status st = ensure_coeffs(c, 0, 0, 1.0, -20.0, 10.0);
   if (st != LX_OK) return st;
   if (c->coef[0].count < 2 * iters + 4) return LX_E_INVAL;
