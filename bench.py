@@ -226,9 +226,10 @@ def run_reference(args, rank, world):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3 / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic",
-            "config": {"workload": "advdiff-periodic-rosenbrock-euler", "nx": n_sample, "ny": n_sample, "nu": NU,
+            "config": {"workload": "advdiff-4096x4096-rosenbrock-euler", "nx": NX, "ny": NX, "nu": NU,
                        "a": ADV, "h_over_dt_cfl": CFL_MULT, "tol": TOL,
-                       "note": "the CPU oracle on a bounded 1024^2 sample of the 4096^2 workload"},
+                       "sample": f"each step a bounded sample: the same recipe at {n_sample}x{n_sample}",
+                       "note": "the CPU oracle, as it stands, on the host cores (single-threaded)"},
             "cpu_baseline": {"value": val, "unit": UNIT, "cores": 1, "kind": "oracle",
                              "sample": f"{args.steps} Ros-Eu steps at {n_sample}x{n_sample}, single-threaded"},
             "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
