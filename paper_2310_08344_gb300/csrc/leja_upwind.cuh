@@ -246,6 +246,59 @@ static __global__ void __launch_bounds__(kThreadsPerBlock)
   }
 }
 
+// h (A u + S) for the upwind diffusion-advection operator on the FP32 pipe:
+// float-float Dot2 over the seven points with the weights h w_k, rounded to
+// double, plus h S in double; records the largest exponent of the result for
+// the Leja loop's input scaling.  Points whose neighbours lie outside the
+// float-float range (|u| beyond 2^+-100) take the FP64 formula.
+static __global__ void __launch_bounds__(kThreadsPerBlock)
+    rhs_df_up3_kernel(Up3Op o, double h, const double* __restrict__ u, const double* __restrict__ src,
+                      double* __restrict__ f_out, LoopState* st) {
+  double wd[7];
+  up3_weights(o, wd);
+  float wh[7], wl[7];
+#pragma unroll
+  for (int k = 0; k < 7; ++k) {
+    wd[k] *= h;
+    const dfv t = df_from_double(wd[k]);
+    wh[k] = t.h;
+    wl[k] = t.l;
+  }
+  int emax = 0;
+  for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < o.n; q += (long long)gridDim.x * blockDim.x) {
+    int i, j;
+    up3_ij(o, q, i, j);
+    long long pts[7];
+    up3_points(o, i, j, pts);
+    double v[7];
+    bool in_range = true;
+#pragma unroll
+    for (int k = 0; k < 7; ++k) {
+      v[k] = __ldg(u + pts[k]);
+      const int ex = (int)((__double_as_longlong(v[k]) >> 52) & 0x7ff);
+      in_range = in_range && (ex == 0 || (ex > 1023 - 100 && ex < 1023 + 100));
+    }
+    double r;
+    if (in_range) {
+      dfv t[7];
+#pragma unroll
+      for (int k = 0; k < 7; ++k) t[k] = df_split_scaled(v[k], 0);
+      const dfv d = df_dot7(wh, wl, t);
+      r = f2d_scaled(d.h, 0) + f2d_scaled(d.l, 0);
+    } else {
+      r = 0.0;
+#pragma unroll
+      for (int k = 0; k < 7; ++k) r = fma(wd[k], v[k], r);
+    }
+    if (src) r = r + h * __ldg(src + q);
+    f_out[q] = r;
+    emax = max(emax, (int)((__double2hiint(r) >> 20) & 0x7ff));
+  }
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) emax = max(emax, __shfl_xor_sync(0xffffffffu, emax, off));
+  if ((threadIdx.x & 31) == 0) atomicMax(&st->wexp, emax);
+}
+
 // EXPRB32 remainder for the upwind Burgers operator: with p1 = a - u,
 // F(a) - F(u) = (a/2) D(p1^2) exactly (quadratic flux), so R = h (a/2) D(p1^2);
 // R = 0 for the linear operator.

@@ -1156,6 +1156,20 @@ lx_status expint_step(lx_ctx* c, const double* u, double* u_low, double* u_high,
     if (iters) *iters = c->h_state->iters_total;
     return (lx_status)c->h_state->status_total;
   }
+  if (P.precision == LX_DF64 && P.kind == LX_ADVDIFF_UP3 && c->integrator == LX_ROS_EU) {
+    // the same for the upwind operator: h (A u + S) on the FP32 pipe, the
+    // Leja loop, and u + p in the loop's output pass
+    rhs_df_up3_kernel<<<G, kThreadsPerBlock, 0, c->stream>>>(c->up3, h, u, c->d_src, c->d_f, c->d_state);
+    ++c->stats.kernels;
+    LX_CUDA(cudaGetLastError());
+    st = launch_loop(c, 0, 1, u, c->d_f, u_high, cc, gamma, h, rtol, atol, u, true);
+    if (st != LX_OK) return st;
+    st = end_call(c);
+    if (st != LX_OK) return st;
+    if (err) *err = 0.0;
+    if (iters) *iters = c->h_state->iters_total;
+    return (lx_status)c->h_state->status_total;
+  }
   // h f(u) and, for Burgers, u_x + u_y at the linearisation point
   if (P.kind == LX_ADVDIFF)
     rhs_kernel<0><<<G, kThreadsPerBlock, 0, c->stream>>>(c->geo, P.nu, P.a, h, u, c->d_f, c->d_s, c->d_src);

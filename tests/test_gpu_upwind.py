@@ -283,3 +283,26 @@ def test_full_size_problem3_properties(lx):
     assert rel(hi, res["FP64"][1]) <= 1e-10 and rel(lo, res["FP64"][0]) <= 1e-10
     assert abs(it - res["FP64"][3]) <= 2 and abs(err - res["FP64"][2]) <= 1e-6 * res["FP64"][2] + 1e-15
     print(f"Problem III 4096^2: iters {it}, err {err:.3e}, df64 vs FP64 {rel(hi, res['FP64'][1]):.2e}")
+
+
+@pytest.mark.parametrize("scale", [1.0, 1e100, 1e-100])
+@pytest.mark.parametrize("source", [False, True])
+def test_df64_ros_eu_up3_rhs_forms(lx, xi_oracle, scale, source):
+    # the float-float right-hand side of the upwind Rosenbrock-Euler step
+    # (values beyond the float-float range take the FP64 formula; the loop
+    # input is scaled by a power of two) against the oracle, on grids with a
+    # ragged row count and two column strips
+    nx, ny = 256, 72
+    u = synth.problem1_ic(nx, ny, seed=19) * scale
+    S = synth.problem2_source(nx, ny) * scale if source else None
+    h = 50 * synth.cfl_step_pm1(nx, ny, NU, A)
+    c, g = _interval(2, nx, ny, A, None)
+    ctx = lx.leja_setup(nx, ny, NU, A, lx.ADVDIFF_UP3, lx.DF64, lx.ROS_EU)
+    if source:
+        Sd = dev(S)
+        assert lx.lx_ctx_set_source(ctx, Sd) == 0
+    hi = torch.empty(nx * ny, dtype=torch.float64, device="cuda")
+    st, err, it = lx.expint_step(ctx, dev(u), None, hi, c, g, h, TOL, TOL * scale)
+    ref, it_o, st_o = oracle.ros_eu(2, nx, ny, NU, A, u, c, g, h, TOL, TOL * scale, xi_oracle, source=S)
+    assert st == 0 and st_o == 0 and abs(it - it_o) <= 1
+    assert rel(hi.cpu().numpy(), ref) <= TOL
