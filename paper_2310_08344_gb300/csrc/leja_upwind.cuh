@@ -1242,4 +1242,80 @@ __global__ void __launch_bounds__(kPipeThreads, MINB)
   if (threadIdx.x == 0) power_pass_finish(st, s, o.n);
 }
 
+// The quadratic upwind Burgers parts on the FP32 pipe (float-float, one
+// thread per point): RHS = true gives h (nu lap u + (a/2) D(u^2) + S) (the
+// step's right-hand side, recording the largest exponent of the result for
+// the Leja loop's input scaling), RHS = false the EXPRB32 remainder
+// h (a/2) D(p1^2).  The squares are float-float products.  A point takes the
+// FP64 formula when a neighbour lies outside [2^-50, 2^e) (e <= 50, chosen so
+// that weight times square stays below 2^118 in float), zero excepted.
+template <bool RHS>
+static __global__ void __launch_bounds__(kThreadsPerBlock)
+    burgers_up3_df_kernel(Up3Op o, double h, const double* __restrict__ x, const double* __restrict__ src,
+                          double* __restrict__ out, LoopState* st) {
+  // weights of [x_C, x_X(-s), x_X(s), x_Y(-s), x_Y(s)] (RHS) and of the squares
+  // at [C, X(-s), X(s), X(2s), Y(-s), Y(s), Y(2s)]
+  const double hx = 0.5 * h * o.gx, hy = 0.5 * h * o.gy;
+  const double wd[12] = {RHS ? h * (-2.0 * o.cxx - 2.0 * o.cyy) : 0.0, RHS ? h * o.cxx : 0.0, RHS ? h * o.cxx : 0.0,
+                         RHS ? h * o.cyy : 0.0, RHS ? h * o.cyy : 0.0, kUp3K0 * (hx + hy), kUp3Km * hx,
+                         kUp3K1 * hx, kUp3K2 * hx, kUp3Km * hy, kUp3K1 * hy, kUp3K2 * hy};
+  float wh[12], wl[12];
+#pragma unroll
+  for (int k = 0; k < 12; ++k) {
+    const dfv t = df_from_double(wd[k]);
+    wh[k] = t.h;
+    wl[k] = t.l;
+  }
+  double wmax = 0.0;
+#pragma unroll
+  for (int k = 0; k < 12; ++k) wmax = fmax(wmax, fabs(wd[k]));
+  const int ew = (wmax > 0.0 && isfinite(wmax)) ? ilogb(wmax) : 0;
+  const int ehi = 1023 + min(50, (118 - ew) / 2);  // biased exponents below ehi qualify
+  int emax = 0;
+  for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < o.n; q += (long long)gridDim.x * blockDim.x) {
+    int i, j;
+    up3_ij(o, q, i, j);
+    long long pts[7];
+    up3_points(o, i, j, pts);
+    double v[7];
+    bool in_range = true;
+#pragma unroll
+    for (int k = 0; k < 7; ++k) {
+      v[k] = __ldg(x + pts[k]);
+      const int ex = (int)((__double_as_longlong(v[k]) >> 52) & 0x7ff);
+      in_range = in_range && (ex == 0 || (ex >= 1023 - 50 && ex < ehi));
+    }
+    double r;
+    if (in_range) {
+      dfv t[12];
+      dfv a[7];
+#pragma unroll
+      for (int k = 0; k < 7; ++k) a[k] = df_split_scaled(v[k], 0);
+      t[0] = a[0];
+      t[1] = a[1];
+      t[2] = a[2];
+      t[3] = a[4];
+      t[4] = a[5];
+#pragma unroll
+      for (int k = 0; k < 7; ++k) t[5 + k] = df_mul(a[k], a[k]);
+      const dfv d = df_dot_n<12>(wh, wl, t);
+      r = f2d_scaled(d.h, 0) + f2d_scaled(d.l, 0);
+    } else {
+      r = wd[0] * v[0] + wd[1] * v[1] + wd[2] * v[2] + wd[3] * v[4] + wd[4] * v[5];
+#pragma unroll
+      for (int k = 0; k < 7; ++k) r = fma(wd[5 + k], v[k] * v[k], r);
+    }
+    if constexpr (RHS) {
+      if (src) r = r + h * __ldg(src + q);
+      emax = max(emax, (int)((__double2hiint(r) >> 20) & 0x7ff));
+    }
+    out[q] = r;
+  }
+  if constexpr (RHS) {
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) emax = max(emax, __shfl_xor_sync(0xffffffffu, emax, off));
+    if ((threadIdx.x & 31) == 0) atomicMax(&st->wexp, emax);
+  }
+}
+
 }  // namespace lexgb

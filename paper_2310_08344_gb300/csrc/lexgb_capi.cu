@@ -1156,10 +1156,14 @@ lx_status expint_step(lx_ctx* c, const double* u, double* u_low, double* u_high,
     if (iters) *iters = c->h_state->iters_total;
     return (lx_status)c->h_state->status_total;
   }
-  if (P.precision == LX_DF64 && P.kind == LX_ADVDIFF_UP3 && c->integrator == LX_ROS_EU) {
-    // the same for the upwind operator: h (A u + S) on the FP32 pipe, the
+  const bool df_up3 = P.precision == LX_DF64 && is_up3(P.kind);
+  if (df_up3 && c->integrator == LX_ROS_EU) {
+    // the same for the upwind operators: h (f(u) + S) on the FP32 pipe, the
     // Leja loop, and u + p in the loop's output pass
-    rhs_df_up3_kernel<<<G, kThreadsPerBlock, 0, c->stream>>>(c->up3, h, u, c->d_src, c->d_f, c->d_state);
+    if (P.kind == LX_ADVDIFF_UP3)
+      rhs_df_up3_kernel<<<G, kThreadsPerBlock, 0, c->stream>>>(c->up3, h, u, c->d_src, c->d_f, c->d_state);
+    else
+      burgers_up3_df_kernel<true><<<G, kThreadsPerBlock, 0, c->stream>>>(c->up3, h, u, c->d_src, c->d_f, c->d_state);
     ++c->stats.kernels;
     LX_CUDA(cudaGetLastError());
     st = launch_loop(c, 0, 1, u, c->d_f, u_high, cc, gamma, h, rtol, atol, u, true);
@@ -1175,6 +1179,10 @@ lx_status expint_step(lx_ctx* c, const double* u, double* u_low, double* u_high,
     rhs_kernel<0><<<G, kThreadsPerBlock, 0, c->stream>>>(c->geo, P.nu, P.a, h, u, c->d_f, c->d_s, c->d_src);
   else if (P.kind == LX_BURGERS)
     rhs_kernel<1><<<G, kThreadsPerBlock, 0, c->stream>>>(c->geo, P.nu, 0.0, h, u, c->d_f, c->d_s, c->d_src);
+  else if (df_up3 && P.kind == LX_ADVDIFF_UP3)
+    rhs_df_up3_kernel<<<G, kThreadsPerBlock, 0, c->stream>>>(c->up3, h, u, c->d_src, c->d_f, c->d_state);
+  else if (df_up3)
+    burgers_up3_df_kernel<true><<<G, kThreadsPerBlock, 0, c->stream>>>(c->up3, h, u, c->d_src, c->d_f, c->d_state);
   else if (P.kind == LX_ADVDIFF_UP3)
     rhs_up3_kernel<false><<<G, kThreadsPerBlock, 0, c->stream>>>(c->up3, h, u, c->d_src, c->d_f);
   else
@@ -1192,14 +1200,18 @@ lx_status expint_step(lx_ctx* c, const double* u, double* u_low, double* u_high,
     if (st != LX_OK) return st;
     if (err) *err = 0.0;
   } else {
-    // p1 = phi_1(h J) h f(u) into u_low
-    st = launch_loop(c, 0, 1, u, c->d_f, u_low, cc, gamma, h, rtol, atol);
+    // p1 = phi_1(h J) h f(u) into u_low (the float-float upwind right-hand
+    // sides have recorded the input exponent)
+    st = launch_loop(c, 0, 1, u, c->d_f, u_low, cc, gamma, h, rtol, atol, nullptr, df_up3);
     if (st != LX_OK) return st;
     // R = h (F(a) - F(u)) into d_f, then a = u + p1 in u_low
     if (P.kind == LX_ADVDIFF)
       exprb32_stage_kernel<0><<<G, kThreadsPerBlock, 0, c->stream>>>(c->geo, h, u, u_low, c->d_f);
     else if (P.kind == LX_BURGERS)
       exprb32_stage_kernel<1><<<G, kThreadsPerBlock, 0, c->stream>>>(c->geo, h, u, u_low, c->d_f);
+    else if (df_up3 && P.kind == LX_BURGERS_UP3)
+      burgers_up3_df_kernel<false><<<G, kThreadsPerBlock, 0, c->stream>>>(c->up3, h, u_low, nullptr, c->d_f,
+                                                                            c->d_state);
     else if (P.kind == LX_ADVDIFF_UP3)
       exprb32_stage_up3_kernel<false><<<G, kThreadsPerBlock, 0, c->stream>>>(c->up3, h, u_low, c->d_f);
     else

@@ -306,3 +306,37 @@ def test_df64_ros_eu_up3_rhs_forms(lx, xi_oracle, scale, source):
     ref, it_o, st_o = oracle.ros_eu(2, nx, ny, NU, A, u, c, g, h, TOL, TOL * scale, xi_oracle, source=S)
     assert st == 0 and st_o == 0 and abs(it - it_o) <= 1
     assert rel(hi.cpu().numpy(), ref) <= TOL
+
+
+@pytest.mark.parametrize("integ", [0, 1])
+@pytest.mark.parametrize("source", [False, True])
+def test_df64_burgers_up3_rhs_ranges(lx, xi_oracle, integ, source):
+    # the float-float right-hand side and EXPRB32 remainder of the upwind
+    # Burgers step on a state with sign changes, exact zeros and values below
+    # the float-float range (their neighbourhoods take the FP64 formula),
+    # against the oracle on a grid with a ragged row count (the float-float
+    # Burgers form needs nx % 128 == 0)
+    nx, ny = 256, 72
+    u = synth.problem3_ic(nx, ny, seed=23) - 2.0
+    u[::97] = 0.0
+    u[5::131] = 1e-25
+    u[11::173] = -3e-17
+    S = synth.problem2_source(nx, ny) if source else None
+    h = 30 * synth.cfl_step_pm1(nx, ny, NU, A * np.abs(u).max())
+    c, g = _interval(3, nx, ny, A, u)
+    ctx = lx.leja_setup(nx, ny, NU, A, lx.BURGERS_UP3, lx.DF64, integ)
+    if source:
+        Sd = dev(S)
+        assert lx.lx_ctx_set_source(ctx, Sd) == 0
+    lo = torch.empty(nx * ny, dtype=torch.float64, device="cuda")
+    hi = torch.empty(nx * ny, dtype=torch.float64, device="cuda")
+    st, err, it = lx.expint_step(ctx, dev(u), lo, hi, c, g, h, TOL, TOL)
+    if integ == 0:
+        ref, it_o, st_o = oracle.ros_eu(3, nx, ny, NU, A, u, c, g, h, TOL, TOL, xi_oracle, source=S)
+        assert st == 0 and st_o == 0 and abs(it - it_o) <= 1
+        assert rel(hi.cpu().numpy(), ref) <= TOL
+    else:
+        rlo, rhi, rerr, it_o, st_o = oracle.exprb32(3, nx, ny, NU, A, u, c, g, h, TOL, TOL, xi_oracle, source=S)
+        assert st == 0 and st_o == 0 and abs(it - it_o) <= 2
+        assert rel(lo.cpu().numpy(), rlo) <= TOL and rel(hi.cpu().numpy(), rhi) <= TOL
+        assert abs(err - rerr) <= 1e-6 * rerr
