@@ -118,6 +118,11 @@ struct lx_ctx {
   float2* d_br = nullptr;   // df64 Burgers: diagonal weight per point
   float* d_uf = nullptr;    // mixed Burgers: u as floats
   float* d_sf = nullptr;    // mixed Burgers: u_x + u_y as floats
+  // linearisation point, 1/gamma and c for which d_bq / d_br / d_uf / d_sf are
+  // current within one call (the two loops of an EXPRB32 step share them);
+  // cleared by every call and by every other writer of those buffers
+  const double* prep_u = nullptr;
+  double prep_ig = 0.0, prep_cc = 0.0;
   const double* d_src = nullptr;  // caller's time-independent source (borrowed), or NULL
   double* d_partials = nullptr;
   int partials_cap = 0;
@@ -476,21 +481,26 @@ lx_status prepare_loop(lx_ctx* c, int strip_h, int kmax, const double* d, const 
   a.up = c->up3;
   a.up_c = cc;
   if (is_up3(P.kind)) a.inv_gamma = ig;
+  const bool prep_current = c->prep_u == u && c->prep_ig == ig && c->prep_cc == cc;
   if (P.precision == LX_MIXED && P.kind == LX_BURGERS) {
     // the mixed form's float copies of u and u_x + u_y, once per loop
     a.uf = c->d_uf;
     a.sf = c->d_sf;
-    to_float_kernel<<<aux_blocks(c), kThreadsPerBlock, 0, c->stream>>>(c->n, u, c->d_uf);
-    to_float_kernel<<<aux_blocks(c), kThreadsPerBlock, 0, c->stream>>>(c->n, c->d_s, c->d_sf);
-    c->stats.kernels += 2;
-    LX_CUDA(cudaGetLastError());
+    if (!prep_current) {
+      to_float_kernel<<<aux_blocks(c), kThreadsPerBlock, 0, c->stream>>>(c->n, u, c->d_uf);
+      to_float_kernel<<<aux_blocks(c), kThreadsPerBlock, 0, c->stream>>>(c->n, c->d_s, c->d_sf);
+      c->stats.kernels += 2;
+      LX_CUDA(cudaGetLastError());
+    }
   }
   if (P.precision == LX_DF64 && P.kind == LX_BURGERS_UP3) {
     // q = u |a| / (6 dx gamma) as float pairs for the point weights
     a.bq = c->d_bq;
-    up3_df_prep_kernel<<<aux_blocks(c), kThreadsPerBlock, 0, c->stream>>>(c->n, u, c->up3.gx * ig, c->d_bq);
-    ++c->stats.kernels;
-    LX_CUDA(cudaGetLastError());
+    if (!prep_current) {
+      up3_df_prep_kernel<<<aux_blocks(c), kThreadsPerBlock, 0, c->stream>>>(c->n, u, c->up3.gx * ig, c->d_bq);
+      ++c->stats.kernels;
+      LX_CUDA(cudaGetLastError());
+    }
   }
   const double wd[4] = {a.wxp, a.wxm, a.wyp, a.wym};
   for (int k = 0; k < 4; ++k) {
@@ -509,11 +519,16 @@ lx_status prepare_loop(lx_ctx* c, int strip_h, int kmax, const double* d, const 
     }
     a.bq = c->d_bq;
     a.br = c->d_br;
-    burgers_df_prep_kernel<<<aux_blocks(c), kThreadsPerBlock, 0, c->stream>>>(c->n, u, c->d_s, ig / (2 * dx), ig,
-                                                                               a.wc0, c->d_bq, c->d_br);
-    ++c->stats.kernels;
-    LX_CUDA(cudaGetLastError());
+    if (!prep_current) {
+      burgers_df_prep_kernel<<<aux_blocks(c), kThreadsPerBlock, 0, c->stream>>>(c->n, u, c->d_s, ig / (2 * dx), ig,
+                                                                                 a.wc0, c->d_bq, c->d_br);
+      ++c->stats.kernels;
+      LX_CUDA(cudaGetLastError());
+    }
   }
+  c->prep_u = u;
+  c->prep_ig = ig;
+  c->prep_cc = cc;
   set_loop_args_kernel<<<1, 1, 0, c->stream>>>(a, c->d_args, c->d_state, c->d_ticket, wexp_known ? 0 : 1);
   ++c->stats.kernels;
   LX_CUDA(cudaGetLastError());
@@ -594,6 +609,7 @@ lx_status launch_loop(lx_ctx* c, int slot, int l, const double* u, const double*
 
 lx_status begin_call(lx_ctx* c) {
   c->ev_used = 0;
+  c->prep_u = nullptr;
   reset_call_kernel<<<1, 1, 0, c->stream>>>(c->d_state, c->d_ticket);
   ++c->stats.kernels;
   LX_CUDA(cudaGetLastError());
@@ -817,6 +833,7 @@ lx_status power_bound(lx_ctx* c, const double* u, const double* v0, int max_iter
   const bool dfu = P.precision == LX_DF64 && is_up3(P.kind);  // float-float passes of the upwind kinds
   if (dfu && P.kind == LX_BURGERS_UP3) {
     // q = u |a| / (6 dx) as float pairs for the point weights of J(u)
+    c->prep_u = nullptr;
     up3_df_prep_kernel<<<G, kThreadsPerBlock, 0, c->stream>>>(c->n, u, c->up3.gx, c->d_bq);
     ++c->stats.kernels;
     LX_CUDA(cudaGetLastError());
@@ -840,6 +857,7 @@ lx_status power_bound(lx_ctx* c, const double* u, const double* v0, int max_iter
         PW.bl[2 * k + 1] = (float)(blv[k] - (double)PW.bl[2 * k]);
       }
       // q = u / (2 dx), r = -2 nu/dx^2 - 2 nu/dy^2 - (u_x + u_y)
+      c->prep_u = nullptr;
       burgers_df_prep_kernel<<<G, kThreadsPerBlock, 0, c->stream>>>(c->n, u, c->d_s, 1.0 / (2 * dx), 1.0,
                                                                      -2.0 * nx2 - 2.0 * ny2, c->d_bq, c->d_br);
       ++c->stats.kernels;
@@ -1204,7 +1222,7 @@ lx_status expint_step(lx_ctx* c, const double* u, double* u_low, double* u_high,
     // sides have recorded the input exponent)
     st = launch_loop(c, 0, 1, u, c->d_f, u_low, cc, gamma, h, rtol, atol, nullptr, df_up3);
     if (st != LX_OK) return st;
-    // R = h (F(a) - F(u)) into d_f, then a = u + p1 in u_low
+    // R = h (F(a) - F(u)) into d_f (u_low keeps p1 until the final pass)
     if (P.kind == LX_ADVDIFF)
       exprb32_stage_kernel<0><<<G, kThreadsPerBlock, 0, c->stream>>>(c->geo, h, u, u_low, c->d_f);
     else if (P.kind == LX_BURGERS)
@@ -1218,14 +1236,11 @@ lx_status expint_step(lx_ctx* c, const double* u, double* u_low, double* u_high,
       exprb32_stage_up3_kernel<true><<<G, kThreadsPerBlock, 0, c->stream>>>(c->up3, h, u_low, c->d_f);
     ++c->stats.kernels;
     LX_CUDA(cudaGetLastError());
-    exprb32_a_kernel<<<G, kThreadsPerBlock, 0, c->stream>>>(c->n, u, u_low);
-    ++c->stats.kernels;
-    LX_CUDA(cudaGetLastError());
     // p3 = phi_3(h J) R
     st = launch_loop(c, 1, 3, u, c->d_f, c->d_p3, cc, gamma, h, rtol, atol);
     if (st != LX_OK) return st;
-    // u_high = a + 2 p3, err = ||2 p3||
-    exprb32_final_kernel<<<G, kThreadsPerBlock, 0, c->stream>>>(c->n, u_low, c->d_p3, u_high, c->d_partials,
+    // a = u + p1 into u_low, u_high = a + 2 p3, err = ||2 p3||
+    exprb32_final_kernel<<<G, kThreadsPerBlock, 0, c->stream>>>(c->n, u, u_low, c->d_p3, u_high, c->d_partials,
                                                                  c->d_ticket, c->d_state);
     ++c->stats.kernels;
     LX_CUDA(cudaGetLastError());
@@ -1422,6 +1437,7 @@ lx_status lx_ctx_autotune(lx_ctx* c, int iters, const char* cache_path, char* re
   LX_CUDA(cudaMemsetAsync(c->d_s, 0, nb, c->stream));
   LX_CUDA(cudaMemsetAsync(c->d_tune, 0, nb, c->stream));
   if (c->d_pdf) LX_CUDA(cudaMemsetAsync(c->d_pdf, 0, sizeof(float2) * (size_t)c->n, c->stream));
+  c->prep_u = nullptr;
   if (c->d_bq) LX_CUDA(cudaMemsetAsync(c->d_bq, 0, sizeof(float2) * (size_t)c->n, c->stream));
   if (c->d_br) LX_CUDA(cudaMemsetAsync(c->d_br, 0, sizeof(float2) * (size_t)c->n, c->stream));
   if (c->d_uf) LX_CUDA(cudaMemsetAsync(c->d_uf, 0, sizeof(float) * (size_t)c->n, c->stream));
