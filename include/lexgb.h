@@ -119,6 +119,16 @@ lx_status lx_leja_coeffs(int l, double h, double c, double gamma, const double* 
  * most K.  The Leja loop stops with LX_E_NOCONV after J - 1 iterations. */
 int lx_leja_coeff_count(double h, double c, double gamma, int K);
 
+/* Focal interval of the real Leja points from a spectral-radius estimate
+ * (Sec. 2.2, Listing 7: the largest eigenvalue magnitude rho, enlarged by
+ * 5 %, gives lambda = -1.05 rho, and the interpolation interval [lambda, 0]
+ * has centre c = lambda / 2 and quarter-width gamma = -lambda / 4).
+ *   rho       spectral-radius estimate (power_bound), finite and > 0
+ *   c, gamma  host doubles, written on success
+ * LX_E_INVAL for NULL outputs or rho not finite and positive (a zero
+ * operator has no interval: gamma would be 0). */
+lx_status lx_spectral_interval(double rho, double* c, double* gamma);
+
 /* ---------------------------------------------------------------------------
  * Context (the paper's struct Leja, Sec. 2.3 Listing 10)
  * ------------------------------------------------------------------------- */
@@ -405,10 +415,9 @@ void mlp_destroy(lx_mlp* m);
 /* ---------------------------------------------------------------------------
  * Allocation-free entry point.  The paper has no counterpart: it exists for
  * callers that cannot allocate device memory at the point of the call --
- * code that runs while a stream is being captured into a CUDA graph (where
- * cudaMalloc/cudaFree are not allowed), applications whose own memory pool
- * owns the device, and time-critical loops that cannot afford the implicit
- * synchronisation of an allocation.
+ * applications whose own memory pool owns the device (and plug-ins loaded
+ * into them), and time-critical loops that cannot afford the implicit device
+ * synchronisation of cudaMalloc/cudaFree.
  * ------------------------------------------------------------------------- */
 
 #define LX_NOALLOC_MAX_POINTS 262144 /* largest nx * ny (512 x 512) */
@@ -429,11 +438,15 @@ void mlp_destroy(lx_mlp* m);
  *                the call synchronises it before returning
  * Every call shares the scratch array and leaves its contents behind; each
  * call clears what must start at zero.  Calls whose GPU work overlaps (other
- * streams, other host threads) race on the array: serialise them.  The first
- * call on a device resolves the array's device address, and the first call
- * in the process computes the Leja point table on the host; make that first
- * call before any stream capture starts.  The host side uses about 64 KB of
- * stack. */
+ * streams, other host threads) race on the array: serialise them.  The call
+ * is driven from the host: it launches the fused iteration in batches of 8
+ * and reads the loop state back, synchronising the stream, after each batch.
+ * Set-up: the first call in the process computes the table of
+ * LX_NOALLOC_MAX_LEJA Leja points on the host (its one host allocation),
+ * and the first call on each device, with that device current, resolves the
+ * array's device address (cudaGetSymbolAddress) and uploads the table with a
+ * synchronous copy; make that first call before any stream capture starts.
+ * Later calls allocate nothing.  The host side uses about 56 KB of stack. */
 lx_status phi_l_apply_noalloc(const lx_problem* prob, int l, const double* w_dev, double* out_dev, double c,
                               double gamma, double h, double rtol, double atol, void* cuda_stream, int* iters);
 

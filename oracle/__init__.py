@@ -65,6 +65,8 @@ def lib():
             L.or_exprb32.argtypes = [C.c_int, C.c_int, C.c_int, C.c_double, C.c_double, _dp, C.c_double,
                                      C.c_double, C.c_double, C.c_double, C.c_double, _dp, C.c_int, _dp, _dp,
                                      _dp, _ip]
+            L.or_leja_phi_given.argtypes = [C.c_int, C.c_int, C.c_int, C.c_double, C.c_double, _dp, _dp, C.c_double,
+                                            C.c_double, C.c_double, C.c_double, _dp, _dp, C.c_int, _dp, _ip]
             L.or_leja_phi_vertical.argtypes = [C.c_int, C.c_int, C.c_int, C.c_double, C.c_double, _dp, C.c_int,
                                                C.c_int, _dp, _dp, C.c_double, C.c_double, C.c_double, C.c_double,
                                                C.c_double, _dp, C.c_int, _dp, _ip]
@@ -79,6 +81,7 @@ def lib():
             L.or_integrate_exprb32.argtypes = [C.c_int, C.c_int, C.c_int, C.c_double, C.c_double, _dp, _dp,
                                                C.c_double, C.c_double, C.c_double, C.c_double, _dp, C.c_int,
                                                C.c_int, _ip, _ip, C.POINTER(C.c_longlong), _dp, _dp]
+            L.or_integrate_exprb32_log.argtypes = L.or_integrate_exprb32.argtypes + [_dp, C.c_int]
             L.or_fd_jv.argtypes = [C.c_int, C.c_int, C.c_int, C.c_double, C.c_double, _RHS, C.c_void_p, C.c_double,
                                    _dp, _dp, _dp]
             L.or_power_iteration_fd.argtypes = [C.c_int, C.c_int, C.c_int, C.c_double, C.c_double, _RHS,
@@ -223,6 +226,105 @@ def leja_phi(kind, nx, ny, nu, a, u, l, w, c, gamma, h, rtol, atol, xi):
     return out, int(it.value), st
 
 
+# ---------------------------------------------------------------------------
+# Divided differences above binary128 (mpmath).  The Newton coefficients of
+# phi_l(h (c + gamma xi)) at the Leja points, by the same plain recursion
+# d_j <- (d_j - d_k)/(xi_j - xi_k) (Sec. 2.1, Eq. 2), carried out with
+# `dps` decimal digits.  Where the spectrum is far from the real focal
+# interval (advection-dominated grids) the Newton basis grows like 4^m, and
+# binary128's absolute rounding floor (about 1e-34 of the largest value)
+# times that growth stops the series from converging; the recursion itself
+# is unchanged, only its working precision is raised.
+# ---------------------------------------------------------------------------
+
+
+def _phi_mp(mp, l, z):
+    """phi_l(z) at the working precision: the power series sum z^k/(k+l)!
+    for |z| < 1, else the recursion phi_{l+1} = (phi_l - 1/l!)/z from exp."""
+    if abs(z) < 1:
+        term = mp.mpf(1) / mp.factorial(l)
+        total = term
+        tiny = mp.mpf(10) ** (-mp.dps - 5)
+        k = 1
+        while True:
+            term = term * z / (k + l)
+            total += term
+            if abs(term) <= tiny * abs(total):
+                break
+            k += 1
+        return total
+    phi = mp.exp(z)
+    inv_fact = mp.mpf(1)
+    for k in range(l):
+        phi = (phi - inv_fact) / z
+        inv_fact = inv_fact / (k + 1)
+    return phi
+
+
+def dd_digits(K: int) -> int:
+    """Working digits for K coefficients: the basis may grow by up to 4 per
+    iteration (log10 4 = 0.6 digits), plus 40 digits of headroom."""
+    return 40 + int(0.7 * K)
+
+
+def _divdiff_rows(d, x):
+    """In place: d_j <- (d_j - d_k)/(x_j - x_k) for k < j, row by row."""
+    for j in range(1, len(d)):
+        dj, xj = d[j], x[j]
+        for k in range(j):
+            dj = (dj - d[k]) / (xj - x[k])
+        d[j] = dj
+    return d
+
+
+def divdiff_values_mp(x, f, dps: int = 60) -> np.ndarray:
+    """Divided differences of the values f (doubles, taken exactly) at the
+    nodes x with dps digits, rounded to double."""
+    import mpmath
+
+    with mpmath.workdps(dps):
+        mp = mpmath.mp
+        xs = [mp.mpf(float(v)) for v in _f64(x)]
+        d = [mp.mpf(float(v)) for v in _f64(f)]
+        return np.array([float(v) for v in _divdiff_rows(d, xs)])
+
+
+def leja_coeffs_mp(l: int, h: float, c: float, gamma: float, xi, dps: int | None = None) -> np.ndarray:
+    """d_j = f[xi_0..xi_j], f(xi) = phi_l(h (c + gamma xi)), with dps digits
+    (default dd_digits(len(xi))), rounded to double at the end."""
+    import mpmath
+
+    xi = _f64(xi)
+    K = len(xi)
+    with mpmath.workdps(dps or dd_digits(K)):
+        mp = mpmath.mp
+        H, Cc, G = mp.mpf(float(h)), mp.mpf(float(c)), mp.mpf(float(gamma))
+        x = [mp.mpf(float(v)) for v in xi]
+        d = [_phi_mp(mp, l, H * (Cc + G * xj)) for xj in x]
+        return np.array([float(v) for v in _divdiff_rows(d, x)])
+
+
+def leja_phi_mp(kind, nx, ny, nu, a, u, l, w, c, gamma, h, rtol, atol, xi, dps=None, k0=128):
+    """leja_phi with the Newton coefficients from leja_coeffs_mp.  Row j of
+    the recursion needs only rows < j, so the coefficients are formed for
+    the first k0 points and the table is doubled (up to len(xi)) while the
+    loop runs out of coefficients; a run that stops inside a shorter table
+    is the run with the full one.  Returns (out, iters, status)."""
+    w = _f64(w)
+    xi = _f64(xi)
+    u = _f64(u) if u is not None else None
+    out = np.zeros_like(w)
+    it = C.c_int(0)
+    K = min(k0, len(xi))
+    while True:
+        d = leja_coeffs_mp(l, h, c, gamma, xi[:K], dps)
+        st = lib().or_leja_phi_given(kind, nx, ny, nu, a, _p(u), _p(w), c, gamma, rtol, atol, _p(xi), _p(d), K,
+                                     _p(out), C.byref(it))
+        if st != E_NOCONV or K >= len(xi):
+            return out, int(it.value), st
+        K = min(2 * K, len(xi))
+
+
 def leja_phi_vertical(kind, nx, ny, nu, a, u, l, alphas, w, c, gamma, h, rtol, atol, xi):
     """phi_l(alpha_j h Op) w for every alpha_j from one Newton basis; returns
     (outputs [nc, n], iters, status)."""
@@ -273,17 +375,24 @@ def controller(h, err, tol):
     return lib().or_controller(h, err, tol)
 
 
-def integrate_exprb32(kind, nx, ny, nu, a, u0, v0, t_final, h0, tol, leja_tol, xi, max_attempts=1000):
-    """Adaptive EXPRB32 run; returns (u, steps, rejected, leja_iters, h_next, t, status)."""
+def integrate_exprb32(kind, nx, ny, nu, a, u0, v0, t_final, h0, tol, leja_tol, xi, max_attempts=1000,
+                      want_log=False):
+    """Adaptive EXPRB32 run; returns (u, steps, rejected, leja_iters, h_next, t, status), plus with
+    want_log an array of attempts (t, step tried, error estimate, accepted)."""
     u = _f64(u0).copy()
     v0 = _f64(v0)
     xi = _f64(xi)
     steps, rej = C.c_int(0), C.c_int(0)
     its = C.c_longlong(0)
     h, t = np.zeros(1), np.zeros(1)
-    st = lib().or_integrate_exprb32(kind, nx, ny, nu, a, _p(u), _p(v0), t_final, h0, tol, leja_tol, _p(xi),
-                                    len(xi), max_attempts, C.byref(steps), C.byref(rej), C.byref(its), _p(h), _p(t))
-    return u, steps.value, rej.value, its.value, float(h[0]), float(t[0]), st
+    log = np.full((max_attempts, 4), np.nan)
+    st = lib().or_integrate_exprb32_log(kind, nx, ny, nu, a, _p(u), _p(v0), t_final, h0, tol, leja_tol, _p(xi),
+                                        len(xi), max_attempts, C.byref(steps), C.byref(rej), C.byref(its), _p(h),
+                                        _p(t), log.ctypes.data_as(_dp), max_attempts)
+    res = (u, steps.value, rej.value, its.value, float(h[0]), float(t[0]), st)
+    if want_log:
+        return res + (log[:steps.value + rej.value].copy(),)
+    return res
 
 
 # ---------------------------------------------------------------------------

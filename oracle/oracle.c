@@ -498,16 +498,14 @@ int or_power_iteration(int kind, int nx, int ny, double nu, double a, const doub
 /*   stop when |d_{m+1}| ||y_{m+1}|| <= rtol ||p_{m+1}|| + atol.             */
 /* ------------------------------------------------------------------------ */
 
-static int leja_phi_core(const or_op* op, int l, const double* w, double c, double gamma,
-                         double h, double rtol, double atol, const double* xi, int K,
-                         double* out, int* iters) {
+/* The loop itself, for Newton coefficients d[0..K) already formed. */
+static int leja_loop_core(const or_op* op, const double* w, double c, double gamma, double rtol, double atol,
+                          const double* xi, const double* d, int K, double* out, int* iters) {
   long n = (long)op->nx * op->ny;
   if (K < 2) return OR_E_INVAL;
-  double* d = (double*)malloc(sizeof(double) * (size_t)K);
   double* y = (double*)malloc(sizeof(double) * (size_t)n);
   double* t = (double*)malloc(sizeof(double) * (size_t)n);
-  if (!d || !y || !t) { free(d); free(y); free(t); return OR_E_NOMEM; }
-  or_leja_coeffs(l, h, c, gamma, xi, K, d);
+  if (!y || !t) { free(y); free(t); return OR_E_NOMEM; }
   for (long q = 0; q < n; ++q) {
     y[q] = w[q];
     out[q] = d[0] * w[q];
@@ -531,10 +529,21 @@ static int leja_phi_core(const or_op* op, int l, const double* w, double c, doub
       break;
     }
   }
-  free(d);
   free(y);
   free(t);
   return status;
+}
+
+static int leja_phi_core(const or_op* op, int l, const double* w, double c, double gamma,
+                         double h, double rtol, double atol, const double* xi, int K,
+                         double* out, int* iters) {
+  if (K < 2) return OR_E_INVAL;
+  double* d = (double*)malloc(sizeof(double) * (size_t)K);
+  if (!d) return OR_E_NOMEM;
+  or_leja_coeffs(l, h, c, gamma, xi, K, d);
+  int st = leja_loop_core(op, w, c, gamma, rtol, atol, xi, d, K, out, iters);
+  free(d);
+  return st;
 }
 
 int or_leja_phi(int kind, int nx, int ny, double nu, double a, const double* u, int l,
@@ -543,6 +552,19 @@ int or_leja_phi(int kind, int nx, int ny, double nu, double a, const double* u, 
   if (nx <= 0 || ny <= 0 || l < 0 || gamma == 0.0) return OR_E_INVAL;
   or_op op = {kind, nx, ny, nu, a, u};
   return leja_phi_core(&op, l, w, c, gamma, h, rtol, atol, xi, K, out, iters);
+}
+
+/* The same loop with caller-supplied coefficients d[0..K) of
+ * f(xi) = phi_l(h (c + gamma xi)) at the points xi, e.g. divided differences
+ * formed by the same recursion at a precision above binary128, for the
+ * regime where binary128 reaches its rounding floor before the series
+ * converges.  Stops with OR_E_NOCONV after K - 1 iterations. */
+int or_leja_phi_given(int kind, int nx, int ny, double nu, double a, const double* u, const double* w,
+                      double c, double gamma, double rtol, double atol, const double* xi, const double* d, int K,
+                      double* out, int* iters) {
+  if (nx <= 0 || ny <= 0 || gamma == 0.0 || !d) return OR_E_INVAL;
+  or_op op = {kind, nx, ny, nu, a, u};
+  return leja_loop_core(&op, w, c, gamma, rtol, atol, xi, d, K, out, iters);
 }
 
 /* ------------------------------------------------------------------------ */
@@ -730,10 +752,13 @@ double or_controller(double h, double err, double tol) {
   return h * f;
 }
 
-int or_integrate_exprb32(int kind, int nx, int ny, double nu, double a, double* u, const double* v0,
-                         double t_final, double h0, double tol, double leja_tol, const double* xi, int K,
-                         int max_attempts, int* steps_out, int* rejected_out, long long* iters_out,
-                         double* h_out, double* t_out) {
+/* The adaptive run.  log (may be NULL): per attempt, four doubles (t at
+ * the attempt, step tried, error estimate, 1 if accepted else 0), at most
+ * log_cap attempts recorded. */
+int or_integrate_exprb32_log(int kind, int nx, int ny, double nu, double a, double* u, const double* v0,
+                             double t_final, double h0, double tol, double leja_tol, const double* xi, int K,
+                             int max_attempts, int* steps_out, int* rejected_out, long long* iters_out,
+                             double* h_out, double* t_out, double* log, int log_cap) {
   long n = (long)nx * ny;
   double* lo = (double*)malloc(sizeof(double) * (size_t)n);
   double* hi = (double*)malloc(sizeof(double) * (size_t)n);
@@ -753,6 +778,12 @@ int or_integrate_exprb32(int kind, int nx, int ny, double nu, double a, double* 
     st = or_exprb32(kind, nx, ny, nu, a, u, c, gamma, hh, leja_tol, leja_tol, xi, K, lo, hi, &err, &it);
     iters_total += it;
     if (st != OR_OK) { status = st; break; }
+    if (log && att < log_cap) {
+      log[4 * att] = t;
+      log[4 * att + 1] = hh;
+      log[4 * att + 2] = err;
+      log[4 * att + 3] = err <= tol ? 1.0 : 0.0;
+    }
     if (err <= tol) {
       memcpy(u, hi, sizeof(double) * (size_t)n);
       t += hh;
@@ -770,6 +801,14 @@ int or_integrate_exprb32(int kind, int nx, int ny, double nu, double a, double* 
   free(lo);
   free(hi);
   return status;
+}
+
+int or_integrate_exprb32(int kind, int nx, int ny, double nu, double a, double* u, const double* v0,
+                         double t_final, double h0, double tol, double leja_tol, const double* xi, int K,
+                         int max_attempts, int* steps_out, int* rejected_out, long long* iters_out,
+                         double* h_out, double* t_out) {
+  return or_integrate_exprb32_log(kind, nx, ny, nu, a, u, v0, t_final, h0, tol, leja_tol, xi, K, max_attempts,
+                                  steps_out, rejected_out, iters_out, h_out, t_out, NULL, 0);
 }
 
 /* ------------------------------------------------------------------------ */

@@ -73,6 +73,7 @@ def lib():
             L.lx_leja_coeffs.argtypes = [C.c_int, C.c_double, C.c_double, C.c_double, _dp, C.c_int, _dp]
             L.lx_leja_coeff_count.argtypes = [C.c_double, C.c_double, C.c_double, C.c_int]
             L.lx_leja_coeff_count.restype = C.c_int
+            L.lx_spectral_interval.argtypes = [C.c_double, _dp, _dp]
             L.leja_setup.argtypes = [C.POINTER(LxProblem), C.c_int, C.c_int, _vp, C.POINTER(_vp)]
             L.leja_destroy.argtypes = [_vp]
             L.leja_destroy.restype = None
@@ -199,9 +200,13 @@ def lx_leja_coeff_count(h: float, c: float, gamma: float, K: int) -> int:
 
 
 def spectral_interval(rho: float):
-    """c and gamma from a spectral-radius estimate (lambda = -1.05 rho)."""
-    lam = -1.05 * rho
-    return lam / 2.0, -lam / 4.0
+    """(c, gamma) of the focal interval for a spectral-radius estimate, from
+    lx_spectral_interval."""
+    c, g = C.c_double(0.0), C.c_double(0.0)
+    st = lib().lx_spectral_interval(float(rho), C.byref(c), C.byref(g))
+    if st != OK:
+        raise LexgbError(st, "lx_spectral_interval")
+    return c.value, g.value
 
 
 # ------------------------------------------------------------------ context

@@ -240,4 +240,16 @@ lx_status lx_leja_coeffs(int l, double h, double c, double gamma, const double* 
 
 int lx_leja_coeff_count(double h, double c, double gamma, int K) { return lexgb::leja_coeff_count(h, c, gamma, K); }
 
+// The focal interval from a spectral-radius estimate (Sec. 2.2, Listing 7's
+// time loop): the eigenvalue bound lambda = -1.05 rho sets the interval
+// [lambda, 0] = [c - 2 gamma, c + 2 gamma], i.e. c = lambda / 2 and
+// gamma = -lambda / 4.
+lx_status lx_spectral_interval(double rho, double* c, double* gamma) {
+  if (!c || !gamma || !std::isfinite(rho) || !(rho > 0.0)) return LX_E_INVAL;
+  const double lambda = -1.05 * rho;
+  *c = lambda / 2.0;
+  *gamma = -lambda / 4.0;
+  return LX_OK;
+}
+
 }  // extern "C"

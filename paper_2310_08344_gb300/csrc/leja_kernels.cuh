@@ -458,16 +458,16 @@ static __global__ void add_kernel(long long n, const double* __restrict__ x, dou
 }
 
 // EXPRB32 middle stage: R = h (F(a) - F(u)) = -h p1 (D p1) for the quadratic
-// Burgers term, a = u + p1 (R = 0 for the linear operator); p1 is only read.
+// Burgers term with p1 = a - u (R = 0 for the linear operator).  p1 is only
+// read: a = u + p1 is formed later, by the final pass.
 template <int KIND>
-__global__ void exprb32_stage_kernel(Geo g, double h, const double* __restrict__ u, double* __restrict__ p1_a,
-                                     double* __restrict__ R) {
+__global__ void exprb32_stage_kernel(Geo g, double h, const double* __restrict__ p1, double* __restrict__ R) {
   for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < g.n; q += (long long)gridDim.x * blockDim.x) {
     if (KIND == 1) {
       long long e, w, nn, s;
       neighbours(g, q, e, w, nn, s);
-      const double dp = (p1_a[e] - p1_a[w]) * g.i2dx + (p1_a[nn] - p1_a[s]) * g.i2dy;
-      R[q] = -h * p1_a[q] * dp;
+      const double dp = (p1[e] - p1[w]) * g.i2dx + (p1[nn] - p1[s]) * g.i2dy;
+      R[q] = -h * p1[q] * dp;
     } else {
       R[q] = 0.0;
     }

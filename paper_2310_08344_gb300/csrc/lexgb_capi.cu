@@ -1224,9 +1224,9 @@ lx_status expint_step(lx_ctx* c, const double* u, double* u_low, double* u_high,
     if (st != LX_OK) return st;
     // R = h (F(a) - F(u)) into d_f (u_low keeps p1 until the final pass)
     if (P.kind == LX_ADVDIFF)
-      exprb32_stage_kernel<0><<<G, kThreadsPerBlock, 0, c->stream>>>(c->geo, h, u, u_low, c->d_f);
+      exprb32_stage_kernel<0><<<G, kThreadsPerBlock, 0, c->stream>>>(c->geo, h, u_low, c->d_f);
     else if (P.kind == LX_BURGERS)
-      exprb32_stage_kernel<1><<<G, kThreadsPerBlock, 0, c->stream>>>(c->geo, h, u, u_low, c->d_f);
+      exprb32_stage_kernel<1><<<G, kThreadsPerBlock, 0, c->stream>>>(c->geo, h, u_low, c->d_f);
     else if (df_up3 && P.kind == LX_BURGERS_UP3)
       burgers_up3_df_kernel<false><<<G, kThreadsPerBlock, 0, c->stream>>>(c->up3, h, u_low, nullptr, c->d_f,
                                                                             c->d_state);
@@ -1524,7 +1524,12 @@ static lx_status integrate_impl(lx_ctx* c, double* u, const double* v0, double t
       status = st;
       break;
     }
-    const double lam = -1.05 * rho, cc = lam / 2.0, gamma = -lam / 4.0;
+    double cc = 0.0, gamma = 0.0;
+    st = lx_spectral_interval(rho, &cc, &gamma);
+    if (st != LX_OK) {
+      status = st;
+      break;
+    }
     double err = 0.0;
     int it = 0;
     st = expint_step(c, u, c->d_io[1], c->d_io[2], cc, gamma, hh, leja_tol, leja_tol, &err, &it);

@@ -2,15 +2,14 @@
 // without any memory allocation by the library.
 //
 // Who needs this: callers that must not allocate device memory at the point
-// of the call -- code running while a CUDA stream is being captured into a
-// graph (cudaMalloc/cudaFree are not permitted during capture), applications
-// that hand the whole device to their own memory pool and forbid other
-// allocators, and solvers embedded in time-critical loops where an
-// allocation's implicit synchronisation is unacceptable.  They pass their
-// input and output vectors, and all scratch (the two Newton-basis vectors,
-// reduction partials, the loop state, the Leja points and coefficients)
-// lives in one file-scope __device__ array of fixed size instead of in a
-// context.
+// of the call -- applications that hand the whole device to their own memory
+// pool and forbid other allocators, plug-ins loaded into such a host
+// application, and solvers embedded in time-critical loops where the
+// implicit device synchronisation of cudaMalloc/cudaFree is unacceptable.
+// They pass their input and output vectors, and all scratch (the two
+// Newton-basis vectors, reduction partials, the loop state, the Leja points
+// and coefficients) lives in one file-scope __device__ array of fixed size
+// instead of in a context.
 //
 // Limits and rules:
 //  * at most LX_NOALLOC_MAX_POINTS grid points and LX_NOALLOC_MAX_LEJA Leja
@@ -21,10 +20,15 @@
 //    parts that must start at zero are cleared by each call, and two calls
 //    whose GPU work overlaps (different streams, or different host threads
 //    without ordering) race on the array and give wrong results;
-//  * the first call on a device looks up the array's device address with
-//    cudaGetSymbolAddress, and the first call in the process computes the
-//    Leja point table on the host; make that first call before any stream
-//    capture begins.
+//  * the call is driven from the host: it launches the fused iteration in
+//    batches of 8, reads the loop state back and synchronises the stream
+//    after each batch;
+//  * set-up: the first call in the process computes the table of
+//    LX_NOALLOC_MAX_LEJA Leja points on the host (the only host allocation,
+//    made once), and the first call on each device, with that device
+//    current, looks up the array's device address with cudaGetSymbolAddress
+//    and uploads the point table with a synchronous copy; make that first
+//    call before any stream capture begins.  Later calls allocate nothing.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -68,15 +72,30 @@ const void* noalloc_kernel(int vec2) {
               : reinterpret_cast<const void*>(&leja_iter_kernel<0, double, 1>);
 }
 
-// Once per device, with that device current: the scratch address and the
-// resident grid sizes of the two kernel variants.
+// The Leja point table, computed once per process at its full length so
+// that no later call grows it.
+double g_xi[LX_NOALLOC_MAX_LEJA];
+bool g_xi_ready = false;
+
+// Once per device, with that device current: the scratch address, the
+// resident grid sizes of the two kernel variants and the point table in the
+// scratch.
 lx_status device_setup(int dev, unsigned char** ptr, int* grid2) {
   std::lock_guard<std::mutex> lock(g_mu);
+  if (!g_xi_ready) {
+    if (leja_points(LX_NOALLOC_MAX_LEJA, g_xi) != LX_OK) return LX_E_INVAL;
+    g_xi_ready = true;
+  }
   if (!g_dev_ptr[dev]) {
     void* p = nullptr;
     cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
     if (e != cudaSuccess || !p) {
       set_last_error("phi_l_apply_noalloc: cudaGetSymbolAddress failed");
+      return LX_E_CUDA;
+    }
+    if (cudaMemcpy(static_cast<unsigned char*>(p) + kOffXi, g_xi, sizeof(g_xi), cudaMemcpyHostToDevice) !=
+        cudaSuccess) {
+      set_last_error("phi_l_apply_noalloc: upload of the Leja point table failed");
       return LX_E_CUDA;
     }
     int sms = 0;
@@ -122,13 +141,12 @@ extern "C" lx_status phi_l_apply_noalloc(const lx_problem* prob, int l, const do
   if (st != LX_OK) return st;
   cudaStream_t stream = reinterpret_cast<cudaStream_t>(cuda_stream);
 
-  // Host side: Leja points and Newton coefficients in stack buffers.
+  // Host side: Newton coefficients in stack buffers, at the points of the
+  // table made at set-up (already in the scratch).
   const int count = leja_coeff_count(h, cc, gamma, LX_NOALLOC_MAX_LEJA);
-  double xi[LX_NOALLOC_MAX_LEJA];
   double d[LX_NOALLOC_MAX_LEJA];
   double ws[6 * (LX_NOALLOC_MAX_LEJA + 8)];
-  if (leja_points(count, xi) != LX_OK) return LX_E_INVAL;
-  st = (lx_status)leja_coeffs_ws(l, h, cc, gamma, xi, count, d, ws);
+  st = (lx_status)leja_coeffs_ws(l, h, cc, gamma, g_xi, count, d, ws);
   if (st != LX_OK) return st;
 
   LoopArgs* d_args = reinterpret_cast<LoopArgs*>(base + kOffArgs);
@@ -139,8 +157,7 @@ extern "C" lx_status phi_l_apply_noalloc(const lx_problem* prob, int l, const do
   double* d_d = reinterpret_cast<double*>(base + kOffD);
   double* y0 = reinterpret_cast<double*>(base + kOffY0);
   double* y1 = reinterpret_cast<double*>(base + kOffY1);
-  if (cudaMemcpyAsync(d_xi, xi, sizeof(double) * count, cudaMemcpyHostToDevice, stream) != cudaSuccess ||
-      cudaMemcpyAsync(d_d, d, sizeof(double) * count, cudaMemcpyHostToDevice, stream) != cudaSuccess)
+  if (cudaMemcpyAsync(d_d, d, sizeof(double) * count, cudaMemcpyHostToDevice, stream) != cudaSuccess)
     return LX_E_CUDA;
 
   const double dx = 1.0 / prob->nx, dy = 1.0 / prob->ny, ig = 1.0 / gamma;

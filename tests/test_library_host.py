@@ -96,3 +96,19 @@ def test_classical_controller_matches_oracle(lx):
         b = oracle.controller(h, err, tol)
         assert abs(a - b) <= 2e-15 * b  # cbrt vs pow(., 1/3): an ulp or two
         assert 0.2 * h * (1 - 1e-15) <= a <= 2.0 * h * (1 + 1e-15)
+
+
+def test_spectral_interval_is_listing7(lx):
+    # lambda = -1.05 rho; the focal interval [c - 2 gamma, c + 2 gamma] is
+    # [lambda, 0] (the Leja point xi_0 = 2 maps to z = 0)
+    from paper_2310_08344_gb300 import LexgbError
+
+    for rho in (1e-3, 1.0, 316285.6445, 1.7e8):
+        c, g = lx.spectral_interval(rho)
+        assert c + 2 * g == 0.0
+        assert abs((c - 2 * g) - (-1.05 * rho)) <= 2e-16 * 1.05 * rho
+        assert g > 0 and c < 0
+        assert (c, g) == oracle.spectral_interval(rho)
+    for bad in (0.0, -1.0, float("nan"), float("inf")):
+        with pytest.raises(LexgbError):
+            lx.spectral_interval(bad)
