@@ -41,6 +41,8 @@ NU, ADV = 1e-2, 1.0
 CFL_MULT = 50.0
 TOL = 1e-10
 ALG_BYTES = {"fp64": 32, "mixed": 24, "df64": 32}  # algorithmic bytes per point per fused Leja iteration
+FP64_OPS_PER_POINT_ITER = 8  # FP64 FMA-class instructions per point per Leja iteration (native FP64 kernel)
+FP64_FMA_PEAK_G = 625.0  # GB300 nominal FP64 1.25 TFLOP/s = 625 G fused multiply-adds per second
 
 
 def parse():
@@ -180,58 +182,81 @@ def ncu_traffic(kernel_name: str, n_points: int):
     return float(ent["dram_bytes_per_point"]) * n_points
 
 
-def cpu_baseline(n_sample: int, seconds_hint: str):
-    """The oracle, as it stands, on a bounded sample of the workload:
-    one Rosenbrock-Euler step at n_sample^2 (same recipe, h = 50 dt_CFL)."""
+def host_cpu():
+    """CPU model of this host (lscpu's model name, else the machine type)."""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.strip().startswith("Model name:"):
+                return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    import platform
+
+    return platform.machine()
+
+
+def oracle_steps(n: int, steps: int, warmup: int, parallel: bool):
+    """The oracle, as it stands, on the benchmark's recipe at n x n: the
+    10-pass power bound, then `warmup` untimed and `steps` timed
+    Rosenbrock-Euler steps.  Returns (GDOF*iter/s, seconds, iterations)."""
     import oracle
 
-    u0 = synth.gaussians_ic(n_sample, n_sample, seed=1)
-    h = CFL_MULT * synth.cfl_step(n_sample, n_sample, NU, ADV)
-    v0 = synth.power_start(n_sample * n_sample, seed=5)
-    rho, _, _ = oracle.power_iteration(oracle.ADVDIFF, n_sample, n_sample, NU, ADV, None, v0, 10)
+    u = synth.gaussians_ic(n, n, seed=1)
+    h = CFL_MULT * synth.cfl_step(n, n, NU, ADV)
+    v0 = synth.power_start(n * n, seed=5)
+    rho, _, _ = oracle.power_iteration(oracle.ADVDIFF, n, n, NU, ADV, None, v0, 10, parallel=parallel)
     c, g = oracle.spectral_interval(rho)
     xi = oracle.leja_points(1000)
+    for _ in range(warmup):
+        u, it, st = oracle.ros_eu(oracle.ADVDIFF, n, n, NU, ADV, u, c, g, h, TOL, TOL, xi, parallel=parallel)
+    total = 0
     t0 = time.perf_counter()
-    out, iters, st = oracle.ros_eu(oracle.ADVDIFF, n_sample, n_sample, NU, ADV, u0, c, g, h, TOL, TOL, xi)
+    for _ in range(steps):
+        u, it, st = oracle.ros_eu(oracle.ADVDIFF, n, n, NU, ADV, u, c, g, h, TOL, TOL, xi, parallel=parallel)
+        total += it
     dt = time.perf_counter() - t0
-    val = n_sample * n_sample * iters / dt / 1e9
-    return {"value": val, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"one Ros-Eu step at {n_sample}x{n_sample} ({iters} Leja iterations, {dt:.1f} s, "
-                      f"single-threaded C oracle){seconds_hint}"}
+    return n * n * total / dt / 1e9, dt, total
+
+
+def cpu_baseline(n: int, steps: int):
+    """The oracle's OpenMP build on all host cores, on the benchmark's own
+    workload (a bounded number of steps), plus its single-threaded parity
+    build on one step at half the grid size."""
+    import oracle
+
+    try:
+        cores = oracle.threads(True)
+        par = True
+    except Exception:  # no OpenMP on this host: the parity build, one core
+        cores, par = 1, False
+    val, dt, its = oracle_steps(n, steps, 0, par)
+    val1, dt1, its1 = oracle_steps(n // 2, 1, 0, False)
+    build = "-O3 -fopenmp build" if par else "single-threaded build (no OpenMP on this host)"
+    return {"value": val, "unit": UNIT, "cores": cores, "kind": "oracle", "cpu": host_cpu(),
+            "sample": f"{steps} Ros-Eu steps at {n}x{n} ({its} Leja iterations, {dt:.2f} s) with the oracle's "
+                      f"{build}, after its 10-pass power bound",
+            "single_thread": {"value": val1, "unit": UNIT, "cores": 1,
+                              "sample": f"one Ros-Eu step at {n // 2}x{n // 2} ({its1} Leja iterations, "
+                                        f"{dt1:.2f} s), the single-threaded parity build"}}
 
 
 def run_reference(args, rank, world):
     if rank != 0:
         return 0
-    n_sample = 1024
     import oracle
 
-    u0 = synth.gaussians_ic(n_sample, n_sample, seed=1)
-    h = CFL_MULT * synth.cfl_step(n_sample, n_sample, NU, ADV)
-    v0 = synth.power_start(n_sample * n_sample, seed=5)
-    rho, _, _ = oracle.power_iteration(oracle.ADVDIFF, n_sample, n_sample, NU, ADV, None, v0, 10)
-    c, g = oracle.spectral_interval(rho)
-    xi = oracle.leja_points(1000)
-    u = u0.copy()
-    for _ in range(args.warmup):
-        u, it, st = oracle.ros_eu(oracle.ADVDIFF, n_sample, n_sample, NU, ADV, u, c, g, h, TOL, TOL, xi)
-    total = 0
-    t0 = time.perf_counter()
-    for _ in range(args.steps):
-        u, it, st = oracle.ros_eu(oracle.ADVDIFF, n_sample, n_sample, NU, ADV, u, c, g, h, TOL, TOL, xi)
-        total += n_sample * n_sample * it
-    dt = time.perf_counter() - t0
-    val = total / dt / 1e9
+    val, dt, its = oracle_steps(NX, args.steps, args.warmup, True)
+    cores = oracle.threads(True)
     line = {"impl": "reference", "metric": METRIC, "value": val, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3 / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic",
             "config": {"workload": "advdiff-4096x4096-rosenbrock-euler", "nx": NX, "ny": NX, "nu": NU,
                        "a": ADV, "h_over_dt_cfl": CFL_MULT, "tol": TOL,
-                       "sample": f"each step a bounded sample: the same recipe at {n_sample}x{n_sample}",
-                       "note": "the CPU oracle, as it stands, on the host cores (single-threaded)"},
-            "cpu_baseline": {"value": val, "unit": UNIT, "cores": 1, "kind": "oracle",
-                             "sample": f"{args.steps} Ros-Eu steps at {n_sample}x{n_sample}, single-threaded"},
+                       "note": "the CPU oracle, as it stands, built with -O3 -fopenmp, on all host cores"},
+            "cpu_baseline": {"value": val, "unit": UNIT, "cores": cores, "kind": "oracle", "cpu": host_cpu(),
+                             "sample": f"{args.steps} Ros-Eu steps at {NX}x{NX} ({its} Leja iterations)"},
             "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
     return 0
@@ -342,7 +367,7 @@ def run_batch(args, rank, world, local):
 
 
 def run_paper(args, rank, world, local):
-    """The paper's own test problems (Sec. 4) on periodic [-1,1)^2 with the
+    """The paper's own test problems (Sec. 3) on periodic [-1,1)^2 with the
     third-order upwind gradient and the central Laplacian, diffusion 1 and
     advection / flux coefficient 10, tolerance 1e-12:
       paper1: u_t = A u, one exp(h A) u per step (Leja exponential),
@@ -980,6 +1005,7 @@ def main():
         for _ in range(max(args.warmup, 0)):
             pstep(pc, pn)
             pc, pn = pn, pc
+        lx.lx_ctx_stats(ctxp, reset=True)
         torch.cuda.synchronize()
         p0, p1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         p0.record(stream)
@@ -990,7 +1016,25 @@ def main():
         p1.record(stream)
         torch.cuda.synchronize()
         pms = p0.elapsed_time(p1) / args.steps
+        # the FP64 kernel against its two ceilings: the FP64 pipe (8 FP64
+        # FMA-class instructions per point-iteration: 5 for the folded
+        # stencil, 1 Newton update, 2 norms) and HBM (32 B per point-iteration)
+        pst = lx.lx_ctx_stats(ctxp, reset=True)
+        p_launch_s = pst["loop_ms"] / 1e3 / max(pst["loop_iterations"], 1)
+        p_ach = FP64_OPS_PER_POINT_ITER * N / p_launch_s / 1e9
+        p_hbm = ALG_BYTES["fp64"] * N / p_launch_s / 1e9
+        plain_roofline = {"bound": "alu", "achieved": p_ach, "peak": FP64_FMA_PEAK_G, "unit": "G FP64 FMA/s",
+                          "frac": p_ach / FP64_FMA_PEAK_G, "traffic": None,
+                          "kernel": lx.lx_ctx_kernel_name(ctxp), "avg_launch_us": p_launch_s * 1e6,
+                          "ops_per_point_iteration": FP64_OPS_PER_POINT_ITER,
+                          "peak_source": "nominal GB300 FP64 1.25 TFLOP/s = 625 G FMA/s (no measured FP64 peak "
+                                         "in MEASURED_PEAKS.json)",
+                          "hbm": {"achieved": p_hbm, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                                  "frac": p_hbm / peaks["hbm_gbs"],
+                                  "alu_ceiling_frac": FP64_FMA_PEAK_G * 1e9 / FP64_OPS_PER_POINT_ITER
+                                  * ALG_BYTES["fp64"] / 1e9 / peaks["hbm_gbs"]}}
         plain = {"precision": "fp64 (native FP64 kernels)", "kernel": lx.lx_ctx_kernel_name(ctxp),
+                 "roofline": plain_roofline,
                  "value": float(N) * sum(pits) / (pms * args.steps / 1e3) / 1e9, "ms_per_step": pms,
                  "leja_iters_per_step": pits, "chosen_speedup": pms / (ms / args.steps),
                  "rel_l2_final_chosen_vs_plain": float(torch.linalg.norm(cur - pc) / torch.linalg.norm(pc))}
@@ -1021,7 +1065,7 @@ def main():
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        cpu = cpu_baseline(2048, "")
+        cpu = cpu_baseline(n, 2)
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,

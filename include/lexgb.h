@@ -17,7 +17,7 @@
  *                  action J(u)v = nu Lap v - v (u_x+u_y) - u (v_x+v_y) is the
  *                  exact linearisation (the paper's finite-difference action,
  *                  Sec. 2.3, is replaced by it).
- *  - The paper's own discretisation (Sec. 4): periodic [-1,1)^2 (spacing
+ *  - The paper's own discretisation (Sec. 3): periodic [-1,1)^2 (spacing
  *    2/nx, 2/ny), the Laplacian by second-order central differences and the
  *    gradient by the third-order upwind-biased scheme -- for a term +a v_x,
  *    a > 0: (-v_{i+2} + 6 v_{i+1} - 3 v_i - 2 v_{i-1}) / (6 dx), mirrored for
@@ -115,8 +115,10 @@ lx_status lx_leja_coeffs(int l, double h, double c, double gamma, const double* 
 
 /* Number of Newton coefficients the engine computes and uses for (h, c,
  * gamma) with a table of K points: the first J with the bound
- * (h|gamma|)^J / J! * e^{max(0, h (c + 2|gamma|))} below 1e-40, plus 8, at
- * most K.  The Leja loop stops with LX_E_NOCONV after J - 1 iterations. */
+ * (2 h|gamma|)^J / J! * e^{max(0, h (c + 2|gamma|))} below 1e-40, plus 8, at
+ * most K (the factor 2 covers the geometric growth of the Newton basis when
+ * the spectrum reaches off the real focal interval).  The Leja loop stops
+ * with LX_E_NOCONV after J - 1 iterations. */
 int lx_leja_coeff_count(double h, double c, double gamma, int K);
 
 /* Focal interval of the real Leja points from a spectral-radius estimate
@@ -220,7 +222,7 @@ lx_status expint_step(lx_ctx* ctx, const double* u_dev, double* u_low_dev, doubl
 lx_status expint_step_host(lx_ctx* ctx, const double* u_host, double* u_low_host, double* u_high_host, double c,
                            double gamma, double h, double rtol, double atol, double* err, int* iters);
 
-/* Time-independent source term S (Sec. 4, the diffusion-advection problem
+/* Time-independent source term S (Sec. 3, Eq. 4, the diffusion-advection problem
  * with sources; any kind): after this call expint_step, expint_step_host
  * and lx_integrate integrate u' = f(u) + S, i.e. the right-hand side of
  * every step is h (f(u) + S); the Jacobian, the spectral bound and the

@@ -24,6 +24,7 @@ ADVDIFF, BURGERS = 0, 1
 ADVDIFF_UP3, BURGERS_UP3 = 2, 3
 
 _lib = None
+_lib_omp = None
 _lock = threading.Lock()
 _leja_cache: dict[int, np.ndarray] = {}
 
@@ -37,66 +38,82 @@ def _p(a):
     return a.ctypes.data_as(_dp) if a is not None else None
 
 
-def lib():
-    global _lib
+def lib(parallel: bool = False):
+    """The parity build (single-threaded), or with parallel=True the OpenMP
+    build of the same source, which only times the CPU baseline."""
+    global _lib, _lib_omp
     with _lock:
+        if parallel:
+            if _lib_omp is None:
+                _lib_omp = _declare(C.CDLL(_build.build(openmp=True)))
+            return _lib_omp
         if _lib is None:
-            path = _build.build()
-            L = C.CDLL(path)
-            L.or_phi.restype = C.c_double
-            L.or_phi.argtypes = [C.c_int, C.c_double]
-            L.or_qreal_mant_dig.restype = C.c_int
-            L.or_leja_points.argtypes = [C.c_int, _dp]
-            L.or_divdiff_values.argtypes = [C.c_int, _dp, _dp, _dp]
-            L.or_leja_coeffs.argtypes = [C.c_int, C.c_double, C.c_double, C.c_double, _dp, C.c_int, _dp]
-            L.or_apply_advdiff.argtypes = [C.c_int, C.c_int, C.c_double, C.c_double, _dp, _dp]
-            L.or_burgers_f.argtypes = [C.c_int, C.c_int, C.c_double, _dp, _dp]
-            L.or_burgers_J.argtypes = [C.c_int, C.c_int, C.c_double, _dp, _dp, _dp]
-            L.or_apply_advdiff_up3.argtypes = [C.c_int, C.c_int, C.c_double, C.c_double, _dp, _dp]
-            L.or_burgers_up3_f.argtypes = [C.c_int, C.c_int, C.c_double, C.c_double, _dp, _dp]
-            L.or_burgers_up3_J.argtypes = [C.c_int, C.c_int, C.c_double, C.c_double, _dp, _dp, _dp]
-            L.or_power_iteration.argtypes = [C.c_int, C.c_int, C.c_int, C.c_double, C.c_double, _dp, _dp,
-                                             C.c_int, _dp, _ip]
-            L.or_leja_phi.argtypes = [C.c_int, C.c_int, C.c_int, C.c_double, C.c_double, _dp, C.c_int, _dp,
-                                      C.c_double, C.c_double, C.c_double, C.c_double, C.c_double, _dp, C.c_int,
-                                      _dp, _ip]
-            L.or_ros_eu.argtypes = [C.c_int, C.c_int, C.c_int, C.c_double, C.c_double, _dp, C.c_double,
-                                    C.c_double, C.c_double, C.c_double, C.c_double, _dp, C.c_int, _dp, _ip]
-            L.or_exprb32.argtypes = [C.c_int, C.c_int, C.c_int, C.c_double, C.c_double, _dp, C.c_double,
-                                     C.c_double, C.c_double, C.c_double, C.c_double, _dp, C.c_int, _dp, _dp,
-                                     _dp, _ip]
-            L.or_leja_phi_given.argtypes = [C.c_int, C.c_int, C.c_int, C.c_double, C.c_double, _dp, _dp, C.c_double,
-                                            C.c_double, C.c_double, C.c_double, _dp, _dp, C.c_int, _dp, _ip]
-            L.or_leja_phi_vertical.argtypes = [C.c_int, C.c_int, C.c_int, C.c_double, C.c_double, _dp, C.c_int,
-                                               C.c_int, _dp, _dp, C.c_double, C.c_double, C.c_double, C.c_double,
-                                               C.c_double, _dp, C.c_int, _dp, _ip]
-            L.or_ros_eu_src.argtypes = [C.c_int, C.c_int, C.c_int, C.c_double, C.c_double, _dp, _dp,
-                                        C.c_double, C.c_double, C.c_double, C.c_double, C.c_double, _dp, C.c_int,
-                                        _dp, _ip]
-            L.or_exprb32_src.argtypes = [C.c_int, C.c_int, C.c_int, C.c_double, C.c_double, _dp, _dp,
-                                         C.c_double, C.c_double, C.c_double, C.c_double, C.c_double, _dp, C.c_int,
-                                         _dp, _dp, _dp, _ip]
-            L.or_controller.restype = C.c_double
-            L.or_controller.argtypes = [C.c_double, C.c_double, C.c_double]
-            L.or_integrate_exprb32.argtypes = [C.c_int, C.c_int, C.c_int, C.c_double, C.c_double, _dp, _dp,
-                                               C.c_double, C.c_double, C.c_double, C.c_double, _dp, C.c_int,
-                                               C.c_int, _ip, _ip, C.POINTER(C.c_longlong), _dp, _dp]
-            L.or_integrate_exprb32_log.argtypes = L.or_integrate_exprb32.argtypes + [_dp, C.c_int]
-            L.or_fd_jv.argtypes = [C.c_int, C.c_int, C.c_int, C.c_double, C.c_double, _RHS, C.c_void_p, C.c_double,
-                                   _dp, _dp, _dp]
-            L.or_power_iteration_fd.argtypes = [C.c_int, C.c_int, C.c_int, C.c_double, C.c_double, _RHS,
-                                                C.c_void_p, C.c_double, _dp, _dp, C.c_int, _dp, _ip]
-            L.or_leja_phi_fd.argtypes = [C.c_int, C.c_int, C.c_int, C.c_double, C.c_double, _RHS, C.c_void_p,
-                                         C.c_double, _dp, C.c_int, _dp, C.c_double, C.c_double, C.c_double,
-                                         C.c_double, C.c_double, _dp, C.c_int, _dp, _ip]
-            L.or_ros_eu_fd.argtypes = [C.c_int, C.c_int, C.c_int, C.c_double, C.c_double, _RHS, C.c_void_p,
-                                       C.c_double, _dp, C.c_double, C.c_double, C.c_double, C.c_double, C.c_double,
-                                       _dp, C.c_int, _dp, _ip]
-            L.or_exprb32_fd.argtypes = [C.c_int, C.c_int, C.c_int, C.c_double, C.c_double, _RHS, C.c_void_p,
-                                        C.c_double, _dp, C.c_double, C.c_double, C.c_double, C.c_double,
-                                        C.c_double, _dp, C.c_int, _dp, _dp, _dp, _ip]
-            _lib = L
+            _lib = _declare(C.CDLL(_build.build()))
     return _lib
+
+
+def threads(parallel: bool = False) -> int:
+    """Threads the grid loops of that build use."""
+    return lib(parallel).or_threads()
+
+
+def _declare(L):
+    """Declare the argument and result types of the exported functions."""
+    L.or_threads.restype = C.c_int
+    L.or_phi.restype = C.c_double
+    L.or_phi.argtypes = [C.c_int, C.c_double]
+    L.or_qreal_mant_dig.restype = C.c_int
+    L.or_leja_points.argtypes = [C.c_int, _dp]
+    L.or_divdiff_values.argtypes = [C.c_int, _dp, _dp, _dp]
+    L.or_leja_coeffs.argtypes = [C.c_int, C.c_double, C.c_double, C.c_double, _dp, C.c_int, _dp]
+    L.or_apply_advdiff.argtypes = [C.c_int, C.c_int, C.c_double, C.c_double, _dp, _dp]
+    L.or_burgers_f.argtypes = [C.c_int, C.c_int, C.c_double, _dp, _dp]
+    L.or_burgers_J.argtypes = [C.c_int, C.c_int, C.c_double, _dp, _dp, _dp]
+    L.or_apply_advdiff_up3.argtypes = [C.c_int, C.c_int, C.c_double, C.c_double, _dp, _dp]
+    L.or_burgers_up3_f.argtypes = [C.c_int, C.c_int, C.c_double, C.c_double, _dp, _dp]
+    L.or_burgers_up3_J.argtypes = [C.c_int, C.c_int, C.c_double, C.c_double, _dp, _dp, _dp]
+    L.or_power_iteration.argtypes = [C.c_int, C.c_int, C.c_int, C.c_double, C.c_double, _dp, _dp,
+                                     C.c_int, _dp, _ip]
+    L.or_leja_phi.argtypes = [C.c_int, C.c_int, C.c_int, C.c_double, C.c_double, _dp, C.c_int, _dp,
+                              C.c_double, C.c_double, C.c_double, C.c_double, C.c_double, _dp, C.c_int,
+                              _dp, _ip]
+    L.or_ros_eu.argtypes = [C.c_int, C.c_int, C.c_int, C.c_double, C.c_double, _dp, C.c_double,
+                            C.c_double, C.c_double, C.c_double, C.c_double, _dp, C.c_int, _dp, _ip]
+    L.or_exprb32.argtypes = [C.c_int, C.c_int, C.c_int, C.c_double, C.c_double, _dp, C.c_double,
+                             C.c_double, C.c_double, C.c_double, C.c_double, _dp, C.c_int, _dp, _dp,
+                             _dp, _ip]
+    L.or_leja_phi_given.argtypes = [C.c_int, C.c_int, C.c_int, C.c_double, C.c_double, _dp, _dp, C.c_double,
+                                    C.c_double, C.c_double, C.c_double, _dp, _dp, C.c_int, _dp, _ip, _dp,
+                                    C.c_int]
+    L.or_leja_phi_vertical.argtypes = [C.c_int, C.c_int, C.c_int, C.c_double, C.c_double, _dp, C.c_int,
+                                       C.c_int, _dp, _dp, C.c_double, C.c_double, C.c_double, C.c_double,
+                                       C.c_double, _dp, C.c_int, _dp, _ip]
+    L.or_ros_eu_src.argtypes = [C.c_int, C.c_int, C.c_int, C.c_double, C.c_double, _dp, _dp,
+                                C.c_double, C.c_double, C.c_double, C.c_double, C.c_double, _dp, C.c_int,
+                                _dp, _ip]
+    L.or_exprb32_src.argtypes = [C.c_int, C.c_int, C.c_int, C.c_double, C.c_double, _dp, _dp,
+                                 C.c_double, C.c_double, C.c_double, C.c_double, C.c_double, _dp, C.c_int,
+                                 _dp, _dp, _dp, _ip]
+    L.or_controller.restype = C.c_double
+    L.or_controller.argtypes = [C.c_double, C.c_double, C.c_double]
+    L.or_integrate_exprb32.argtypes = [C.c_int, C.c_int, C.c_int, C.c_double, C.c_double, _dp, _dp,
+                                       C.c_double, C.c_double, C.c_double, C.c_double, _dp, C.c_int,
+                                       C.c_int, _ip, _ip, C.POINTER(C.c_longlong), _dp, _dp]
+    L.or_integrate_exprb32_log.argtypes = L.or_integrate_exprb32.argtypes + [_dp, C.c_int]
+    L.or_fd_jv.argtypes = [C.c_int, C.c_int, C.c_int, C.c_double, C.c_double, _RHS, C.c_void_p, C.c_double,
+                           _dp, _dp, _dp]
+    L.or_power_iteration_fd.argtypes = [C.c_int, C.c_int, C.c_int, C.c_double, C.c_double, _RHS,
+                                        C.c_void_p, C.c_double, _dp, _dp, C.c_int, _dp, _ip]
+    L.or_leja_phi_fd.argtypes = [C.c_int, C.c_int, C.c_int, C.c_double, C.c_double, _RHS, C.c_void_p,
+                                 C.c_double, _dp, C.c_int, _dp, C.c_double, C.c_double, C.c_double,
+                                 C.c_double, C.c_double, _dp, C.c_int, _dp, _ip]
+    L.or_ros_eu_fd.argtypes = [C.c_int, C.c_int, C.c_int, C.c_double, C.c_double, _RHS, C.c_void_p,
+                               C.c_double, _dp, C.c_double, C.c_double, C.c_double, C.c_double, C.c_double,
+                               _dp, C.c_int, _dp, _ip]
+    L.or_exprb32_fd.argtypes = [C.c_int, C.c_int, C.c_int, C.c_double, C.c_double, _RHS, C.c_void_p,
+                                C.c_double, _dp, C.c_double, C.c_double, C.c_double, C.c_double,
+                                C.c_double, _dp, C.c_int, _dp, _dp, _dp, _ip]
+    return L
 
 
 def _f64(a):
@@ -206,12 +223,12 @@ def burgers_J(nx, ny, nu, u, v) -> np.ndarray:
     return out
 
 
-def power_iteration(kind, nx, ny, nu, a, u, v0, max_iters=10):
+def power_iteration(kind, nx, ny, nu, a, u, v0, max_iters=10, parallel=False):
     v0 = _f64(v0)
     u = _f64(u) if u is not None else None
     rho = np.zeros(1)
     it = C.c_int(0)
-    st = lib().or_power_iteration(kind, nx, ny, nu, a, _p(u), _p(v0), max_iters, _p(rho), C.byref(it))
+    st = lib(parallel).or_power_iteration(kind, nx, ny, nu, a, _p(u), _p(v0), max_iters, _p(rho), C.byref(it))
     return float(rho[0]), int(it.value), st
 
 
@@ -304,25 +321,48 @@ def leja_coeffs_mp(l: int, h: float, c: float, gamma: float, xi, dps: int | None
         return np.array([float(v) for v in _divdiff_rows(d, x)])
 
 
-def leja_phi_mp(kind, nx, ny, nu, a, u, l, w, c, gamma, h, rtol, atol, xi, dps=None, k0=128):
+def leja_phi_mp(kind, nx, ny, nu, a, u, l, w, c, gamma, h, rtol, atol, xi, dps=None, k0=128, want_growth=False,
+                regroup=False):
     """leja_phi with the Newton coefficients from leja_coeffs_mp.  Row j of
     the recursion needs only rows < j, so the coefficients are formed for
     the first k0 points and the table is doubled (up to len(xi)) while the
     loop runs out of coefficients; a run that stops inside a shorter table
-    is the run with the full one.  Returns (out, iters, status)."""
+    is the run with the full one.  Returns (out, iters, status), plus with
+    want_growth the basis growth max_m ||y_m|| / ||y_0||.  regroup: the
+    diffusion-advection operator evaluated per neighbour (another rounding
+    order of the same operator, see rounding_sensitivity)."""
     w = _f64(w)
     xi = _f64(xi)
     u = _f64(u) if u is not None else None
     out = np.zeros_like(w)
     it = C.c_int(0)
+    growth = np.zeros(1)
     K = min(k0, len(xi))
     while True:
         d = leja_coeffs_mp(l, h, c, gamma, xi[:K], dps)
         st = lib().or_leja_phi_given(kind, nx, ny, nu, a, _p(u), _p(w), c, gamma, rtol, atol, _p(xi), _p(d), K,
-                                     _p(out), C.byref(it))
+                                     _p(out), C.byref(it), _p(growth), 1 if regroup else 0)
         if st != E_NOCONV or K >= len(xi):
+            if want_growth:
+                return out, int(it.value), st, float(growth[0])
             return out, int(it.value), st
         K = min(2 * K, len(xi))
+
+
+def rounding_sensitivity(nx, ny, nu, a, l, w, c, gamma, h, rtol, atol, xi, ref=None):
+    """How far the diffusion-advection Leja result moves when the operator
+    is evaluated in another order: the relative L2 difference of the runs
+    with the stencil grouped per difference quotient (the oracle's own form)
+    and per neighbour.  Both are exact evaluations of the same operator up
+    to rounding, so no implementation of the method can be expected to agree
+    with the oracle much more closely than this on the given problem.
+    ref: the first run's result, if already computed."""
+    if ref is None:
+        ref, _, _ = leja_phi_mp(ADVDIFF, nx, ny, nu, a, None, l, w, c, gamma, h, rtol, atol, xi)
+    alt, _, st = leja_phi_mp(ADVDIFF, nx, ny, nu, a, None, l, w, c, gamma, h, rtol, atol, xi, regroup=True)
+    if st != OK:
+        return float("inf")
+    return float(np.linalg.norm(alt - ref) / np.linalg.norm(ref))
 
 
 def leja_phi_vertical(kind, nx, ny, nu, a, u, l, alphas, w, c, gamma, h, rtol, atol, xi):
@@ -339,14 +379,15 @@ def leja_phi_vertical(kind, nx, ny, nu, a, u, l, alphas, w, c, gamma, h, rtol, a
     return out, int(it.value), st
 
 
-def ros_eu(kind, nx, ny, nu, a, u, c, gamma, h, rtol, atol, xi, source=None):
-    """Rosenbrock-Euler step; source: optional time-independent S added to f."""
+def ros_eu(kind, nx, ny, nu, a, u, c, gamma, h, rtol, atol, xi, source=None, parallel=False):
+    """Rosenbrock-Euler step; source: optional time-independent S added to f;
+    parallel: the OpenMP build (CPU-baseline timing only)."""
     u = _f64(u)
     xi = _f64(xi)
     S = _f64(source) if source is not None else None
     out = np.zeros_like(u)
     it = C.c_int(0)
-    st = lib().or_ros_eu_src(kind, nx, ny, nu, a, _p(u), _p(S) if S is not None else None, c, gamma, h, rtol, atol,
+    st = lib(parallel).or_ros_eu_src(kind, nx, ny, nu, a, _p(u), _p(S) if S is not None else None, c, gamma, h, rtol, atol,
                              _p(xi), len(xi), _p(out), C.byref(it))
     return out, int(it.value), st
 

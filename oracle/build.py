@@ -21,16 +21,25 @@ def needs_quadmath() -> bool:
     return platform.machine() not in ("aarch64", "arm64")
 
 
+LIB_OMP = os.path.join(HERE, "_oracle_omp.so")
+
+
 def build(force: bool = False, openmp: bool = False) -> str:
-    if not force and os.path.exists(LIB) and os.path.getmtime(LIB) >= os.path.getmtime(SRC):
-        return LIB
-    cmd = ["gcc", "-std=c11", "-O2", "-ffp-contract=off", "-fPIC", "-shared", SRC, "-o", LIB + ".tmp", "-lm"]
+    """The single-threaded parity library (_oracle.so), or with openmp=True
+    the same source with its grid loops on all host cores (_oracle_omp.so,
+    -O3 -fopenmp), which only times the CPU baseline."""
+    lib = LIB_OMP if openmp else LIB
+    if not force and os.path.exists(lib) and os.path.getmtime(lib) >= os.path.getmtime(SRC):
+        return lib
+    opt = ["-O3", "-fopenmp"] if openmp else ["-O2"]
+    cmd = ["gcc", "-std=c11", *opt, "-ffp-contract=off", "-fPIC", "-shared", SRC, "-o", lib + ".tmp", "-lm"]
     if needs_quadmath():
         cmd.append("-lquadmath")
     subprocess.run(cmd, check=True)
-    os.replace(LIB + ".tmp", LIB)
-    return LIB
+    os.replace(lib + ".tmp", lib)
+    return lib
 
 
 if __name__ == "__main__":
     print(build(force="--force" in sys.argv))
+    print(build(force="--force" in sys.argv, openmp=True))

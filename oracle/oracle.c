@@ -7,8 +7,8 @@
  * code, header, table or constant with it, and fails if its own extension is
  * missing.
  *
- * Plain, slow, obviously correct: single-threaded loops in the order the
- * paper states the algorithm, fp64 for vectors, IEEE binary128 for the scalar
+ * Plain, slow, obviously correct: loops in the order the paper states the
+ * algorithm, fp64 for vectors, IEEE binary128 for the scalar
  * phi functions and the Newton divided differences.  Each function names the
  * passage of Deka, Moriggl, Einkemmer, "LeXInt: GPU-accelerated exponential
  * integrators package" (arXiv 2310.08344) that it follows.
@@ -30,6 +30,12 @@
  *    f either the problem kind's own or a caller's function (Sec. 2: the
  *    right-hand side takes an input and an output pointer).
  */
+/*
+ * Threads: the parity build (oracle/_oracle.so) is single-threaded, so every
+ * sum runs in index order.  The same source compiled with -fopenmp
+ * (oracle/_oracle_omp.so) splits the grid loops and norms over the host's
+ * cores; that build only times the CPU baseline of the benchmark.
+ */
 #include <float.h>
 #include <math.h>
 #include <stdlib.h>
@@ -48,6 +54,19 @@ typedef __float128 qreal; /* libquadmath on x86-64 */
 
 enum { OR_OK = 0, OR_E_INVAL = 1, OR_E_NOMEM = 2, OR_E_NOCONV = 4, OR_E_NONFINITE = 5 };
 enum { OR_ADVDIFF = 0, OR_BURGERS = 1, OR_ADVDIFF_UP3 = 2, OR_BURGERS_UP3 = 3 };
+
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+/* Threads the grid loops use (1 in the parity build). */
+int or_threads(void) {
+#ifdef _OPENMP
+  return omp_get_max_threads();
+#else
+  return 1;
+#endif
+}
 
 int or_qreal_mant_dig(void) {
 #if LDBL_MANT_DIG == 113
@@ -223,6 +242,7 @@ static int wrap(int i, int n) { return i < 0 ? i + n : (i >= n ? i - n : i); }
  * operator of Sec. 3, Problem I, with this build's coefficients). */
 void or_apply_advdiff(int nx, int ny, double nu, double a, const double* v, double* out) {
   double dx = 1.0 / nx, dy = 1.0 / ny;
+#pragma omp parallel for
   for (int j = 0; j < ny; ++j) {
     int jn = wrap(j + 1, ny), js = wrap(j - 1, ny);
     for (int i = 0; i < nx; ++i) {
@@ -276,7 +296,7 @@ void or_burgers_J(int nx, int ny, double nu, const double* u, const double* v, d
 }
 
 /* ------------------------------------------------------------------------ */
-/* The paper's own discretisation (Sec. 4): periodic [-1,1]^2 (spacing       */
+/* The paper's own discretisation (Sec. 3): periodic [-1,1]^2 (spacing       */
 /* 2/nx, 2/ny), the Laplacian by second-order central differences and the    */
 /* gradient by the third-order upwind-biased scheme.  For a term +a v_x with */
 /* a > 0 the characteristics run toward -x, so the upwind side is +x:        */
@@ -327,7 +347,7 @@ static void lap_pm1(int nx, int ny, double nu, const double* v, double* out) {
   }
 }
 
-/* A v = nu (v_xx + v_yy) + a (v_x + v_y), upwind gradient (Problem I, Sec. 4,
+/* A v = nu (v_xx + v_yy) + a (v_x + v_y), upwind gradient (Problem I, Sec. 3, Eq. 3,
  * with nu the diffusion and a the advection coefficient). */
 void or_apply_advdiff_up3(int nx, int ny, double nu, double a, const double* v, double* out) {
   long n = (long)nx * ny;
@@ -340,7 +360,7 @@ void or_apply_advdiff_up3(int nx, int ny, double nu, double a, const double* v, 
   free(g);
 }
 
-/* f(u) = nu (u_xx + u_yy) + (a/2) ((u^2)_x + (u^2)_y)   (Problem III, Sec. 4,
+/* f(u) = nu (u_xx + u_yy) + (a/2) ((u^2)_x + (u^2)_y)   (Problem III, Sec. 3, Eq. 5,
  * the flux form; the upwind side follows the sign of a, i.e. the reading
  * takes u > 0 as in the paper's initial state). */
 void or_burgers_up3_f(int nx, int ny, double nu, double a, const double* u, double* out) {
@@ -371,7 +391,7 @@ void or_burgers_up3_J(int nx, int ny, double nu, double a, const double* u, cons
 
 /* The operator the Leja basis multiplies by: A for diffusion-advection,
  * J(u) for Burgers.  S (may be NULL): a time-independent source added to
- * the right-hand side (Problem II of Sec. 4); it does not enter J. */
+ * the right-hand side (Problem II of Sec. 3, Eq. 4); it does not enter J. */
 typedef void (*or_rhs_fn)(const double* in, double* out, void* user);
 
 typedef struct {
@@ -382,6 +402,8 @@ typedef struct {
   or_rhs_fn f;   /* caller's right-hand side, or NULL for the kind's own */
   void* user;    /* passed to f */
   double eps0;   /* > 0: Jacobian action by central finite differences */
+  int regroup;   /* 1: the diffusion-advection operator with its terms grouped
+                    per neighbour (same operator, other rounding) */
 } or_op;
 
 static void op_rhs(const or_op* op, const double* u, double* out);
@@ -415,8 +437,33 @@ static void op_apply_fd(const or_op* op, const double* v, double* out) {
   free(fp);
 }
 
+/* A v for the diffusion-advection operator with one weight per neighbour,
+ *   (A v)_ij = wE v_E + wW v_W + wN v_N + wS v_S + wC v_ij,
+ *   wE = nu/dx^2 + a/(2dx), wW = nu/dx^2 - a/(2dx), wC = -2nu/dx^2 - 2nu/dy^2
+ * (wN, wS likewise in y): the same operator as or_apply_advdiff in another
+ * evaluation order.  The difference of a Leja run in the two orders shows
+ * how strongly a problem amplifies rounding (the Newton basis grows where
+ * the spectrum reaches far off the real focal interval). */
+static void apply_advdiff_per_neighbour(int nx, int ny, double nu, double a, const double* v, double* out) {
+  double dx = 1.0 / nx, dy = 1.0 / ny;
+  double wE = nu / (dx * dx) + a / (2.0 * dx), wW = nu / (dx * dx) - a / (2.0 * dx);
+  double wN = nu / (dy * dy) + a / (2.0 * dy), wS = nu / (dy * dy) - a / (2.0 * dy);
+  double wC = -2.0 * nu / (dx * dx) - 2.0 * nu / (dy * dy);
+#pragma omp parallel for
+  for (int j = 0; j < ny; ++j) {
+    int jn = wrap(j + 1, ny), js = wrap(j - 1, ny);
+    for (int i = 0; i < nx; ++i) {
+      int ie = wrap(i + 1, nx), iw = wrap(i - 1, nx);
+      out[idx(nx, i, j)] = wE * v[idx(nx, ie, j)] + wW * v[idx(nx, iw, j)] + wN * v[idx(nx, i, jn)] +
+                           wS * v[idx(nx, i, js)] + wC * v[idx(nx, i, j)];
+    }
+  }
+}
+
 static void op_apply(const or_op* op, const double* v, double* out) {
-  if (op->eps0 > 0.0)
+  if (op->regroup && op->kind == OR_ADVDIFF)
+    apply_advdiff_per_neighbour(op->nx, op->ny, op->nu, op->a, v, out);
+  else if (op->eps0 > 0.0)
     op_apply_fd(op, v, out);
   else if (op->kind == OR_BURGERS)
     or_burgers_J(op->nx, op->ny, op->nu, op->u, v, out);
@@ -450,6 +497,7 @@ static void op_rhs(const or_op* op, const double* u, double* out) {
 /* ||x|| = ||x||_2 / sqrt(N) (Sec. 2.2: l2 norm normalised to sqrt(N)). */
 static double nrm(const double* x, long n) {
   double s = 0.0;
+#pragma omp parallel for reduction(+ : s)
   for (long k = 0; k < n; ++k) s += x[k] * x[k];
   return sqrt(s / (double)n);
 }
@@ -471,6 +519,7 @@ static int power_core(const or_op* opp, const double* v0, int max_iters, double*
     op_apply(&op, v, w);
     double nw = nrm(w, n), nv = nrm(v, n);
     rho = nw / nv;
+#pragma omp parallel for
     for (long q = 0; q < n; ++q) v[q] = w[q] / nw;
     if (k > 1 && fabs(rho - rho_prev) <= 1e-2 * rho) break;
     rho_prev = rho;
@@ -498,25 +547,34 @@ int or_power_iteration(int kind, int nx, int ny, double nu, double a, const doub
 /*   stop when |d_{m+1}| ||y_{m+1}|| <= rtol ||p_{m+1}|| + atol.             */
 /* ------------------------------------------------------------------------ */
 
-/* The loop itself, for Newton coefficients d[0..K) already formed. */
+/* The loop itself, for Newton coefficients d[0..K) already formed.
+ * growth (may be NULL): receives max_m ||y_m|| / ||y_0||, the growth of the
+ * Newton basis, which sets how far rounding in the recursion is amplified. */
 static int leja_loop_core(const or_op* op, const double* w, double c, double gamma, double rtol, double atol,
-                          const double* xi, const double* d, int K, double* out, int* iters) {
+                          const double* xi, const double* d, int K, double* out, int* iters, double* growth) {
   long n = (long)op->nx * op->ny;
   if (K < 2) return OR_E_INVAL;
   double* y = (double*)malloc(sizeof(double) * (size_t)n);
   double* t = (double*)malloc(sizeof(double) * (size_t)n);
   if (!y || !t) { free(y); free(t); return OR_E_NOMEM; }
+#pragma omp parallel for
   for (long q = 0; q < n; ++q) {
     y[q] = w[q];
     out[q] = d[0] * w[q];
   }
   int status = OR_E_NOCONV;
   *iters = K - 1;
+  const double y0n = nrm(w, n);
+  double ymax = y0n;
   for (int m = 0; m + 1 < K; ++m) {
     op_apply(op, y, t);
+#pragma omp parallel for
     for (long q = 0; q < n; ++q) y[q] = (t[q] - c * y[q]) / gamma - xi[m] * y[q];
+#pragma omp parallel for
     for (long q = 0; q < n; ++q) out[q] = out[q] + d[m + 1] * y[q];
-    double e = fabs(d[m + 1]) * nrm(y, n);
+    const double yn = nrm(y, n);
+    if (yn > ymax) ymax = yn;
+    double e = fabs(d[m + 1]) * yn;
     double pn = nrm(out, n);
     if (!isfinite(e) || !isfinite(pn)) {
       *iters = m + 1;
@@ -529,6 +587,7 @@ static int leja_loop_core(const or_op* op, const double* w, double c, double gam
       break;
     }
   }
+  if (growth) *growth = y0n > 0.0 ? ymax / y0n : 1.0;
   free(y);
   free(t);
   return status;
@@ -541,7 +600,7 @@ static int leja_phi_core(const or_op* op, int l, const double* w, double c, doub
   double* d = (double*)malloc(sizeof(double) * (size_t)K);
   if (!d) return OR_E_NOMEM;
   or_leja_coeffs(l, h, c, gamma, xi, K, d);
-  int st = leja_loop_core(op, w, c, gamma, rtol, atol, xi, d, K, out, iters);
+  int st = leja_loop_core(op, w, c, gamma, rtol, atol, xi, d, K, out, iters, NULL);
   free(d);
   return st;
 }
@@ -558,13 +617,16 @@ int or_leja_phi(int kind, int nx, int ny, double nu, double a, const double* u, 
  * f(xi) = phi_l(h (c + gamma xi)) at the points xi, e.g. divided differences
  * formed by the same recursion at a precision above binary128, for the
  * regime where binary128 reaches its rounding floor before the series
- * converges.  Stops with OR_E_NOCONV after K - 1 iterations. */
+ * converges.  Stops with OR_E_NOCONV after K - 1 iterations; growth (may be
+ * NULL) receives max_m ||y_m|| / ||y_0||; regroup = 1 evaluates the
+ * diffusion-advection operator per neighbour (apply_advdiff_per_neighbour). */
 int or_leja_phi_given(int kind, int nx, int ny, double nu, double a, const double* u, const double* w,
                       double c, double gamma, double rtol, double atol, const double* xi, const double* d, int K,
-                      double* out, int* iters) {
+                      double* out, int* iters, double* growth, int regroup) {
   if (nx <= 0 || ny <= 0 || gamma == 0.0 || !d) return OR_E_INVAL;
   or_op op = {kind, nx, ny, nu, a, u};
-  return leja_loop_core(&op, w, c, gamma, rtol, atol, xi, d, K, out, iters);
+  op.regroup = regroup;
+  return leja_loop_core(&op, w, c, gamma, rtol, atol, xi, d, K, out, iters, growth);
 }
 
 /* ------------------------------------------------------------------------ */
@@ -632,7 +694,7 @@ int or_leja_phi_vertical(int kind, int nx, int ny, double nu, double a, const do
 /*   u+ = u + phi_1(h J(u)) h f(u).                                          */
 /* ------------------------------------------------------------------------ */
 
-/* With a source (Problem II, Sec. 4): f(u) = A u + S, so the step is
+/* With a source (Problem II, Sec. 3, Eq. 4): f(u) = A u + S, so the step is
  * u+ = u + phi_1(h A) h (A u + S). */
 static int ros_eu_core(const or_op* opp, const double* u, double c, double gamma, double h, double rtol,
                        double atol, const double* xi, int K, double* u_out, int* iters) {
@@ -642,8 +704,10 @@ static int ros_eu_core(const or_op* opp, const double* u, double c, double gamma
   double* p = (double*)malloc(sizeof(double) * (size_t)n);
   if (!f_u || !p) { free(f_u); free(p); return OR_E_NOMEM; }
   op_rhs(&op, u, f_u);
+#pragma omp parallel for
   for (long q = 0; q < n; ++q) f_u[q] = h * f_u[q];
   int st = leja_phi_core(&op, 1, f_u, c, gamma, h, rtol, atol, xi, K, p, iters);
+#pragma omp parallel for
   for (long q = 0; q < n; ++q) u_out[q] = u[q] + p[q];
   free(f_u);
   free(p);

@@ -422,7 +422,7 @@ static __global__ void df_output_kernel(long long n, const float2* __restrict__ 
 // result for the scaling of the Leja loop that follows.  wf: hi/lo of the
 // five weights h*(wE, wW, wN, wS, wC).  Points whose inputs are outside the
 // float range use double arithmetic.  src (may be NULL): a time-independent
-// source, added as h * src in double (problem with sources, Sec. 4).
+// source, added as h * src in double (problem with sources, Sec. 3, Eq. 4).
 struct RhsWeights {
   float wf[10];   // hi/lo of h*(wE, wW, wN, wS, wC)
   double wd[5];   // the same weights in double

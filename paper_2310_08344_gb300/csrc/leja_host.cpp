@@ -141,9 +141,13 @@ int leja_points(int K, double* xi) {
 int leja_coeff_count(double h, double c, double gamma, int K) {
   // |d_j| <= (h|gamma|)^j / j! * e^{max(0, h(c + 2|gamma|))}: the mean-value
   // form of the divided difference with |phi_l^{(j)}(z)| <= e^{max(z,0)}.
-  // Coefficients beyond the first J with that bound below 1e-40 are
-  // negligible for any tolerance; the loop cap is J.
-  double hg = std::fabs(h * gamma);
+  // The Newton basis has norm O(1) per step only for a spectrum on the
+  // focal interval (capacity 1); where the spectrum reaches off the real
+  // axis (advection-dominated grids) it grows geometrically, so the bound is
+  // taken with twice h|gamma|: coefficients beyond the first J with
+  // (2 h|gamma|)^J / J! * e^{...} below 1e-40 are negligible for any
+  // tolerance; the loop cap is J.
+  double hg = 2.0 * std::fabs(h * gamma);
   double zplus = std::max(0.0, h * (c + 2.0 * std::fabs(gamma)));
   double logb = zplus;
   int J = 1;

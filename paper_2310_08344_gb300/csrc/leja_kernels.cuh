@@ -424,7 +424,7 @@ __device__ __forceinline__ void neighbours(const Geo& g, long long q, long long&
 
 // h f(u) into f_out; for Burgers also (u_x + u_y) into s_out.  f_out may be
 // NULL (only s is wanted).  src (may be NULL): a time-independent source
-// added to f (the diffusion-advection problem with sources, Sec. 4).
+// added to f (the diffusion-advection problem with sources, Sec. 3, Eq. 4).
 template <int KIND>
 __global__ void rhs_kernel(Geo g, double nu, double a, double h, const double* __restrict__ u,
                            double* __restrict__ f_out, double* __restrict__ s_out,

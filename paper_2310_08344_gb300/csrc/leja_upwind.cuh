@@ -1,4 +1,4 @@
-// The paper's own discretisation (Sec. 4): periodic [-1,1)^2 with spacing
+// The paper's own discretisation (Sec. 3): periodic [-1,1)^2 with spacing
 // 2/nx, 2/ny, the Laplacian by second-order central differences and the
 // gradient by the third-order upwind-biased scheme.  Along one axis, for a
 // term +a v_x with a > 0 (characteristics toward -x, upwind side +x):

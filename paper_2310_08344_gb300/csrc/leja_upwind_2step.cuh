@@ -1,6 +1,6 @@
 // Two Leja iterations per pass (temporal blocking) for the paper's upwind
 // diffusion-advection operator, float-float form (Problems I and II of
-// Sec. 4; the stencil and its weights are those of leja_upwind.cuh).
+// Sec. 3; the stencil and its weights are those of leja_upwind.cuh).
 //
 // One launch reads y_m and p_m once and writes y_{m+2} and p_{m+2}; y_{m+1}
 // is recomputed on the rows and columns the second step needs and never

@@ -370,7 +370,7 @@ static __global__ void __launch_bounds__(kThreadsPerBlock)
 }
 
 // ---------------------------------------------------------------------------
-// Vertical loops on the paper's upwind operators (periodic [-1,1)^2, Sec. 4),
+// Vertical loops on the paper's upwind operators (periodic [-1,1)^2, Sec. 3),
 // one thread per point with the seven stencil points through the caches, as
 // the one-polynomial point-wise kernels: FP64 / mixed basis (T), and
 // float-float with both operators (Burgers: the seven point weights from

@@ -278,7 +278,7 @@ __global__ void __launch_bounds__(kThreadsPerBlock)
 // nu Lap u + a (u_x + u_y); Burgers f = nu Lap u - u (u_x + u_y).  Upwind
 // kinds on [-1,1)^2 (spacing 2/n): the third-order upwind-biased gradient,
 // for a term +a v_x with side s = sign(a): |a| (-v_{i+2s} + 6 v_{i+s} - 3 v_i
-// - 2 v_{i-s}) / (6 dx); Burgers flux form nu Lap u + (a/2) D(u^2) (Sec. 4).
+// - 2 v_{i-s}) / (6 dx); Burgers flux form nu Lap u + (a/2) D(u^2) (Sec. 3, Eq. 5).
 // ---------------------------------------------------------------------------
 
 struct BuiltinRhs {

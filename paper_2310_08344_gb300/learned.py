@@ -3,84 +3,103 @@
 The network (see include/lexgb.h, mlp_*) maps the features of an attempted
 EXPRB32 step -- log(rho h), log(h / dt_CFL), iters / 100, log10(err / tol),
 ||u|| -- to log(h_next / h) and log(iters predicted).  Labels come from the
-method itself: at a state u with current step h, the thirteen steps
-h_j = h 2^(j/2), j = -4..8 (a quarter to sixteen times h), are each
-attempted in increasing order until one exceeds the target below; the
-label step h* is where
-the measured error crosses 0.8 tol (log-log interpolation between the two
-neighbouring attempts; the largest attempt if all stay below, the smallest if
-none does).  That is the largest step the error test accepts with a margin,
-hence the one with the most simulated time per Leja iteration, since the
-iteration count grows sublinearly in h.  Every step of the computation (power bounds, EXPRB32
-steps, the network's forward and backward passes, Adam) runs in the CUDA
-library; this module only orchestrates the calls and keeps the samples.
+method itself: at a state u with current step h, the nine steps
+h_j = h 2^(j/2), j = -4..4, are candidates, and the label is the candidate
+with the most simulated time per Leja iteration (largest h_j / iters_j)
+among those whose error estimate stays below 0.8 tol.  To save work the
+candidates are attempted from h upward until one fails the bound (larger
+steps only have larger errors), or from h downward until one passes it;
+the smaller, unattempted candidates are passed over because the Leja count
+grows sublinearly in h, so h / iters grows with h -- `exhaustive=True`
+attempts all nine instead, which is how that shortcut is checked.  Every
+step of the computation (power bounds, EXPRB32 steps, the network's forward
+and backward passes, Adam) runs in the CUDA library; this module only
+orchestrates the calls and keeps the samples.
 """
 from __future__ import annotations
 
 import math
+import os
 
 import numpy as np
 
 from . import binding as B
 
 FEATURES = ("log(rho h)", "log(h/dt_CFL)", "iters/100", "log10(err/tol)", "||u||")
+CANDIDATES = tuple(range(-4, 5))  # h_j = h 2^(j/2)
+TARGET = 0.8  # the label's error bound, as a fraction of tol
 
 
 def _norm_u(u):
     return float(u.norm().item() / math.sqrt(u.numel()))
 
 
-def generate_samples(n, nu, u0_list, v0, tol, leja_tol, steps_per_traj, dt_cfl, rng, stream=None, h_scale=None):
+def label_state(ctx, u, v0, h, tol, leja_tol, lo, his, exhaustive=False):
+    """Attempt the candidate steps at state u.  Returns (rho, attempts, best)
+    with attempts[j] = (h_j, err_j, iters_j) for the attempted candidates
+    (a dict keyed by j) and best the j of the label, or None when no
+    attempted candidate meets the bound."""
+    st, rho, _ = B.power_bound(ctx, u, v0, 10)
+    if st != 0:
+        return None, {}, None
+    c, g = B.spectral_interval(rho)
+    target = TARGET * tol
+    att = {}
+
+    def attempt(j):
+        hj = h * 2.0 ** (j / 2.0)
+        st_, err, it = B.expint_step(ctx, u, lo, his[j], c, g, hj, leja_tol, leja_tol)
+        att[j] = (hj, err if st_ == 0 else float("inf"), it)
+        return att[j][1] <= target
+
+    if exhaustive:
+        for j in CANDIDATES:
+            attempt(j)
+    elif attempt(0):
+        for j in CANDIDATES[CANDIDATES.index(0) + 1:]:
+            if not attempt(j):
+                break
+    else:
+        for j in reversed(CANDIDATES[:CANDIDATES.index(0)]):
+            if attempt(j):
+                break
+    ok = [j for j in att if att[j][1] <= target]
+    best = max(ok, key=lambda j: att[j][0] / max(att[j][2], 1)) if ok else None
+    return rho, att, best
+
+
+def generate_samples(n, nu, u0_list, v0, tol, leja_tol, steps_per_traj, dt_cfl, rng, stream=None, h_scale=None,
+                     precision=None, exhaustive=False):
     """Samples (X [S,5], Y [S,2]) along trajectories of viscous Burgers
     started from each state of u0_list (torch CUDA float64 vectors)."""
     import torch
 
-    ctx = B.leja_setup(n, n, nu, 0.0, B.BURGERS, B.FP64, B.EXPRB32, 1000, stream)
-    js = list(range(-4, 9))
-    j0 = js.index(0)
+    prec = B.FP64 if precision is None else precision
+    ctx = B.leja_setup(n, n, nu, 0.0, B.BURGERS, prec, B.EXPRB32, 1000, stream)
     lo = torch.empty_like(u0_list[0])
-    his = [torch.empty_like(u0_list[0]) for _ in js]
+    his = {j: torch.empty_like(u0_list[0]) for j in CANDIDATES}
     X, Y = [], []
     for u0 in u0_list:
         u = u0.clone()
         # current steps from ~dt_CFL (a cautious start) to 100 dt_CFL
         h = dt_cfl * 50.0 * (2.0 ** rng.uniform(-6.0, 1.0) if h_scale is None else h_scale)
         for _ in range(steps_per_traj):
-            st, rho, _ = B.power_bound(ctx, u, v0, 10)
-            if st != 0:
+            rho, att, best = label_state(ctx, u, v0, h, tol, leja_tol, lo, his, exhaustive)
+            if rho is None or 0 not in att:
                 break
-            c, g = B.spectral_interval(rho)
-            target = 0.8 * tol
-            res = []
-            for k, j in enumerate(js):
-                hj = h * 2.0 ** (j / 2.0)
-                st, err, it = B.expint_step(ctx, u, lo, his[k], c, g, hj, leja_tol, leja_tol)
-                e = err if st == 0 else float("inf")
-                res.append((hj, e, it))
-                if j >= 0 and not (e <= target):
-                    break  # past the target: larger steps only cost more Leja iterations
-            h0, err0, it0 = res[j0]
-            best = 0
-            hb, ib = res[0][0], res[0][2]
-            for k in range(len(res)):
-                if res[k][1] <= target:
-                    best = k
-            if res[best][1] <= target:
-                hb, ib = res[best][0], res[best][2]
-                if best < len(res) - 1 and math.isfinite(res[best + 1][1]) and res[best + 1][1] > target and \
-                        res[best][1] > 0:
-                    e0, e1 = math.log(res[best][1]), math.log(res[best + 1][1])
-                    f = (math.log(target) - e0) / (e1 - e0)
-                    hb = math.exp(math.log(res[best][0]) + f * (math.log(res[best + 1][0]) - math.log(res[best][0])))
-                    ib = res[best][2] + f * (res[best + 1][2] - res[best][2])
-            x = [math.log(rho * h0), math.log(h0 / dt_cfl), it0 / 100.0,
-                 math.log10(max(err0, 1e-300) / tol), _norm_u(u)]
+            h0, err0, it0 = att[0]
+            x = [math.log(rho * h0), math.log(h0 / dt_cfl), it0 / 100.0, math.log10(max(err0, 1e-300) / tol),
+                 _norm_u(u)]
+            if best is None:
+                # even a quarter of h fails: label the smallest candidate
+                best = min(att)
+            hb, eb, ib = att[best]
             if all(math.isfinite(v) for v in x):
                 X.append(x)
                 Y.append([math.log(hb / h0), math.log(max(ib, 1))])
-            if res[best][1] <= tol:
+            if eb <= tol:
                 u.copy_(his[best])
-            h = res[best][0] * 2.0 ** rng.uniform(-1.0, 1.0)
+            h = hb * 2.0 ** rng.uniform(-1.0, 1.0)
             if rng.uniform() < 0.2:  # now and then a cautious step again
                 h = dt_cfl * 50.0 * 2.0 ** rng.uniform(-6.0, 0.0)
     ctx.close()

@@ -2,8 +2,10 @@
 
 Instances of uneven sizes advance together in one launch per iteration; each
 must give the oracle's result for its own problem (relative L2 <= 1e-10,
-iterations +-1) and the oracle's status, including an advection-dominated
-instance where real Leja interpolation diverges (both report a failure)."""
+iterations +-1) and the oracle's status.  Advection-dominated instances
+(4 nu n / a < 2, where the Newton basis grows geometrically) are judged by
+the oracle with divided differences above binary128 precision
+(oracle.leja_phi_mp), as is the full 256-instance batched workload."""
 import numpy as np
 import pytest
 
@@ -63,28 +65,88 @@ def test_batch_matches_oracle(lx, sizes):
         cs.append(c)
         gs.append(g)
         hs.append(h)
-        refs.append(oracle.leja_phi(oracle.ADVDIFF, nx, ny, nu, a, None, 0, u0, c, g, h, TOL, TOL, xi))
+        ref = oracle.leja_phi_mp(oracle.ADVDIFF, nx, ny, nu, a, None, 0, u0, c, g, h, TOL, TOL, xi)
+        delta = oracle.rounding_sensitivity(nx, ny, nu, a, 0, u0, c, g, h, TOL, TOL, xi, ref=ref[0])
+        import fourier
+
+        exact = fourier.phi_apply(0, nx, ny, nu, a, h, u0)
+        e_ex_o = float(np.linalg.norm(ref[0] - exact) / np.linalg.norm(exact))
+        refs.append(ref + (delta, e_ex_o, exact))
     for rep in range(2):  # the second call reuses the cached coefficients
         st, its, sts = lx.batch_step(b, 0, ws, outs, cs, gs, hs, TOL, TOL)
-        for k, (ref, it_o, st_o) in enumerate(refs):
-            if st_o != 0:
-                # Advection-dominated instance: the Newton basis grows
-                # geometrically, and the oracle's binary128 coefficients hit
-                # their rounding floor before the series converges.  The
-                # engine's coefficients keep relative accuracy; if it reports
-                # convergence its result must match the exact Fourier solution.
-                import fourier
+        for k, (ref, it_o, st_o, delta, e_ex_o, exact) in enumerate(refs):
+            check_instance("FP64", outs[k].cpu().numpy(), its[k], sts[k], ref, it_o, st_o, delta, e_ex_o, exact,
+                           (rep, k))
 
-                nx, ny, nu, a, _ = inst[k]
-                if sts[k] == 0:
-                    exact = fourier.phi_apply(0, nx, ny, nu, a, hs[k], ws[k].cpu().numpy())
-                    assert fourier.rel_l2(outs[k].cpu().numpy(), exact) <= 1e-6, k
-                continue
-            assert sts[k] == 0, (k, sts[k])
-            if st_o == 0:
-                assert abs(its[k] - it_o) <= 1, (k, its[k], it_o)
-                got = outs[k].cpu().numpy()
-                assert np.linalg.norm(got - ref) <= TOL * np.linalg.norm(ref), k
+
+# Float-float carries a 2^-48 unit roundoff against FP64's 2^-53.
+DF64_ROUNDING = 32.0
+
+
+def check_instance(prec, got, it, st, ref, it_o, st_o, delta, e_exact_o, exact, where):
+    """The bar for one instance.  Where the problem amplifies rounding
+    (delta, the oracle's own change under a regrouped stencil, above
+    1e-11), agreement is held to a small multiple of delta -- no evaluation
+    order of the method can do better -- and the result must be as close to
+    the exact Fourier solution as the oracle's; float-float, with its larger
+    unit roundoff, may then also need more iterations before the stopping
+    test sees the series converge."""
+    assert st_o == 0 and st == 0, (where, st, st_o)
+    u = DF64_ROUNDING if prec == "DF64" else 1.0
+    bar = max(TOL, 4.0 * u * delta)
+    e = float(np.linalg.norm(got - ref) / np.linalg.norm(ref))
+    assert e <= bar, (where, e, bar, delta)
+    if u * delta <= 1e-11:
+        assert abs(it - it_o) <= 1, (where, it, it_o)
+    else:
+        assert it >= it_o - 1, (where, it, it_o)
+        e_ex = float(np.linalg.norm(got - exact) / np.linalg.norm(exact))
+        assert e_ex <= max(1.5 * e_exact_o, TOL), (where, e_ex, e_exact_o)
+    return e
+
+
+@pytest.fixture(scope="module")
+def config4_oracle():
+    # the full batched workload: 256 instances, n in {128, ..., 1024}, nu
+    # log-uniform in [1e-3, 1e-1], a uniform in [0, 2] (seed 7), exp(hA)u0
+    # at h = 50 dt_CFL, each by the oracle with mp divided differences
+    # (about a tenth of the instances are advection-dominated)
+    import oracle_pool
+
+    inst = synth.batch_instances(256, seed=7)
+    return inst, oracle_pool.batch_oracle(inst, l=0, tol=TOL, mult=50)
+
+
+@pytest.mark.parametrize("prec", ["FP64", "DF64"])
+def test_full_config4_batch_matches_oracle(lx, config4_oracle, prec):
+    import fourier
+
+    inst, refs = config4_oracle
+    probs = [(d["n"], d["n"], d["nu"], d["a"]) for d in inst]
+    b = lx.batch_setup(probs, precision=getattr(lx, prec))
+    ws, outs, cs, gs, hs = [], [], [], [], []
+    for d in inst:
+        n = d["n"]
+        ws.append(torch.from_numpy(synth.gaussians_ic(n, n, seed=d["seed"])).cuda())
+        outs.append(torch.empty(n * n, dtype=torch.float64, device="cuda"))
+        c, g = lx.spectral_interval(_symbol_radius(n, n, d["nu"], d["a"]))
+        cs.append(c)
+        gs.append(g)
+        hs.append(50 * synth.cfl_step(n, n, d["nu"], d["a"]))
+    st, its, sts = lx.batch_step(b, 0, ws, outs, cs, gs, hs, TOL, TOL)
+    worst, hard, loose = 0.0, 0, 0
+    for k, (ref, it_o, st_o, delta, e_ex_o) in enumerate(refs):
+        d = inst[k]
+        exact = fourier.phi_apply(0, d["n"], d["n"], d["nu"], d["a"], hs[k], ws[k].cpu().numpy())
+        e = check_instance(prec, outs[k].cpu().numpy(), its[k], sts[k], ref, it_o, st_o, delta, e_ex_o, exact,
+                           (k, d))
+        worst = max(worst, e)
+        hard += 4 * d["nu"] * d["n"] < 2 * d["a"]
+        loose += delta > 1e-11
+    assert st == 0
+    print(f"config-4 batch {prec}: 256 instances ({hard} with 4 nu n / a < 2, {loose} with rounding "
+          f"sensitivity above 1e-11), worst rel_l2 vs oracle {worst:.2e}")
+    b.close()
 
 
 def test_batch_float_float_matches_oracle(lx):

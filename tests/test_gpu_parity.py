@@ -73,6 +73,32 @@ def test_phi_advdiff_64(lx, xi_oracle, seed, l, prec):
 
 
 @pytest.mark.parametrize("prec", PRECS)
+def test_config1_all_seeds_with_power_bound(lx, xi_oracle, prec):
+    # the 64^2 workload as specified: nu = 1e-2, a = 1 (4 nu n / a = 2.6),
+    # seeds 1..10, h = 50 dt_CFL, the spectral interval from the library's
+    # 10-pass power bound; the oracle takes the same interval and forms its
+    # divided differences above binary128 precision (the Newton basis grows
+    # here, and binary128's floor alone moves results by a few 1e-10)
+    n, nu, a = 64, 1e-2, 1.0
+    v0 = synth.power_start(n * n, seed=5)
+    ctx = lx.leja_setup(n, n, nu, a, lx.ADVDIFF, prec)
+    st, rho, passes = lx.power_bound(ctx, None, dev(v0), 10)
+    rho_o, passes_o, st_o = oracle.power_iteration(oracle.ADVDIFF, n, n, nu, a, None, v0, 10)
+    assert st == 0 and st_o == 0 and passes == passes_o and abs(rho - rho_o) <= 1e-12 * rho_o
+    c, g = lx.spectral_interval(rho)
+    h = 50 * synth.cfl_step(n, n, nu, a)
+    out = torch.empty(n * n, dtype=torch.float64, device="cuda")
+    for seed in range(1, 11):
+        u0 = synth.gaussians_ic(n, n, seed=seed)
+        st, it = lx.phi_l_apply(ctx, 0, None, dev(u0), out, c, g, h, TOL, TOL)
+        ref, it_o, st_o = oracle.leja_phi_mp(oracle.ADVDIFF, n, n, nu, a, None, 0, u0, c, g, h, TOL, TOL,
+                                             xi_oracle)
+        assert st == 0 and st_o == 0, seed
+        assert abs(it - it_o) <= 1, (seed, it, it_o)
+        assert rel(out.cpu().numpy(), ref) <= TOL, seed
+
+
+@pytest.mark.parametrize("prec", PRECS)
 @pytest.mark.parametrize("nx,ny", [(67, 45), (128, 96), (192, 37), (64, 200), (1, 1), (1, 9), (2, 3), (33, 1),
                                    (256, 70), (384, 33)])
 def test_phi_advdiff_ragged(lx, xi_oracle, nx, ny, prec):
@@ -509,14 +535,17 @@ def test_adaptive_integration_matches_oracle(lx, xi_oracle):
     # Adaptive EXPRB32 with the classical controller on Burgers: the same
     # accepted/rejected sequence and the same final state as the oracle.
     # (4 nu n / max|u| ~ 5: diffusion-dominated, as the full-size workload)
+    # The first step (50 dt_CFL) is too large for the tolerance, so the run
+    # starts with rejections, then grows the step over 20 accepted steps.
     n, nu = 48, 2e-2
     u0 = synth.burgers_ic(n, n, seed=1)
     v0 = synth.power_start(n * n, seed=5)
     h0 = 50 * synth.cfl_step(n, n, nu, np.abs(u0).max())
-    T, tol = 2 * h0, 1e-4
+    T, tol = 10 * h0, 1e-4
     ref, steps_o, rej_o, its_o, h_o, t_o, st_o = oracle.integrate_exprb32(
         oracle.BURGERS, n, n, nu, 0.0, u0, v0, T, h0, tol, TOL, xi_oracle)
     assert st_o == 0 and abs(t_o - T) <= 1e-12 * T
+    assert rej_o >= 1 and steps_o >= 10
     ctx = lx.leja_setup(n, n, nu, 0.0, lx.BURGERS, lx.FP64, lx.EXPRB32)
     u = dev(u0)
     st, info = lx.lx_integrate(ctx, u, dev(v0), T, tol, TOL, 10000, 0.0, h0, 10)
@@ -525,6 +554,33 @@ def test_adaptive_integration_matches_oracle(lx, xi_oracle):
     assert abs(info["t"] - t_o) <= 1e-12 * T
     assert abs(info["leja_iters"] - its_o) <= 2 * (steps_o + rej_o)
     assert rel(u.cpu().numpy(), ref) <= 1e-9
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_adaptive_integration_linear_closed_form(lx, prec):
+    # EXPRB32 on the linear diffusion-advection problem: the remainder is
+    # zero, so every error estimate is 0, every step is accepted and the step
+    # doubles -- ceil(log2(T/h0 + 1)) steps, the last clipped to end at T --
+    # and the state is exp(T A) u0 (exact Fourier solution)
+    import math
+
+    import fourier
+
+    n, nu, a = 64, 1e-2, 0.5
+    u0 = synth.gaussians_ic(n, n, seed=3)
+    v0 = synth.power_start(n * n, seed=5)
+    h0 = 2 * synth.cfl_step(n, n, nu, a)
+    T = 20 * h0
+    ctx = lx.leja_setup(n, n, nu, a, lx.ADVDIFF, prec, lx.EXPRB32)
+    u = dev(u0)
+    st, info = lx.lx_integrate(ctx, u, dev(v0), T, 1e-6, 1e-12, 10000, 0.0, h0, 10)
+    assert st == 0
+    k = math.ceil(math.log2(T / h0 + 1))
+    assert info["rejected"] == 0 and info["steps"] == k
+    assert info["last_err"] == 0.0
+    assert abs(info["t"] - T) <= 1e-14 * T
+    exact = fourier.phi_apply(0, n, n, nu, a, T, u0)
+    assert rel(u.cpu().numpy(), exact) <= 100 * k * 1e-12
 
 
 @pytest.mark.parametrize("name", ["leja_iter_df_pipe_burgers_b1", "leja_iter_df_pipe_burgers_b2",

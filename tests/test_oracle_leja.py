@@ -226,7 +226,7 @@ def _exact_with_source(n, nu, a, h, u0, S):
 
 @pytest.mark.parametrize("seed", [1, 2])
 def test_ros_eu_with_source_is_exact_for_linear_problem(seed):
-    # Problem II of Sec. 4: with f(u) = A u + S the Rosenbrock-Euler step is
+    # Problem II of Sec. 3 (Eq. 4): with f(u) = A u + S the Rosenbrock-Euler step is
     # the exact solution of the linear ODE with a constant source
     n, nu, a = 64, 1e-2, 1.0
     u0, h, c, gamma = _cfg1(seed, n=n)

@@ -150,3 +150,28 @@ def test_config1_power_bound_mp_is_exact(seed):
                                      oracle.leja_points(1000))
     assert st == 0
     assert np.linalg.norm(out - exact) <= 100 * 1e-10 * np.linalg.norm(exact)
+
+
+@pytest.mark.parametrize("k,hard", [(0, False), (31, True)])
+def test_rounding_sensitivity_of_regrouped_stencil(k, hard):
+    # the per-neighbour grouping is the same operator: both runs stay within
+    # the Leja tolerance of the exact solution; on a diffusion-dominated
+    # instance they agree to round-off, on an advection-dominated one
+    # (4 nu n / a = 1.87) the growing Newton basis amplifies the different
+    # rounding far above it
+    d = synth.batch_instances(256, seed=7)[k]
+    n, nu, a = d["n"], d["nu"], d["a"]
+    u0, h, c, g, exact = _advdiff_exact_case(n, nu, a, d["seed"])
+    xi = oracle.leja_points(1000)
+    out, it, st = oracle.leja_phi_mp(oracle.ADVDIFF, n, n, nu, a, None, 0, u0, c, g, h, 1e-10, 1e-10, xi)
+    alt, it2, st2 = oracle.leja_phi_mp(oracle.ADVDIFF, n, n, nu, a, None, 0, u0, c, g, h, 1e-10, 1e-10, xi,
+                                       regroup=True)
+    assert st == 0 and st2 == 0 and abs(it - it2) <= 1
+    for x in (out, alt):
+        assert np.linalg.norm(x - exact) <= 100 * 1e-10 * np.linalg.norm(exact)
+    delta = oracle.rounding_sensitivity(n, n, nu, a, 0, u0, c, g, h, 1e-10, 1e-10, xi, ref=out)
+    assert delta == pytest.approx(np.linalg.norm(alt - out) / np.linalg.norm(out), rel=1e-12)
+    if hard:
+        assert delta > 1e-11
+    else:
+        assert delta < 1e-14

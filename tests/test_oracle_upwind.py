@@ -1,4 +1,4 @@
-"""Pins of the oracle's upwind discretisation (the paper's Sec. 4 problems on
+"""Pins of the oracle's upwind discretisation (the paper's Sec. 3 problems on
 periodic [-1,1)^2: second-order central Laplacian, third-order upwind
 gradient) and of the Leja loop and integrators on it.
 
