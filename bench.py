@@ -716,14 +716,17 @@ def run_rhs(args, rank, world, local):
 
 
 def run_learned(args, rank, world, local):
-    """The learned step-size controller on the scope's test: trained on
-    Burgers trajectories at 96^2 (nu = 2e-2, tol 1e-4, thirteen candidate
-    steps per state) with the library's tensor-core kernels, then applied to
-    Burgers at n^2 (default 2048^2, nu = 5e-3) adaptive to T = 200 dt_CFL,
-    against the classical controller from the same first step; the embedded
-    error test accepts or rejects every step in both runs.  Reported: Leja
-    iterations, steps, rejections, wall time and the error of the final state
-    against a tight-tolerance run."""
+    """The learned step-size controller on its workload: the network shipped
+    with the package (trained by paper_2310_08344_gb300/train_controller.py
+    on Burgers trajectories at 256^2 and 512^2 with the library's
+    tensor-core kernels) applied to Burgers at n^2 (default 2048^2,
+    nu = 5e-3), adaptive EXPRB32 to T = 200 dt_CFL (the scope's test) and to
+    T = 2000 dt_CFL (a run the ramp-up does not dominate), from a first step
+    of 10 dt_CFL, against the classical controller from the same step; the
+    embedded error test accepts or rejects every step in all runs.  Reported:
+    Leja iterations, steps, rejections, wall time per simulated time unit
+    (best of three runs) and the error of the final state against a
+    tight-tolerance run."""
     import torch
 
     import paper_2310_08344_gb300 as lx
@@ -732,61 +735,58 @@ def run_learned(args, rank, world, local):
     torch.cuda.set_device(local)
     stream = torch.cuda.current_stream()
     tol, leja_tol = 1e-4, 1e-10
-    # training at 96^2
-    nt, nut = 96, 2e-2
-    rng = np.random.default_rng(11)
-    v0t = torch.from_numpy(synth.power_start(nt * nt, seed=5)).cuda()
-    ics = [torch.from_numpy(synth.burgers_ic(nt, nt, seed=100 + k)).cuda() for k in range(24)]
-    dtt = synth.cfl_step(nt, nt, nut, 1.0)
-    t0 = time.perf_counter()
-    X, Y = learned.generate_samples(nt, nut, ics, v0t, tol, leja_tol, 40, dtt, rng)
-    t_gen = time.perf_counter() - t0
-    t0 = time.perf_counter()
-    model, norm, losses = learned.train(X, Y, epochs=300, batch=256, lr=2e-3, seed=0)
-    t_train = time.perf_counter() - t0
-    # the test at n^2
+    model, meta = learned.load_model(stream=stream)
     n = args.n if args.n != NX else 2048
     nu = 5e-3
     N = n * n
-    dt = synth.cfl_step(n, n, nu, 1.0)
-    T = 200 * dt
     u0 = synth.burgers_ic(n, n, seed=12)
+    dt = synth.cfl_step(n, n, nu, float(np.abs(u0).max()))
     v0 = torch.from_numpy(synth.power_start(N, seed=5)).cuda()
     prec = {"fp64": lx.FP64, "mixed": lx.MIXED, "df64": lx.DF64}[args.precision]
     ctx = lx.leja_setup(n, n, nu, 0.0, lx.BURGERS, prec, lx.EXPRB32, 1000, stream)
-    ref = torch.from_numpy(u0).cuda()
-    st, info_ref = lx.lx_integrate(ctx, ref, v0, T, 1e-9, leja_tol, 100000, 0.0, 3 * dt, 10)
-    if st != 0:
-        raise SystemExit(f"reference run failed: {st}")
-    runs = {}
     h0 = 10 * dt
-    for name in ("classical", "learned", "classical", "learned"):  # the second pair is timed warm
-        u = torch.from_numpy(u0).cuda()
-        torch.cuda.synchronize()
-        t1 = time.perf_counter()
-        if name == "classical":
-            st, info = lx.lx_integrate(ctx, u, v0, T, tol, leja_tol, 100000, 0.0, h0, 10)
-        else:
-            st, info = lx.lx_integrate_learned(ctx, u, v0, T, tol, leja_tol, model, dt, 100000, 0.0, h0, 10)
-        torch.cuda.synchronize()
-        wall = time.perf_counter() - t1
+    horizons = {}
+    for horizon in (200, 2000):
+        T = horizon * dt
+        ref = torch.from_numpy(u0).cuda()
+        st, _ = lx.lx_integrate(ctx, ref, v0, T, 1e-9, leja_tol, 100000, 0.0, h0, 10)
         if st != 0:
-            raise SystemExit(f"{name} run failed: {st}")
-        err = float((u - ref).norm().item() / ref.norm().item())
-        runs[name] = {"leja_iters": info["leja_iters"], "steps": info["steps"], "rejected": info["rejected"],
-                      "wall_ms": wall * 1e3, "rel_err_vs_tight": err}
-    c, l = runs["classical"], runs["learned"]
-    gain = c["leja_iters"] / max(l["leja_iters"], 1)
-    line = {"metric": "Leja iterations to T, classical / learned controller", "value": gain, "unit": "ratio",
-            "n_gpus": world, "steps": 1, "warmup": 1, "ms_per_step": l["wall_ms"], "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None,
+            raise SystemExit(f"reference run failed: {st}")
+        runs = {}
+        for name in ("classical", "learned"):
+            best = None
+            for _ in range(3):
+                u = torch.from_numpy(u0).cuda()
+                torch.cuda.synchronize()
+                t1 = time.perf_counter()
+                if name == "classical":
+                    st, info = lx.lx_integrate(ctx, u, v0, T, tol, leja_tol, 100000, 0.0, h0, 10)
+                else:
+                    st, info = lx.lx_integrate_learned(ctx, u, v0, T, tol, leja_tol, model, dt, 100000, 0.0, h0, 10)
+                torch.cuda.synchronize()
+                wall = time.perf_counter() - t1
+                if st != 0:
+                    raise SystemExit(f"{name} run failed: {st}")
+                if best is None or wall < best["wall_ms"] / 1e3:
+                    best = {"leja_iters": info["leja_iters"], "steps": info["steps"], "rejected": info["rejected"],
+                            "wall_ms": wall * 1e3, "wall_ms_per_unit_time": wall * 1e3 / T,
+                            "rel_err_vs_tight": float((u - ref).norm().item() / ref.norm().item())}
+            runs[name] = best
+        c, l = runs["classical"], runs["learned"]
+        horizons[f"T={horizon}dt_CFL"] = {"runs": runs, "gain_leja_iters": c["leja_iters"] / max(l["leja_iters"], 1),
+                                          "gain_wall": c["wall_ms"] / l["wall_ms"]}
+    main_h = horizons["T=200dt_CFL"]
+    line = {"metric": "Leja iterations to T, classical / learned controller", "value": main_h["gain_leja_iters"],
+            "unit": "ratio", "n_gpus": world, "steps": 1, "warmup": 0,
+            "ms_per_step": main_h["runs"]["learned"]["wall_ms"], "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None,
             "dtype": {"fp64": "f64", "mixed": "f32+f64", "df64": "f32x2 (float-float, FP64-accurate)"}[args.precision],
             "data": "synthetic",
-            "config": {"workload": f"learned-controller-burgers-{n}x{n}", "nu": nu, "t_final_over_dt_cfl": 200,
-                       "tol": tol, "leja_tol": leja_tol, "first_step_over_dt_cfl": 10,
-                       "training": {"grid": nt, "nu": nut, "samples": int(X.shape[0]), "generate_s": t_gen,
-                                    "train_s": t_train, "final_loss": float(losses[-1])}},
-            "runs": runs, "wall_gain": c["wall_ms"] / l["wall_ms"]}
+            "config": {"workload": f"learned-controller-burgers-{n}x{n}", "nu": nu, "tol": tol, "leja_tol": leja_tol,
+                       "first_step_over_dt_cfl": 10,
+                       "network": {k: meta[k] for k in ("samples", "groups", "label", "candidates", "loss_last",
+                                                        "epochs") if k in meta}},
+            "horizons": horizons, "wall_gain": main_h["gain_wall"]}
     if rank == 0:
         print(json.dumps(line))
     ctx.close()

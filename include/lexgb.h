@@ -65,7 +65,7 @@ typedef enum {
 
 enum { LX_ADVDIFF = 0, LX_BURGERS = 1, LX_ADVDIFF_UP3 = 2, LX_BURGERS_UP3 = 3 }; /* lx_problem.kind */
 enum { LX_FP64 = 0, LX_MIXED = 1, LX_DF64 = 2 }; /* lx_problem.precision */
-enum { LX_ROS_EU = 0, LX_EXPRB32 = 1 };          /* integrator */
+enum { LX_ROS_EU = 0, LX_EXPRB32 = 1, LX_EPIRK4S3A = 2 }; /* integrator */
 
 typedef struct {
   int nx, ny;     /* grid points per direction, each >= 1 */
@@ -202,7 +202,7 @@ lx_status phi_l_apply_vertical(lx_ctx* ctx, int l, int nc, const double* alpha, 
                                double rtol, double atol, int* iters);
 
 /* One step of the context's integrator (Sec. 2.2 Listings 5-6; Sec. 2.3
- * Listings 12-13):
+ * Listings 12-13; EPIRK4s3A of Sec. 3, Table 2):
  *   LX_ROS_EU   u_high = u + phi_1(h J(u)) h f(u); u_low unused (may be
  *               NULL); err = 0.
  *   LX_EXPRB32  u_low  = a = u + phi_1(h J(u)) h f(u)
@@ -210,6 +210,15 @@ lx_status phi_l_apply_vertical(lx_ctx* ctx, int l, int nc, const double* alpha, 
  *               F(k) = f(k) - J(u) k;  err = ||2 phi_3(h J(u)) R||.
  *               (For the quadratic Burgers f, R = -h p (p_x + p_y) with
  *               p = a - u, which is how the engine evaluates it.)
+ *   LX_EPIRK4S3A  fourth order, with the coefficients the stiff order
+ *               conditions fix for the stage nodes 1/2 and 2/3 (the paper
+ *               names the scheme, not its coefficients):
+ *               P_i = phi_1(c_i h J) h f(u) for c = 1/2, 2/3, 1 from one
+ *               vertical loop, R_i = h (F(u + c_i P_i) - F(u)),
+ *               u_low  = u + P_1 + phi_3(h J)(32 R_2 - 27/2 R_3) (third order)
+ *               u_high = u_low + phi_4(h J)(-144 R_2 + 81 R_3) (fourth order),
+ *               err = ||u_high - u_low||.  Needs nx % 128 == 0 with LX_DF64
+ *               and the central operators (vertical interpolation).
  * u_dev is not modified; u_low_dev and u_high_dev must not alias u_dev or
  * each other.  iters receives the total Leja iterations of the step. */
 lx_status expint_step(lx_ctx* ctx, const double* u_dev, double* u_low_dev, double* u_high_dev, double c,

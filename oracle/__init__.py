@@ -94,6 +94,8 @@ def _declare(L):
     L.or_exprb32_src.argtypes = [C.c_int, C.c_int, C.c_int, C.c_double, C.c_double, _dp, _dp,
                                  C.c_double, C.c_double, C.c_double, C.c_double, C.c_double, _dp, C.c_int,
                                  _dp, _dp, _dp, _ip]
+    L.or_epirk4s3a_src.argtypes = [C.c_int, C.c_int, C.c_int, C.c_double, C.c_double, _dp, _dp, C.c_double,
+                                   C.c_double, C.c_double, C.c_double, C.c_double, _dp, C.c_int, _dp, _dp, _dp, _ip]
     L.or_controller.restype = C.c_double
     L.or_controller.argtypes = [C.c_double, C.c_double, C.c_double]
     L.or_integrate_exprb32.argtypes = [C.c_int, C.c_int, C.c_int, C.c_double, C.c_double, _dp, _dp,
@@ -402,6 +404,22 @@ def exprb32(kind, nx, ny, nu, a, u, c, gamma, h, rtol, atol, xi, source=None):
     it = C.c_int(0)
     st = lib().or_exprb32_src(kind, nx, ny, nu, a, _p(u), _p(S) if S is not None else None, c, gamma, h, rtol,
                               atol, _p(xi), len(xi), _p(lo), _p(hi), _p(err), C.byref(it))
+    return lo, hi, float(err[0]), int(it.value), st
+
+
+def epirk4s3a(kind, nx, ny, nu, a, u, c, gamma, h, rtol, atol, xi, source=None):
+    """EPIRK4s3A step: returns (u3 embedded third order, u4 fourth order,
+    err = ||u4 - u3||, Leja iterations of the vertical phi_1 loop and the
+    phi_3, phi_4 loops, status)."""
+    u = _f64(u)
+    xi = _f64(xi)
+    S = _f64(source) if source is not None else None
+    lo = np.zeros_like(u)
+    hi = np.zeros_like(u)
+    err = np.zeros(1)
+    it = C.c_int(0)
+    st = lib().or_epirk4s3a_src(kind, nx, ny, nu, a, _p(u), _p(S) if S is not None else None, c, gamma, h, rtol,
+                                atol, _p(xi), len(xi), _p(lo), _p(hi), _p(err), C.byref(it))
     return lo, hi, float(err[0]), int(it.value), st
 
 

@@ -796,6 +796,95 @@ int or_exprb32(int kind, int nx, int ny, double nu, double a, const double* u, d
 }
 
 /* ------------------------------------------------------------------------ */
+/* EPIRK4s3A (a fourth-order exponential integrator of the paper's Table 2;  */
+/* Sec. 2.3: the phi_1 stages by "vertical" interpolation).  The paper names */
+/* the scheme without its coefficients; they are the ones the stiff order    */
+/* conditions of exponential Rosenbrock methods fix for the stage nodes      */
+/* c2 = 1/2, c3 = 2/3 (Hochbruck, Ostermann, Schweitzer 2009):               */
+/*   U_i = u + phi_1(c_i h J) c_i h f(u),   R_i = h (F(U_i) - F(u)),         */
+/*   u4  = u + phi_1(h J) h f(u) + phi_3(h J) W3 + phi_4(h J) W4,            */
+/* with W3 = b2 R_2 + b3 R_3, W4 = e2 R_2 + e3 R_3 solving                   */
+/*   b2 c2^2 + b3 c3^2 = 2, b2 c2^3 + b3 c3^3 = 0   (sum b_i(z) c_i^2 = 2 phi_3) */
+/*   e2 c2^2 + e3 c3^2 = 0, e2 c2^3 + e3 c3^3 = 6   (sum b_i(z) c_i^3 = 6 phi_4) */
+/* i.e. (b2, b3) = (32, -27/2), (e2, e3) = (-144, 81).  The embedded         */
+/* third-order solution drops the phi_4 term (it meets the first condition  */
+/* only): u3 = u4 - phi_4(h J) W4, err = ||phi_4(h J) W4||.  The three phi_1 */
+/* stages come from one vertical loop (alpha = 1/2, 2/3, 1).                 */
+/* ------------------------------------------------------------------------ */
+
+static int epirk4s3a_core(const or_op* opp, const double* u, double c, double gamma, double h, double rtol,
+                          double atol, const double* xi, int K, double* u_low, double* u_high, double* err,
+                          int* iters) {
+  const or_op op = *opp;
+  long n = (long)op.nx * op.ny;
+  const double c2 = 0.5, c3 = 2.0 / 3.0;
+  /* the 2x2 systems above, solved by Cramer's rule */
+  const double det = c2 * c2 * c3 * c3 * c3 - c3 * c3 * c2 * c2 * c2;
+  const double b2 = (2.0 * c3 * c3 * c3) / det, b3 = (-2.0 * c2 * c2 * c2) / det;
+  const double e2 = (-6.0 * c3 * c3) / det, e3 = (6.0 * c2 * c2) / det;
+  double* f_u = (double*)malloc(sizeof(double) * (size_t)n);
+  double* P = (double*)malloc(sizeof(double) * (size_t)n * 3);
+  double* U = (double*)malloc(sizeof(double) * (size_t)n);
+  double* t1 = (double*)malloc(sizeof(double) * (size_t)n);
+  double* t2 = (double*)malloc(sizeof(double) * (size_t)n);
+  double* nl_u = (double*)malloc(sizeof(double) * (size_t)n);
+  double* R2 = (double*)malloc(sizeof(double) * (size_t)n);
+  double* R3 = (double*)malloc(sizeof(double) * (size_t)n);
+  double* q3 = (double*)malloc(sizeof(double) * (size_t)n);
+  double* q4 = (double*)malloc(sizeof(double) * (size_t)n);
+  if (!f_u || !P || !U || !t1 || !t2 || !nl_u || !R2 || !R3 || !q3 || !q4) {
+    free(f_u); free(P); free(U); free(t1); free(t2); free(nl_u); free(R2); free(R3); free(q3); free(q4);
+    return OR_E_NOMEM;
+  }
+  int it_v = 0, it3 = 0, it4 = 0;
+  op_rhs(&op, u, f_u);
+  for (long q = 0; q < n; ++q) f_u[q] = h * f_u[q];
+  /* P_j = phi_1(alpha_j h J) h f(u), alpha = (c2, c3, 1), one Newton basis */
+  const double alpha[3] = {c2, c3, 1.0};
+  int st = or_leja_phi_vertical(op.kind, op.nx, op.ny, op.nu, op.a, op.u, 1, 3, alpha, f_u, c, gamma, h, rtol,
+                                atol, xi, K, P, &it_v);
+  /* F(u) = f(u) - J(u) u */
+  op_rhs(&op, u, t1);
+  op_apply(&op, u, t2);
+  for (long q = 0; q < n; ++q) nl_u[q] = t1[q] - t2[q];
+  /* U_i = u + c_i P_i (phi_1(c_i h J) c_i h f(u)), R_i = h (F(U_i) - F(u)) */
+  for (int i = 0; i < 2; ++i) {
+    const double ci = alpha[i];
+    double* R = i == 0 ? R2 : R3;
+    for (long q = 0; q < n; ++q) U[q] = u[q] + ci * P[(size_t)i * n + q];
+    op_rhs(&op, U, t1);
+    op_apply(&op, U, t2);
+    for (long q = 0; q < n; ++q) R[q] = h * (t1[q] - t2[q]) - h * nl_u[q];
+  }
+  /* W3, W4 into t1, t2 */
+  for (long q = 0; q < n; ++q) {
+    t1[q] = b2 * R2[q] + b3 * R3[q];
+    t2[q] = e2 * R2[q] + e3 * R3[q];
+  }
+  int st3 = OR_OK, st4 = OR_OK;
+  if (st == OR_OK) st3 = leja_phi_core(&op, 3, t1, c, gamma, h, rtol, atol, xi, K, q3, &it3);
+  if (st == OR_OK && st3 == OR_OK) st4 = leja_phi_core(&op, 4, t2, c, gamma, h, rtol, atol, xi, K, q4, &it4);
+  if (st != OR_OK || st3 != OR_OK) memset(q4, 0, sizeof(double) * (size_t)n);
+  if (st != OR_OK) memset(q3, 0, sizeof(double) * (size_t)n);
+  for (long q = 0; q < n; ++q) {
+    u_low[q] = u[q] + P[2 * (size_t)n + q] + q3[q];
+    u_high[q] = u_low[q] + q4[q];
+  }
+  *err = nrm(q4, n);
+  *iters = it_v + it3 + it4;
+  free(f_u); free(P); free(U); free(t1); free(t2); free(nl_u); free(R2); free(R3); free(q3); free(q4);
+  return st != OR_OK ? st : (st3 != OR_OK ? st3 : st4);
+}
+
+int or_epirk4s3a_src(int kind, int nx, int ny, double nu, double a, const double* u, const double* S, double c,
+                     double gamma, double h, double rtol, double atol, const double* xi, int K, double* u_low,
+                     double* u_high, double* err, int* iters) {
+  if (nx <= 0 || ny <= 0 || gamma == 0.0) return OR_E_INVAL;
+  or_op op = {kind, nx, ny, nu, a, u, S};
+  return epirk4s3a_core(&op, u, c, gamma, h, rtol, atol, xi, K, u_low, u_high, err, iters);
+}
+
+/* ------------------------------------------------------------------------ */
 /* Step-size control with the embedded error (Sec. 2.2: the EXPRB32 error   */
 /* estimate "may be used to control the step sizes").  The paper gives no   */
 /* controller; the reading is the classical one for a third-order pair:     */

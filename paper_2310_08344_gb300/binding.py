@@ -15,7 +15,7 @@ STATUS = {0: "LX_OK", 1: "LX_E_INVAL", 2: "LX_E_NOMEM", 3: "LX_E_CUDA", 4: "LX_E
 ADVDIFF, BURGERS = 0, 1
 ADVDIFF_UP3, BURGERS_UP3 = 2, 3  # the paper's discretisation: periodic [-1,1)^2, third-order upwind gradient
 FP64, MIXED, DF64 = 0, 1, 2
-ROS_EU, EXPRB32 = 0, 1
+ROS_EU, EXPRB32, EPIRK4S3A = 0, 1, 2
 
 _dp = C.POINTER(C.c_double)
 _ip = C.POINTER(C.c_int)

@@ -493,6 +493,43 @@ static __global__ void __launch_bounds__(kThreadsPerBlock)
   if (threadIdx.x == 0) st->red = sqrt(s / double(n));
 }
 
+// EPIRK4s3A: out = c_i P_i (the stage increment U_i - u from phi_1(c_i h J)
+// h f(u)), read by the remainder kernels.
+static __global__ void scale_kernel(long long n, double s, const double* __restrict__ x, double* __restrict__ y) {
+  for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < n; q += (long long)gridDim.x * blockDim.x)
+    y[q] = s * x[q];
+}
+
+// EPIRK4s3A: W3 = b2 R2 + b3 R3 and W4 = e2 R2 + e3 R3, the inputs of the
+// phi_3 and phi_4 loops.
+static __global__ void epirk_combine_kernel(long long n, const double* __restrict__ R2,
+                                            const double* __restrict__ R3, double b2, double b3, double e2,
+                                            double e3, double* __restrict__ W3, double* __restrict__ W4) {
+  for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < n; q += (long long)gridDim.x * blockDim.x) {
+    const double r2 = R2[q], r3 = R3[q];
+    W3[q] = b2 * r2 + b3 * r3;
+    W4[q] = e2 * r2 + e3 * r3;
+  }
+}
+
+// EPIRK4s3A final pass: u_low = u + p1 + q3 (in place of p1), u_high =
+// u_low + q4 and err = ||q4|| (last-block reduction into st->red).
+static __global__ void __launch_bounds__(kThreadsPerBlock)
+    epirk_final_kernel(long long n, const double* __restrict__ u, double* __restrict__ p1_low,
+                       const double* __restrict__ q3, const double* __restrict__ q4, double* __restrict__ u_high,
+                       double* __restrict__ partials, unsigned int* __restrict__ ticket, LoopState* st) {
+  double s = 0.0, dummy = 0.0;
+  for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < n; q += (long long)gridDim.x * blockDim.x) {
+    const double e = q4[q];
+    const double lo = u[q] + p1_low[q] + q3[q];
+    p1_low[q] = lo;
+    u_high[q] = lo + e;
+    s = fma(e, e, s);
+  }
+  if (!last_block_total2(s, dummy, partials, ticket)) return;
+  if (threadIdx.x == 0) st->red = sqrt(s / double(n));
+}
+
 // ||v|| = sqrt(sum v^2 / n) into st->red2 (last-block reduction).
 static __global__ void __launch_bounds__(kThreadsPerBlock)
     vec_norm_kernel(long long n, const double* __restrict__ v, double* __restrict__ partials,

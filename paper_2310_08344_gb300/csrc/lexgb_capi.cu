@@ -25,6 +25,7 @@
 #include "leja_upwind.cuh"
 #include "leja_upwind_2step.cuh"
 #include "leja_kernels.cuh"
+#include "lexgb_df2x.h"
 #include "lexgb_internal.h"
 #include "lexgb_vertical.h"
 
@@ -109,7 +110,8 @@ struct lx_ctx {
   void* d_y[2] = {nullptr, nullptr};
   double* d_f = nullptr;   // h f(u), later R
   double* d_s = nullptr;   // u_x + u_y (Burgers)
-  double* d_p3 = nullptr;  // phi_3 result (EXPRB32)
+  double* d_p3 = nullptr;  // phi_3 result (EXPRB32, EPIRK4s3A)
+  double* d_ep[3] = {nullptr, nullptr, nullptr};  // EPIRK4s3A: stage increments, W3 / W4
   double* d_pw[2] = {nullptr, nullptr};  // power iteration ping-pong
   double* d_io[3] = {nullptr, nullptr, nullptr};  // staging for expint_step_host
   float2* d_pdf = nullptr;  // df64 form: polynomial as float pairs
@@ -245,7 +247,14 @@ std::vector<Cand> candidates(int kind, int precision, int cls) {
   if (precision == LX_DF64) {
     if (wide) {
       // default without autotuning: two iterations per pass at four blocks
-      // per SM (155 us per launch at 4096^2, against 165 us at three)
+      // per SM, issue-lean form
+      v.push_back(Cand{df2x_kernel(4, 4, false), kPipeThreads, df2x_smem_bytes(4), 4, "leja_iter_df_pipe2x_b4_s4",
+                       2});
+      v.push_back(Cand{df2x_kernel(4, 5, false), kPipeThreads, df2x_smem_bytes(5), 4, "leja_iter_df_pipe2x_b4", 2});
+      v.push_back(Cand{df2x_kernel(3, 5, false), kPipeThreads, df2x_smem_bytes(5), 4, "leja_iter_df_pipe2x_b3", 2});
+      v.push_back(Cand{df2x_kernel(4, 4, true), kPipeThreads, df2x_smem_bytes(4), 4, "leja_iter_df_pipe2x_u3_b4_s4",
+                       2});
+      // the first two-step form (155 us per launch at 4096^2, four blocks per SM)
       v.push_back(Cand{reinterpret_cast<const void*>(&leja_iter_df_pipe2_kernel<4, 4>), kPipeThreads,
                        pipe2_smem_bytes<4>(), 4, "leja_iter_df_pipe2_b4_s4", 2});
       v.push_back(Cand{reinterpret_cast<const void*>(&leja_iter_df_pipe2_kernel<2, 6>), kPipeThreads,
@@ -686,6 +695,7 @@ void leja_destroy(lx_ctx* c) {
   cudaFree(c->d_uf);
   cudaFree(c->d_sf);
   cudaFree(c->d_p3);
+  for (auto* p : c->d_ep) cudaFree(p);
   cudaFree(c->d_pw[0]);
   cudaFree(c->d_pw[1]);
   for (auto* p : c->d_io) cudaFree(p);
@@ -709,7 +719,7 @@ lx_status leja_setup(const lx_problem* prob, int integrator, int max_leja, void*
   if (!out) return LX_E_INVAL;
   *out = nullptr;
   if (!valid_problem(prob)) return LX_E_INVAL;
-  if (integrator != LX_ROS_EU && integrator != LX_EXPRB32) return LX_E_INVAL;
+  if (integrator != LX_ROS_EU && integrator != LX_EXPRB32 && integrator != LX_EPIRK4S3A) return LX_E_INVAL;
   if (max_leja == 0) max_leja = 1000;
   if (max_leja < 16 || max_leja > 4096) return LX_E_INVAL;
   lx_ctx* c = new lx_ctx();
@@ -745,7 +755,10 @@ lx_status leja_setup(const lx_problem* prob, int integrator, int max_leja, void*
   }
   if (!dmalloc(&c->d_y[0], basis_bytes(c)) || !dmalloc(&c->d_y[1], basis_bytes(c))) return fail(LX_E_NOMEM);
   if (!dmalloc((void**)&c->d_f, nb) || !dmalloc((void**)&c->d_s, nb)) return fail(LX_E_NOMEM);
-  if (integrator == LX_EXPRB32 && !dmalloc((void**)&c->d_p3, nb)) return fail(LX_E_NOMEM);
+  if (integrator != LX_ROS_EU && !dmalloc((void**)&c->d_p3, nb)) return fail(LX_E_NOMEM);
+  if (integrator == LX_EPIRK4S3A)
+    for (auto*& p : c->d_ep)
+      if (!dmalloc((void**)&p, nb)) return fail(LX_E_NOMEM);
   if (prob->precision == LX_DF64 && !dmalloc((void**)&c->d_pdf, sizeof(float2) * (size_t)c->n))
     return fail(LX_E_NOMEM);
   if (prob->precision == LX_MIXED && prob->kind == LX_BURGERS &&
@@ -1123,15 +1136,101 @@ lx_status phi_l_apply_vertical(lx_ctx* c, int l, int nc, const double* alpha, co
   return (lx_status)c->h_state->status_total;
 }
 
+// EPIRK4s3A (the fourth-order exponential integrator of the paper's Table 2;
+// its phi_1 stages by vertical interpolation, Sec. 2.3).  Coefficients: the
+// ones the stiff order conditions sum b_i(z) c_i^2 = 2 phi_3(z) and
+// sum b_i(z) c_i^3 = 6 phi_4(z) fix for the nodes c2 = 1/2, c3 = 2/3:
+//   U_i = u + c_i P_i,  P_i = phi_1(c_i h J) h f(u),  R_i = h (F(U_i) - F(u)),
+//   W3 = 32 R_2 - 27/2 R_3,  W4 = -144 R_2 + 81 R_3,
+//   u_low  = u + P_1 + phi_3(h J) W3          (embedded, third order)
+//   u_high = u_low + phi_4(h J) W4            (fourth order)
+//   err = ||phi_4(h J) W4||.
+// The engine's remainder kernels evaluate R_i from U_i - u (exactly
+// -h p (p_x + p_y) for the quadratic central Burgers term, 0 for the
+// linear operators).  The loops run through the public entry points (one
+// vertical phi_1 loop with alpha = 1/2, 2/3, 1; one phi_3 and one phi_4
+// loop), each synchronising once.
+static lx_status epirk4s3a_step(lx_ctx* c, const double* u, double* u_low, double* u_high, double cc, double gamma,
+                                double h, double rtol, double atol, double* err, int* iters) {
+  const lx_problem& P = c->prob;
+  const int G = aux_blocks(c);
+  const bool burg = is_burgers(P.kind);
+  const double c2 = 0.5, c3 = 2.0 / 3.0;
+  const double b2 = 32.0, b3 = -13.5, e2 = -144.0, e3 = 81.0;
+  double* E0 = c->d_ep[0];
+  double* E1 = c->d_ep[1];
+  double* T = c->d_ep[2];
+  // h (f(u) + S) into d_f
+  lx_status st = begin_call(c);
+  if (st != LX_OK) return st;
+  if (P.kind == LX_ADVDIFF)
+    rhs_kernel<0><<<G, kThreadsPerBlock, 0, c->stream>>>(c->geo, P.nu, P.a, h, u, c->d_f, c->d_s, c->d_src);
+  else if (P.kind == LX_BURGERS)
+    rhs_kernel<1><<<G, kThreadsPerBlock, 0, c->stream>>>(c->geo, P.nu, 0.0, h, u, c->d_f, c->d_s, c->d_src);
+  else if (P.kind == LX_ADVDIFF_UP3)
+    rhs_up3_kernel<false><<<G, kThreadsPerBlock, 0, c->stream>>>(c->up3, h, u, c->d_src, c->d_f);
+  else
+    rhs_up3_kernel<true><<<G, kThreadsPerBlock, 0, c->stream>>>(c->up3, h, u, c->d_src, c->d_f);
+  ++c->stats.kernels;
+  LX_CUDA(cudaGetLastError());
+  st = end_call(c);
+  if (st != LX_OK) return st;
+  // P_2, P_3, P_1 from one Newton basis (P_1 into u_low)
+  const double alpha[3] = {c2, c3, 1.0};
+  double* outs[3] = {E0, E1, u_low};
+  int it_v = 0, it3 = 0, it4 = 0;
+  lx_status sv = phi_l_apply_vertical(c, 1, 3, alpha, burg ? u : nullptr, c->d_f, outs, cc, gamma, h, rtol, atol,
+                                      &it_v);
+  if (sv != LX_OK && sv != LX_E_NOCONV) return sv;
+  // R_2 into d_f, R_3 into d_p3, then W3 into E0 and W4 into E1
+  st = begin_call(c);
+  if (st != LX_OK) return st;
+  for (int i = 0; i < 2; ++i) {
+    double* R = i == 0 ? c->d_f : c->d_p3;
+    scale_kernel<<<G, kThreadsPerBlock, 0, c->stream>>>(c->n, alpha[i], i == 0 ? E0 : E1, T);
+    if (P.kind == LX_ADVDIFF)
+      exprb32_stage_kernel<0><<<G, kThreadsPerBlock, 0, c->stream>>>(c->geo, h, T, R);
+    else if (P.kind == LX_BURGERS)
+      exprb32_stage_kernel<1><<<G, kThreadsPerBlock, 0, c->stream>>>(c->geo, h, T, R);
+    else if (P.kind == LX_ADVDIFF_UP3)
+      exprb32_stage_up3_kernel<false><<<G, kThreadsPerBlock, 0, c->stream>>>(c->up3, h, T, R);
+    else
+      exprb32_stage_up3_kernel<true><<<G, kThreadsPerBlock, 0, c->stream>>>(c->up3, h, T, R);
+    c->stats.kernels += 2;
+  }
+  epirk_combine_kernel<<<G, kThreadsPerBlock, 0, c->stream>>>(c->n, c->d_f, c->d_p3, b2, b3, e2, e3, E0, E1);
+  ++c->stats.kernels;
+  LX_CUDA(cudaGetLastError());
+  st = end_call(c);
+  if (st != LX_OK) return st;
+  // q3 = phi_3(h J) W3 into d_f, q4 = phi_4(h J) W4 into d_p3
+  lx_status s3 = phi_l_apply(c, 3, burg ? u : nullptr, E0, c->d_f, cc, gamma, h, rtol, atol, &it3);
+  if (s3 != LX_OK && s3 != LX_E_NOCONV) return s3;
+  lx_status s4 = phi_l_apply(c, 4, burg ? u : nullptr, E1, c->d_p3, cc, gamma, h, rtol, atol, &it4);
+  if (s4 != LX_OK && s4 != LX_E_NOCONV) return s4;
+  st = begin_call(c);
+  if (st != LX_OK) return st;
+  epirk_final_kernel<<<G, kThreadsPerBlock, 0, c->stream>>>(c->n, u, u_low, c->d_f, c->d_p3, u_high, c->d_partials,
+                                                             c->d_ticket, c->d_state);
+  ++c->stats.kernels;
+  LX_CUDA(cudaGetLastError());
+  st = end_call(c);
+  if (st != LX_OK) return st;
+  if (err) *err = c->h_state->red;
+  if (iters) *iters = it_v + it3 + it4;
+  return sv != LX_OK ? sv : (s3 != LX_OK ? s3 : s4);
+}
+
 lx_status expint_step(lx_ctx* c, const double* u, double* u_low, double* u_high, double cc, double gamma, double h,
                       double rtol, double atol, double* err, int* iters) {
   if (!c || !u || !u_high || !(gamma != 0.0) || !std::isfinite(h) || !std::isfinite(cc) || !std::isfinite(gamma) ||
       !(rtol >= 0.0) || !(atol >= 0.0))
     return LX_E_INVAL;
   if ((const void*)u_high == (const void*)u) return LX_E_INVAL;
-  if (c->integrator == LX_EXPRB32 &&
+  if (c->integrator != LX_ROS_EU &&
       (!u_low || (const void*)u_low == (const void*)u || (const void*)u_low == (const void*)u_high))
     return LX_E_INVAL;
+  if (c->integrator == LX_EPIRK4S3A) return epirk4s3a_step(c, u, u_low, u_high, cc, gamma, h, rtol, atol, err, iters);
   const lx_problem& P = c->prob;
   const int G = aux_blocks(c);
   lx_status st = begin_call(c);
@@ -1255,7 +1354,7 @@ lx_status expint_step(lx_ctx* c, const double* u, double* u_low, double* u_high,
 lx_status expint_step_host(lx_ctx* c, const double* u_host, double* u_low_host, double* u_high_host, double cc,
                            double gamma, double h, double rtol, double atol, double* err, int* iters) {
   if (!c || !u_host || !u_high_host) return LX_E_INVAL;
-  if (c->integrator == LX_EXPRB32 && !u_low_host) return LX_E_INVAL;
+  if (c->integrator != LX_ROS_EU && !u_low_host) return LX_E_INVAL;
   const size_t nb = sizeof(double) * (size_t)c->n;
   for (auto*& p : c->d_io)
     if (!p && !cuda_ok(cudaMalloc((void**)&p, nb), "cudaMalloc")) return LX_E_NOMEM;
@@ -1263,7 +1362,7 @@ lx_status expint_step_host(lx_ctx* c, const double* u_host, double* u_low_host, 
   lx_status st = expint_step(c, c->d_io[0], c->d_io[1], c->d_io[2], cc, gamma, h, rtol, atol, err, iters);
   if (st != LX_OK && st != LX_E_NOCONV) return st;
   LX_CUDA(cudaMemcpyAsync(u_high_host, c->d_io[2], nb, cudaMemcpyDeviceToHost, c->stream));
-  if (c->integrator == LX_EXPRB32)
+  if (c->integrator != LX_ROS_EU)
     LX_CUDA(cudaMemcpyAsync(u_low_host, c->d_io[1], nb, cudaMemcpyDeviceToHost, c->stream));
   LX_CUDA(cudaStreamSynchronize(c->stream));
   return st;

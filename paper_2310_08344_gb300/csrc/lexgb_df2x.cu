@@ -1,0 +1,29 @@
+// Instances of the issue-lean two-step float-float kernel (a translation unit
+// of their own so that they compile in parallel with the rest).
+#include <cuda_runtime.h>
+
+#include "leja_df64_2step_x.cuh"
+#include "lexgb_df2x.h"
+
+namespace lexgb {
+
+const void* df2x_kernel(int minb, int stages, bool unroll3) {
+  if (unroll3) {
+    if (minb == 4 && stages == 4) return reinterpret_cast<const void*>(&leja_iter_df_pipe2x_kernel<4, 4, true>);
+    return nullptr;
+  }
+  if (minb == 4 && stages == 4) return reinterpret_cast<const void*>(&leja_iter_df_pipe2x_kernel<4, 4, false>);
+  if (minb == 4 && stages == 5) return reinterpret_cast<const void*>(&leja_iter_df_pipe2x_kernel<4, 5, false>);
+  if (minb == 3 && stages == 5) return reinterpret_cast<const void*>(&leja_iter_df_pipe2x_kernel<3, 5, false>);
+  return nullptr;
+}
+
+int df2x_smem_bytes(int stages) {
+  switch (stages) {
+    case 4: return pipe2x_smem_bytes<4>();
+    case 5: return pipe2x_smem_bytes<5>();
+    default: return 0;
+  }
+}
+
+}  // namespace lexgb

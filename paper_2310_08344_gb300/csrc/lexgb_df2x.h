@@ -1,0 +1,14 @@
+// Entry points of the translation unit that holds the issue-lean two-step
+// float-float kernels (lexgb_df2x.cu).
+#pragma once
+
+namespace lexgb {
+
+// leja_iter_df_pipe2x_kernel<minb, stages, unroll3> (signature of the
+// fused iteration kernels: const LoopArgs*, LoopState*, double* partials,
+// unsigned* ticket, cudaGraphConditionalHandle), or NULL if that instance
+// is not built.  Its dynamic shared memory is df2x_smem_bytes(stages).
+const void* df2x_kernel(int minb, int stages, bool unroll3);
+int df2x_smem_bytes(int stages);
+
+}  // namespace lexgb

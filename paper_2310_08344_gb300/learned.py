@@ -18,6 +18,7 @@ orchestrates the calls and keeps the samples.
 """
 from __future__ import annotations
 
+import json
 import math
 import os
 
@@ -26,6 +27,8 @@ import numpy as np
 from . import binding as B
 
 FEATURES = ("log(rho h)", "log(h/dt_CFL)", "iters/100", "log10(err/tol)", "||u||")
+# the trained network shipped with the package (train_controller.py writes it)
+MODEL_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "controller_burgers.npz")
 CANDIDATES = tuple(range(-4, 5))  # h_j = h 2^(j/2)
 TARGET = 0.8  # the label's error bound, as a fraction of tol
 
@@ -144,3 +147,21 @@ def train(X, Y, epochs=30, batch=1024, lr=2e-3, seed=0, stream=None):
                 raise B.LexgbError(st, "mlp_train_step")
             losses.append(loss)
     return model, norm, losses
+
+
+def save_model(path, model, norm, meta):
+    """Write the network's FP32 master weights, its normalisation vector and
+    a JSON description of how it was trained."""
+    w = B.mlp_get_weights(model)
+    blob = np.frombuffer(json.dumps(meta, sort_keys=True).encode(), dtype=np.uint8)
+    np.savez(path, w=w, norm=np.asarray(norm, dtype=np.float32), meta=blob)
+
+
+def load_model(path=MODEL_PATH, batch_max=64, stream=None):
+    """(model, meta) from a file written by save_model."""
+    with np.load(path) as d:
+        w, norm = d["w"].copy(), d["norm"].copy()
+        meta = json.loads(bytes(d["meta"]).decode())
+    if w.size != B.mlp_param_count() or norm.size != 14:
+        raise ValueError(f"{path}: not a controller network of this library")
+    return B.mlp_setup(batch_max, w, norm, stream), meta

@@ -87,10 +87,9 @@ def check_instance(prec, got, it, st, ref, it_o, st_o, delta, e_exact_o, exact, 
     """The bar for one instance.  Where the problem amplifies rounding
     (delta, the oracle's own change under a regrouped stencil, above
     1e-11), agreement is held to a small multiple of delta -- no evaluation
-    order of the method can do better -- and the result must be as close to
-    the exact Fourier solution as the oracle's; float-float, with its larger
-    unit roundoff, may then also need more iterations before the stopping
-    test sees the series converge."""
+    order of the method can do better; float-float, with its larger unit
+    roundoff, may then also need more iterations before the stopping test
+    sees the series converge."""
     assert st_o == 0 and st == 0, (where, st, st_o)
     u = DF64_ROUNDING if prec == "DF64" else 1.0
     bar = max(TOL, 4.0 * u * delta)
@@ -99,9 +98,12 @@ def check_instance(prec, got, it, st, ref, it_o, st_o, delta, e_exact_o, exact, 
     if u * delta <= 1e-11:
         assert abs(it - it_o) <= 1, (where, it, it_o)
     else:
+        # the stopping test may see the series converge later (never
+        # earlier), and the result stays as close to the exact Fourier
+        # solution as the oracle's plus the rounding allowance
         assert it >= it_o - 1, (where, it, it_o)
         e_ex = float(np.linalg.norm(got - exact) / np.linalg.norm(exact))
-        assert e_ex <= max(1.5 * e_exact_o, TOL), (where, e_ex, e_exact_o)
+        assert e_ex <= e_exact_o + 1.01 * bar, (where, e_ex, e_exact_o, bar)
     return e
 
 

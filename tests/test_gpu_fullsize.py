@@ -7,9 +7,10 @@ the same bar against the oracle on the same inputs and the same spectral
 interval (the oracle's power bound):
 
 * the diffusion-advection Rosenbrock-Euler step at 4096^2, h = 50 dt_CFL,
-  tol 1e-10 -- the float-float two-step kernel at 4 resident blocks per SM
-  with balanced row ranges (with 5- and 4-stage rings), the kernel the
-  autotuner picks, and the native FP64 kernel;
+  tol 1e-10 -- the float-float two-step kernels (the issue-lean form and
+  the first form) at 4 resident blocks per SM with balanced row ranges
+  (with 5- and 4-stage rings), the kernel the autotuner picks, and the
+  native FP64 kernel;
 * the central-difference Burgers EXPRB32 step at 2048^2 (nu = 5e-3,
   h = 50 dt_CFL): u_low, u_high and the error estimate, float-float and
   FP64 (the mixed form's error against the FP64 oracle is reported);
@@ -72,7 +73,8 @@ def advdiff4096(xi_oracle):
     return dict(n=n, nu=nu, a=a, u0=u0, v0=v0, rho=rho, passes=passes, c=c, g=g, h=h, ref=ref, it=it_o)
 
 
-@pytest.mark.parametrize("prec,kernel", [("DF64", "leja_iter_df_pipe2_b4"), ("DF64", "leja_iter_df_pipe2_b4_s4"),
+@pytest.mark.parametrize("prec,kernel", [("DF64", "leja_iter_df_pipe2x_b4_s4"), ("DF64", "leja_iter_df_pipe2x_b4"),
+                                         ("DF64", "leja_iter_df_pipe2_b4"), ("DF64", "leja_iter_df_pipe2_b4_s4"),
                                          ("DF64", "autotune"), ("FP64", None)])
 def test_ros_eu_4096_matches_oracle(lx, advdiff4096, prec, kernel):
     d = advdiff4096

@@ -1,16 +1,20 @@
 """What the learned step-size controller gains over the classical one.
 
-Training samples come from the method itself (Burgers trajectories,
-thirteen candidate steps per state from a quarter to sixteen times the
-current one, label = the largest step whose error estimate stays below
-0.8 tol).  The network is trained
-on the GPU with the library's tensor-core kernels.  Then an unseen initial
-state is integrated to the same end time with both controllers, once from a
-well-chosen and once from a cautious first step; the embedded error test
-accepts or rejects every step in all runs.  Reported: Leja
-iterations (the paper's cost proxy), attempts, rejections and the error of
-the final state against a tight-tolerance reference."""
-import math
+The network shipped with the package (controller_burgers.npz, written by
+paper_2310_08344_gb300/train_controller.py from about 2e4 labelled states of
+Burgers trajectories at 256^2 and 512^2, both initial-state families of the
+workloads) is applied to the workload it was made for: viscous Burgers at
+2048^2 (nu = 5e-3), adaptive EXPRB32 to T = 200 dt_CFL from a first step of
+10 dt_CFL, tol 1e-4, against the classical controller from the same first
+step.  The embedded error test accepts or rejects every step in both runs.
+Asserted: fewer Leja iterations and less wall time (best of three runs each)
+at the same accuracy class against a tight-tolerance run; reported as well:
+a ten times longer horizon, where the ramp-up is a small part of the run.
+
+A second test runs the training pipeline itself at a small scale (samples
+from the library's own EXPRB32 steps, labels, GPU training), and checks the
+shortcut of the label search against trying all nine candidate steps.
+"""
 import time
 
 import numpy as np
@@ -31,54 +35,84 @@ def lx():
     return m
 
 
-def test_learned_controller_gain(lx):
+def _run(lx, ctx, name, u0, v0, T, tol, leja_tol, h0, model, dt, reps=3):
+    best = None
+    for _ in range(reps):
+        u = torch.from_numpy(u0).cuda()
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
+        if name == "classical":
+            st, info = lx.lx_integrate(ctx, u, v0, T, tol, leja_tol, 100000, 0.0, h0, 10)
+        else:
+            st, info = lx.lx_integrate_learned(ctx, u, v0, T, tol, leja_tol, model, dt, 100000, 0.0, h0, 10)
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - t1
+        assert st == 0 and abs(info["t"] - T) <= 1e-12 * T
+        if best is None or wall < best[0]["wall"]:
+            best = (dict(info, wall=wall), u)
+    return best
+
+
+@pytest.mark.parametrize("horizon", [200, 2000])
+def test_trained_controller_gain(lx, horizon):
+    from paper_2310_08344_gb300 import learned
+
+    model, meta = learned.load_model()
+    n, nu, tol, leja_tol = 2048, 5e-3, 1e-4, 1e-10
+    u0 = synth.burgers_ic(n, n, seed=12)  # the test seed
+    v0 = torch.from_numpy(synth.power_start(n * n, seed=5)).cuda()
+    dt = synth.cfl_step(n, n, nu, np.abs(u0).max())
+    T, h0 = horizon * dt, 10 * dt
+    ctx = lx.leja_setup(n, n, nu, 0.0, lx.BURGERS, lx.DF64, lx.EXPRB32)
+    ref = torch.from_numpy(u0).cuda()
+    st, _ = lx.lx_integrate(ctx, ref, v0, T, 1e-9, leja_tol, 100000, 0.0, h0, 10)
+    assert st == 0
+    runs = {}
+    for name in ("classical", "learned"):
+        info, u = _run(lx, ctx, name, u0, v0, T, tol, leja_tol, h0, model, dt)
+        info["err"] = float((u - ref).norm().item() / ref.norm().item())
+        runs[name] = info
+    c, l = runs["classical"], runs["learned"]
+    gain_iters = c["leja_iters"] / l["leja_iters"]
+    gain_wall = c["wall"] / l["wall"]
+    print(f"\nBurgers {n}^2 to {horizon} dt_CFL (network: {meta['samples']} samples, loss {meta['loss_last']:.4f}):")
+    for k, v in runs.items():
+        print(f"  {k:9s}: steps {v['steps']:4d} rejected {v['rejected']:3d} leja_iters {v['leja_iters']:6d} "
+              f"wall {v['wall'] * 1e3:8.1f} ms  rel err vs tight run {v['err']:.2e}")
+    print(f"  gain (classical / learned): Leja iterations {gain_iters:.3f}, wall time {gain_wall:.3f}")
+    # the same accuracy class: the error test bounds both runs alike
+    assert l["err"] <= max(3.0 * c["err"], 10 * tol)
+    if horizon == 200:
+        assert gain_iters > 1.0 and gain_wall > 1.0
+    # the long run (ramp-up a small part of it) is reported, not asserted
+
+
+def test_training_pipeline_small(lx):
     from paper_2310_08344_gb300 import learned
 
     n, nu, tol, leja_tol = 96, 2e-2, 1e-4, 1e-10
     rng = np.random.default_rng(11)
     v0 = torch.from_numpy(synth.power_start(n * n, seed=5)).cuda()
-    ics = [torch.from_numpy(synth.burgers_ic(n, n, seed=100 + k)).cuda() for k in range(24)]
+    ics = [torch.from_numpy(synth.burgers_ic(n, n, seed=100 + k)).cuda() for k in range(6)]
     dt = synth.cfl_step(n, n, nu, 1.0)
-    t0 = time.perf_counter()
-    X, Y = learned.generate_samples(n, nu, ics, v0, tol, leja_tol, 40, dt, rng)
-    t_gen = time.perf_counter() - t0
-    assert X.shape[0] >= 800 and np.all(np.isfinite(X)) and np.all(np.isfinite(Y))
-    model, norm, losses = learned.train(X, Y, epochs=300, batch=256, lr=2e-3, seed=0)
-    assert losses[-1] < losses[0]
-
-    u0 = synth.burgers_ic(n, n, seed=12)
-    T = 1500 * dt  # tens of controlled steps
+    X, Y = learned.generate_samples(n, nu, ics, v0, tol, leja_tol, 25, dt, rng)
+    assert X.shape[0] >= 100 and np.all(np.isfinite(X)) and np.all(np.isfinite(Y))
+    # labels: steps between a quarter and four times the current one
+    assert np.all(Y[:, 0] >= np.log(0.25) - 1e-5) and np.all(Y[:, 0] <= np.log(4.0) + 1e-5)
+    model, norm, losses = learned.train(X, Y, epochs=40, batch=128, lr=2e-3, seed=0)
+    assert np.mean(losses[-5:]) < 0.5 * np.mean(losses[:5])
+    # the label search's shortcut (stop at the first failing larger step;
+    # skip the smaller ones once h passes) against all nine candidates
     ctx = lx.leja_setup(n, n, nu, 0.0, lx.BURGERS, lx.FP64, lx.EXPRB32)
-    ref = torch.from_numpy(u0).cuda()
-    st, info_ref = lx.lx_integrate(ctx, ref, v0, T, 1e-9, leja_tol, 100000, 0.0, 3 * dt, 10)
-    assert st == 0 and abs(info_ref["t"] - T) <= 1e-12 * T
-    print(f"\nsamples {X.shape[0]} (generated in {t_gen:.1f} s), final loss {losses[-1]:.4f}")
-    # two first steps: a well-chosen one (25 dt_CFL) and a cautious one (dt_CFL)
-    for h0 in (25 * dt, dt):
-        runs = {}
-        for name in ("classical", "learned"):
-            u = torch.from_numpy(u0).cuda()
-            torch.cuda.synchronize()
-            t1 = time.perf_counter()
-            if name == "classical":
-                st, info = lx.lx_integrate(ctx, u, v0, T, tol, leja_tol, 100000, 0.0, h0, 10)
-            else:
-                st, info = lx.lx_integrate_learned(ctx, u, v0, T, tol, leja_tol, model, dt, 100000, 0.0, h0, 10)
-            torch.cuda.synchronize()
-            wall = time.perf_counter() - t1
-            assert st == 0 and abs(info["t"] - T) <= 1e-12 * T
-            err = float((u - ref).norm().item() / ref.norm().item())
-            runs[name] = dict(info, wall=wall, err=err)
-        c, l = runs["classical"], runs["learned"]
-        gain_iters = c["leja_iters"] / l["leja_iters"]
-        gain_wall = c["wall"] / l["wall"]
-        print(f"first step {h0 / dt:.0f} dt_CFL:")
-        for k, v in runs.items():
-            print(f"  {k:9s}: steps {v['steps']:4d} rejected {v['rejected']:3d} leja_iters {v['leja_iters']:6d} "
-                  f"wall {v['wall']*1e3:8.1f} ms  rel err vs reference {v['err']:.2e}")
-        print(f"  gain (classical / learned): Leja iterations {gain_iters:.3f}, wall time {gain_wall:.3f}")
-        # the same accuracy class: the learned run's error stays within a few times the classical one
-        assert l["err"] <= max(3.0 * c["err"], 10 * tol)
-        assert c["steps"] >= 20
-        # and it does not cost much more than the classical controller
-        assert gain_iters >= 0.8
+    lo = torch.empty_like(ics[0])
+    his = {j: torch.empty_like(ics[0]) for j in learned.CANDIDATES}
+    same = total = 0
+    for k, u in enumerate(ics):
+        for f in (0.3, 1.0, 4.0, 16.0):
+            h = f * 10 * dt
+            _, _, b_short = learned.label_state(ctx, u, v0, h, tol, leja_tol, lo, his)
+            _, att, b_full = learned.label_state(ctx, u, v0, h, tol, leja_tol, lo, his, exhaustive=True)
+            total += 1
+            same += b_short == b_full
+    print(f"label shortcut agrees with the exhaustive search on {same} of {total} states")
+    assert same >= 0.9 * total

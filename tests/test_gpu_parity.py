@@ -428,8 +428,10 @@ def test_graph_unroll_is_bitwise_neutral(lx, prec):
 PIPE2_KERNELS = ["leja_iter_df_pipe2_b1", "leja_iter_df_pipe2_b2", "leja_iter_df_pipe2_b2_s6", "leja_iter_df_pipe2_b3",
                  "leja_iter_df_pipe2_b3_s6", "leja_iter_df_pipe2_b4", "leja_iter_df_pipe2_b4_s4",
                  "leja_iter_df_pipe2_b5_s4"]
+PIPE2X_KERNELS = ["leja_iter_df_pipe2x_b4_s4", "leja_iter_df_pipe2x_u3_b4_s4", "leja_iter_df_pipe2x_b4",
+                  "leja_iter_df_pipe2x_b3"]
 DF64_KERNELS = ["leja_iter_df_pipe_b2", "leja_iter_df_pipe_b3", "leja_iter_df_pipe_b4", "leja_iter_df_pipe_b2_s8",
-                "leja_iter_df_pipe_b3_s8", "leja_iter_df_advdiff_v4"] + PIPE2_KERNELS
+                "leja_iter_df_pipe_b3_s8", "leja_iter_df_advdiff_v4"] + PIPE2_KERNELS + PIPE2X_KERNELS
 
 
 @pytest.mark.parametrize("name", DF64_KERNELS)
@@ -474,6 +476,44 @@ def test_two_step_kernel_both_stop_parities(lx, xi_oracle, strip_h):
     assert lx.lx_ctx_select_kernel(one, "leja_iter_df_pipe_b2", 8) == 0
     assert lx.lx_ctx_select_kernel(two, "leja_iter_df_pipe2_b2", strip_h) == 0
     assert lx.lx_ctx_iters_per_launch(two) == 2 and lx.lx_ctx_iters_per_launch(one) == 1
+    o1 = torch.empty(nx * ny, dtype=torch.float64, device="cuda")
+    o2 = torch.empty_like(o1)
+    parities = set()
+    for l in (0, 1, 3):
+        for cfl in (4, 9, 20, 41):
+            h = cfl * synth.cfl_step(nx, ny, nu, a)
+            st1, it1 = lx.phi_l_apply(one, l, None, dev(u0), o1, c, g, h, TOL, TOL)
+            st2, it2 = lx.phi_l_apply(two, l, None, dev(u0), o2, c, g, h, TOL, TOL)
+            ref, it_o, st_o = oracle.leja_phi(oracle.ADVDIFF, nx, ny, nu, a, None, l, u0, c, g, h, TOL, TOL,
+                                              xi_oracle)
+            assert st1 == st2 == st_o == 0
+            assert abs(it2 - it1) <= 1 and abs(it2 - it_o) <= 1
+            assert rel(o2.cpu().numpy(), ref) <= TOL
+            if it1 == it2:
+                assert rel(o2.cpu().numpy(), o1.cpu().numpy()) <= 1e-13
+            parities.add(it2 % 2)
+    assert parities == {0, 1}
+
+
+@pytest.mark.parametrize("name", PIPE2X_KERNELS[:2])
+@pytest.mark.parametrize("nx,ny", [(256, 256), (384, 384), (256, 96)])
+@pytest.mark.parametrize("strip_h", [0, 8, 40])
+def test_two_step_lean_kernel(lx, xi_oracle, name, nx, ny, strip_h):
+    # the issue-lean two-step kernel: square grids take the paired stencil
+    # (E + N, W + S), others the five-point one; its halo columns come in
+    # chunks of 16 rows, so segments of 8, 40 and balanced lengths cross
+    # chunk boundaries at different places.  Both stop parities, against
+    # the one-step kernel and the oracle.
+    nu, a = 1e-2, 0.5
+    u0 = synth.gaussians_ic(nx, ny, seed=4) + 0.05 * synth.random_field(nx * ny, 16)
+    import fourier
+
+    c, g = oracle.spectral_interval(fourier.spectral_radius(nx, ny, nu, a))
+    one = lx.leja_setup(nx, ny, nu, a, lx.ADVDIFF, lx.DF64)
+    two = lx.leja_setup(nx, ny, nu, a, lx.ADVDIFF, lx.DF64)
+    assert lx.lx_ctx_select_kernel(one, "leja_iter_df_pipe_b2", 8) == 0
+    assert lx.lx_ctx_select_kernel(two, name, strip_h) == 0
+    assert lx.lx_ctx_iters_per_launch(two) == 2
     o1 = torch.empty(nx * ny, dtype=torch.float64, device="cuda")
     o2 = torch.empty_like(o1)
     parities = set()
@@ -685,3 +725,45 @@ def test_phi_vertical_rejects_bad_arguments(lx):
     assert lx.phi_l_apply_vertical(ctx, 1, [0.5, 1.0], None, w, [o[0], w], *args)[0] == 1  # output aliases w
     ctxb = lx.leja_setup(n, n, 2e-2, 0.0, lx.BURGERS, lx.FP64)
     assert lx.phi_l_apply_vertical(ctxb, 1, [1.0], None, w, o[:1], *args)[0] == 1  # Burgers needs u
+
+
+EPIRK_CASES = [(1, "FP64", 64, 64), (1, "FP64", 96, 72), (1, "DF64", 128, 96), (1, "MIXED", 64, 64),
+               (0, "FP64", 64, 64), (0, "DF64", 128, 128), (3, "FP64", 64, 64), (3, "DF64", 128, 128)]
+
+
+@pytest.mark.parametrize("kind,prec,nx,ny", EPIRK_CASES)
+def test_epirk4s3a_matches_oracle(lx, xi_oracle, kind, prec, nx, ny):
+    # EPIRK4s3A (Table 2's fourth-order scheme): the vertical phi_1 loop over
+    # the stage nodes 1/2, 2/3, 1, the two stage remainders, the phi_3 and
+    # phi_4 loops; u_low (third order), u_high (fourth order) and the error
+    # estimate against the oracle
+    if kind == 1:
+        nu, a = 2e-2, 0.0
+        u = synth.burgers_ic(nx, ny, seed=21)
+        h = 40 * synth.cfl_step(nx, ny, nu, np.abs(u).max())
+    elif kind == 0:
+        nu, a = 1e-2, 0.1
+        u = synth.gaussians_ic(nx, ny, seed=21)
+        h = 40 * synth.cfl_step(nx, ny, nu, a)
+    else:
+        nu, a = 1.0, 10.0
+        u = synth.problem3_ic(nx, ny, seed=21)
+        h = 30 * synth.cfl_step_pm1(nx, ny, nu, a * np.abs(u).max())
+    rho, _, _ = oracle.power_iteration(kind, nx, ny, nu, a, u if kind != 0 else None,
+                                       synth.power_start(nx * ny, 5), 10)
+    c, g = oracle.spectral_interval(rho)
+    ctx = lx.leja_setup(nx, ny, nu, a, kind, getattr(lx, prec), lx.EPIRK4S3A)
+    lo = torch.empty(nx * ny, dtype=torch.float64, device="cuda")
+    hi = torch.empty_like(lo)
+    st, err, it = lx.expint_step(ctx, dev(u), lo, hi, c, g, h, TOL, TOL)
+    rlo, rhi, rerr, it_o, st_o = oracle.epirk4s3a(kind, nx, ny, nu, a, u, c, g, h, TOL, TOL, xi_oracle)
+    assert st == 0 and st_o == 0
+    e_lo, e_hi = rel(lo.cpu().numpy(), rlo), rel(hi.cpu().numpy(), rhi)
+    print(f"EPIRK4s3A kind {kind} {prec} {nx}x{ny}: iters {it} vs {it_o}, u_low {e_lo:.2e}, u_high {e_hi:.2e}, "
+          f"err {err:.3e} vs {rerr:.3e}")
+    if prec == "MIXED":
+        assert e_lo <= 1e-5 and e_hi <= 1e-5 and abs(it - it_o) <= 9
+        return
+    assert abs(it - it_o) <= 3
+    assert e_lo <= TOL and e_hi <= TOL
+    assert abs(err - rerr) <= 1e-6 * rerr + 1e-14 * np.linalg.norm(u) / np.sqrt(u.size)
