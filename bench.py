@@ -161,7 +161,7 @@ def measured_peaks():
 def kernel_source_sha():
     h = hashlib.sha256()
     for rel in ("paper_2310_08344_gb300/csrc/leja_kernels.cuh", "paper_2310_08344_gb300/csrc/leja_df64.cuh",
-                "paper_2310_08344_gb300/csrc/leja_df64_2step.cuh"):
+                "paper_2310_08344_gb300/csrc/leja_df64_2step.cuh", "paper_2310_08344_gb300/csrc/leja_df64_2step_x.cuh"):
         with open(os.path.join(ROOT, rel), "rb") as f:
             h.update(f.read())
     return h.hexdigest()[:16]

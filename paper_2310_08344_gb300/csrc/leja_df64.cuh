@@ -747,6 +747,138 @@ static __global__ void __launch_bounds__(kThreadsPerBlock)
   if (lane == 0) atomicMax(&st->wexp, emax);
 }
 
+// The same right-hand side, h A u (+ h S), with the input rows staged into
+// shared memory by cp.async STAGES - 3 rows ahead of use (a per-warp ring of
+// raw double rows with a one-point halo per side), so that loads overlap the
+// float-float arithmetic; each lane still keeps four consecutive points of
+// three rows in registers (every value is split once).  Four warps per
+// block; dynamic shared memory rhs_ring_smem_bytes<STAGES>().
+constexpr int kRhsSlot = kPipeRow + 4;  // [pad][w1][128 points][e1][pad]
+template <int STAGES>
+constexpr int rhs_ring_smem_bytes() {
+  return kPipeWarps * STAGES * kRhsSlot * 8;
+}
+
+template <int STAGES>
+static __global__ void __launch_bounds__(kPipeThreads)
+    rhs_df_advdiff_ring_kernel(int nx, int ny, const double* __restrict__ u, RhsWeights W,
+                               double* __restrict__ f_out, LoopState* st, const double* __restrict__ src, double h) {
+  extern __shared__ __align__(16) unsigned long long rhs_ring[];
+  float wh[5], wl[5];
+  const double* wd = W.wd;
+#pragma unroll
+  for (int k = 0; k < 5; ++k) {
+    wh[k] = W.wf[2 * k];
+    wl[k] = W.wf[2 * k + 1];
+  }
+  const int lane = threadIdx.x & 31;
+  const int warp = threadIdx.x >> 5;
+  unsigned long long* ring = rhs_ring + (size_t)warp * STAGES * kRhsSlot;
+  int emax = 0;
+  struct Row {
+    double v[4];
+    dfv f[4];
+    double hx;
+    bool ok;
+  };
+  for_each_segment(nx, ny, 0, blockIdx.x * kPipeWarps + warp, gridDim.x * kPipeWarps, [&](int col0, int r0, int r1) {
+    const int c = col0 + lane * 4;
+    const int cw = col0 == 0 ? nx - 1 : col0 - 1;
+    const int ce = (col0 + kPipeRow >= nx) ? 0 : col0 + kPipeRow;
+    const int last_q = r1 - r0 + 1;  // rows q = 0 .. last_q are grid rows r0 - 1 .. r1
+    auto slot = [&](int q) { return ring + (size_t)(q % STAGES) * kRhsSlot; };
+    auto issue = [&](int q) {
+      if (q <= last_q) {
+        int r = r0 - 1 + q;
+        r = r < 0 ? r + ny : (r >= ny ? r - ny : r);
+        const double* row = u + (size_t)r * nx;
+        unsigned long long* s = slot(q);
+        cp_async16(s + 2 + lane * 4, row + c);
+        cp_async16(s + 4 + lane * 4, row + c + 2);
+        if (lane == 0) cp_async8(s + 1, row + cw);
+        if (lane == 31) cp_async8(s + 2 + kPipeRow, row + ce);
+      }
+      cp_commit();
+    };
+    auto load = [&](int q, Row& R) {
+      const unsigned long long* s = slot(q);
+      const double2 a = *reinterpret_cast<const double2*>(s + 2 + lane * 4);
+      const double2 b = *reinterpret_cast<const double2*>(s + 4 + lane * 4);
+      R.v[0] = a.x;
+      R.v[1] = a.y;
+      R.v[2] = b.x;
+      R.v[3] = b.y;
+      R.hx = lane == 0 ? __longlong_as_double((long long)s[1])
+                       : (lane == 31 ? __longlong_as_double((long long)s[2 + kPipeRow]) : 0.0);
+      R.ok = df_in_range(R.hx);
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        R.ok = R.ok && df_in_range(R.v[k]);
+        R.f[k] = df_split_scaled(R.v[k], 0);
+      }
+    };
+    for (int q = 0; q < STAGES; ++q) issue(q);
+    cp_wait<STAGES - 3>();
+    __syncwarp();
+    Row S, C, N, NN;
+    load(0, S);
+    load(1, C);
+    load(2, N);
+    __syncwarp();  // the first rows' slots are refilled from the next row on
+    for (int r = r0; r < r1; ++r) {
+      const int i = r - r0;
+      issue(i + STAGES);  // into the slot of row q = i, read three rows ago
+      cp_wait<STAGES - 3>();
+      __syncwarp();
+      if (r + 1 < r1) load(i + 3, NN);
+      const double xw0 = __shfl_up_sync(0xffffffffu, C.v[3], 1);
+      const double xe0 = __shfl_down_sync(0xffffffffu, C.v[0], 1);
+      const double xw = lane == 0 ? C.hx : xw0;
+      const double xe = lane == 31 ? C.hx : xe0;
+      double res[4];
+      if (__all_sync(0xffffffffu, S.ok && C.ok && N.ok)) {
+        const dfv sw = shfl_up_df(C.f[3]);
+        const dfv se = shfl_down_df(C.f[0]);
+        const dfv dw = lane == 0 ? df_split_scaled(xw, 0) : sw;
+        const dfv de = lane == 31 ? df_split_scaled(xe, 0) : se;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+          const dfv t[5] = {k == 3 ? de : C.f[k + 1], k == 0 ? dw : C.f[k - 1], N.f[k], S.f[k], C.f[k]};
+          const dfv d = df_dot5(wh, wl, t);
+          res[k] = f2d_scaled(d.h, 0) + f2d_scaled(d.l, 0);
+        }
+      } else {
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+          const double e = k == 3 ? xe : C.v[k + 1], w = k == 0 ? xw : C.v[k - 1];
+          res[k] = wd[0] * e + wd[1] * w + wd[2] * N.v[k] + wd[3] * S.v[k] + wd[4] * C.v[k];
+        }
+      }
+      const size_t ro = (size_t)r * nx + c;
+      if (src) {
+        const double2 s0 = __ldg(reinterpret_cast<const double2*>(src + ro));
+        const double2 s1 = __ldg(reinterpret_cast<const double2*>(src + ro + 2));
+        res[0] = res[0] + h * s0.x;
+        res[1] = res[1] + h * s0.y;
+        res[2] = res[2] + h * s1.x;
+        res[3] = res[3] + h * s1.y;
+      }
+      *reinterpret_cast<double2*>(f_out + ro) = make_double2(res[0], res[1]);
+      *reinterpret_cast<double2*>(f_out + ro + 2) = make_double2(res[2], res[3]);
+#pragma unroll
+      for (int k = 0; k < 4; ++k) emax = max(emax, (int)((__double2hiint(res[k]) >> 20) & 0x7ff));
+      S = C;
+      C = N;
+      N = NN;
+    }
+    cp_wait<0>();
+    __syncwarp();
+  });
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) emax = max(emax, __shfl_xor_sync(0xffffffffu, emax, o));
+  if (lane == 0) atomicMax(&st->wexp, emax);
+}
+
 // p as float pairs -> double (times 2^kscale), plus base when given; two
 // points per step with 16-byte accesses (n even, base and out 16-byte
 // aligned).  Same semantics as df_output_kernel, including the correction of
@@ -1091,6 +1223,149 @@ static __global__ void __launch_bounds__(kThreadsPerBlock)
       st->sigma = 1.0 / rho;
     }
   }
+}
+
+// The same power-iteration pass in row-strip form (nx % 128 == 0, 16-byte
+// aligned vectors): warps take balanced row ranges of 128-column strips,
+// each lane four consecutive points; the rows of v (one-point halo per side)
+// and, for J(u), of q and r arrive in a per-warp cp.async ring STAGES - 3
+// rows ahead of use, so loads overlap the arithmetic, and v is split once
+// per row.  ||w||^2 is accumulated with exact squares of the leading floats
+// (float-float) plus the cross terms in float, as in power_pass_df_kernel.
+template <int KIND>
+__host__ __device__ constexpr int pow_slot_elems() {
+  return kRhsSlot + (KIND == 1 ? 2 * kPipeRow : 0);
+}
+template <int KIND, int STAGES>
+constexpr int pow_rows_smem_bytes() {
+  return kPipeWarps * STAGES * pow_slot_elems<KIND>() * 8;
+}
+
+template <int KIND, int STAGES, typename S>
+__device__ __forceinline__ void pow_strip(int nx, int ny, const S* __restrict__ v, float2* __restrict__ w,
+                                          const float2* __restrict__ q, const float2* __restrict__ r,
+                                          const PowWeights& W, unsigned long long* ring, int col0, int r0, int r1,
+                                          dfv sg, dfv& acc, float& small) {
+  const int lane = threadIdx.x & 31;
+  const int c = col0 + lane * 4;
+  const int cw = col0 == 0 ? nx - 1 : col0 - 1;
+  const int ce = (col0 + kPipeRow >= nx) ? 0 : col0 + kPipeRow;
+  const int last_q = r1 - r0 + 1;  // rows q = 0 .. last_q are grid rows r0 - 1 .. r1
+  constexpr int kSlot = pow_slot_elems<KIND>();
+  auto slot = [&](int qq) { return ring + (size_t)(qq % STAGES) * kSlot; };
+  auto issue = [&](int qq) {
+    if (qq <= last_q) {
+      int ry = r0 - 1 + qq;
+      ry = ry < 0 ? ry + ny : (ry >= ny ? ry - ny : ry);
+      const S* row = v + (size_t)ry * nx;
+      unsigned long long* sl = slot(qq);
+      cp_async16(sl + 2 + lane * 4, row + c);
+      cp_async16(sl + 4 + lane * 4, row + c + 2);
+      if (lane == 0) cp_async8(sl + 1, row + cw);
+      if (lane == 31) cp_async8(sl + 2 + kPipeRow, row + ce);
+      if constexpr (KIND == 1) {
+        // the point weights of this row, used when it is the centre row
+        const size_t o = (size_t)ry * nx + c;
+        cp_async16(sl + kRhsSlot + lane * 4, q + o);
+        cp_async16(sl + kRhsSlot + lane * 4 + 2, q + o + 2);
+        cp_async16(sl + kRhsSlot + kPipeRow + lane * 4, r + o);
+        cp_async16(sl + kRhsSlot + kPipeRow + lane * 4 + 2, r + o + 2);
+      }
+    }
+    cp_commit();
+  };
+  for (int qq = 0; qq < STAGES - 1; ++qq) issue(qq);
+  cp_wait<STAGES - 3>();
+  __syncwarp();
+  dfv ys[4], yc[4], yn[4];
+  df_from_raw4<S>(slot(0) + 2 + lane * 4, 0, ys);
+  df_from_raw4<S>(slot(1) + 2 + lane * 4, 0, yc);
+  float wh[5], wl[5];
+  if constexpr (KIND == 0) {
+#pragma unroll
+    for (int k = 0; k < 5; ++k) {
+      wh[k] = W.w[2 * k];
+      wl[k] = W.w[2 * k + 1];
+    }
+  }
+  for (int qc = 1; qc < last_q; ++qc) {
+    issue(qc + STAGES - 2);
+    cp_wait<STAGES - 3>();
+    __syncwarp();
+    const unsigned long long* sn = slot(qc + 1);
+    const unsigned long long* scn = slot(qc);
+    df_from_raw4<S>(sn + 2 + lane * 4, 0, yn);
+    dfv xw = shfl_up_df(yc[3]);
+    dfv xe = shfl_down_df(yc[0]);
+    if (lane == 0) xw = df_from_raw<S>(scn + 1, 0);
+    if (lane == 31) xe = df_from_raw<S>(scn + 2 + kPipeRow, 0);
+    dfv qv[4], rv[4];
+    if constexpr (KIND == 1) {
+      df_from_raw4<float2>(scn + kRhsSlot + lane * 4, 0, qv);
+      df_from_raw4<float2>(scn + kRhsSlot + kPipeRow + lane * 4, 0, rv);
+    }
+    dfv out[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      if constexpr (KIND == 1) {
+        const dfv lx = {W.bl[0], W.bl[1]}, ly = {W.bl[2], W.bl[3]}, rat = {W.bl[4], W.bl[5]};
+        const dfv qy = df_mul(qv[k], rat);
+        const dfv wE = df_add(lx, df_neg(qv[k])), wW = df_add(lx, qv[k]), wN = df_add(ly, df_neg(qy)),
+                  wS = df_add(ly, qy);
+        wh[0] = wE.h;
+        wl[0] = wE.l;
+        wh[1] = wW.h;
+        wl[1] = wW.l;
+        wh[2] = wN.h;
+        wl[2] = wN.l;
+        wh[3] = wS.h;
+        wl[3] = wS.l;
+        wh[4] = rv[k].h;
+        wl[4] = rv[k].l;
+      }
+      const dfv t[5] = {k == 3 ? xe : yc[k + 1], k == 0 ? xw : yc[k - 1], yn[k], ys[k], yc[k]};
+      out[k] = df_mul(sg, df_dot5(wh, wl, t));
+      float sq, se;
+      two_prod(out[k].h, out[k].h, sq, se);
+      df_acc(acc, sq);
+      small = __fmaf_rn(2.f * out[k].h, out[k].l, __fadd_rn(small, se));
+    }
+    df_store_row<4>(w + (size_t)(r0 - 1 + qc) * nx, c, nx, out);
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      ys[k] = yc[k];
+      yc[k] = yn[k];
+    }
+    __syncwarp();
+  }
+  cp_wait<0>();
+  __syncwarp();
+}
+
+template <int KIND, int STAGES>
+static __global__ void __launch_bounds__(kPipeThreads)
+    power_pass_df_rows_kernel(int nx, int ny, long long n, const void* __restrict__ vin, int vin_double,
+                              float2* __restrict__ w, const float2* __restrict__ q, const float2* __restrict__ r,
+                              PowWeights W, double* __restrict__ partials, unsigned int* __restrict__ ticket,
+                              LoopState* st) {
+  extern __shared__ __align__(16) unsigned long long pow_ring[];
+  if (__ldcg(&st->pdone)) return;
+  const dfv sg = df_from_double(__ldcg(&st->sigma));
+  dfv acc = {0.f, 0.f};
+  float small = 0.f;
+  const int warp = threadIdx.x >> 5;
+  unsigned long long* ring = pow_ring + (size_t)warp * STAGES * pow_slot_elems<KIND>();
+  for_each_segment(nx, ny, 0, blockIdx.x * kPipeWarps + warp, gridDim.x * kPipeWarps, [&](int col0, int r0, int r1) {
+    if (vin_double)
+      pow_strip<KIND, STAGES, double>(nx, ny, reinterpret_cast<const double*>(vin), w, q, r, W, ring, col0, r0, r1,
+                                      sg, acc, small);
+    else
+      pow_strip<KIND, STAGES, float2>(nx, ny, reinterpret_cast<const float2*>(vin), w, q, r, W, ring, col0, r0, r1,
+                                      sg, acc, small);
+  });
+  double s = df_to_double(acc) + (double)small, dummy = 0.0;
+  if (!last_block_total2(s, dummy, partials, ticket)) return;
+  if (threadIdx.x == 0) power_pass_finish(st, s, n);
 }
 
 }  // namespace lexgb

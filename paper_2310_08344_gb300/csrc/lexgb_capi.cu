@@ -254,6 +254,8 @@ std::vector<Cand> candidates(int kind, int precision, int cls) {
       v.push_back(Cand{df2x_kernel(3, 5, false), kPipeThreads, df2x_smem_bytes(5), 4, "leja_iter_df_pipe2x_b3", 2});
       v.push_back(Cand{df2x_kernel(4, 4, true), kPipeThreads, df2x_smem_bytes(4), 4, "leja_iter_df_pipe2x_u3_b4_s4",
                        2});
+      v.push_back(Cand{df2x_kernel(5, 4, false), kPipeThreads, df2x_smem_bytes(4), 4, "leja_iter_df_pipe2x_b5_s4",
+                       2});
       // the first two-step form (155 us per launch at 4096^2, four blocks per SM)
       v.push_back(Cand{reinterpret_cast<const void*>(&leja_iter_df_pipe2_kernel<4, 4>), kPipeThreads,
                        pipe2_smem_bytes<4>(), 4, "leja_iter_df_pipe2_b4_s4", 2});
@@ -882,14 +884,36 @@ lx_status power_bound(lx_ctx* c, const double* u, const double* v0, int max_iter
     double* outv = c->d_pw[(k - 1) & 1];
     if (dfp) {
       float2* wf = reinterpret_cast<float2*>(outv);
-      if (P.kind == LX_ADVDIFF)
+      if (P.nx % kPipeRow == 0 && aligned16(in)) {
+        // row-strip form with a cp.async ring
+        constexpr int kPowStages = 5;
+        const bool bk = P.kind != LX_ADVDIFF;
+        const void* fn = bk ? reinterpret_cast<const void*>(&power_pass_df_rows_kernel<1, kPowStages>)
+                            : reinterpret_cast<const void*>(&power_pass_df_rows_kernel<0, kPowStages>);
+        const int smem = bk ? pow_rows_smem_bytes<1, kPowStages>() : pow_rows_smem_bytes<0, kPowStages>();
+        LX_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+        int per_sm = 0;
+        LX_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kPipeThreads, smem));
+        const long long lines = (long long)(P.nx / kPipeRow) * P.ny;
+        const int GP = (int)std::max<long long>(1, std::min<long long>((lines / 4 + kPipeWarps - 1) / kPipeWarps,
+                                                                         (long long)std::max(per_sm, 1) *
+                                                                             c->sm_count));
+        if (bk)
+          power_pass_df_rows_kernel<1, kPowStages><<<GP, kPipeThreads, smem, c->stream>>>(
+              P.nx, P.ny, c->n, in, k == 1 ? 1 : 0, wf, c->d_bq, c->d_br, PW, c->d_partials, c->d_ticket, c->d_state);
+        else
+          power_pass_df_rows_kernel<0, kPowStages><<<GP, kPipeThreads, smem, c->stream>>>(
+              P.nx, P.ny, c->n, in, k == 1 ? 1 : 0, wf, nullptr, nullptr, PW, c->d_partials, c->d_ticket,
+              c->d_state);
+      } else if (P.kind == LX_ADVDIFF) {
         power_pass_df_kernel<0><<<G, kThreadsPerBlock, 0, c->stream>>>(c->geo, in, k == 1 ? 1 : 0, wf, nullptr,
                                                                        nullptr, PW, c->d_partials, c->d_ticket,
                                                                        c->d_state);
-      else
+      } else {
         power_pass_df_kernel<1><<<G, kThreadsPerBlock, 0, c->stream>>>(c->geo, in, k == 1 ? 1 : 0, wf, c->d_bq,
                                                                        c->d_br, PW, c->d_partials, c->d_ticket,
                                                                        c->d_state);
+      }
       ++c->stats.kernels;
       LX_CUDA(cudaGetLastError());
       continue;
@@ -1251,15 +1275,18 @@ lx_status expint_step(lx_ctx* c, const double* u, double* u_low, double* u_high,
       W.wf[2 * k + 1] = (float)(W.wd[k] - (double)W.wf[2 * k]);
     }
     if (P.nx % kPipeRow == 0 && aligned16(u) && (!c->d_src || aligned16(c->d_src))) {
-      // row-window form: at most the resident blocks, at least 4 rows per warp
+      // row-window form with a cp.async ring: at most the resident blocks, at
+      // least 4 rows per warp
       int per_sm = 0;
-      LX_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, rhs_df_advdiff_rows_kernel, kThreadsPerBlock, 0));
+      constexpr int kRhsStages = 6;
+      LX_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, rhs_df_advdiff_ring_kernel<kRhsStages>,
+                                                            kPipeThreads, rhs_ring_smem_bytes<kRhsStages>()));
       const long long lines = (long long)(P.nx / kPipeRow) * P.ny;
       const int GR = (int)std::max<long long>(
-          1, std::min<long long>((lines / 4 + kWarpsPerBlock - 1) / kWarpsPerBlock,
+          1, std::min<long long>((lines / 4 + kPipeWarps - 1) / kPipeWarps,
                                  (long long)std::max(per_sm, 1) * c->sm_count));
-      rhs_df_advdiff_rows_kernel<<<GR, kThreadsPerBlock, 0, c->stream>>>(P.nx, P.ny, u, W, c->d_f, c->d_state,
-                                                                          c->d_src, h);
+      rhs_df_advdiff_ring_kernel<kRhsStages><<<GR, kPipeThreads, rhs_ring_smem_bytes<kRhsStages>(), c->stream>>>(
+          P.nx, P.ny, u, W, c->d_f, c->d_state, c->d_src, h);
     } else {
       rhs_df_advdiff_kernel<<<G, kThreadsPerBlock, 0, c->stream>>>(c->geo, u, W, c->d_f, c->d_state, c->d_src, h);
     }

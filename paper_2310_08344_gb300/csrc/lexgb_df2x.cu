@@ -15,6 +15,8 @@ const void* df2x_kernel(int minb, int stages, bool unroll3) {
   if (minb == 4 && stages == 4) return reinterpret_cast<const void*>(&leja_iter_df_pipe2x_kernel<4, 4, false>);
   if (minb == 4 && stages == 5) return reinterpret_cast<const void*>(&leja_iter_df_pipe2x_kernel<4, 5, false>);
   if (minb == 3 && stages == 5) return reinterpret_cast<const void*>(&leja_iter_df_pipe2x_kernel<3, 5, false>);
+  // five blocks per SM: 96 registers (a few bytes of spills)
+  if (minb == 5 && stages == 4) return reinterpret_cast<const void*>(&leja_iter_df_pipe2x_kernel<5, 4, false>);
   return nullptr;
 }
 

@@ -8,8 +8,9 @@ workloads) is applied to the workload it was made for: viscous Burgers at
 10 dt_CFL, tol 1e-4, against the classical controller from the same first
 step.  The embedded error test accepts or rejects every step in both runs.
 Asserted: fewer Leja iterations and less wall time (best of three runs each)
-at the same accuracy class against a tight-tolerance run; reported as well:
-a ten times longer horizon, where the ramp-up is a small part of the run.
+at the same accuracy class against a tight-tolerance run; on a ten times
+longer horizon, where the ramp-up is a small part of the run, fewer Leja
+iterations (the wall time is reported).
 
 A second test runs the training pipeline itself at a small scale (samples
 from the library's own EXPRB32 steps, labels, GPU training), and checks the
@@ -82,9 +83,12 @@ def test_trained_controller_gain(lx, horizon):
     print(f"  gain (classical / learned): Leja iterations {gain_iters:.3f}, wall time {gain_wall:.3f}")
     # the same accuracy class: the error test bounds both runs alike
     assert l["err"] <= max(3.0 * c["err"], 10 * tol)
+    # fewer Leja iterations on both horizons; on the long one (ramp-up a
+    # small part of it) the wall-time gain is within run-to-run noise and is
+    # reported, not asserted
+    assert gain_iters > 1.0
     if horizon == 200:
-        assert gain_iters > 1.0 and gain_wall > 1.0
-    # the long run (ramp-up a small part of it) is reported, not asserted
+        assert gain_wall > 1.0
 
 
 def test_training_pipeline_small(lx):
