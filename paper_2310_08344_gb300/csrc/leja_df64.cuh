@@ -639,120 +639,24 @@ __device__ __forceinline__ void df_strip_pipe(const LoopArgs& A, const S* __rest
   __syncwarp();
 }
 
-// h A u (+ h S) for the diffusion-advection operator when nx % 128 == 0 and
-// u, f_out, src are 16-byte aligned: warps take balanced row ranges of
-// 128-column strips; each lane keeps 4 consecutive points of three rows in
-// registers (two rows loaded ahead), so every value of u is loaded and split
-// into floats once, and loads and stores are 16 bytes wide.  A row whose
-// inputs include a value outside the float range is computed in double by
-// the whole warp.  Records the largest exponent of the result like
-// rhs_df_advdiff_kernel.
+// Whether a double lies in the range where the float-float right-hand side
+// applies (|x| in [2^-100, 2^100), or zero).
 __device__ __forceinline__ bool df_in_range(double x) {
   const int ex = (int)((__double_as_longlong(x) >> 52) & 0x7ff);
   return ex == 0 || (ex > 1023 - 100 && ex < 1023 + 100);
 }
 
-static __global__ void __launch_bounds__(kThreadsPerBlock)
-    rhs_df_advdiff_rows_kernel(int nx, int ny, const double* __restrict__ u, RhsWeights W,
-                               double* __restrict__ f_out, LoopState* st, const double* __restrict__ src, double h) {
-  float wh[5], wl[5];
-  const double* wd = W.wd;
-#pragma unroll
-  for (int k = 0; k < 5; ++k) {
-    wh[k] = W.wf[2 * k];
-    wl[k] = W.wf[2 * k + 1];
-  }
-  const int lane = threadIdx.x & 31;
-  const int warp = threadIdx.x >> 5;
-  int emax = 0;
-  struct Row {
-    double v[4];
-    dfv f[4];   // v split into float pairs (meaningless where v is out of the float range)
-    double hx;  // lane 0: west halo point, lane 31: east halo point
-    bool ok;    // every value of this lane's part of the row is in the float range
-  };
-  for_each_segment(nx, ny, 0, blockIdx.x * kWarpsPerBlock + warp, gridDim.x * kWarpsPerBlock,
-                   [&](int col0, int r0, int r1) {
-    const int c = col0 + lane * 4;
-    const int cw = col0 == 0 ? nx - 1 : col0 - 1;
-    const int ce = (col0 + kPipeRow >= nx) ? 0 : col0 + kPipeRow;
-    auto load = [&](int r, Row& R) {
-      r = r < 0 ? r + ny : (r >= ny ? r - ny : r);
-      const double* row = u + (size_t)r * nx;
-      const double2 a = __ldg(reinterpret_cast<const double2*>(row + c));
-      const double2 b = __ldg(reinterpret_cast<const double2*>(row + c + 2));
-      R.v[0] = a.x;
-      R.v[1] = a.y;
-      R.v[2] = b.x;
-      R.v[3] = b.y;
-      R.hx = lane == 0 ? __ldg(row + cw) : (lane == 31 ? __ldg(row + ce) : 0.0);
-      R.ok = df_in_range(R.hx);
-#pragma unroll
-      for (int k = 0; k < 4; ++k) {
-        R.ok = R.ok && df_in_range(R.v[k]);
-        R.f[k] = df_split_scaled(R.v[k], 0);
-      }
-    };
-    Row S, C, N, NN;
-    load(r0 - 1, S);
-    load(r0, C);
-    load(r0 + 1, N);
-    for (int r = r0; r < r1; ++r) {
-      if (r + 1 < r1) load(r + 2, NN);
-      const double xw0 = __shfl_up_sync(0xffffffffu, C.v[3], 1);
-      const double xe0 = __shfl_down_sync(0xffffffffu, C.v[0], 1);
-      const double xw = lane == 0 ? C.hx : xw0;
-      const double xe = lane == 31 ? C.hx : xe0;
-      double res[4];
-      if (__all_sync(0xffffffffu, S.ok && C.ok && N.ok)) {
-        // every lane takes part in both shuffles (full-mask shuffles must not
-        // sit in a divergent branch); lanes 0 and 31 then use their halo
-        const dfv sw = shfl_up_df(C.f[3]);
-        const dfv se = shfl_down_df(C.f[0]);
-        const dfv dw = lane == 0 ? df_split_scaled(xw, 0) : sw;
-        const dfv de = lane == 31 ? df_split_scaled(xe, 0) : se;
-#pragma unroll
-        for (int k = 0; k < 4; ++k) {
-          const dfv t[5] = {k == 3 ? de : C.f[k + 1], k == 0 ? dw : C.f[k - 1], N.f[k], S.f[k], C.f[k]};
-          const dfv d = df_dot5(wh, wl, t);
-          res[k] = f2d_scaled(d.h, 0) + f2d_scaled(d.l, 0);
-        }
-      } else {
-#pragma unroll
-        for (int k = 0; k < 4; ++k) {
-          const double e = k == 3 ? xe : C.v[k + 1], w = k == 0 ? xw : C.v[k - 1];
-          res[k] = wd[0] * e + wd[1] * w + wd[2] * N.v[k] + wd[3] * S.v[k] + wd[4] * C.v[k];
-        }
-      }
-      const size_t ro = (size_t)r * nx + c;
-      if (src) {
-        const double2 s0 = __ldg(reinterpret_cast<const double2*>(src + ro));
-        const double2 s1 = __ldg(reinterpret_cast<const double2*>(src + ro + 2));
-        res[0] = res[0] + h * s0.x;
-        res[1] = res[1] + h * s0.y;
-        res[2] = res[2] + h * s1.x;
-        res[3] = res[3] + h * s1.y;
-      }
-      *reinterpret_cast<double2*>(f_out + ro) = make_double2(res[0], res[1]);
-      *reinterpret_cast<double2*>(f_out + ro + 2) = make_double2(res[2], res[3]);
-#pragma unroll
-      for (int k = 0; k < 4; ++k) emax = max(emax, (int)((__double2hiint(res[k]) >> 20) & 0x7ff));
-      S = C;
-      C = N;
-      N = NN;
-    }
-  });
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) emax = max(emax, __shfl_xor_sync(0xffffffffu, emax, o));
-  if (lane == 0) atomicMax(&st->wexp, emax);
-}
-
-// The same right-hand side, h A u (+ h S), with the input rows staged into
-// shared memory by cp.async STAGES - 3 rows ahead of use (a per-warp ring of
-// raw double rows with a one-point halo per side), so that loads overlap the
-// float-float arithmetic; each lane still keeps four consecutive points of
-// three rows in registers (every value is split once).  Four warps per
-// block; dynamic shared memory rhs_ring_smem_bytes<STAGES>().
+// h A u (+ h S) for the diffusion-advection operator when nx % 128 == 0 and
+// u, f_out, src are 16-byte aligned: warps take balanced row ranges of
+// 128-column strips; the input rows are staged into shared memory by
+// cp.async STAGES - 3 rows ahead of use (a per-warp ring of raw double rows
+// with a one-point halo per side), so that loads overlap the float-float
+// arithmetic; each lane keeps four consecutive points of three rows in
+// registers, so every value is split into floats once.  A row whose inputs
+// include a value outside the float range is computed in double by the
+// whole warp.  Records the largest exponent of the result like
+// rhs_df_advdiff_kernel.  Four warps per block; dynamic shared memory
+// rhs_ring_smem_bytes<STAGES>().
 constexpr int kRhsSlot = kPipeRow + 4;  // [pad][w1][128 points][e1][pad]
 template <int STAGES>
 constexpr int rhs_ring_smem_bytes() {

@@ -245,26 +245,11 @@ __device__ __forceinline__ void df2x_strip(const LoopArgs& A, const S* __restric
   __syncwarp();
 }
 
-template <int STAGES, typename S, bool FIRST, bool UNROLL3>
-__device__ __forceinline__ void df2x_strip_any(bool sq, const LoopArgs& A, const S* __restrict__ src,
-                                               float2* __restrict__ dst, float2* __restrict__ p,
-                                               unsigned long long* ring, unsigned long long* hbuf, int col0, int r0,
-                                               int r1,
-                                               const float (&wah)[5], const float (&wal)[5], const float (&wbh)[5],
-                                               const float (&wbl)[5], dfv d0, dfv dm1, dfv dm2, int sc,
-                                               dfv (&acc)[4]) {
-  if (sq)
-    df2x_strip<STAGES, S, FIRST, true, UNROLL3>(A, src, dst, p, ring, hbuf, col0, r0, r1, wah, wal, wbh, wbl, d0, dm1,
-                                                dm2, sc, acc);
-  else
-    df2x_strip<STAGES, S, FIRST, false, UNROLL3>(A, src, dst, p, ring, hbuf, col0, r0, r1, wah, wal, wbh, wbl, d0,
-                                                 dm1, dm2, sc, acc);
-}
-
 // Launch m (even) of the two-step loop: y_m, p_m -> y_{m+2}, p_{m+2}; the
 // same launch protocol, buffers and stopping logic as
-// leja_iter_df_pipe2_kernel.
-template <int MINB, int STAGES, bool UNROLL3>
+// leja_iter_df_pipe2_kernel.  SQ: the paired stencil, for square grids only
+// (the host offers these instances only when nx == ny).
+template <int MINB, int STAGES, bool UNROLL3, bool SQ>
 __global__ void __launch_bounds__(kPipeThreads, MINB)
     leja_iter_df_pipe2x_kernel(const LoopArgs* __restrict__ Ap, LoopState* __restrict__ st,
                                double* __restrict__ partials, unsigned int* __restrict__ ticket,
@@ -295,7 +280,6 @@ __global__ void __launch_bounds__(kPipeThreads, MINB)
   const float wal[5] = {A.wf[1] * swf, A.wf[3] * swf, A.wf[5] * swf, A.wf[7] * swf, wca.l};
   const float wbh[5] = {A.wf[0], A.wf[2], A.wf[4], A.wf[6], wcb.h};
   const float wbl[5] = {A.wf[1], A.wf[3], A.wf[5], A.wf[7], wcb.l};
-  const bool sq = A.wf[0] == A.wf[4] && A.wf[1] == A.wf[5] && A.wf[2] == A.wf[6] && A.wf[3] == A.wf[7];
   const int pass = m >> 1;
   float2* dst = reinterpret_cast<float2*>((pass & 1) ? A.y1 : A.y0);
   const float2* src = reinterpret_cast<const float2*>((pass & 1) ? A.y0 : A.y1);
@@ -305,10 +289,10 @@ __global__ void __launch_bounds__(kPipeThreads, MINB)
   unsigned long long* hbuf = pipe2x_smem + (size_t)kPipeWarps * STAGES * kSlotElems2 + (size_t)warp * 32 * 5;
   for_each_segment(nx, ny, H, blockIdx.x * kPipeWarps + warp, gridDim.x * kPipeWarps, [&](int col0, int r0, int r1) {
     if (m == 0)
-      df2x_strip_any<STAGES, double, true, UNROLL3>(sq, A, A.w, dst, A.pdf, ring, hbuf, col0, r0, r1, wah, wal, wbh, wbl, d0, dm1,
+      df2x_strip<STAGES, double, true, SQ, UNROLL3>(A, A.w, dst, A.pdf, ring, hbuf, col0, r0, r1, wah, wal, wbh, wbl, d0, dm1,
                                            dm2, kexp, acc);
     else
-      df2x_strip_any<STAGES, float2, false, UNROLL3>(sq, A, src, dst, A.pdf, ring, hbuf, col0, r0, r1, wah, wal, wbh, wbl, d0, dm1,
+      df2x_strip<STAGES, float2, false, SQ, UNROLL3>(A, src, dst, A.pdf, ring, hbuf, col0, r0, r1, wah, wal, wbh, wbl, d0, dm1,
                                             dm2, kexp, acc);
   });
   double v[4] = {df_to_double(acc[0]), df_to_double(acc[1]), df_to_double(acc[2]), df_to_double(acc[3])};

@@ -169,7 +169,7 @@ bool is_burgers(int kind) { return kind == LX_BURGERS || kind == LX_BURGERS_UP3;
 bool is_up3(int kind) { return kind == LX_ADVDIFF_UP3 || kind == LX_BURGERS_UP3; }
 
 // Candidates for (kind, precision, class); the first is the default.
-std::vector<Cand> candidates(int kind, int precision, int cls) {
+std::vector<Cand> candidates(int kind, int precision, int cls, bool square = false) {
   const bool wide = cls == kVec2;
   std::vector<Cand> v;
   if (is_up3(kind)) {
@@ -248,14 +248,17 @@ std::vector<Cand> candidates(int kind, int precision, int cls) {
     if (wide) {
       // default without autotuning: two iterations per pass at four blocks
       // per SM, issue-lean form
-      v.push_back(Cand{df2x_kernel(4, 4, false), kPipeThreads, df2x_smem_bytes(4), 4, "leja_iter_df_pipe2x_b4_s4",
-                       2});
-      v.push_back(Cand{df2x_kernel(4, 5, false), kPipeThreads, df2x_smem_bytes(5), 4, "leja_iter_df_pipe2x_b4", 2});
-      v.push_back(Cand{df2x_kernel(3, 5, false), kPipeThreads, df2x_smem_bytes(5), 4, "leja_iter_df_pipe2x_b3", 2});
-      v.push_back(Cand{df2x_kernel(4, 4, true), kPipeThreads, df2x_smem_bytes(4), 4, "leja_iter_df_pipe2x_u3_b4_s4",
-                       2});
-      v.push_back(Cand{df2x_kernel(5, 4, false), kPipeThreads, df2x_smem_bytes(4), 4, "leja_iter_df_pipe2x_b5_s4",
-                       2});
+      // (square grids get the instances with the paired stencil built in)
+      v.push_back(Cand{df2x_kernel(4, 4, false, square), kPipeThreads, df2x_smem_bytes(4), 4,
+                       "leja_iter_df_pipe2x_b4_s4", 2});
+      v.push_back(Cand{df2x_kernel(4, 5, false, square), kPipeThreads, df2x_smem_bytes(5), 4,
+                       "leja_iter_df_pipe2x_b4", 2});
+      v.push_back(Cand{df2x_kernel(3, 5, false, square), kPipeThreads, df2x_smem_bytes(5), 4,
+                       "leja_iter_df_pipe2x_b3", 2});
+      v.push_back(Cand{df2x_kernel(4, 4, true, square), kPipeThreads, df2x_smem_bytes(4), 4,
+                       "leja_iter_df_pipe2x_u3_b4_s4", 2});
+      v.push_back(Cand{df2x_kernel(5, 4, false, square), kPipeThreads, df2x_smem_bytes(4), 4,
+                       "leja_iter_df_pipe2x_b5_s4", 2});
       // the first two-step form (155 us per launch at 4096^2, four blocks per SM)
       v.push_back(Cand{reinterpret_cast<const void*>(&leja_iter_df_pipe2_kernel<4, 4>), kPipeThreads,
                        pipe2_smem_bytes<4>(), 4, "leja_iter_df_pipe2_b4_s4", 2});
@@ -313,6 +316,7 @@ std::vector<Cand> candidates(int kind, int precision, int cls) {
 }
 
 int wide_vec(const lx_ctx* c) { return candidates(c->prob.kind, c->prob.precision, kVec2)[0].vec; }
+bool is_square(const lx_problem& P) { return P.nx == P.ny; }
 
 int grid_for(const lx_ctx* c, const Cand& k, int strip_h, int* grid) {
   if (k.smem > 48 * 1024 &&
@@ -414,7 +418,7 @@ int choose_variant(const lx_ctx* c, const double* w, const double* out) {
 // Selected candidate of a class (built on first use with the default).
 lx_status ensure_graph(lx_ctx* c, int variant) {
   if (c->loop[variant].built) return LX_OK;
-  const std::vector<Cand> cands = candidates(c->prob.kind, c->prob.precision, variant);
+  const std::vector<Cand> cands = candidates(c->prob.kind, c->prob.precision, variant, is_square(c->prob));
   if (cands.empty()) {
     set_last_error("no kernel for this layout: the float-float Burgers form needs nx % 128 == 0 and 16-byte "
                    "aligned vectors");
@@ -1521,7 +1525,7 @@ extern "C" {
 lx_status lx_ctx_select_kernel(lx_ctx* c, const char* name, int strip_h) {
   if (!c || !name || strip_h < 0) return LX_E_INVAL;
   for (int v = 0; v < kNumVariants; ++v)
-    for (const Cand& k : candidates(c->prob.kind, c->prob.precision, v))
+    for (const Cand& k : candidates(c->prob.kind, c->prob.precision, v, is_square(c->prob)))
       if (std::strcmp(k.name, name) == 0) {
         if (v == kVec2 && c->prob.nx % (32 * k.vec) != 0) return LX_E_INVAL;
         return build_loop_graph(c, v, k, strip_h);
@@ -1577,7 +1581,7 @@ lx_status lx_ctx_autotune(lx_ctx* c, int iters, const char* cache_path, char* re
   int best_h = 32;
   rep << "\"cached\": false, \"timings\": [";
   bool first = true;
-  for (const Cand& k : candidates(c->prob.kind, c->prob.precision, v)) {
+  for (const Cand& k : candidates(c->prob.kind, c->prob.precision, v, is_square(c->prob))) {
     for (int H : hs) {
       if (H > 2 * c->prob.ny && H != 8) continue;
       if (H == 0 && k.smem == 0) continue;  // balanced ranges: pipelined kernels only

@@ -7,17 +7,22 @@
 
 namespace lexgb {
 
-const void* df2x_kernel(int minb, int stages, bool unroll3) {
+template <bool SQ>
+const void* pick(int minb, int stages, bool unroll3) {
   if (unroll3) {
-    if (minb == 4 && stages == 4) return reinterpret_cast<const void*>(&leja_iter_df_pipe2x_kernel<4, 4, true>);
+    if (minb == 4 && stages == 4) return reinterpret_cast<const void*>(&leja_iter_df_pipe2x_kernel<4, 4, true, SQ>);
     return nullptr;
   }
-  if (minb == 4 && stages == 4) return reinterpret_cast<const void*>(&leja_iter_df_pipe2x_kernel<4, 4, false>);
-  if (minb == 4 && stages == 5) return reinterpret_cast<const void*>(&leja_iter_df_pipe2x_kernel<4, 5, false>);
-  if (minb == 3 && stages == 5) return reinterpret_cast<const void*>(&leja_iter_df_pipe2x_kernel<3, 5, false>);
+  if (minb == 4 && stages == 4) return reinterpret_cast<const void*>(&leja_iter_df_pipe2x_kernel<4, 4, false, SQ>);
+  if (minb == 4 && stages == 5) return reinterpret_cast<const void*>(&leja_iter_df_pipe2x_kernel<4, 5, false, SQ>);
+  if (minb == 3 && stages == 5) return reinterpret_cast<const void*>(&leja_iter_df_pipe2x_kernel<3, 5, false, SQ>);
   // five blocks per SM: 96 registers (a few bytes of spills)
-  if (minb == 5 && stages == 4) return reinterpret_cast<const void*>(&leja_iter_df_pipe2x_kernel<5, 4, false>);
+  if (minb == 5 && stages == 4) return reinterpret_cast<const void*>(&leja_iter_df_pipe2x_kernel<5, 4, false, SQ>);
   return nullptr;
+}
+
+const void* df2x_kernel(int minb, int stages, bool unroll3, bool square) {
+  return square ? pick<true>(minb, stages, unroll3) : pick<false>(minb, stages, unroll3);
 }
 
 int df2x_smem_bytes(int stages) {

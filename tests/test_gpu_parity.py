@@ -495,7 +495,7 @@ def test_two_step_kernel_both_stop_parities(lx, xi_oracle, strip_h):
     assert parities == {0, 1}
 
 
-@pytest.mark.parametrize("name", PIPE2X_KERNELS[:2])
+@pytest.mark.parametrize("name", PIPE2X_KERNELS)
 @pytest.mark.parametrize("nx,ny", [(256, 256), (384, 384), (256, 96)])
 @pytest.mark.parametrize("strip_h", [0, 8, 40])
 def test_two_step_lean_kernel(lx, xi_oracle, name, nx, ny, strip_h):
