@@ -243,9 +243,9 @@ lx_status expint_step_host(lx_ctx* ctx, const double* u_host, double* u_low_host
  * affected. */
 lx_status lx_ctx_set_source(lx_ctx* ctx, const double* s_dev);
 
-/* Classical step-size controller for the embedded third-order pair (the
- * paper notes that the EXPRB32 error "may be used to control the step
- * sizes", Sec. 2.2, without giving a controller):
+/* Classical step-size controller for the embedded third-order pair (Sec.
+ * 2.2 mentions that the EXPRB32 error estimate can steer the step size but
+ * gives no controller):
  *   h_new = h * min(2, max(0.2, 0.9 (tol/err)^(1/3)))   (factor 2 if err = 0).
  * Host arithmetic only. */
 double lx_controller_classical(double h, double err, double tol);

@@ -494,7 +494,7 @@ static void op_rhs(const or_op* op, const double* u, double* out) {
   }
 }
 
-/* ||x|| = ||x||_2 / sqrt(N) (Sec. 2.2: l2 norm normalised to sqrt(N)). */
+/* ||x|| = ||x||_2 / sqrt(N) (Sec. 2.2: the l2 norm scaled by 1/sqrt(N)). */
 static double nrm(const double* x, long n) {
   double s = 0.0;
 #pragma omp parallel for reduction(+ : s)
@@ -885,8 +885,8 @@ int or_epirk4s3a_src(int kind, int nx, int ny, double nu, double a, const double
 }
 
 /* ------------------------------------------------------------------------ */
-/* Step-size control with the embedded error (Sec. 2.2: the EXPRB32 error   */
-/* estimate "may be used to control the step sizes").  The paper gives no   */
+/* Step-size control with the embedded error (Sec. 2.2 mentions that the    */
+/* EXPRB32 error estimate can steer the step size).  The paper gives no     */
 /* controller; the reading is the classical one for a third-order pair:     */
 /* accept when err <= tol, and h_new = h * min(2, max(0.2,                  */
 /* 0.9 (tol/err)^(1/3))) after every attempt (factor 2 when err = 0).       */

@@ -19,9 +19,10 @@
 //    full-warp five-point product per row for the two lanes at the edges);
 //  * sums of squares accumulate in float per lane over 16 rows, then in
 //    float-float;
-//  * optionally (UNROLL3) the row loop is unrolled three times so that the
-//    rolling windows of y_m and y_{m+1} rows rotate by renaming, not by
-//    copying, at three times the code size.
+//  * the row loop rotates its register windows by copying: unrolling it
+//    three times to rotate them by renaming made it instruction-cache bound
+//    (170 against 139 us per launch at 4096^2), and moving the chunk work
+//    out of the row loop into an outer loop over 16-row chunks cost 5 %.
 #pragma once
 
 #include "leja_df64_2step.cuh"
@@ -114,7 +115,7 @@ __device__ __forceinline__ void df_flush4(dfv (&acc)[4], float (&fs)[4]) {
 }
 
 // One segment (rows r0..r1-1 of one 128-point column strip); as df2_strip.
-template <int STAGES, typename S, bool FIRST, bool SQ, bool UNROLL3>
+template <int STAGES, typename S, bool FIRST, bool SQ>
 __device__ __forceinline__ void df2x_strip(const LoopArgs& A, const S* __restrict__ src, float2* __restrict__ dst,
                                            float2* __restrict__ p, unsigned long long* ring,
                                            unsigned long long* hbuf, int col0, int r0, int r1,
@@ -165,6 +166,8 @@ __device__ __forceinline__ void df2x_strip(const LoopArgs& A, const S* __restric
   dfv hwin = {0.f, 0.f};  // this lane's halo value of the current 16-row chunk
   float fs[4] = {0.f, 0.f, 0.f, 0.f};
   const int sl_base = lane == 0 ? 0 : 16;
+  // one row of the walk: step m on y_m row a+1, and (a >= 2) step m+1 on
+  // output row r0 + a - 2
   auto row = [&](int a, dfv(&ms)[4], dfv(&mc)[4], dfv(&mn)[4], dfv(&bs)[4], dfv(&bc)[4], dfv(&ya)[4]) {
     issue(a + STAGES - 1);
     cp_wait<STAGES - 3>();
@@ -184,6 +187,8 @@ __device__ __forceinline__ void df2x_strip(const LoopArgs& A, const S* __restric
       // step m+1: y_{m+2} on output row r0 + t from y_{m+1} rows t-1 .. t+1
       const int t = a - 2;
       if ((t & 15) == 0) {
+        // a new chunk of 16 output rows: its halo values of y_{m+1} (the
+        // inputs arrived with the ring's copies at least 8 rows earlier)
         df_flush4(acc, fs);
         hwin = df2x_halo_compute<S, SQ>(hbuf, sc, wah, wal);
       }
@@ -218,27 +223,19 @@ __device__ __forceinline__ void df2x_strip(const LoopArgs& A, const S* __restric
     // no barrier here: the next row's copies go to the slot last read two
     // rows ago, before the barrier at the start of this row
   };
-  const int alast = nrows + 1;
-  if constexpr (UNROLL3) {
-    for (int a = 0;;) {
-      row(a, M0, M1, M2, B0, B1, B2);
-      if (++a > alast) break;
-      row(a, M1, M2, M0, B1, B2, B0);
-      if (++a > alast) break;
-      row(a, M2, M0, M1, B2, B0, B1);
-      if (++a > alast) break;
-    }
-  } else {
-    for (int a = 0; a <= alast; ++a) {
-      row(a, M0, M1, M2, B0, B1, B2);
+  auto rotate = [&]() {
 #pragma unroll
-      for (int k = 0; k < 4; ++k) {
-        M0[k] = M1[k];
-        M1[k] = M2[k];
-        B0[k] = B1[k];
-        B1[k] = B2[k];
-      }
+    for (int k = 0; k < 4; ++k) {
+      M0[k] = M1[k];
+      M1[k] = M2[k];
+      B0[k] = B1[k];
+      B1[k] = B2[k];
     }
+  };
+  const int alast = nrows + 1;
+  for (int a = 0; a <= alast; ++a) {
+    row(a, M0, M1, M2, B0, B1, B2);
+    rotate();
   }
   df_flush4(acc, fs);
   cp_wait<0>();
@@ -249,7 +246,7 @@ __device__ __forceinline__ void df2x_strip(const LoopArgs& A, const S* __restric
 // same launch protocol, buffers and stopping logic as
 // leja_iter_df_pipe2_kernel.  SQ: the paired stencil, for square grids only
 // (the host offers these instances only when nx == ny).
-template <int MINB, int STAGES, bool UNROLL3, bool SQ>
+template <int MINB, int STAGES, bool SQ>
 __global__ void __launch_bounds__(kPipeThreads, MINB)
     leja_iter_df_pipe2x_kernel(const LoopArgs* __restrict__ Ap, LoopState* __restrict__ st,
                                double* __restrict__ partials, unsigned int* __restrict__ ticket,
@@ -289,10 +286,10 @@ __global__ void __launch_bounds__(kPipeThreads, MINB)
   unsigned long long* hbuf = pipe2x_smem + (size_t)kPipeWarps * STAGES * kSlotElems2 + (size_t)warp * 32 * 5;
   for_each_segment(nx, ny, H, blockIdx.x * kPipeWarps + warp, gridDim.x * kPipeWarps, [&](int col0, int r0, int r1) {
     if (m == 0)
-      df2x_strip<STAGES, double, true, SQ, UNROLL3>(A, A.w, dst, A.pdf, ring, hbuf, col0, r0, r1, wah, wal, wbh, wbl, d0, dm1,
+      df2x_strip<STAGES, double, true, SQ>(A, A.w, dst, A.pdf, ring, hbuf, col0, r0, r1, wah, wal, wbh, wbl, d0, dm1,
                                            dm2, kexp, acc);
     else
-      df2x_strip<STAGES, float2, false, SQ, UNROLL3>(A, src, dst, A.pdf, ring, hbuf, col0, r0, r1, wah, wal, wbh, wbl, d0, dm1,
+      df2x_strip<STAGES, float2, false, SQ>(A, src, dst, A.pdf, ring, hbuf, col0, r0, r1, wah, wal, wbh, wbl, d0, dm1,
                                             dm2, kexp, acc);
   });
   double v[4] = {df_to_double(acc[0]), df_to_double(acc[1]), df_to_double(acc[2]), df_to_double(acc[3])};

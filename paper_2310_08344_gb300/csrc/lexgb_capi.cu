@@ -249,16 +249,12 @@ std::vector<Cand> candidates(int kind, int precision, int cls, bool square = fal
       // default without autotuning: two iterations per pass at four blocks
       // per SM, issue-lean form
       // (square grids get the instances with the paired stencil built in)
-      v.push_back(Cand{df2x_kernel(4, 4, false, square), kPipeThreads, df2x_smem_bytes(4), 4,
-                       "leja_iter_df_pipe2x_b4_s4", 2});
-      v.push_back(Cand{df2x_kernel(4, 5, false, square), kPipeThreads, df2x_smem_bytes(5), 4,
-                       "leja_iter_df_pipe2x_b4", 2});
-      v.push_back(Cand{df2x_kernel(3, 5, false, square), kPipeThreads, df2x_smem_bytes(5), 4,
-                       "leja_iter_df_pipe2x_b3", 2});
-      v.push_back(Cand{df2x_kernel(4, 4, true, square), kPipeThreads, df2x_smem_bytes(4), 4,
-                       "leja_iter_df_pipe2x_u3_b4_s4", 2});
-      v.push_back(Cand{df2x_kernel(5, 4, false, square), kPipeThreads, df2x_smem_bytes(4), 4,
-                       "leja_iter_df_pipe2x_b5_s4", 2});
+      v.push_back(Cand{df2x_kernel(4, 4, square), kPipeThreads, df2x_smem_bytes(4), 4, "leja_iter_df_pipe2x_b4_s4",
+                       2});
+      v.push_back(Cand{df2x_kernel(4, 5, square), kPipeThreads, df2x_smem_bytes(5), 4, "leja_iter_df_pipe2x_b4", 2});
+      v.push_back(Cand{df2x_kernel(3, 5, square), kPipeThreads, df2x_smem_bytes(5), 4, "leja_iter_df_pipe2x_b3", 2});
+      v.push_back(Cand{df2x_kernel(5, 4, square), kPipeThreads, df2x_smem_bytes(4), 4, "leja_iter_df_pipe2x_b5_s4",
+                       2});
       // the first two-step form (155 us per launch at 4096^2, four blocks per SM)
       v.push_back(Cand{reinterpret_cast<const void*>(&leja_iter_df_pipe2_kernel<4, 4>), kPipeThreads,
                        pipe2_smem_bytes<4>(), 4, "leja_iter_df_pipe2_b4_s4", 2});

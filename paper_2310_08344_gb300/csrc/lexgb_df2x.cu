@@ -8,21 +8,17 @@
 namespace lexgb {
 
 template <bool SQ>
-const void* pick(int minb, int stages, bool unroll3) {
-  if (unroll3) {
-    if (minb == 4 && stages == 4) return reinterpret_cast<const void*>(&leja_iter_df_pipe2x_kernel<4, 4, true, SQ>);
-    return nullptr;
-  }
-  if (minb == 4 && stages == 4) return reinterpret_cast<const void*>(&leja_iter_df_pipe2x_kernel<4, 4, false, SQ>);
-  if (minb == 4 && stages == 5) return reinterpret_cast<const void*>(&leja_iter_df_pipe2x_kernel<4, 5, false, SQ>);
-  if (minb == 3 && stages == 5) return reinterpret_cast<const void*>(&leja_iter_df_pipe2x_kernel<3, 5, false, SQ>);
+const void* pick(int minb, int stages) {
+  if (minb == 4 && stages == 4) return reinterpret_cast<const void*>(&leja_iter_df_pipe2x_kernel<4, 4, SQ>);
+  if (minb == 4 && stages == 5) return reinterpret_cast<const void*>(&leja_iter_df_pipe2x_kernel<4, 5, SQ>);
+  if (minb == 3 && stages == 5) return reinterpret_cast<const void*>(&leja_iter_df_pipe2x_kernel<3, 5, SQ>);
   // five blocks per SM: 96 registers (a few bytes of spills)
-  if (minb == 5 && stages == 4) return reinterpret_cast<const void*>(&leja_iter_df_pipe2x_kernel<5, 4, false, SQ>);
+  if (minb == 5 && stages == 4) return reinterpret_cast<const void*>(&leja_iter_df_pipe2x_kernel<5, 4, SQ>);
   return nullptr;
 }
 
-const void* df2x_kernel(int minb, int stages, bool unroll3, bool square) {
-  return square ? pick<true>(minb, stages, unroll3) : pick<false>(minb, stages, unroll3);
+const void* df2x_kernel(int minb, int stages, bool square) {
+  return square ? pick<true>(minb, stages) : pick<false>(minb, stages);
 }
 
 int df2x_smem_bytes(int stages) {

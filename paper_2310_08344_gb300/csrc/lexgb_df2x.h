@@ -4,14 +4,14 @@
 
 namespace lexgb {
 
-// leja_iter_df_pipe2x_kernel<minb, stages, unroll3, square> (signature of
+// leja_iter_df_pipe2x_kernel<minb, stages, square> (signature of
 // the fused iteration kernels: const LoopArgs*, LoopState*, double*
 // partials, unsigned* ticket, cudaGraphConditionalHandle), or NULL if that
 // instance is not built.  square: the instance with the paired stencil of
 // a grid with nx == ny (east and north weights equal, west and south
 // equal); the other instance takes any grid.  Its dynamic shared memory is
 // df2x_smem_bytes(stages).
-const void* df2x_kernel(int minb, int stages, bool unroll3, bool square);
+const void* df2x_kernel(int minb, int stages, bool square);
 int df2x_smem_bytes(int stages);
 
 }  // namespace lexgb

@@ -428,8 +428,8 @@ def test_graph_unroll_is_bitwise_neutral(lx, prec):
 PIPE2_KERNELS = ["leja_iter_df_pipe2_b1", "leja_iter_df_pipe2_b2", "leja_iter_df_pipe2_b2_s6", "leja_iter_df_pipe2_b3",
                  "leja_iter_df_pipe2_b3_s6", "leja_iter_df_pipe2_b4", "leja_iter_df_pipe2_b4_s4",
                  "leja_iter_df_pipe2_b5_s4"]
-PIPE2X_KERNELS = ["leja_iter_df_pipe2x_b4_s4", "leja_iter_df_pipe2x_u3_b4_s4", "leja_iter_df_pipe2x_b4",
-                  "leja_iter_df_pipe2x_b3", "leja_iter_df_pipe2x_b5_s4"]
+PIPE2X_KERNELS = ["leja_iter_df_pipe2x_b4_s4", "leja_iter_df_pipe2x_b4", "leja_iter_df_pipe2x_b3",
+                  "leja_iter_df_pipe2x_b5_s4"]
 DF64_KERNELS = ["leja_iter_df_pipe_b2", "leja_iter_df_pipe_b3", "leja_iter_df_pipe_b4", "leja_iter_df_pipe_b2_s8",
                 "leja_iter_df_pipe_b3_s8", "leja_iter_df_advdiff_v4"] + PIPE2_KERNELS + PIPE2X_KERNELS
 
