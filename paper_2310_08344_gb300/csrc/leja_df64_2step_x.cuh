@@ -19,6 +19,9 @@
 //    full-warp five-point product per row for the two lanes at the edges);
 //  * sums of squares accumulate in float per lane over 16 rows, then in
 //    float-float;
+//  * the stencil's and the Newton update's final renormalisations are
+//    Fast2Sum instead of TwoSum (the error bound argued at df_dot3_f2s;
+//    139 -> 134 us per launch at 4096^2);
 //  * the row loop rotates its register windows by copying: unrolling it
 //    three times to rotate them by renaming made it instruction-cache bound
 //    (170 against 139 us per launch at 4096^2), and moving the chunk work
@@ -37,8 +40,34 @@ __device__ __forceinline__ dfv df_add_loose(dfv a, dfv b) {
   return {s, __fadd_rn(e, __fadd_rn(a.l, b.l))};
 }
 
+// sum_{k<3} w_k y_k as df_dot3, with the final renormalisation by Fast2Sum:
+// when |s| >= |c| it is exact; otherwise s has cancelled below the
+// correction c, and the pair misses s + c by at most a unit roundoff of |c|,
+// where |c| is itself of order u sum |w_k y_k| (the products' rounding
+// errors and low parts) -- the order of Dot2's own error bound, u^2 sum
+// |w_k y_k|, so the accuracy class is unchanged.
+__device__ __forceinline__ dfv df_dot3_f2s(const float (&wh)[3], const float (&wl)[3], const dfv (&y)[3]) {
+  float s, c, p, e, t;
+  two_prod(wh[0], y[0].h, s, c);
+#pragma unroll
+  for (int k = 1; k < 3; ++k) {
+    two_prod(wh[k], y[k].h, p, e);
+    two_sum(s, p, s, t);
+    c = __fadd_rn(c, __fadd_rn(t, e));
+  }
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    c = __fmaf_rn(wh[k], y[k].l, c);
+    c = __fmaf_rn(wl[k], y[k].h, c);
+  }
+  dfv r;
+  fast_two_sum(s, c, r.h, r.l);
+  return r;
+}
+
 // p + d1 y1 + d2 y2 as one compensated sum (exact products, error-free
-// additions of the leading parts, the remaining terms accumulated in float).
+// additions of the leading parts, the remaining terms accumulated in float;
+// the final renormalisation by Fast2Sum, as in df_dot3_f2s).
 __device__ __forceinline__ dfv df_axpy2(dfv d1, dfv y1, dfv d2, dfv y2, dfv p) {
   float q1, e1, q2, e2, s, t1, t2;
   two_prod(d1.h, y1.h, q1, e1);
@@ -51,7 +80,7 @@ __device__ __forceinline__ dfv df_axpy2(dfv d1, dfv y1, dfv d2, dfv y2, dfv p) {
   two_sum(s, q2, s, t2);
   const float c = __fadd_rn(__fadd_rn(p.l, e1), __fadd_rn(__fadd_rn(e2, t1), t2));
   dfv r;
-  two_sum(s, c, r.h, r.l);
+  fast_two_sum(s, c, r.h, r.l);
   return r;
 }
 
@@ -65,7 +94,7 @@ __device__ __forceinline__ dfv df_stencil(const float (&wh)[5], const float (&wl
     const float h3[3] = {wh[0], wh[1], wh[4]};
     const float l3[3] = {wl[0], wl[1], wl[4]};
     const dfv t[3] = {df_add_loose(e, n), df_add_loose(w, s), c};
-    return df_dot3(h3, l3, t);
+    return df_dot3_f2s(h3, l3, t);
   } else {
     const dfv t[5] = {e, w, n, s, c};
     return df_dot5(wh, wl, t);
@@ -128,7 +157,7 @@ __device__ __forceinline__ void df2x_strip(const LoopArgs& A, const S* __restric
   const int ce = (col0 + kPipeRow >= nx) ? 0 : col0 + kPipeRow;  // first of the two east halo points
   const int nrows = r1 - r0;
   const int last_q = nrows + 3;  // y_m rows q = 0 .. nrows+3 are rows r0-2 .. r1+1
-  auto slot = [&](int q) { return ring + (size_t)(q % STAGES) * kSlotElems2; };
+  auto slot = [&](int q) { return ring + (size_t)((unsigned)q % STAGES) * kSlotElems2; };
   auto issue = [&](int q) {
     // halo inputs of the next 16-row chunk, 8 rows before it is needed
     // (row q is issued at a = q - STAGES + 1, output row t = a - 2)
