@@ -22,6 +22,9 @@
 //  * the stencil's and the Newton update's final renormalisations are
 //    Fast2Sum instead of TwoSum (the error bound argued at df_dot3_f2s;
 //    139 -> 134 us per launch at 4096^2);
+//  * on square grids, three of each lane's four (W,S) pair sums are the
+//    (E,N) sums of the row before, one column over (same operands, same
+//    values): one error-free addition per point and step instead of two;
 //  * the row loop rotates its register windows by copying: unrolling it
 //    three times to rotate them by renaming made it instruction-cache bound
 //    (170 against 139 us per launch at 4096^2), and moving the chunk work
@@ -87,14 +90,20 @@ __device__ __forceinline__ dfv df_axpy2(dfv d1, dfv y1, dfv d2, dfv y2, dfv p) {
 // One application of the folded stencil w_E y_E + w_W y_W + w_N y_N +
 // w_S y_S + w_C y_C (weights in the order E, W, N, S, C).  SQ: w_N = w_E and
 // w_S = w_W.
+// Square grids: w_E (y_E + y_N) + w_W (y_W + y_S) + w_C y_C from the two
+// pair sums sen = y_E + y_N and sws = y_W + y_S.
+__device__ __forceinline__ dfv df_stencil_sq(const float (&wh)[5], const float (&wl)[5], dfv sen, dfv sws, dfv c) {
+  const float h3[3] = {wh[0], wh[1], wh[4]};
+  const float l3[3] = {wl[0], wl[1], wl[4]};
+  const dfv t[3] = {sen, sws, c};
+  return df_dot3_f2s(h3, l3, t);
+}
+
 template <bool SQ>
 __device__ __forceinline__ dfv df_stencil(const float (&wh)[5], const float (&wl)[5], dfv e, dfv w, dfv n, dfv s,
                                           dfv c) {
   if constexpr (SQ) {
-    const float h3[3] = {wh[0], wh[1], wh[4]};
-    const float l3[3] = {wl[0], wl[1], wl[4]};
-    const dfv t[3] = {df_add_loose(e, n), df_add_loose(w, s), c};
-    return df_dot3_f2s(h3, l3, t);
+    return df_stencil_sq(wh, wl, df_add_loose(e, n), df_add_loose(w, s), c);
   } else {
     const dfv t[5] = {e, w, n, s, c};
     return df_dot5(wh, wl, t);
@@ -192,6 +201,17 @@ __device__ __forceinline__ void df2x_strip(const LoopArgs& A, const S* __restric
   df_from_raw4<S>(slot(1) + 2 + lane * 4, sc, M1);
 #pragma unroll
   for (int k = 0; k < 4; ++k) B0[k] = B1[k] = dfv{0.f, 0.f};
+  // square grids: y_W + y_S at (r, i) is the sum y_E + y_N at (r-1, i-1),
+  // so each row takes three of its four (W,S) sums from the (E,N) sums of
+  // the row before, one column to the left (the same two operands, so the
+  // same values); only the lane's first column forms its own.  qa, qb:
+  // the (E,N) sums of the previous y_m and y_{m+1} rows at columns c .. c+2.
+  dfv qa[3], qb[3];
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    qa[k] = df_add_loose(M0[k + 1], M1[k]);  // y_m row 0
+    qb[k] = dfv{0.f, 0.f};
+  }
   dfv hwin = {0.f, 0.f};  // this lane's halo value of the current 16-row chunk
   float fs[4] = {0.f, 0.f, 0.f, 0.f};
   const int sl_base = lane == 0 ? 0 : 16;
@@ -209,9 +229,27 @@ __device__ __forceinline__ void df2x_strip(const LoopArgs& A, const S* __restric
     dfv xe = shfl_down_df(mc[0]);
     if (lane == 0) xw = df_from_raw<S>(s1 + 1, sc);
     if (lane == 31) xe = df_from_raw<S>(s1 + 2 + kPipeRow, sc);
+    if constexpr (SQ) {
+      dfv sen[4];
 #pragma unroll
-    for (int k = 0; k < 4; ++k)
-      ya[k] = df_stencil<SQ>(wah, wal, k == 3 ? xe : mc[k + 1], k == 0 ? xw : mc[k - 1], mn[k], ms[k], mc[k]);
+      for (int k = 0; k < 4; ++k) sen[k] = df_add_loose(k == 3 ? xe : mc[k + 1], mn[k]);
+      const dfv sws0 = df_add_loose(xw, ms[0]);
+#pragma unroll
+      for (int k = 0; k < 4; ++k) ya[k] = df_stencil_sq(wah, wal, sen[k], k == 0 ? sws0 : qa[k - 1], mc[k]);
+#pragma unroll
+      for (int k = 0; k < 3; ++k) qa[k] = sen[k];
+    } else {
+#pragma unroll
+      for (int k = 0; k < 4; ++k)
+        ya[k] = df_stencil<SQ>(wah, wal, k == 3 ? xe : mc[k + 1], k == 0 ? xw : mc[k - 1], mn[k], ms[k], mc[k]);
+    }
+    // square grids: the (E,N) sums of y_{m+1} row a at columns c .. c+2
+    // (for the next row's step m+1; at a = 0 not yet meaningful)
+    dfv senb[3];
+    if constexpr (SQ) {
+#pragma unroll
+      for (int k = 0; k < 3; ++k) senb[k] = df_add_loose(bc[k + 1], ya[k]);
+    }
     if (a >= 2) {
       // step m+1: y_{m+2} on output row r0 + t from y_{m+1} rows t-1 .. t+1
       const int t = a - 2;
@@ -235,9 +273,17 @@ __device__ __forceinline__ void df2x_strip(const LoopArgs& A, const S* __restric
         df_from_raw4<float2>(s2 + kY2Slot + lane * 4, sc, pold);
       }
       dfv yb[4], pb[4];
+      dfv senb3, swsb0;
+      if constexpr (SQ) {
+        senb3 = df_add_loose(be, ya[3]);
+        swsb0 = df_add_loose(bw, bs[0]);
+      }
 #pragma unroll
       for (int k = 0; k < 4; ++k) {
-        yb[k] = df_stencil<SQ>(wbh, wbl, k == 3 ? be : bc[k + 1], k == 0 ? bw : bc[k - 1], ya[k], bs[k], bc[k]);
+        if constexpr (SQ)
+          yb[k] = df_stencil_sq(wbh, wbl, k == 3 ? senb3 : senb[k], k == 0 ? swsb0 : qb[k - 1], bc[k]);
+        else
+          yb[k] = df_stencil<SQ>(wbh, wbl, k == 3 ? be : bc[k + 1], k == 0 ? bw : bc[k - 1], ya[k], bs[k], bc[k]);
         pb[k] = df_axpy2(dm1, bc[k], dm2, yb[k], pold[k]);
         const float p1h = __fmaf_rn(dm1.h, bc[k].h, pold[k].h);  // leading float of p_{m+1}
         fs[0] = __fmaf_rn(bc[k].h, bc[k].h, fs[0]);
@@ -248,6 +294,10 @@ __device__ __forceinline__ void df2x_strip(const LoopArgs& A, const S* __restric
       const size_t ro = (size_t)(r0 + t) * nx;
       df_store_row<4>(dst + ro, c, nx, yb);
       df_store_row<4>(p + ro, c, nx, pb);
+    }
+    if constexpr (SQ) {
+#pragma unroll
+      for (int k = 0; k < 3; ++k) qb[k] = senb[k];
     }
     // no barrier here: the next row's copies go to the slot last read two
     // rows ago, before the barrier at the start of this row
