@@ -226,6 +226,14 @@ std::vector<Cand> candidates(int kind, int precision, int cls, bool square = fal
   }
   if (precision == LX_DF64 && kind == LX_BURGERS) {
     if (wide) {
+      // the issue-lean two-step form first (square grids get the paired
+      // stencil): 34.0 us per Leja iteration at 2048^2 with a 5-row ring at 2
+      // blocks/SM, 35.6 us with 4 rows at 3, against 47.7 us for the first
+      // two-step form
+      v.push_back(Cand{df2bx_kernel(2, 5, square), kPipeThreads, df2bx_smem_bytes(5), 4,
+                       "leja_iter_df_pipe2bx_b2", 2});
+      v.push_back(Cand{df2bx_kernel(3, 4, square), kPipeThreads, df2bx_smem_bytes(4), 4,
+                       "leja_iter_df_pipe2bx_b3_s4", 2});
       v.push_back(Cand{reinterpret_cast<const void*>(&leja_iter_df_pipe_burgers_kernel<1>), kPipeThreads,
                        kPipeSmemBytesB, 4, "leja_iter_df_pipe_burgers_b1"});
       v.push_back(Cand{reinterpret_cast<const void*>(&leja_iter_df_pipe_burgers_kernel<2>), kPipeThreads,

@@ -1,5 +1,6 @@
-// Entry points of the translation unit that holds the issue-lean two-step
-// float-float kernels (lexgb_df2x.cu).
+// Entry points of the translation units that hold the issue-lean two-step
+// float-float kernels (lexgb_df2x.cu: diffusion-advection; lexgb_df2bx.cu:
+// the Burgers Jacobian).
 #pragma once
 
 namespace lexgb {
@@ -13,5 +14,11 @@ namespace lexgb {
 // df2x_smem_bytes(stages).
 const void* df2x_kernel(int minb, int stages, bool square);
 int df2x_smem_bytes(int stages);
+
+// leja_iter_df_pipe2bx_kernel<minb, stages, square> (the Burgers Jacobian,
+// same signature), or NULL if not built; square as above (nx == ny).  Its
+// dynamic shared memory is df2bx_smem_bytes(stages).
+const void* df2bx_kernel(int minb, int stages, bool square);
+int df2bx_smem_bytes(int stages);
 
 }  // namespace lexgb

@@ -626,7 +626,8 @@ def test_adaptive_integration_linear_closed_form(lx, prec):
 @pytest.mark.parametrize("name", ["leja_iter_df_pipe_burgers_b1", "leja_iter_df_pipe_burgers_b2",
                                   "leja_iter_df_pipe_burgers_b3_s4", "leja_iter_df_pipe2_burgers_b1",
                                   "leja_iter_df_pipe2_burgers_b2", "leja_iter_df_pipe2_burgers_b3_s4",
-                                  "leja_iter_df_pipe_burgers_b4_s3"])
+                                  "leja_iter_df_pipe_burgers_b4_s3", "leja_iter_df_pipe2bx_b3_s4",
+                                  "leja_iter_df_pipe2bx_b2"])
 @pytest.mark.parametrize("strip_h", [0, 8, 32, 128])
 def test_df64_burgers_candidates_parity(lx, xi_oracle, name, strip_h):
     nx, ny, nu = 256, 100, 2e-2
@@ -642,6 +643,33 @@ def test_df64_burgers_candidates_parity(lx, xi_oracle, name, strip_h):
     ref, it_o, st_o = oracle.leja_phi(oracle.BURGERS, nx, ny, nu, 0.0, u, 3, w, c, g, h, TOL, TOL, xi_oracle)
     assert st == 0 and st_o == 0 and abs(it - it_o) <= 1
     assert rel(out.cpu().numpy(), ref) <= TOL
+
+
+@pytest.mark.parametrize("name", ["leja_iter_df_pipe2bx_b3_s4", "leja_iter_df_pipe2bx_b2"])
+@pytest.mark.parametrize("nx,ny", [(256, 256), (384, 384), (128, 200)])
+@pytest.mark.parametrize("strip_h", [0, 8, 40])
+@pytest.mark.parametrize("hf", [30, 45])
+def test_two_step_lean_burgers_kernel(lx, xi_oracle, name, nx, ny, strip_h, hf):
+    # the issue-lean two-step Burgers kernel: the paired stencil on square
+    # grids (the (W,S) sums carried from the row before), the five-point form
+    # otherwise; the column halo 16 rows at a time (segments of 8 and 40 rows
+    # cut chunks short); two step sizes, so that loops stop after an even and
+    # an odd number of iterations
+    nu = 2e-2
+    u = synth.burgers_ic(nx, ny, seed=8)
+    w = synth.random_field(nx * ny, seed=9)
+    h = hf * synth.cfl_step(nx, ny, nu, np.abs(u).max())
+    rho, _, _ = oracle.power_iteration(oracle.BURGERS, nx, ny, nu, 0.0, u, synth.power_start(nx * ny, 5), 10)
+    c, g = oracle.spectral_interval(rho)
+    ctx = lx.leja_setup(nx, ny, nu, 0.0, lx.BURGERS, lx.DF64)
+    assert lx.lx_ctx_select_kernel(ctx, name, strip_h) == 0
+    assert lx.lx_ctx_iters_per_launch(ctx) == 2
+    for l in (0, 2):
+        out = torch.empty(nx * ny, dtype=torch.float64, device="cuda")
+        st, it = lx.phi_l_apply(ctx, l, dev(u), dev(w), out, c, g, h, TOL, TOL)
+        ref, it_o, st_o = oracle.leja_phi(oracle.BURGERS, nx, ny, nu, 0.0, u, l, w, c, g, h, TOL, TOL, xi_oracle)
+        assert st == 0 and st_o == 0 and abs(it - it_o) <= 1
+        assert rel(out.cpu().numpy(), ref) <= TOL
 
 
 @pytest.mark.parametrize("prec", ["fp64", "mixed", "df64"])
