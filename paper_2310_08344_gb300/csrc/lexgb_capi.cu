@@ -1782,6 +1782,9 @@ const void* batch_kernel_ptr() {
   return reinterpret_cast<const void*>(&leja_batch_kernel<VEC>);
 }
 
+// the float-float batch kernel's resident blocks per SM and ring depth
+constexpr int kBatchDfMinBlocks = 3, kBatchDfStages = 5;
+
 lx_status build_batch_graph(lx_batch* b, int v) {
   if (b->exec[v]) return LX_OK;
   const void* fn = v == 0 ? batch_kernel_ptr<2>() : batch_kernel_ptr<1>();
@@ -1794,9 +1797,9 @@ lx_status build_batch_graph(lx_batch* b, int v) {
   if (b->df) {
     // float-float: two Leja iterations per pass on the shared-memory-
     // pipelined strip, 4 warps per block
-    fn = reinterpret_cast<const void*>(&leja_batch_df_pipe2_kernel<3, 5>);
+    fn = batch_df2x_kernel(kBatchDfMinBlocks, kBatchDfStages);
     threads = kPipeThreads;
-    smem = pipe2_smem_bytes<5>();
+    smem = batch_df2x_smem_bytes(kBatchDfStages);
     LX_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
     LX_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, threads, smem));
     const int wantp = (b->total_strips[v] + kPipeWarps - 1) / kPipeWarps;

@@ -21,4 +21,13 @@ int df2x_smem_bytes(int stages);
 const void* df2bx_kernel(int minb, int stages, bool square);
 int df2bx_smem_bytes(int stages);
 
+// leja_batch_df_pipe2x_kernel<minb, stages> (lexgb_batch_df.cu: the
+// float-float batch, two Leja iterations per pass; signature BatchInst*,
+// const int* strip_inst, BatchState*, double* partials, unsigned* tickets,
+// unsigned* block_ticket, const double* xi, int H, int total_strips,
+// cudaGraphConditionalHandle, int use_cond), or NULL if not built; its
+// dynamic shared memory is batch_df2x_smem_bytes(stages).
+const void* batch_df2x_kernel(int minb, int stages);
+int batch_df2x_smem_bytes(int stages);
+
 }  // namespace lexgb
