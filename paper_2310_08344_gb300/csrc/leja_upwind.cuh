@@ -137,7 +137,10 @@ static __global__ void __launch_bounds__(kThreadsPerBlock)
 // Float-float form of the upwind diffusion-advection iteration (constant
 // weights, Dot2 over the seven points; storage scaling as the other df64
 // kernels: stored y_m = y_m 2^-sig, p in 2^-kscale units, the new basis
-// vector renormalised by 2^-dlt).
+// vector renormalised by 2^-dlt).  The final renormalisation is Fast2Sum:
+// exact when |s| >= |c|; otherwise s has cancelled below the correction c,
+// itself of order u sum |w_k y_k|, and the pair misses s + c by at most a
+// unit roundoff of |c| -- the order of Dot2's own bound u^2 sum |w_k y_k|.
 __device__ __forceinline__ dfv df_dot7(const float (&wh)[7], const float (&wl)[7], const dfv (&y)[7]) {
   float s, c, p, e, t;
   two_prod(wh[0], y[0].h, s, c);
@@ -153,7 +156,7 @@ __device__ __forceinline__ dfv df_dot7(const float (&wh)[7], const float (&wl)[7
     c = __fmaf_rn(wl[k], y[k].h, c);
   }
   dfv r;
-  two_sum(s, c, r.h, r.l);
+  fast_two_sum(s, c, r.h, r.l);
   return r;
 }
 
@@ -873,6 +876,7 @@ namespace lexgb {
 // flight.
 // ---------------------------------------------------------------------------
 
+// sum_{k<N} w_k y_k (Dot2, the final renormalisation as df_dot7's).
 template <int N>
 __device__ __forceinline__ dfv df_dot_n(const float (&wh)[N], const float (&wl)[N], const dfv (&y)[N]) {
   float s, c, p, e, t;
@@ -889,7 +893,7 @@ __device__ __forceinline__ dfv df_dot_n(const float (&wh)[N], const float (&wl)[
     c = __fmaf_rn(wl[k], y[k].h, c);
   }
   dfv r;
-  two_sum(s, c, r.h, r.l);
+  fast_two_sum(s, c, r.h, r.l);
   return r;
 }
 
