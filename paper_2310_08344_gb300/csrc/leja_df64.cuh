@@ -143,6 +143,14 @@ __device__ __forceinline__ dfv df_dot3(const float (&wh)[3], const float (&wl)[3
   return r;
 }
 
+// a + b as an unnormalised float pair: the rounded sum of the leading parts
+// and, in the low part, its exact rounding error plus both low parts.
+__device__ __forceinline__ dfv df_add_loose(dfv a, dfv b) {
+  float s, e;
+  two_sum(a.h, b.h, s, e);
+  return {s, __fadd_rn(e, __fadd_rn(a.l, b.l))};
+}
+
 // p + d * y
 __device__ __forceinline__ dfv df_axpy(dfv d, dfv y, dfv p) {
   float q, qe, s, t;

@@ -35,14 +35,6 @@
 
 namespace lexgb {
 
-// a + b as an unnormalised float pair: the rounded sum of the leading parts
-// and, in the low part, its exact rounding error plus both low parts.
-__device__ __forceinline__ dfv df_add_loose(dfv a, dfv b) {
-  float s, e;
-  two_sum(a.h, b.h, s, e);
-  return {s, __fadd_rn(e, __fadd_rn(a.l, b.l))};
-}
-
 // sum_{k<3} w_k y_k as df_dot3, with the final renormalisation by Fast2Sum:
 // when |s| >= |c| it is exact; otherwise s has cancelled below the
 // correction c, and the pair misses s + c by at most a unit roundoff of |c|,

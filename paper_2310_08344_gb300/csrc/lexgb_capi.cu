@@ -182,9 +182,9 @@ std::vector<Cand> candidates(int kind, int precision, int cls, bool square = fal
         // product form first (z = q y formed once per point, constant
         // weights; 592 us per iteration at 8192^2 with balanced row ranges,
         // against 782 us for the point-weight form), then the point-weight form
-        v.push_back(Cand{reinterpret_cast<const void*>(&leja_iter_df_pipe_burgers_up3z_kernel<3, 5>), kPipeThreads,
+        v.push_back(Cand{up3z_leja_kernel(3, 5), kPipeThreads,
                          up3z_smem_bytes<5>(), 4, "leja_iter_df_pipe_burgers_up3z_b3", 1, 0});
-        v.push_back(Cand{reinterpret_cast<const void*>(&leja_iter_df_pipe_burgers_up3z_kernel<2, 6>), kPipeThreads,
+        v.push_back(Cand{up3z_leja_kernel(2, 6), kPipeThreads,
                          up3z_smem_bytes<6>(), 4, "leja_iter_df_pipe_burgers_up3z_b2", 1, 0});
         v.push_back(Cand{reinterpret_cast<const void*>(&leja_iter_df_pipe_burgers_up3_kernel<2>), kPipeThreads,
                          kUpSmemBytesB, 4, "leja_iter_df_pipe_burgers_up3_b2"});
@@ -818,8 +818,7 @@ lx_status leja_setup(const lx_problem* prob, int integrator, int max_leja, void*
 // (at least four rows) per warp, at most the resident blocks of one wave.
 lx_status size_pow_pipe_grid(lx_ctx* c) {
   const bool b = c->prob.kind == LX_BURGERS_UP3;
-  const void* f = b ? reinterpret_cast<const void*>(&power_pass_df_pipe_burgers_up3z_kernel<3, 5>)
-                    : reinterpret_cast<const void*>(&power_pass_df_pipe_up3_kernel<3>);
+  const void* f = b ? up3z_power_kernel() : reinterpret_cast<const void*>(&power_pass_df_pipe_up3_kernel<3>);
   const int smem = b ? up3z_smem_bytes<5>() : kUpSmemBytes;
   LX_CUDA(cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
   int per_sm = 0;
@@ -941,9 +940,17 @@ lx_status power_bound(lx_ctx* c, const double* u, const double* v0, int max_iter
             c->up3, in, k == 1 ? 1 : 0, wf, nullptr, c->d_partials, c->d_ticket, c->d_state);
       } else if (pipe) {
         // pipelined product form
-        power_pass_df_pipe_burgers_up3z_kernel<3, 5><<<c->pow_pipe_grid, kPipeThreads, up3z_smem_bytes<5>(),
-                                                         c->stream>>>(c->up3, in, k == 1 ? 1 : 0, wf, c->d_bq,
-                                                                      c->d_partials, c->d_ticket, c->d_state);
+        Up3Op op = c->up3;
+        const void* vin = in;
+        int vin_double = k == 1 ? 1 : 0;
+        float2* wout = wf;
+        const float2* q = c->d_bq;
+        double* partials = c->d_partials;
+        unsigned int* ticket = c->d_ticket;
+        LoopState* st = c->d_state;
+        void* args[] = {&op, &vin, &vin_double, &wout, &q, &partials, &ticket, &st};
+        LX_CUDA(cudaLaunchKernel(up3z_power_kernel(), dim3(c->pow_pipe_grid), dim3(kPipeThreads), args,
+                                 up3z_smem_bytes<5>(), c->stream));
       } else {
         power_pass_df_up3_kernel<true><<<G, kThreadsPerBlock, 0, c->stream>>>(
             c->up3, in, k == 1 ? 1 : 0, wf, c->d_bq, c->d_partials, c->d_ticket, c->d_state);

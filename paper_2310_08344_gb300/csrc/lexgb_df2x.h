@@ -1,6 +1,8 @@
-// Entry points of the translation units that hold the issue-lean two-step
-// float-float kernels (lexgb_df2x.cu: diffusion-advection; lexgb_df2bx.cu:
-// the Burgers Jacobian).
+// Entry points of the translation units that hold kernels compiled apart
+// from the C ABI's own unit: the issue-lean two-step float-float kernels
+// (lexgb_df2x.cu: diffusion-advection; lexgb_df2bx.cu: the Burgers Jacobian;
+// lexgb_batch_df.cu: the float-float batch) and the product-form kernels of
+// the upwind Burgers Jacobian (lexgb_up3z.cu).
 #pragma once
 
 namespace lexgb {
@@ -29,5 +31,14 @@ int df2bx_smem_bytes(int stages);
 // dynamic shared memory is batch_df2x_smem_bytes(stages).
 const void* batch_df2x_kernel(int minb, int stages);
 int batch_df2x_smem_bytes(int stages);
+
+// leja_iter_df_pipe_burgers_up3z_kernel<minb, stages> (the fused iteration
+// signature) for (3, 5) and (2, 6), or NULL; its dynamic shared memory is
+// up3z_smem_bytes<stages>() (leja_upwind.cuh).
+const void* up3z_leja_kernel(int minb, int stages);
+// power_pass_df_pipe_burgers_up3z_kernel<3, 5>: (Up3Op, const void* vin,
+// int vin_double, float2* w, const float2* q, double* partials, unsigned*
+// ticket, LoopState*), dynamic shared memory up3z_smem_bytes<5>().
+const void* up3z_power_kernel();
 
 }  // namespace lexgb

@@ -214,6 +214,33 @@ def test_df64_burgers_up3_candidates(lx, xi_oracle, name, strip_h, a):
     assert rel(out.cpu().numpy(), ref) <= TOL
 
 
+@pytest.mark.parametrize("name", ["leja_iter_df_pipe_burgers_up3z_b3", "leja_iter_df_pipe_burgers_up3z_b2"])
+@pytest.mark.parametrize("strip_h", [0, 8])
+@pytest.mark.parametrize("a", [A, -4.0])
+def test_df64_burgers_up3_square_form(lx, xi_oracle, name, strip_h, a):
+    # square grid: the product form's six-term stencil (pair sums of y and z
+    # along x and y, two of them carried from the row before) in the Leja
+    # loop after its first launch, and in the power passes after the first;
+    # both upwind sides
+    nx = ny = 256
+    u = synth.problem3_ic(nx, ny, seed=9) * np.sign(a)
+    w = synth.random_field(nx * ny, seed=10)
+    h = 30 * synth.cfl_step_pm1(nx, ny, NU, abs(a) * np.abs(u).max())
+    v0 = synth.power_start(nx * ny, seed=5)
+    rho, passes, st = oracle.power_iteration(oracle.BURGERS_UP3, nx, ny, NU, a, u, v0, 10)
+    assert st == 0
+    c, g = oracle.spectral_interval(rho)
+    ctx = lx.leja_setup(nx, ny, NU, a, lx.BURGERS_UP3, lx.DF64)
+    assert lx.lx_ctx_select_kernel(ctx, name, strip_h) == 0
+    st, rho_g, passes_g = lx.power_bound(ctx, dev(u), dev(v0), 10)
+    assert st == 0 and passes_g == passes and abs(rho_g - rho) <= 1e-12 * rho
+    out = torch.empty(nx * ny, dtype=torch.float64, device="cuda")
+    st, it = lx.phi_l_apply(ctx, 1, dev(u), dev(w), out, c, g, h, TOL, TOL)
+    ref, it_o, st_o = oracle.leja_phi(oracle.BURGERS_UP3, nx, ny, NU, a, u, 1, w, c, g, h, TOL, TOL, xi_oracle)
+    assert st == 0 and st_o == 0 and abs(it - it_o) <= 1
+    assert rel(out.cpu().numpy(), ref) <= TOL
+
+
 @pytest.mark.parametrize("name", ["leja_iter_df_pipe2_up3_b3", "leja_iter_df_pipe_up3_b3"])
 @pytest.mark.parametrize("tol", [1e-10, 3e-9, 1e-7, 1e-5])
 @pytest.mark.parametrize("a", [A, -4.0])
