@@ -12,11 +12,11 @@ INCLUDE = os.path.join(ROOT, "include")
 LIB = os.path.join(PKG, "_lexgb.so")
 SOURCES = ["lexgb_capi.cu", "lexgb_noalloc.cu", "lexgb_mlp.cu", "lexgb_vertical.cu", "lexgb_rhs.cu", "lexgb_df2x.cu",
            "lexgb_df2bx.cu", "lexgb_batch_df.cu",
-           "lexgb_up3z.cu", "leja_host.cpp"]
+           "lexgb_up3z.cu", "lexgb_up3x.cu", "leja_host.cpp"]
 HEADERS = ["leja_kernels.cuh", "leja_df64.cuh", "leja_df64_2step.cuh", "leja_vertical.cuh", "leja_batch.cuh",
            "leja_upwind.cuh", "leja_upwind_2step.cuh", "lexgb_internal.h", "lexgb_vertical.h",
            "leja_df64_2step_x.cuh", "lexgb_df2x.h", "leja_df64_2step_bx.cuh", "leja_batch_state.h",
-           "leja_upwind_z.cuh"]
+           "leja_upwind_z.cuh", "leja_upwind_2step_x.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -197,6 +197,12 @@ std::vector<Cand> candidates(int kind, int precision, int cls, bool square = fal
         // then one (390 us; 411 us with 8-row strips instead of balanced row
         // ranges): the kernels are issue-bound, so halving the traffic gains
         // only what the smaller instruction count per iteration gives
+        // the issue-lean two-step form first (square grids get the paired
+        // stencil), then the first two-step form
+        v.push_back(Cand{up3x_kernel(3, 6, square), kPipeThreads, up3x_smem_bytes(6), 4, "leja_iter_df_pipe2x_up3_b3",
+                         2, 0});
+        v.push_back(Cand{up3x_kernel(3, 5, square), kPipeThreads, up3x_smem_bytes(5), 4,
+                         "leja_iter_df_pipe2x_up3_b3_s5", 2, 0});
         v.push_back(Cand{reinterpret_cast<const void*>(&leja_iter_df_pipe2_up3_kernel<3, 6>), kPipeThreads,
                          up3_2step_smem_bytes<6>(), 4, "leja_iter_df_pipe2_up3_b3", 2, 0});
         v.push_back(Cand{reinterpret_cast<const void*>(&leja_iter_df_pipe_up3_kernel<3>), kPipeThreads,

@@ -41,4 +41,12 @@ const void* up3z_leja_kernel(int minb, int stages);
 // ticket, LoopState*), dynamic shared memory up3z_smem_bytes<5>().
 const void* up3z_power_kernel();
 
+// leja_iter_df_pipe2x_up3_kernel<minb, stages, square> (lexgb_up3x.cu: the
+// issue-lean two-step kernel of the upwind diffusion-advection operator;
+// fused iteration signature) for minb 3, stages 5 or 6, or NULL; square:
+// the paired stencil (nx == ny with equal x and y coefficients).  Its
+// dynamic shared memory is up3x_smem_bytes(stages).
+const void* up3x_kernel(int minb, int stages, bool square);
+int up3x_smem_bytes(int stages);
+
 }  // namespace lexgb

@@ -173,7 +173,9 @@ def test_phi_vertical_up3(lx, xi_oracle, kind, prec, nx, ny, alphas):
                                           ("leja_iter_df_pipe_up3_b2", 32), ("leja_iter_df_up3", 8),
                                           ("leja_iter_df_pipe2_up3_b3", 0), ("leja_iter_df_pipe2_up3_b3", 8),
                                           ("leja_iter_df_pipe2_up3_b3", 32), ("leja_iter_df_pipe2_up3_b2", 0),
-                                          ("leja_iter_df_pipe2_up3_b4", 0)])
+                                          ("leja_iter_df_pipe2_up3_b4", 0), ("leja_iter_df_pipe2x_up3_b3", 0),
+                                          ("leja_iter_df_pipe2x_up3_b3", 8), ("leja_iter_df_pipe2x_up3_b3", 40),
+                                          ("leja_iter_df_pipe2x_up3_b3_s5", 0)])
 @pytest.mark.parametrize("a", [A, -4.0])
 def test_df64_up3_candidates(lx, xi_oracle, name, strip_h, a):
     # every float-float candidate of the upwind operator on a grid with two
@@ -241,7 +243,32 @@ def test_df64_burgers_up3_square_form(lx, xi_oracle, name, strip_h, a):
     assert rel(out.cpu().numpy(), ref) <= TOL
 
 
-@pytest.mark.parametrize("name", ["leja_iter_df_pipe2_up3_b3", "leja_iter_df_pipe_up3_b3"])
+@pytest.mark.parametrize("name", ["leja_iter_df_pipe2x_up3_b3", "leja_iter_df_pipe2x_up3_b3_s5"])
+@pytest.mark.parametrize("n", [256, 384])
+@pytest.mark.parametrize("strip_h", [0, 8, 40])
+@pytest.mark.parametrize("tol", [1e-10, 1e-7])
+@pytest.mark.parametrize("a", [A, -4.0])
+def test_df64_up3_lean_square(lx, xi_oracle, name, n, strip_h, tol, a):
+    # the issue-lean two-step kernel on square grids: pair sums of the x and
+    # y neighbours with the (-s) pair carried along the walk, the three halo
+    # columns 16 output rows at a time (segments of 8 and 40 rows cut chunks
+    # short), both upwind sides, stops after odd and even counts
+    u0 = synth.problem1_ic(n, n, seed=17)
+    h = 40 * synth.cfl_step_pm1(n, n, NU, a)
+    c, g = _interval(oracle.ADVDIFF_UP3, n, n, a, None)
+    ctx = lx.leja_setup(n, n, NU, a, lx.ADVDIFF_UP3, lx.DF64)
+    assert lx.lx_ctx_select_kernel(ctx, name, strip_h) == 0
+    out = torch.empty(n * n, dtype=torch.float64, device="cuda")
+    for l in (0, 1):
+        st, it = lx.phi_l_apply(ctx, l, None, dev(u0), out, c, g, h, tol, tol)
+        ref, it_o, st_o = oracle.leja_phi(oracle.ADVDIFF_UP3, n, n, NU, a, None, l, u0, c, g, h, tol, tol, xi_oracle)
+        assert st == 0 and st_o == 0 and abs(it - it_o) <= 1
+        bar = 1e-10 if it == it_o else 100 * tol
+        assert rel(out.cpu().numpy(), ref) <= bar
+
+
+@pytest.mark.parametrize("name", ["leja_iter_df_pipe2_up3_b3", "leja_iter_df_pipe_up3_b3",
+                                  "leja_iter_df_pipe2x_up3_b3"])
 @pytest.mark.parametrize("tol", [1e-10, 3e-9, 1e-7, 1e-5])
 @pytest.mark.parametrize("a", [A, -4.0])
 def test_df64_up3_two_step_stop_parities(lx, xi_oracle, name, tol, a):
