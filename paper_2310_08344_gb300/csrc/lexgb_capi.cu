@@ -142,6 +142,7 @@ struct lx_ctx {
   // the first (which uses d_pdf), and the loop graphs by class and count
   VertArgs* d_vargs = nullptr;
   double* d_vcoef = nullptr;
+  double* d_vfix = nullptr;  // two-step df64 loops: per-polynomial odd-stop coefficients
   float2* d_pdfv[kMaxVertical] = {};
   LoopGraph vloop[kNumVariants][kMaxVertical];
   int aux_grid = 0;
@@ -698,6 +699,7 @@ void leja_destroy(lx_ctx* c) {
     for (auto& L : row) destroy_graph(L);
   cudaFree(c->d_vargs);
   cudaFree(c->d_vcoef);
+  cudaFree(c->d_vfix);
   for (int j = 1; j < kMaxVertical; ++j) cudaFree(c->d_pdfv[j]);
   for (auto& S : c->coef) {
     if (S.dev) cudaFree(S.dev);
@@ -1043,12 +1045,17 @@ lx_status phi_l_apply_vertical(lx_ctx* c, int l, int nc, const double* alpha, co
     wide = P.nx % 64 == 0 && aligned16(w) && aligned16(c->d_y[0]) && aligned16(c->d_y[1]);
     for (int j = 0; j < nc; ++j) wide = wide && aligned16(out[j]);
   }
-  const void* fn = vertical_kernel(P.kind, P.precision, wide, nc);
+  // float-float diffusion-advection: two Leja iterations per pass
+  const bool two = df && P.kind == LX_ADVDIFF;
+  int smem2 = 0;
+  const void* fn = two ? vertical2x_kernel(nc, &smem2) : vertical_kernel(P.kind, P.precision, wide, nc);
   if (!fn) return LX_E_INVAL;
   // lazily allocated vertical buffers
   if (!c->d_vargs && !cuda_ok(cudaMalloc((void**)&c->d_vargs, sizeof(VertArgs)), "cudaMalloc")) return LX_E_NOMEM;
   if (!c->d_vcoef &&
       !cuda_ok(cudaMalloc((void**)&c->d_vcoef, sizeof(double) * kMaxVertical * (size_t)c->K), "cudaMalloc"))
+    return LX_E_NOMEM;
+  if (two && !c->d_vfix && !cuda_ok(cudaMalloc((void**)&c->d_vfix, sizeof(double) * kMaxVertical), "cudaMalloc"))
     return LX_E_NOMEM;
   c->d_pdfv[0] = c->d_pdf;
   for (int j = 1; df && j < nc; ++j)
@@ -1075,11 +1082,12 @@ lx_status phi_l_apply_vertical(lx_ctx* c, int l, int nc, const double* alpha, co
   }
   LX_CUDA(cudaStreamSynchronize(c->stream));  // dh is host memory of this frame
   const int variant = wide ? kVec2 : kVec1;
-  const int H = (df && !up) ? 8 : c->strip_h;
+  const int H = two ? 0 : ((df && !up) ? 8 : c->strip_h);
   LoopGraph& L = c->vloop[variant][nc - 1];
   if (!L.built || L.cand.func != fn) {
     destroy_graph(L);
-    const Cand k{fn, kThreadsPerBlock, 0, (df && !up) ? 4 : (wide ? 2 : 1), "leja_iter_vertical"};
+    const Cand k = two ? Cand{fn, kPipeThreads, smem2, 4, "leja_iter_df_vertical2x", 2, 0}
+                       : Cand{fn, kThreadsPerBlock, 0, (df && !up) ? 4 : (wide ? 2 : 1), "leja_iter_vertical"};
     int grid = 0;
     const int gs = grid_for(c, k, H, &grid);
     if (gs != LX_OK) return (lx_status)gs;
@@ -1110,7 +1118,8 @@ lx_status phi_l_apply_vertical(lx_ctx* c, int l, int nc, const double* alpha, co
     std::memset(&kp, 0, sizeof(kp));
     kp.func = const_cast<void*>(fn);
     kp.gridDim = dim3(L.grid);
-    kp.blockDim = dim3(kThreadsPerBlock);
+    kp.blockDim = dim3(k.threads);
+    kp.sharedMemBytes = (unsigned)k.smem;
     kp.kernelParams = kargs;
     cudaGraphNode_t prev = nullptr;
     for (int q = 0; q < L.unroll; ++q) {
@@ -1131,6 +1140,7 @@ lx_status phi_l_apply_vertical(lx_ctx* c, int l, int nc, const double* alpha, co
     V.p[j] = out[j];
     V.pdf[j] = c->d_pdfv[j];
   }
+  V.fixd = c->d_vfix;
   LX_CUDA(upload_vertical_args(V, c->d_vargs, c->stream));
   ++c->stats.kernels;
   if (c->ev_used + 2 > 8) return LX_E_INVAL;
@@ -1148,7 +1158,7 @@ lx_status phi_l_apply_vertical(lx_ctx* c, int l, int nc, const double* alpha, co
     void* kargs[] = {(void*)&args, (void*)&vargs, (void*)&stp, (void*)&partials, (void*)&ticket, (void*)&cond};
     for (int it = 0; it < count - 1; it += 8) {
       for (int q = 0; q < 8; ++q)
-        LX_CUDA(cudaLaunchKernel(fn, dim3(L.grid), dim3(kThreadsPerBlock), kargs, 0, c->stream));
+        LX_CUDA(cudaLaunchKernel(fn, dim3(L.grid), dim3(L.cand.threads), kargs, (size_t)L.cand.smem, c->stream));
       c->stats.kernels += 8;
       LX_CUDA(cudaMemcpyAsync(c->h_state, c->d_state, sizeof(LoopState), cudaMemcpyDeviceToHost, c->stream));
       LX_CUDA(cudaStreamSynchronize(c->stream));
@@ -1159,6 +1169,11 @@ lx_status phi_l_apply_vertical(lx_ctx* c, int l, int nc, const double* alpha, co
   c->ev_used += 2;
   if (df) {
     for (int j = 0; j < nc; ++j) {
+      if (two) {
+        // this polynomial's odd-stop coefficient into the loop state
+        LX_CUDA(select_vertical_fix(c->d_state, c->d_vfix, j, c->stream));
+        ++c->stats.kernels;
+      }
       if (c->n % 2 == 0 && aligned16(out[j])) {
         const long long n2 = c->n / 2;
         const int G2 = (int)std::max<long long>(

@@ -3,6 +3,7 @@
 #include <cuda_runtime.h>
 
 #include "leja_vertical.cuh"
+#include "leja_vertical_2x.cuh"
 #include "lexgb.h"
 #include "lexgb_vertical.h"
 
@@ -59,6 +60,23 @@ const void* vertical_kernel(int kind, int precision, bool wide, int np) {
   return kind == LX_BURGERS ? pick_np<1>(precision, wide, np) : pick_np<0>(precision, wide, np);
 }
 
+
+const void* vertical2x_kernel(int np, int* smem) {
+  // four resident blocks' worth of shared memory is not there for more than
+  // two polynomials: 3 blocks per SM up to two, 2 beyond
+  switch (np) {
+    case 1: *smem = pipe2x_vert_smem_bytes<4, 1>(); return reinterpret_cast<const void*>(&leja_iter_df_vertical2x_kernel<3, 4, 1>);
+    case 2: *smem = pipe2x_vert_smem_bytes<4, 2>(); return reinterpret_cast<const void*>(&leja_iter_df_vertical2x_kernel<3, 4, 2>);
+    case 3: *smem = pipe2x_vert_smem_bytes<4, 3>(); return reinterpret_cast<const void*>(&leja_iter_df_vertical2x_kernel<2, 4, 3>);
+    case 4: *smem = pipe2x_vert_smem_bytes<4, 4>(); return reinterpret_cast<const void*>(&leja_iter_df_vertical2x_kernel<2, 4, 4>);
+    default: *smem = 0; return nullptr;
+  }
+}
+
+cudaError_t select_vertical_fix(void* state, const double* fixd, int j, cudaStream_t stream) {
+  vertical_select_fix_kernel<<<1, 1, 0, stream>>>(static_cast<LoopState*>(state), fixd, j);
+  return cudaGetLastError();
+}
 
 cudaError_t upload_vertical_args(const VertArgs& v, VertArgs* dst, cudaStream_t stream) {
   set_vertical_args_kernel<<<1, 1, 0, stream>>>(v, dst);
