@@ -296,6 +296,124 @@ __device__ __forceinline__ void bx_strip(const LoopArgs& A, const S* __restrict_
   __syncwarp();
 }
 
+// One power-iteration pass (Sec. 2, Listing 7) on the Burgers Jacobian of a
+// square grid: the row-strip walk and ring of pow_strip (leja_df64.cuh; v
+// with a one-point halo, q = u/(2 dx) and r = the centre term per row), with
+// the lean point form of bx_strip -- the (E,N) pair sum by one error-free
+// addition, the (W,S) pair carried from the previous row one column over,
+// the weights lx -+ q by unnormalised additions, a three-term Dot2 -- then
+// w = J(u) v / ||v|| and ||w||^2 to double accuracy as in pow_strip.
+template <int STAGES, typename S>
+__device__ __forceinline__ void pow_bx_strip(int nx, int ny, const S* __restrict__ v, float2* __restrict__ w,
+                                             const float2* __restrict__ q, const float2* __restrict__ r, dfv lx,
+                                             unsigned long long* ring, int col0, int r0, int r1, dfv sg, dfv& acc,
+                                             float& small) {
+  const int lane = threadIdx.x & 31;
+  const int c = col0 + lane * 4;
+  const int cw = col0 == 0 ? nx - 1 : col0 - 1;
+  const int ce = (col0 + kPipeRow >= nx) ? 0 : col0 + kPipeRow;
+  const int last_q = r1 - r0 + 1;  // rows q = 0 .. last_q are grid rows r0 - 1 .. r1
+  constexpr int kSlot = pow_slot_elems<1>();
+  auto slot = [&](int qq) { return ring + (size_t)((unsigned)qq % STAGES) * kSlot; };
+  auto issue = [&](int qq) {
+    if (qq <= last_q) {
+      const int ry = wrap_row(r0 - 1 + qq, ny);
+      const S* row = v + (size_t)ry * nx;
+      unsigned long long* sl = slot(qq);
+      cp_async16(sl + 2 + lane * 4, row + c);
+      cp_async16(sl + 4 + lane * 4, row + c + 2);
+      if (lane == 0) cp_async8(sl + 1, row + cw);
+      if (lane == 31) cp_async8(sl + 2 + kPipeRow, row + ce);
+      const size_t o = (size_t)ry * nx + c;
+      cp_async16(sl + kRhsSlot + lane * 4, q + o);
+      cp_async16(sl + kRhsSlot + lane * 4 + 2, q + o + 2);
+      cp_async16(sl + kRhsSlot + kPipeRow + lane * 4, r + o);
+      cp_async16(sl + kRhsSlot + kPipeRow + lane * 4 + 2, r + o + 2);
+    }
+    cp_commit();
+  };
+  for (int qq = 0; qq < STAGES - 1; ++qq) issue(qq);
+  cp_wait<STAGES - 3>();
+  __syncwarp();
+  dfv ys[4], yc[4], yn[4], qa[3];
+  df_from_raw4<S>(slot(0) + 2 + lane * 4, 0, ys);
+  df_from_raw4<S>(slot(1) + 2 + lane * 4, 0, yc);
+#pragma unroll
+  for (int k = 0; k < 3; ++k) qa[k] = df_add_loose(ys[k + 1], yc[k]);  // row r0 - 1
+  for (int qc = 1; qc < last_q; ++qc) {
+    issue(qc + STAGES - 2);
+    cp_wait<STAGES - 3>();
+    __syncwarp();
+    const unsigned long long* sn = slot(qc + 1);
+    const unsigned long long* scn = slot(qc);
+    df_from_raw4<S>(sn + 2 + lane * 4, 0, yn);
+    dfv xw = shfl_up_df(yc[3]);
+    dfv xe = shfl_down_df(yc[0]);
+    if (lane == 0) xw = df_from_raw<S>(scn + 1, 0);
+    if (lane == 31) xe = df_from_raw<S>(scn + 2 + kPipeRow, 0);
+    dfv qv[4], rv[4], sen[4];
+    df_from_raw4<float2>(scn + kRhsSlot + lane * 4, 0, qv);
+    df_from_raw4<float2>(scn + kRhsSlot + kPipeRow + lane * 4, 0, rv);
+#pragma unroll
+    for (int k = 0; k < 4; ++k) sen[k] = df_add_loose(k == 3 ? xe : yc[k + 1], yn[k]);
+    const dfv sws0 = df_add_loose(xw, ys[0]);
+    dfv out[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      const dfv wE = df_add_loose(lx, df_negv(qv[k]));
+      const dfv wW = df_add_loose(lx, qv[k]);
+      const float wh[3] = {wE.h, wW.h, rv[k].h};
+      const float wl[3] = {wE.l, wW.l, rv[k].l};
+      const dfv t[3] = {sen[k], k == 0 ? sws0 : qa[k - 1], yc[k]};
+      out[k] = df_mul(sg, df_dot3_f2s(wh, wl, t));
+      float sq, se;
+      two_prod(out[k].h, out[k].h, sq, se);
+      df_acc(acc, sq);
+      small = __fmaf_rn(2.f * out[k].h, out[k].l, __fadd_rn(small, se));
+    }
+    df_store_row<4>(w + (size_t)(r0 - 1 + qc) * nx, c, nx, out);
+#pragma unroll
+    for (int k = 0; k < 3; ++k) qa[k] = sen[k];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      ys[k] = yc[k];
+      yc[k] = yn[k];
+    }
+    __syncwarp();
+  }
+  cp_wait<0>();
+  __syncwarp();
+}
+
+// power_pass_df_rows_kernel<1, STAGES> (the same arguments, shared memory
+// and stopping test) with pow_bx_strip: square grids only (lx = ly, dx = dy).
+template <int STAGES>
+__global__ void __launch_bounds__(kPipeThreads)
+    power_pass_df_bx_kernel(int nx, int ny, long long n, const void* __restrict__ vin, int vin_double,
+                            float2* __restrict__ w, const float2* __restrict__ q, const float2* __restrict__ r,
+                            PowWeights W, double* __restrict__ partials, unsigned int* __restrict__ ticket,
+                            LoopState* st) {
+  extern __shared__ __align__(16) unsigned long long powbx_ring[];
+  if (__ldcg(&st->pdone)) return;
+  const dfv sg = df_from_double(__ldcg(&st->sigma));
+  const dfv lx = {W.bl[0], W.bl[1]};
+  dfv acc = {0.f, 0.f};
+  float small = 0.f;
+  const int warp = threadIdx.x >> 5;
+  unsigned long long* ring = powbx_ring + (size_t)warp * STAGES * pow_slot_elems<1>();
+  for_each_segment(nx, ny, 0, blockIdx.x * kPipeWarps + warp, gridDim.x * kPipeWarps, [&](int col0, int r0, int r1) {
+    if (vin_double)
+      pow_bx_strip<STAGES, double>(nx, ny, reinterpret_cast<const double*>(vin), w, q, r, lx, ring, col0, r0, r1, sg,
+                                   acc, small);
+    else
+      pow_bx_strip<STAGES, float2>(nx, ny, reinterpret_cast<const float2*>(vin), w, q, r, lx, ring, col0, r0, r1, sg,
+                                   acc, small);
+  });
+  double s = df_to_double(acc) + (double)small, dummy = 0.0;
+  if (!last_block_total2(s, dummy, partials, ticket)) return;
+  if (threadIdx.x == 0) power_pass_finish(st, s, n);
+}
+
 // Launch m (even) of the two-step loop for the Burgers Jacobian: y_m, p_m ->
 // y_{m+2}, p_{m+2}; the launch protocol, buffers, scaling and stopping logic
 // of leja_iter_df_pipe2_burgers_kernel.  SQ: the paired stencil, for square

@@ -903,8 +903,11 @@ lx_status power_bound(lx_ctx* c, const double* u, const double* v0, int max_iter
         // row-strip form with a cp.async ring
         constexpr int kPowStages = 5;
         const bool bk = P.kind != LX_ADVDIFF;
-        const void* fn = bk ? reinterpret_cast<const void*>(&power_pass_df_rows_kernel<1, kPowStages>)
-                            : reinterpret_cast<const void*>(&power_pass_df_rows_kernel<0, kPowStages>);
+        // square Burgers grids: the lean pass (paired stencil, same arguments)
+        const bool bsq = bk && P.nx == P.ny;
+        const void* fn = bsq ? df2bx_power_kernel()
+                             : (bk ? reinterpret_cast<const void*>(&power_pass_df_rows_kernel<1, kPowStages>)
+                                   : reinterpret_cast<const void*>(&power_pass_df_rows_kernel<0, kPowStages>));
         const int smem = bk ? pow_rows_smem_bytes<1, kPowStages>() : pow_rows_smem_bytes<0, kPowStages>();
         LX_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
         int per_sm = 0;
@@ -913,7 +916,19 @@ lx_status power_bound(lx_ctx* c, const double* u, const double* v0, int max_iter
         const int GP = (int)std::max<long long>(1, std::min<long long>((lines / 4 + kPipeWarps - 1) / kPipeWarps,
                                                                          (long long)std::max(per_sm, 1) *
                                                                              c->sm_count));
-        if (bk)
+        if (bsq) {
+          int nx = P.nx, ny = P.ny, vin_double = k == 1 ? 1 : 0;
+          long long n = c->n;
+          const void* vin = in;
+          float2* wout = wf;
+          const float2* qq = c->d_bq;
+          const float2* rr = c->d_br;
+          double* partials = c->d_partials;
+          unsigned int* ticket = c->d_ticket;
+          LoopState* stp = c->d_state;
+          void* args[] = {&nx, &ny, &n, &vin, &vin_double, &wout, &qq, &rr, &PW, &partials, &ticket, &stp};
+          LX_CUDA(cudaLaunchKernel(fn, dim3(GP), dim3(kPipeThreads), args, (size_t)smem, c->stream));
+        } else if (bk)
           power_pass_df_rows_kernel<1, kPowStages><<<GP, kPipeThreads, smem, c->stream>>>(
               P.nx, P.ny, c->n, in, k == 1 ? 1 : 0, wf, c->d_bq, c->d_br, PW, c->d_partials, c->d_ticket, c->d_state);
         else

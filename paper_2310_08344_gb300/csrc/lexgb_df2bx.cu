@@ -19,6 +19,8 @@ const void* df2bx_kernel(int minb, int stages, bool square) {
   return square ? pick_bx<true>(minb, stages) : pick_bx<false>(minb, stages);
 }
 
+const void* df2bx_power_kernel() { return reinterpret_cast<const void*>(&power_pass_df_bx_kernel<5>); }
+
 int df2bx_smem_bytes(int stages) {
   switch (stages) {
     case 4: return pipe2bx_smem_bytes<4>();

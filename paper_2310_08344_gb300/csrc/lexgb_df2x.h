@@ -22,6 +22,10 @@ int df2x_smem_bytes(int stages);
 // dynamic shared memory is df2bx_smem_bytes(stages).
 const void* df2bx_kernel(int minb, int stages, bool square);
 int df2bx_smem_bytes(int stages);
+// power_pass_df_bx_kernel<5>: the lean power pass of the Burgers Jacobian on
+// square grids, with the arguments and shared memory of
+// power_pass_df_rows_kernel<1, 5> (leja_df64.cuh).
+const void* df2bx_power_kernel();
 
 // leja_batch_df_pipe2x_kernel<minb, stages> (lexgb_batch_df.cu: the
 // float-float batch, two Leja iterations per pass; signature BatchInst*,
