@@ -34,10 +34,15 @@ def up_to_date() -> bool:
     return all(os.path.getmtime(f) <= t for f in _inputs() if os.path.exists(f))
 
 
+def _threads() -> int:
+    """Translation units compiled at once: one per core, at most one per source."""
+    return max(1, min(os.cpu_count() or 4, len(SOURCES)))
+
+
 def nvcc_command(out: str, extra=()):
     nvcc = os.environ.get("NVCC", "nvcc")
     return [nvcc, "-O3", "-std=c++17", *ARCH, "-lineinfo", "-Xcompiler", "-fPIC,-O2", "-shared",
-            "--threads", "4", "-diag-suppress", "177", f"-I{INCLUDE}", *extra, *[os.path.join(CSRC, s) for s in SOURCES], "-o", out]
+            "--threads", str(_threads()), "-diag-suppress", "177", f"-I{INCLUDE}", *extra, *[os.path.join(CSRC, s) for s in SOURCES], "-o", out]
 
 
 def build(force: bool = False, verbose: bool = False) -> str:

@@ -414,6 +414,91 @@ __global__ void __launch_bounds__(kPipeThreads)
   if (threadIdx.x == 0) power_pass_finish(st, s, n);
 }
 
+// The point weights of J(u) as float pairs, from u alone: q = u gx and
+// r = wc0 - (u_x + u_y) ig with u_x + u_y = (u_E - u_W) / (2 dx) +
+// (u_N - u_S) / (2 dy) (central differences, as the FP64 right-hand side
+// forms it) -- the float-float counterpart of the FP64 gradient followed by
+// burgers_df_prep_kernel.  Row strips with balanced row ranges, u rows (one-
+// point halo) through a per-warp cp.async ring, each value split once
+// (nx % 128 == 0, u 16-byte aligned).  cst: gx, ig, wc0, 1/(2 dx), 1/(2 dy)
+// as float pairs.
+struct BxWeights {
+  float c[10];
+};
+
+template <int STAGES>
+__global__ void __launch_bounds__(kPipeThreads)
+    burgers_weights_df_kernel(int nx, int ny, const double* __restrict__ u, BxWeights W, float2* __restrict__ q,
+                              float2* __restrict__ r) {
+  extern __shared__ __align__(16) unsigned long long bw_ring[];
+  const dfv gx = {W.c[0], W.c[1]}, ig = {W.c[2], W.c[3]}, wc0 = {W.c[4], W.c[5]};
+  const dfv i2dx = {W.c[6], W.c[7]}, i2dy = {W.c[8], W.c[9]};
+  const int lane = threadIdx.x & 31;
+  const int warp = threadIdx.x >> 5;
+  unsigned long long* ring = bw_ring + (size_t)warp * STAGES * kRhsSlot;
+  for_each_segment(nx, ny, 0, blockIdx.x * kPipeWarps + warp, gridDim.x * kPipeWarps, [&](int col0, int r0, int r1) {
+    const int c = col0 + lane * 4;
+    const int cw = col0 == 0 ? nx - 1 : col0 - 1;
+    const int ce = (col0 + kPipeRow >= nx) ? 0 : col0 + kPipeRow;
+    const int last_q = r1 - r0 + 1;  // rows q = 0 .. last_q are grid rows r0 - 1 .. r1
+    auto slot = [&](int qq) { return ring + (size_t)((unsigned)qq % STAGES) * kRhsSlot; };
+    auto issue = [&](int qq) {
+      if (qq <= last_q) {
+        const int ry = wrap_row(r0 - 1 + qq, ny);
+        const double* row = u + (size_t)ry * nx;
+        unsigned long long* sl = slot(qq);
+        cp_async16(sl + 2 + lane * 4, row + c);
+        cp_async16(sl + 4 + lane * 4, row + c + 2);
+        if (lane == 0) cp_async8(sl + 1, row + cw);
+        if (lane == 31) cp_async8(sl + 2 + kPipeRow, row + ce);
+      }
+      cp_commit();
+    };
+    for (int qq = 0; qq < STAGES - 1; ++qq) issue(qq);
+    cp_wait<STAGES - 3>();
+    __syncwarp();
+    dfv ys[4], yc[4], yn[4];
+    df_from_raw4<double>(slot(0) + 2 + lane * 4, 0, ys);
+    df_from_raw4<double>(slot(1) + 2 + lane * 4, 0, yc);
+    for (int qc = 1; qc < last_q; ++qc) {
+      issue(qc + STAGES - 2);
+      cp_wait<STAGES - 3>();
+      __syncwarp();
+      const unsigned long long* sn = slot(qc + 1);
+      const unsigned long long* scn = slot(qc);
+      df_from_raw4<double>(sn + 2 + lane * 4, 0, yn);
+      dfv xw = shfl_up_df(yc[3]);
+      dfv xe = shfl_down_df(yc[0]);
+      if (lane == 0) xw = df_from_raw<double>(scn + 1, 0);
+      if (lane == 31) xe = df_from_raw<double>(scn + 2 + kPipeRow, 0);
+      float2 qo[4], ro[4];
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        const dfv ddx = df_add_loose(k == 3 ? xe : yc[k + 1], df_negv(k == 0 ? xw : yc[k - 1]));
+        const dfv ddy = df_add_loose(yn[k], df_negv(ys[k]));
+        const dfv grad = df_add_loose(df_mul(ddx, i2dx), df_mul(ddy, i2dy));
+        const dfv qk = df_mul(yc[k], gx);
+        const dfv rk = df_axpy(df_negv(ig), grad, wc0);  // wc0 - ig grad
+        qo[k] = make_float2(qk.h, qk.l);
+        ro[k] = make_float2(rk.h, rk.l);
+      }
+      const size_t ro_off = (size_t)(r0 - 1 + qc) * nx + c;
+      *reinterpret_cast<float4*>(q + ro_off) = make_float4(qo[0].x, qo[0].y, qo[1].x, qo[1].y);
+      *reinterpret_cast<float4*>(q + ro_off + 2) = make_float4(qo[2].x, qo[2].y, qo[3].x, qo[3].y);
+      *reinterpret_cast<float4*>(r + ro_off) = make_float4(ro[0].x, ro[0].y, ro[1].x, ro[1].y);
+      *reinterpret_cast<float4*>(r + ro_off + 2) = make_float4(ro[2].x, ro[2].y, ro[3].x, ro[3].y);
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        ys[k] = yc[k];
+        yc[k] = yn[k];
+      }
+      __syncwarp();
+    }
+    cp_wait<0>();
+    __syncwarp();
+  });
+}
+
 // Launch m (even) of the two-step loop for the Burgers Jacobian: y_m, p_m ->
 // y_{m+2}, p_{m+2}; the launch protocol, buffers, scaling and stopping logic
 // of leja_iter_df_pipe2_burgers_kernel.  SQ: the paired stencil, for square

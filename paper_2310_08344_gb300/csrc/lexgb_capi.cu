@@ -546,8 +546,12 @@ lx_status prepare_loop(lx_ctx* c, int strip_h, int kmax, const double* d, const 
     a.bq = c->d_bq;
     a.br = c->d_br;
     if (!prep_current) {
-      burgers_df_prep_kernel<<<aux_blocks(c), kThreadsPerBlock, 0, c->stream>>>(c->n, u, c->d_s, ig / (2 * dx), ig,
-                                                                                 a.wc0, c->d_bq, c->d_br);
+      if (P.nx % kPipeRow == 0 && aligned16(u))
+        LX_CUDA(burgers_weights_df(P.nx, P.ny, u, ig / (2 * dx), ig, a.wc0, dx, dy, c->d_bq, c->d_br, c->sm_count,
+                                   c->stream));
+      else
+        burgers_df_prep_kernel<<<aux_blocks(c), kThreadsPerBlock, 0, c->stream>>>(c->n, u, c->d_s, ig / (2 * dx),
+                                                                                   ig, a.wc0, c->d_bq, c->d_br);
       ++c->stats.kernels;
       LX_CUDA(cudaGetLastError());
     }
@@ -850,7 +854,10 @@ lx_status power_bound(lx_ctx* c, const double* u, const double* v0, int max_iter
   const int G = aux_blocks(c);
   const lx_problem& P = c->prob;
   LX_CUDA(cudaEventRecord(c->ev_pow[0], c->stream));
-  if (P.kind == LX_BURGERS) {
+  // float-float Burgers: the point weights straight from u on the FP32 pipe
+  // (no FP64 gradient)
+  const bool dfw = P.kind == LX_BURGERS && P.precision == LX_DF64 && P.nx % kPipeRow == 0 && aligned16(u);
+  if (P.kind == LX_BURGERS && !dfw) {
     rhs_kernel<1><<<G, kThreadsPerBlock, 0, c->stream>>>(c->geo, P.nu, 0.0, 0.0, u, nullptr, c->d_s);
     ++c->stats.kernels;
     LX_CUDA(cudaGetLastError());
@@ -888,8 +895,12 @@ lx_status power_bound(lx_ctx* c, const double* u, const double* v0, int max_iter
       }
       // q = u / (2 dx), r = -2 nu/dx^2 - 2 nu/dy^2 - (u_x + u_y)
       c->prep_u = nullptr;
-      burgers_df_prep_kernel<<<G, kThreadsPerBlock, 0, c->stream>>>(c->n, u, c->d_s, 1.0 / (2 * dx), 1.0,
-                                                                     -2.0 * nx2 - 2.0 * ny2, c->d_bq, c->d_br);
+      if (dfw)
+        LX_CUDA(burgers_weights_df(P.nx, P.ny, u, 1.0 / (2 * dx), 1.0, -2.0 * nx2 - 2.0 * ny2, dx, dy, c->d_bq,
+                                   c->d_br, c->sm_count, c->stream));
+      else
+        burgers_df_prep_kernel<<<G, kThreadsPerBlock, 0, c->stream>>>(c->n, u, c->d_s, 1.0 / (2 * dx), 1.0,
+                                                                       -2.0 * nx2 - 2.0 * ny2, c->d_bq, c->d_br);
       ++c->stats.kernels;
       LX_CUDA(cudaGetLastError());
     }

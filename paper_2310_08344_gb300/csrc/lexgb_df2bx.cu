@@ -3,6 +3,8 @@
 // with the rest).
 #include <cuda_runtime.h>
 
+#include <algorithm>
+
 #include "leja_df64_2step_bx.cuh"
 #include "lexgb_df2x.h"
 
@@ -17,6 +19,27 @@ const void* pick_bx(int minb, int stages) {
 
 const void* df2bx_kernel(int minb, int stages, bool square) {
   return square ? pick_bx<true>(minb, stages) : pick_bx<false>(minb, stages);
+}
+
+cudaError_t burgers_weights_df(int nx, int ny, const double* u, double gx, double ig, double wc0, double dx,
+                               double dy, float2* q, float2* r, int sm_count, cudaStream_t stream) {
+  constexpr int kStages = 5;
+  const double cv[5] = {gx, ig, wc0, 1.0 / (2 * dx), 1.0 / (2 * dy)};
+  BxWeights W;
+  for (int k = 0; k < 5; ++k) {
+    W.c[2 * k] = (float)cv[k];
+    W.c[2 * k + 1] = (float)(cv[k] - (double)W.c[2 * k]);
+  }
+  const int smem = kPipeWarps * kStages * kRhsSlot * 8;
+  int per_sm = 0;
+  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, burgers_weights_df_kernel<kStages>,
+                                                                kPipeThreads, smem);
+  if (e != cudaSuccess) return e;
+  const long long lines = (long long)(nx / kPipeRow) * ny;
+  const long long want = (lines / 4 + kPipeWarps - 1) / kPipeWarps;
+  const int grid = (int)std::max<long long>(1, std::min<long long>(want, (long long)std::max(per_sm, 1) * sm_count));
+  burgers_weights_df_kernel<kStages><<<grid, kPipeThreads, smem, stream>>>(nx, ny, u, W, q, r);
+  return cudaGetLastError();
 }
 
 const void* df2bx_power_kernel() { return reinterpret_cast<const void*>(&power_pass_df_bx_kernel<5>); }

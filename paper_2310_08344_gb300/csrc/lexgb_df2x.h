@@ -5,6 +5,8 @@
 // the upwind Burgers Jacobian (lexgb_up3z.cu).
 #pragma once
 
+#include <cuda_runtime.h>
+
 namespace lexgb {
 
 // leja_iter_df_pipe2x_kernel<minb, stages, square> (signature of
@@ -26,6 +28,11 @@ int df2bx_smem_bytes(int stages);
 // square grids, with the arguments and shared memory of
 // power_pass_df_rows_kernel<1, 5> (leja_df64.cuh).
 const void* df2bx_power_kernel();
+// The point weights of the Burgers Jacobian as float pairs from u alone
+// (burgers_weights_df_kernel): q = u gx, r = wc0 - (u_x + u_y) ig, central
+// differences with spacings dx, dy; nx % 128 == 0 and u 16-byte aligned.
+cudaError_t burgers_weights_df(int nx, int ny, const double* u, double gx, double ig, double wc0, double dx,
+                               double dy, float2* q, float2* r, int sm_count, cudaStream_t stream);
 
 // leja_batch_df_pipe2x_kernel<minb, stages> (lexgb_batch_df.cu: the
 // float-float batch, two Leja iterations per pass; signature BatchInst*,
