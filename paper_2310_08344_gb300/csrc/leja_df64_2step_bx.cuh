@@ -499,6 +499,96 @@ __global__ void __launch_bounds__(kPipeThreads)
   });
 }
 
+// Fields of an EXPRB32 step of the Burgers problem (central differences)
+// in float-float on the FP32 pipe, written as doubles -- the counterparts
+// of the FP64 rhs_kernel<1> and exprb32_stage_kernel<1>:
+//   MODE 0: f_out = h (nu lap v - v (v_x + v_y)) [+ h src]   (h F(u), v = u)
+//   MODE 1: f_out = -h v (v_x + v_y)   (the stage remainder h (F(a) - F(u))
+//           of the quadratic term with v = p1 = a - u)
+// lap and v_x + v_y by central differences.  Row strips with balanced row
+// ranges, v rows (one-point halo) through a per-warp cp.async ring, each
+// value split once (nx % 128 == 0, v and f_out 16-byte aligned).  cst as
+// float pairs: h nu / dx^2, h nu / dy^2, 1/(2 dx), 1/(2 dy), -h, h.
+struct BxField {
+  float c[12];
+};
+
+template <int MODE, int STAGES>
+__global__ void __launch_bounds__(kPipeThreads)
+    burgers_field_df_kernel(int nx, int ny, const double* __restrict__ v, const double* __restrict__ src, BxField K,
+                            double* __restrict__ f_out) {
+  extern __shared__ __align__(16) unsigned long long bf_ring[];
+  const dfv ax = {K.c[0], K.c[1]}, ay = {K.c[2], K.c[3]}, i2dx = {K.c[4], K.c[5]}, i2dy = {K.c[6], K.c[7]};
+  const dfv mh = {K.c[8], K.c[9]}, hp = {K.c[10], K.c[11]};
+  const int lane = threadIdx.x & 31;
+  const int warp = threadIdx.x >> 5;
+  unsigned long long* ring = bf_ring + (size_t)warp * STAGES * kRhsSlot;
+  for_each_segment(nx, ny, 0, blockIdx.x * kPipeWarps + warp, gridDim.x * kPipeWarps, [&](int col0, int r0, int r1) {
+    const int c = col0 + lane * 4;
+    const int cw = col0 == 0 ? nx - 1 : col0 - 1;
+    const int ce = (col0 + kPipeRow >= nx) ? 0 : col0 + kPipeRow;
+    const int last_q = r1 - r0 + 1;  // rows q = 0 .. last_q are grid rows r0 - 1 .. r1
+    auto slot = [&](int qq) { return ring + (size_t)((unsigned)qq % STAGES) * kRhsSlot; };
+    auto issue = [&](int qq) {
+      if (qq <= last_q) {
+        const int ry = wrap_row(r0 - 1 + qq, ny);
+        const double* row = v + (size_t)ry * nx;
+        unsigned long long* sl = slot(qq);
+        cp_async16(sl + 2 + lane * 4, row + c);
+        cp_async16(sl + 4 + lane * 4, row + c + 2);
+        if (lane == 0) cp_async8(sl + 1, row + cw);
+        if (lane == 31) cp_async8(sl + 2 + kPipeRow, row + ce);
+      }
+      cp_commit();
+    };
+    for (int qq = 0; qq < STAGES - 1; ++qq) issue(qq);
+    cp_wait<STAGES - 3>();
+    __syncwarp();
+    dfv ys[4], yc[4], yn[4];
+    df_from_raw4<double>(slot(0) + 2 + lane * 4, 0, ys);
+    df_from_raw4<double>(slot(1) + 2 + lane * 4, 0, yc);
+    for (int qc = 1; qc < last_q; ++qc) {
+      issue(qc + STAGES - 2);
+      cp_wait<STAGES - 3>();
+      __syncwarp();
+      const unsigned long long* sn = slot(qc + 1);
+      const unsigned long long* scn = slot(qc);
+      df_from_raw4<double>(sn + 2 + lane * 4, 0, yn);
+      dfv xw = shfl_up_df(yc[3]);
+      dfv xe = shfl_down_df(yc[0]);
+      if (lane == 0) xw = df_from_raw<double>(scn + 1, 0);
+      if (lane == 31) xe = df_from_raw<double>(scn + 2 + kPipeRow, 0);
+      const size_t o = (size_t)(r0 - 1 + qc) * nx + c;
+      double res[4];
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        const dfv e = k == 3 ? xe : yc[k + 1], w = k == 0 ? xw : yc[k - 1];
+        const dfv grad = df_add_loose(df_mul(df_add_loose(e, df_negv(w)), i2dx),
+                                      df_mul(df_add_loose(yn[k], df_negv(ys[k])), i2dy));
+        dfv f = df_mul(mh, df_mul(yc[k], grad));  // -h v (v_x + v_y)
+        if constexpr (MODE == 0) {
+          const dfv c2 = {2.f * yc[k].h, 2.f * yc[k].l};
+          const dfv lxx = df_add_loose(df_add_loose(e, w), df_negv(c2));
+          const dfv lyy = df_add_loose(df_add_loose(yn[k], ys[k]), df_negv(c2));
+          f = df_add_loose(f, df_add_loose(df_mul(ax, lxx), df_mul(ay, lyy)));
+          if (src) f = df_add_loose(f, df_mul(hp, df_split_scaled(__ldg(src + o + k), 0)));
+        }
+        res[k] = f2d_scaled(f.h, 0) + f2d_scaled(f.l, 0);  // both exact; one rounding to double
+      }
+      *reinterpret_cast<double2*>(f_out + o) = make_double2(res[0], res[1]);
+      *reinterpret_cast<double2*>(f_out + o + 2) = make_double2(res[2], res[3]);
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        ys[k] = yc[k];
+        yc[k] = yn[k];
+      }
+      __syncwarp();
+    }
+    cp_wait<0>();
+    __syncwarp();
+  });
+}
+
 // Launch m (even) of the two-step loop for the Burgers Jacobian: y_m, p_m ->
 // y_{m+2}, p_{m+2}; the launch protocol, buffers, scaling and stopping logic
 // of leja_iter_df_pipe2_burgers_kernel.  SQ: the paired stencil, for square

@@ -1241,6 +1241,10 @@ static lx_status epirk4s3a_step(lx_ctx* c, const double* u, double* u_low, doubl
   const lx_problem& P = c->prob;
   const int G = aux_blocks(c);
   const bool burg = is_burgers(P.kind);
+  // float-float central Burgers: h F(u) and the stage remainders on the FP32
+  // pipe (as in expint_step)
+  const bool dfb = P.precision == LX_DF64 && P.kind == LX_BURGERS && P.nx % kPipeRow == 0 && aligned16(u) &&
+                   (!c->d_src || aligned16(c->d_src));
   const double c2 = 0.5, c3 = 2.0 / 3.0;
   const double b2 = 32.0, b3 = -13.5, e2 = -144.0, e3 = 81.0;
   double* E0 = c->d_ep[0];
@@ -1251,6 +1255,9 @@ static lx_status epirk4s3a_step(lx_ctx* c, const double* u, double* u_low, doubl
   if (st != LX_OK) return st;
   if (P.kind == LX_ADVDIFF)
     rhs_kernel<0><<<G, kThreadsPerBlock, 0, c->stream>>>(c->geo, P.nu, P.a, h, u, c->d_f, c->d_s, c->d_src);
+  else if (P.kind == LX_BURGERS && dfb)
+    LX_CUDA(burgers_field_df(0, P.nx, P.ny, u, c->d_src, h, P.nu, 1.0 / P.nx, 1.0 / P.ny, c->d_f, c->sm_count,
+                             c->stream));
   else if (P.kind == LX_BURGERS)
     rhs_kernel<1><<<G, kThreadsPerBlock, 0, c->stream>>>(c->geo, P.nu, 0.0, h, u, c->d_f, c->d_s, c->d_src);
   else if (P.kind == LX_ADVDIFF_UP3)
@@ -1276,6 +1283,9 @@ static lx_status epirk4s3a_step(lx_ctx* c, const double* u, double* u_low, doubl
     scale_kernel<<<G, kThreadsPerBlock, 0, c->stream>>>(c->n, alpha[i], i == 0 ? E0 : E1, T);
     if (P.kind == LX_ADVDIFF)
       exprb32_stage_kernel<0><<<G, kThreadsPerBlock, 0, c->stream>>>(c->geo, h, T, R);
+    else if (P.kind == LX_BURGERS && dfb && aligned16(T) && aligned16(R))
+      LX_CUDA(burgers_field_df(1, P.nx, P.ny, T, nullptr, h, P.nu, 1.0 / P.nx, 1.0 / P.ny, R, c->sm_count,
+                               c->stream));
     else if (P.kind == LX_BURGERS)
       exprb32_stage_kernel<1><<<G, kThreadsPerBlock, 0, c->stream>>>(c->geo, h, T, R);
     else if (P.kind == LX_ADVDIFF_UP3)
@@ -1363,6 +1373,10 @@ lx_status expint_step(lx_ctx* c, const double* u, double* u_low, double* u_high,
     return (lx_status)c->h_state->status_total;
   }
   const bool df_up3 = P.precision == LX_DF64 && is_up3(P.kind);
+  // float-float central Burgers: h F(u) and the stage remainder on the FP32
+  // pipe (the point weights come from u itself, so u_x + u_y is not needed)
+  const bool dfb = P.precision == LX_DF64 && P.kind == LX_BURGERS && P.nx % kPipeRow == 0 && aligned16(u) &&
+                   (!c->d_src || aligned16(c->d_src));
   if (df_up3 && c->integrator == LX_ROS_EU) {
     // the same for the upwind operators: h (f(u) + S) on the FP32 pipe, the
     // Leja loop, and u + p in the loop's output pass
@@ -1383,6 +1397,9 @@ lx_status expint_step(lx_ctx* c, const double* u, double* u_low, double* u_high,
   // h f(u) and, for Burgers, u_x + u_y at the linearisation point
   if (P.kind == LX_ADVDIFF)
     rhs_kernel<0><<<G, kThreadsPerBlock, 0, c->stream>>>(c->geo, P.nu, P.a, h, u, c->d_f, c->d_s, c->d_src);
+  else if (P.kind == LX_BURGERS && dfb)
+    LX_CUDA(burgers_field_df(0, P.nx, P.ny, u, c->d_src, h, P.nu, 1.0 / P.nx, 1.0 / P.ny, c->d_f, c->sm_count,
+                             c->stream));
   else if (P.kind == LX_BURGERS)
     rhs_kernel<1><<<G, kThreadsPerBlock, 0, c->stream>>>(c->geo, P.nu, 0.0, h, u, c->d_f, c->d_s, c->d_src);
   else if (df_up3 && P.kind == LX_ADVDIFF_UP3)
@@ -1413,6 +1430,9 @@ lx_status expint_step(lx_ctx* c, const double* u, double* u_low, double* u_high,
     // R = h (F(a) - F(u)) into d_f (u_low keeps p1 until the final pass)
     if (P.kind == LX_ADVDIFF)
       exprb32_stage_kernel<0><<<G, kThreadsPerBlock, 0, c->stream>>>(c->geo, h, u_low, c->d_f);
+    else if (P.kind == LX_BURGERS && dfb && aligned16(u_low))
+      LX_CUDA(burgers_field_df(1, P.nx, P.ny, u_low, nullptr, h, P.nu, 1.0 / P.nx, 1.0 / P.ny, c->d_f, c->sm_count,
+                               c->stream));
     else if (P.kind == LX_BURGERS)
       exprb32_stage_kernel<1><<<G, kThreadsPerBlock, 0, c->stream>>>(c->geo, h, u_low, c->d_f);
     else if (df_up3 && P.kind == LX_BURGERS_UP3)

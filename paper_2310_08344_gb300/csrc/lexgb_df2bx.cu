@@ -42,6 +42,31 @@ cudaError_t burgers_weights_df(int nx, int ny, const double* u, double gx, doubl
   return cudaGetLastError();
 }
 
+cudaError_t burgers_field_df(int mode, int nx, int ny, const double* v, const double* src, double h, double nu,
+                             double dx, double dy, double* f_out, int sm_count, cudaStream_t stream) {
+  constexpr int kStages = 5;
+  const double cv[6] = {h * nu / (dx * dx), h * nu / (dy * dy), 1.0 / (2 * dx), 1.0 / (2 * dy), -h, h};
+  BxField K;
+  for (int k = 0; k < 6; ++k) {
+    K.c[2 * k] = (float)cv[k];
+    K.c[2 * k + 1] = (float)(cv[k] - (double)K.c[2 * k]);
+  }
+  const int smem = kPipeWarps * kStages * kRhsSlot * 8;
+  const void* fn = mode == 0 ? reinterpret_cast<const void*>(&burgers_field_df_kernel<0, kStages>)
+                             : reinterpret_cast<const void*>(&burgers_field_df_kernel<1, kStages>);
+  int per_sm = 0;
+  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kPipeThreads, smem);
+  if (e != cudaSuccess) return e;
+  const long long lines = (long long)(nx / kPipeRow) * ny;
+  const long long want = (lines / 4 + kPipeWarps - 1) / kPipeWarps;
+  const int grid = (int)std::max<long long>(1, std::min<long long>(want, (long long)std::max(per_sm, 1) * sm_count));
+  if (mode == 0)
+    burgers_field_df_kernel<0, kStages><<<grid, kPipeThreads, smem, stream>>>(nx, ny, v, src, K, f_out);
+  else
+    burgers_field_df_kernel<1, kStages><<<grid, kPipeThreads, smem, stream>>>(nx, ny, v, nullptr, K, f_out);
+  return cudaGetLastError();
+}
+
 const void* df2bx_power_kernel() { return reinterpret_cast<const void*>(&power_pass_df_bx_kernel<5>); }
 
 int df2bx_smem_bytes(int stages) {

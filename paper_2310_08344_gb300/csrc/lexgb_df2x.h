@@ -33,6 +33,12 @@ const void* df2bx_power_kernel();
 // differences with spacings dx, dy; nx % 128 == 0 and u 16-byte aligned.
 cudaError_t burgers_weights_df(int nx, int ny, const double* u, double gx, double ig, double wc0, double dx,
                                double dy, float2* q, float2* r, int sm_count, cudaStream_t stream);
+// Fields of a Burgers EXPRB32 step in float-float, written as doubles
+// (burgers_field_df_kernel): mode 0, f_out = h (nu lap v - v (v_x + v_y))
+// (+ h src when src is not NULL); mode 1, f_out = -h v (v_x + v_y).  nx %
+// 128 == 0; v, src and f_out 16-byte aligned.
+cudaError_t burgers_field_df(int mode, int nx, int ny, const double* v, const double* src, double h, double nu,
+                             double dx, double dy, double* f_out, int sm_count, cudaStream_t stream);
 
 // leja_batch_df_pipe2x_kernel<minb, stages> (lexgb_batch_df.cu: the
 // float-float batch, two Leja iterations per pass; signature BatchInst*,
