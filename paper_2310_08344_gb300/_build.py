@@ -16,7 +16,8 @@ SOURCES = ["lexgb_capi.cu", "lexgb_noalloc.cu", "lexgb_mlp.cu", "lexgb_vertical.
 HEADERS = ["leja_kernels.cuh", "leja_df64.cuh", "leja_df64_2step.cuh", "leja_vertical.cuh", "leja_batch.cuh",
            "leja_upwind.cuh", "leja_upwind_2step.cuh", "lexgb_internal.h", "lexgb_vertical.h",
            "leja_df64_2step_x.cuh", "lexgb_df2x.h", "leja_df64_2step_bx.cuh", "leja_batch_state.h",
-           "leja_upwind_z.cuh", "leja_upwind_2step_x.cuh"]
+           "leja_upwind_z.cuh", "leja_upwind_2step_x.cuh",
+           "leja_vertical_2x.cuh", "leja_vertical_2bx.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

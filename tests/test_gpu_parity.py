@@ -701,7 +701,7 @@ def test_df64_burgers_rejects_unsupported_layout(lx):
 
 VERT_CASES = [(0, "FP64", 64, 64), (0, "FP64", 100, 37), (0, "MIXED", 64, 64), (0, "DF64", 128, 96),
               (0, "DF64", 256, 256), (0, "DF64", 384, 200), (1, "FP64", 64, 64), (1, "FP64", 72, 40),
-              (1, "DF64", 128, 64)]
+              (1, "DF64", 128, 64), (1, "DF64", 256, 256), (1, "DF64", 384, 200)]
 
 
 @pytest.mark.parametrize("kind,prec,nx,ny", VERT_CASES)
@@ -742,24 +742,33 @@ def test_phi_vertical_matches_oracle(lx, xi_oracle, kind, prec, nx, ny, nc):
         assert rel(outs[0].cpu().numpy(), one.cpu().numpy()) <= 1e-12
 
 
+@pytest.mark.parametrize("kind,nc", [(0, 2), (0, 4), (1, 1), (1, 3)])
 @pytest.mark.parametrize("nx,ny", [(256, 256), (128, 96)])
-@pytest.mark.parametrize("nc", [2, 4])
 @pytest.mark.parametrize("tol", [1e-10, 3e-9, 1e-7, 1e-5])
-def test_phi_vertical_df64_two_step_stop_parities(lx, xi_oracle, nx, ny, nc, tol):
-    # the float-float vertical loop of the diffusion-advection operator runs
-    # two Leja iterations per launch: several tolerances give odd and even
-    # stop counts, and an odd stop must return every p^(j)_{m+1} (the output
-    # pass removes each polynomial's own extra term)
-    l, nu, a = 1, 1e-2, 0.5
+def test_phi_vertical_df64_two_step_stop_parities(lx, xi_oracle, kind, nx, ny, nc, tol):
+    # the float-float vertical loops of the diffusion-advection operator and
+    # the Burgers Jacobian (up to three polynomials) run two Leja iterations
+    # per launch: several tolerances give odd and even stop counts, and an
+    # odd stop must return every p^(j)_{m+1} (the output pass removes each
+    # polynomial's own extra term)
+    l = 1
     alphas = [0.25, 0.5, 0.75, 1.0][-nc:]
-    w = synth.gaussians_ic(nx, ny, seed=14) + 0.05 * synth.random_field(nx * ny, 15)
-    h = 40 * synth.cfl_step(nx, ny, nu, a)
-    rho, _, _ = oracle.power_iteration(0, nx, ny, nu, a, None, synth.power_start(nx * ny, 5), 10)
+    if kind == 0:
+        nu, a, u = 1e-2, 0.5, None
+        w = synth.gaussians_ic(nx, ny, seed=14) + 0.05 * synth.random_field(nx * ny, 15)
+        h = 40 * synth.cfl_step(nx, ny, nu, a)
+    else:
+        nu, a = 2e-2, 0.0
+        u = synth.burgers_ic(nx, ny, seed=14)
+        w = synth.random_field(nx * ny, seed=15)
+        h = 40 * synth.cfl_step(nx, ny, nu, np.abs(u).max())
+    rho, _, _ = oracle.power_iteration(kind, nx, ny, nu, a, u, synth.power_start(nx * ny, 5), 10)
     c, g = oracle.spectral_interval(rho)
-    ctx = lx.leja_setup(nx, ny, nu, a, 0, lx.DF64)
+    ctx = lx.leja_setup(nx, ny, nu, a, kind, lx.DF64)
     outs = [torch.empty(nx * ny, dtype=torch.float64, device="cuda") for _ in alphas]
-    st, it = lx.phi_l_apply_vertical(ctx, l, alphas, None, dev(w), outs, c, g, h, tol, tol)
-    refs, it_o, st_o = oracle.leja_phi_vertical(0, nx, ny, nu, a, None, l, alphas, w, c, g, h, tol, tol, xi_oracle)
+    st, it = lx.phi_l_apply_vertical(ctx, l, alphas, dev(u) if u is not None else None, dev(w), outs, c, g, h, tol,
+                                     tol)
+    refs, it_o, st_o = oracle.leja_phi_vertical(kind, nx, ny, nu, a, u, l, alphas, w, c, g, h, tol, tol, xi_oracle)
     assert st == 0 and st_o == 0 and abs(it - it_o) <= 1
     bar = 1e-10 if it == it_o else 100 * tol
     for j in range(nc):
