@@ -1072,9 +1072,10 @@ lx_status phi_l_apply_vertical(lx_ctx* c, int l, int nc, const double* alpha, co
     for (int j = 0; j < nc; ++j) wide = wide && aligned16(out[j]);
   }
   // float-float diffusion-advection: two Leja iterations per pass
-  const bool two = df && P.kind == LX_ADVDIFF;
+  const bool two = df && (P.kind == LX_ADVDIFF || (P.kind == LX_BURGERS && nc <= 3));
   int smem2 = 0;
-  const void* fn = two ? vertical2x_kernel(nc, &smem2) : vertical_kernel(P.kind, P.precision, wide, nc);
+  const void* fn = !two ? vertical_kernel(P.kind, P.precision, wide, nc)
+                        : (P.kind == LX_ADVDIFF ? vertical2x_kernel(nc, &smem2) : vertical2bx_kernel(nc, &smem2));
   if (!fn) return LX_E_INVAL;
   // lazily allocated vertical buffers
   if (!c->d_vargs && !cuda_ok(cudaMalloc((void**)&c->d_vargs, sizeof(VertArgs)), "cudaMalloc")) return LX_E_NOMEM;
@@ -1112,7 +1113,8 @@ lx_status phi_l_apply_vertical(lx_ctx* c, int l, int nc, const double* alpha, co
   LoopGraph& L = c->vloop[variant][nc - 1];
   if (!L.built || L.cand.func != fn) {
     destroy_graph(L);
-    const Cand k = two ? Cand{fn, kPipeThreads, smem2, 4, "leja_iter_df_vertical2x", 2, 0}
+    const Cand k = two ? Cand{fn, kPipeThreads, smem2, 4,
+                              P.kind == LX_ADVDIFF ? "leja_iter_df_vertical2x" : "leja_iter_df_vertical2bx", 2, 0}
                        : Cand{fn, kThreadsPerBlock, 0, (df && !up) ? 4 : (wide ? 2 : 1), "leja_iter_vertical"};
     int grid = 0;
     const int gs = grid_for(c, k, H, &grid);

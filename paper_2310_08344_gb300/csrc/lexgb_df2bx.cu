@@ -6,6 +6,7 @@
 #include <algorithm>
 
 #include "leja_df64_2step_bx.cuh"
+#include "leja_vertical_2bx.cuh"
 #include "lexgb_df2x.h"
 
 namespace lexgb {
@@ -65,6 +66,17 @@ cudaError_t burgers_field_df(int mode, int nx, int ny, const double* v, const do
   else
     burgers_field_df_kernel<1, kStages><<<grid, kPipeThreads, smem, stream>>>(nx, ny, v, nullptr, K, f_out);
   return cudaGetLastError();
+}
+
+const void* vertical2bx_kernel(int np, int* smem) {
+  // y, q, r and NP polynomial rows in the ring: two resident blocks up to
+  // three polynomials
+  switch (np) {
+    case 1: *smem = pipe2bx_vert_smem_bytes<4, 1>(); return reinterpret_cast<const void*>(&leja_iter_df_vertical2bx_kernel<2, 4, 1>);
+    case 2: *smem = pipe2bx_vert_smem_bytes<4, 2>(); return reinterpret_cast<const void*>(&leja_iter_df_vertical2bx_kernel<2, 4, 2>);
+    case 3: *smem = pipe2bx_vert_smem_bytes<4, 3>(); return reinterpret_cast<const void*>(&leja_iter_df_vertical2bx_kernel<2, 4, 3>);
+    default: *smem = 0; return nullptr;
+  }
 }
 
 const void* df2bx_power_kernel() { return reinterpret_cast<const void*>(&power_pass_df_bx_kernel<5>); }

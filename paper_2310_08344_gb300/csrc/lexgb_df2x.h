@@ -28,6 +28,10 @@ int df2bx_smem_bytes(int stages);
 // square grids, with the arguments and shared memory of
 // power_pass_df_rows_kernel<1, 5> (leja_df64.cuh).
 const void* df2bx_power_kernel();
+// leja_iter_df_vertical2bx_kernel for np = 1..3 polynomials (the two-step
+// float-float vertical loop of the Burgers Jacobian; the signature of the
+// vertical kernels, 128 threads, dynamic shared memory *smem), or NULL.
+const void* vertical2bx_kernel(int np, int* smem);
 // The point weights of the Burgers Jacobian as float pairs from u alone
 // (burgers_weights_df_kernel): q = u gx, r = wc0 - (u_x + u_y) ig, central
 // differences with spacings dx, dy; nx % 128 == 0 and u 16-byte aligned.
