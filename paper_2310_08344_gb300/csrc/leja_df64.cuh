@@ -151,6 +151,31 @@ __device__ __forceinline__ dfv df_add_loose(dfv a, dfv b) {
   return {s, __fadd_rn(e, __fadd_rn(a.l, b.l))};
 }
 
+// sum_{k<3} w_k y_k as df_dot3, with the final renormalisation by Fast2Sum:
+// when |s| >= |c| it is exact; otherwise s has cancelled below the
+// correction c, and the pair misses s + c by at most a unit roundoff of |c|,
+// where |c| is itself of order u sum |w_k y_k| (the products' rounding
+// errors and low parts) -- the order of Dot2's own error bound, u^2 sum
+// |w_k y_k|, so the accuracy class is unchanged.
+__device__ __forceinline__ dfv df_dot3_f2s(const float (&wh)[3], const float (&wl)[3], const dfv (&y)[3]) {
+  float s, c, p, e, t;
+  two_prod(wh[0], y[0].h, s, c);
+#pragma unroll
+  for (int k = 1; k < 3; ++k) {
+    two_prod(wh[k], y[k].h, p, e);
+    two_sum(s, p, s, t);
+    c = __fadd_rn(c, __fadd_rn(t, e));
+  }
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    c = __fmaf_rn(wh[k], y[k].l, c);
+    c = __fmaf_rn(wl[k], y[k].h, c);
+  }
+  dfv r;
+  fast_two_sum(s, c, r.h, r.l);
+  return r;
+}
+
 // p + d * y
 __device__ __forceinline__ dfv df_axpy(dfv d, dfv y, dfv p) {
   float q, qe, s, t;
@@ -687,6 +712,11 @@ static __global__ void __launch_bounds__(kPipeThreads)
   const int warp = threadIdx.x >> 5;
   unsigned long long* ring = rhs_ring + (size_t)warp * STAGES * kRhsSlot;
   int emax = 0;
+  // square grids (the east and north weights equal, and west and south):
+  // the paired stencil, (W,S) sums carried from the row before one column
+  // over while the rows stay on the float-float path
+  const bool sq = nx == ny && W.wd[0] == W.wd[2] && W.wd[1] == W.wd[3];
+  const float h3[3] = {wh[0], wh[1], wh[4]}, l3[3] = {wl[0], wl[1], wl[4]};
   struct Row {
     double v[4];
     dfv f[4];
@@ -737,6 +767,10 @@ static __global__ void __launch_bounds__(kPipeThreads)
     load(1, C);
     load(2, N);
     __syncwarp();  // the first rows' slots are refilled from the next row on
+    dfv qa[3];  // (E,N) sums of the previous row at columns c .. c+2
+#pragma unroll
+    for (int k = 0; k < 3; ++k) qa[k] = df_add_loose(S.f[k + 1], C.f[k]);
+    bool carry = true;  // qa holds the previous row's sums
     for (int r = r0; r < r1; ++r) {
       const int i = r - r0;
       issue(i + STAGES);  // into the slot of row q = i, read three rows ago
@@ -751,15 +785,41 @@ static __global__ void __launch_bounds__(kPipeThreads)
       if (__all_sync(0xffffffffu, S.ok && C.ok && N.ok)) {
         const dfv sw = shfl_up_df(C.f[3]);
         const dfv se = shfl_down_df(C.f[0]);
-        const dfv dw = lane == 0 ? df_split_scaled(xw, 0) : sw;
-        const dfv de = lane == 31 ? df_split_scaled(xe, 0) : se;
+        const dfv dh = df_split_scaled(lane == 0 ? xw : xe, 0);  // the halo value of lanes 0 and 31
+        const dfv dw = lane == 0 ? dh : sw;
+        const dfv de = lane == 31 ? dh : se;
+        if (sq) {
+          dfv sen[4];
 #pragma unroll
-        for (int k = 0; k < 4; ++k) {
-          const dfv t[5] = {k == 3 ? de : C.f[k + 1], k == 0 ? dw : C.f[k - 1], N.f[k], S.f[k], C.f[k]};
-          const dfv d = df_dot5(wh, wl, t);
-          res[k] = f2d_scaled(d.h, 0) + f2d_scaled(d.l, 0);
+          for (int k = 0; k < 4; ++k) sen[k] = df_add_loose(k == 3 ? de : C.f[k + 1], N.f[k]);
+          dfv sws[4];
+          sws[0] = df_add_loose(dw, S.f[0]);
+          if (carry) {
+#pragma unroll
+            for (int k = 1; k < 4; ++k) sws[k] = qa[k - 1];
+          } else {
+#pragma unroll
+            for (int k = 1; k < 4; ++k) sws[k] = df_add_loose(C.f[k - 1], S.f[k]);
+          }
+#pragma unroll
+          for (int k = 0; k < 4; ++k) {
+            const dfv t[3] = {sen[k], sws[k], C.f[k]};
+            const dfv d = df_dot3_f2s(h3, l3, t);
+            res[k] = f2d_scaled(d.h, 0) + f2d_scaled(d.l, 0);
+          }
+#pragma unroll
+          for (int k = 0; k < 3; ++k) qa[k] = sen[k];
+          carry = true;
+        } else {
+#pragma unroll
+          for (int k = 0; k < 4; ++k) {
+            const dfv t[5] = {k == 3 ? de : C.f[k + 1], k == 0 ? dw : C.f[k - 1], N.f[k], S.f[k], C.f[k]};
+            const dfv d = df_dot5(wh, wl, t);
+            res[k] = f2d_scaled(d.h, 0) + f2d_scaled(d.l, 0);
+          }
         }
       } else {
+        carry = false;
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
           const double e = k == 3 ? xe : C.v[k + 1], w = k == 0 ? xw : C.v[k - 1];

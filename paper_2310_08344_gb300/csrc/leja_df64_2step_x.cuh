@@ -35,31 +35,6 @@
 
 namespace lexgb {
 
-// sum_{k<3} w_k y_k as df_dot3, with the final renormalisation by Fast2Sum:
-// when |s| >= |c| it is exact; otherwise s has cancelled below the
-// correction c, and the pair misses s + c by at most a unit roundoff of |c|,
-// where |c| is itself of order u sum |w_k y_k| (the products' rounding
-// errors and low parts) -- the order of Dot2's own error bound, u^2 sum
-// |w_k y_k|, so the accuracy class is unchanged.
-__device__ __forceinline__ dfv df_dot3_f2s(const float (&wh)[3], const float (&wl)[3], const dfv (&y)[3]) {
-  float s, c, p, e, t;
-  two_prod(wh[0], y[0].h, s, c);
-#pragma unroll
-  for (int k = 1; k < 3; ++k) {
-    two_prod(wh[k], y[k].h, p, e);
-    two_sum(s, p, s, t);
-    c = __fadd_rn(c, __fadd_rn(t, e));
-  }
-#pragma unroll
-  for (int k = 0; k < 3; ++k) {
-    c = __fmaf_rn(wh[k], y[k].l, c);
-    c = __fmaf_rn(wl[k], y[k].h, c);
-  }
-  dfv r;
-  fast_two_sum(s, c, r.h, r.l);
-  return r;
-}
-
 // p + d1 y1 + d2 y2 as one compensated sum (exact products, error-free
 // additions of the leading parts, the remaining terms accumulated in float;
 // the final renormalisation by Fast2Sum, as in df_dot3_f2s).

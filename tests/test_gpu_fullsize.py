@@ -16,7 +16,7 @@ interval (the oracle's power bound):
   FP64 (the mixed form's error against the FP64 oracle is reported);
 * the paper's Problem I at 4096^2 on its own discretisation (third-order
   upwind gradient, [-1,1)^2), exp(hA)u at h = 100 dt_CFL, tol 1e-12, on the
-  two-step upwind kernel.
+  issue-lean and first two-step upwind kernels.
 
 Bar: relative L2 <= 1e-10 and the same Leja iteration count +-1 (+-2 for
 EXPRB32's two loops); the error estimate to 1e-6 relative (the oracle forms
@@ -142,7 +142,8 @@ def test_exprb32_burgers_2048_matches_oracle(lx, burgers2048, prec):
 
 
 # ------------------------------------------------------ Problem I at 4096^2
-def test_problem1_4096_two_step_upwind_matches_oracle(lx, xi_oracle):
+@pytest.fixture(scope="module")
+def problem1_4096(xi_oracle):
     nu, a, n, tol = 1.0, 10.0, 4096, 1e-12
     u0 = synth.problem1_ic(n, n)
     v0 = synth.power_start(n * n, seed=5)
@@ -152,16 +153,24 @@ def test_problem1_4096_two_step_upwind_matches_oracle(lx, xi_oracle):
     h = 100 * synth.cfl_step_pm1(n, n, nu, a)
     ref, it_o, st_o = oracle.leja_phi(oracle.ADVDIFF_UP3, n, n, nu, a, None, 0, u0, c, g, h, tol, tol, xi_oracle)
     assert st_o == 0
+    return dict(nu=nu, a=a, n=n, tol=tol, u0=u0, v0=v0, rho=rho, passes=passes, c=c, g=g, h=h, ref=ref, it=it_o)
+
+
+@pytest.mark.parametrize("kernel", ["leja_iter_df_pipe2x_up3_b3", "leja_iter_df_pipe2_up3_b3"])
+def test_problem1_4096_two_step_upwind_matches_oracle(lx, problem1_4096, kernel):
+    d = problem1_4096
+    n, nu, a, tol = d["n"], d["nu"], d["a"], d["tol"]
+    c, g, h = d["c"], d["g"], d["h"]
     ctx = lx.leja_setup(n, n, nu, a, lx.ADVDIFF_UP3, lx.DF64)
-    assert lx.lx_ctx_select_kernel(ctx, "leja_iter_df_pipe2_up3_b3", 0) == 0
+    assert lx.lx_ctx_select_kernel(ctx, kernel, 0) == 0
     assert lx.lx_ctx_iters_per_launch(ctx) == 2
-    st, rho_g, passes_g = lx.power_bound(ctx, None, dev(v0), 10)
-    assert st == 0 and passes_g == passes and abs(rho_g - rho) <= 1e-12 * rho
+    st, rho_g, passes_g = lx.power_bound(ctx, None, dev(d["v0"]), 10)
+    assert st == 0 and passes_g == d["passes"] and abs(rho_g - d["rho"]) <= 1e-12 * d["rho"]
     out = torch.empty(n * n, dtype=torch.float64, device="cuda")
-    st, it = lx.phi_l_apply(ctx, 0, None, dev(u0), out, c, g, h, tol, tol)
+    st, it = lx.phi_l_apply(ctx, 0, None, dev(d["u0"]), out, c, g, h, tol, tol)
     assert st == 0
-    e = rel(out.cpu().numpy(), ref)
-    print(f"Problem I 4096^2 two-step upwind: iters {it} (oracle {it_o}), rel_l2 vs oracle {e:.3e}")
-    assert abs(it - it_o) <= 1
+    e = rel(out.cpu().numpy(), d["ref"])
+    print(f"Problem I 4096^2 {kernel}: iters {it} (oracle {d['it']}), rel_l2 vs oracle {e:.3e}")
+    assert abs(it - d["it"]) <= 1
     assert e <= TOL
     ctx.close()
