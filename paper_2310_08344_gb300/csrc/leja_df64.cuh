@@ -66,7 +66,11 @@ __device__ __forceinline__ double df_to_double(dfv a) { return (double)a.h + (do
 // x * 2^-k split into hi + lo floats with integer operations only (no FP64
 // pipe work): hi keeps the leading 24 significant bits (truncated), lo the
 // next 24 of the remaining 29 (rounded).  Values whose scaled magnitude is
-// below 2^-126 become 0; above the float range, +-inf; NaN stays NaN.
+// below 2^-126 become 0; above the float range, +-inf; NaN stays NaN.  lo is
+// scaled in two steps, by 2^-29 and then by 2^(ef - 23), so that it stays
+// exact down to a scaled magnitude of 2^-103 (a one-step scale by
+// 2^(ef - 52) is not a normal float below 2^-74, which would leave the
+// value with its leading 24 bits only).
 __device__ __forceinline__ dfv df_split_scaled(double x, int k) {
   const unsigned long long b = (unsigned long long)__double_as_longlong(x);
   const unsigned sign = (unsigned)(b >> 32) & 0x80000000u;
@@ -79,9 +83,9 @@ __device__ __forceinline__ dfv df_split_scaled(double x, int k) {
   dfv r;
   r.h = __int_as_float((int)(sign | ((unsigned)(ef + 127) << 23) | (unsigned)(mant >> 29)));
   const unsigned rest = (unsigned)(mant & 0x1fffffffULL);  // value rest * 2^(ef - 52)
-  const int el = ef - 52 + 127;
+  const int el = ef - 23 + 127;
   const float scale = el >= 1 ? __int_as_float((int)(sign | ((unsigned)el << 23))) : 0.f;
-  r.l = __uint2float_rn(rest) * scale;
+  r.l = (__uint2float_rn(rest) * 0x1p-29f) * scale;
   return r;
 }
 
@@ -89,13 +93,15 @@ __device__ __forceinline__ dfv df_split_scaled(double x, int k) {
 // around it instead of evaluating it (on the FP64 pipe) for every value.
 static __device__ __noinline__ double f2d_scaled_slow(float f, int k) { return (double)f * pow2(k); }
 
-// Exact float -> double by integer operations (zero and subnormals -> 0;
+// Exact float -> double by integer operations (zero -> 0; subnormals,
 // infinities and NaN through the conversion instruction), then scaled by 2^k
-// through the exponent field when that stays in range.
+// through the exponent field when that stays in range.  Subnormals matter
+// where results are small without scaling (the low float of a value below
+// about 2^-102 is one).
 __device__ __forceinline__ double f2d_scaled(float f, int k) {
   const unsigned b = __float_as_uint(f);
   const int e = (int)((b >> 23) & 0xffu);
-  if (e == 0) return 0.0;
+  if (e == 0) return (b & 0x7fffffu) ? f2d_scaled_slow(f, k) : 0.0;
   const int ed = e + 896 + k;
   if (e == 0xff || ed < 1 || ed > 2046) return f2d_scaled_slow(f, k);
   const unsigned long long db = ((unsigned long long)(b & 0x80000000u) << 32) | ((unsigned long long)ed << 52) |
@@ -684,19 +690,26 @@ __device__ __forceinline__ bool df_in_range(double x) {
 // 128-column strips; the input rows are staged into shared memory by
 // cp.async STAGES - 3 rows ahead of use (a per-warp ring of raw double rows
 // with a one-point halo per side), so that loads overlap the float-float
-// arithmetic; each lane keeps four consecutive points of three rows in
-// registers, so every value is split into floats once.  A row whose inputs
-// include a value outside the float range is computed in double by the
-// whole warp.  Records the largest exponent of the result like
-// rhs_df_advdiff_kernel.  Four warps per block; dynamic shared memory
-// rhs_ring_smem_bytes<STAGES>().
+// arithmetic.  Each lane keeps the float-float splits of its four points of
+// the centre and north rows in registers (every value is split once); a row
+// whose inputs include a value outside the float-float range is computed in
+// double by the whole warp from the input re-read in global memory.  Records
+// the largest exponent of the result like rhs_df_advdiff_kernel.
+// SQ (square grids with the east and north weights equal, and the west and
+// south ones): the paired stencil w_E (y_E + y_N) + w_W (y_W + y_S) +
+// w_C y_C; the (W,S) sums at columns c+1 .. c+3 are the (E,N) sums of the
+// row before at c .. c+2 (the same two operands, so the same values), which
+// are formed on every row, so that the carry stays valid across rows
+// computed in double (a row on the float-float path has all its inputs, and
+// so those of the carried sums, in range).  Four warps per block; dynamic
+// shared memory rhs_ring_smem_bytes<STAGES>().
 constexpr int kRhsSlot = kPipeRow + 4;  // [pad][w1][128 points][e1][pad]
 template <int STAGES>
 constexpr int rhs_ring_smem_bytes() {
   return kPipeWarps * STAGES * kRhsSlot * 8;
 }
 
-template <int STAGES>
+template <int STAGES, bool SQ>
 static __global__ void __launch_bounds__(kPipeThreads)
     rhs_df_advdiff_ring_kernel(int nx, int ny, const double* __restrict__ u, RhsWeights W,
                                double* __restrict__ f_out, LoopState* st, const double* __restrict__ src, double h) {
@@ -712,17 +725,7 @@ static __global__ void __launch_bounds__(kPipeThreads)
   const int warp = threadIdx.x >> 5;
   unsigned long long* ring = rhs_ring + (size_t)warp * STAGES * kRhsSlot;
   int emax = 0;
-  // square grids (the east and north weights equal, and west and south):
-  // the paired stencil, (W,S) sums carried from the row before one column
-  // over while the rows stay on the float-float path
-  const bool sq = nx == ny && W.wd[0] == W.wd[2] && W.wd[1] == W.wd[3];
   const float h3[3] = {wh[0], wh[1], wh[4]}, l3[3] = {wl[0], wl[1], wl[4]};
-  struct Row {
-    double v[4];
-    dfv f[4];
-    double hx;
-    bool ok;
-  };
   for_each_segment(nx, ny, 0, blockIdx.x * kPipeWarps + warp, gridDim.x * kPipeWarps, [&](int col0, int r0, int r1) {
     const int c = col0 + lane * 4;
     const int cw = col0 == 0 ? nx - 1 : col0 - 1;
@@ -742,89 +745,85 @@ static __global__ void __launch_bounds__(kPipeThreads)
       }
       cp_commit();
     };
-    auto load = [&](int q, Row& R) {
+    // the lane's four values of staged row q, split; whether all are in range
+    auto load = [&](int q, dfv(&f)[4]) {
       const unsigned long long* s = slot(q);
       const double2 a = *reinterpret_cast<const double2*>(s + 2 + lane * 4);
       const double2 b = *reinterpret_cast<const double2*>(s + 4 + lane * 4);
-      R.v[0] = a.x;
-      R.v[1] = a.y;
-      R.v[2] = b.x;
-      R.v[3] = b.y;
-      R.hx = lane == 0 ? __longlong_as_double((long long)s[1])
-                       : (lane == 31 ? __longlong_as_double((long long)s[2 + kPipeRow]) : 0.0);
-      R.ok = df_in_range(R.hx);
+      const double v[4] = {a.x, a.y, b.x, b.y};
+      bool ok = true;
 #pragma unroll
       for (int k = 0; k < 4; ++k) {
-        R.ok = R.ok && df_in_range(R.v[k]);
-        R.f[k] = df_split_scaled(R.v[k], 0);
+        ok = ok && df_in_range(v[k]);
+        f[k] = df_split_scaled(v[k], 0);
       }
+      return ok;
     };
     for (int q = 0; q < STAGES; ++q) issue(q);
     cp_wait<STAGES - 3>();
     __syncwarp();
-    Row S, C, N, NN;
-    load(0, S);
-    load(1, C);
-    load(2, N);
-    __syncwarp();  // the first rows' slots are refilled from the next row on
-    dfv qa[3];  // (E,N) sums of the previous row at columns c .. c+2
+    dfv S[4], C[4], N[4];  // SQ: only S[0] is kept after the first row
+    bool okS = load(0, S), okC = load(1, C), okN = load(2, N);
+    dfv qa[3];  // SQ: the (E,N) sums of the previous row at columns c .. c+2
+    if constexpr (SQ) {
 #pragma unroll
-    for (int k = 0; k < 3; ++k) qa[k] = df_add_loose(S.f[k + 1], C.f[k]);
-    bool carry = true;  // qa holds the previous row's sums
+      for (int k = 0; k < 3; ++k) qa[k] = df_add_loose(S[k + 1], C[k]);
+    }
     for (int r = r0; r < r1; ++r) {
       const int i = r - r0;
-      issue(i + STAGES);  // into the slot of row q = i, read three rows ago
+      issue(i + STAGES);  // into the slot of row q = i, whose values are in registers
       cp_wait<STAGES - 3>();
       __syncwarp();
-      if (r + 1 < r1) load(i + 3, NN);
-      const double xw0 = __shfl_up_sync(0xffffffffu, C.v[3], 1);
-      const double xe0 = __shfl_down_sync(0xffffffffu, C.v[0], 1);
-      const double xw = lane == 0 ? C.hx : xw0;
-      const double xe = lane == 31 ? C.hx : xe0;
+      // the strip's halo value of row r: lane 0 west, lane 31 east (each
+      // reads only the word its own copy wrote)
+      const unsigned long long* scn = slot(i + 1);
+      const double hx = lane == 0 ? __longlong_as_double((long long)scn[1])
+                                  : (lane == 31 ? __longlong_as_double((long long)scn[2 + kPipeRow]) : 0.0);
+      const bool okH = df_in_range(hx);
+      dfv sen[4];
+      if constexpr (SQ) {
+#pragma unroll
+        for (int k = 0; k < 3; ++k) sen[k] = df_add_loose(C[k + 1], N[k]);
+      }
       double res[4];
-      if (__all_sync(0xffffffffu, S.ok && C.ok && N.ok)) {
-        const dfv sw = shfl_up_df(C.f[3]);
-        const dfv se = shfl_down_df(C.f[0]);
-        const dfv dh = df_split_scaled(lane == 0 ? xw : xe, 0);  // the halo value of lanes 0 and 31
+      if (__all_sync(0xffffffffu, okS && okC && okN && okH)) {
+        const dfv sw = shfl_up_df(C[3]);
+        const dfv se = shfl_down_df(C[0]);
+        const dfv dh = df_split_scaled(hx, 0);
         const dfv dw = lane == 0 ? dh : sw;
         const dfv de = lane == 31 ? dh : se;
-        if (sq) {
-          dfv sen[4];
-#pragma unroll
-          for (int k = 0; k < 4; ++k) sen[k] = df_add_loose(k == 3 ? de : C.f[k + 1], N.f[k]);
-          dfv sws[4];
-          sws[0] = df_add_loose(dw, S.f[0]);
-          if (carry) {
-#pragma unroll
-            for (int k = 1; k < 4; ++k) sws[k] = qa[k - 1];
-          } else {
-#pragma unroll
-            for (int k = 1; k < 4; ++k) sws[k] = df_add_loose(C.f[k - 1], S.f[k]);
-          }
+        if constexpr (SQ) {
+          sen[3] = df_add_loose(de, N[3]);
+          const dfv sws0 = df_add_loose(dw, S[0]);
 #pragma unroll
           for (int k = 0; k < 4; ++k) {
-            const dfv t[3] = {sen[k], sws[k], C.f[k]};
+            const dfv t[3] = {sen[k], k == 0 ? sws0 : qa[k - 1], C[k]};
             const dfv d = df_dot3_f2s(h3, l3, t);
             res[k] = f2d_scaled(d.h, 0) + f2d_scaled(d.l, 0);
           }
-#pragma unroll
-          for (int k = 0; k < 3; ++k) qa[k] = sen[k];
-          carry = true;
         } else {
 #pragma unroll
           for (int k = 0; k < 4; ++k) {
-            const dfv t[5] = {k == 3 ? de : C.f[k + 1], k == 0 ? dw : C.f[k - 1], N.f[k], S.f[k], C.f[k]};
+            const dfv t[5] = {k == 3 ? de : C[k + 1], k == 0 ? dw : C[k - 1], N[k], S[k], C[k]};
             const dfv d = df_dot5(wh, wl, t);
             res[k] = f2d_scaled(d.h, 0) + f2d_scaled(d.l, 0);
           }
         }
       } else {
-        carry = false;
+        // in double, from the input rows r - 1, r, r + 1 in global memory
+        const int rs = r == 0 ? ny - 1 : r - 1, rn = r + 1 == ny ? 0 : r + 1;
+        const double* rowC = u + (size_t)r * nx;
+        const double* rowS = u + (size_t)rs * nx;
+        const double* rowN = u + (size_t)rn * nx;
+        double vc[6];
+        vc[0] = __ldg(rowC + (lane == 0 ? cw : c - 1));
+        vc[5] = __ldg(rowC + (lane == 31 ? ce : c + 4));
 #pragma unroll
-        for (int k = 0; k < 4; ++k) {
-          const double e = k == 3 ? xe : C.v[k + 1], w = k == 0 ? xw : C.v[k - 1];
-          res[k] = wd[0] * e + wd[1] * w + wd[2] * N.v[k] + wd[3] * S.v[k] + wd[4] * C.v[k];
-        }
+        for (int k = 0; k < 4; ++k) vc[k + 1] = __ldg(rowC + c + k);
+#pragma unroll
+        for (int k = 0; k < 4; ++k)
+          res[k] = wd[0] * vc[k + 2] + wd[1] * vc[k] + wd[2] * __ldg(rowN + c + k) + wd[3] * __ldg(rowS + c + k) +
+                   wd[4] * vc[k + 1];
       }
       const size_t ro = (size_t)r * nx + c;
       if (src) {
@@ -839,9 +838,21 @@ static __global__ void __launch_bounds__(kPipeThreads)
       *reinterpret_cast<double2*>(f_out + ro + 2) = make_double2(res[2], res[3]);
 #pragma unroll
       for (int k = 0; k < 4; ++k) emax = max(emax, (int)((__double2hiint(res[k]) >> 20) & 0x7ff));
-      S = C;
-      C = N;
-      N = NN;
+      // next row: S <- C, C <- N, N <- staged row q = i + 3 (complete since
+      // this row's wait)
+      if constexpr (SQ) {
+#pragma unroll
+        for (int k = 0; k < 3; ++k) qa[k] = sen[k];
+        S[0] = C[0];
+      } else {
+#pragma unroll
+        for (int k = 0; k < 4; ++k) S[k] = C[k];
+      }
+#pragma unroll
+      for (int k = 0; k < 4; ++k) C[k] = N[k];
+      okS = okC;
+      okC = okN;
+      if (r + 1 < r1) okN = load(i + 3, N);
     }
     cp_wait<0>();
     __syncwarp();

@@ -1353,14 +1353,24 @@ lx_status expint_step(lx_ctx* c, const double* u, double* u_low, double* u_high,
       // least 4 rows per warp
       int per_sm = 0;
       constexpr int kRhsStages = 6;
-      LX_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, rhs_df_advdiff_ring_kernel<kRhsStages>,
-                                                            kPipeThreads, rhs_ring_smem_bytes<kRhsStages>()));
+      // square grids with equal east/north and west/south weights: the
+      // paired stencil
+      const bool sq = P.nx == P.ny && W.wd[0] == W.wd[2] && W.wd[1] == W.wd[3];
+      const void* rk = sq ? reinterpret_cast<const void*>(&rhs_df_advdiff_ring_kernel<kRhsStages, true>)
+                          : reinterpret_cast<const void*>(&rhs_df_advdiff_ring_kernel<kRhsStages, false>);
+      LX_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, rk, kPipeThreads,
+                                                            rhs_ring_smem_bytes<kRhsStages>()));
       const long long lines = (long long)(P.nx / kPipeRow) * P.ny;
       const int GR = (int)std::max<long long>(
           1, std::min<long long>((lines / 4 + kPipeWarps - 1) / kPipeWarps,
                                  (long long)std::max(per_sm, 1) * c->sm_count));
-      rhs_df_advdiff_ring_kernel<kRhsStages><<<GR, kPipeThreads, rhs_ring_smem_bytes<kRhsStages>(), c->stream>>>(
-          P.nx, P.ny, u, W, c->d_f, c->d_state, c->d_src, h);
+      if (sq)
+        rhs_df_advdiff_ring_kernel<kRhsStages, true><<<GR, kPipeThreads, rhs_ring_smem_bytes<kRhsStages>(), c->stream>>>(
+            P.nx, P.ny, u, W, c->d_f, c->d_state, c->d_src, h);
+      else
+        rhs_df_advdiff_ring_kernel<kRhsStages, false>
+            <<<GR, kPipeThreads, rhs_ring_smem_bytes<kRhsStages>(), c->stream>>>(P.nx, P.ny, u, W, c->d_f,
+                                                                                  c->d_state, c->d_src, h);
     } else {
       rhs_df_advdiff_kernel<<<G, kThreadsPerBlock, 0, c->stream>>>(c->geo, u, W, c->d_f, c->d_state, c->d_src, h);
     }

@@ -249,15 +249,17 @@ def test_expint_step_with_source(lx, xi_oracle, kind, integ, n, prec):
     assert st == 0 and rel(hi.cpu().numpy(), ref0) <= TOL
 
 
-@pytest.mark.parametrize("nx,ny", [(128, 100), (256, 7)])
-@pytest.mark.parametrize("scale", [1.0, 1e100, 1e-100])
+@pytest.mark.parametrize("nx,ny", [(128, 100), (256, 7), (128, 128)])
+@pytest.mark.parametrize("scale", [1.0, 1e100, 1e-100, 1e-25, 1e-29])
 @pytest.mark.parametrize("offset", [0, 1])
 def test_df64_ros_eu_rhs_forms(lx, xi_oracle, nx, ny, scale, offset):
     # the float-float Rosenbrock-Euler path: row-window h A u (aligned input,
-    # nx % 128 == 0) or the point-wise fallback (offset view), and inputs far
-    # outside the float range (computed in double inside the same kernels).
-    # 1e+-100: outside the float range, while the oracle's sums of squares
-    # still fit in a double.
+    # nx % 128 == 0; the paired stencil on the square grid) or the point-wise
+    # fallback (offset view), and inputs far outside the float range
+    # (computed in double inside the same kernels).  1e+-100: outside the
+    # float range, while the oracle's sums of squares still fit in a double.
+    # 1e-25 and 1e-29: inside the range, where the low float of each split
+    # lies below 2^-126 unless it is scaled in two steps.
     nu, a = 1e-2, 0.5
     u = synth.gaussians_ic(nx, ny, seed=12) + 0.1
     h = 30 * synth.cfl_step(nx, ny, nu, a)
@@ -273,6 +275,33 @@ def test_df64_ros_eu_rhs_forms(lx, xi_oracle, nx, ny, scale, offset):
     ref, it_o, st_o = oracle.ros_eu(0, nx, ny, nu, a, u * scale, c, g, h, TOL, TOL * scale, xi_oracle)
     assert st == 0 and st_o == 0 and abs(it - it_o) <= 1 and it_o > 5
     assert rel(hi.cpu().numpy(), ref) <= TOL
+
+
+@pytest.mark.parametrize("nx,ny", [(256, 256), (256, 192)])
+def test_df64_ros_eu_rhs_mixed_range(lx, xi_oracle, nx, ny):
+    # a band of rows far below the float range: the right-hand side computes
+    # the rows that touch it in double and the others in float-float, and on
+    # the square grid the carried pair sums pass through the double rows
+    nu, a = 1e-2, 0.5
+    u = synth.gaussians_ic(nx, ny, seed=13) + 0.1
+    u.reshape(ny, nx)[40:47] *= 1e-120
+    u.reshape(ny, nx)[100, 5:9] *= 1e-120  # a few points of one row
+    h = 30 * synth.cfl_step(nx, ny, nu, a)
+    import fourier
+
+    c, g = oracle.spectral_interval(fourier.spectral_radius(nx, ny, nu, a))
+    ctx = lx.leja_setup(nx, ny, nu, a, lx.ADVDIFF, lx.DF64, lx.ROS_EU)
+    hi = torch.empty(nx * ny, dtype=torch.float64, device="cuda")
+    st, err, it = lx.expint_step(ctx, dev(u), None, hi, c, g, h, TOL, TOL)
+    ref, it_o, st_o = oracle.ros_eu(0, nx, ny, nu, a, u, c, g, h, TOL, TOL, xi_oracle)
+    assert st == 0 and st_o == 0 and abs(it - it_o) <= 1
+    got = hi.cpu().numpy()
+    assert rel(got, ref) <= TOL
+    # the rows away from the band, on their own scale
+    far = np.ones((ny, nx), bool)
+    far[30:57] = False
+    far[90:111] = False
+    assert rel(got.reshape(ny, nx)[far], ref.reshape(ny, nx)[far]) <= TOL
 
 
 def test_expint_step_host_buffers(lx, xi_oracle):
