@@ -678,11 +678,28 @@ __device__ __forceinline__ void df_strip_pipe(const LoopArgs& A, const S* __rest
   __syncwarp();
 }
 
-// Whether a double lies in the range where the float-float right-hand side
-// applies (|x| in [2^-100, 2^100), or zero).
-__device__ __forceinline__ bool df_in_range(double x) {
-  const int ex = (int)((__double_as_longlong(x) >> 52) & 0x7ff);
-  return ex == 0 || (ex > 1023 - 100 && ex < 1023 + 100);
+// Split for the right-hand side's float-float rows, without branches or
+// conversion instructions: x with |x| in [2^-99, 2^100), or zero (a
+// subnormal counts as zero); ok reports whether x is one of them (a value
+// outside gives an unspecified pair, and its row is computed in double).
+// hi: the leading 24 bits (truncated), from the bits shifted left by 3 with
+// the exponent rebased modulo 2^9 (exact over the range); lo: the remaining
+// 29 bits rounded to 23, as the float whose bits are those of
+// M = +-2^(e-23) plus the rounded bits, minus M (exact: the two lie within a
+// factor of 2).  |x - hi - lo| <= 2^-47 |x|.
+__device__ __forceinline__ dfv df_split_rhs(double x, bool& ok) {
+  const unsigned hi = (unsigned)__double2hiint(x), lo = (unsigned)__double2loint(x);
+  const unsigned a = hi & 0x7ff00000u;
+  ok = a == 0u || (a - (924u << 20)) < (199u << 20);
+  const unsigned t = __funnelshift_l(lo, hi, 3);
+  const unsigned sign = hi & 0x80000000u;
+  const unsigned mb = ((t & 0xff800000u) - (407u << 23)) | sign;
+  const unsigned r = ((lo & 0x1fffffffu) + 32u) >> 6;
+  const float l = __fsub_rn(__uint_as_float(mb + r), __uint_as_float(mb));
+  dfv v;
+  v.h = __uint_as_float(a ? ((t - 0xC0000000u) | sign) : sign);
+  v.l = a ? l : 0.f;
+  return v;
 }
 
 // h A u (+ h S) for the diffusion-advection operator when nx % 128 == 0 and
@@ -754,8 +771,9 @@ static __global__ void __launch_bounds__(kPipeThreads)
       bool ok = true;
 #pragma unroll
       for (int k = 0; k < 4; ++k) {
-        ok = ok && df_in_range(v[k]);
-        f[k] = df_split_scaled(v[k], 0);
+        bool okk;
+        f[k] = df_split_rhs(v[k], okk);
+        ok = ok && okk;
       }
       return ok;
     };
@@ -779,7 +797,8 @@ static __global__ void __launch_bounds__(kPipeThreads)
       const unsigned long long* scn = slot(i + 1);
       const double hx = lane == 0 ? __longlong_as_double((long long)scn[1])
                                   : (lane == 31 ? __longlong_as_double((long long)scn[2 + kPipeRow]) : 0.0);
-      const bool okH = df_in_range(hx);
+      bool okH;
+      const dfv dh = df_split_rhs(hx, okH);
       dfv sen[4];
       if constexpr (SQ) {
 #pragma unroll
@@ -789,7 +808,6 @@ static __global__ void __launch_bounds__(kPipeThreads)
       if (__all_sync(0xffffffffu, okS && okC && okN && okH)) {
         const dfv sw = shfl_up_df(C[3]);
         const dfv se = shfl_down_df(C[0]);
-        const dfv dh = df_split_scaled(hx, 0);
         const dfv dw = lane == 0 ? dh : sw;
         const dfv de = lane == 31 ? dh : se;
         if constexpr (SQ) {
