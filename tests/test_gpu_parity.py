@@ -250,7 +250,7 @@ def test_expint_step_with_source(lx, xi_oracle, kind, integ, n, prec):
 
 
 @pytest.mark.parametrize("nx,ny", [(128, 100), (256, 7), (128, 128)])
-@pytest.mark.parametrize("scale", [1.0, 1e100, 1e-100, 1e-25, 1e-29])
+@pytest.mark.parametrize("scale", [1.0, 1e100, 1e-100, 1e-25, 1e-29, 2e30])
 @pytest.mark.parametrize("offset", [0, 1])
 def test_df64_ros_eu_rhs_forms(lx, xi_oracle, nx, ny, scale, offset):
     # the float-float Rosenbrock-Euler path: row-window h A u (aligned input,
@@ -259,7 +259,9 @@ def test_df64_ros_eu_rhs_forms(lx, xi_oracle, nx, ny, scale, offset):
     # (computed in double inside the same kernels).  1e+-100: outside the
     # float range, while the oracle's sums of squares still fit in a double.
     # 1e-25 and 1e-29: inside the range, where the low float of each split
-    # lies below 2^-126 unless it is scaled in two steps.
+    # lies below 2^-126 unless it is scaled in two steps; 1e-29 and 2e30 put
+    # the state across the lower (2^-99) and upper (2^100) ends of the range
+    # of the row-window form, so that some rows are computed in double.
     nu, a = 1e-2, 0.5
     u = synth.gaussians_ic(nx, ny, seed=12) + 0.1
     h = 30 * synth.cfl_step(nx, ny, nu, a)
